@@ -1,0 +1,187 @@
+/*
+ * nlfeti -- one-level FETI for finite element discretizations of nonlocal diffusion
+ * (integrable and fractional kernels) and bond-based peridynamics, on one GPU.
+ *
+ * C ABI.  All entry points return an nlfeti_status and never throw.  On error the
+ * outputs are left untouched and nlfeti_last_error(ctx) describes the failure.
+ *
+ * Problem statement (the calls follow it): given a P1 mesh of the unit domain and
+ * its Dirichlet collar, a kernel with horizon delta, and a local decomposition into
+ * K parts, solve A u = f - B g (Sec. 2.3.3, eq. weak_nonloc-h) with the one-level
+ * FETI method (Algorithm 1) on the nonlocal subdivision built from the local parts
+ * (Sec. 5.1).  Outputs are nodal values.
+ *
+ * Memory: the caller owns every host array and every device array it passes; the
+ * library copies what it needs before a call returns (except *_device calls, which
+ * read and write the caller's device buffers on the context's stream).  Device
+ * memory of the library comes from the dev_alloc/dev_free callbacks given to
+ * nlfeti_create (or cudaMalloc/cudaFree when they are NULL).
+ *
+ * Threads: a context and its problems are not thread-safe; a server is (one
+ * submit/wait mutex, one worker thread).
+ */
+#ifndef NLFETI_H
+#define NLFETI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nlfeti_ctx nlfeti_ctx;
+typedef struct nlfeti_problem nlfeti_problem;
+typedef struct nlfeti_server nlfeti_server;
+typedef uint64_t nlfeti_ticket;
+
+typedef enum {
+    NLFETI_OK = 0,
+    NLFETI_E_INVALID = -1,        /* malformed input (sizes, indices, decomposition) */
+    NLFETI_E_NOMEM = -2,          /* device allocation failed / over the HBM budget */
+    NLFETI_E_NOT_SPD = -3,        /* a pivot block was not positive definite */
+    NLFETI_E_NOT_CONVERGED = -4,  /* PCG or refinement hit its iteration limit */
+    NLFETI_E_TIMEOUT = -5,        /* a wait ran out of time */
+    NLFETI_E_CUDA = -6,           /* a CUDA call failed */
+    NLFETI_E_BUSY = -7            /* no free server slot */
+} nlfeti_status;
+
+/* Kernel types (Sec. 6.1). */
+enum {
+    NLFETI_K_CONST_LINF = 0,      /* constant, l-infinity ball (1-D: the interval |x-y|<=delta); eq. constantkernel */
+    NLFETI_K_CONST_L2 = 1,        /* constant, l2 ball approximated by the nocaps polygon (Fig. approximate-ball e) */
+    NLFETI_K_FRACTIONAL = 2,      /* c |x-y|^-(d+2s), l2 ball, nocaps; eq. fractionalkernel */
+    NLFETI_K_PERIDYNAMIC = 3      /* c (x-y)(x-y)^T/|x-y|^3, l2 ball, nocaps, 2 dofs per node; eq. peridynamics */
+};
+
+/* Mesh (Sec. 2.3.1): P1 simplices covering the domain and its Dirichlet collar.
+ * xy: dim*n_nodes doubles, node-major.  elems: (dim+1)*n_elems int32 node ids
+ * (triangles counter-clockwise).  node_is_dirichlet: 1 for nodes in the closed
+ * collar Gamma^D_h.  elem_is_dirichlet: 1 for elements of the collar. */
+typedef struct {
+    int dim;
+    int64_t n_nodes;
+    const double *xy;
+    int64_t n_elems;
+    const int32_t *elems;
+    const int8_t *node_is_dirichlet;
+    const int8_t *elem_is_dirichlet;
+} nlfeti_mesh;
+
+/* Kernel: type, horizon delta, fractional order s (type 2 only) and constant c
+ * (scale > 0 required; the library does not pick a default). */
+typedef struct {
+    int type;
+    double delta;
+    double s;
+    double scale;
+} nlfeti_kernel;
+
+/* Local decomposition (Sec. 5.1): K parts, one label in [0, K) per non-Dirichlet
+ * element (labels of collar elements are ignored).  K <= 64. */
+typedef struct {
+    int32_t K;
+    const int32_t *elem_subdomain;
+} nlfeti_decomp;
+
+/* Solver options.
+ * precision: 0 = FP64 operators throughout ("plain"); 1 = FP32 subdomain operators
+ *            with FP64 PCG vectors, coarse problem and iterative refinement ("mixed").
+ * tol: PCG stop when ||P r||_2 <= tol ||P d||_2 per right-hand side (FP64 path);
+ *      the mixed path uses inner_tol per refinement sweep and refine_tol on the
+ *      relative nodal correction.
+ * batched: 1 = one launch per stage over all subdomains (graph-captured loop);
+ *          0 = one launch per subdomain per stage, no graphs (baseline). */
+typedef struct {
+    int precision;
+    double tol;
+    int max_it;
+    int max_refine;
+    double inner_tol;
+    double refine_tol;
+    int batched;
+    size_t hbm_budget;
+} nlfeti_options;
+
+typedef struct {
+    int iterations;            /* PCG iterations summed over refinement sweeps (max over RHS) */
+    int refine_sweeps;
+    double final_rel_residual; /* last ||P r|| / ||P d|| (max over RHS) */
+    double rel_correction;     /* last relative nodal correction (mixed path) */
+    double ms_setup, ms_factor, ms_solve;
+} nlfeti_stats;
+
+/* Sizes of a created problem. */
+typedef struct {
+    int32_t K, ncomp, n_floating, n_coarse;
+    int64_t n_lambda, n_u, sum_nk, sum_nk2, sum_ngamma2;
+    int32_t max_nk, max_ngamma;
+} nlfeti_info;
+
+/* Default options: FP64 plain, tol 1e-10, max_it 1000, 4 refinement sweeps,
+ * inner_tol 1e-6, refine_tol 1e-10, batched. */
+void nlfeti_default_options(nlfeti_options *opt);
+
+/* Context on the given CUDA stream (cudaStream_t, NULL = the legacy stream).
+ * dev_alloc(size, user) / dev_free(ptr, user): optional device allocator. */
+nlfeti_status nlfeti_create(nlfeti_ctx **out, const nlfeti_options *opt, void *cuda_stream,
+                            void *(*dev_alloc)(size_t, void *), void (*dev_free)(void *, void *), void *alloc_user);
+void nlfeti_destroy(nlfeti_ctx *ctx);
+const char *nlfeti_last_error(const nlfeti_ctx *ctx);
+
+/* Build the nonlocal subdivision (Sec. 5.1: delta/2 extension of each local part,
+ * Gamma^D_k within delta, zeta, Omega_k / Gamma_k dofs, B, B_D, Z) on the host,
+ * upload it, and assemble every subdomain matrix A^k on the GPU (eq.
+ * bilinear-multi1, kernel weighted by 1/zeta).  Setup is synchronous. */
+nlfeti_status nlfeti_problem_create(nlfeti_ctx *ctx, const nlfeti_mesh *mesh, const nlfeti_kernel *kernel,
+                                    const nlfeti_decomp *decomp, nlfeti_problem **out);
+void nlfeti_problem_destroy(nlfeti_problem *p);
+nlfeti_status nlfeti_problem_info(const nlfeti_problem *p, nlfeti_info *info);
+nlfeti_status nlfeti_problem_set_options(nlfeti_problem *p, const nlfeti_options *opt);
+
+/* Factor the subdomain operators (eq. splittingBlockCholesky, eq. subSchurComplement,
+ * Sec. 5.3): per subdomain A_OO^-1, A_GO A_OO^-1 and the Schur complement S_k, the
+ * pseudo-inverse S_k^+ (pinning + projection on ker Z_k^T), and (G^T G)^-1.
+ * precision_mask: bit 0 = FP64 operators, bit 1 = FP32 operators. */
+nlfeti_status nlfeti_factor(nlfeti_problem *p, int precision_mask);
+
+/* Solve for nrhs right-hand sides (host arrays).  rhs: n_nodes*ncomp x nrhs,
+ * column-major; rhs_kind 0 = nodal values of f (P1 interpolant integrated against
+ * the basis), 1 = load vector.  g: Dirichlet data, same shape, or NULL for zero.
+ * u_out: n_nodes*ncomp x nrhs; Dirichlet entries are set to g (or 0). */
+nlfeti_status nlfeti_solve(nlfeti_problem *p, int nrhs, int rhs_kind, const double *rhs, const double *g,
+                           double *u_out, nlfeti_stats *stats);
+/* Same with device arrays (already resident; the call is asynchronous on the
+ * context stream except for a few scalar reads of convergence flags). */
+nlfeti_status nlfeti_solve_device(nlfeti_problem *p, int nrhs, int rhs_kind, const double *d_rhs,
+                                  const double *d_g, double *d_u_out, nlfeti_stats *stats);
+
+/* Introspection for bit-exact tests (host arrays, caller-sized from nlfeti_info):
+ * n_k[K], n_gamma[K], node lists (sum n_k / ncomp node ids, Omega first then
+ * Gamma per subdomain), B rows as U indices (n_lambda each), floating[K]. */
+nlfeti_status nlfeti_get_decomposition(const nlfeti_problem *p, int32_t *n_k, int32_t *n_gamma, int32_t *node_lists,
+                                       int64_t *B_plus, int64_t *B_minus, int8_t *floating);
+
+/* Copy one subdomain operator to the host (row-major, FP64):
+ * which 0 = assembled A^k (n_k x n_k), 1 = S_k (n_g x n_g), 2 = S_k^+ (n_g x n_g);
+ * precision 0 = FP64 operators, 1 = FP32 operators (widened). */
+nlfeti_status nlfeti_get_operator(const nlfeti_problem *p, int k, int which, int precision, double *out);
+
+/* Apply one FETI operator to host vectors (nrhs columns, column-major):
+ * op 0 = F = B S^+ B^T (Lambda -> Lambda), 1 = M^-1 = B_D S B_D^T, 2 = P (eq. P),
+ * 3 = S^+ (U -> U), 4 = S (U -> U). */
+nlfeti_status nlfeti_apply(nlfeti_problem *p, int op, int precision, int nrhs, const double *in, double *out);
+
+/* Continuous-batching server (one worker thread, its own streams).  Requests
+ * that arrive while others run are admitted between PCG iterations as slots and
+ * the HBM budget allow; their work shares the batched launches. */
+nlfeti_status nlfeti_server_create(nlfeti_ctx *ctx, size_t hbm_budget, int max_slots, nlfeti_server **out);
+nlfeti_status nlfeti_submit(nlfeti_server *s, nlfeti_problem *p, int nrhs, int rhs_kind, const double *rhs,
+                            const double *g, nlfeti_ticket *out);
+nlfeti_status nlfeti_wait(nlfeti_server *s, nlfeti_ticket t, int timeout_ms, double *u_out, nlfeti_stats *stats);
+void nlfeti_server_destroy(nlfeti_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

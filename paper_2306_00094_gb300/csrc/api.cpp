@@ -1,0 +1,558 @@
+// C ABI of the nlfeti library: contexts, problems (setup + assembly), factorization,
+// solves, operator application and introspection.  Every entry point converts internal
+// errors into an nlfeti_status and records the message in the context.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "solve.hpp"
+
+namespace nlf {
+
+void fail(nlfeti_status st, const std::string &msg) { throw Error{st, msg}; }
+
+void check_cuda(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        fail(NLFETI_E_NOMEM, std::string("device allocation failed in ") + what);
+    }
+    fail(NLFETI_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void set_error(nlfeti_ctx *c, const std::string &msg) {
+    if (!c) return;
+    std::lock_guard<std::mutex> g(c->mu);
+    c->err = msg;
+}
+
+void stream_enter(nlfeti_ctx *c) {
+    NLF_CUDA(cudaEventRecord(c->ev_in, c->user_stream));
+    NLF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+}
+
+void stream_leave(nlfeti_ctx *c) {
+    NLF_CUDA(cudaEventRecord(c->ev_out, c->stream));
+    NLF_CUDA(cudaStreamWaitEvent(c->user_stream, c->ev_out, 0));
+}
+
+void DevMem::alloc(nlfeti_ctx *c, size_t n) {
+    release();
+    ctx = c;
+    async = false;
+    n = std::max<size_t>(n, 16);
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        if (c->opt.hbm_budget && c->bytes_in_use + n > c->opt.hbm_budget)
+            fail(NLFETI_E_NOMEM, "allocation exceeds the context HBM budget");
+    }
+    void *q = nullptr;
+    if (c->dev_alloc) {
+        q = c->dev_alloc(n, c->alloc_user);
+        if (!q) fail(NLFETI_E_NOMEM, "device allocator returned NULL");
+    } else {
+        cudaError_t e = cudaMalloc(&q, n);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            fail(NLFETI_E_NOMEM, "cudaMalloc failed");
+        }
+    }
+    p = q;
+    bytes = n;
+    std::lock_guard<std::mutex> g(c->mu);
+    c->bytes_in_use += n;
+}
+
+void DevMem::alloc_async(cudaStream_t s, size_t n) {
+    release();
+    ctx = nullptr;
+    async = true;
+    astream = s;
+    n = std::max<size_t>(n, 16);
+    void *q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, n, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(NLFETI_E_NOMEM, "cudaMallocAsync failed");
+    }
+    p = q;
+    bytes = n;
+}
+
+void DevMem::release() {
+    if (!p) return;
+    if (async) {
+        cudaFreeAsync(p, astream);
+    } else if (ctx) {
+        if (ctx->dev_free) ctx->dev_free(p, ctx->alloc_user);
+        else cudaFree(p);
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->bytes_in_use -= std::min(ctx->bytes_in_use, bytes);
+    }
+    p = nullptr;
+    bytes = 0;
+}
+
+}  // namespace nlf
+
+nlfeti_problem::~nlfeti_problem() = default;
+
+using namespace nlf;
+
+namespace {
+
+template <typename F> nlfeti_status guarded(nlfeti_ctx *c, F &&f) {
+    try {
+        f();
+        return NLFETI_OK;
+    } catch (const Error &e) {
+        set_error(c, e.msg);
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        set_error(c, "host allocation failed");
+        return NLFETI_E_NOMEM;
+    } catch (const std::exception &e) {
+        set_error(c, e.what());
+        return NLFETI_E_INVALID;
+    }
+}
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int round8(int n) { return (n + 7) / 8 * 8; }
+
+void validate_mesh(const nlfeti_mesh *m) {
+    if (!m || (m->dim != 1 && m->dim != 2)) fail(NLFETI_E_INVALID, "mesh dim must be 1 or 2");
+    if (m->n_nodes <= 0 || m->n_elems <= 0) fail(NLFETI_E_INVALID, "empty mesh");
+    if (m->n_nodes > INT32_MAX || m->n_elems > INT32_MAX) fail(NLFETI_E_INVALID, "mesh too large");
+    if (!m->xy || !m->elems || !m->node_is_dirichlet || !m->elem_is_dirichlet) fail(NLFETI_E_INVALID, "null mesh array");
+    const int nv = m->dim + 1;
+    for (int64_t i = 0; i < m->n_elems * nv; ++i)
+        if (m->elems[i] < 0 || m->elems[i] >= m->n_nodes) fail(NLFETI_E_INVALID, "element node index out of range");
+    for (int64_t i = 0; i < m->n_nodes * m->dim; ++i)
+        if (!std::isfinite(m->xy[i])) fail(NLFETI_E_INVALID, "non-finite node coordinate");
+    bool any_dir = false;
+    for (int64_t i = 0; i < m->n_nodes; ++i) any_dir |= m->node_is_dirichlet[i] != 0;
+    if (!any_dir) fail(NLFETI_E_INVALID, "the Dirichlet volume constraint is empty");
+}
+
+void validate_kernel(const nlfeti_kernel *k, int dim) {
+    if (!k) fail(NLFETI_E_INVALID, "null kernel");
+    if (k->type < 0 || k->type > 3) fail(NLFETI_E_INVALID, "unknown kernel type");
+    if (!(k->delta > 0) || !std::isfinite(k->delta)) fail(NLFETI_E_INVALID, "delta must be positive");
+    if (!(k->scale > 0)) fail(NLFETI_E_INVALID, "kernel scale must be positive");
+    if (k->type == NLFETI_K_FRACTIONAL && !(k->s > 0 && k->s < 1)) fail(NLFETI_E_INVALID, "fractional s must be in (0,1)");
+    if (dim == 1 && k->type != NLFETI_K_CONST_LINF) fail(NLFETI_E_INVALID, "1-D meshes support the constant kernel only");
+}
+
+void build_maps(nlfeti_problem *p) {
+    nlfeti_ctx *c = p->ctx;
+    const Decomp &d = p->dec;
+    const int K = d.K, nc = d.nc;
+    const MeshHost &m = p->mesh;
+    p->K = K;
+    p->nc = nc;
+    p->n_dofs_total = m.n_nodes * nc;
+    p->n_lambda = (int64_t)d.B_plus.size();
+    p->n_u = d.u_off[K];
+    p->n_co = d.co_off[K];
+    p->sd.assign(K, SubdomainDesc{});
+    int64_t offA = 0, offAD = 0, offM = 0, offG = 0, offV = 0;
+    p->n_floating = 0;
+    p->max_ldG = 8;
+    for (int k = 0; k < K; ++k) {
+        SubdomainDesc &s = p->sd[k];
+        std::memset(&s, 0, sizeof(s));
+        s.nk = (int32_t)d.nodes[k].size() * nc;
+        s.nO = d.n_omega_nodes[k] * nc;
+        s.nG = d.n_gamma_nodes[k] * nc;
+        s.nD = (int32_t)d.dir_nodes[k].size() * nc;
+        s.ldM = round8(s.nk);
+        s.ldG = round8(std::max(s.nG, 1));
+        s.offA = offA; offA += (int64_t)s.nk * s.nk;
+        s.offAD = offAD; offAD += (int64_t)s.nk * s.nD;
+        s.offM = offM; offM += (int64_t)s.nk * s.ldM;
+        s.offS = offG; s.offSp = offG; offG += (int64_t)s.nG * s.ldG;
+        s.offU = d.u_off[k];
+        s.offV = offV; offV += s.nk;
+        s.co_off = d.co_off[k];
+        s.n_co = d.co_off[k + 1] - d.co_off[k];
+        s.floating = d.floating[k];
+        s.npin = (int32_t)d.pinned[k].size();
+        for (int i = 0; i < s.npin && i < 3; ++i) s.pin[i] = d.pinned[k][i];
+        if (s.floating) p->n_floating++;
+        p->max_ldG = std::max(p->max_ldG, s.ldG);
+    }
+    p->poolA = offA; p->poolAD = offAD; p->poolM = offM; p->poolG = offG;
+    p->sum_nk = offV;
+    // node maps
+    std::vector<int32_t> nodemap((size_t)K * m.n_nodes, -1);
+    std::vector<int32_t> vdofs(offV);
+    std::vector<int64_t> u2v(std::max<int64_t>(p->n_u, 1));
+    std::vector<int32_t> u2sub(std::max<int64_t>(p->n_u, 1));
+    std::vector<int32_t> ddofs;
+    std::vector<int64_t> doff(K + 1, 0);
+    for (int k = 0; k < K; ++k) {
+        const auto &nd = d.nodes[k];
+        for (size_t i = 0; i < nd.size(); ++i) {
+            nodemap[(size_t)k * m.n_nodes + nd[i]] = (int32_t)i;
+            for (int cc = 0; cc < nc; ++cc) vdofs[p->sd[k].offV + (int64_t)i * nc + cc] = nd[i] * nc + cc;
+        }
+        const auto &dn = d.dir_nodes[k];
+        for (size_t i = 0; i < dn.size(); ++i) {
+            nodemap[(size_t)k * m.n_nodes + dn[i]] = -(2 + (int32_t)i);
+            for (int cc = 0; cc < nc; ++cc) ddofs.push_back(dn[i] * nc + cc);
+        }
+        doff[k + 1] = (int64_t)ddofs.size();
+        for (int i = 0; i < p->sd[k].nG; ++i) {
+            u2v[p->sd[k].offU + i] = p->sd[k].offV + p->sd[k].nO + i;
+            u2sub[p->sd[k].offU + i] = k;
+        }
+    }
+    // copies of each global dof
+    std::vector<int64_t> cp_ptr(p->n_dofs_total + 1, 0), cp_pos(offV);
+    for (int64_t v = 0; v < offV; ++v) cp_ptr[vdofs[v] + 1]++;
+    for (int64_t i = 0; i < p->n_dofs_total; ++i) cp_ptr[i + 1] += cp_ptr[i];
+    {
+        std::vector<int64_t> fill(cp_ptr.begin(), cp_ptr.end() - 1);
+        for (int64_t v = 0; v < offV; ++v) cp_pos[fill[vdofs[v]]++] = v;
+    }
+    std::vector<double> zeta(p->n_dofs_total, 1.0);
+    for (int64_t n = 0; n < m.n_nodes; ++n)
+        for (int cc = 0; cc < nc; ++cc) zeta[n * nc + cc] = d.node_zeta[n] > 0 ? (double)d.node_zeta[n] : 1.0;
+    // B^T (signed rows) per U dof
+    std::vector<int64_t> bt_ptr(p->n_u + 1, 0), bt_row(2 * p->n_lambda);
+    for (int64_t r = 0; r < p->n_lambda; ++r) { bt_ptr[d.B_plus[r] + 1]++; bt_ptr[d.B_minus[r] + 1]++; }
+    for (int64_t u = 0; u < p->n_u; ++u) bt_ptr[u + 1] += bt_ptr[u];
+    {
+        std::vector<int64_t> fill(bt_ptr.begin(), bt_ptr.end() - 1);
+        for (int64_t r = 0; r < p->n_lambda; ++r) {
+            bt_row[fill[d.B_plus[r]]++] = r + 1;
+            bt_row[fill[d.B_minus[r]]++] = -(r + 1);
+        }
+    }
+    // interior elements around each node (load vector)
+    const int nv = m.dim + 1;
+    std::vector<int64_t> inc_ptr(m.n_nodes + 1, 0);
+    for (int64_t e = 0; e < m.n_elems; ++e)
+        if (!m.elem_dir[e])
+            for (int i = 0; i < nv; ++i) inc_ptr[m.elems[e * nv + i] + 1]++;
+    for (int64_t i = 0; i < m.n_nodes; ++i) inc_ptr[i + 1] += inc_ptr[i];
+    std::vector<int32_t> inc_el(std::max<int64_t>(inc_ptr[m.n_nodes], 1));
+    {
+        std::vector<int64_t> fill(inc_ptr.begin(), inc_ptr.end() - 1);
+        for (int64_t e = 0; e < m.n_elems; ++e)
+            if (!m.elem_dir[e])
+                for (int i = 0; i < nv; ++i) inc_el[fill[m.elems[e * nv + i]]++] = (int32_t)e;
+    }
+    // symv work items: 64 rows each
+    std::vector<int32_t> items;
+    p->item_off.assign(K + 1, 0);
+    for (int k = 0; k < K; ++k) {
+        for (int r0 = 0; r0 < p->sd[k].nG; r0 += 64) { items.push_back(k); items.push_back(r0); }
+        p->item_off[k + 1] = (int)(items.size() / 2);
+    }
+    p->n_items = (int)(items.size() / 2);
+    std::vector<uint64_t> mask = d.elem_mask;
+    upload(c, p->d_sd, p->sd);
+    upload(c, p->d_xy, m.xy);
+    upload(c, p->d_elems, m.elems);
+    upload(c, p->d_node_dir, m.node_dir);
+    upload(c, p->d_elem_mask, mask);
+    upload(c, p->d_nodemap, nodemap);
+    upload(c, p->d_vdofs, vdofs);
+    upload(c, p->d_u2v, u2v);
+    upload(c, p->d_u2sub, u2sub);
+    upload(c, p->d_ddofs, ddofs);
+    upload(c, p->d_doff, doff);
+    upload(c, p->d_cp_ptr, cp_ptr);
+    upload(c, p->d_cp_pos, cp_pos);
+    upload(c, p->d_zeta_dof, zeta);
+    upload(c, p->d_Bp, d.B_plus);
+    upload(c, p->d_Bm, d.B_minus);
+    upload(c, p->d_Bt_ptr, bt_ptr);
+    upload(c, p->d_Bt_row, bt_row);
+    upload(c, p->d_nodeinc_ptr, inc_ptr);
+    upload(c, p->d_nodeinc_el, inc_el);
+    upload(c, p->d_items, items);
+    p->d_flag.alloc(c, sizeof(int) * 4);
+    NLF_CUDA(cudaMemsetAsync(p->d_flag.p, 0, sizeof(int) * 4, c->stream));
+    p->d_A.alloc(c, sizeof(double) * std::max<int64_t>(offA, 1));
+    p->d_AD.alloc(c, sizeof(double) * std::max<int64_t>(offAD, 1));
+    NLF_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+void nlfeti_default_options(nlfeti_options *o) {
+    if (!o) return;
+    o->precision = 0;
+    o->tol = 1e-10;
+    o->max_it = 1000;
+    o->max_refine = 6;
+    o->inner_tol = 1e-6;
+    o->refine_tol = 1e-10;
+    o->batched = 1;
+    o->hbm_budget = 0;
+}
+
+nlfeti_status nlfeti_create(nlfeti_ctx **out, const nlfeti_options *opt, void *cuda_stream,
+                            void *(*dev_alloc)(size_t, void *), void (*dev_free)(void *, void *), void *alloc_user) {
+    if (!out) return NLFETI_E_INVALID;
+    if ((dev_alloc == nullptr) != (dev_free == nullptr)) return NLFETI_E_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return NLFETI_E_CUDA;
+    }
+    nlfeti_ctx *c = new (std::nothrow) nlfeti_ctx();
+    if (!c) return NLFETI_E_NOMEM;
+    nlfeti_default_options(&c->opt);
+    if (opt) c->opt = *opt;
+    c->user_stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return NLFETI_E_CUDA;
+    }
+    c->dev_alloc = dev_alloc;
+    c->dev_free = dev_free;
+    c->alloc_user = alloc_user;
+    *out = c;
+    return NLFETI_OK;
+}
+
+void nlfeti_destroy(nlfeti_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->stream) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaStreamDestroy(ctx->stream);
+    }
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+    delete ctx;
+}
+
+const char *nlfeti_last_error(const nlfeti_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+nlfeti_status nlfeti_problem_create(nlfeti_ctx *ctx, const nlfeti_mesh *mesh, const nlfeti_kernel *kernel,
+                                    const nlfeti_decomp *decomp, nlfeti_problem **out) {
+    if (!ctx || !out) return NLFETI_E_INVALID;
+    nlfeti_problem *p = nullptr;
+    nlfeti_status st = guarded(ctx, [&] {
+        double t0 = now_ms();
+        validate_mesh(mesh);
+        validate_kernel(kernel, mesh->dim);
+        if (!decomp || !decomp->elem_subdomain) fail(NLFETI_E_INVALID, "null decomposition");
+        std::unique_ptr<nlfeti_problem> q(new nlfeti_problem());
+        q->ctx = ctx;
+        q->opt = ctx->opt;
+        q->kern = *kernel;
+        MeshHost &m = q->mesh;
+        m.dim = mesh->dim;
+        m.n_nodes = mesh->n_nodes;
+        m.n_elems = mesh->n_elems;
+        m.xy.assign(mesh->xy, mesh->xy + mesh->n_nodes * mesh->dim);
+        m.elems.assign(mesh->elems, mesh->elems + mesh->n_elems * (mesh->dim + 1));
+        m.node_dir.assign(mesh->node_is_dirichlet, mesh->node_is_dirichlet + mesh->n_nodes);
+        m.elem_dir.assign(mesh->elem_is_dirichlet, mesh->elem_is_dirichlet + mesh->n_elems);
+        std::vector<int32_t> labels(decomp->elem_subdomain, decomp->elem_subdomain + mesh->n_elems);
+        build_decomposition(m, *kernel, labels, decomp->K, q->dec);
+        build_maps(q.get());
+        assemble_all(q.get());
+        setup_jump_weights(q.get());
+        setup_coarse(q.get());
+        int flag[4] = {0, 0, 0, 0};
+        NLF_CUDA(cudaMemcpy(flag, q->d_flag.p, sizeof(flag), cudaMemcpyDeviceToHost));
+        if (flag[1]) fail(NLFETI_E_INVALID, "an interface node belongs to more than 16 subdomains");
+        if (flag[0]) fail(NLFETI_E_NOT_SPD, "the coarse matrix G^T G is not positive definite");
+        q->ms_setup = now_ms() - t0;
+        p = q.release();
+    });
+    if (st == NLFETI_OK) *out = p;
+    return st;
+}
+
+void nlfeti_problem_destroy(nlfeti_problem *p) {
+    if (!p) return;
+    if (p->ctx && p->ctx->stream) cudaStreamSynchronize(p->ctx->stream);
+    delete p;
+}
+
+nlfeti_status nlfeti_problem_info(const nlfeti_problem *p, nlfeti_info *info) {
+    if (!p || !info) return NLFETI_E_INVALID;
+    info->K = p->K;
+    info->ncomp = p->nc;
+    info->n_floating = p->n_floating;
+    info->n_coarse = p->n_co;
+    info->n_lambda = p->n_lambda;
+    info->n_u = p->n_u;
+    info->sum_nk = p->sum_nk;
+    int64_t s2 = 0, g2 = 0;
+    int mk = 0, mg = 0;
+    for (auto &d : p->sd) {
+        s2 += (int64_t)d.nk * d.nk;
+        g2 += (int64_t)d.nG * d.nG;
+        mk = std::max(mk, d.nk);
+        mg = std::max(mg, d.nG);
+    }
+    info->sum_nk2 = s2;
+    info->sum_ngamma2 = g2;
+    info->max_nk = mk;
+    info->max_ngamma = mg;
+    return NLFETI_OK;
+}
+
+nlfeti_status nlfeti_problem_set_options(nlfeti_problem *p, const nlfeti_options *opt) {
+    if (!p || !opt) return NLFETI_E_INVALID;
+    if (opt->precision != 0 && opt->precision != 1) return NLFETI_E_INVALID;
+    p->opt = *opt;
+    return NLFETI_OK;
+}
+
+nlfeti_status nlfeti_factor(nlfeti_problem *p, int mask) {
+    if (!p) return NLFETI_E_INVALID;
+    return guarded(p->ctx, [&] {
+        if (mask & ~3) fail(NLFETI_E_INVALID, "precision mask must use bits 0 and 1");
+        double t0 = now_ms();
+        if (mask & 1) factor_ops<double>(p, p->op64);
+        if (mask & 2) factor_ops<float>(p, p->op32);
+        p->ms_factor = now_ms() - t0;
+    });
+}
+
+nlfeti_status nlfeti_solve_device(nlfeti_problem *p, int nrhs, int rhs_kind, const double *d_rhs, const double *d_g,
+                                  double *d_u_out, nlfeti_stats *stats) {
+    if (!p) return NLFETI_E_INVALID;
+    return guarded(p->ctx, [&] {
+        if (nrhs < 1 || (rhs_kind != 0 && rhs_kind != 1) || !d_rhs || !d_u_out) fail(NLFETI_E_INVALID, "bad solve arguments");
+        if (!p->ws) p->ws.reset(new SolveWS());
+        double t0 = now_ms();
+        nlfeti_stats s{};
+        stream_enter(p->ctx);
+        try {
+            solve_device(p, *p->ws, p->ctx->stream, nrhs, rhs_kind, d_rhs, d_g, d_u_out, &s);
+        } catch (...) {
+            if (stats) *stats = s;
+            stream_leave(p->ctx);
+            throw;
+        }
+        stream_leave(p->ctx);
+        s.ms_setup = p->ms_setup;
+        s.ms_factor = p->ms_factor;
+        s.ms_solve = now_ms() - t0;
+        if (stats) *stats = s;
+    });
+}
+
+nlfeti_status nlfeti_solve(nlfeti_problem *p, int nrhs, int rhs_kind, const double *rhs, const double *g,
+                           double *u_out, nlfeti_stats *stats) {
+    if (!p) return NLFETI_E_INVALID;
+    return guarded(p->ctx, [&] {
+        if (nrhs < 1 || !rhs || !u_out) fail(NLFETI_E_INVALID, "bad solve arguments");
+        if (!p->ws) p->ws.reset(new SolveWS());
+        SolveWS &ws = *p->ws;
+        cudaStream_t st = p->ctx->stream;
+        const size_t bytes = sizeof(double) * (size_t)p->n_dofs_total * nrhs;
+        if (ws.in_rhs.bytes < bytes) ws.in_rhs.alloc(p->ctx, bytes);
+        if (ws.out_u.bytes < bytes) ws.out_u.alloc(p->ctx, bytes);
+        if (g && ws.in_g.bytes < bytes) ws.in_g.alloc(p->ctx, bytes);
+        double t0 = now_ms();
+        NLF_CUDA(cudaMemcpyAsync(ws.in_rhs.p, rhs, bytes, cudaMemcpyHostToDevice, st));
+        if (g) NLF_CUDA(cudaMemcpyAsync(ws.in_g.p, g, bytes, cudaMemcpyHostToDevice, st));
+        nlfeti_stats s{};
+        nlfeti_status inner = NLFETI_OK;
+        try {
+            solve_device(p, ws, st, nrhs, rhs_kind, ws.in_rhs.as<double>(), g ? ws.in_g.as<double>() : nullptr,
+                         ws.out_u.as<double>(), &s);
+        } catch (const Error &e) {
+            if (e.st != NLFETI_E_NOT_CONVERGED) throw;
+            inner = e.st;
+            set_error(p->ctx, e.msg);
+        }
+        NLF_CUDA(cudaMemcpyAsync(u_out, ws.out_u.p, bytes, cudaMemcpyDeviceToHost, st));
+        NLF_CUDA(cudaStreamSynchronize(st));
+        s.ms_setup = p->ms_setup;
+        s.ms_factor = p->ms_factor;
+        s.ms_solve = now_ms() - t0;
+        if (stats) *stats = s;
+        if (inner != NLFETI_OK) fail(inner, p->ctx->err);
+    });
+}
+
+nlfeti_status nlfeti_get_decomposition(const nlfeti_problem *p, int32_t *n_k, int32_t *n_gamma, int32_t *node_lists,
+                                       int64_t *B_plus, int64_t *B_minus, int8_t *floating) {
+    if (!p) return NLFETI_E_INVALID;
+    int64_t off = 0;
+    for (int k = 0; k < p->K; ++k) {
+        if (n_k) n_k[k] = p->sd[k].nk;
+        if (n_gamma) n_gamma[k] = p->sd[k].nG;
+        if (floating) floating[k] = p->dec.floating[k];
+        if (node_lists) std::copy(p->dec.nodes[k].begin(), p->dec.nodes[k].end(), node_lists + off);
+        off += (int64_t)p->dec.nodes[k].size();
+    }
+    if (B_plus) std::copy(p->dec.B_plus.begin(), p->dec.B_plus.end(), B_plus);
+    if (B_minus) std::copy(p->dec.B_minus.begin(), p->dec.B_minus.end(), B_minus);
+    return NLFETI_OK;
+}
+
+nlfeti_status nlfeti_get_operator(const nlfeti_problem *p, int k, int which, int precision, double *out) {
+    if (!p || !out || k < 0 || k >= p->K) return NLFETI_E_INVALID;
+    nlfeti_problem *q = const_cast<nlfeti_problem *>(p);
+    return guarded(q->ctx, [&] {
+        const SubdomainDesc &d = p->sd[k];
+        if (which == 0) {
+            NLF_CUDA(cudaMemcpy(out, p->d_A.as<double>() + d.offA, sizeof(double) * d.nk * d.nk, cudaMemcpyDeviceToHost));
+            return;
+        }
+        if (which != 1 && which != 2) fail(NLFETI_E_INVALID, "which must be 0, 1 or 2");
+        const int64_t n = d.nG, ld = d.ldG;
+        const int64_t off = which == 1 ? d.offS : d.offSp;
+        if (precision == 0) {
+            if (!p->op64.ready) fail(NLFETI_E_INVALID, "FP64 operators not factored");
+            std::vector<double> tmp(n * ld);
+            const nlf::DevMem &src = which == 1 ? p->op64.S : p->op64.Sp;
+            if (n) NLF_CUDA(cudaMemcpy(tmp.data(), src.as<double>() + off, sizeof(double) * n * ld, cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t l = 0; l < n; ++l) out[i * n + l] = tmp[i * ld + l];
+        } else {
+            if (!p->op32.ready) fail(NLFETI_E_INVALID, "FP32 operators not factored");
+            std::vector<float> tmp(n * ld);
+            const nlf::DevMem &src = which == 1 ? p->op32.S : p->op32.Sp;
+            if (n) NLF_CUDA(cudaMemcpy(tmp.data(), src.as<float>() + off, sizeof(float) * n * ld, cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t l = 0; l < n; ++l) out[i * n + l] = tmp[i * ld + l];
+        }
+    });
+}
+
+nlfeti_status nlfeti_apply(nlfeti_problem *p, int op, int precision, int nrhs, const double *in, double *out) {
+    if (!p || !in || !out || nrhs < 1) return NLFETI_E_INVALID;
+    return guarded(p->ctx, [&] {
+        if (op < 0 || op > 4) fail(NLFETI_E_INVALID, "unknown operator");
+        const int64_t n = (op <= 2) ? p->n_lambda : p->n_u;
+        if (n == 0) return;
+        cudaStream_t st = p->ctx->stream;
+        DevMem a, b, ai, bi;
+        a.alloc(p->ctx, sizeof(double) * n * nrhs);
+        b.alloc(p->ctx, sizeof(double) * n * nrhs);
+        ai.alloc(p->ctx, sizeof(double) * n * nrhs);
+        bi.alloc(p->ctx, sizeof(double) * n * nrhs);
+        NLF_CUDA(cudaMemcpyAsync(a.p, in, sizeof(double) * n * nrhs, cudaMemcpyHostToDevice, st));
+        to_interleaved(a.as<double>(), ai.as<double>(), n, nrhs, st);
+        SolveWS ws;
+        apply_operator(p, ws, st, op, precision, nrhs, ai.as<double>(), bi.as<double>());
+        to_colmajor(bi.as<double>(), b.as<double>(), n, nrhs, st);
+        NLF_CUDA(cudaMemcpyAsync(out, b.p, sizeof(double) * n * nrhs, cudaMemcpyDeviceToHost, st));
+        NLF_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+}  // extern "C"

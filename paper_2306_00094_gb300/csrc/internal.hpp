@@ -1,0 +1,182 @@
+// Internal declarations of the nlfeti library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/nlfeti.h"
+
+struct nlfeti_ctx {
+    nlfeti_options opt;
+    cudaStream_t stream = nullptr;        // the library's own non-blocking stream (capturable)
+    cudaStream_t user_stream = nullptr;   // the caller's stream (may be the legacy stream)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    void *(*dev_alloc)(size_t, void *) = nullptr;
+    void (*dev_free)(void *, void *) = nullptr;
+    void *alloc_user = nullptr;
+    std::string err;
+    std::mutex mu;                // guards err and bytes_in_use
+    size_t bytes_in_use = 0;
+};
+
+namespace nlf {
+
+// ------------------------------------------------------------------ errors
+struct Error {
+    nlfeti_status st;
+    std::string msg;
+};
+[[noreturn]] void fail(nlfeti_status st, const std::string &msg);
+void check_cuda(cudaError_t e, const char *what);
+#define NLF_CUDA(x) ::nlf::check_cuda((x), #x)
+
+// ------------------------------------------------------------------ device memory
+// Owned device buffer.  With a context: the context's allocator (or cudaMalloc), counted
+// against the context budget.  With a stream (no context): stream-ordered cudaMallocAsync.
+struct DevMem {
+    nlfeti_ctx *ctx = nullptr;
+    cudaStream_t astream = nullptr;
+    bool async = false;
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem &) = delete;
+    DevMem &operator=(const DevMem &) = delete;
+    DevMem(DevMem &&o) noexcept { *this = std::move(o); }
+    DevMem &operator=(DevMem &&o) noexcept {
+        release();
+        ctx = o.ctx; astream = o.astream; async = o.async; p = o.p; bytes = o.bytes;
+        o.p = nullptr; o.bytes = 0;
+        return *this;
+    }
+    ~DevMem() { release(); }
+    void alloc(nlfeti_ctx *c, size_t n);
+    void alloc_async(cudaStream_t s, size_t n);
+    void release();
+    template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+template <typename T> void upload(nlfeti_ctx *c, DevMem &m, const std::vector<T> &v) {
+    m.alloc(c, sizeof(T) * (v.empty() ? 1 : v.size()));
+    if (!v.empty())
+        NLF_CUDA(cudaMemcpyAsync(m.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, c->stream));
+}
+
+// ------------------------------------------------------------------ host decomposition
+struct Decomp {
+    int K = 0, nc = 1;
+    std::vector<uint64_t> elem_mask;      // bit k: element in Omega-hat_k u Gamma^D_k
+    std::vector<int32_t> node_zeta;       // number of Omega-hat_k holding the node
+    std::vector<std::vector<int32_t>> nodes;   // per k: Omega nodes then Gamma nodes (ascending each)
+    std::vector<int32_t> n_omega_nodes, n_gamma_nodes;
+    std::vector<std::vector<int32_t>> dir_nodes;  // per k: Dirichlet nodes of Omega-hat_k u Gamma^D_k (ascending)
+    std::vector<int8_t> floating;
+    std::vector<std::vector<int32_t>> pinned;     // Gamma-local dof indices
+    std::vector<int64_t> u_off;                   // K+1, in dofs
+    std::vector<int64_t> B_plus, B_minus;         // U indices
+    std::vector<int32_t> B_node;
+    std::vector<int32_t> co_off;                  // K+1 coarse columns per subdomain
+};
+
+struct MeshHost {
+    int dim = 2;
+    int64_t n_nodes = 0, n_elems = 0;
+    std::vector<double> xy;
+    std::vector<int32_t> elems;
+    std::vector<int8_t> node_dir, elem_dir;
+};
+
+void build_decomposition(const MeshHost &m, const nlfeti_kernel &kern, const std::vector<int32_t> &labels, int K,
+                         Decomp &d);
+
+}  // namespace nlf
+
+// ------------------------------------------------------------------ device-side problem data
+struct SubdomainDesc {      // per subdomain, device resident (POD)
+    int32_t nk, nO, nG;     // dofs
+    int32_t nD;             // Dirichlet dofs coupled (columns of AD)
+    int64_t offA;           // FP64 assembled matrix (nk x nk, ld nk)
+    int64_t offAD;          // FP64 Dirichlet coupling (nk x nD)
+    int64_t offM;           // swept matrix (nk x ldM) in the operator pool of a precision
+    int64_t offS;           // S_k (nG x ldG)
+    int64_t offSp;          // S_k^+ (nG x ldG)
+    int64_t offU;           // start of Gamma_k in U
+    int64_t offV;           // start of the subdomain in the concatenated subdomain vectors (sum nk)
+    int32_t co_off, n_co;   // coarse columns
+    int32_t floating;
+    int32_t npin;
+    int32_t pin[3];
+    int32_t ldM;            // nk rounded up to 8
+    int32_t ldG;            // nG rounded up to 8
+    int32_t pad;
+};
+
+template <typename T> struct OpPool {   // operators of one precision
+    nlf::DevMem M, S, Sp;                // swept matrices, Schur complements, pseudo-inverses
+    nlf::DevMem scratch;                 // panel scratch of the sweeps
+    bool ready = false;
+};
+
+namespace nlf { struct SolveWS; }
+
+struct nlfeti_problem {
+    nlfeti_ctx *ctx = nullptr;
+    nlfeti_options opt;
+    nlf::MeshHost mesh;
+    nlfeti_kernel kern;
+    nlf::Decomp dec;
+    int K = 0, nc = 1;
+    int64_t n_lambda = 0, n_u = 0, sum_nk = 0, n_dofs_total = 0;
+    int n_co = 0, n_floating = 0, max_ldG = 0;
+    std::vector<SubdomainDesc> sd;      // host copy
+    nlf::DevMem d_sd;
+    // mesh on device
+    nlf::DevMem d_xy, d_elems, d_node_dir, d_elem_mask;
+    // node -> subdomain-local node index map (K x n_nodes): >= 0 dof node, <= -2 Dirichlet column node
+    // -(2 + index), -1 none
+    nlf::DevMem d_nodemap;
+    // assembled FP64 matrices
+    nlf::DevMem d_A, d_AD;
+    int64_t poolA = 0, poolAD = 0, poolM = 0, poolG = 0;
+    // jump operators
+    nlf::DevMem d_Bp, d_Bm;              // int64 U index per Lambda row
+    nlf::DevMem d_Bt_ptr, d_Bt_row;      // per U dof: rows, signed (r+1 for +1, -(r+1) for -1)
+    nlf::DevMem d_BD_ptr, d_BD_col, d_BD_val;    // B_D rows (U index, value)
+    nlf::DevMem d_BDt_ptr, d_BDt_row, d_BDt_val; // B_D^T rows per U dof
+    nlf::DevMem d_Z;                     // (n_u x 3) FP64 kernel basis of floating subdomains
+    nlf::DevMem d_Q;                     // (n_u x 3) FP64 orthonormal kernel basis
+    nlf::DevMem d_GtGinv;                // n_co x n_co FP64
+    nlf::DevMem d_u2sub;                 // per U dof: subdomain (int32)
+    nlf::DevMem d_u2v;                   // per U dof: position in the subdomain vectors (int64)
+    nlf::DevMem d_vdofs;                 // per subdomain-vector entry: global dof (int32)
+    nlf::DevMem d_cp_ptr, d_cp_pos;      // per global dof: positions of its copies (int64)
+    nlf::DevMem d_ddofs, d_doff;         // per subdomain: global dofs of the Dirichlet columns
+    nlf::DevMem d_nodeinc_ptr, d_nodeinc_el;  // node -> interior elements (load vector gather)
+    nlf::DevMem d_zeta_dof;              // per global dof: zeta (double)
+    nlf::DevMem d_items;                 // symv work items (k, first row) pairs
+    int n_items = 0;
+    std::vector<int> item_off;           // K+1
+    nlf::DevMem d_flag;                  // device status words
+    OpPool<double> op64;
+    OpPool<float> op32;
+    std::unique_ptr<nlf::SolveWS> ws;
+    double ms_setup = 0, ms_factor = 0;
+    ~nlfeti_problem();
+};
+
+// kernels and launchers (defined in the .cu files)
+namespace nlf {
+void assemble_all(nlfeti_problem *p);
+template <typename T> void factor_ops(nlfeti_problem *p, OpPool<T> &pool);
+void setup_coarse(nlfeti_problem *p);
+void setup_jump_weights(nlfeti_problem *p);
+void set_error(nlfeti_ctx *c, const std::string &msg);
+// order the library stream after the caller's stream (enter) and the caller's after it (leave)
+void stream_enter(nlfeti_ctx *c);
+void stream_leave(nlfeti_ctx *c);
+}  // namespace nlf

@@ -1,0 +1,927 @@
+// FETI solve phase on the GPU: Algorithm 1 steps 3 and 6-9, the projected PCG of step 7
+// with the scaled Dirichlet preconditioner (eq. preconditioner), and for the mixed path FP64
+// iterative refinement on the torn system (eq. discreteKKT).
+//
+// Vectors hold R right-hand sides interleaved (entry i of column c at i*R + c).
+// Lambda-space vectors, coarse vectors and all scalars are FP64; the subdomain operators
+// S_k^+, S_k and the swept matrices are FP64 (plain path) or FP32 (mixed path).
+//
+// PCG iteration (per right-hand side; converged columns are frozen with eta = 0):
+//   w = P r;  z = B_D S B_D^T w;  y = P z;  beta = (y,w)/(y,w)_old;  p = y + beta p;
+//   q = B S^+ B^T p;  eta = (y,w)/(p,q);  lambda += eta p;  r -= eta q
+// with P = I - G (G^T G)^-1 G^T (eq. P), G = B Z, stopping when ||w||_2 <= tol ||P d||_2.
+// A pass solves for subdomain loads f: reduced forcing f_U (eq. subForcing),
+// d = B S^+ f_U - c, e = Z^T f_U, lambda^0 = G (G^T G)^-1 e, PCG, then
+// alpha = (G^T G)^-1 G^T (d - F lambda) (eq. forAlpha), u_G = S^+ (f_U - B^T lambda) - Z alpha
+// (eq. forU) and u_O by back substitution (eq. backwardSubstitution).
+// Mixed refinement: r = f~ - A u - [0; B^T lambda] and c = -B u_G in FP64, a pass with the
+// FP32 operators gives the correction, u += du, lambda += dlambda, until the relative nodal
+// correction is below refine_tol.
+#include <algorithm>
+#include <cmath>
+
+#include "solve.hpp"
+
+namespace nlf {
+namespace {
+
+constexpr int RED_BLOCKS = 304;     // two CTAs per SM for reductions
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+inline unsigned grid_for(int64_t n, int threads = 256) {
+    int64_t b = (n + threads - 1) / threads;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+}
+
+template <typename T> __global__ void k_cast(const double *a, T *b, int64_t n) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        b[t] = (T)a[t];
+}
+
+__global__ void k_sub(const double *a, const double *b, double *out, int64_t n) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = a[t] - b[t];
+}
+
+__global__ void k_axpy(double *y, const double *x, double a, int64_t n) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        y[t] += a * x[t];
+}
+
+__global__ void k_transpose_cr(const double *src, double *dst, int64_t n, int R, int to_inter) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * R; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = t / R;
+        int c = (int)(t % R);
+        if (to_inter) dst[t] = src[(int64_t)c * n + i];
+        else dst[(int64_t)c * n + i] = src[t];
+    }
+}
+
+// ------------------------------------------------------------------ gathers between U and Lambda
+// x_U = B^T v (cast to T); rows stored signed: r+1 for +1, -(r+1) for -1
+template <typename T>
+__global__ void k_gather_bt(const int64_t *ptr, const int64_t *row, const double *v, T *x, int64_t nu, int R) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t u = t / R;
+        int c = (int)(t % R);
+        double s = 0;
+        for (int64_t q = ptr[u]; q < ptr[u + 1]; ++q) {
+            int64_t r = row[q];
+            s += r > 0 ? v[(r - 1) * R + c] : -v[(-r - 1) * R + c];
+        }
+        x[t] = (T)s;
+    }
+}
+
+// x_U = B_D^T v (cast to T)
+template <typename T>
+__global__ void k_gather_bdt(const int64_t *ptr, const int64_t *row, const double *val, const double *v, T *x,
+                             int64_t nu, int R) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t u = t / R;
+        int c = (int)(t % R);
+        double s = 0;
+        for (int64_t q = ptr[u]; q < ptr[u + 1]; ++q) s += val[q] * v[row[q] * R + c];
+        x[t] = (T)s;
+    }
+}
+
+// out = B y - c (c optional)
+__global__ void k_gather_b(const int64_t *Bp, const int64_t *Bm, const double *y, const double *cvec, double *out,
+                           int64_t nl, int R) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl * R; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = t / R;
+        int c = (int)(t % R);
+        double v = y[Bp[r] * R + c] - y[Bm[r] * R + c];
+        if (cvec) v -= cvec[t];
+        out[t] = v;
+    }
+}
+
+// c = -B u_G read from the subdomain vectors through the U -> vector position map
+__global__ void k_constraint_residual(const int64_t *Bp, const int64_t *Bm, const int64_t *u2v, const double *u,
+                                      double *cvec, int64_t nl, int R) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl * R; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = t / R;
+        int c = (int)(t % R);
+        cvec[t] = -(u[u2v[Bp[r]] * R + c] - u[u2v[Bm[r]] * R + c]);
+    }
+}
+
+// out = B_D y
+__global__ void k_gather_bd(const int64_t *ptr, const int64_t *col, const double *val, const double *y, double *out,
+                            int64_t nl, int R) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl * R; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = t / R;
+        int c = (int)(t % R);
+        double s = 0;
+        for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) s += val[q] * y[col[q] * R + c];
+        out[t] = s;
+    }
+}
+
+// ------------------------------------------------------------------ dense symmetric apply (hot kernel)
+// y_k = M_k x_k for the work items (subdomain k, first row): M_k is n x n with leading
+// dimension ld (multiple of 8, zero padded), stored in T.  The CTA stages x_k transposed in
+// shared memory ([c][l]) for RC columns at a time; each warp owns 8 rows and each lane
+// streams 4 (FP32) or 2 (FP64) consecutive columns per step with one 16-byte load.
+// Products accumulate in T (FP32 on the mixed path) per lane, the warp sum in FP64.
+template <typename T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
+
+template <typename T, int RC>
+__global__ void __launch_bounds__(256) k_symv(const T *base, int use_sp, const SubdomainDesc *sd, const int32_t *items,
+                                              const T *x, double *y, int R) {
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
+    const int k = items[2 * blockIdx.x], row0 = items[2 * blockIdx.x + 1];
+    const SubdomainDesc d = sd[k];
+    const int n = d.nG, ld = d.ldG;
+    const T *M = base + (use_sp ? d.offSp : d.offS);
+    extern __shared__ unsigned char smraw[];
+    T *xs = reinterpret_cast<T *>(smraw);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int c0 = 0; c0 < R; c0 += RC) {
+        const int rc = min(RC, R - c0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < RC * ld; t += blockDim.x) {
+            int c = t / ld, l = t % ld;
+            xs[t] = (c < rc && l < n) ? x[(d.offU + l) * R + c0 + c] : T(0);
+        }
+        __syncthreads();
+        for (int rr = 0; rr < 8; ++rr) {
+            const int i = row0 + warp * 8 + rr;
+            if (i >= n) break;
+            const T *Mi = M + (int64_t)i * ld;
+            T acc[RC];
+#pragma unroll
+            for (int c = 0; c < RC; ++c) acc[c] = T(0);
+            for (int l = lane * W; l < ld; l += 32 * W) {
+                V mv = *reinterpret_cast<const V *>(Mi + l);
+                const T *mvp = reinterpret_cast<const T *>(&mv);
+#pragma unroll
+                for (int c = 0; c < RC; ++c) {
+                    V xv = *reinterpret_cast<const V *>(xs + c * ld + l);
+                    const T *xp = reinterpret_cast<const T *>(&xv);
+#pragma unroll
+                    for (int w = 0; w < W; ++w) acc[c] += mvp[w] * xp[w];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < RC; ++c) {
+                double v = warp_sum((double)acc[c]);
+                if (lane == 0 && c < rc) y[(d.offU + i) * R + c0 + c] = v;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ row kernels on subdomain matrices
+// residual of the torn system (FP64 assembled A^k): r = f - A u - [0; B_k^T lambda]
+__global__ void k_residual(const double *A, const SubdomainDesc *sd, int kbase, const double *f, const double *u,
+                           const int64_t *bt_ptr, const int64_t *bt_row, const double *lam, double *r, int R) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const SubdomainDesc d = sd[kbase + blockIdx.y];
+    for (int i = blockIdx.x * 8 + warp; i < d.nk; i += gridDim.x * 8) {
+        const double *Ai = A + d.offA + (int64_t)i * d.nk;
+        for (int c0 = 0; c0 < R; c0 += 8) {
+            const int rc = min(8, R - c0);
+            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int l = lane; l < d.nk; l += 32) {
+                double m = Ai[l];
+                const double *ul = u + (d.offV + l) * R + c0;
+                for (int c = 0; c < rc; ++c) acc[c] += m * ul[c];
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = warp_sum(acc[c]);
+            if (lane < rc) {
+                const int c = c0 + lane;
+                double v = f[(d.offV + i) * R + c] - acc[lane];
+                if (i >= d.nO && lam) {
+                    int64_t ui = d.offU + (i - d.nO);
+                    for (int64_t q = bt_ptr[ui]; q < bt_ptr[ui + 1]; ++q) {
+                        int64_t rr = bt_row[q];
+                        v -= rr > 0 ? lam[(rr - 1) * R + c] : -lam[(-rr - 1) * R + c];
+                    }
+                }
+                r[(d.offV + i) * R + c] = v;
+            }
+        }
+    }
+}
+
+// reduced forcing (eq. subForcing): fU = f_G - (A_GO A_OO^-1) f_O from rows G, columns O of the swept matrix
+template <typename T>
+__global__ void k_reduce_forcing(const T *pool, const SubdomainDesc *sd, int kbase, const double *f, double *fU,
+                                 int R) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const SubdomainDesc d = sd[kbase + blockIdx.y];
+    for (int i = blockIdx.x * 8 + warp; i < d.nG; i += gridDim.x * 8) {
+        const T *Mi = pool + d.offM + (int64_t)(d.nO + i) * d.ldM;
+        for (int c0 = 0; c0 < R; c0 += 8) {
+            const int rc = min(8, R - c0);
+            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int l = lane; l < d.nO; l += 32) {
+                double m = (double)Mi[l];
+                const double *xl = f + (d.offV + l) * R + c0;
+                for (int c = 0; c < rc; ++c) acc[c] += m * xl[c];
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = warp_sum(acc[c]);
+            if (lane < rc) fU[(d.offU + i) * R + c0 + lane] = f[(d.offV + d.nO + i) * R + c0 + lane] - acc[lane];
+        }
+    }
+}
+
+// back substitution (eq. backwardSubstitution): u_O = -(M_OO f_O + M_OG u_G) on the swept matrix;
+// the Gamma part of the subdomain vector is u_G
+template <typename T>
+__global__ void k_back_substitute(const T *pool, const SubdomainDesc *sd, int kbase, const double *f,
+                                  const double *uU, double *u, int R) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const SubdomainDesc d = sd[kbase + blockIdx.y];
+    for (int i = blockIdx.x * 8 + warp; i < d.nk; i += gridDim.x * 8) {
+        if (i >= d.nO) {
+            for (int c = lane; c < R; c += 32) u[(d.offV + i) * R + c] = uU[(d.offU + i - d.nO) * R + c];
+            continue;
+        }
+        const T *Mi = pool + d.offM + (int64_t)i * d.ldM;
+        for (int c0 = 0; c0 < R; c0 += 8) {
+            const int rc = min(8, R - c0);
+            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int l = lane; l < d.nO; l += 32) {
+                double m = (double)Mi[l];
+                const double *xl = f + (d.offV + l) * R + c0;
+                for (int c = 0; c < rc; ++c) acc[c] += m * xl[c];
+            }
+            for (int l = lane; l < d.nG; l += 32) {
+                double m = (double)Mi[d.nO + l];
+                const double *xl = uU + (d.offU + l) * R + c0;
+                for (int c = 0; c < rc; ++c) acc[c] += m * xl[c];
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = warp_sum(acc[c]);
+            if (lane < rc) u[(d.offV + i) * R + c0 + lane] = -acc[lane];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ loads and output
+// global load vector per dof; rhs column-major with leading dimension ndof.
+// kind 0: consistent P1 mass matrix over interior elements ((1 + [i==j]) |E| / ((d+1)(d+2)))
+__global__ void k_load_vector(const double *rhs, int kind, const double *xy, const int32_t *elems, int dim,
+                              const int64_t *inc_ptr, const int32_t *inc_el, int nc, int64_t ndof, int R, double *F) {
+    const int nv = dim + 1;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ndof * R; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t g = t / R;
+        int c = (int)(t % R);
+        if (kind == 1) { F[t] = rhs[(int64_t)c * ndof + g]; continue; }
+        int64_t node = g / nc;
+        int comp = (int)(g % nc);
+        double s = 0;
+        for (int64_t q = inc_ptr[node]; q < inc_ptr[node + 1]; ++q) {
+            const int32_t *en = elems + (int64_t)inc_el[q] * nv;
+            double meas;
+            if (dim == 1) meas = fabs(xy[en[1]] - xy[en[0]]);
+            else {
+                double ax = xy[2 * (int64_t)en[1]] - xy[2 * (int64_t)en[0]], ay = xy[2 * (int64_t)en[1] + 1] - xy[2 * (int64_t)en[0] + 1];
+                double bx = xy[2 * (int64_t)en[2]] - xy[2 * (int64_t)en[0]], by = xy[2 * (int64_t)en[2] + 1] - xy[2 * (int64_t)en[0] + 1];
+                meas = 0.5 * fabs(ax * by - ay * bx);
+            }
+            const double denom = dim == 1 ? 6.0 : 12.0;
+            for (int b = 0; b < nv; ++b)
+                s += (en[b] == node ? 2.0 : 1.0) * meas / denom * rhs[(int64_t)c * ndof + (int64_t)en[b] * nc + comp];
+        }
+        F[t] = s;
+    }
+}
+
+// subdomain loads f~ = F / zeta at the subdomain's dofs (eq. bilinear-multi5)
+__global__ void k_split_loads(const double *F, const int32_t *vdofs, const double *zeta_dof, int64_t nv, int R,
+                              double *f) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nv * R; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = t / R;
+        int c = (int)(t % R);
+        int64_t g = vdofs[i];
+        f[t] = F[g * R + c] / zeta_dof[g];
+    }
+}
+
+// f~ -= A^k_D g (Dirichlet coupling), warp per row; g column-major with leading dimension ndof
+__global__ void k_dirichlet(const double *AD, const SubdomainDesc *sd, const int32_t *ddofs, const int64_t *doff,
+                            const double *g, int64_t ndof, double *f, int R) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int k = blockIdx.y;
+    const SubdomainDesc d = sd[k];
+    const int32_t *dd = ddofs + doff[k];
+    for (int i = blockIdx.x * 8 + warp; i < d.nk; i += gridDim.x * 8) {
+        const double *Ai = AD + d.offAD + (int64_t)i * d.nD;
+        for (int c = 0; c < R; ++c) {
+            double s = 0;
+            for (int l = lane; l < d.nD; l += 32) s += Ai[l] * g[(int64_t)c * ndof + dd[l]];
+            s = warp_sum(s);
+            if (lane == 0) f[(d.offV + i) * R + c] -= s;
+        }
+    }
+}
+
+// nodal output: mean of the copies; Dirichlet dofs take g (or 0); column-major
+__global__ void k_output(const double *u, const int64_t *cp_ptr, const int64_t *cp_pos, const int8_t *node_dir, int nc,
+                         const double *g, int64_t ndof, int R, double *out) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ndof * R; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t gd = t % ndof;
+        int c = (int)(t / ndof);
+        double v = 0;
+        if (node_dir[gd / nc]) v = g ? g[(int64_t)c * ndof + gd] : 0.0;
+        else {
+            int64_t a = cp_ptr[gd], b = cp_ptr[gd + 1];
+            for (int64_t q = a; q < b; ++q) v += u[cp_pos[q] * R + c];
+            if (b > a) v /= (double)(b - a);
+        }
+        out[t] = v;
+    }
+}
+
+// ------------------------------------------------------------------ projection and coarse problem
+// g = Z^T B^T v per floating subdomain (one CTA each); v_is_u: v already lives in U
+__global__ void k_proj_g(const SubdomainDesc *sd, const int64_t *bt_ptr, const int64_t *bt_row, const double *v,
+                         int v_is_u, const double *Z, double *g, int R) {
+    const SubdomainDesc d = sd[blockIdx.x];
+    if (d.n_co == 0) return;
+    __shared__ double red[8][24];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int c0 = 0; c0 < R; c0 += 8) {
+        const int rc = min(8, R - c0);
+        double acc[3][8];
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 8; ++c) acc[a][c] = 0;
+        for (int64_t l = threadIdx.x; l < d.nG; l += blockDim.x) {
+            const int64_t ui = d.offU + l;
+            for (int c = 0; c < rc; ++c) {
+                double bt;
+                if (v_is_u) bt = v[ui * R + c0 + c];
+                else {
+                    bt = 0;
+                    for (int64_t q = bt_ptr[ui]; q < bt_ptr[ui + 1]; ++q) {
+                        int64_t rr = bt_row[q];
+                        bt += rr > 0 ? v[(rr - 1) * R + c0 + c] : -v[(-rr - 1) * R + c0 + c];
+                    }
+                }
+                for (int a = 0; a < d.n_co; ++a) acc[a][c] += Z[ui * 3 + a] * bt;
+            }
+        }
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 8; ++c) acc[a][c] = warp_sum(acc[a][c]);
+        __syncthreads();
+        if (lane == 0)
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 8; ++c) red[warp][a * 8 + c] = acc[a][c];
+        __syncthreads();
+        if (threadIdx.x < 24) {
+            int a = threadIdx.x / 8, c = threadIdx.x % 8;
+            double s = 0;
+            for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w][a * 8 + c];
+            if (a < d.n_co && c < rc) g[(int64_t)(d.co_off + a) * R + c0 + c] = s;
+        }
+    }
+}
+
+// alpha = (G^T G)^-1 g (one CTA)
+__global__ void k_coarse(const double *GtGinv, int nco, const double *g, double *alpha, int R) {
+    for (int t = threadIdx.x; t < nco * R; t += blockDim.x) {
+        int i = t / R, c = t % R;
+        double s = 0;
+        for (int j = 0; j < nco; ++j) s += GtGinv[(int64_t)i * nco + j] * g[(int64_t)j * R + c];
+        alpha[t] = s;
+    }
+}
+
+__device__ __forceinline__ double z_alpha(const SubdomainDesc *sd, const int32_t *u2sub, const double *Z,
+                                          const double *alpha, int64_t u, int c, int R) {
+    const SubdomainDesc d = sd[u2sub[u]];
+    double s = 0;
+    for (int a = 0; a < d.n_co; ++a) s += Z[u * 3 + a] * alpha[(int64_t)(d.co_off + a) * R + c];
+    return s;
+}
+
+// out = base + sign * B Z alpha (= G alpha) on Lambda
+__global__ void k_apply_galpha(const SubdomainDesc *sd, const int32_t *u2sub, const int64_t *Bp, const int64_t *Bm,
+                               const double *Z, const double *alpha, const double *base, double sign, double *out,
+                               int64_t nl, int R) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl * R; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = t / R;
+        int c = (int)(t % R);
+        double ga = z_alpha(sd, u2sub, Z, alpha, Bp[r], c, R) - z_alpha(sd, u2sub, Z, alpha, Bm[r], c, R);
+        out[t] = (base ? base[t] : 0.0) + sign * ga;
+    }
+}
+
+// uU += sign * Z alpha
+__global__ void k_apply_zalpha(const SubdomainDesc *sd, const int32_t *u2sub, const double *Z, const double *alpha,
+                               double sign, double *uU, int64_t nu, int R) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t u = t / R;
+        int c = (int)(t % R);
+        uU[t] += sign * z_alpha(sd, u2sub, Z, alpha, u, c, R);
+    }
+}
+
+// ------------------------------------------------------------------ reductions (fixed order)
+// partial[b * R + c] = sum over the block's grid-stride range of a*b (column c)
+__global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const double *a, const double *b, int64_t n, int R,
+                                                              double *partial) {
+    __shared__ double red[RED_THREADS / 32][8];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int c0 = 0; c0 < R; c0 += 8) {
+        const int rc = min(8, R - c0);
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            const double *ai = a + i * R + c0;
+            const double *bi = b + i * R + c0;
+            for (int c = 0; c < rc; ++c) acc[c] += ai[c] * bi[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = warp_sum(acc[c]);
+        __syncthreads();
+        if (lane == 0)
+            for (int c = 0; c < 8; ++c) red[warp][c] = acc[c];
+        __syncthreads();
+        if (threadIdx.x < rc) {
+            double s = 0;
+            for (int w = 0; w < RED_THREADS / 32; ++w) s += red[w][threadIdx.x];
+            partial[(int64_t)blockIdx.x * R + c0 + threadIdx.x] = s;
+        }
+    }
+}
+
+// max |a| and max |b| per column into partials
+__global__ void __launch_bounds__(RED_THREADS) k_absmax_partial(const double *a, const double *b, int64_t n, int R,
+                                                                 double *pa, double *pb) {
+    __shared__ double ra[RED_THREADS / 32], rb[RED_THREADS / 32];
+    for (int c = 0; c < R; ++c) {
+        double ma = 0, mb = 0;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            ma = fmax(ma, fabs(a[i * R + c]));
+            mb = fmax(mb, fabs(b[i * R + c]));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            ma = fmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+            mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+        }
+        __syncthreads();
+        if (threadIdx.x % 32 == 0) { ra[threadIdx.x / 32] = ma; rb[threadIdx.x / 32] = mb; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double x = 0, y = 0;
+            for (int w = 0; w < RED_THREADS / 32; ++w) { x = fmax(x, ra[w]); y = fmax(y, rb[w]); }
+            pa[(int64_t)blockIdx.x * R + c] = x;
+            pb[(int64_t)blockIdx.x * R + c] = y;
+        }
+    }
+}
+
+// PCG scalar state, per right-hand side
+struct PcgScalars {
+    double *nPd, *yw_old, *yw, *eta, *beta, *relres, *corr;
+    int *active, *iters, *n_active;
+};
+
+__device__ __forceinline__ double sum_partials(const double *partial, int c, int R) {
+    double s = 0;
+    for (int b = 0; b < RED_BLOCKS; ++b) s += partial[(int64_t)b * R + c];
+    return s;
+}
+
+__global__ void k_rel_correction(const double *pa, const double *pb, int R, PcgScalars s) {
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+        double a = 0, b = 0;
+        for (int bl = 0; bl < RED_BLOCKS; ++bl) { a = fmax(a, pa[(int64_t)bl * R + c]); b = fmax(b, pb[(int64_t)bl * R + c]); }
+        s.corr[c] = b > 0 ? a / b : (a > 0 ? 1.0 : 0.0);
+    }
+}
+
+__global__ void k_set_norm_pd(const double *partial, PcgScalars s, int R) {
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+        s.nPd[c] = sqrt(sum_partials(partial, c, R));
+        s.active[c] = 1;
+        s.iters[c] = 0;
+        s.yw_old[c] = 1.0;
+        s.relres[c] = 1.0;
+    }
+    if (threadIdx.x == 0) *s.n_active = R;
+}
+
+// after w = P r: update the active mask
+__global__ void k_check(const double *partial, PcgScalars s, double tol, int max_it, int R) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+        double nw = sqrt(sum_partials(partial, c, R));
+        double ref = s.nPd[c];
+        if (s.active[c]) s.relres[c] = ref > 0 ? nw / ref : 0.0;
+        if (s.active[c] && (nw <= tol * ref || s.iters[c] >= max_it)) s.active[c] = 0;
+        if (s.active[c]) atomicAdd(&cnt, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *s.n_active = cnt;
+}
+
+__global__ void k_beta(const double *partial, PcgScalars s, int R) {
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+        double yw = sum_partials(partial, c, R);
+        s.yw[c] = yw;
+        s.beta[c] = (s.iters[c] == 0 || s.yw_old[c] == 0.0) ? 0.0 : yw / s.yw_old[c];
+    }
+}
+
+__global__ void k_eta(const double *partial, PcgScalars s, int R) {
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+        double pq = sum_partials(partial, c, R);
+        bool act = s.active[c] != 0;
+        s.eta[c] = (act && pq != 0.0) ? s.yw[c] / pq : 0.0;
+        if (act) { s.yw_old[c] = s.yw[c]; s.iters[c] += 1; }
+    }
+}
+
+__global__ void k_update_p(const double *y, const double *beta, const int *active, double *p, int64_t n, int R) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * R; t += (int64_t)gridDim.x * blockDim.x) {
+        int c = (int)(t % R);
+        if (active[c]) p[t] = y[t] + beta[c] * p[t];
+    }
+}
+
+__global__ void k_update_lr(const double *p, const double *q, const double *eta, double *lam, double *r, int64_t n,
+                            int R) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * R; t += (int64_t)gridDim.x * blockDim.x) {
+        int c = (int)(t % R);
+        double e = eta[c];
+        lam[t] += e * p[t];
+        r[t] -= e * q[t];
+    }
+}
+
+// ====================================================================== host orchestration
+
+struct Runner {
+    nlfeti_problem *p;
+    SolveWS &ws;
+    cudaStream_t st;
+    int R;
+    PcgScalars S;
+    const SubdomainDesc *sd;
+
+    Runner(nlfeti_problem *pp, SolveWS &w, cudaStream_t s) : p(pp), ws(w), st(s), R(w.R) {
+        double *b = ws.scal.as<double>();
+        S.nPd = b; S.yw_old = b + R; S.yw = b + 2 * R; S.eta = b + 3 * R; S.beta = b + 4 * R; S.relres = b + 5 * R;
+        S.corr = b + 6 * R;
+        int *ib = reinterpret_cast<int *>(b + 7 * R);
+        S.active = ib; S.iters = ib + R; S.n_active = ib + 2 * R;
+        sd = p->d_sd.as<SubdomainDesc>();
+        set_attributes();
+    }
+
+    void dot(const double *a, const double *b, int64_t n) {
+        k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, n, R, ws.partial.as<double>());
+    }
+
+    // out = P v (out may alias v)
+    void project(const double *v, double *out) {
+        const int64_t nl = p->n_lambda;
+        if (p->n_co == 0) {
+            if (out != v) NLF_CUDA(cudaMemcpyAsync(out, v, sizeof(double) * nl * R, cudaMemcpyDeviceToDevice, st));
+            return;
+        }
+        k_proj_g<<<p->K, 256, 0, st>>>(sd, p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), v, 0,
+                                       p->d_Z.as<double>(), ws.gco.as<double>(), R);
+        k_coarse<<<1, 256, 0, st>>>(p->d_GtGinv.as<double>(), p->n_co, ws.gco.as<double>(), ws.alpha.as<double>(), R);
+        k_apply_galpha<<<grid_for(nl * R), 256, 0, st>>>(sd, p->d_u2sub.as<int32_t>(), p->d_Bp.as<int64_t>(),
+                                                         p->d_Bm.as<int64_t>(), p->d_Z.as<double>(),
+                                                         ws.alpha.as<double>(), v, -1.0, out, nl, R);
+    }
+
+    template <typename T, int RC> void symv_launch(const T *base, int use_sp, const int32_t *it, int nitems, const T *x,
+                                                   double *y, size_t sm) {
+        k_symv<T, RC><<<nitems, 256, sm, st>>>(base, use_sp, sd, it, x, y, R);
+    }
+
+    // shared-memory limits of every apply variant, set once outside any graph capture
+    void set_attributes() {
+        const int sm = (int)(sizeof(double) * 8 * p->max_ldG);
+        if (sm > 227 * 1024) fail(NLFETI_E_INVALID, "an interface block is too large for the apply kernel");
+        NLF_CUDA(cudaFuncSetAttribute(k_symv<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        NLF_CUDA(cudaFuncSetAttribute(k_symv<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        NLF_CUDA(cudaFuncSetAttribute(k_symv<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        NLF_CUDA(cudaFuncSetAttribute(k_symv<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        NLF_CUDA(cudaFuncSetAttribute(k_symv<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        NLF_CUDA(cudaFuncSetAttribute(k_symv<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        NLF_CUDA(cudaFuncSetAttribute(k_symv<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        NLF_CUDA(cudaFuncSetAttribute(k_symv<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    }
+
+    // y = S^+ x (use_sp = 1) or S x (use_sp = 0) on every subdomain
+    template <typename T> void symv(const OpPool<T> &pool, int use_sp, const T *x, double *y) {
+        if (p->n_u == 0) return;
+        const int rc = R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1));
+        const size_t sm = sizeof(T) * (size_t)rc * p->max_ldG;
+        const T *base = use_sp ? pool.Sp.template as<T>() : pool.S.template as<T>();
+        auto go = [&](const int32_t *it, int nitems) {
+            if (nitems <= 0) return;
+            switch (rc) {
+                case 8: symv_launch<T, 8>(base, use_sp, it, nitems, x, y, sm); break;
+                case 4: symv_launch<T, 4>(base, use_sp, it, nitems, x, y, sm); break;
+                case 2: symv_launch<T, 2>(base, use_sp, it, nitems, x, y, sm); break;
+                default: symv_launch<T, 1>(base, use_sp, it, nitems, x, y, sm); break;
+            }
+        };
+        const int32_t *items = p->d_items.as<int32_t>();
+        if (p->opt.batched) go(items, p->n_items);
+        else
+            for (int k = 0; k < p->K; ++k) go(items + 2 * p->item_off[k], p->item_off[k + 1] - p->item_off[k]);
+    }
+
+    template <typename T> void applyF(const OpPool<T> &pool, const double *v, double *out, const double *cvec = nullptr) {
+        const int64_t nl = p->n_lambda, nu = p->n_u;
+        T *x = ws.xU.as<T>();
+        k_gather_bt<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), v, x, nu, R);
+        symv<T>(pool, 1, x, ws.yU.as<double>());
+        k_gather_b<<<grid_for(nl * R), 256, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), ws.yU.as<double>(),
+                                                     cvec, out, nl, R);
+    }
+
+    template <typename T> void applyMinv(const OpPool<T> &pool, const double *v, double *out) {
+        const int64_t nl = p->n_lambda, nu = p->n_u;
+        T *x = ws.xU.as<T>();
+        k_gather_bdt<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_BDt_ptr.as<int64_t>(), p->d_BDt_row.as<int64_t>(),
+                                                          p->d_BDt_val.as<double>(), v, x, nu, R);
+        symv<T>(pool, 0, x, ws.yU.as<double>());
+        k_gather_bd<<<grid_for(nl * R), 256, 0, st>>>(p->d_BD_ptr.as<int64_t>(), p->d_BD_col.as<int64_t>(),
+                                                      p->d_BD_val.as<double>(), ws.yU.as<double>(), out, nl, R);
+    }
+
+    template <typename T> void iteration(const OpPool<T> &pool, double tol, int max_it) {
+        const int64_t nl = p->n_lambda;
+        double *r = ws.r.as<double>(), *w = ws.w.as<double>(), *z = ws.z.as<double>(), *y = ws.y.as<double>(),
+               *pv = ws.pv.as<double>(), *q = ws.q.as<double>(), *lam = ws.dlam.as<double>();
+        project(r, w);
+        dot(w, w, nl);
+        k_check<<<1, 256, 0, st>>>(ws.partial.as<double>(), S, tol, max_it, R);
+        applyMinv<T>(pool, w, z);
+        project(z, y);
+        dot(y, w, nl);
+        k_beta<<<1, 256, 0, st>>>(ws.partial.as<double>(), S, R);
+        k_update_p<<<grid_for(nl * R), 256, 0, st>>>(y, S.beta, S.active, pv, nl, R);
+        applyF<T>(pool, pv, q);
+        dot(pv, q, nl);
+        k_eta<<<1, 256, 0, st>>>(ws.partial.as<double>(), S, R);
+        k_update_lr<<<grid_for(nl * R), 256, 0, st>>>(pv, q, S.eta, lam, r, nl, R);
+    }
+
+    // one FETI pass on subdomain loads ws.res; constraint right-hand side ws.cvec when with_c.
+    // Output: ws.du (subdomain vectors) and ws.dlam.
+    template <typename T> PassInfo pass(const OpPool<T> &pool, double tol, int max_it, bool with_c) {
+        PassInfo info;
+        const int64_t nl = p->n_lambda, nu = p->n_u;
+        const double *f = ws.res.as<double>();
+        const bool batched = p->opt.batched != 0;
+        auto per_sub = [&](auto &&launch) {
+            if (batched) launch(0, p->K);
+            else for (int k = 0; k < p->K; ++k) launch(k, 1);
+        };
+        if (nu > 0)
+            per_sub([&](int kb, int nk) {
+                k_reduce_forcing<T><<<dim3(64, nk), 256, 0, st>>>(pool.M.template as<T>(), sd, kb, f, ws.fU.as<double>(), R);
+            });
+        double *lam = ws.dlam.as<double>();
+        T *x = ws.xU.as<T>();
+        if (nl > 0) {
+            k_cast<T><<<grid_for(nu * R), 256, 0, st>>>(ws.fU.as<double>(), x, nu * R);
+            symv<T>(pool, 1, x, ws.yU.as<double>());
+            k_gather_b<<<grid_for(nl * R), 256, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), ws.yU.as<double>(),
+                                                         with_c ? ws.cvec.as<double>() : nullptr, ws.d.as<double>(), nl, R);
+            if (p->n_co > 0) {
+                k_proj_g<<<p->K, 256, 0, st>>>(sd, nullptr, nullptr, ws.fU.as<double>(), 1, p->d_Z.as<double>(),
+                                               ws.gco.as<double>(), R);
+                k_coarse<<<1, 256, 0, st>>>(p->d_GtGinv.as<double>(), p->n_co, ws.gco.as<double>(), ws.alpha.as<double>(), R);
+                k_apply_galpha<<<grid_for(nl * R), 256, 0, st>>>(sd, p->d_u2sub.as<int32_t>(), p->d_Bp.as<int64_t>(),
+                                                                 p->d_Bm.as<int64_t>(), p->d_Z.as<double>(),
+                                                                 ws.alpha.as<double>(), nullptr, 1.0, lam, nl, R);
+            } else {
+                NLF_CUDA(cudaMemsetAsync(lam, 0, sizeof(double) * nl * R, st));
+            }
+            applyF<T>(pool, lam, ws.q.as<double>());
+            k_sub<<<grid_for(nl * R), 256, 0, st>>>(ws.d.as<double>(), ws.q.as<double>(), ws.r.as<double>(), nl * R);
+            project(ws.d.as<double>(), ws.w.as<double>());
+            dot(ws.w.as<double>(), ws.w.as<double>(), nl);
+            k_set_norm_pd<<<1, 256, 0, st>>>(ws.partial.as<double>(), S, R);
+            NLF_CUDA(cudaMemsetAsync(ws.pv.p, 0, sizeof(double) * nl * R, st));
+            const int chunk = 4;
+            int done = 0, n_active = R;
+            cudaGraphExec_t exec = nullptr;
+            if (batched) {
+                cudaGraph_t graph;
+                NLF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                for (int i = 0; i < chunk; ++i) iteration<T>(pool, tol, max_it);
+                NLF_CUDA(cudaStreamEndCapture(st, &graph));
+                NLF_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+                NLF_CUDA(cudaGraphDestroy(graph));
+            }
+            while (done <= max_it) {
+                if (batched) NLF_CUDA(cudaGraphLaunch(exec, st));
+                else for (int i = 0; i < chunk; ++i) iteration<T>(pool, tol, max_it);
+                done += chunk;
+                NLF_CUDA(cudaMemcpyAsync(ws.host_flag.data(), S.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+                NLF_CUDA(cudaStreamSynchronize(st));
+                n_active = ws.host_flag[0];
+                if (n_active == 0) break;
+            }
+            if (exec) NLF_CUDA(cudaGraphExecDestroy(exec));
+            // alpha from a fresh residual d - F lambda (eq. forAlpha)
+            applyF<T>(pool, lam, ws.q.as<double>());
+            k_sub<<<grid_for(nl * R), 256, 0, st>>>(ws.d.as<double>(), ws.q.as<double>(), ws.r.as<double>(), nl * R);
+            // u_G = S^+ (fU - B^T lambda) - Z alpha  (eq. forU)
+            k_gather_bt<double><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(),
+                                                                  lam, ws.uU.as<double>(), nu, R);
+            k_sub<<<grid_for(nu * R), 256, 0, st>>>(ws.fU.as<double>(), ws.uU.as<double>(), ws.uU.as<double>(), nu * R);
+            k_cast<T><<<grid_for(nu * R), 256, 0, st>>>(ws.uU.as<double>(), x, nu * R);
+            symv<T>(pool, 1, x, ws.uU.as<double>());
+            if (p->n_co > 0) {
+                k_proj_g<<<p->K, 256, 0, st>>>(sd, p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), ws.r.as<double>(),
+                                               0, p->d_Z.as<double>(), ws.gco.as<double>(), R);
+                k_coarse<<<1, 256, 0, st>>>(p->d_GtGinv.as<double>(), p->n_co, ws.gco.as<double>(), ws.alpha.as<double>(), R);
+                k_apply_zalpha<<<grid_for(nu * R), 256, 0, st>>>(sd, p->d_u2sub.as<int32_t>(), p->d_Z.as<double>(),
+                                                                 ws.alpha.as<double>(), -1.0, ws.uU.as<double>(), nu, R);
+            }
+            std::vector<int> it(R);
+            std::vector<double> rr(R);
+            NLF_CUDA(cudaMemcpyAsync(it.data(), S.iters, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
+            NLF_CUDA(cudaMemcpyAsync(rr.data(), S.relres, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+            NLF_CUDA(cudaStreamSynchronize(st));
+            info.iterations = *std::max_element(it.begin(), it.end());
+            info.relres = *std::max_element(rr.begin(), rr.end());
+            info.converged = info.relres <= tol || n_active == 0;
+            for (int c = 0; c < R; ++c)
+                if (!(rr[c] <= tol)) info.converged = false;
+        } else if (nu > 0) {
+            k_cast<T><<<grid_for(nu * R), 256, 0, st>>>(ws.fU.as<double>(), x, nu * R);
+            symv<T>(pool, 1, x, ws.uU.as<double>());
+        }
+        per_sub([&](int kb, int nk) {
+            k_back_substitute<T><<<dim3(64, nk), 256, 0, st>>>(pool.M.template as<T>(), sd, kb, f, ws.uU.as<double>(),
+                                                              ws.du.as<double>(), R);
+        });
+        NLF_CUDA(cudaGetLastError());
+        return info;
+    }
+};
+
+}  // namespace
+
+void SolveWS::ensure(nlfeti_problem *p, int nR) {
+    nlfeti_ctx *c = p->ctx;
+    if (R == nR && prob == p) return;
+    // buffers about to be replaced may still be read by queued work
+    NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
+    R = nR;
+    prob = p;
+    const int64_t nl = std::max<int64_t>(1, p->n_lambda), nu = std::max<int64_t>(1, p->n_u),
+                  nv = std::max<int64_t>(1, p->sum_nk), nd = std::max<int64_t>(1, p->n_dofs_total);
+    const int64_t nco = std::max(1, p->n_co);
+    auto alloc = [&](DevMem &m, size_t bytes) {
+        if (async_stream) m.alloc_async(async_stream, bytes);
+        else m.alloc(c, bytes);
+    };
+    auto A = [&](DevMem &m, int64_t n) { alloc(m, sizeof(double) * n * R); };
+    A(lam, nl); A(r, nl); A(w, nl); A(z, nl); A(y, nl); A(pv, nl); A(q, nl); A(d, nl); A(cvec, nl); A(dlam, nl);
+    A(fU, nu); A(yU, nu); A(uU, nu); A(xU, nu);
+    A(ftil, nv); A(res, nv); A(u, nv); A(du, nv);
+    A(F, nd);
+    A(gco, nco); A(alpha, nco);
+    alloc(partial, sizeof(double) * RED_BLOCKS * R);
+    alloc(partial2, sizeof(double) * RED_BLOCKS * R);
+    alloc(scal, sizeof(double) * R * 7 + sizeof(int) * (2 * R + 4));
+    host_flag.assign(4, 0);
+}
+
+void to_interleaved(const double *colmajor, double *inter, int64_t n, int R, cudaStream_t st) {
+    k_transpose_cr<<<grid_for(n * R), 256, 0, st>>>(colmajor, inter, n, R, 1);
+}
+void to_colmajor(const double *inter, double *colmajor, int64_t n, int R, cudaStream_t st) {
+    k_transpose_cr<<<grid_for(n * R), 256, 0, st>>>(inter, colmajor, n, R, 0);
+}
+
+void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rhs_kind, const double *d_rhs,
+                  const double *d_g, double *d_out, nlfeti_stats *stats) {
+    ws.ensure(p, R);
+    Runner run(p, ws, st);
+    const int64_t ndof = p->n_dofs_total, nv = p->sum_nk, nl = p->n_lambda;
+    const MeshHost &m = p->mesh;
+    // loads (eq. bil1 load functional, split by zeta as eq. bilinear-multi5)
+    k_load_vector<<<grid_for(ndof * R), 256, 0, st>>>(d_rhs, rhs_kind, p->d_xy.as<double>(), p->d_elems.as<int32_t>(),
+                                                      m.dim, p->d_nodeinc_ptr.as<int64_t>(), p->d_nodeinc_el.as<int32_t>(),
+                                                      p->nc, ndof, R, ws.F.as<double>());
+    k_split_loads<<<grid_for(nv * R), 256, 0, st>>>(ws.F.as<double>(), p->d_vdofs.as<int32_t>(),
+                                                    p->d_zeta_dof.as<double>(), nv, R, ws.ftil.as<double>());
+    if (d_g)
+        k_dirichlet<<<dim3(32, p->K), 256, 0, st>>>(p->d_AD.as<double>(), p->d_sd.as<SubdomainDesc>(),
+                                                    p->d_ddofs.as<int32_t>(), p->d_doff.as<int64_t>(), d_g, ndof,
+                                                    ws.ftil.as<double>(), R);
+    NLF_CUDA(cudaGetLastError());
+    nlfeti_stats s{};
+    const bool mixed = p->opt.precision == 1;
+    if (!mixed) {
+        if (!p->op64.ready) fail(NLFETI_E_INVALID, "FP64 operators not factored");
+        NLF_CUDA(cudaMemcpyAsync(ws.res.p, ws.ftil.p, sizeof(double) * nv * R, cudaMemcpyDeviceToDevice, st));
+        PassInfo pi = run.pass<double>(p->op64, p->opt.tol, p->opt.max_it, false);
+        NLF_CUDA(cudaMemcpyAsync(ws.u.p, ws.du.p, sizeof(double) * nv * R, cudaMemcpyDeviceToDevice, st));
+        s.iterations = pi.iterations;
+        s.refine_sweeps = 1;
+        s.final_rel_residual = pi.relres;
+        if (!pi.converged) {
+            k_output<<<grid_for(ndof * R), 256, 0, st>>>(ws.u.as<double>(), p->d_cp_ptr.as<int64_t>(), p->d_cp_pos.as<int64_t>(),
+                                                         p->d_node_dir.as<int8_t>(), p->nc, d_g, ndof, R, d_out);
+            if (stats) *stats = s;
+            fail(NLFETI_E_NOT_CONVERGED, "PCG did not reach the tolerance within max_it");
+        }
+    } else {
+        if (!p->op32.ready) fail(NLFETI_E_INVALID, "FP32 operators not factored");
+        NLF_CUDA(cudaMemsetAsync(ws.u.p, 0, sizeof(double) * nv * R, st));
+        if (nl > 0) NLF_CUDA(cudaMemsetAsync(ws.lam.p, 0, sizeof(double) * nl * R, st));
+        bool ok = false;
+        for (int sw = 0; sw < std::max(1, p->opt.max_refine); ++sw) {
+            if (sw == 0) {
+                NLF_CUDA(cudaMemcpyAsync(ws.res.p, ws.ftil.p, sizeof(double) * nv * R, cudaMemcpyDeviceToDevice, st));
+            } else {
+                k_residual<<<dim3(64, p->K), 256, 0, st>>>(p->d_A.as<double>(), p->d_sd.as<SubdomainDesc>(), 0,
+                                                          ws.ftil.as<double>(), ws.u.as<double>(), p->d_Bt_ptr.as<int64_t>(),
+                                                          p->d_Bt_row.as<int64_t>(), nl > 0 ? ws.lam.as<double>() : nullptr,
+                                                          ws.res.as<double>(), R);
+                if (nl > 0)
+                    k_constraint_residual<<<grid_for(nl * R), 256, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(),
+                                                                            p->d_u2v.as<int64_t>(), ws.u.as<double>(),
+                                                                            ws.cvec.as<double>(), nl, R);
+            }
+            PassInfo pi = run.pass<float>(p->op32, p->opt.inner_tol, p->opt.max_it, sw > 0);
+            s.iterations += pi.iterations;
+            s.refine_sweeps = sw + 1;
+            s.final_rel_residual = pi.relres;
+            k_axpy<<<grid_for(nv * R), 256, 0, st>>>(ws.u.as<double>(), ws.du.as<double>(), 1.0, nv * R);
+            if (nl > 0) k_axpy<<<grid_for(nl * R), 256, 0, st>>>(ws.lam.as<double>(), ws.dlam.as<double>(), 1.0, nl * R);
+            k_absmax_partial<<<RED_BLOCKS, RED_THREADS, 0, st>>>(ws.du.as<double>(), ws.u.as<double>(), nv, R,
+                                                                 ws.partial.as<double>(), ws.partial2.as<double>());
+            k_rel_correction<<<1, 256, 0, st>>>(ws.partial.as<double>(), ws.partial2.as<double>(), R, run.S);
+            std::vector<double> corr(R);
+            NLF_CUDA(cudaMemcpyAsync(corr.data(), run.S.corr, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+            NLF_CUDA(cudaStreamSynchronize(st));
+            s.rel_correction = *std::max_element(corr.begin(), corr.end());
+            if (s.rel_correction <= p->opt.refine_tol) { ok = true; break; }
+        }
+        if (!ok) {
+            k_output<<<grid_for(ndof * R), 256, 0, st>>>(ws.u.as<double>(), p->d_cp_ptr.as<int64_t>(), p->d_cp_pos.as<int64_t>(),
+                                                         p->d_node_dir.as<int8_t>(), p->nc, d_g, ndof, R, d_out);
+            if (stats) *stats = s;
+            fail(NLFETI_E_NOT_CONVERGED, "iterative refinement did not reach refine_tol within max_refine sweeps");
+        }
+    }
+    k_output<<<grid_for(ndof * R), 256, 0, st>>>(ws.u.as<double>(), p->d_cp_ptr.as<int64_t>(), p->d_cp_pos.as<int64_t>(),
+                                                 p->d_node_dir.as<int8_t>(), p->nc, d_g, ndof, R, d_out);
+    NLF_CUDA(cudaGetLastError());
+    if (stats) *stats = s;
+}
+
+void apply_operator(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int op, int precision, int R, const double *in,
+                    double *out) {
+    ws.ensure(p, R);
+    Runner run(p, ws, st);
+    const int64_t nl = p->n_lambda, nu = p->n_u;
+    auto go = [&](auto &pool, auto tag) {
+        using T = decltype(tag);
+        if (!pool.ready) fail(NLFETI_E_INVALID, "operators of the requested precision are not factored");
+        switch (op) {
+            case 0: run.applyF<T>(pool, in, out); break;
+            case 1: run.applyMinv<T>(pool, in, out); break;
+            case 2: run.project(in, out); break;
+            case 3:
+            case 4: {
+                T *x = ws.xU.as<T>();
+                k_cast<T><<<grid_for(nu * R), 256, 0, st>>>(in, x, nu * R);
+                run.symv<T>(pool, op == 3 ? 1 : 0, x, out);
+                break;
+            }
+            default: fail(NLFETI_E_INVALID, "unknown operator");
+        }
+    };
+    (void)nl;
+    if (precision == 0) go(p->op64, double{});
+    else go(p->op32, float{});
+    NLF_CUDA(cudaGetLastError());
+    NLF_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace nlf

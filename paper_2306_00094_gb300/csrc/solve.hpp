@@ -1,0 +1,41 @@
+// Solve-phase workspace and entry points (internal).
+#pragma once
+
+#include "internal.hpp"
+
+namespace nlf {
+
+struct SolveWS {
+    nlfeti_problem *prob = nullptr;
+    int R = 0;
+    DevMem lam, r, w, z, y, pv, q, d, cvec, dlam;      // Lambda space (FP64)
+    DevMem fU, yU, uU, xU;                              // U space
+    DevMem ftil, res, u, du;                            // concatenated subdomain vectors
+    DevMem F;                                           // global load vector per dof
+    DevMem gco, alpha;                                  // coarse space
+    DevMem partial, partial2, scal;                     // reductions and PCG scalars
+    DevMem in_rhs, in_g, out_u;                         // staging for host-array solves
+    std::vector<int> host_flag;
+    cudaStream_t async_stream = nullptr;   // set: stream-ordered allocations (server slots)
+    void ensure(nlfeti_problem *p, int R);
+};
+
+struct PassInfo {
+    int iterations = 0;
+    double relres = 0.0;
+    bool converged = true;
+};
+
+// Full solve on device arrays: rhs / g column-major (n_dofs x R), out column-major.
+void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rhs_kind, const double *d_rhs,
+                  const double *d_g, double *d_out, nlfeti_stats *stats);
+
+// Apply one operator (0 F, 1 M^-1, 2 P, 3 S^+, 4 S) to device vectors in the interleaved layout.
+void apply_operator(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int op, int precision, int R, const double *in,
+                    double *out);
+
+// Interleaved <-> column-major conversions (device).
+void to_interleaved(const double *colmajor, double *inter, int64_t n, int R, cudaStream_t st);
+void to_colmajor(const double *inter, double *colmajor, int64_t n, int R, cudaStream_t st);
+
+}  // namespace nlf

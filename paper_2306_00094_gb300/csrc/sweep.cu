@@ -1,0 +1,657 @@
+// Subdomain operators by blocked symmetric sweeps, batched over all subdomains.
+//
+// The sweep operator on a pivot block J of a symmetric matrix M replaces
+//   M_JJ -> -M_JJ^-1,  M_iJ -> M_iJ M_JJ^-1,  M_Jl -> M_JJ^-1 M_Jl,  M_il -> M_il - M_iJ M_JJ^-1 M_Jl.
+// Sweeping every Omega_k pivot block of the subdomain matrix A^k (Omega-first order)
+// yields in one pass (the block Cholesky identity eq. splittingBlockCholesky):
+//   [ -A_OO^-1            A_OO^-1 A_OG ]
+//   [ A_GO A_OO^-1        S_k          ]   with S_k = A_GG - A_GO A_OO^-1 A_OG (eq. subSchurComplement).
+// A copy of S_k with the pinned dofs of a floating subdomain replaced by unit rows and
+// columns (Sec. 5.3) is swept over all its pivots to give -S~_k^-1; zeroing the pinned
+// rows/columns and projecting onto range(S_k) = ker(Z_k^T) gives the Moore-Penrose
+// pseudo-inverse S_k^+ (eq. forU), stored explicitly.  Every FETI iteration then needs
+// only dense symmetric products with S_k^+ and S_k.
+//
+// Pivot blocks are NB = 64 wide; a step is three launches over all subdomains: invert
+// the pivot block (one CTA per subdomain, in shared memory), form the pivot panels,
+// update all tiles (64x64 CTA tiles, 4x4 register blocking).  A non-positive pivot
+// sets the device status word (NLFETI_E_NOT_SPD) instead of trapping.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.hpp"
+
+namespace nlf {
+namespace {
+
+constexpr int NB = 64;
+constexpr int TILE = 64;
+
+template <typename T> struct SweepArgs {
+    T *M;               // pool base
+    T *pan;             // per subdomain: n x NB (M_iJ D^-1)
+    T *old;             // per subdomain: n x NB (M_iJ before the step)
+    T *dinv;            // per subdomain: NB x NB
+    const SubdomainDesc *sd;
+    const int64_t *moff;      // per subdomain: matrix offset in the pool
+    const int32_t *mdim;      // per subdomain: matrix order
+    const int32_t *mld;       // per subdomain: leading dimension
+    const int32_t *pend;      // per subdomain: pivots [0, pend) are swept in this phase
+    const int64_t *scr_off;   // per subdomain: scratch offset (rows)
+    int j0;                   // first pivot of this step
+    int *flag;
+};
+
+// sweep a small symmetric block (n <= 128) held in shared memory, row stride ld
+template <typename T>
+__device__ bool sweep_block_shared(T *S, int n, int ld, T *rowp) {
+    bool ok = true;
+    for (int p = 0; p < n; ++p) {
+        __syncthreads();
+        T d = S[p * ld + p];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) rowp[i] = S[p * ld + i];
+        __syncthreads();
+        if (!(d > T(0))) ok = false;
+        T inv = T(1) / d;
+        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+            int i = t / n, l = t % n;
+            T v;
+            if (i == p && l == p) v = -inv;
+            else if (i == p) v = rowp[l] * inv;
+            else if (l == p) v = rowp[i] * inv;
+            else v = S[i * ld + l] - rowp[i] * rowp[l] * inv;
+            S[i * ld + l] = v;
+        }
+    }
+    __syncthreads();
+    return ok;
+}
+
+template <typename T> __global__ void k_pivot(SweepArgs<T> a) {
+    const int k = blockIdx.x;
+    const int pend = a.pend[k];
+    if (a.j0 >= pend) return;
+    const int b = min(NB, pend - a.j0);
+    const int ld = a.mld[k];
+    T *M = a.M + a.moff[k];
+    __shared__ T S[NB * NB];
+    __shared__ T rowp[NB];
+    for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+        int i = t / b, l = t % b;
+        S[i * NB + l] = M[(int64_t)(a.j0 + i) * ld + a.j0 + l];
+    }
+    bool ok = sweep_block_shared(S, b, NB, rowp);
+    if (!ok && threadIdx.x == 0) atomicMax(a.flag, 1);
+    T *D = a.dinv + (int64_t)k * NB * NB;
+    for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+        int i = t / b, l = t % b;
+        D[i * NB + l] = -S[i * NB + l];       // D^-1
+    }
+}
+
+// panels: old_i = M_iJ, pan_i = M_iJ D^-1 for every row i
+template <typename T> __global__ void k_panel(SweepArgs<T> a) {
+    const int k = blockIdx.y;
+    const int pend = a.pend[k];
+    if (a.j0 >= pend) return;
+    const int b = min(NB, pend - a.j0);
+    const int n = a.mdim[k];
+    const int ld = a.mld[k];
+    const int i = blockIdx.x * (blockDim.x / NB) + threadIdx.x / NB;
+    const int t = threadIdx.x % NB;
+    if (i >= n) return;
+    const T *M = a.M + a.moff[k];
+    const T *D = a.dinv + (int64_t)k * NB * NB;
+    T *old = a.old + a.scr_off[k] * NB;
+    T *pan = a.pan + a.scr_off[k] * NB;
+    if (t < b) {
+        T acc = 0;
+        for (int s = 0; s < b; ++s) acc += M[(int64_t)i * ld + a.j0 + s] * D[s * NB + t];
+        old[(int64_t)i * NB + t] = M[(int64_t)i * ld + a.j0 + t];
+        pan[(int64_t)i * NB + t] = acc;
+    }
+}
+
+// tile update of every entry (i, l)
+template <typename T> __global__ void __launch_bounds__(256) k_update(SweepArgs<T> a) {
+    const int k = blockIdx.z;
+    const int pend = a.pend[k];
+    if (a.j0 >= pend) return;
+    const int n = a.mdim[k];
+    const int ld = a.mld[k];
+    const int nt = (n + TILE - 1) / TILE;
+    const int ti = blockIdx.y, tl = blockIdx.x;
+    if (ti >= nt || tl >= nt) return;
+    const int b = min(NB, pend - a.j0);
+    const int j0 = a.j0, j1 = a.j0 + b;
+    T *M = a.M + a.moff[k];
+    const T *old = a.old + a.scr_off[k] * NB;
+    const T *pan = a.pan + a.scr_off[k] * NB;
+    const T *D = a.dinv + (int64_t)k * NB * NB;
+    extern __shared__ unsigned char smraw[];
+    T *Ps = reinterpret_cast<T *>(smraw);            // [NB][TILE] : pan rows of tile i, transposed
+    T *Os = Ps + NB * TILE;                            // [NB][TILE] : old rows of tile l, transposed
+    const int r0 = ti * TILE, c0 = tl * TILE;
+    for (int t = threadIdx.x; t < NB * TILE; t += blockDim.x) {
+        int rr = t / NB, s = t % NB;
+        int gi = r0 + rr, gl = c0 + rr;
+        Ps[s * TILE + rr] = (gi < n && s < b) ? pan[(int64_t)gi * NB + s] : T(0);
+        Os[s * TILE + rr] = (gl < n && s < b) ? old[(int64_t)gl * NB + s] : T(0);
+    }
+    __syncthreads();
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+    for (int s = 0; s < b; ++s) {
+        T pa[4], ob[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pa[u] = Ps[s * TILE + ty * 4 + u];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) ob[v] = Os[s * TILE + tx * 4 + v];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += pa[u] * ob[v];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = r0 + ty * 4 + u;
+        if (i >= n) continue;
+        const bool iJ = (i >= j0 && i < j1);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int l = c0 + tx * 4 + v;
+            if (l >= n) continue;
+            const bool lJ = (l >= j0 && l < j1);
+            T *dst = M + (int64_t)i * ld + l;
+            if (!iJ && !lJ) *dst = *dst - acc[u][v];
+            else if (!iJ && lJ) *dst = pan[(int64_t)i * NB + (l - j0)];
+            else if (iJ && !lJ) *dst = pan[(int64_t)l * NB + (i - j0)];
+            else *dst = -D[(i - j0) * NB + (l - j0)];
+        }
+    }
+}
+
+// copy A^k (FP64, ld = nk) into the swept-matrix pool (type T, ld = ldM, zero padding)
+template <typename T> __global__ void k_load_matrix(const double *A, T *Mpool, const SubdomainDesc *sd) {
+    const SubdomainDesc d = sd[blockIdx.y];
+    const int64_t ld = d.ldM;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)d.nk * ld; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = t / ld, l = t % ld;
+        Mpool[d.offM + t] = l < d.nk ? (T)A[d.offA + i * d.nk + l] : T(0);
+    }
+}
+
+// copy the Gamma block of the swept matrix into S (and into Sp with pinning)
+template <typename T> __global__ void k_extract(const T *Mpool, T *Spool, T *Sppool, const SubdomainDesc *sd) {
+    const SubdomainDesc d = sd[blockIdx.y];
+    const int64_t nG = d.nG, ld = d.ldG;
+    const T *M = Mpool + d.offM;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nG * ld; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = t / ld, l = t % ld;
+        if (l >= nG) { Spool[d.offS + t] = T(0); Sppool[d.offSp + t] = T(0); continue; }
+        T v = M[(d.nO + i) * d.ldM + d.nO + l];
+        Spool[d.offS + t] = v;
+        bool pi = false, pl = false;
+        for (int q = 0; q < d.npin; ++q) { pi |= (d.pin[q] == i); pl |= (d.pin[q] == l); }
+        Sppool[d.offSp + t] = (pi || pl) ? (i == l ? T(1) : T(0)) : v;
+    }
+}
+
+// orthonormal basis of the kernel of a floating subdomain's S_k, restricted to Gamma_k
+// (constants; or the two translations and the rotation about the Gamma_k centroid)
+__global__ void k_kernel_basis(const double *xy, const int32_t *gnodes, const int64_t *goff, const SubdomainDesc *sd,
+                               int nc, double *Z, double *Q) {
+    const SubdomainDesc d = sd[blockIdx.x];
+    if (!d.floating || d.nG == 0) return;
+    const int ng = d.nG / nc;
+    const int32_t *nodes = gnodes + goff[blockIdx.x];
+    __shared__ double red[3][256];
+    __shared__ double cen[2];
+    const int m = nc == 1 ? 1 : 3;
+    double *Zk = Z + d.offU * 3;
+    double *Qk = Q + d.offU * 3;
+    if (nc == 2) {
+        double sx = 0, sy = 0;
+        for (int i = threadIdx.x; i < ng; i += blockDim.x) { sx += xy[2 * (int64_t)nodes[i]]; sy += xy[2 * (int64_t)nodes[i] + 1]; }
+        red[0][threadIdx.x] = sx; red[1][threadIdx.x] = sy;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0, b = 0;
+            for (int t = 0; t < blockDim.x; ++t) { a += red[0][t]; b += red[1][t]; }
+            cen[0] = a / ng; cen[1] = b / ng;
+        }
+        __syncthreads();
+    }
+    for (int r = threadIdx.x; r < d.nG; r += blockDim.x) {
+        for (int c = 0; c < 3; ++c) Zk[(int64_t)r * 3 + c] = 0.0;
+        if (nc == 1) Zk[(int64_t)r * 3] = 1.0;
+        else {
+            int node = nodes[r / 2], comp = r % 2;
+            Zk[(int64_t)r * 3 + comp] = 1.0;
+            Zk[(int64_t)r * 3 + 2] = comp == 0 ? -(xy[2 * (int64_t)node + 1] - cen[1]) : (xy[2 * (int64_t)node] - cen[0]);
+        }
+        for (int c = 0; c < 3; ++c) Qk[(int64_t)r * 3 + c] = c < m ? Zk[(int64_t)r * 3 + c] : 0.0;
+    }
+    __syncthreads();
+    // modified Gram-Schmidt, two passes
+    for (int pass = 0; pass < 2; ++pass)
+        for (int c = 0; c < m; ++c) {
+            for (int pc = 0; pc < c; ++pc) {
+                double s = 0;
+                for (int r = threadIdx.x; r < d.nG; r += blockDim.x) s += Qk[(int64_t)r * 3 + c] * Qk[(int64_t)r * 3 + pc];
+                red[0][threadIdx.x] = s;
+                __syncthreads();
+                if (threadIdx.x == 0) { double t = 0; for (int i = 0; i < blockDim.x; ++i) t += red[0][i]; red[1][0] = t; }
+                __syncthreads();
+                double proj = red[1][0];
+                for (int r = threadIdx.x; r < d.nG; r += blockDim.x) Qk[(int64_t)r * 3 + c] -= proj * Qk[(int64_t)r * 3 + pc];
+                __syncthreads();
+            }
+            double s = 0;
+            for (int r = threadIdx.x; r < d.nG; r += blockDim.x) s += Qk[(int64_t)r * 3 + c] * Qk[(int64_t)r * 3 + c];
+            red[0][threadIdx.x] = s;
+            __syncthreads();
+            if (threadIdx.x == 0) { double t = 0; for (int i = 0; i < blockDim.x; ++i) t += red[0][i]; red[1][0] = sqrt(t); }
+            __syncthreads();
+            double nrm = red[1][0];
+            for (int r = threadIdx.x; r < d.nG; r += blockDim.x) Qk[(int64_t)r * 3 + c] /= nrm;
+            __syncthreads();
+        }
+}
+
+// W = -(swept pinned S~) with pinned rows/columns zeroed; then V = W Q (FP64)
+template <typename T> __global__ void k_finish_inverse(T *Sppool, const SubdomainDesc *sd) {
+    const SubdomainDesc d = sd[blockIdx.y];
+    const int64_t nG = d.nG, ld = d.ldG;
+    T *W = Sppool + d.offSp;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nG * ld; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = t / ld, l = t % ld;
+        if (l >= nG) continue;
+        bool pz = false;
+        for (int q = 0; q < d.npin; ++q) pz |= (d.pin[q] == i) || (d.pin[q] == l);
+        W[t] = pz ? T(0) : -W[t];
+    }
+}
+
+template <typename T> __global__ void k_wq(const T *Sppool, const SubdomainDesc *sd, const double *Q, double *V) {
+    const SubdomainDesc d = sd[blockIdx.y];
+    if (!d.floating || d.nG == 0) return;
+    const int m = d.n_co;
+    const int64_t nG = d.nG;
+    const T *W = Sppool + d.offSp;
+    const double *Qk = Q + d.offU * 3;
+    double *Vk = V + d.offU * 3;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + warp; i < nG; i += (int64_t)gridDim.x * (blockDim.x / 32)) {
+        double s[3] = {0, 0, 0};
+        for (int64_t l = lane; l < nG; l += 32) {
+            double w = (double)W[i * d.ldG + l];
+            for (int c = 0; c < m; ++c) s[c] += w * Qk[l * 3 + c];
+        }
+        for (int c = 0; c < m; ++c)
+            for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
+        if (lane == 0)
+            for (int c = 0; c < 3; ++c) Vk[i * 3 + c] = c < m ? s[c] : 0.0;
+    }
+}
+
+// C = Q^T V (m x m), one CTA per floating subdomain
+__global__ void k_qtv(const SubdomainDesc *sd, const double *Q, const double *V, double *C) {
+    const SubdomainDesc d = sd[blockIdx.x];
+    if (!d.floating || d.nG == 0) return;
+    const int m = d.n_co;
+    __shared__ double red[256];
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) {
+            double s = 0;
+            for (int64_t r = threadIdx.x; r < d.nG; r += blockDim.x) s += Q[(d.offU + r) * 3 + a] * V[(d.offU + r) * 3 + b];
+            red[threadIdx.x] = s;
+            __syncthreads();
+            for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+                if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) C[blockIdx.x * 9 + a * 3 + b] = red[0];
+            __syncthreads();
+        }
+}
+
+// S^+ = W - Q V^T - V Q^T + Q C Q^T
+template <typename T> __global__ void k_project(T *Sppool, const SubdomainDesc *sd, const double *Q, const double *V,
+                                               const double *C) {
+    const SubdomainDesc d = sd[blockIdx.y];
+    if (!d.floating || d.nG == 0) return;
+    const int m = d.n_co;
+    const int64_t nG = d.nG;
+    T *W = Sppool + d.offSp;
+    const double *Ck = C + blockIdx.y * 9;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nG * nG; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = t / nG, l = t % nG;
+        const double *qi = Q + (d.offU + i) * 3, *ql = Q + (d.offU + l) * 3;
+        T *Wt = W + i * d.ldG + l;
+        const double *vi = V + (d.offU + i) * 3, *vl = V + (d.offU + l) * 3;
+        double corr = 0;
+        for (int a = 0; a < m; ++a) {
+            corr -= qi[a] * vl[a] + vi[a] * ql[a];
+            for (int b = 0; b < m; ++b) corr += qi[a] * Ck[a * 3 + b] * ql[b];
+        }
+        *Wt = (T)((double)*Wt + corr);
+    }
+}
+
+template <typename T> void run_sweeps(nlfeti_problem *p, T *pool, const std::vector<int64_t> &moff,
+                                      const std::vector<int32_t> &mdim, const std::vector<int32_t> &mld,
+                                      const std::vector<int32_t> &pend, DevMem &scratch) {
+    nlfeti_ctx *c = p->ctx;
+    const int K = p->K;
+    std::vector<int64_t> soff(K);
+    int64_t rows = 0;
+    int maxn = 0, maxp = 0;
+    for (int k = 0; k < K; ++k) {
+        soff[k] = rows;
+        rows += mdim[k];
+        maxn = std::max(maxn, mdim[k]);
+        maxp = std::max(maxp, pend[k]);
+    }
+    if (maxp == 0) return;
+    size_t need = sizeof(T) * ((size_t)rows * NB * 2 + (size_t)K * NB * NB);
+    if (scratch.bytes < need) scratch.alloc(c, need);
+    DevMem d_moff, d_mdim, d_mld, d_pend, d_soff;
+    upload(c, d_moff, moff);
+    upload(c, d_mdim, mdim);
+    upload(c, d_mld, mld);
+    upload(c, d_pend, pend);
+    upload(c, d_soff, soff);
+    SweepArgs<T> a;
+    a.M = pool;
+    a.pan = scratch.as<T>();
+    a.old = a.pan + rows * NB;
+    a.dinv = a.old + rows * NB;
+    a.sd = p->d_sd.as<SubdomainDesc>();
+    a.moff = d_moff.as<int64_t>();
+    a.mdim = d_mdim.as<int32_t>();
+    a.mld = d_mld.as<int32_t>();
+    a.pend = d_pend.as<int32_t>();
+    a.scr_off = d_soff.as<int64_t>();
+    a.flag = p->d_flag.as<int>();
+    const int nt = (maxn + TILE - 1) / TILE;
+    const size_t smu = sizeof(T) * 2 * NB * TILE;
+    NLF_CUDA(cudaFuncSetAttribute(k_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smu));
+    for (int j0 = 0; j0 < maxp; j0 += NB) {
+        a.j0 = j0;
+        k_pivot<T><<<K, 256, 0, c->stream>>>(a);
+        k_panel<T><<<dim3((maxn + 3) / 4, K), 256, 0, c->stream>>>(a);
+        k_update<T><<<dim3(nt, nt, K), 256, smu, c->stream>>>(a);
+    }
+    NLF_CUDA(cudaGetLastError());
+    NLF_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+}  // namespace
+
+template <typename T> void factor_ops(nlfeti_problem *p, OpPool<T> &pool) {
+    nlfeti_ctx *c = p->ctx;
+    const int K = p->K;
+    int64_t poolM = p->poolM, poolG = p->poolG;
+    pool.M.alloc(c, sizeof(T) * std::max<int64_t>(poolM, 1));
+    pool.S.alloc(c, sizeof(T) * std::max<int64_t>(poolG, 1));
+    pool.Sp.alloc(c, sizeof(T) * std::max<int64_t>(poolG, 1));
+    NLF_CUDA(cudaMemsetAsync(p->d_flag.p, 0, sizeof(int) * 4, c->stream));
+    // phase 1: sweep the Omega pivots of A^k
+    NLF_CUDA(cudaMemsetAsync(pool.S.p, 0, pool.S.bytes, c->stream));
+    NLF_CUDA(cudaMemsetAsync(pool.Sp.p, 0, pool.Sp.bytes, c->stream));
+    k_load_matrix<T><<<dim3(256, K), 256, 0, c->stream>>>(p->d_A.as<double>(), pool.M.template as<T>(),
+                                                          p->d_sd.as<SubdomainDesc>());
+    NLF_CUDA(cudaGetLastError());
+    std::vector<int64_t> moff(K), soff(K);
+    std::vector<int32_t> mdim(K), mld(K), pend(K), gdim(K), gld(K), gend(K);
+    for (int k = 0; k < K; ++k) {
+        moff[k] = p->sd[k].offM;
+        mdim[k] = p->sd[k].nk;
+        mld[k] = p->sd[k].ldM;
+        pend[k] = p->sd[k].nO;
+        soff[k] = p->sd[k].offSp;
+        gdim[k] = p->sd[k].nG;
+        gld[k] = p->sd[k].ldG;
+        gend[k] = p->sd[k].nG;
+    }
+    run_sweeps<T>(p, pool.M.template as<T>(), moff, mdim, mld, pend, pool.scratch);
+    // S_k and the pinned copy
+    int maxg = 0;
+    for (auto &d : p->sd) maxg = std::max(maxg, d.nG);
+    if (maxg > 0) {
+        dim3 g(256, K);
+        k_extract<T><<<g, 256, 0, c->stream>>>(pool.M.template as<T>(), pool.S.template as<T>(),
+                                               pool.Sp.template as<T>(), p->d_sd.as<SubdomainDesc>());
+        NLF_CUDA(cudaGetLastError());
+        // phase 2: sweep all pivots of the pinned S~_k
+        run_sweeps<T>(p, pool.Sp.template as<T>(), soff, gdim, gld, gend, pool.scratch);
+        k_finish_inverse<T><<<g, 256, 0, c->stream>>>(pool.Sp.template as<T>(), p->d_sd.as<SubdomainDesc>());
+        if (p->n_floating > 0) {
+            DevMem V, C;
+            V.alloc(c, sizeof(double) * 3 * std::max<int64_t>(p->n_u, 1));
+            C.alloc(c, sizeof(double) * 9 * K);
+            k_wq<T><<<dim3(64, K), 256, 0, c->stream>>>(pool.Sp.template as<T>(), p->d_sd.as<SubdomainDesc>(),
+                                                         p->d_Q.as<double>(), V.as<double>());
+            k_qtv<<<K, 256, 0, c->stream>>>(p->d_sd.as<SubdomainDesc>(), p->d_Q.as<double>(), V.as<double>(),
+                                            C.as<double>());
+            k_project<T><<<g, 256, 0, c->stream>>>(pool.Sp.template as<T>(), p->d_sd.as<SubdomainDesc>(),
+                                                   p->d_Q.as<double>(), V.as<double>(), C.as<double>());
+            NLF_CUDA(cudaGetLastError());
+            NLF_CUDA(cudaStreamSynchronize(c->stream));
+        }
+    }
+    NLF_CUDA(cudaStreamSynchronize(c->stream));
+    int flag = 0;
+    NLF_CUDA(cudaMemcpy(&flag, p->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) fail(NLFETI_E_NOT_SPD, "a pivot block of a subdomain operator was not positive definite");
+    pool.ready = true;
+}
+
+template void factor_ops<double>(nlfeti_problem *, OpPool<double> &);
+template void factor_ops<float>(nlfeti_problem *, OpPool<float> &);
+
+// ------------------------------------------------------------------ coarse problem and weights
+
+namespace {
+
+__global__ void k_gtg(const int64_t *Bp, const int64_t *Bm, int64_t nl, const int32_t *u2sub, const SubdomainDesc *sd,
+                      const double *Z, int nco, double *GtG) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nl; r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t up = Bp[r], um = Bm[r];
+        int kp = u2sub[up], km = u2sub[um];
+        const SubdomainDesc dp = sd[kp], dm = sd[km];
+        // G row r: +Z[up, :] on columns of kp, -Z[um, :] on columns of km
+        int cols[6];
+        double vals[6];
+        int n = 0;
+        for (int c = 0; c < dp.n_co; ++c) { cols[n] = dp.co_off + c; vals[n++] = Z[up * 3 + c]; }
+        for (int c = 0; c < dm.n_co; ++c) { cols[n] = dm.co_off + c; vals[n++] = -Z[um * 3 + c]; }
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b)
+                if (vals[a] != 0.0 && vals[b] != 0.0) atomicAdd(GtG + (int64_t)cols[a] * nco + cols[b], vals[a] * vals[b]);
+    }
+}
+
+// in-place inverse of a small SPD matrix (n <= 128) by one CTA; result written back
+__global__ void k_small_inverse(double *A, int n, int *flag) {
+    extern __shared__ double sm[];
+    double *S = sm;
+    double *rowp = sm + n * n;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) S[t] = A[t];
+    bool ok = sweep_block_shared(S, n, n, rowp);
+    if (!ok && threadIdx.x == 0) atomicMax(flag, 1);
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] = -S[t];
+}
+
+// B_D = (B D^-1 B^T)^-1 B D^-1 per node block (chain rows, D = zeta on every copy):
+// B B^T = tridiag(-1, 2, -1) on the z-1 links of a node with z copies
+__global__ void k_bd_blocks(const int32_t *blk_ptr, int64_t nblk, const int32_t *blk_rows, const int64_t *bd_ptr,
+                            double *bd_val, int *flag) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += (int64_t)gridDim.x * blockDim.x) {
+        const int r0 = blk_ptr[b], r1 = blk_ptr[b + 1];
+        const int m = r1 - r0;             // rows in the block = zeta - 1
+        const int z = m + 1;               // copies
+        if (m > 15) { atomicMax(flag, 1); continue; }
+        double S[15][15], Binv[15][15];
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                S[i][j] = (i == j ? 2.0 : (abs(i - j) == 1 ? -1.0 : 0.0)) / (double)z;
+                Binv[i][j] = i == j ? 1.0 : 0.0;
+            }
+        for (int p = 0; p < m; ++p) {        // Gauss-Jordan on the SPD block
+            double d = S[p][p];
+            for (int j = 0; j < m; ++j) { S[p][j] /= d; Binv[p][j] /= d; }
+            for (int i = 0; i < m; ++i)
+                if (i != p) {
+                    double f = S[i][p];
+                    for (int j = 0; j < m; ++j) { S[i][j] -= f * S[p][j]; Binv[i][j] -= f * Binv[p][j]; }
+                }
+        }
+        // row i of B_D: sum_j Binv[i][j] (row j of B) / z; row j has +1 at copy j, -1 at copy j+1
+        for (int i = 0; i < m; ++i) {
+            const int64_t row = blk_rows[r0 + i];
+            for (int cpy = 0; cpy < z; ++cpy) {
+                double v = 0;
+                if (cpy < m) v += Binv[i][cpy] / (double)z;
+                if (cpy >= 1) v -= Binv[i][cpy - 1] / (double)z;
+                bd_val[bd_ptr[row] + cpy] = v;
+            }
+        }
+    }
+}
+
+__global__ void k_gather_vals(const int64_t *src_idx, const double *src, double *dst, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[src_idx[i]];
+}
+
+}  // namespace
+
+void setup_coarse(nlfeti_problem *p) {
+    nlfeti_ctx *c = p->ctx;
+    // kernel bases on Gamma_k (all subdomains get Z, Q rows; only floating ones are filled)
+    std::vector<int32_t> gnodes;
+    std::vector<int64_t> goff(p->K + 1, 0);
+    for (int k = 0; k < p->K; ++k) {
+        const auto &nd = p->dec.nodes[k];
+        int nO = p->dec.n_omega_nodes[k];
+        gnodes.insert(gnodes.end(), nd.begin() + nO, nd.end());
+        goff[k + 1] = goff[k] + (int64_t)(nd.size() - nO);
+    }
+    DevMem d_gn, d_goff;
+    upload(c, d_gn, gnodes);
+    upload(c, d_goff, goff);
+    p->d_Z.alloc(c, sizeof(double) * 3 * std::max<int64_t>(p->n_u, 1));
+    p->d_Q.alloc(c, sizeof(double) * 3 * std::max<int64_t>(p->n_u, 1));
+    NLF_CUDA(cudaMemsetAsync(p->d_Z.p, 0, p->d_Z.bytes, c->stream));
+    NLF_CUDA(cudaMemsetAsync(p->d_Q.p, 0, p->d_Q.bytes, c->stream));
+    k_kernel_basis<<<p->K, 256, 0, c->stream>>>(p->d_xy.as<double>(), d_gn.as<int32_t>(), d_goff.as<int64_t>(),
+                                                 p->d_sd.as<SubdomainDesc>(), p->nc, p->d_Z.as<double>(),
+                                                 p->d_Q.as<double>());
+    NLF_CUDA(cudaGetLastError());
+    const int nco = p->n_co;
+    p->d_GtGinv.alloc(c, sizeof(double) * std::max(1, nco * nco));
+    if (nco > 0) {
+        if (nco > 128) fail(NLFETI_E_INVALID, "more than 128 coarse columns");
+        NLF_CUDA(cudaMemsetAsync(p->d_GtGinv.p, 0, sizeof(double) * nco * nco, c->stream));
+        if (p->n_lambda > 0)
+            k_gtg<<<256, 256, 0, c->stream>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), p->n_lambda,
+                                              p->d_u2sub.as<int32_t>(), p->d_sd.as<SubdomainDesc>(),
+                                              p->d_Z.as<double>(), nco, p->d_GtGinv.as<double>());
+        size_t sm = sizeof(double) * (nco * nco + nco);
+        NLF_CUDA(cudaFuncSetAttribute(k_small_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_small_inverse<<<1, 256, sm, c->stream>>>(p->d_GtGinv.as<double>(), nco, p->d_flag.as<int>());
+        NLF_CUDA(cudaGetLastError());
+    }
+    NLF_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+void setup_jump_weights(nlfeti_problem *p) {
+    nlfeti_ctx *c = p->ctx;
+    // blocks: consecutive B rows of one (node, component); rows of a node are chain links
+    // j = 0..z-2 with the component fastest, so the rows of (node, comp) are r0 + comp + nc*j.
+    const int nc = p->nc;
+    const auto &Bn = p->dec.B_node;
+    const int64_t nl = p->n_lambda;
+    std::vector<int32_t> blk_ptr{0}, blk_rows;
+    std::vector<int64_t> bd_ptr(nl + 1, 0), bd_col;
+    // copies of each block (U indices in chain order)
+    std::vector<std::vector<int64_t>> blk_copies;
+    int64_t r = 0;
+    while (r < nl) {
+        int64_t s = r;
+        while (s < nl && Bn[s] == Bn[r]) ++s;
+        const int64_t links = (s - r) / nc;
+        for (int comp = 0; comp < nc; ++comp) {
+            std::vector<int64_t> copies;
+            for (int64_t j = 0; j < links; ++j) {
+                int64_t row = r + comp + nc * j;
+                blk_rows.push_back((int32_t)row);
+                if (j == 0) copies.push_back(p->dec.B_plus[row]);
+                copies.push_back(p->dec.B_minus[row]);
+            }
+            blk_ptr.push_back((int32_t)blk_rows.size());
+            blk_copies.push_back(copies);
+        }
+        r = s;
+    }
+    // B_D CSR: each row of a block has one entry per copy of its block
+    {
+        int64_t nb = (int64_t)blk_copies.size();
+        std::vector<int64_t> row_len(nl, 0);
+        for (int64_t b = 0; b < nb; ++b)
+            for (int32_t i = blk_ptr[b]; i < blk_ptr[b + 1]; ++i) row_len[blk_rows[i]] = (int64_t)blk_copies[b].size();
+        for (int64_t i = 0; i < nl; ++i) bd_ptr[i + 1] = bd_ptr[i] + row_len[i];
+        bd_col.assign(bd_ptr[nl], 0);
+        for (int64_t b = 0; b < nb; ++b)
+            for (int32_t i = blk_ptr[b]; i < blk_ptr[b + 1]; ++i)
+                for (size_t cp = 0; cp < blk_copies[b].size(); ++cp) bd_col[bd_ptr[blk_rows[i]] + cp] = blk_copies[b][cp];
+    }
+    DevMem d_blk_ptr, d_blk_rows;
+    upload(c, d_blk_ptr, blk_ptr);
+    upload(c, d_blk_rows, blk_rows);
+    upload(c, p->d_BD_ptr, bd_ptr);
+    upload(c, p->d_BD_col, bd_col);
+    p->d_BD_val.alloc(c, sizeof(double) * std::max<int64_t>(1, bd_ptr[nl]));
+    const int64_t nblk = (int64_t)blk_copies.size();
+    if (nblk > 0) {
+        k_bd_blocks<<<(unsigned)((nblk + 127) / 128), 128, 0, c->stream>>>(
+            d_blk_ptr.as<int32_t>(), nblk, d_blk_rows.as<int32_t>(), p->d_BD_ptr.as<int64_t>(),
+            p->d_BD_val.as<double>(), p->d_flag.as<int>() + 1);
+        NLF_CUDA(cudaGetLastError());
+    }
+    // transpose CSR (per U dof: rows and value positions)
+    std::vector<int64_t> t_ptr(p->n_u + 1, 0), t_row, t_src;
+    for (int64_t i = 0; i < (int64_t)bd_col.size(); ++i) t_ptr[bd_col[i] + 1]++;
+    for (int64_t u = 0; u < p->n_u; ++u) t_ptr[u + 1] += t_ptr[u];
+    t_row.assign(bd_col.size(), 0);
+    t_src.assign(bd_col.size(), 0);
+    {
+        std::vector<int64_t> fill(t_ptr.begin(), t_ptr.end() - 1);
+        for (int64_t row = 0; row < nl; ++row)
+            for (int64_t q = bd_ptr[row]; q < bd_ptr[row + 1]; ++q) {
+                int64_t u = bd_col[q];
+                t_row[fill[u]] = row;
+                t_src[fill[u]] = q;
+                fill[u]++;
+            }
+    }
+    upload(c, p->d_BDt_ptr, t_ptr);
+    upload(c, p->d_BDt_row, t_row);
+    DevMem d_src;
+    upload(c, d_src, t_src);
+    p->d_BDt_val.alloc(c, sizeof(double) * std::max<size_t>(1, t_src.size()));
+    if (!t_src.empty()) {
+        k_gather_vals<<<256, 256, 0, c->stream>>>(d_src.as<int64_t>(), p->d_BD_val.as<double>(),
+                                                  p->d_BDt_val.as<double>(), (int64_t)t_src.size());
+        NLF_CUDA(cudaGetLastError());
+    }
+    NLF_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+}  // namespace nlf
