@@ -172,6 +172,21 @@ nlfeti_status nlfeti_get_operator(const nlfeti_problem *p, int k, int which, int
  * 3 = S^+ (U -> U), 4 = S (U -> U). */
 nlfeti_status nlfeti_apply(nlfeti_problem *p, int op, int precision, int nrhs, const double *in, double *out);
 
+/* Kernel accounting of a problem's solves (for roofline reporting).  With profiling on,
+ * every launch of the dense interface apply (the per-iteration products with S_k^+ and
+ * S_k) is bracketed by CUDA events on the library stream, also inside captured graphs.
+ * kernel_launches counts every kernel of the library launched by solves (graph kernel
+ * nodes included).  apply_bytes: operator bytes read by those launches (sum over
+ * launches of sum_k n_gamma_k * ld_k * sizeof(element)).  Reading resets the counters. */
+typedef struct {
+    int64_t kernel_launches;
+    int64_t apply_launches;
+    double apply_ms;
+    double apply_bytes;
+} nlfeti_profile;
+nlfeti_status nlfeti_set_profiling(nlfeti_problem *p, int on);
+nlfeti_status nlfeti_get_profile(nlfeti_problem *p, nlfeti_profile *out);
+
 /* Continuous-batching server (one worker thread, its own streams).  Requests
  * that arrive while others run are admitted between PCG iterations as slots and
  * the HBM budget allow; their work shares the batched launches. */

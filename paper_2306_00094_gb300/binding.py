@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "OK", -1: "INVALID", -2: "NOMEM", -3: "NOT_SPD", -4: "NOT_CON
 EXPORTED = ["nlfeti_default_options", "nlfeti_create", "nlfeti_destroy", "nlfeti_last_error", "nlfeti_problem_create",
             "nlfeti_problem_destroy", "nlfeti_problem_info", "nlfeti_problem_set_options", "nlfeti_factor",
             "nlfeti_solve", "nlfeti_solve_device", "nlfeti_get_decomposition", "nlfeti_get_operator",
-            "nlfeti_apply", "nlfeti_server_create", "nlfeti_submit", "nlfeti_wait", "nlfeti_server_destroy"]
+            "nlfeti_apply", "nlfeti_set_profiling", "nlfeti_get_profile", "nlfeti_server_create", "nlfeti_submit",
+            "nlfeti_wait", "nlfeti_server_destroy"]
 
 
 class NlfetiError(RuntimeError):
@@ -50,6 +51,11 @@ class Info(C.Structure):
     _fields_ = [("K", C.c_int32), ("ncomp", C.c_int32), ("n_floating", C.c_int32), ("n_coarse", C.c_int32),
                 ("n_lambda", C.c_int64), ("n_u", C.c_int64), ("sum_nk", C.c_int64), ("sum_nk2", C.c_int64),
                 ("sum_ngamma2", C.c_int64), ("max_nk", C.c_int32), ("max_ngamma", C.c_int32)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("kernel_launches", C.c_int64), ("apply_launches", C.c_int64), ("apply_ms", C.c_double),
+                ("apply_bytes", C.c_double)]
 
 
 class Mesh(C.Structure):
@@ -100,6 +106,8 @@ def load(build_if_missing: bool = True):
         "nlfeti_get_decomposition": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "nlfeti_get_operator": (i32, [vp, i32, i32, i32, vp]),
         "nlfeti_apply": (i32, [vp, i32, i32, i32, vp, vp]),
+        "nlfeti_set_profiling": (i32, [vp, i32]),
+        "nlfeti_get_profile": (i32, [vp, C.POINTER(Profile)]),
         "nlfeti_server_create": (i32, [vp, C.c_size_t, i32, C.POINTER(vp)]),
         "nlfeti_submit": (i32, [vp, vp, i32, i32, vp, vp, C.POINTER(C.c_uint64)]),
         "nlfeti_wait": (i32, [vp, C.c_uint64, i32, vp, C.POINTER(Stats)]),
@@ -228,6 +236,21 @@ class Problem:
         if raise_on_error:
             self.ctx.check(code)
         return out, st.as_dict()
+
+    def solve_host_ptr(self, rhs_ptr, rhs_kind, out_ptr, nrhs, g_ptr=None):
+        """Host arrays given by address (e.g. pinned torch tensors), column-major n_dofs x nrhs."""
+        st = Stats()
+        self.ctx.check(self.ctx.lib.nlfeti_solve(self.h, int(nrhs), int(rhs_kind), rhs_ptr, g_ptr, out_ptr,
+                                                 C.byref(st)))
+        return st.as_dict()
+
+    def set_profiling(self, on: bool):
+        self.ctx.check(self.ctx.lib.nlfeti_set_profiling(self.h, 1 if on else 0))
+
+    def profile(self):
+        pr = Profile()
+        self.ctx.check(self.ctx.lib.nlfeti_get_profile(self.h, C.byref(pr)))
+        return {k: getattr(pr, k) for k, _ in Profile._fields_}
 
     def solve_device(self, d_rhs, rhs_kind, d_out, d_g=None, nrhs=None):
         """Device pointers (ints) or torch tensors (column-major, n_dofs x nrhs as contiguous (nrhs, n_dofs))."""

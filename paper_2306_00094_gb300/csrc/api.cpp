@@ -487,6 +487,20 @@ nlfeti_status nlfeti_solve(nlfeti_problem *p, int nrhs, int rhs_kind, const doub
     });
 }
 
+nlfeti_status nlfeti_set_profiling(nlfeti_problem *p, int on) {
+    if (!p) return NLFETI_E_INVALID;
+    p->prof_on = on != 0;
+    return NLFETI_OK;
+}
+
+nlfeti_status nlfeti_get_profile(nlfeti_problem *p, nlfeti_profile *out) {
+    if (!p || !out) return NLFETI_E_INVALID;
+    std::lock_guard<std::mutex> g(p->prof_mu);
+    *out = p->prof;
+    p->prof = nlfeti_profile{};
+    return NLFETI_OK;
+}
+
 nlfeti_status nlfeti_get_decomposition(const nlfeti_problem *p, int32_t *n_k, int32_t *n_gamma, int32_t *node_lists,
                                        int64_t *B_plus, int64_t *B_minus, int8_t *floating) {
     if (!p) return NLFETI_E_INVALID;

@@ -166,6 +166,9 @@ struct nlfeti_problem {
     OpPool<float> op32;
     std::unique_ptr<nlf::SolveWS> ws;
     double ms_setup = 0, ms_factor = 0;
+    bool prof_on = false;
+    std::mutex prof_mu;
+    nlfeti_profile prof{};
     ~nlfeti_problem();
 };
 

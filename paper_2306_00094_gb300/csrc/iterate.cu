@@ -576,6 +576,19 @@ struct Runner {
     int R;
     PcgScalars S;
     const SubdomainDesc *sd;
+    // kernel accounting: launches made eagerly, launches recorded into the graph being
+    // captured, and event pairs around the interface applies (graph slots are re-recorded
+    // by every launch of the graph)
+    bool capturing = false;
+    int64_t eager_launches = 0, cap_launches = 0;
+    struct Slot {
+        cudaEvent_t a, b;
+        int launches;
+        double bytes;
+    };
+    std::vector<Slot> graph_slots, eager_slots;
+    int64_t apply_launches = 0;
+    double apply_ms = 0, apply_bytes = 0;
 
     Runner(nlfeti_problem *pp, SolveWS &w, cudaStream_t s) : p(pp), ws(w), st(s), R(w.R) {
         double *b = ws.scal.as<double>();
@@ -587,8 +600,44 @@ struct Runner {
         set_attributes();
     }
 
+    ~Runner() {
+        harvest(eager_slots, true);
+        drop(graph_slots);
+        std::lock_guard<std::mutex> g(p->prof_mu);
+        p->prof.kernel_launches += eager_launches;
+        p->prof.apply_launches += apply_launches;
+        p->prof.apply_ms += apply_ms;
+        p->prof.apply_bytes += apply_bytes;
+    }
+
+    void note_launch() {
+        if (capturing) ++cap_launches;
+        else ++eager_launches;
+    }
+
+    void drop(std::vector<Slot> &v) {
+        for (auto &s : v) { cudaEventDestroy(s.a); cudaEventDestroy(s.b); }
+        v.clear();
+    }
+
+    // add the elapsed times of completed slots (the stream has been synchronized)
+    void harvest(std::vector<Slot> &v, bool clear) {
+        for (auto &s : v) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, s.a, s.b) == cudaSuccess) {
+                apply_ms += ms;
+                apply_launches += s.launches;
+                apply_bytes += s.bytes;
+            } else {
+                cudaGetLastError();
+            }
+        }
+        if (clear) drop(v);
+    }
+
     void dot(const double *a, const double *b, int64_t n) {
         k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, n, R, ws.partial.as<double>());
+        note_launch();
     }
 
     // out = P v (out may alias v)
@@ -600,15 +649,19 @@ struct Runner {
         }
         k_proj_g<<<p->K, 256, 0, st>>>(sd, p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), v, 0,
                                        p->d_Z.as<double>(), ws.gco.as<double>(), R);
+                                       note_launch();
         k_coarse<<<1, 256, 0, st>>>(p->d_GtGinv.as<double>(), p->n_co, ws.gco.as<double>(), ws.alpha.as<double>(), R);
+        note_launch();
         k_apply_galpha<<<grid_for(nl * R), 256, 0, st>>>(sd, p->d_u2sub.as<int32_t>(), p->d_Bp.as<int64_t>(),
                                                          p->d_Bm.as<int64_t>(), p->d_Z.as<double>(),
                                                          ws.alpha.as<double>(), v, -1.0, out, nl, R);
+                                                         note_launch();
     }
 
     template <typename T, int RC> void symv_launch(const T *base, int use_sp, const int32_t *it, int nitems, const T *x,
                                                    double *y, size_t sm) {
         k_symv<T, RC><<<nitems, 256, sm, st>>>(base, use_sp, sd, it, x, y, R);
+        note_launch();
     }
 
     // shared-memory limits of every apply variant, set once outside any graph capture
@@ -641,18 +694,40 @@ struct Runner {
             }
         };
         const int32_t *items = p->d_items.as<int32_t>();
-        if (p->opt.batched) go(items, p->n_items);
+        Slot slot{};
+        const bool timed = p->prof_on;
+        if (timed) {
+            NLF_CUDA(cudaEventCreate(&slot.a));
+            NLF_CUDA(cudaEventCreate(&slot.b));
+            NLF_CUDA(cudaEventRecord(slot.a, st));
+        }
+        int launches = 0;
+        if (p->opt.batched) { go(items, p->n_items); launches = 1; }
         else
-            for (int k = 0; k < p->K; ++k) go(items + 2 * p->item_off[k], p->item_off[k + 1] - p->item_off[k]);
+            for (int k = 0; k < p->K; ++k) {
+                go(items + 2 * p->item_off[k], p->item_off[k + 1] - p->item_off[k]);
+                launches += p->item_off[k + 1] > p->item_off[k];
+            }
+        if (timed) {
+            NLF_CUDA(cudaEventRecord(slot.b, st));
+            double bytes = 0;
+            for (const auto &d : p->sd)
+                bytes += (double)d.nG * d.ldG * sizeof(T) + (double)d.nG * R * (sizeof(T) + sizeof(double));
+            slot.launches = launches;
+            slot.bytes = bytes;
+            (capturing ? graph_slots : eager_slots).push_back(slot);
+        }
     }
 
     template <typename T> void applyF(const OpPool<T> &pool, const double *v, double *out, const double *cvec = nullptr) {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         T *x = ws.xU.as<T>();
         k_gather_bt<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), v, x, nu, R);
+        note_launch();
         symv<T>(pool, 1, x, ws.yU.as<double>());
         k_gather_b<<<grid_for(nl * R), 256, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), ws.yU.as<double>(),
                                                      cvec, out, nl, R);
+                                                     note_launch();
     }
 
     template <typename T> void applyMinv(const OpPool<T> &pool, const double *v, double *out) {
@@ -660,9 +735,11 @@ struct Runner {
         T *x = ws.xU.as<T>();
         k_gather_bdt<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_BDt_ptr.as<int64_t>(), p->d_BDt_row.as<int64_t>(),
                                                           p->d_BDt_val.as<double>(), v, x, nu, R);
+                                                          note_launch();
         symv<T>(pool, 0, x, ws.yU.as<double>());
         k_gather_bd<<<grid_for(nl * R), 256, 0, st>>>(p->d_BD_ptr.as<int64_t>(), p->d_BD_col.as<int64_t>(),
                                                       p->d_BD_val.as<double>(), ws.yU.as<double>(), out, nl, R);
+                                                      note_launch();
     }
 
     template <typename T> void iteration(const OpPool<T> &pool, double tol, int max_it) {
@@ -672,15 +749,20 @@ struct Runner {
         project(r, w);
         dot(w, w, nl);
         k_check<<<1, 256, 0, st>>>(ws.partial.as<double>(), S, tol, max_it, R);
+        note_launch();
         applyMinv<T>(pool, w, z);
         project(z, y);
         dot(y, w, nl);
         k_beta<<<1, 256, 0, st>>>(ws.partial.as<double>(), S, R);
+        note_launch();
         k_update_p<<<grid_for(nl * R), 256, 0, st>>>(y, S.beta, S.active, pv, nl, R);
+        note_launch();
         applyF<T>(pool, pv, q);
         dot(pv, q, nl);
         k_eta<<<1, 256, 0, st>>>(ws.partial.as<double>(), S, R);
+        note_launch();
         k_update_lr<<<grid_for(nl * R), 256, 0, st>>>(pv, q, S.eta, lam, r, nl, R);
+        note_launch();
     }
 
     // one FETI pass on subdomain loads ws.res; constraint right-hand side ws.cvec when with_c.
@@ -697,66 +779,91 @@ struct Runner {
         if (nu > 0)
             per_sub([&](int kb, int nk) {
                 k_reduce_forcing<T><<<dim3(64, nk), 256, 0, st>>>(pool.M.template as<T>(), sd, kb, f, ws.fU.as<double>(), R);
+                note_launch();
             });
         double *lam = ws.dlam.as<double>();
         T *x = ws.xU.as<T>();
         if (nl > 0) {
             k_cast<T><<<grid_for(nu * R), 256, 0, st>>>(ws.fU.as<double>(), x, nu * R);
+            note_launch();
             symv<T>(pool, 1, x, ws.yU.as<double>());
             k_gather_b<<<grid_for(nl * R), 256, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), ws.yU.as<double>(),
                                                          with_c ? ws.cvec.as<double>() : nullptr, ws.d.as<double>(), nl, R);
+                                                         note_launch();
             if (p->n_co > 0) {
                 k_proj_g<<<p->K, 256, 0, st>>>(sd, nullptr, nullptr, ws.fU.as<double>(), 1, p->d_Z.as<double>(),
                                                ws.gco.as<double>(), R);
+                                               note_launch();
                 k_coarse<<<1, 256, 0, st>>>(p->d_GtGinv.as<double>(), p->n_co, ws.gco.as<double>(), ws.alpha.as<double>(), R);
+                note_launch();
                 k_apply_galpha<<<grid_for(nl * R), 256, 0, st>>>(sd, p->d_u2sub.as<int32_t>(), p->d_Bp.as<int64_t>(),
                                                                  p->d_Bm.as<int64_t>(), p->d_Z.as<double>(),
                                                                  ws.alpha.as<double>(), nullptr, 1.0, lam, nl, R);
+                                                                 note_launch();
             } else {
                 NLF_CUDA(cudaMemsetAsync(lam, 0, sizeof(double) * nl * R, st));
             }
             applyF<T>(pool, lam, ws.q.as<double>());
             k_sub<<<grid_for(nl * R), 256, 0, st>>>(ws.d.as<double>(), ws.q.as<double>(), ws.r.as<double>(), nl * R);
+            note_launch();
             project(ws.d.as<double>(), ws.w.as<double>());
             dot(ws.w.as<double>(), ws.w.as<double>(), nl);
             k_set_norm_pd<<<1, 256, 0, st>>>(ws.partial.as<double>(), S, R);
+            note_launch();
             NLF_CUDA(cudaMemsetAsync(ws.pv.p, 0, sizeof(double) * nl * R, st));
             const int chunk = 4;
             int done = 0, n_active = R;
             cudaGraphExec_t exec = nullptr;
             if (batched) {
                 cudaGraph_t graph;
+                capturing = true;
+                cap_launches = 0;
                 NLF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
                 for (int i = 0; i < chunk; ++i) iteration<T>(pool, tol, max_it);
                 NLF_CUDA(cudaStreamEndCapture(st, &graph));
+                capturing = false;
                 NLF_CUDA(cudaGraphInstantiate(&exec, graph, 0));
                 NLF_CUDA(cudaGraphDestroy(graph));
             }
             while (done <= max_it) {
-                if (batched) NLF_CUDA(cudaGraphLaunch(exec, st));
-                else for (int i = 0; i < chunk; ++i) iteration<T>(pool, tol, max_it);
+                if (batched) {
+                    NLF_CUDA(cudaGraphLaunch(exec, st));
+                    eager_launches += cap_launches;
+                } else {
+                    for (int i = 0; i < chunk; ++i) iteration<T>(pool, tol, max_it);
+                }
                 done += chunk;
                 NLF_CUDA(cudaMemcpyAsync(ws.host_flag.data(), S.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
                 NLF_CUDA(cudaStreamSynchronize(st));
+                harvest(graph_slots, false);
+                harvest(eager_slots, true);
                 n_active = ws.host_flag[0];
                 if (n_active == 0) break;
             }
             if (exec) NLF_CUDA(cudaGraphExecDestroy(exec));
+            drop(graph_slots);
             // alpha from a fresh residual d - F lambda (eq. forAlpha)
             applyF<T>(pool, lam, ws.q.as<double>());
             k_sub<<<grid_for(nl * R), 256, 0, st>>>(ws.d.as<double>(), ws.q.as<double>(), ws.r.as<double>(), nl * R);
+            note_launch();
             // u_G = S^+ (fU - B^T lambda) - Z alpha  (eq. forU)
             k_gather_bt<double><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(),
                                                                   lam, ws.uU.as<double>(), nu, R);
+                                                                  note_launch();
             k_sub<<<grid_for(nu * R), 256, 0, st>>>(ws.fU.as<double>(), ws.uU.as<double>(), ws.uU.as<double>(), nu * R);
+            note_launch();
             k_cast<T><<<grid_for(nu * R), 256, 0, st>>>(ws.uU.as<double>(), x, nu * R);
+            note_launch();
             symv<T>(pool, 1, x, ws.uU.as<double>());
             if (p->n_co > 0) {
                 k_proj_g<<<p->K, 256, 0, st>>>(sd, p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), ws.r.as<double>(),
                                                0, p->d_Z.as<double>(), ws.gco.as<double>(), R);
+                                               note_launch();
                 k_coarse<<<1, 256, 0, st>>>(p->d_GtGinv.as<double>(), p->n_co, ws.gco.as<double>(), ws.alpha.as<double>(), R);
+                note_launch();
                 k_apply_zalpha<<<grid_for(nu * R), 256, 0, st>>>(sd, p->d_u2sub.as<int32_t>(), p->d_Z.as<double>(),
                                                                  ws.alpha.as<double>(), -1.0, ws.uU.as<double>(), nu, R);
+                                                                 note_launch();
             }
             std::vector<int> it(R);
             std::vector<double> rr(R);
@@ -770,11 +877,13 @@ struct Runner {
                 if (!(rr[c] <= tol)) info.converged = false;
         } else if (nu > 0) {
             k_cast<T><<<grid_for(nu * R), 256, 0, st>>>(ws.fU.as<double>(), x, nu * R);
+            note_launch();
             symv<T>(pool, 1, x, ws.uU.as<double>());
         }
         per_sub([&](int kb, int nk) {
             k_back_substitute<T><<<dim3(64, nk), 256, 0, st>>>(pool.M.template as<T>(), sd, kb, f, ws.uU.as<double>(),
                                                               ws.du.as<double>(), R);
+                                                              note_launch();
         });
         NLF_CUDA(cudaGetLastError());
         return info;
@@ -833,6 +942,7 @@ void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rh
                                                     p->d_ddofs.as<int32_t>(), p->d_doff.as<int64_t>(), d_g, ndof,
                                                     ws.ftil.as<double>(), R);
     NLF_CUDA(cudaGetLastError());
+    run.eager_launches += 2 + (d_g ? 1 : 0);
     nlfeti_stats s{};
     const bool mixed = p->opt.precision == 1;
     if (!mixed) {
@@ -866,6 +976,7 @@ void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rh
                     k_constraint_residual<<<grid_for(nl * R), 256, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(),
                                                                             p->d_u2v.as<int64_t>(), ws.u.as<double>(),
                                                                             ws.cvec.as<double>(), nl, R);
+                run.eager_launches += 1 + (nl > 0);
             }
             PassInfo pi = run.pass<float>(p->op32, p->opt.inner_tol, p->opt.max_it, sw > 0);
             s.iterations += pi.iterations;
@@ -876,6 +987,7 @@ void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rh
             k_absmax_partial<<<RED_BLOCKS, RED_THREADS, 0, st>>>(ws.du.as<double>(), ws.u.as<double>(), nv, R,
                                                                  ws.partial.as<double>(), ws.partial2.as<double>());
             k_rel_correction<<<1, 256, 0, st>>>(ws.partial.as<double>(), ws.partial2.as<double>(), R, run.S);
+            run.eager_launches += 3 + (nl > 0);
             std::vector<double> corr(R);
             NLF_CUDA(cudaMemcpyAsync(corr.data(), run.S.corr, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
             NLF_CUDA(cudaStreamSynchronize(st));
@@ -892,6 +1004,7 @@ void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rh
     k_output<<<grid_for(ndof * R), 256, 0, st>>>(ws.u.as<double>(), p->d_cp_ptr.as<int64_t>(), p->d_cp_pos.as<int64_t>(),
                                                  p->d_node_dir.as<int8_t>(), p->nc, d_g, ndof, R, d_out);
     NLF_CUDA(cudaGetLastError());
+    run.eager_launches += 1;
     if (stats) *stats = s;
 }
 
