@@ -118,8 +118,9 @@ typedef struct {
     int32_t max_nk, max_ngamma;
 } nlfeti_info;
 
-/* Default options: FP64 plain, tol 1e-10, max_it 1000, 4 refinement sweeps,
- * inner_tol 1e-6, refine_tol 1e-10, batched. */
+/* Default options: FP64 plain, tol 1e-10, max_it 1000, at most 10 refinement sweeps,
+ * inner_tol 1e-3 (each sweep's contraction is limited by the FP32 operators to ~1e-4
+ * anyway), refine_tol 1e-9, batched. */
 void nlfeti_default_options(nlfeti_options *opt);
 
 /* Context on the given CUDA stream (cudaStream_t, NULL = the legacy stream).

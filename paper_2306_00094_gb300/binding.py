@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import sys
 
 import numpy as np
 
@@ -176,6 +177,10 @@ class Context:
             self.h = None
 
     def __del__(self):
+        # at interpreter shutdown torch (whose allocator frees our device memory) may already be
+        # torn down; the process exit releases everything, so nothing is done then
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -298,6 +303,10 @@ class Problem:
             self.h = None
 
     def __del__(self):
+        # at interpreter shutdown torch (whose allocator frees our device memory) may already be
+        # torn down; the process exit releases everything, so nothing is done then
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -342,6 +351,10 @@ class Server:
             self.h = None
 
     def __del__(self):
+        # at interpreter shutdown torch (whose allocator frees our device memory) may already be
+        # torn down; the process exit releases everything, so nothing is done then
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:

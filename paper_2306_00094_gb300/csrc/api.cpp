@@ -248,14 +248,21 @@ void build_maps(nlfeti_problem *p) {
             if (!m.elem_dir[e])
                 for (int i = 0; i < nv; ++i) inc_el[fill[m.elems[e * nv + i]]++] = (int32_t)e;
     }
-    // symv work items: 64 rows each
+    // apply work items: kApplyRows rows each
     std::vector<int32_t> items;
     p->item_off.assign(K + 1, 0);
     for (int k = 0; k < K; ++k) {
-        for (int r0 = 0; r0 < p->sd[k].nG; r0 += 64) { items.push_back(k); items.push_back(r0); }
+        for (int r0 = 0; r0 < p->sd[k].nG; r0 += kApplyRows) { items.push_back(k); items.push_back(r0); }
         p->item_off[k + 1] = (int)(items.size() / 2);
     }
     p->n_items = (int)(items.size() / 2);
+    std::vector<int32_t> items_o;
+    p->item_off_o.assign(K + 1, 0);
+    for (int k = 0; k < K; ++k) {
+        for (int r0 = 0; r0 < p->sd[k].nO; r0 += kApplyRows) { items_o.push_back(k); items_o.push_back(r0); }
+        p->item_off_o[k + 1] = (int)(items_o.size() / 2);
+    }
+    upload(c, p->d_items_o, items_o);
     std::vector<uint64_t> mask = d.elem_mask;
     upload(c, p->d_sd, p->sd);
     upload(c, p->d_xy, m.xy);
@@ -294,9 +301,9 @@ void nlfeti_default_options(nlfeti_options *o) {
     o->precision = 0;
     o->tol = 1e-10;
     o->max_it = 1000;
-    o->max_refine = 6;
-    o->inner_tol = 1e-6;
-    o->refine_tol = 1e-10;
+    o->max_refine = 10;
+    o->inner_tol = 1e-3;
+    o->refine_tol = 1e-9;
     o->batched = 1;
     o->hbm_budget = 0;
 }
@@ -329,8 +336,7 @@ nlfeti_status nlfeti_create(nlfeti_ctx **out, const nlfeti_options *opt, void *c
     return NLFETI_OK;
 }
 
-void nlfeti_destroy(nlfeti_ctx *ctx) {
-    if (!ctx) return;
+static void ctx_free(nlfeti_ctx *ctx) {
     if (ctx->stream) {
         cudaStreamSynchronize(ctx->stream);
         cudaStreamDestroy(ctx->stream);
@@ -339,6 +345,41 @@ void nlfeti_destroy(nlfeti_ctx *ctx) {
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     delete ctx;
 }
+
+// A context outlives its problems and servers: destroying it while they are alive only
+// marks it, and the last of them to be destroyed frees it.
+void nlfeti_destroy(nlfeti_ctx *ctx) {
+    if (!ctx) return;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (ctx->children > 0) {
+            ctx->destroy_pending = true;
+            return;
+        }
+    }
+    ctx_free(ctx);
+}
+
+}  // extern "C"
+
+namespace nlf {
+void ctx_attach(nlfeti_ctx *c) {
+    std::lock_guard<std::mutex> g(c->mu);
+    c->children++;
+}
+
+void ctx_detach(nlfeti_ctx *c) {
+    bool free_now;
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        c->children--;
+        free_now = c->destroy_pending && c->children == 0;
+    }
+    if (free_now) ctx_free(c);
+}
+}  // namespace nlf
+
+extern "C" {
 
 const char *nlfeti_last_error(const nlfeti_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
@@ -376,14 +417,19 @@ nlfeti_status nlfeti_problem_create(nlfeti_ctx *ctx, const nlfeti_mesh *mesh, co
         q->ms_setup = now_ms() - t0;
         p = q.release();
     });
-    if (st == NLFETI_OK) *out = p;
+    if (st == NLFETI_OK) {
+        ctx_attach(ctx);
+        *out = p;
+    }
     return st;
 }
 
 void nlfeti_problem_destroy(nlfeti_problem *p) {
     if (!p) return;
-    if (p->ctx && p->ctx->stream) cudaStreamSynchronize(p->ctx->stream);
+    nlfeti_ctx *c = p->ctx;
+    if (c && c->stream) cudaStreamSynchronize(c->stream);
     delete p;
+    if (c) ctx_detach(c);
 }
 
 nlfeti_status nlfeti_problem_info(const nlfeti_problem *p, nlfeti_info *info) {

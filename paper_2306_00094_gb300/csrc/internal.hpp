@@ -20,8 +20,10 @@ struct nlfeti_ctx {
     void (*dev_free)(void *, void *) = nullptr;
     void *alloc_user = nullptr;
     std::string err;
-    std::mutex mu;                // guards err and bytes_in_use
+    std::mutex mu;                // guards err, bytes_in_use and the child count
     size_t bytes_in_use = 0;
+    int children = 0;             // live problems and servers
+    bool destroy_pending = false; // nlfeti_destroy was called while children were alive
 };
 
 namespace nlf {
@@ -116,6 +118,8 @@ struct SubdomainDesc {      // per subdomain, device resident (POD)
     int32_t pad;
 };
 
+constexpr int kApplyRows = 32;          // rows of an interface-apply work item
+
 template <typename T> struct OpPool {   // operators of one precision
     nlf::DevMem M, S, Sp;                // swept matrices, Schur complements, pseudo-inverses
     nlf::DevMem scratch;                 // panel scratch of the sweeps
@@ -158,9 +162,11 @@ struct nlfeti_problem {
     nlf::DevMem d_ddofs, d_doff;         // per subdomain: global dofs of the Dirichlet columns
     nlf::DevMem d_nodeinc_ptr, d_nodeinc_el;  // node -> interior elements (load vector gather)
     nlf::DevMem d_zeta_dof;              // per global dof: zeta (double)
-    nlf::DevMem d_items;                 // symv work items (k, first row) pairs
+    nlf::DevMem d_items;                 // row-product work items over Gamma rows: (k, first row) pairs
     int n_items = 0;
     std::vector<int> item_off;           // K+1
+    nlf::DevMem d_items_o;               // work items over Omega rows (back substitution)
+    std::vector<int> item_off_o;         // K+1
     nlf::DevMem d_flag;                  // device status words
     OpPool<double> op64;
     OpPool<float> op32;
@@ -182,4 +188,7 @@ void set_error(nlfeti_ctx *c, const std::string &msg);
 // order the library stream after the caller's stream (enter) and the caller's after it (leave)
 void stream_enter(nlfeti_ctx *c);
 void stream_leave(nlfeti_ctx *c);
+// a live problem or server keeps its context alive
+void ctx_attach(nlfeti_ctx *c);
+void ctx_detach(nlfeti_ctx *c);
 }  // namespace nlf

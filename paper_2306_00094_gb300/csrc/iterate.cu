@@ -126,59 +126,124 @@ __global__ void k_gather_bd(const int64_t *ptr, const int64_t *col, const double
 }
 
 // ------------------------------------------------------------------ dense symmetric apply (hot kernel)
-// y_k = M_k x_k for the work items (subdomain k, first row): M_k is n x n with leading
-// dimension ld (multiple of 8, zero padded), stored in T.  The CTA stages x_k transposed in
-// shared memory ([c][l]) for RC columns at a time; each warp owns 8 rows and each lane
-// streams 4 (FP32) or 2 (FP64) consecutive columns per step with one 16-byte load.
-// Products accumulate in T (FP32 on the mixed path) per lane, the warp sum in FP64.
+// y_k = M_k x_k for the work items (subdomain k, first row of a 32-row block): M_k is n x n
+// with leading dimension ld (multiple of 8, zero padded), stored in T.  Each warp owns 4
+// rows; each lane streams 4 (FP32) or 2 (FP64) consecutive columns of all 4 rows per step
+// with 16-byte streaming loads (two steps unrolled: 8 loads in flight per lane).  x_k is
+// staged in shared memory in chunks of SYMV_CW columns ([c][column], row stride padded by 4
+// to avoid bank conflicts), so a CTA needs 16 KB (FP32) and up to 8 CTAs share an SM.
+// Products accumulate in T per lane; the lane sum is a shuffle tree in T.
 template <typename T> struct Vec;
 template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
 template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
 
-template <typename T, int RC>
-__global__ void __launch_bounds__(256) k_symv(const T *base, int use_sp, const SubdomainDesc *sd, const int32_t *items,
-                                              const T *x, double *y, int R) {
+static_assert(kApplyRows == 32, "the apply kernel owns 32 rows per CTA (8 warps x 4)");
+constexpr int SYMV_CW = 512;      // staged columns per chunk
+
+// Modes of the row-product kernel (same streaming structure, different rows/columns/vectors):
+//   ROWS_APPLY:   y_U = M x_U with M = S_k^+ or S_k (rows and columns Gamma_k, x cast to T);
+//   ROWS_FORCING: f_U = f_G - (A_GO A_OO^-1) f_O, rows Gamma / columns Omega of the swept
+//                 matrix (eq. subForcing);
+//   ROWS_BACKSUB: u_O = -(M_OO f_O + M_OG u_G) = A_OO^-1 (f_O - A_OG u_G), rows Omega / all
+//                 columns of the swept matrix (eq. backwardSubstitution).
+enum { ROWS_APPLY = 0, ROWS_FORCING = 1, ROWS_BACKSUB = 2 };
+
+template <typename T, int RC, int MODE>
+__global__ void __launch_bounds__(256, 3) k_rows(const T *base, int use_sp, const SubdomainDesc *sd, const int32_t *items,
+                                                 const T *x, const double *xa, const double *xb, double *y, int R) {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
+    constexpr int XS = SYMV_CW + 4;                 // padded row of the staged x
+    __shared__ __align__(16) T xs[RC * XS];
     const int k = items[2 * blockIdx.x], row0 = items[2 * blockIdx.x + 1];
     const SubdomainDesc d = sd[k];
-    const int n = d.nG, ld = d.ldG;
-    const T *M = base + (use_sp ? d.offSp : d.offS);
-    extern __shared__ unsigned char smraw[];
-    T *xs = reinterpret_cast<T *>(smraw);
+    const int n = MODE == ROWS_BACKSUB ? d.nO : d.nG;                       // rows
+    const int ncols = MODE == ROWS_APPLY ? d.nG : (MODE == ROWS_FORCING ? d.nO : d.nk);
+    const int ld = MODE == ROWS_APPLY ? d.ldG : d.ldM;
+    const int ncp = min(ld, (ncols + 7) / 8 * 8);                           // padded columns
+    const int rbase = MODE == ROWS_FORCING ? d.nO : 0;                      // first matrix row
+    const T *M = base + (MODE == ROWS_APPLY ? (use_sp ? d.offSp : d.offS) : d.offM);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int ib = row0 + warp * 4;
+    const T *Mr[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) Mr[r] = M + (int64_t)(rbase + min(ib + r, n - 1)) * ld;
     for (int c0 = 0; c0 < R; c0 += RC) {
         const int rc = min(RC, R - c0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < RC * ld; t += blockDim.x) {
-            int c = t / ld, l = t % ld;
-            xs[t] = (c < rc && l < n) ? x[(d.offU + l) * R + c0 + c] : T(0);
-        }
-        __syncthreads();
-        for (int rr = 0; rr < 8; ++rr) {
-            const int i = row0 + warp * 8 + rr;
-            if (i >= n) break;
-            const T *Mi = M + (int64_t)i * ld;
-            T acc[RC];
+        T acc[4][RC];
 #pragma unroll
-            for (int c = 0; c < RC; ++c) acc[c] = T(0);
-            for (int l = lane * W; l < ld; l += 32 * W) {
-                V mv = *reinterpret_cast<const V *>(Mi + l);
-                const T *mvp = reinterpret_cast<const T *>(&mv);
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int c = 0; c < RC; ++c) {
-                    V xv = *reinterpret_cast<const V *>(xs + c * ld + l);
-                    const T *xp = reinterpret_cast<const T *>(&xv);
+            for (int c = 0; c < RC; ++c) acc[r][c] = T(0);
+        for (int l0 = 0; l0 < ncp; l0 += SYMV_CW) {
+            const int cw = min(SYMV_CW, ncp - l0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < RC * cw; t += blockDim.x) {
+                const int l = t / RC, c = t % RC, gl = l0 + l;
+                T v = T(0);
+                if (c < rc && gl < ncols) {
+                    if (MODE == ROWS_APPLY) v = x[(d.offU + gl) * R + c0 + c];
+                    else if (MODE == ROWS_FORCING || gl < d.nO) v = (T)xa[(d.offV + gl) * R + c0 + c];
+                    else v = (T)xb[(d.offU + gl - d.nO) * R + c0 + c];
+                }
+                xs[c * XS + l] = v;
+            }
+            __syncthreads();
+            if (ib < n) {
+                int l = lane * W;
+                for (; l + 32 * W < cw; l += 64 * W) {
+                    V mv[2][4];
 #pragma unroll
-                    for (int w = 0; w < W; ++w) acc[c] += mvp[w] * xp[w];
+                    for (int u = 0; u < 2; ++u)
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+                            mv[u][r] = __ldcs(reinterpret_cast<const V *>(Mr[r] + l0 + l + u * 32 * W));
+#pragma unroll
+                    for (int u = 0; u < 2; ++u)
+#pragma unroll
+                        for (int c = 0; c < RC; ++c) {
+                            V xv = *reinterpret_cast<const V *>(xs + c * XS + l + u * 32 * W);
+                            const T *xp = reinterpret_cast<const T *>(&xv);
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                const T *mp = reinterpret_cast<const T *>(&mv[u][r]);
+#pragma unroll
+                                for (int w = 0; w < W; ++w) acc[r][c] += mp[w] * xp[w];
+                            }
+                        }
+                }
+                for (; l < cw; l += 32 * W) {
+                    V mv[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) mv[r] = __ldcs(reinterpret_cast<const V *>(Mr[r] + l0 + l));
+#pragma unroll
+                    for (int c = 0; c < RC; ++c) {
+                        V xv = *reinterpret_cast<const V *>(xs + c * XS + l);
+                        const T *xp = reinterpret_cast<const T *>(&xv);
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const T *mp = reinterpret_cast<const T *>(&mv[r]);
+#pragma unroll
+                            for (int w = 0; w < W; ++w) acc[r][c] += mp[w] * xp[w];
+                        }
+                    }
                 }
             }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
             for (int c = 0; c < RC; ++c) {
-                double v = warp_sum((double)acc[c]);
-                if (lane == 0 && c < rc) y[(d.offU + i) * R + c0 + c] = v;
+                T v = acc[r][c];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0 && c < rc && ib + r < n) {
+                    const int i = ib + r;
+                    if (MODE == ROWS_APPLY) y[(d.offU + i) * R + c0 + c] = (double)v;
+                    else if (MODE == ROWS_FORCING)
+                        y[(d.offU + i) * R + c0 + c] = xa[(d.offV + d.nO + i) * R + c0 + c] - (double)v;
+                    else y[(d.offV + i) * R + c0 + c] = -(double)v;
+                }
             }
-        }
     }
 }
 
@@ -216,59 +281,12 @@ __global__ void k_residual(const double *A, const SubdomainDesc *sd, int kbase, 
     }
 }
 
-// reduced forcing (eq. subForcing): fU = f_G - (A_GO A_OO^-1) f_O from rows G, columns O of the swept matrix
-template <typename T>
-__global__ void k_reduce_forcing(const T *pool, const SubdomainDesc *sd, int kbase, const double *f, double *fU,
-                                 int R) {
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const SubdomainDesc d = sd[kbase + blockIdx.y];
-    for (int i = blockIdx.x * 8 + warp; i < d.nG; i += gridDim.x * 8) {
-        const T *Mi = pool + d.offM + (int64_t)(d.nO + i) * d.ldM;
-        for (int c0 = 0; c0 < R; c0 += 8) {
-            const int rc = min(8, R - c0);
-            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int l = lane; l < d.nO; l += 32) {
-                double m = (double)Mi[l];
-                const double *xl = f + (d.offV + l) * R + c0;
-                for (int c = 0; c < rc; ++c) acc[c] += m * xl[c];
-            }
-#pragma unroll
-            for (int c = 0; c < 8; ++c) acc[c] = warp_sum(acc[c]);
-            if (lane < rc) fU[(d.offU + i) * R + c0 + lane] = f[(d.offV + d.nO + i) * R + c0 + lane] - acc[lane];
-        }
-    }
-}
-
-// back substitution (eq. backwardSubstitution): u_O = -(M_OO f_O + M_OG u_G) on the swept matrix;
-// the Gamma part of the subdomain vector is u_G
-template <typename T>
-__global__ void k_back_substitute(const T *pool, const SubdomainDesc *sd, int kbase, const double *f,
-                                  const double *uU, double *u, int R) {
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const SubdomainDesc d = sd[kbase + blockIdx.y];
-    for (int i = blockIdx.x * 8 + warp; i < d.nk; i += gridDim.x * 8) {
-        if (i >= d.nO) {
-            for (int c = lane; c < R; c += 32) u[(d.offV + i) * R + c] = uU[(d.offU + i - d.nO) * R + c];
-            continue;
-        }
-        const T *Mi = pool + d.offM + (int64_t)i * d.ldM;
-        for (int c0 = 0; c0 < R; c0 += 8) {
-            const int rc = min(8, R - c0);
-            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int l = lane; l < d.nO; l += 32) {
-                double m = (double)Mi[l];
-                const double *xl = f + (d.offV + l) * R + c0;
-                for (int c = 0; c < rc; ++c) acc[c] += m * xl[c];
-            }
-            for (int l = lane; l < d.nG; l += 32) {
-                double m = (double)Mi[d.nO + l];
-                const double *xl = uU + (d.offU + l) * R + c0;
-                for (int c = 0; c < rc; ++c) acc[c] += m * xl[c];
-            }
-#pragma unroll
-            for (int c = 0; c < 8; ++c) acc[c] = warp_sum(acc[c]);
-            if (lane < rc) u[(d.offV + i) * R + c0 + lane] = -acc[lane];
-        }
+// subdomain vector entries of Gamma_k from a U-space vector: v[u2v[i]] = uU[i]
+__global__ void k_scatter_u(const int64_t *u2v, const double *uU, double *v, int64_t nu, int R) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / R;
+        const int c = (int)(t % R);
+        v[u2v[i] * R + c] = uU[t];
     }
 }
 
@@ -348,60 +366,6 @@ __global__ void k_output(const double *u, const int64_t *cp_ptr, const int64_t *
     }
 }
 
-// ------------------------------------------------------------------ projection and coarse problem
-// g = Z^T B^T v per floating subdomain (one CTA each); v_is_u: v already lives in U
-__global__ void k_proj_g(const SubdomainDesc *sd, const int64_t *bt_ptr, const int64_t *bt_row, const double *v,
-                         int v_is_u, const double *Z, double *g, int R) {
-    const SubdomainDesc d = sd[blockIdx.x];
-    if (d.n_co == 0) return;
-    __shared__ double red[8][24];
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int c0 = 0; c0 < R; c0 += 8) {
-        const int rc = min(8, R - c0);
-        double acc[3][8];
-        for (int a = 0; a < 3; ++a)
-            for (int c = 0; c < 8; ++c) acc[a][c] = 0;
-        for (int64_t l = threadIdx.x; l < d.nG; l += blockDim.x) {
-            const int64_t ui = d.offU + l;
-            for (int c = 0; c < rc; ++c) {
-                double bt;
-                if (v_is_u) bt = v[ui * R + c0 + c];
-                else {
-                    bt = 0;
-                    for (int64_t q = bt_ptr[ui]; q < bt_ptr[ui + 1]; ++q) {
-                        int64_t rr = bt_row[q];
-                        bt += rr > 0 ? v[(rr - 1) * R + c0 + c] : -v[(-rr - 1) * R + c0 + c];
-                    }
-                }
-                for (int a = 0; a < d.n_co; ++a) acc[a][c] += Z[ui * 3 + a] * bt;
-            }
-        }
-        for (int a = 0; a < 3; ++a)
-            for (int c = 0; c < 8; ++c) acc[a][c] = warp_sum(acc[a][c]);
-        __syncthreads();
-        if (lane == 0)
-            for (int a = 0; a < 3; ++a)
-                for (int c = 0; c < 8; ++c) red[warp][a * 8 + c] = acc[a][c];
-        __syncthreads();
-        if (threadIdx.x < 24) {
-            int a = threadIdx.x / 8, c = threadIdx.x % 8;
-            double s = 0;
-            for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w][a * 8 + c];
-            if (a < d.n_co && c < rc) g[(int64_t)(d.co_off + a) * R + c0 + c] = s;
-        }
-    }
-}
-
-// alpha = (G^T G)^-1 g (one CTA)
-__global__ void k_coarse(const double *GtGinv, int nco, const double *g, double *alpha, int R) {
-    for (int t = threadIdx.x; t < nco * R; t += blockDim.x) {
-        int i = t / R, c = t % R;
-        double s = 0;
-        for (int j = 0; j < nco; ++j) s += GtGinv[(int64_t)i * nco + j] * g[(int64_t)j * R + c];
-        alpha[t] = s;
-    }
-}
-
 __device__ __forceinline__ double z_alpha(const SubdomainDesc *sd, const int32_t *u2sub, const double *Z,
                                           const double *alpha, int64_t u, int c, int R) {
     const SubdomainDesc d = sd[u2sub[u]];
@@ -432,11 +396,27 @@ __global__ void k_apply_zalpha(const SubdomainDesc *sd, const int32_t *u2sub, co
     }
 }
 
-// ------------------------------------------------------------------ reductions (fixed order)
-// partial[b * R + c] = sum over the block's grid-stride range of a*b (column c)
-__global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const double *a, const double *b, int64_t n, int R,
-                                                              double *partial) {
+// PCG scalar state, per right-hand side
+struct PcgScalars {
+    double *nPd, *yw_old, *yw, *eta, *beta, *relres, *corr;
+    int *active, *iters, *n_active;
+    unsigned *counter;     // arrival counter of the fused reductions (reset by the last block)
+};
+
+enum { FIN_NPD = 0, FIN_CHECK = 1, FIN_BETA = 2, FIN_ETA = 3 };
+
+// Dot products per column with the scalar update fused in: every block writes its partial
+// sums; the last block to arrive adds all partials in a fixed order (deterministic) and
+// updates the PCG scalars:
+//   NPD:   ||P d|| and the initial state;      CHECK: ||w|| and the active mask;
+//   BETA:  (y,w) and beta = (y,w)/(y,w)_old;    ETA:   (p,q) and eta = (y,w)/(p,q).
+template <int MODE>
+__global__ void __launch_bounds__(RED_THREADS) k_dot_final(const double *a, const double *b, int64_t n, int R,
+                                                            double *partial, PcgScalars s, double tol, int max_it) {
     __shared__ double red[RED_THREADS / 32][8];
+    __shared__ double tot[RED_THREADS];
+    __shared__ bool last;
+    __shared__ int cnt;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     for (int c0 = 0; c0 < R; c0 += 8) {
         const int rc = min(8, R - c0);
@@ -453,10 +433,124 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const double *a, co
             for (int c = 0; c < 8; ++c) red[warp][c] = acc[c];
         __syncthreads();
         if (threadIdx.x < rc) {
-            double s = 0;
-            for (int w = 0; w < RED_THREADS / 32; ++w) s += red[w][threadIdx.x];
-            partial[(int64_t)blockIdx.x * R + c0 + threadIdx.x] = s;
+            double t = 0;
+            for (int w = 0; w < RED_THREADS / 32; ++w) t += red[w][threadIdx.x];
+            partial[(int64_t)blockIdx.x * R + c0 + threadIdx.x] = t;
         }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(s.counter, 1u);
+        last = (prev == gridDim.x - 1);
+        cnt = 0;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int c = 0; c < R; ++c) {
+        double t = 0;
+        for (int bl = threadIdx.x; bl < (int)gridDim.x; bl += blockDim.x) t += __ldcg(partial + (int64_t)bl * R + c);
+        tot[threadIdx.x] = t;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) tot[threadIdx.x] += tot[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double v = tot[0];
+            if (MODE == FIN_NPD) {
+                s.nPd[c] = sqrt(v);
+                s.active[c] = 1;
+                s.iters[c] = 0;
+                s.yw_old[c] = 1.0;
+                s.relres[c] = 1.0;
+            } else if (MODE == FIN_CHECK) {
+                const double nw = sqrt(v), ref = s.nPd[c];
+                if (s.active[c]) s.relres[c] = ref > 0 ? nw / ref : 0.0;
+                if (s.active[c] && (nw <= tol * ref || s.iters[c] >= max_it)) s.active[c] = 0;
+                cnt += s.active[c] ? 1 : 0;
+            } else if (MODE == FIN_BETA) {
+                s.yw[c] = v;
+                s.beta[c] = (s.iters[c] == 0 || s.yw_old[c] == 0.0) ? 0.0 : v / s.yw_old[c];
+            } else {
+                const bool act = s.active[c] != 0;
+                s.eta[c] = (act && v != 0.0) ? s.yw[c] / v : 0.0;
+                if (act) { s.yw_old[c] = s.yw[c]; s.iters[c] += 1; }
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (MODE == FIN_NPD) *s.n_active = R;
+        if (MODE == FIN_CHECK) *s.n_active = cnt;
+        *s.counter = 0u;
+    }
+}
+
+// g_part = Z^T B^T v over one slice of a floating subdomain's Gamma dofs (grid: K x PSPLIT);
+// v_is_u: v already lives in U
+constexpr int PSPLIT = 8;
+__global__ void k_proj_g_part(const SubdomainDesc *sd, const int64_t *bt_ptr, const int64_t *bt_row, const double *v,
+                              int v_is_u, const double *Z, double *gpart, int R) {
+    const SubdomainDesc d = sd[blockIdx.x];
+    if (d.n_co == 0) return;
+    __shared__ double red[8][24];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int64_t chunk = (d.nG + PSPLIT - 1) / PSPLIT;
+    const int64_t l0 = blockIdx.y * chunk, l1 = min((int64_t)d.nG, l0 + chunk);
+    for (int c0 = 0; c0 < R; c0 += 8) {
+        const int rc = min(8, R - c0);
+        double acc[3][8];
+        for (int q = 0; q < 3; ++q)
+            for (int c = 0; c < 8; ++c) acc[q][c] = 0;
+        for (int64_t l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
+            const int64_t ui = d.offU + l;
+            for (int c = 0; c < rc; ++c) {
+                double bt;
+                if (v_is_u) bt = v[ui * R + c0 + c];
+                else {
+                    bt = 0;
+                    for (int64_t q = bt_ptr[ui]; q < bt_ptr[ui + 1]; ++q) {
+                        int64_t rr = bt_row[q];
+                        bt += rr > 0 ? v[(rr - 1) * R + c0 + c] : -v[(-rr - 1) * R + c0 + c];
+                    }
+                }
+                for (int q = 0; q < d.n_co; ++q) acc[q][c] += Z[ui * 3 + q] * bt;
+            }
+        }
+        for (int q = 0; q < 3; ++q)
+            for (int c = 0; c < 8; ++c) acc[q][c] = warp_sum(acc[q][c]);
+        __syncthreads();
+        if (lane == 0)
+            for (int q = 0; q < 3; ++q)
+                for (int c = 0; c < 8; ++c) red[warp][q * 8 + c] = acc[q][c];
+        __syncthreads();
+        if (threadIdx.x < 24) {
+            int q = threadIdx.x / 8, c = threadIdx.x % 8;
+            double t = 0;
+            for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w][q * 8 + c];
+            if (q < d.n_co && c < rc)
+                gpart[((int64_t)(d.co_off + q) * PSPLIT + blockIdx.y) * R + c0 + c] = t;
+        }
+    }
+}
+
+// alpha = (G^T G)^-1 g with g summed from the slices in a fixed order (one CTA)
+__global__ void k_coarse_parts(const double *GtGinv, int nco, const double *gpart, double *alpha, int R) {
+    extern __shared__ double gs[];
+    for (int t = threadIdx.x; t < nco * R; t += blockDim.x) {
+        int i = t / R, c = t % R;
+        double s = 0;
+        for (int j = 0; j < PSPLIT; ++j) s += gpart[((int64_t)i * PSPLIT + j) * R + c];
+        gs[t] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nco * R; t += blockDim.x) {
+        int i = t / R, c = t % R;
+        double s = 0;
+        for (int j = 0; j < nco; ++j) s += GtGinv[(int64_t)i * nco + j] * gs[j * R + c];
+        alpha[t] = s;
     }
 }
 
@@ -486,67 +580,11 @@ __global__ void __launch_bounds__(RED_THREADS) k_absmax_partial(const double *a,
     }
 }
 
-// PCG scalar state, per right-hand side
-struct PcgScalars {
-    double *nPd, *yw_old, *yw, *eta, *beta, *relres, *corr;
-    int *active, *iters, *n_active;
-};
-
-__device__ __forceinline__ double sum_partials(const double *partial, int c, int R) {
-    double s = 0;
-    for (int b = 0; b < RED_BLOCKS; ++b) s += partial[(int64_t)b * R + c];
-    return s;
-}
-
 __global__ void k_rel_correction(const double *pa, const double *pb, int R, PcgScalars s) {
     for (int c = threadIdx.x; c < R; c += blockDim.x) {
         double a = 0, b = 0;
         for (int bl = 0; bl < RED_BLOCKS; ++bl) { a = fmax(a, pa[(int64_t)bl * R + c]); b = fmax(b, pb[(int64_t)bl * R + c]); }
         s.corr[c] = b > 0 ? a / b : (a > 0 ? 1.0 : 0.0);
-    }
-}
-
-__global__ void k_set_norm_pd(const double *partial, PcgScalars s, int R) {
-    for (int c = threadIdx.x; c < R; c += blockDim.x) {
-        s.nPd[c] = sqrt(sum_partials(partial, c, R));
-        s.active[c] = 1;
-        s.iters[c] = 0;
-        s.yw_old[c] = 1.0;
-        s.relres[c] = 1.0;
-    }
-    if (threadIdx.x == 0) *s.n_active = R;
-}
-
-// after w = P r: update the active mask
-__global__ void k_check(const double *partial, PcgScalars s, double tol, int max_it, int R) {
-    __shared__ int cnt;
-    if (threadIdx.x == 0) cnt = 0;
-    __syncthreads();
-    for (int c = threadIdx.x; c < R; c += blockDim.x) {
-        double nw = sqrt(sum_partials(partial, c, R));
-        double ref = s.nPd[c];
-        if (s.active[c]) s.relres[c] = ref > 0 ? nw / ref : 0.0;
-        if (s.active[c] && (nw <= tol * ref || s.iters[c] >= max_it)) s.active[c] = 0;
-        if (s.active[c]) atomicAdd(&cnt, 1);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *s.n_active = cnt;
-}
-
-__global__ void k_beta(const double *partial, PcgScalars s, int R) {
-    for (int c = threadIdx.x; c < R; c += blockDim.x) {
-        double yw = sum_partials(partial, c, R);
-        s.yw[c] = yw;
-        s.beta[c] = (s.iters[c] == 0 || s.yw_old[c] == 0.0) ? 0.0 : yw / s.yw_old[c];
-    }
-}
-
-__global__ void k_eta(const double *partial, PcgScalars s, int R) {
-    for (int c = threadIdx.x; c < R; c += blockDim.x) {
-        double pq = sum_partials(partial, c, R);
-        bool act = s.active[c] != 0;
-        s.eta[c] = (act && pq != 0.0) ? s.yw[c] / pq : 0.0;
-        if (act) { s.yw_old[c] = s.yw[c]; s.iters[c] += 1; }
     }
 }
 
@@ -596,8 +634,14 @@ struct Runner {
         S.corr = b + 6 * R;
         int *ib = reinterpret_cast<int *>(b + 7 * R);
         S.active = ib; S.iters = ib + R; S.n_active = ib + 2 * R;
+        S.counter = reinterpret_cast<unsigned *>(ib + 2 * R + 1);
         sd = p->d_sd.as<SubdomainDesc>();
         set_attributes();
+    }
+
+    template <int MODE> void dot_final(const double *a, const double *b, int64_t n, double tol = 0, int max_it = 0) {
+        k_dot_final<MODE><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, n, R, ws.partial.as<double>(), S, tol, max_it);
+        note_launch();
     }
 
     ~Runner() {
@@ -635,8 +679,13 @@ struct Runner {
         if (clear) drop(v);
     }
 
-    void dot(const double *a, const double *b, int64_t n) {
-        k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, n, R, ws.partial.as<double>());
+    // alpha = (G^T G)^-1 Z^T B^T v  (or (G^T G)^-1 Z^T v for v in U)
+    void coarse_alpha(const double *v, int v_is_u) {
+        k_proj_g_part<<<dim3(p->K, PSPLIT), 256, 0, st>>>(sd, p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), v,
+                                                           v_is_u, p->d_Z.as<double>(), ws.gco.as<double>(), R);
+        note_launch();
+        k_coarse_parts<<<1, 256, sizeof(double) * p->n_co * R, st>>>(p->d_GtGinv.as<double>(), p->n_co,
+                                                                      ws.gco.as<double>(), ws.alpha.as<double>(), R);
         note_launch();
     }
 
@@ -647,69 +696,60 @@ struct Runner {
             if (out != v) NLF_CUDA(cudaMemcpyAsync(out, v, sizeof(double) * nl * R, cudaMemcpyDeviceToDevice, st));
             return;
         }
-        k_proj_g<<<p->K, 256, 0, st>>>(sd, p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), v, 0,
-                                       p->d_Z.as<double>(), ws.gco.as<double>(), R);
-                                       note_launch();
-        k_coarse<<<1, 256, 0, st>>>(p->d_GtGinv.as<double>(), p->n_co, ws.gco.as<double>(), ws.alpha.as<double>(), R);
-        note_launch();
+        coarse_alpha(v, 0);
         k_apply_galpha<<<grid_for(nl * R), 256, 0, st>>>(sd, p->d_u2sub.as<int32_t>(), p->d_Bp.as<int64_t>(),
                                                          p->d_Bm.as<int64_t>(), p->d_Z.as<double>(),
                                                          ws.alpha.as<double>(), v, -1.0, out, nl, R);
                                                          note_launch();
     }
 
-    template <typename T, int RC> void symv_launch(const T *base, int use_sp, const int32_t *it, int nitems, const T *x,
-                                                   double *y, size_t sm) {
-        k_symv<T, RC><<<nitems, 256, sm, st>>>(base, use_sp, sd, it, x, y, R);
+    template <typename T, int RC, int MODE> void rows_launch(const T *base, int use_sp, const int32_t *it, int nitems,
+                                                            const T *x, const double *xa, const double *xb, double *y) {
+        k_rows<T, RC, MODE><<<nitems, 256, 0, st>>>(base, use_sp, sd, it, x, xa, xb, y, R);
         note_launch();
     }
 
-    // shared-memory limits of every apply variant, set once outside any graph capture
-    void set_attributes() {
-        const int sm = (int)(sizeof(double) * 8 * p->max_ldG);
-        if (sm > 227 * 1024) fail(NLFETI_E_INVALID, "an interface block is too large for the apply kernel");
-        NLF_CUDA(cudaFuncSetAttribute(k_symv<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-        NLF_CUDA(cudaFuncSetAttribute(k_symv<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-        NLF_CUDA(cudaFuncSetAttribute(k_symv<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-        NLF_CUDA(cudaFuncSetAttribute(k_symv<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-        NLF_CUDA(cudaFuncSetAttribute(k_symv<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-        NLF_CUDA(cudaFuncSetAttribute(k_symv<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-        NLF_CUDA(cudaFuncSetAttribute(k_symv<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-        NLF_CUDA(cudaFuncSetAttribute(k_symv<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    // one row-product stage over every subdomain: one launch (batched) or one per subdomain;
+    // returns the number of launches
+    template <typename T, int MODE> int rows(const T *base, int use_sp, const T *x, const double *xa, const double *xb,
+                                             double *y, const DevMem &items, const std::vector<int> &off) {
+        const int rc = R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1));
+        auto go = [&](const int32_t *it, int nitems) {
+            if (nitems <= 0) return 0;
+            switch (rc) {
+                case 8: rows_launch<T, 8, MODE>(base, use_sp, it, nitems, x, xa, xb, y); break;
+                case 4: rows_launch<T, 4, MODE>(base, use_sp, it, nitems, x, xa, xb, y); break;
+                case 2: rows_launch<T, 2, MODE>(base, use_sp, it, nitems, x, xa, xb, y); break;
+                default: rows_launch<T, 1, MODE>(base, use_sp, it, nitems, x, xa, xb, y); break;
+            }
+            return 1;
+        };
+        const int32_t *it = items.as<int32_t>();
+        const int K = p->K;
+        if (p->opt.batched) return go(it, off[K]);
+        int launches = 0;
+        for (int k = 0; k < K; ++k) launches += go(it + 2 * off[k], off[k + 1] - off[k]);
+        return launches;
     }
+
+    void set_attributes() {}
 
     // y = S^+ x (use_sp = 1) or S x (use_sp = 0) on every subdomain
     template <typename T> void symv(const OpPool<T> &pool, int use_sp, const T *x, double *y) {
         if (p->n_u == 0) return;
-        const int rc = R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1));
-        const size_t sm = sizeof(T) * (size_t)rc * p->max_ldG;
         const T *base = use_sp ? pool.Sp.template as<T>() : pool.S.template as<T>();
-        auto go = [&](const int32_t *it, int nitems) {
-            if (nitems <= 0) return;
-            switch (rc) {
-                case 8: symv_launch<T, 8>(base, use_sp, it, nitems, x, y, sm); break;
-                case 4: symv_launch<T, 4>(base, use_sp, it, nitems, x, y, sm); break;
-                case 2: symv_launch<T, 2>(base, use_sp, it, nitems, x, y, sm); break;
-                default: symv_launch<T, 1>(base, use_sp, it, nitems, x, y, sm); break;
-            }
-        };
-        const int32_t *items = p->d_items.as<int32_t>();
         Slot slot{};
         const bool timed = p->prof_on;
+        // inside a capture the records must become event nodes of the graph to be timed
+        const unsigned rec_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
         if (timed) {
             NLF_CUDA(cudaEventCreate(&slot.a));
             NLF_CUDA(cudaEventCreate(&slot.b));
-            NLF_CUDA(cudaEventRecord(slot.a, st));
+            NLF_CUDA(cudaEventRecordWithFlags(slot.a, st, rec_flags));
         }
-        int launches = 0;
-        if (p->opt.batched) { go(items, p->n_items); launches = 1; }
-        else
-            for (int k = 0; k < p->K; ++k) {
-                go(items + 2 * p->item_off[k], p->item_off[k + 1] - p->item_off[k]);
-                launches += p->item_off[k + 1] > p->item_off[k];
-            }
+        const int launches = rows<T, ROWS_APPLY>(base, use_sp, x, nullptr, nullptr, y, p->d_items, p->item_off);
         if (timed) {
-            NLF_CUDA(cudaEventRecord(slot.b, st));
+            NLF_CUDA(cudaEventRecordWithFlags(slot.b, st, rec_flags));
             double bytes = 0;
             for (const auto &d : p->sd)
                 bytes += (double)d.nG * d.ldG * sizeof(T) + (double)d.nG * R * (sizeof(T) + sizeof(double));
@@ -747,20 +787,14 @@ struct Runner {
         double *r = ws.r.as<double>(), *w = ws.w.as<double>(), *z = ws.z.as<double>(), *y = ws.y.as<double>(),
                *pv = ws.pv.as<double>(), *q = ws.q.as<double>(), *lam = ws.dlam.as<double>();
         project(r, w);
-        dot(w, w, nl);
-        k_check<<<1, 256, 0, st>>>(ws.partial.as<double>(), S, tol, max_it, R);
-        note_launch();
+        dot_final<FIN_CHECK>(w, w, nl, tol, max_it);
         applyMinv<T>(pool, w, z);
         project(z, y);
-        dot(y, w, nl);
-        k_beta<<<1, 256, 0, st>>>(ws.partial.as<double>(), S, R);
-        note_launch();
+        dot_final<FIN_BETA>(y, w, nl);
         k_update_p<<<grid_for(nl * R), 256, 0, st>>>(y, S.beta, S.active, pv, nl, R);
         note_launch();
         applyF<T>(pool, pv, q);
-        dot(pv, q, nl);
-        k_eta<<<1, 256, 0, st>>>(ws.partial.as<double>(), S, R);
-        note_launch();
+        dot_final<FIN_ETA>(pv, q, nl);
         k_update_lr<<<grid_for(nl * R), 256, 0, st>>>(pv, q, S.eta, lam, r, nl, R);
         note_launch();
     }
@@ -772,15 +806,9 @@ struct Runner {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         const double *f = ws.res.as<double>();
         const bool batched = p->opt.batched != 0;
-        auto per_sub = [&](auto &&launch) {
-            if (batched) launch(0, p->K);
-            else for (int k = 0; k < p->K; ++k) launch(k, 1);
-        };
         if (nu > 0)
-            per_sub([&](int kb, int nk) {
-                k_reduce_forcing<T><<<dim3(64, nk), 256, 0, st>>>(pool.M.template as<T>(), sd, kb, f, ws.fU.as<double>(), R);
-                note_launch();
-            });
+            rows<T, ROWS_FORCING>(pool.M.template as<T>(), 0, nullptr, f, nullptr, ws.fU.as<double>(), p->d_items,
+                                  p->item_off);
         double *lam = ws.dlam.as<double>();
         T *x = ws.xU.as<T>();
         if (nl > 0) {
@@ -791,11 +819,7 @@ struct Runner {
                                                          with_c ? ws.cvec.as<double>() : nullptr, ws.d.as<double>(), nl, R);
                                                          note_launch();
             if (p->n_co > 0) {
-                k_proj_g<<<p->K, 256, 0, st>>>(sd, nullptr, nullptr, ws.fU.as<double>(), 1, p->d_Z.as<double>(),
-                                               ws.gco.as<double>(), R);
-                                               note_launch();
-                k_coarse<<<1, 256, 0, st>>>(p->d_GtGinv.as<double>(), p->n_co, ws.gco.as<double>(), ws.alpha.as<double>(), R);
-                note_launch();
+                coarse_alpha(ws.fU.as<double>(), 1);
                 k_apply_galpha<<<grid_for(nl * R), 256, 0, st>>>(sd, p->d_u2sub.as<int32_t>(), p->d_Bp.as<int64_t>(),
                                                                  p->d_Bm.as<int64_t>(), p->d_Z.as<double>(),
                                                                  ws.alpha.as<double>(), nullptr, 1.0, lam, nl, R);
@@ -807,9 +831,7 @@ struct Runner {
             k_sub<<<grid_for(nl * R), 256, 0, st>>>(ws.d.as<double>(), ws.q.as<double>(), ws.r.as<double>(), nl * R);
             note_launch();
             project(ws.d.as<double>(), ws.w.as<double>());
-            dot(ws.w.as<double>(), ws.w.as<double>(), nl);
-            k_set_norm_pd<<<1, 256, 0, st>>>(ws.partial.as<double>(), S, R);
-            note_launch();
+            dot_final<FIN_NPD>(ws.w.as<double>(), ws.w.as<double>(), nl);
             NLF_CUDA(cudaMemsetAsync(ws.pv.p, 0, sizeof(double) * nl * R, st));
             const int chunk = 4;
             int done = 0, n_active = R;
@@ -856,11 +878,7 @@ struct Runner {
             note_launch();
             symv<T>(pool, 1, x, ws.uU.as<double>());
             if (p->n_co > 0) {
-                k_proj_g<<<p->K, 256, 0, st>>>(sd, p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), ws.r.as<double>(),
-                                               0, p->d_Z.as<double>(), ws.gco.as<double>(), R);
-                                               note_launch();
-                k_coarse<<<1, 256, 0, st>>>(p->d_GtGinv.as<double>(), p->n_co, ws.gco.as<double>(), ws.alpha.as<double>(), R);
-                note_launch();
+                coarse_alpha(ws.r.as<double>(), 0);
                 k_apply_zalpha<<<grid_for(nu * R), 256, 0, st>>>(sd, p->d_u2sub.as<int32_t>(), p->d_Z.as<double>(),
                                                                  ws.alpha.as<double>(), -1.0, ws.uU.as<double>(), nu, R);
                                                                  note_launch();
@@ -880,11 +898,13 @@ struct Runner {
             note_launch();
             symv<T>(pool, 1, x, ws.uU.as<double>());
         }
-        per_sub([&](int kb, int nk) {
-            k_back_substitute<T><<<dim3(64, nk), 256, 0, st>>>(pool.M.template as<T>(), sd, kb, f, ws.uU.as<double>(),
-                                                              ws.du.as<double>(), R);
-                                                              note_launch();
-        });
+        rows<T, ROWS_BACKSUB>(pool.M.template as<T>(), 0, nullptr, f, ws.uU.as<double>(), ws.du.as<double>(),
+                              p->d_items_o, p->item_off_o);
+        if (nu > 0) {
+            k_scatter_u<<<grid_for(nu * R), 256, 0, st>>>(p->d_u2v.as<int64_t>(), ws.uU.as<double>(), ws.du.as<double>(),
+                                                          nu, R);
+            note_launch();
+        }
         NLF_CUDA(cudaGetLastError());
         return info;
     }
@@ -911,10 +931,11 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     A(fU, nu); A(yU, nu); A(uU, nu); A(xU, nu);
     A(ftil, nv); A(res, nv); A(u, nv); A(du, nv);
     A(F, nd);
-    A(gco, nco); A(alpha, nco);
+    A(gco, nco * PSPLIT); A(alpha, nco);
     alloc(partial, sizeof(double) * RED_BLOCKS * R);
     alloc(partial2, sizeof(double) * RED_BLOCKS * R);
-    alloc(scal, sizeof(double) * R * 7 + sizeof(int) * (2 * R + 4));
+    alloc(scal, sizeof(double) * R * 7 + sizeof(int) * (2 * R + 8));
+    NLF_CUDA(cudaMemsetAsync(scal.p, 0, scal.bytes, async_stream ? async_stream : c->stream));
     host_flag.assign(4, 0);
 }
 

@@ -143,6 +143,7 @@ nlfeti_status nlfeti_server_create(nlfeti_ctx *ctx, size_t hbm_budget, int max_s
         delete s;
         return NLFETI_E_INVALID;
     }
+    ctx_attach(ctx);
     *out = s;
     return NLFETI_OK;
 }
@@ -212,7 +213,9 @@ void nlfeti_server_destroy(nlfeti_server *s) {
     }
     s->cv_work.notify_all();
     for (auto &t : s->workers) t.join();
+    nlfeti_ctx *c = s->ctx;
     delete s;
+    ctx_detach(c);
 }
 
 }  // extern "C"
