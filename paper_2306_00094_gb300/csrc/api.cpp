@@ -160,7 +160,7 @@ void build_maps(nlfeti_problem *p) {
     p->n_u = d.u_off[K];
     p->n_co = d.co_off[K];
     p->sd.assign(K, SubdomainDesc{});
-    int64_t offA = 0, offAD = 0, offM = 0, offG = 0, offV = 0;
+    int64_t offA = 0, offAD = 0, offM = 0, offG = 0, offV = 0, offUp = 0;
     p->n_floating = 0;
     p->max_ldG = 8;
     for (int k = 0; k < K; ++k) {
@@ -177,6 +177,7 @@ void build_maps(nlfeti_problem *p) {
         s.offM = offM; offM += (int64_t)s.nk * s.ldM;
         s.offS = offG; s.offSp = offG; offG += (int64_t)s.nG * s.ldG;
         s.offU = d.u_off[k];
+        s.offUp = offUp; offUp += s.ldG;
         s.offV = offV; offV += s.nk;
         s.co_off = d.co_off[k];
         s.n_co = d.co_off[k + 1] - d.co_off[k];
@@ -188,6 +189,7 @@ void build_maps(nlfeti_problem *p) {
     }
     p->poolA = offA; p->poolAD = offAD; p->poolM = offM; p->poolG = offG;
     p->sum_nk = offV;
+    p->n_up = offUp;
     // node maps
     std::vector<int32_t> nodemap((size_t)K * m.n_nodes, -1);
     std::vector<int32_t> vdofs(offV);

@@ -116,6 +116,8 @@ struct SubdomainDesc {      // per subdomain, device resident (POD)
     int32_t ldM;            // nk rounded up to 8
     int32_t ldG;            // nG rounded up to 8
     int32_t pad;
+    int64_t offUp;          // start of Gamma_k in the padded U layout (sum of ldG); the apply input
+                            // for R right-hand sides sits at offUp*R as R columns of ldG entries
 };
 
 constexpr int kApplyRows = 32;          // rows of an interface-apply work item
@@ -135,7 +137,7 @@ struct nlfeti_problem {
     nlfeti_kernel kern;
     nlf::Decomp dec;
     int K = 0, nc = 1;
-    int64_t n_lambda = 0, n_u = 0, sum_nk = 0, n_dofs_total = 0;
+    int64_t n_lambda = 0, n_u = 0, sum_nk = 0, n_dofs_total = 0, n_up = 0;
     int n_co = 0, n_floating = 0, max_ldG = 0;
     std::vector<SubdomainDesc> sd;      // host copy
     nlf::DevMem d_sd;

@@ -125,130 +125,10 @@ __global__ void k_gather_bd(const int64_t *ptr, const int64_t *col, const double
     }
 }
 
-// ------------------------------------------------------------------ dense symmetric apply (hot kernel)
-// y_k = M_k x_k for the work items (subdomain k, first row of a 32-row block): M_k is n x n
-// with leading dimension ld (multiple of 8, zero padded), stored in T.  Each warp owns 4
-// rows; each lane streams 4 (FP32) or 2 (FP64) consecutive columns of all 4 rows per step
-// with 16-byte streaming loads (two steps unrolled: 8 loads in flight per lane).  x_k is
-// staged in shared memory in chunks of SYMV_CW columns ([c][column], row stride padded by 4
-// to avoid bank conflicts), so a CTA needs 16 KB (FP32) and up to 8 CTAs share an SM.
-// Products accumulate in T per lane; the lane sum is a shuffle tree in T.
-template <typename T> struct Vec;
-template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
-template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
+#include "rows.cuh"
 
-static_assert(kApplyRows == 32, "the apply kernel owns 32 rows per CTA (8 warps x 4)");
-constexpr int SYMV_CW = 512;      // staged columns per chunk
-
-// Modes of the row-product kernel (same streaming structure, different rows/columns/vectors):
-//   ROWS_APPLY:   y_U = M x_U with M = S_k^+ or S_k (rows and columns Gamma_k, x cast to T);
-//   ROWS_FORCING: f_U = f_G - (A_GO A_OO^-1) f_O, rows Gamma / columns Omega of the swept
-//                 matrix (eq. subForcing);
-//   ROWS_BACKSUB: u_O = -(M_OO f_O + M_OG u_G) = A_OO^-1 (f_O - A_OG u_G), rows Omega / all
-//                 columns of the swept matrix (eq. backwardSubstitution).
-enum { ROWS_APPLY = 0, ROWS_FORCING = 1, ROWS_BACKSUB = 2 };
-
-template <typename T, int RC, int MODE>
-__global__ void __launch_bounds__(256, 3) k_rows(const T *base, int use_sp, const SubdomainDesc *sd, const int32_t *items,
-                                                 const T *x, const double *xa, const double *xb, double *y, int R) {
-    using V = typename Vec<T>::type;
-    constexpr int W = Vec<T>::W;
-    constexpr int XS = SYMV_CW + 4;                 // padded row of the staged x
-    __shared__ __align__(16) T xs[RC * XS];
-    const int k = items[2 * blockIdx.x], row0 = items[2 * blockIdx.x + 1];
-    const SubdomainDesc d = sd[k];
-    const int n = MODE == ROWS_BACKSUB ? d.nO : d.nG;                       // rows
-    const int ncols = MODE == ROWS_APPLY ? d.nG : (MODE == ROWS_FORCING ? d.nO : d.nk);
-    const int ld = MODE == ROWS_APPLY ? d.ldG : d.ldM;
-    const int ncp = min(ld, (ncols + 7) / 8 * 8);                           // padded columns
-    const int rbase = MODE == ROWS_FORCING ? d.nO : 0;                      // first matrix row
-    const T *M = base + (MODE == ROWS_APPLY ? (use_sp ? d.offSp : d.offS) : d.offM);
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int ib = row0 + warp * 4;
-    const T *Mr[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) Mr[r] = M + (int64_t)(rbase + min(ib + r, n - 1)) * ld;
-    for (int c0 = 0; c0 < R; c0 += RC) {
-        const int rc = min(RC, R - c0);
-        T acc[4][RC];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int c = 0; c < RC; ++c) acc[r][c] = T(0);
-        for (int l0 = 0; l0 < ncp; l0 += SYMV_CW) {
-            const int cw = min(SYMV_CW, ncp - l0);
-            __syncthreads();
-            for (int t = threadIdx.x; t < RC * cw; t += blockDim.x) {
-                const int l = t / RC, c = t % RC, gl = l0 + l;
-                T v = T(0);
-                if (c < rc && gl < ncols) {
-                    if (MODE == ROWS_APPLY) v = x[(d.offU + gl) * R + c0 + c];
-                    else if (MODE == ROWS_FORCING || gl < d.nO) v = (T)xa[(d.offV + gl) * R + c0 + c];
-                    else v = (T)xb[(d.offU + gl - d.nO) * R + c0 + c];
-                }
-                xs[c * XS + l] = v;
-            }
-            __syncthreads();
-            if (ib < n) {
-                int l = lane * W;
-                for (; l + 32 * W < cw; l += 64 * W) {
-                    V mv[2][4];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u)
-#pragma unroll
-                        for (int r = 0; r < 4; ++r)
-                            mv[u][r] = __ldcs(reinterpret_cast<const V *>(Mr[r] + l0 + l + u * 32 * W));
-#pragma unroll
-                    for (int u = 0; u < 2; ++u)
-#pragma unroll
-                        for (int c = 0; c < RC; ++c) {
-                            V xv = *reinterpret_cast<const V *>(xs + c * XS + l + u * 32 * W);
-                            const T *xp = reinterpret_cast<const T *>(&xv);
-#pragma unroll
-                            for (int r = 0; r < 4; ++r) {
-                                const T *mp = reinterpret_cast<const T *>(&mv[u][r]);
-#pragma unroll
-                                for (int w = 0; w < W; ++w) acc[r][c] += mp[w] * xp[w];
-                            }
-                        }
-                }
-                for (; l < cw; l += 32 * W) {
-                    V mv[4];
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) mv[r] = __ldcs(reinterpret_cast<const V *>(Mr[r] + l0 + l));
-#pragma unroll
-                    for (int c = 0; c < RC; ++c) {
-                        V xv = *reinterpret_cast<const V *>(xs + c * XS + l);
-                        const T *xp = reinterpret_cast<const T *>(&xv);
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            const T *mp = reinterpret_cast<const T *>(&mv[r]);
-#pragma unroll
-                            for (int w = 0; w < W; ++w) acc[r][c] += mp[w] * xp[w];
-                        }
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int c = 0; c < RC; ++c) {
-                T v = acc[r][c];
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0 && c < rc && ib + r < n) {
-                    const int i = ib + r;
-                    if (MODE == ROWS_APPLY) y[(d.offU + i) * R + c0 + c] = (double)v;
-                    else if (MODE == ROWS_FORCING)
-                        y[(d.offU + i) * R + c0 + c] = xa[(d.offV + d.nO + i) * R + c0 + c] - (double)v;
-                    else y[(d.offV + i) * R + c0 + c] = -(double)v;
-                }
-            }
-    }
-}
-
-// ------------------------------------------------------------------ row kernels on subdomain matrices
-// residual of the torn system (FP64 assembled A^k): r = f - A u - [0; B_k^T lambda]
+// r = f~ - A^k u - [0; B_k^T lambda] per subdomain (residual of the torn system, eq. discreteKKT);
+// one warp per row, FP64 throughout (refinement residual of the mixed path)
 __global__ void k_residual(const double *A, const SubdomainDesc *sd, int kbase, const double *f, const double *u,
                            const int64_t *bt_ptr, const int64_t *bt_row, const double *lam, double *r, int R) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -762,7 +642,8 @@ struct Runner {
     template <typename T> void applyF(const OpPool<T> &pool, const double *v, double *out, const double *cvec = nullptr) {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         T *x = ws.xU.as<T>();
-        k_gather_bt<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), v, x, nu, R);
+        k_gather_apply<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(),
+                                                            nullptr, v, x, sd, p->d_u2sub.as<int32_t>(), nu, R);
         note_launch();
         symv<T>(pool, 1, x, ws.yU.as<double>());
         k_gather_b<<<grid_for(nl * R), 256, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), ws.yU.as<double>(),
@@ -773,9 +654,10 @@ struct Runner {
     template <typename T> void applyMinv(const OpPool<T> &pool, const double *v, double *out) {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         T *x = ws.xU.as<T>();
-        k_gather_bdt<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_BDt_ptr.as<int64_t>(), p->d_BDt_row.as<int64_t>(),
-                                                          p->d_BDt_val.as<double>(), v, x, nu, R);
-                                                          note_launch();
+        k_gather_apply<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_BDt_ptr.as<int64_t>(), p->d_BDt_row.as<int64_t>(),
+                                                            p->d_BDt_val.as<double>(), v, x, sd,
+                                                            p->d_u2sub.as<int32_t>(), nu, R);
+        note_launch();
         symv<T>(pool, 0, x, ws.yU.as<double>());
         k_gather_bd<<<grid_for(nl * R), 256, 0, st>>>(p->d_BD_ptr.as<int64_t>(), p->d_BD_col.as<int64_t>(),
                                                       p->d_BD_val.as<double>(), ws.yU.as<double>(), out, nl, R);
@@ -812,7 +694,7 @@ struct Runner {
         double *lam = ws.dlam.as<double>();
         T *x = ws.xU.as<T>();
         if (nl > 0) {
-            k_cast<T><<<grid_for(nu * R), 256, 0, st>>>(ws.fU.as<double>(), x, nu * R);
+            k_to_apply<T><<<grid_for(nu * R), 256, 0, st>>>(ws.fU.as<double>(), x, sd, p->d_u2sub.as<int32_t>(), nu, R);
             note_launch();
             symv<T>(pool, 1, x, ws.yU.as<double>());
             k_gather_b<<<grid_for(nl * R), 256, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), ws.yU.as<double>(),
@@ -874,7 +756,7 @@ struct Runner {
                                                                   note_launch();
             k_sub<<<grid_for(nu * R), 256, 0, st>>>(ws.fU.as<double>(), ws.uU.as<double>(), ws.uU.as<double>(), nu * R);
             note_launch();
-            k_cast<T><<<grid_for(nu * R), 256, 0, st>>>(ws.uU.as<double>(), x, nu * R);
+            k_to_apply<T><<<grid_for(nu * R), 256, 0, st>>>(ws.uU.as<double>(), x, sd, p->d_u2sub.as<int32_t>(), nu, R);
             note_launch();
             symv<T>(pool, 1, x, ws.uU.as<double>());
             if (p->n_co > 0) {
@@ -894,7 +776,7 @@ struct Runner {
             for (int c = 0; c < R; ++c)
                 if (!(rr[c] <= tol)) info.converged = false;
         } else if (nu > 0) {
-            k_cast<T><<<grid_for(nu * R), 256, 0, st>>>(ws.fU.as<double>(), x, nu * R);
+            k_to_apply<T><<<grid_for(nu * R), 256, 0, st>>>(ws.fU.as<double>(), x, sd, p->d_u2sub.as<int32_t>(), nu, R);
             note_launch();
             symv<T>(pool, 1, x, ws.uU.as<double>());
         }
@@ -928,7 +810,9 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     };
     auto A = [&](DevMem &m, int64_t n) { alloc(m, sizeof(double) * n * R); };
     A(lam, nl); A(r, nl); A(w, nl); A(z, nl); A(y, nl); A(pv, nl); A(q, nl); A(d, nl); A(cvec, nl); A(dlam, nl);
-    A(fU, nu); A(yU, nu); A(uU, nu); A(xU, nu);
+    A(fU, nu); A(yU, nu); A(uU, nu);
+    A(xU, std::max<int64_t>(1, p->n_up));   // apply layout (padding zeroed by the gathers)
+    NLF_CUDA(cudaMemsetAsync(xU.p, 0, xU.bytes, async_stream ? async_stream : c->stream));
     A(ftil, nv); A(res, nv); A(u, nv); A(du, nv);
     A(F, nd);
     A(gco, nco * PSPLIT); A(alpha, nco);
@@ -1044,7 +928,7 @@ void apply_operator(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int op, int
             case 3:
             case 4: {
                 T *x = ws.xU.as<T>();
-                k_cast<T><<<grid_for(nu * R), 256, 0, st>>>(in, x, nu * R);
+                k_to_apply<T><<<grid_for(nu * R), 256, 0, st>>>(in, x, run.sd, p->d_u2sub.as<int32_t>(), nu, R);
                 run.symv<T>(pool, op == 3 ? 1 : 0, x, out);
                 break;
             }
