@@ -265,6 +265,11 @@ void build_maps(nlfeti_problem *p) {
         p->item_off_o[k + 1] = (int)(items_o.size() / 2);
     }
     upload(c, p->d_items_o, items_o);
+    std::vector<int32_t> items_a;
+    for (int k = 0; k < K; ++k)
+        for (int r0 = 0; r0 < p->sd[k].nk; r0 += kApplyRows) { items_a.push_back(k); items_a.push_back(r0); }
+    p->n_items_a = (int)(items_a.size() / 2);
+    upload(c, p->d_items_a, items_a);
     std::vector<uint64_t> mask = d.elem_mask;
     upload(c, p->d_sd, p->sd);
     upload(c, p->d_xy, m.xy);

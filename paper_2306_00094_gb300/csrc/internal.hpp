@@ -125,6 +125,8 @@ constexpr int kApplyRows = 32;          // rows of an interface-apply work item
 template <typename T> struct OpPool {   // operators of one precision
     nlf::DevMem M, S, Sp;                // swept matrices, Schur complements, pseudo-inverses
     nlf::DevMem scratch;                 // panel scratch of the sweeps
+    nlf::DevMem Ahi, Alo;                // FP32 pool only: A^k = Ahi + Alo (FP32 pairs, swept-matrix layout),
+                                         // for the double-single refinement residual
     bool ready = false;
 };
 
@@ -169,6 +171,8 @@ struct nlfeti_problem {
     std::vector<int> item_off;           // K+1
     nlf::DevMem d_items_o;               // work items over Omega rows (back substitution)
     std::vector<int> item_off_o;         // K+1
+    nlf::DevMem d_items_a;               // work items over all rows of A^k (refinement residual)
+    int n_items_a = 0;
     nlf::DevMem d_flag;                  // device status words
     OpPool<double> op64;
     OpPool<float> op32;

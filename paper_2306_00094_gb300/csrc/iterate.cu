@@ -19,6 +19,7 @@
 // correction is below refine_tol.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "solve.hpp"
 
@@ -127,41 +128,6 @@ __global__ void k_gather_bd(const int64_t *ptr, const int64_t *col, const double
 
 #include "rows.cuh"
 
-// r = f~ - A^k u - [0; B_k^T lambda] per subdomain (residual of the torn system, eq. discreteKKT);
-// one warp per row, FP64 throughout (refinement residual of the mixed path)
-__global__ void k_residual(const double *A, const SubdomainDesc *sd, int kbase, const double *f, const double *u,
-                           const int64_t *bt_ptr, const int64_t *bt_row, const double *lam, double *r, int R) {
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const SubdomainDesc d = sd[kbase + blockIdx.y];
-    for (int i = blockIdx.x * 8 + warp; i < d.nk; i += gridDim.x * 8) {
-        const double *Ai = A + d.offA + (int64_t)i * d.nk;
-        for (int c0 = 0; c0 < R; c0 += 8) {
-            const int rc = min(8, R - c0);
-            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int l = lane; l < d.nk; l += 32) {
-                double m = Ai[l];
-                const double *ul = u + (d.offV + l) * R + c0;
-                for (int c = 0; c < rc; ++c) acc[c] += m * ul[c];
-            }
-#pragma unroll
-            for (int c = 0; c < 8; ++c) acc[c] = warp_sum(acc[c]);
-            if (lane < rc) {
-                const int c = c0 + lane;
-                double v = f[(d.offV + i) * R + c] - acc[lane];
-                if (i >= d.nO && lam) {
-                    int64_t ui = d.offU + (i - d.nO);
-                    for (int64_t q = bt_ptr[ui]; q < bt_ptr[ui + 1]; ++q) {
-                        int64_t rr = bt_row[q];
-                        v -= rr > 0 ? lam[(rr - 1) * R + c] : -lam[(-rr - 1) * R + c];
-                    }
-                }
-                r[(d.offV + i) * R + c] = v;
-            }
-        }
-    }
-}
-
-// subdomain vector entries of Gamma_k from a U-space vector: v[u2v[i]] = uU[i]
 __global__ void k_scatter_u(const int64_t *u2v, const double *uU, double *v, int64_t nu, int R) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = t / R;
@@ -285,60 +251,52 @@ struct PcgScalars {
 
 enum { FIN_NPD = 0, FIN_CHECK = 1, FIN_BETA = 2, FIN_ETA = 3 };
 
-// Dot products per column with the scalar update fused in: every block writes its partial
-// sums; the last block to arrive adds all partials in a fixed order (deterministic) and
-// updates the PCG scalars:
+// Reductions over Lambda use one thread per row and a grid sized to the vector (independent
+// of the number of right-hand sides), so every column is summed in the same order whatever
+// the batch it is part of: per thread over its rows, a warp tree, the warps in order, and the
+// blocks in order by the last block to arrive.
+inline unsigned red_blocks(int64_t n) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(RED_BLOCKS, (n + RED_THREADS - 1) / RED_THREADS));
+}
+
+// per-block sums of 8 columns (c0 .. c0 + rc) into partial[block][c]
+__device__ __forceinline__ void block_partial(double (&acc)[8], double *partial, int64_t block, int c0, int rc, int R) {
+    __shared__ double red[RED_THREADS / 32][8];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const double t = warp_reduce_scatter<double, 8>(acc, lane);   // lanes 4j hold column j
+    __syncthreads();
+    if (lane % 4 == 0) red[warp][lane / 4] = t;
+    __syncthreads();
+    if (threadIdx.x < rc) {
+        double x = 0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) x += red[w][threadIdx.x];
+        partial[block * R + c0 + threadIdx.x] = x;
+    }
+}
+
+// true in the last block of the grid to arrive (after every block's partials are visible)
+__device__ __forceinline__ bool arrive_last(unsigned *counter) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// last block: column totals over the nb block partials (warp per column, fixed order) and the
+// PCG scalar update:
 //   NPD:   ||P d|| and the initial state;      CHECK: ||w|| and the active mask;
 //   BETA:  (y,w) and beta = (y,w)/(y,w)_old;    ETA:   (p,q) and eta = (y,w)/(p,q).
 template <int MODE>
-__global__ void __launch_bounds__(RED_THREADS) k_dot_final(const double *a, const double *b, int64_t n, int R,
-                                                            double *partial, PcgScalars s, double tol, int max_it) {
-    __shared__ double red[RED_THREADS / 32][8];
-    __shared__ double tot[RED_THREADS];
-    __shared__ bool last;
-    __shared__ int cnt;
+__device__ void finish_scalars(const double *partial, int nb, int R, PcgScalars s, double tol, int max_it) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int c0 = 0; c0 < R; c0 += 8) {
-        const int rc = min(8, R - c0);
-        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-            const double *ai = a + i * R + c0;
-            const double *bi = b + i * R + c0;
-            for (int c = 0; c < rc; ++c) acc[c] += ai[c] * bi[c];
-        }
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = warp_sum(acc[c]);
-        __syncthreads();
-        if (lane == 0)
-            for (int c = 0; c < 8; ++c) red[warp][c] = acc[c];
-        __syncthreads();
-        if (threadIdx.x < rc) {
-            double t = 0;
-            for (int w = 0; w < RED_THREADS / 32; ++w) t += red[w][threadIdx.x];
-            partial[(int64_t)blockIdx.x * R + c0 + threadIdx.x] = t;
-        }
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned prev = atomicAdd(s.counter, 1u);
-        last = (prev == gridDim.x - 1);
-        cnt = 0;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    for (int c = 0; c < R; ++c) {
-        double t = 0;
-        for (int bl = threadIdx.x; bl < (int)gridDim.x; bl += blockDim.x) t += __ldcg(partial + (int64_t)bl * R + c);
-        tot[threadIdx.x] = t;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) tot[threadIdx.x] += tot[threadIdx.x + o];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            const double v = tot[0];
+    for (int c = warp; c < R; c += RED_THREADS / 32) {
+        double v = 0;
+        for (int bl = lane; bl < nb; bl += 32) v += __ldcg(partial + (int64_t)bl * R + c);
+        v = warp_sum(v);
+        if (lane == 0) {
             if (MODE == FIN_NPD) {
                 s.nPd[c] = sqrt(v);
                 s.active[c] = 1;
@@ -349,7 +307,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot_final(const double *a, cons
                 const double nw = sqrt(v), ref = s.nPd[c];
                 if (s.active[c]) s.relres[c] = ref > 0 ? nw / ref : 0.0;
                 if (s.active[c] && (nw <= tol * ref || s.iters[c] >= max_it)) s.active[c] = 0;
-                cnt += s.active[c] ? 1 : 0;
             } else if (MODE == FIN_BETA) {
                 s.yw[c] = v;
                 s.beta[c] = (s.iters[c] == 0 || s.yw_old[c] == 0.0) ? 0.0 : v / s.yw_old[c];
@@ -359,79 +316,157 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot_final(const double *a, cons
                 if (act) { s.yw_old[c] = s.yw[c]; s.iters[c] += 1; }
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         if (MODE == FIN_NPD) *s.n_active = R;
-        if (MODE == FIN_CHECK) *s.n_active = cnt;
+        if (MODE == FIN_CHECK) {
+            int cnt = 0;
+            for (int c = 0; c < R; ++c) cnt += s.active[c] != 0;
+            *s.n_active = cnt;
+        }
         *s.counter = 0u;
     }
 }
 
-// g_part = Z^T B^T v over one slice of a floating subdomain's Gamma dofs (grid: K x PSPLIT);
-// v_is_u: v already lives in U
-constexpr int PSPLIT = 8;
-__global__ void k_proj_g_part(const SubdomainDesc *sd, const int64_t *bt_ptr, const int64_t *bt_row, const double *v,
-                              int v_is_u, const double *Z, double *gpart, int R) {
-    const SubdomainDesc d = sd[blockIdx.x];
-    if (d.n_co == 0) return;
-    __shared__ double red[8][24];
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int64_t chunk = (d.nG + PSPLIT - 1) / PSPLIT;
-    const int64_t l0 = blockIdx.y * chunk, l1 = min((int64_t)d.nG, l0 + chunk);
+// (a, b) per column with the scalar update of MODE
+template <int MODE>
+__global__ void __launch_bounds__(RED_THREADS) k_dot_final(const double *a, const double *b, int64_t n, int R,
+                                                            double *partial, PcgScalars s, double tol, int max_it) {
     for (int c0 = 0; c0 < R; c0 += 8) {
         const int rc = min(8, R - c0);
-        double acc[3][8];
-        for (int q = 0; q < 3; ++q)
-            for (int c = 0; c < 8; ++c) acc[q][c] = 0;
-        for (int64_t l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
-            const int64_t ui = d.offU + l;
-            for (int c = 0; c < rc; ++c) {
-                double bt;
-                if (v_is_u) bt = v[ui * R + c0 + c];
-                else {
-                    bt = 0;
-                    for (int64_t q = bt_ptr[ui]; q < bt_ptr[ui + 1]; ++q) {
-                        int64_t rr = bt_row[q];
-                        bt += rr > 0 ? v[(rr - 1) * R + c0 + c] : -v[(-rr - 1) * R + c0 + c];
-                    }
-                }
-                for (int q = 0; q < d.n_co; ++q) acc[q][c] += Z[ui * 3 + q] * bt;
-            }
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c < rc) acc[c] += a[i * R + c0 + c] * b[i * R + c0 + c];
         }
-        for (int q = 0; q < 3; ++q)
-            for (int c = 0; c < 8; ++c) acc[q][c] = warp_sum(acc[q][c]);
-        __syncthreads();
-        if (lane == 0)
-            for (int q = 0; q < 3; ++q)
-                for (int c = 0; c < 8; ++c) red[warp][q * 8 + c] = acc[q][c];
-        __syncthreads();
-        if (threadIdx.x < 24) {
-            int q = threadIdx.x / 8, c = threadIdx.x % 8;
-            double t = 0;
-            for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w][q * 8 + c];
-            if (q < d.n_co && c < rc)
-                gpart[((int64_t)(d.co_off + q) * PSPLIT + blockIdx.y) * R + c0 + c] = t;
-        }
+        block_partial(acc, partial, blockIdx.x, c0, rc, R);
     }
+    if (arrive_last(s.counter)) finish_scalars<MODE>(partial, gridDim.x, R, s, tol, max_it);
 }
 
-// alpha = (G^T G)^-1 g with g summed from the slices in a fixed order (one CTA)
-__global__ void k_coarse_parts(const double *GtGinv, int nco, const double *gpart, double *alpha, int R) {
-    extern __shared__ double gs[];
+// out = P v = v - G alpha (alpha from k_proj_g; NULL when there is no coarse space), with the
+// dot product of MODE: CHECK (out, out), BETA (out, other)
+template <int MODE>
+__global__ void __launch_bounds__(RED_THREADS) k_project_dot(const SubdomainDesc *sd, const int32_t *u2sub,
+                                                              const int64_t *Bp, const int64_t *Bm, const double *Z,
+                                                              const double *alpha, const double *v,
+                                                              const double *other, double *out, int64_t nl, int R,
+                                                              double *partial, PcgScalars s, double tol, int max_it) {
+    for (int c0 = 0; c0 < R; c0 += 8) {
+        const int rc = min(8, R - c0);
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t up = alpha ? Bp[i] : 0, um = alpha ? Bm[i] : 0;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c < rc) {
+                    const int64_t t = i * R + c0 + c;
+                    double x = v[t];
+                    if (alpha)
+                        x += -1.0 * (z_alpha(sd, u2sub, Z, alpha, up, c0 + c, R) -
+                                     z_alpha(sd, u2sub, Z, alpha, um, c0 + c, R));
+                    out[t] = x;
+                    acc[c] += x * (MODE == FIN_CHECK ? x : other[t]);
+                }
+        }
+        block_partial(acc, partial, blockIdx.x, c0, rc, R);
+    }
+    if (arrive_last(s.counter)) finish_scalars<MODE>(partial, gridDim.x, R, s, tol, max_it);
+}
+
+// q = B y (y on U) with (p, q) and the ETA update
+__global__ void __launch_bounds__(RED_THREADS) k_gather_b_eta(const int64_t *Bp, const int64_t *Bm, const double *y,
+                                                               const double *pv, double *q, int64_t nl, int R,
+                                                               double *partial, PcgScalars s) {
+    for (int c0 = 0; c0 < R; c0 += 8) {
+        const int rc = min(8, R - c0);
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t up = Bp[i], um = Bm[i];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c < rc) {
+                    const int64_t t = i * R + c0 + c;
+                    const double x = y[up * R + c0 + c] - y[um * R + c0 + c];
+                    q[t] = x;
+                    acc[c] += pv[t] * x;
+                }
+        }
+        block_partial(acc, partial, blockIdx.x, c0, rc, R);
+    }
+    if (arrive_last(s.counter)) finish_scalars<FIN_ETA>(partial, gridDim.x, R, s, 0.0, 0);
+}
+
+// alpha = (G^T G)^-1 G^T v with G^T v = Z^T B^T v (or Z^T v for v in U).  Grid K x PSPLIT:
+// block (k, j) sums slice j of floating subdomain k's Gamma dofs into gpart; the last block
+// to arrive adds the slices in order (gsum) and applies (G^T G)^-1.
+constexpr int PSPLIT = 8;
+__global__ void __launch_bounds__(256) k_proj_g(const SubdomainDesc *sd, const int64_t *bt_ptr, const int64_t *bt_row,
+                                                const double *v, int v_is_u, const double *Z, double *gpart,
+                                                double *gsum, const double *GtGinv, int nco, double *alpha, int R,
+                                                unsigned *counter) {
+    __shared__ double red[8][32];
+    const SubdomainDesc d = sd[blockIdx.x];
+    const int nq = d.n_co;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (nq > 0) {
+        const int64_t chunk = (d.nG + PSPLIT - 1) / PSPLIT;
+        const int64_t l0 = blockIdx.y * chunk, l1 = min((int64_t)d.nG, l0 + chunk);
+        for (int c0 = 0; c0 < R; c0 += 8) {
+            const int rc = min(8, R - c0);
+            double acc[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) acc[t] = 0;
+            for (int64_t l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
+                const int64_t ui = d.offU + l;
+                double z[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) z[q] = q < nq ? Z[ui * 3 + q] : 0.0;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    if (c >= rc) continue;
+                    double bt;
+                    if (v_is_u) bt = v[ui * R + c0 + c];
+                    else {
+                        bt = 0;
+                        for (int64_t q = bt_ptr[ui]; q < bt_ptr[ui + 1]; ++q) {
+                            const int64_t rr = bt_row[q];
+                            bt += rr > 0 ? v[(rr - 1) * R + c0 + c] : -v[(-rr - 1) * R + c0 + c];
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) acc[q * 8 + c] += z[q] * bt;
+                }
+            }
+            const double tot = warp_reduce_scatter<double, 32>(acc, lane);   // lane = q * 8 + c
+            __syncthreads();
+            red[warp][lane] = tot;
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                const int q = threadIdx.x / 8, c = threadIdx.x % 8;
+                double x = 0;
+                for (int w = 0; w < 8; ++w) x += red[w][threadIdx.x];
+                if (q < nq && c < rc) gpart[((int64_t)(d.co_off + q) * PSPLIT + blockIdx.y) * R + c0 + c] = x;
+            }
+        }
+    }
+    if (!arrive_last(counter)) return;
     for (int t = threadIdx.x; t < nco * R; t += blockDim.x) {
-        int i = t / R, c = t % R;
-        double s = 0;
-        for (int j = 0; j < PSPLIT; ++j) s += gpart[((int64_t)i * PSPLIT + j) * R + c];
-        gs[t] = s;
+        const int i = t / R, c = t % R;
+        double g = 0;
+        for (int j = 0; j < PSPLIT; ++j) g += __ldcg(gpart + ((int64_t)i * PSPLIT + j) * R + c);
+        gsum[t] = g;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < nco * R; t += blockDim.x) {
-        int i = t / R, c = t % R;
-        double s = 0;
-        for (int j = 0; j < nco; ++j) s += GtGinv[(int64_t)i * nco + j] * gs[j * R + c];
-        alpha[t] = s;
+        const int i = t / R, c = t % R;
+        double a = 0;
+        for (int j = 0; j < nco; ++j) a += GtGinv[(int64_t)i * nco + j] * gsum[(int64_t)j * R + c];
+        alpha[t] = a;
     }
+    if (threadIdx.x == 0) *counter = 0u;
 }
 
 // max |a| and max |b| per column into partials
@@ -487,6 +522,24 @@ __global__ void k_update_lr(const double *p, const double *q, const double *eta,
 
 // ====================================================================== host orchestration
 
+// ws.res = ftil - A^k u - [0; B^T lambda] on every subdomain (double-single, FP32 pool pairs)
+void residual_ds(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, const double *lam) {
+    if (p->n_items_a == 0) return;
+    const OpPool<float> &pool = p->op32;
+    auto go = [&](auto rc_tag) {
+        constexpr int RC = decltype(rc_tag)::value;
+        k_residual_ds<RC><<<p->n_items_a, 256, 0, st>>>(pool.Ahi.as<float>(), pool.Alo.as<float>(),
+                                                       p->d_sd.as<SubdomainDesc>(), p->d_items_a.as<int32_t>(),
+                                                       ws.ftil.as<double>(), ws.u.as<double>(),
+                                                       p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), lam,
+                                                       ws.res.as<double>(), R);
+    };
+    if (R >= 8) go(std::integral_constant<int, 8>{});
+    else if (R >= 4) go(std::integral_constant<int, 4>{});
+    else if (R >= 2) go(std::integral_constant<int, 2>{});
+    else go(std::integral_constant<int, 1>{});
+}
+
 struct Runner {
     nlfeti_problem *p;
     SolveWS &ws;
@@ -505,6 +558,9 @@ struct Runner {
         double bytes;
     };
     std::vector<Slot> graph_slots, eager_slots;
+    // inside PCG iterations: the interface applies and their gathers return at once when no
+    // right-hand side is active any more (every later update is masked by the active flags)
+    const int *gate = nullptr;
     int64_t apply_launches = 0;
     double apply_ms = 0, apply_bytes = 0;
 
@@ -520,7 +576,7 @@ struct Runner {
     }
 
     template <int MODE> void dot_final(const double *a, const double *b, int64_t n, double tol = 0, int max_it = 0) {
-        k_dot_final<MODE><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, n, R, ws.partial.as<double>(), S, tol, max_it);
+        k_dot_final<MODE><<<red_blocks(n), RED_THREADS, 0, st>>>(a, b, n, R, ws.partial.as<double>(), S, tol, max_it);
         note_launch();
     }
 
@@ -561,11 +617,10 @@ struct Runner {
 
     // alpha = (G^T G)^-1 Z^T B^T v  (or (G^T G)^-1 Z^T v for v in U)
     void coarse_alpha(const double *v, int v_is_u) {
-        k_proj_g_part<<<dim3(p->K, PSPLIT), 256, 0, st>>>(sd, p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), v,
-                                                           v_is_u, p->d_Z.as<double>(), ws.gco.as<double>(), R);
-        note_launch();
-        k_coarse_parts<<<1, 256, sizeof(double) * p->n_co * R, st>>>(p->d_GtGinv.as<double>(), p->n_co,
-                                                                      ws.gco.as<double>(), ws.alpha.as<double>(), R);
+        k_proj_g<<<dim3(p->K, PSPLIT), 256, 0, st>>>(sd, p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), v, v_is_u,
+                                                      p->d_Z.as<double>(), ws.gco.as<double>(), ws.gsum.as<double>(),
+                                                      p->d_GtGinv.as<double>(), p->n_co, ws.alpha.as<double>(), R,
+                                                      S.counter);
         note_launch();
     }
 
@@ -580,12 +635,24 @@ struct Runner {
         k_apply_galpha<<<grid_for(nl * R), 256, 0, st>>>(sd, p->d_u2sub.as<int32_t>(), p->d_Bp.as<int64_t>(),
                                                          p->d_Bm.as<int64_t>(), p->d_Z.as<double>(),
                                                          ws.alpha.as<double>(), v, -1.0, out, nl, R);
-                                                         note_launch();
+        note_launch();
+    }
+
+    // out = P v with the PCG dot product of MODE fused in (CHECK: (out, out); BETA: (out, other))
+    template <int MODE> void project_dot(const double *v, const double *other, double *out, double tol = 0,
+                                         int max_it = 0) {
+        const int64_t nl = p->n_lambda;
+        if (p->n_co > 0) coarse_alpha(v, 0);
+        k_project_dot<MODE><<<red_blocks(nl), RED_THREADS, 0, st>>>(
+            sd, p->d_u2sub.as<int32_t>(), p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), p->d_Z.as<double>(),
+            p->n_co > 0 ? ws.alpha.as<double>() : nullptr, v, other, out, nl, R, ws.partial.as<double>(), S, tol, max_it);
+        note_launch();
     }
 
     template <typename T, int RC, int MODE> void rows_launch(const T *base, int use_sp, const int32_t *it, int nitems,
                                                             const T *x, const double *xa, const double *xb, double *y) {
-        k_rows<T, RC, MODE><<<nitems, 256, 0, st>>>(base, use_sp, sd, it, x, xa, xb, y, R);
+        k_rows<T, RC, MODE><<<nitems, 256, 0, st>>>(base, use_sp, sd, it, x, xa, xb, y, R,
+                                                    MODE == ROWS_APPLY ? gate : nullptr);
         note_launch();
     }
 
@@ -643,7 +710,7 @@ struct Runner {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         T *x = ws.xU.as<T>();
         k_gather_apply<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(),
-                                                            nullptr, v, x, sd, p->d_u2sub.as<int32_t>(), nu, R);
+                                                            nullptr, v, x, sd, p->d_u2sub.as<int32_t>(), nu, R, gate);
         note_launch();
         symv<T>(pool, 1, x, ws.yU.as<double>());
         k_gather_b<<<grid_for(nl * R), 256, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), ws.yU.as<double>(),
@@ -651,12 +718,26 @@ struct Runner {
                                                      note_launch();
     }
 
+    // q = F pv with (pv, q) and the ETA update fused into the final gather
+    template <typename T> void applyF_eta(const OpPool<T> &pool, const double *pv, double *q) {
+        const int64_t nl = p->n_lambda, nu = p->n_u;
+        T *x = ws.xU.as<T>();
+        k_gather_apply<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(),
+                                                            nullptr, pv, x, sd, p->d_u2sub.as<int32_t>(), nu, R, gate);
+        note_launch();
+        symv<T>(pool, 1, x, ws.yU.as<double>());
+        k_gather_b_eta<<<red_blocks(nl), RED_THREADS, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(),
+                                                               ws.yU.as<double>(), pv, q, nl, R,
+                                                               ws.partial.as<double>(), S);
+        note_launch();
+    }
+
     template <typename T> void applyMinv(const OpPool<T> &pool, const double *v, double *out) {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         T *x = ws.xU.as<T>();
         k_gather_apply<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_BDt_ptr.as<int64_t>(), p->d_BDt_row.as<int64_t>(),
                                                             p->d_BDt_val.as<double>(), v, x, sd,
-                                                            p->d_u2sub.as<int32_t>(), nu, R);
+                                                            p->d_u2sub.as<int32_t>(), nu, R, gate);
         note_launch();
         symv<T>(pool, 0, x, ws.yU.as<double>());
         k_gather_bd<<<grid_for(nl * R), 256, 0, st>>>(p->d_BD_ptr.as<int64_t>(), p->d_BD_col.as<int64_t>(),
@@ -668,15 +749,14 @@ struct Runner {
         const int64_t nl = p->n_lambda;
         double *r = ws.r.as<double>(), *w = ws.w.as<double>(), *z = ws.z.as<double>(), *y = ws.y.as<double>(),
                *pv = ws.pv.as<double>(), *q = ws.q.as<double>(), *lam = ws.dlam.as<double>();
-        project(r, w);
-        dot_final<FIN_CHECK>(w, w, nl, tol, max_it);
-        applyMinv<T>(pool, w, z);
-        project(z, y);
-        dot_final<FIN_BETA>(y, w, nl);
+        project_dot<FIN_CHECK>(r, nullptr, w, tol, max_it);     // w = P r, ||w||, stop test
+        gate = S.n_active;
+        applyMinv<T>(pool, w, z);                                // z = M^-1 w
+        project_dot<FIN_BETA>(z, w, y);                          // y = P z, (y, w), beta
         k_update_p<<<grid_for(nl * R), 256, 0, st>>>(y, S.beta, S.active, pv, nl, R);
         note_launch();
-        applyF<T>(pool, pv, q);
-        dot_final<FIN_ETA>(pv, q, nl);
+        applyF_eta<T>(pool, pv, q);                              // q = F p, (p, q), eta
+        gate = nullptr;
         k_update_lr<<<grid_for(nl * R), 256, 0, st>>>(pv, q, S.eta, lam, r, nl, R);
         note_launch();
     }
@@ -815,7 +895,7 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     NLF_CUDA(cudaMemsetAsync(xU.p, 0, xU.bytes, async_stream ? async_stream : c->stream));
     A(ftil, nv); A(res, nv); A(u, nv); A(du, nv);
     A(F, nd);
-    A(gco, nco * PSPLIT); A(alpha, nco);
+    A(gco, nco * PSPLIT); A(gsum, nco); A(alpha, nco);
     alloc(partial, sizeof(double) * RED_BLOCKS * R);
     alloc(partial2, sizeof(double) * RED_BLOCKS * R);
     alloc(scal, sizeof(double) * R * 7 + sizeof(int) * (2 * R + 8));
@@ -873,10 +953,7 @@ void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rh
             if (sw == 0) {
                 NLF_CUDA(cudaMemcpyAsync(ws.res.p, ws.ftil.p, sizeof(double) * nv * R, cudaMemcpyDeviceToDevice, st));
             } else {
-                k_residual<<<dim3(64, p->K), 256, 0, st>>>(p->d_A.as<double>(), p->d_sd.as<SubdomainDesc>(), 0,
-                                                          ws.ftil.as<double>(), ws.u.as<double>(), p->d_Bt_ptr.as<int64_t>(),
-                                                          p->d_Bt_row.as<int64_t>(), nl > 0 ? ws.lam.as<double>() : nullptr,
-                                                          ws.res.as<double>(), R);
+                residual_ds(p, ws, st, R, nl > 0 ? ws.lam.as<double>() : nullptr);
                 if (nl > 0)
                     k_constraint_residual<<<grid_for(nl * R), 256, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(),
                                                                             p->d_u2v.as<int64_t>(), ws.u.as<double>(),

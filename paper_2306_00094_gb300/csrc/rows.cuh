@@ -87,11 +87,13 @@ __device__ __forceinline__ T warp_reduce_scatter(T (&v)[V], int lane) {
 
 template <typename T, int RC, int MODE>
 __global__ void __launch_bounds__(256, 2) k_rows(const T *base, int use_sp, const SubdomainDesc *sd, const int32_t *items,
-                                                 const T *x, const double *xa, const double *xb, double *y, int R) {
+                                                 const T *x, const double *xa, const double *xb, double *y, int R,
+                                                 const int *gate) {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
     constexpr int XS = ROWS_CW + 4;
     __shared__ __align__(16) T xs[MODE == ROWS_APPLY ? 4 : RC * XS];
+    if (gate && *gate == 0) return;
     const int k = items[2 * blockIdx.x], row0 = items[2 * blockIdx.x + 1];
     const SubdomainDesc d = sd[k];
     const int n = MODE == ROWS_BACKSUB ? d.nO : d.nG;                       // rows
@@ -187,7 +189,8 @@ __global__ void __launch_bounds__(256, 2) k_rows(const T *base, int use_sp, cons
 // -(r+1)); consecutive threads take consecutive U dofs of one column (coalesced stores)
 template <typename T>
 __global__ void k_gather_apply(const int64_t *ptr, const int64_t *row, const double *val, const double *v, T *x,
-                               const SubdomainDesc *sd, const int32_t *u2sub, int64_t nu, int R) {
+                               const SubdomainDesc *sd, const int32_t *u2sub, int64_t nu, int R, const int *gate) {
+    if (gate && *gate == 0) return;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(t / nu);
         const int64_t u = t % nu;
@@ -211,5 +214,106 @@ __global__ void k_to_apply(const double *uU, T *x, const SubdomainDesc *sd, cons
         const int c = (int)(t / nu);
         const int64_t u = t % nu;
         apply_store<T>(x, sd, u2sub, u, c, R, (T)uU[u * R + c]);
+    }
+}
+
+// Refinement residual of the torn system (eq. discreteKKT) with FP64 accuracy on the FP32
+// pipes: r = f~ - A^k u - [0; B_k^T lambda] per subdomain.  A^k is read as FP32 pairs
+// (hi + lo), u is split into FP32 pairs (uh + ul) when staged in shared memory.  For each
+// product the lane keeps hi*uh rounded (p) and its exact rounding error (fma), adds p to a
+// running FP32 sum with TwoSum (exact error), and gathers the errors and the cross terms
+// hi*ul + lo*uh in a second FP32 sum; lo*ul (2^-48 relative) is dropped.  The two sums of
+// each lane are added in FP64 and reduced across the warp in FP64.  Relative to
+// sum_j |a_ij u_j| the result is accurate to a few 1e-13, the limit being the FP32 sum of
+// the small terms over a lane's columns.  Work item = (subdomain, 32 rows of A^k).
+template <int RC>
+__global__ void __launch_bounds__(256, 2) k_residual_ds(const float *Ahi, const float *Alo, const SubdomainDesc *sd,
+                                                        const int32_t *items, const double *f, const double *u,
+                                                        const int64_t *bt_ptr, const int64_t *bt_row,
+                                                        const double *lam, double *r, int R) {
+    constexpr int XS = ROWS_CW + 4;
+    __shared__ __align__(16) float xh[RC * XS];
+    __shared__ __align__(16) float xl[RC * XS];
+    const int k = items[2 * blockIdx.x], row0 = items[2 * blockIdx.x + 1];
+    const SubdomainDesc d = sd[k];
+    const int n = d.nk, ld = d.ldM;
+    const int ncp = min(ld, (n + 7) / 8 * 8);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int ib = row0 + warp * 4;
+    int64_t roff[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) roff[q] = d.offM + (int64_t)min(ib + q, n - 1) * ld;
+    for (int c0 = 0; c0 < R; c0 += RC) {
+        const int rc = min(RC, R - c0);
+        float sh[4][RC], sl[4][RC];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int c = 0; c < RC; ++c) { sh[q][c] = 0.f; sl[q][c] = 0.f; }
+        for (int l0 = 0; l0 < ncp; l0 += ROWS_CW) {
+            const int cw = min(ROWS_CW, ncp - l0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < RC * cw; t += blockDim.x) {
+                const int l = t / RC, c = t % RC, gl = l0 + l;
+                const double v = (c < rc && gl < n) ? u[(d.offV + gl) * R + c0 + c] : 0.0;
+                const float h = (float)v;
+                xh[c * XS + l] = h;
+                xl[c * XS + l] = (float)(v - (double)h);
+            }
+            __syncthreads();
+            if (ib < n) {
+                for (int l = lane * 4; l < cw; l += 128) {
+                    float4 mh[4], ml[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        mh[q] = __ldcs(reinterpret_cast<const float4 *>(Ahi + roff[q] + l0 + l));
+                        ml[q] = __ldcs(reinterpret_cast<const float4 *>(Alo + roff[q] + l0 + l));
+                    }
+#pragma unroll
+                    for (int c = 0; c < RC; ++c) {
+                        const float4 a4 = *reinterpret_cast<const float4 *>(xh + c * XS + l);
+                        const float4 b4 = *reinterpret_cast<const float4 *>(xl + c * XS + l);
+                        const float uh[4] = {a4.x, a4.y, a4.z, a4.w}, ul[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float ah[4] = {mh[q].x, mh[q].y, mh[q].z, mh[q].w};
+                            const float al[4] = {ml[q].x, ml[q].y, ml[q].z, ml[q].w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                // explicit round-to-nearest intrinsics: no contraction into fma
+                                const float p = __fmul_rn(ah[e], uh[e]);
+                                const float pe = fmaf(ah[e], uh[e], -p);          // hi*uh - p exactly
+                                const float s = __fadd_rn(sh[q][c], p);          // TwoSum(sh, p)
+                                const float bb = __fsub_rn(s, sh[q][c]);
+                                const float se = __fadd_rn(__fsub_rn(sh[q][c], __fsub_rn(s, bb)), __fsub_rn(p, bb));
+                                sh[q][c] = s;
+                                sl[q][c] = __fadd_rn(sl[q][c], __fadd_rn(se, fmaf(ah[e], ul[e], fmaf(al[e], uh[e], pe))));
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        constexpr int V = 4 * RC;
+        double v[V];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int c = 0; c < RC; ++c) v[q * RC + c] = (double)sh[q][c] + (double)sl[q][c];
+        const double tot = warp_reduce_scatter<double, V>(v, lane);
+        constexpr int G = 32 / V;
+        const int idx = lane / G, q = idx / RC, c = idx % RC, i = ib + q;
+        if (lane % G == 0 && c < rc && i < n) {
+            const int cc = c0 + c;
+            double res = f[(d.offV + i) * R + cc] - tot;
+            if (i >= d.nO && lam) {
+                const int64_t ui = d.offU + (i - d.nO);
+                for (int64_t t = bt_ptr[ui]; t < bt_ptr[ui + 1]; ++t) {
+                    const int64_t rr = bt_row[t];
+                    res -= rr > 0 ? lam[(rr - 1) * R + cc] : -lam[(-rr - 1) * R + cc];
+                }
+            }
+            r[(d.offV + i) * R + cc] = res;
+        }
     }
 }

@@ -12,7 +12,7 @@ struct SolveWS {
     DevMem fU, yU, uU, xU;                              // U space
     DevMem ftil, res, u, du;                            // concatenated subdomain vectors
     DevMem F;                                           // global load vector per dof
-    DevMem gco, alpha;                                  // coarse space
+    DevMem gco, gsum, alpha;                            // coarse space
     DevMem partial, partial2, scal;                     // reductions and PCG scalars
     DevMem in_rhs, in_g, out_u;                         // staging for host-array solves
     std::vector<int> host_flag;

@@ -17,6 +17,7 @@
 // update all tiles (64x64 CTA tiles, 4x4 register blocking).  A non-positive pivot
 // sets the device status word (NLFETI_E_NOT_SPD) instead of trapping.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 
 #include "internal.hpp"
@@ -182,6 +183,20 @@ template <typename T> __global__ void k_load_matrix(const double *A, T *Mpool, c
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)d.nk * ld; t += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = t / ld, l = t % ld;
         Mpool[d.offM + t] = l < d.nk ? (T)A[d.offA + i * d.nk + l] : T(0);
+    }
+}
+
+// A^k (FP64) -> hi + lo FP32 pairs in the swept-matrix layout (ld_M, zero padding):
+// hi = fl32(a), lo = fl32(a - hi), so hi + lo equals a to about 2^-48 relative
+__global__ void k_split_ds(const double *A, float *hi, float *lo, const SubdomainDesc *sd) {
+    const SubdomainDesc d = sd[blockIdx.y];
+    const int64_t ld = d.ldM;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)d.nk * ld; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / ld, l = t % ld;
+        const double a = l < d.nk ? A[d.offA + i * d.nk + l] : 0.0;
+        const float h = (float)a;
+        hi[d.offM + t] = h;
+        lo[d.offM + t] = (float)(a - (double)h);
     }
 }
 
@@ -406,6 +421,12 @@ template <typename T> void factor_ops(nlfeti_problem *p, OpPool<T> &pool) {
     NLF_CUDA(cudaMemsetAsync(pool.Sp.p, 0, pool.Sp.bytes, c->stream));
     k_load_matrix<T><<<dim3(256, K), 256, 0, c->stream>>>(p->d_A.as<double>(), pool.M.template as<T>(),
                                                           p->d_sd.as<SubdomainDesc>());
+    if constexpr (std::is_same<T, float>::value) {
+        pool.Ahi.alloc(c, sizeof(float) * std::max<int64_t>(poolM, 1));
+        pool.Alo.alloc(c, sizeof(float) * std::max<int64_t>(poolM, 1));
+        k_split_ds<<<dim3(256, K), 256, 0, c->stream>>>(p->d_A.as<double>(), pool.Ahi.template as<float>(),
+                                                        pool.Alo.template as<float>(), p->d_sd.as<SubdomainDesc>());
+    }
     NLF_CUDA(cudaGetLastError());
     std::vector<int64_t> moff(K), soff(K);
     std::vector<int32_t> mdim(K), mld(K), pend(K), gdim(K), gld(K), gend(K);
