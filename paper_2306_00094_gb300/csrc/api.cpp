@@ -160,7 +160,7 @@ void build_maps(nlfeti_problem *p) {
     p->n_u = d.u_off[K];
     p->n_co = d.co_off[K];
     p->sd.assign(K, SubdomainDesc{});
-    int64_t offA = 0, offAD = 0, offM = 0, offG = 0, offV = 0, offUp = 0;
+    int64_t offA = 0, offAD = 0, offM = 0, offG = 0, offV = 0, offUp = 0, offVp = 0;
     p->n_floating = 0;
     p->max_ldG = 8;
     for (int k = 0; k < K; ++k) {
@@ -178,6 +178,7 @@ void build_maps(nlfeti_problem *p) {
         s.offS = offG; s.offSp = offG; offG += (int64_t)s.nG * s.ldG;
         s.offU = d.u_off[k];
         s.offUp = offUp; offUp += s.ldG;
+        s.offVp = offVp; offVp += s.ldM;
         s.offV = offV; offV += s.nk;
         s.co_off = d.co_off[k];
         s.n_co = d.co_off[k + 1] - d.co_off[k];
@@ -190,6 +191,7 @@ void build_maps(nlfeti_problem *p) {
     p->poolA = offA; p->poolAD = offAD; p->poolM = offM; p->poolG = offG;
     p->sum_nk = offV;
     p->n_up = offUp;
+    p->n_vp = offVp;
     // node maps
     std::vector<int32_t> nodemap((size_t)K * m.n_nodes, -1);
     std::vector<int32_t> vdofs(offV);
@@ -267,7 +269,7 @@ void build_maps(nlfeti_problem *p) {
     upload(c, p->d_items_o, items_o);
     std::vector<int32_t> items_a;
     for (int k = 0; k < K; ++k)
-        for (int r0 = 0; r0 < p->sd[k].nk; r0 += kApplyRows) { items_a.push_back(k); items_a.push_back(r0); }
+        for (int r0 = 0; r0 < p->sd[k].nk; r0 += kResidualRows) { items_a.push_back(k); items_a.push_back(r0); }
     p->n_items_a = (int)(items_a.size() / 2);
     upload(c, p->d_items_a, items_a);
     std::vector<uint64_t> mask = d.elem_mask;

@@ -118,9 +118,12 @@ struct SubdomainDesc {      // per subdomain, device resident (POD)
     int32_t pad;
     int64_t offUp;          // start of Gamma_k in the padded U layout (sum of ldG); the apply input
                             // for R right-hand sides sits at offUp*R as R columns of ldG entries
+    int64_t offVp;          // start of the subdomain in the padded subdomain-vector layout (sum of
+                            // ldM): R columns of ldM entries at offVp*R (refinement residual input)
 };
 
 constexpr int kApplyRows = 32;          // rows of an interface-apply work item
+constexpr int kResidualRows = 16;       // rows of a refinement-residual work item
 
 template <typename T> struct OpPool {   // operators of one precision
     nlf::DevMem M, S, Sp;                // swept matrices, Schur complements, pseudo-inverses
@@ -139,7 +142,7 @@ struct nlfeti_problem {
     nlfeti_kernel kern;
     nlf::Decomp dec;
     int K = 0, nc = 1;
-    int64_t n_lambda = 0, n_u = 0, sum_nk = 0, n_dofs_total = 0, n_up = 0;
+    int64_t n_lambda = 0, n_u = 0, sum_nk = 0, n_dofs_total = 0, n_up = 0, n_vp = 0;
     int n_co = 0, n_floating = 0, max_ldG = 0;
     std::vector<SubdomainDesc> sd;      // host copy
     nlf::DevMem d_sd;
@@ -159,6 +162,11 @@ struct nlfeti_problem {
     nlf::DevMem d_Z;                     // (n_u x 3) FP64 kernel basis of floating subdomains
     nlf::DevMem d_Q;                     // (n_u x 3) FP64 orthonormal kernel basis
     nlf::DevMem d_GtGinv;                // n_co x n_co FP64
+    // rows of G = B Z: per Lambda row gw slots (coarse column, value), the first gw/2 for the
+    // +1 side (Z rows of B_plus), the rest for the -1 side; empty slots have column -1
+    int gw = 0;
+    nlf::DevMem d_Gcol, d_Gval;
+    nlf::DevMem d_float_ids;             // floating subdomains (int32)
     nlf::DevMem d_u2sub;                 // per U dof: subdomain (int32)
     nlf::DevMem d_u2v;                   // per U dof: position in the subdomain vectors (int64)
     nlf::DevMem d_vdofs;                 // per subdomain-vector entry: global dof (int32)
@@ -171,7 +179,7 @@ struct nlfeti_problem {
     std::vector<int> item_off;           // K+1
     nlf::DevMem d_items_o;               // work items over Omega rows (back substitution)
     std::vector<int> item_off_o;         // K+1
-    nlf::DevMem d_items_a;               // work items over all rows of A^k (refinement residual)
+    nlf::DevMem d_items_a;               // kResidualRows-row work items over all rows of A^k (residual)
     int n_items_a = 0;
     nlf::DevMem d_flag;                  // device status words
     OpPool<double> op64;

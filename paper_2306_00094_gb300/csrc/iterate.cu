@@ -220,15 +220,26 @@ __device__ __forceinline__ double z_alpha(const SubdomainDesc *sd, const int32_t
     return s;
 }
 
-// out = base + sign * B Z alpha (= G alpha) on Lambda
-__global__ void k_apply_galpha(const SubdomainDesc *sd, const int32_t *u2sub, const int64_t *Bp, const int64_t *Bm,
-                               const double *Z, const double *alpha, const double *base, double sign, double *out,
-                               int64_t nl, int R) {
+// (G alpha)_r for column c from the slots of row r of G = B Z
+__device__ __forceinline__ double g_alpha(const int32_t *gcol, const double *gval, int gw, const double *alpha,
+                                          int64_t r, int c, int R) {
+    const int h = gw / 2;
+    double sp = 0, sm = 0;
+    for (int e = 0; e < h; ++e) {
+        const int cp = gcol[r * gw + e], cm = gcol[r * gw + h + e];
+        if (cp >= 0) sp += gval[r * gw + e] * alpha[(int64_t)cp * R + c];
+        if (cm >= 0) sm += gval[r * gw + h + e] * alpha[(int64_t)cm * R + c];
+    }
+    return sp - sm;
+}
+
+// out = base + sign * G alpha on Lambda
+__global__ void k_apply_galpha(const int32_t *gcol, const double *gval, int gw, const double *alpha,
+                               const double *base, double sign, double *out, int64_t nl, int R) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl * R; t += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = t / R;
-        int c = (int)(t % R);
-        double ga = z_alpha(sd, u2sub, Z, alpha, Bp[r], c, R) - z_alpha(sd, u2sub, Z, alpha, Bm[r], c, R);
-        out[t] = (base ? base[t] : 0.0) + sign * ga;
+        const int64_t r = t / R;
+        const int c = (int)(t % R);
+        out[t] = (base ? base[t] : 0.0) + sign * g_alpha(gcol, gval, gw, alpha, r, c, R);
     }
 }
 
@@ -251,26 +262,26 @@ struct PcgScalars {
 
 enum { FIN_NPD = 0, FIN_CHECK = 1, FIN_BETA = 2, FIN_ETA = 3 };
 
-// Reductions over Lambda use one thread per row and a grid sized to the vector (independent
-// of the number of right-hand sides), so every column is summed in the same order whatever
-// the batch it is part of: per thread over its rows, a warp tree, the warps in order, and the
-// blocks in order by the last block to arrive.
-inline unsigned red_blocks(int64_t n) {
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(RED_BLOCKS, (n + RED_THREADS - 1) / RED_THREADS));
+// Reductions over Lambda: grid (row blocks, right-hand sides), one thread per row of one
+// column.  The row blocks depend on the vector length only, so every column is summed in the
+// same order whatever batch it is part of: per thread over its rows, a warp tree, the warps
+// in order, and the row blocks in order by the last block to arrive.
+inline dim3 red_grid(int64_t n, int R) {
+    return dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(RED_BLOCKS, (n + RED_THREADS - 1) / RED_THREADS)),
+                (unsigned)R);
 }
 
-// per-block sums of 8 columns (c0 .. c0 + rc) into partial[block][c]
-__device__ __forceinline__ void block_partial(double (&acc)[8], double *partial, int64_t block, int c0, int rc, int R) {
-    __shared__ double red[RED_THREADS / 32][8];
+// block sum of one value per thread into partial[blockIdx.x][blockIdx.y]
+__device__ __forceinline__ void block_partial(double acc, double *partial, int R) {
+    __shared__ double red[RED_THREADS / 32];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const double t = warp_reduce_scatter<double, 8>(acc, lane);   // lanes 4j hold column j
+    acc = warp_sum(acc);
+    if (lane == 0) red[warp] = acc;
     __syncthreads();
-    if (lane % 4 == 0) red[warp][lane / 4] = t;
-    __syncthreads();
-    if (threadIdx.x < rc) {
+    if (threadIdx.x == 0) {
         double x = 0;
-        for (int w = 0; w < RED_THREADS / 32; ++w) x += red[w][threadIdx.x];
-        partial[block * R + c0 + threadIdx.x] = x;
+        for (int w = 0; w < RED_THREADS / 32; ++w) x += red[w];
+        partial[(int64_t)blockIdx.x * R + blockIdx.y] = x;
     }
 }
 
@@ -279,14 +290,14 @@ __device__ __forceinline__ bool arrive_last(unsigned *counter) {
     __shared__ bool last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1;
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x * gridDim.y * gridDim.z - 1;
     __syncthreads();
     if (last) __threadfence();
     return last;
 }
 
-// last block: column totals over the nb block partials (warp per column, fixed order) and the
-// PCG scalar update:
+// last block: column totals over the nb row-block partials (warp per column, fixed order)
+// and the PCG scalar update:
 //   NPD:   ||P d|| and the initial state;      CHECK: ||w|| and the active mask;
 //   BETA:  (y,w) and beta = (y,w)/(y,w)_old;    ETA:   (p,q) and eta = (y,w)/(p,q).
 template <int MODE>
@@ -333,46 +344,31 @@ __device__ void finish_scalars(const double *partial, int nb, int R, PcgScalars 
 template <int MODE>
 __global__ void __launch_bounds__(RED_THREADS) k_dot_final(const double *a, const double *b, int64_t n, int R,
                                                             double *partial, PcgScalars s, double tol, int max_it) {
-    for (int c0 = 0; c0 < R; c0 += 8) {
-        const int rc = min(8, R - c0);
-        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-                if (c < rc) acc[c] += a[i * R + c0 + c] * b[i * R + c0 + c];
-        }
-        block_partial(acc, partial, blockIdx.x, c0, rc, R);
-    }
+    const int c = blockIdx.y;
+    double acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += a[i * R + c] * b[i * R + c];
+    block_partial(acc, partial, R);
     if (arrive_last(s.counter)) finish_scalars<MODE>(partial, gridDim.x, R, s, tol, max_it);
 }
 
 // out = P v = v - G alpha (alpha from k_proj_g; NULL when there is no coarse space), with the
 // dot product of MODE: CHECK (out, out), BETA (out, other)
 template <int MODE>
-__global__ void __launch_bounds__(RED_THREADS) k_project_dot(const SubdomainDesc *sd, const int32_t *u2sub,
-                                                              const int64_t *Bp, const int64_t *Bm, const double *Z,
+__global__ void __launch_bounds__(RED_THREADS) k_project_dot(const int32_t *gcol, const double *gval, int gw,
                                                               const double *alpha, const double *v,
                                                               const double *other, double *out, int64_t nl, int R,
                                                               double *partial, PcgScalars s, double tol, int max_it) {
-    for (int c0 = 0; c0 < R; c0 += 8) {
-        const int rc = min(8, R - c0);
-        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t up = alpha ? Bp[i] : 0, um = alpha ? Bm[i] : 0;
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-                if (c < rc) {
-                    const int64_t t = i * R + c0 + c;
-                    double x = v[t];
-                    if (alpha)
-                        x += -1.0 * (z_alpha(sd, u2sub, Z, alpha, up, c0 + c, R) -
-                                     z_alpha(sd, u2sub, Z, alpha, um, c0 + c, R));
-                    out[t] = x;
-                    acc[c] += x * (MODE == FIN_CHECK ? x : other[t]);
-                }
-        }
-        block_partial(acc, partial, blockIdx.x, c0, rc, R);
+    const int c = blockIdx.y;
+    double acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i * R + c;
+        double x = v[t];
+        if (alpha) x += -1.0 * g_alpha(gcol, gval, gw, alpha, i, c, R);
+        out[t] = x;
+        acc += x * (MODE == FIN_CHECK ? x : other[t]);
     }
+    block_partial(acc, partial, R);
     if (arrive_last(s.counter)) finish_scalars<MODE>(partial, gridDim.x, R, s, tol, max_it);
 }
 
@@ -380,90 +376,71 @@ __global__ void __launch_bounds__(RED_THREADS) k_project_dot(const SubdomainDesc
 __global__ void __launch_bounds__(RED_THREADS) k_gather_b_eta(const int64_t *Bp, const int64_t *Bm, const double *y,
                                                                const double *pv, double *q, int64_t nl, int R,
                                                                double *partial, PcgScalars s) {
-    for (int c0 = 0; c0 < R; c0 += 8) {
-        const int rc = min(8, R - c0);
-        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t up = Bp[i], um = Bm[i];
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-                if (c < rc) {
-                    const int64_t t = i * R + c0 + c;
-                    const double x = y[up * R + c0 + c] - y[um * R + c0 + c];
-                    q[t] = x;
-                    acc[c] += pv[t] * x;
-                }
-        }
-        block_partial(acc, partial, blockIdx.x, c0, rc, R);
+    const int c = blockIdx.y;
+    double acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i * R + c;
+        const double x = y[Bp[i] * R + c] - y[Bm[i] * R + c];
+        q[t] = x;
+        acc += pv[t] * x;
     }
+    block_partial(acc, partial, R);
     if (arrive_last(s.counter)) finish_scalars<FIN_ETA>(partial, gridDim.x, R, s, 0.0, 0);
 }
 
-// alpha = (G^T G)^-1 G^T v with G^T v = Z^T B^T v (or Z^T v for v in U).  Grid K x PSPLIT:
-// block (k, j) sums slice j of floating subdomain k's Gamma dofs into gpart; the last block
-// to arrive adds the slices in order (gsum) and applies (G^T G)^-1.
+// alpha = (G^T G)^-1 G^T v with G^T v = Z^T B^T v (or Z^T v for v in U).  Grid (floating
+// subdomains, PSPLIT slices, right-hand sides): block (f, j, c) sums slice j of floating
+// subdomain f's Gamma dofs for column c into gpart; the last block to arrive adds the slices
+// in order (gsum) and applies (G^T G)^-1.
 constexpr int PSPLIT = 8;
-__global__ void __launch_bounds__(256) k_proj_g(const SubdomainDesc *sd, const int64_t *bt_ptr, const int64_t *bt_row,
-                                                const double *v, int v_is_u, const double *Z, double *gpart,
-                                                double *gsum, const double *GtGinv, int nco, double *alpha, int R,
+__global__ void __launch_bounds__(256) k_proj_g(const SubdomainDesc *sd, const int32_t *float_ids,
+                                                const int64_t *bt_ptr, const int64_t *bt_row, const double *v,
+                                                int v_is_u, const double *Z, double *gpart, double *gsum,
+                                                const double *GtGinv, int nco, double *alpha, int R,
                                                 unsigned *counter) {
-    __shared__ double red[8][32];
-    const SubdomainDesc d = sd[blockIdx.x];
-    const int nq = d.n_co;
+    __shared__ double red[8][3];
+    const SubdomainDesc d = sd[float_ids[blockIdx.x]];
+    const int nq = d.n_co, c = blockIdx.z;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (nq > 0) {
-        const int64_t chunk = (d.nG + PSPLIT - 1) / PSPLIT;
-        const int64_t l0 = blockIdx.y * chunk, l1 = min((int64_t)d.nG, l0 + chunk);
-        for (int c0 = 0; c0 < R; c0 += 8) {
-            const int rc = min(8, R - c0);
-            double acc[32];
-#pragma unroll
-            for (int t = 0; t < 32; ++t) acc[t] = 0;
-            for (int64_t l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
-                const int64_t ui = d.offU + l;
-                double z[3];
-#pragma unroll
-                for (int q = 0; q < 3; ++q) z[q] = q < nq ? Z[ui * 3 + q] : 0.0;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    if (c >= rc) continue;
-                    double bt;
-                    if (v_is_u) bt = v[ui * R + c0 + c];
-                    else {
-                        bt = 0;
-                        for (int64_t q = bt_ptr[ui]; q < bt_ptr[ui + 1]; ++q) {
-                            const int64_t rr = bt_row[q];
-                            bt += rr > 0 ? v[(rr - 1) * R + c0 + c] : -v[(-rr - 1) * R + c0 + c];
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) acc[q * 8 + c] += z[q] * bt;
-                }
-            }
-            const double tot = warp_reduce_scatter<double, 32>(acc, lane);   // lane = q * 8 + c
-            __syncthreads();
-            red[warp][lane] = tot;
-            __syncthreads();
-            if (threadIdx.x < 32) {
-                const int q = threadIdx.x / 8, c = threadIdx.x % 8;
-                double x = 0;
-                for (int w = 0; w < 8; ++w) x += red[w][threadIdx.x];
-                if (q < nq && c < rc) gpart[((int64_t)(d.co_off + q) * PSPLIT + blockIdx.y) * R + c0 + c] = x;
+    const int64_t chunk = (d.nG + PSPLIT - 1) / PSPLIT;
+    const int64_t l0 = blockIdx.y * chunk, l1 = min((int64_t)d.nG, l0 + chunk);
+    double acc[3] = {0, 0, 0};
+    for (int64_t l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
+        const int64_t ui = d.offU + l;
+        double bt;
+        if (v_is_u) bt = v[ui * R + c];
+        else {
+            bt = 0;
+            for (int64_t q = bt_ptr[ui]; q < bt_ptr[ui + 1]; ++q) {
+                const int64_t rr = bt_row[q];
+                bt += rr > 0 ? v[(rr - 1) * R + c] : -v[(-rr - 1) * R + c];
             }
         }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc[q] += (q < nq ? Z[ui * 3 + q] : 0.0) * bt;
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) acc[q] = warp_sum(acc[q]);
+    if (lane == 0)
+        for (int q = 0; q < 3; ++q) red[warp][q] = acc[q];
+    __syncthreads();
+    if (threadIdx.x < nq) {
+        double x = 0;
+        for (int w = 0; w < 8; ++w) x += red[w][threadIdx.x];
+        gpart[((int64_t)(d.co_off + threadIdx.x) * PSPLIT + blockIdx.y) * R + c] = x;
     }
     if (!arrive_last(counter)) return;
     for (int t = threadIdx.x; t < nco * R; t += blockDim.x) {
-        const int i = t / R, c = t % R;
+        const int i = t / R, cc = t % R;
         double g = 0;
-        for (int j = 0; j < PSPLIT; ++j) g += __ldcg(gpart + ((int64_t)i * PSPLIT + j) * R + c);
+        for (int j = 0; j < PSPLIT; ++j) g += __ldcg(gpart + ((int64_t)i * PSPLIT + j) * R + cc);
         gsum[t] = g;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < nco * R; t += blockDim.x) {
-        const int i = t / R, c = t % R;
+        const int i = t / R, cc = t % R;
         double a = 0;
-        for (int j = 0; j < nco; ++j) a += GtGinv[(int64_t)i * nco + j] * gsum[(int64_t)j * R + c];
+        for (int j = 0; j < nco; ++j) a += GtGinv[(int64_t)i * nco + j] * gsum[(int64_t)j * R + cc];
         alpha[t] = a;
     }
     if (threadIdx.x == 0) *counter = 0u;
@@ -495,11 +472,20 @@ __global__ void __launch_bounds__(RED_THREADS) k_absmax_partial(const double *a,
     }
 }
 
+// corr = max |du| / max |u| per column from the RED_BLOCKS partial maxima (warp per column)
 __global__ void k_rel_correction(const double *pa, const double *pb, int R, PcgScalars s) {
-    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int c = warp; c < R; c += blockDim.x / 32) {
         double a = 0, b = 0;
-        for (int bl = 0; bl < RED_BLOCKS; ++bl) { a = fmax(a, pa[(int64_t)bl * R + c]); b = fmax(b, pb[(int64_t)bl * R + c]); }
-        s.corr[c] = b > 0 ? a / b : (a > 0 ? 1.0 : 0.0);
+        for (int bl = lane; bl < RED_BLOCKS; bl += 32) {
+            a = fmax(a, pa[(int64_t)bl * R + c]);
+            b = fmax(b, pb[(int64_t)bl * R + c]);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+        }
+        if (lane == 0) s.corr[c] = b > 0 ? a / b : (a > 0 ? 1.0 : 0.0);
     }
 }
 
@@ -522,17 +508,19 @@ __global__ void k_update_lr(const double *p, const double *q, const double *eta,
 
 // ====================================================================== host orchestration
 
-// ws.res = ftil - A^k u - [0; B^T lambda] on every subdomain (double-single, FP32 pool pairs)
+// ws.res = ftil - A^k u - [0; B^T lambda] on every subdomain (double-single, FP32 pool pairs):
+// u is first split into FP32 hi / lo pairs in the padded layout, then the row kernel runs
 void residual_ds(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, const double *lam) {
     if (p->n_items_a == 0) return;
     const OpPool<float> &pool = p->op32;
+    float *uh = ws.uhl.as<float>(), *ul = uh + p->n_vp * R;
+    k_split_u<<<dim3(p->K, R), 256, 0, st>>>(ws.u.as<double>(), p->d_sd.as<SubdomainDesc>(), uh, ul, R);
     auto go = [&](auto rc_tag) {
         constexpr int RC = decltype(rc_tag)::value;
         k_residual_ds<RC><<<p->n_items_a, 256, 0, st>>>(pool.Ahi.as<float>(), pool.Alo.as<float>(),
                                                        p->d_sd.as<SubdomainDesc>(), p->d_items_a.as<int32_t>(),
-                                                       ws.ftil.as<double>(), ws.u.as<double>(),
-                                                       p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), lam,
-                                                       ws.res.as<double>(), R);
+                                                       ws.ftil.as<double>(), uh, ul, p->d_Bt_ptr.as<int64_t>(),
+                                                       p->d_Bt_row.as<int64_t>(), lam, ws.res.as<double>(), R);
     };
     if (R >= 8) go(std::integral_constant<int, 8>{});
     else if (R >= 4) go(std::integral_constant<int, 4>{});
@@ -576,7 +564,7 @@ struct Runner {
     }
 
     template <int MODE> void dot_final(const double *a, const double *b, int64_t n, double tol = 0, int max_it = 0) {
-        k_dot_final<MODE><<<red_blocks(n), RED_THREADS, 0, st>>>(a, b, n, R, ws.partial.as<double>(), S, tol, max_it);
+        k_dot_final<MODE><<<red_grid(n, R), RED_THREADS, 0, st>>>(a, b, n, R, ws.partial.as<double>(), S, tol, max_it);
         note_launch();
     }
 
@@ -617,7 +605,8 @@ struct Runner {
 
     // alpha = (G^T G)^-1 Z^T B^T v  (or (G^T G)^-1 Z^T v for v in U)
     void coarse_alpha(const double *v, int v_is_u) {
-        k_proj_g<<<dim3(p->K, PSPLIT), 256, 0, st>>>(sd, p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), v, v_is_u,
+        k_proj_g<<<dim3(p->n_floating, PSPLIT, R), 256, 0, st>>>(sd, p->d_float_ids.as<int32_t>(),
+                                                                  p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), v, v_is_u,
                                                       p->d_Z.as<double>(), ws.gco.as<double>(), ws.gsum.as<double>(),
                                                       p->d_GtGinv.as<double>(), p->n_co, ws.alpha.as<double>(), R,
                                                       S.counter);
@@ -632,8 +621,7 @@ struct Runner {
             return;
         }
         coarse_alpha(v, 0);
-        k_apply_galpha<<<grid_for(nl * R), 256, 0, st>>>(sd, p->d_u2sub.as<int32_t>(), p->d_Bp.as<int64_t>(),
-                                                         p->d_Bm.as<int64_t>(), p->d_Z.as<double>(),
+        k_apply_galpha<<<grid_for(nl * R), 256, 0, st>>>(p->d_Gcol.as<int32_t>(), p->d_Gval.as<double>(), p->gw,
                                                          ws.alpha.as<double>(), v, -1.0, out, nl, R);
         note_launch();
     }
@@ -643,9 +631,9 @@ struct Runner {
                                          int max_it = 0) {
         const int64_t nl = p->n_lambda;
         if (p->n_co > 0) coarse_alpha(v, 0);
-        k_project_dot<MODE><<<red_blocks(nl), RED_THREADS, 0, st>>>(
-            sd, p->d_u2sub.as<int32_t>(), p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), p->d_Z.as<double>(),
-            p->n_co > 0 ? ws.alpha.as<double>() : nullptr, v, other, out, nl, R, ws.partial.as<double>(), S, tol, max_it);
+        k_project_dot<MODE><<<red_grid(nl, R), RED_THREADS, 0, st>>>(
+            p->d_Gcol.as<int32_t>(), p->d_Gval.as<double>(), p->gw, p->n_co > 0 ? ws.alpha.as<double>() : nullptr, v,
+            other, out, nl, R, ws.partial.as<double>(), S, tol, max_it);
         note_launch();
     }
 
@@ -726,7 +714,7 @@ struct Runner {
                                                             nullptr, pv, x, sd, p->d_u2sub.as<int32_t>(), nu, R, gate);
         note_launch();
         symv<T>(pool, 1, x, ws.yU.as<double>());
-        k_gather_b_eta<<<red_blocks(nl), RED_THREADS, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(),
+        k_gather_b_eta<<<red_grid(nl, R), RED_THREADS, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(),
                                                                ws.yU.as<double>(), pv, q, nl, R,
                                                                ws.partial.as<double>(), S);
         note_launch();
@@ -782,9 +770,8 @@ struct Runner {
                                                          note_launch();
             if (p->n_co > 0) {
                 coarse_alpha(ws.fU.as<double>(), 1);
-                k_apply_galpha<<<grid_for(nl * R), 256, 0, st>>>(sd, p->d_u2sub.as<int32_t>(), p->d_Bp.as<int64_t>(),
-                                                                 p->d_Bm.as<int64_t>(), p->d_Z.as<double>(),
-                                                                 ws.alpha.as<double>(), nullptr, 1.0, lam, nl, R);
+                k_apply_galpha<<<grid_for(nl * R), 256, 0, st>>>(p->d_Gcol.as<int32_t>(), p->d_Gval.as<double>(),
+                                                                 p->gw, ws.alpha.as<double>(), nullptr, 1.0, lam, nl, R);
                                                                  note_launch();
             } else {
                 NLF_CUDA(cudaMemsetAsync(lam, 0, sizeof(double) * nl * R, st));
@@ -894,6 +881,7 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     A(xU, std::max<int64_t>(1, p->n_up));   // apply layout (padding zeroed by the gathers)
     NLF_CUDA(cudaMemsetAsync(xU.p, 0, xU.bytes, async_stream ? async_stream : c->stream));
     A(ftil, nv); A(res, nv); A(u, nv); A(du, nv);
+    alloc(uhl, sizeof(float) * 2 * std::max<int64_t>(1, p->n_vp) * R);
     A(F, nd);
     A(gco, nco * PSPLIT); A(gsum, nco); A(alpha, nco);
     alloc(partial, sizeof(double) * RED_BLOCKS * R);

@@ -217,87 +217,86 @@ __global__ void k_to_apply(const double *uU, T *x, const SubdomainDesc *sd, cons
     }
 }
 
+// u (interleaved subdomain vectors, FP64) -> FP32 pairs uh + ul in the padded layout: for
+// subdomain k, R columns of ld_M entries at offVp * R, zero beyond n_k.  Grid (K, R).
+__global__ void k_split_u(const double *u, const SubdomainDesc *sd, float *uh, float *ul, int R) {
+    const SubdomainDesc d = sd[blockIdx.x];
+    const int c = blockIdx.y;
+    for (int l = threadIdx.x; l < d.ldM; l += blockDim.x) {
+        const double v = l < d.nk ? u[(d.offV + l) * R + c] : 0.0;
+        const float h = (float)v;
+        const int64_t o = d.offVp * R + (int64_t)c * d.ldM + l;
+        uh[o] = h;
+        ul[o] = (float)(v - (double)h);
+    }
+}
+
 // Refinement residual of the torn system (eq. discreteKKT) with FP64 accuracy on the FP32
 // pipes: r = f~ - A^k u - [0; B_k^T lambda] per subdomain.  A^k is read as FP32 pairs
-// (hi + lo), u is split into FP32 pairs (uh + ul) when staged in shared memory.  For each
-// product the lane keeps hi*uh rounded (p) and its exact rounding error (fma), adds p to a
-// running FP32 sum with TwoSum (exact error), and gathers the errors and the cross terms
-// hi*ul + lo*uh in a second FP32 sum; lo*ul (2^-48 relative) is dropped.  The two sums of
-// each lane are added in FP64 and reduced across the warp in FP64.  Relative to
-// sum_j |a_ij u_j| the result is accurate to a few 1e-13, the limit being the FP32 sum of
-// the small terms over a lane's columns.  Work item = (subdomain, 32 rows of A^k).
+// (hi + lo) and u as FP32 pairs (uh + ul, from k_split_u).  For each product the lane keeps
+// hi*uh rounded (p) and its exact rounding error (fma), adds p to a running FP32 sum with
+// TwoSum (exact error), and gathers the errors and the cross terms hi*ul + lo*uh in a second
+// FP32 sum; lo*ul (2^-48 relative) is dropped.  The two sums of each lane are added in FP64
+// and reduced across the warp in FP64.  Relative to sum_j |a_ij u_j| the result is accurate
+// to a few 1e-13, the limit being the FP32 sum of the small terms over a lane's columns.
+// Work item = (subdomain, kResidualRows rows of A^k); warp w owns rows 2w, 2w + 1 and
+// streams their columns with 16-byte loads; u is read in place (L1).
 template <int RC>
-__global__ void __launch_bounds__(256, 2) k_residual_ds(const float *Ahi, const float *Alo, const SubdomainDesc *sd,
-                                                        const int32_t *items, const double *f, const double *u,
-                                                        const int64_t *bt_ptr, const int64_t *bt_row,
-                                                        const double *lam, double *r, int R) {
-    constexpr int XS = ROWS_CW + 4;
-    __shared__ __align__(16) float xh[RC * XS];
-    __shared__ __align__(16) float xl[RC * XS];
+__global__ void __launch_bounds__(256, 3) k_residual_ds(const float *Ahi, const float *Alo, const SubdomainDesc *sd,
+                                                        const int32_t *items, const double *f, const float *uh,
+                                                        const float *ul, const int64_t *bt_ptr,
+                                                        const int64_t *bt_row, const double *lam, double *r, int R) {
+    static_assert(kResidualRows == 16, "8 warps x 2 rows");
     const int k = items[2 * blockIdx.x], row0 = items[2 * blockIdx.x + 1];
     const SubdomainDesc d = sd[k];
     const int n = d.nk, ld = d.ldM;
     const int ncp = min(ld, (n + 7) / 8 * 8);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int ib = row0 + warp * 4;
-    int64_t roff[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) roff[q] = d.offM + (int64_t)min(ib + q, n - 1) * ld;
+    const int ib = row0 + warp * 2;
+    const int64_t roff0 = d.offM + (int64_t)min(ib, n - 1) * ld, roff1 = d.offM + (int64_t)min(ib + 1, n - 1) * ld;
     for (int c0 = 0; c0 < R; c0 += RC) {
         const int rc = min(RC, R - c0);
-        float sh[4][RC], sl[4][RC];
+        const int64_t xo = d.offVp * R + (int64_t)c0 * ld;
+        float sh[2][RC], sl[2][RC];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < 2; ++q)
 #pragma unroll
             for (int c = 0; c < RC; ++c) { sh[q][c] = 0.f; sl[q][c] = 0.f; }
-        for (int l0 = 0; l0 < ncp; l0 += ROWS_CW) {
-            const int cw = min(ROWS_CW, ncp - l0);
-            __syncthreads();
-            for (int t = threadIdx.x; t < RC * cw; t += blockDim.x) {
-                const int l = t / RC, c = t % RC, gl = l0 + l;
-                const double v = (c < rc && gl < n) ? u[(d.offV + gl) * R + c0 + c] : 0.0;
-                const float h = (float)v;
-                xh[c * XS + l] = h;
-                xl[c * XS + l] = (float)(v - (double)h);
-            }
-            __syncthreads();
-            if (ib < n) {
-                for (int l = lane * 4; l < cw; l += 128) {
-                    float4 mh[4], ml[4];
+        if (ib < n) {
+            for (int l = lane * 4; l < ncp; l += 128) {
+                const float4 mh[2] = {__ldcs(reinterpret_cast<const float4 *>(Ahi + roff0 + l)),
+                                      __ldcs(reinterpret_cast<const float4 *>(Ahi + roff1 + l))};
+                const float4 ml[2] = {__ldcs(reinterpret_cast<const float4 *>(Alo + roff0 + l)),
+                                      __ldcs(reinterpret_cast<const float4 *>(Alo + roff1 + l))};
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        mh[q] = __ldcs(reinterpret_cast<const float4 *>(Ahi + roff[q] + l0 + l));
-                        ml[q] = __ldcs(reinterpret_cast<const float4 *>(Alo + roff[q] + l0 + l));
-                    }
+                for (int c = 0; c < RC; ++c) {
+                    if (c >= rc) continue;
+                    const float4 a4 = __ldg(reinterpret_cast<const float4 *>(uh + xo + (int64_t)c * ld + l));
+                    const float4 b4 = __ldg(reinterpret_cast<const float4 *>(ul + xo + (int64_t)c * ld + l));
+                    const float xh[4] = {a4.x, a4.y, a4.z, a4.w}, xl[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
-                    for (int c = 0; c < RC; ++c) {
-                        const float4 a4 = *reinterpret_cast<const float4 *>(xh + c * XS + l);
-                        const float4 b4 = *reinterpret_cast<const float4 *>(xl + c * XS + l);
-                        const float uh[4] = {a4.x, a4.y, a4.z, a4.w}, ul[4] = {b4.x, b4.y, b4.z, b4.w};
+                    for (int q = 0; q < 2; ++q) {
+                        const float ah[4] = {mh[q].x, mh[q].y, mh[q].z, mh[q].w};
+                        const float al[4] = {ml[q].x, ml[q].y, ml[q].z, ml[q].w};
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const float ah[4] = {mh[q].x, mh[q].y, mh[q].z, mh[q].w};
-                            const float al[4] = {ml[q].x, ml[q].y, ml[q].z, ml[q].w};
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                // explicit round-to-nearest intrinsics: no contraction into fma
-                                const float p = __fmul_rn(ah[e], uh[e]);
-                                const float pe = fmaf(ah[e], uh[e], -p);          // hi*uh - p exactly
-                                const float s = __fadd_rn(sh[q][c], p);          // TwoSum(sh, p)
-                                const float bb = __fsub_rn(s, sh[q][c]);
-                                const float se = __fadd_rn(__fsub_rn(sh[q][c], __fsub_rn(s, bb)), __fsub_rn(p, bb));
-                                sh[q][c] = s;
-                                sl[q][c] = __fadd_rn(sl[q][c], __fadd_rn(se, fmaf(ah[e], ul[e], fmaf(al[e], uh[e], pe))));
-                            }
+                        for (int e = 0; e < 4; ++e) {
+                            // explicit round-to-nearest intrinsics: no contraction into fma
+                            const float p = __fmul_rn(ah[e], xh[e]);
+                            const float pe = fmaf(ah[e], xh[e], -p);            // hi*uh - p exactly
+                            const float s = __fadd_rn(sh[q][c], p);            // TwoSum(sh, p)
+                            const float bb = __fsub_rn(s, sh[q][c]);
+                            const float se = __fadd_rn(__fsub_rn(sh[q][c], __fsub_rn(s, bb)), __fsub_rn(p, bb));
+                            sh[q][c] = s;
+                            sl[q][c] = __fadd_rn(sl[q][c], __fadd_rn(se, fmaf(ah[e], xl[e], fmaf(al[e], xh[e], pe))));
                         }
                     }
                 }
             }
         }
-        constexpr int V = 4 * RC;
+        constexpr int V = 2 * RC;
         double v[V];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < 2; ++q)
 #pragma unroll
             for (int c = 0; c < RC; ++c) v[q * RC + c] = (double)sh[q][c] + (double)sl[q][c];
         const double tot = warp_reduce_scatter<double, V>(v, lane);

@@ -11,6 +11,7 @@ struct SolveWS {
     DevMem lam, r, w, z, y, pv, q, d, cvec, dlam;      // Lambda space (FP64)
     DevMem fU, yU, uU, xU;                              // U space
     DevMem ftil, res, u, du;                            // concatenated subdomain vectors
+    DevMem uhl;                                         // u as FP32 hi / lo pairs, padded layout
     DevMem F;                                           // global load vector per dof
     DevMem gco, gsum, alpha;                            // coarse space
     DevMem partial, partial2, scal;                     // reductions and PCG scalars

@@ -498,6 +498,23 @@ __global__ void k_gtg(const int64_t *Bp, const int64_t *Bm, int64_t nl, const in
     }
 }
 
+// slots of the rows of G = B Z (see nlfeti_problem::gw)
+__global__ void k_g_rows(const int64_t *Bp, const int64_t *Bm, int64_t nl, const int32_t *u2sub,
+                         const SubdomainDesc *sd, const double *Z, int gw, int32_t *gcol, double *gval) {
+    const int h = gw / 2;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nl; r += (int64_t)gridDim.x * blockDim.x) {
+        for (int side = 0; side < 2; ++side) {
+            const int64_t u = side ? Bm[r] : Bp[r];
+            const SubdomainDesc d = sd[u2sub[u]];
+            for (int a = 0; a < h; ++a) {
+                const int64_t slot = r * gw + side * h + a;
+                gcol[slot] = a < d.n_co ? d.co_off + a : -1;
+                gval[slot] = a < d.n_co ? Z[u * 3 + a] : 0.0;
+            }
+        }
+    }
+}
+
 // in-place inverse of a small SPD matrix (n <= 128) by one CTA; result written back
 __global__ void k_small_inverse(double *A, int n, int *flag) {
     extern __shared__ double sm[];
@@ -576,6 +593,20 @@ void setup_coarse(nlfeti_problem *p) {
                                                  p->d_Q.as<double>());
     NLF_CUDA(cudaGetLastError());
     const int nco = p->n_co;
+    int max_nco = 0;
+    std::vector<int32_t> fl;
+    for (int k = 0; k < p->K; ++k) {
+        max_nco = std::max(max_nco, (int)p->sd[k].n_co);
+        if (p->sd[k].n_co > 0) fl.push_back(k);
+    }
+    upload(c, p->d_float_ids, fl);
+    p->gw = 2 * max_nco;
+    p->d_Gcol.alloc(c, sizeof(int32_t) * std::max<int64_t>(1, p->n_lambda * p->gw));
+    p->d_Gval.alloc(c, sizeof(double) * std::max<int64_t>(1, p->n_lambda * p->gw));
+    if (p->gw > 0 && p->n_lambda > 0)
+        k_g_rows<<<256, 256, 0, c->stream>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), p->n_lambda,
+                                             p->d_u2sub.as<int32_t>(), p->d_sd.as<SubdomainDesc>(), p->d_Z.as<double>(),
+                                             p->gw, p->d_Gcol.as<int32_t>(), p->d_Gval.as<double>());
     p->d_GtGinv.alloc(c, sizeof(double) * std::max(1, nco * nco));
     if (nco > 0) {
         if (nco > 128) fail(NLFETI_E_INVALID, "more than 128 coarse columns");
