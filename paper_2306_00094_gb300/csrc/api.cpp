@@ -1,6 +1,7 @@
 // C ABI of the nlfeti library: contexts, problems (setup + assembly), factorization,
 // solves, operator application and introspection.  Every entry point converts internal
 // errors into an nlfeti_status and records the message in the context.
+#include <atomic>
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -402,6 +403,8 @@ nlfeti_status nlfeti_problem_create(nlfeti_ctx *ctx, const nlfeti_mesh *mesh, co
         validate_kernel(kernel, mesh->dim);
         if (!decomp || !decomp->elem_subdomain) fail(NLFETI_E_INVALID, "null decomposition");
         std::unique_ptr<nlfeti_problem> q(new nlfeti_problem());
+        static std::atomic<uint64_t> next_uid{1};
+        q->uid = next_uid++;
         q->ctx = ctx;
         q->opt = ctx->opt;
         q->kern = *kernel;
@@ -477,6 +480,7 @@ nlfeti_status nlfeti_factor(nlfeti_problem *p, int mask) {
     return guarded(p->ctx, [&] {
         if (mask & ~3) fail(NLFETI_E_INVALID, "precision mask must use bits 0 and 1");
         double t0 = now_ms();
+        ++p->factor_gen;
         if (mask & 1) factor_ops<double>(p, p->op64);
         if (mask & 2) factor_ops<float>(p, p->op32);
         p->ms_factor = now_ms() - t0;

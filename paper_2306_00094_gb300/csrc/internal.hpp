@@ -137,6 +137,8 @@ namespace nlf { struct SolveWS; }
 
 struct nlfeti_problem {
     nlfeti_ctx *ctx = nullptr;
+    uint64_t uid = 0;                   // unique per problem of the process (workspaces and graphs key on it)
+    uint64_t factor_gen = 0;            // bumped by every factorization (operator buffers may move)
     nlfeti_options opt;
     nlf::MeshHost mesh;
     nlfeti_kernel kern;

@@ -257,6 +257,7 @@ __global__ void k_apply_zalpha(const SubdomainDesc *sd, const int32_t *u2sub, co
 struct PcgScalars {
     double *nPd, *yw_old, *yw, *eta, *beta, *relres, *corr;
     int *active, *iters, *n_active;
+    int *loops;            // PCG iterations run by the current graph loop
     unsigned *counter;     // arrival counter of the fused reductions (reset by the last block)
 };
 
@@ -496,8 +497,17 @@ __global__ void k_update_p(const double *y, const double *beta, const int *activ
     }
 }
 
+// lambda += eta p, r -= eta q.  Inside a graph loop (use_cond) the first thread also counts
+// the iteration and sets the loop condition: continue while a right-hand side is active and
+// fewer than limit iterations have run (the count bounds the loop whatever the scalars hold).
 __global__ void k_update_lr(const double *p, const double *q, const double *eta, double *lam, double *r, int64_t n,
-                            int R) {
+                            int R, cudaGraphConditionalHandle cond, int use_cond, const int *n_active, int *loops,
+                            int limit) {
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int l = *loops + 1;
+        *loops = l;
+        cudaGraphSetConditional(cond, (*n_active > 0 && l < limit) ? 1u : 0u);
+    }
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * R; t += (int64_t)gridDim.x * blockDim.x) {
         int c = (int)(t % R);
         double e = eta[c];
@@ -549,6 +559,9 @@ struct Runner {
     // inside PCG iterations: the interface applies and their gathers return at once when no
     // right-hand side is active any more (every later update is masked by the active flags)
     const int *gate = nullptr;
+    // the WHILE node of the graph loop being captured (set by k_update_lr)
+    cudaGraphConditionalHandle cond = 0;
+    bool use_cond = false;
     int64_t apply_launches = 0;
     double apply_ms = 0, apply_bytes = 0;
 
@@ -557,8 +570,8 @@ struct Runner {
         S.nPd = b; S.yw_old = b + R; S.yw = b + 2 * R; S.eta = b + 3 * R; S.beta = b + 4 * R; S.relres = b + 5 * R;
         S.corr = b + 6 * R;
         int *ib = reinterpret_cast<int *>(b + 7 * R);
-        S.active = ib; S.iters = ib + R; S.n_active = ib + 2 * R;
-        S.counter = reinterpret_cast<unsigned *>(ib + 2 * R + 1);
+        S.active = ib; S.iters = ib + R; S.n_active = ib + 2 * R; S.loops = ib + 2 * R + 1;
+        S.counter = reinterpret_cast<unsigned *>(ib + 2 * R + 2);
         sd = p->d_sd.as<SubdomainDesc>();
         set_attributes();
     }
@@ -745,8 +758,59 @@ struct Runner {
         note_launch();
         applyF_eta<T>(pool, pv, q);                              // q = F p, (p, q), eta
         gate = nullptr;
-        k_update_lr<<<grid_for(nl * R), 256, 0, st>>>(pv, q, S.eta, lam, r, nl, R);
+        k_update_lr<<<grid_for(nl * R), 256, 0, st>>>(pv, q, S.eta, lam, r, nl, R, cond, use_cond ? 1 : 0,
+                                                      S.n_active, S.loops, max_it + 1);
         note_launch();
+    }
+
+    // The PCG loop of a pass as one graph: a WHILE node whose body is one iteration; cached
+    // in the workspace and reused by every pass with the same factorization and settings.
+    template <typename T> const PcgGraph &while_graph(const OpPool<T> &pool, double tol, int max_it) {
+        const int prec = std::is_same<T, float>::value ? 1 : 0;
+        for (const auto &g : ws.graphs)
+            if (g.factor_gen == p->factor_gen && g.precision == prec && g.tol == tol && g.max_it == max_it) return g;
+        PcgGraph g;
+        g.factor_gen = p->factor_gen;
+        g.precision = prec;
+        g.tol = tol;
+        g.max_it = max_it;
+        cudaGraph_t graph = nullptr;
+        NLF_CUDA(cudaGraphCreate(&graph, 0));
+        try {
+            NLF_CUDA(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams np = {};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = cond;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node;
+            NLF_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np));
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            capturing = true;
+            use_cond = true;
+            cap_launches = 0;
+            NLF_CUDA(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            iteration<T>(pool, tol, max_it);
+            cudaGraph_t captured = nullptr;
+            capturing = false;
+            use_cond = false;
+            NLF_CUDA(cudaStreamEndCapture(st, &captured));
+            NLF_CUDA(cudaGraphInstantiate(&g.exec, graph, 0));
+        } catch (...) {
+            if (capturing) {
+                cudaGraph_t junk = nullptr;
+                cudaStreamEndCapture(st, &junk);
+                capturing = false;
+                use_cond = false;
+            }
+            cudaGetLastError();
+            cudaGraphDestroy(graph);
+            throw;
+        }
+        cudaGraphDestroy(graph);
+        g.body_launches = cap_launches;
+        ws.graphs.push_back(g);
+        return ws.graphs.back();
     }
 
     // one FETI pass on subdomain loads ws.res; constraint right-hand side ws.cvec when with_c.
@@ -785,7 +849,19 @@ struct Runner {
             const int chunk = 4;
             int done = 0, n_active = R;
             cudaGraphExec_t exec = nullptr;
-            if (batched) {
+            if (batched && !p->prof_on) {
+                // device-side loop: one launch, one read-back per pass
+                const PcgGraph &g = while_graph<T>(pool, tol, max_it);
+                NLF_CUDA(cudaMemsetAsync(S.loops, 0, sizeof(int), st));
+                NLF_CUDA(cudaGraphLaunch(g.exec, st));
+                NLF_CUDA(cudaMemcpyAsync(ws.host_flag.data(), S.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                NLF_CUDA(cudaStreamSynchronize(st));
+                n_active = ws.host_flag[0];
+                eager_launches += (int64_t)ws.host_flag[1] * g.body_launches;
+                done = max_it + 1;      // skip the chunked loop below
+            } else if (batched) {
+                // profiling: chunks of iterations with event-timed applies (event nodes are not
+                // allowed inside a WHILE body), the host checks convergence between chunks
                 cudaGraph_t graph;
                 capturing = true;
                 cap_launches = 0;
@@ -861,13 +937,25 @@ struct Runner {
 
 }  // namespace
 
+void SolveWS::drop_graphs() {
+    if (graphs.empty()) return;
+    // a graph may still run on the workspace's stream
+    if (async_stream) cudaStreamSynchronize(async_stream);
+    else if (prob) cudaStreamSynchronize(prob->ctx->stream);
+    for (auto &g : graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+}
+
 void SolveWS::ensure(nlfeti_problem *p, int nR) {
     nlfeti_ctx *c = p->ctx;
-    if (R == nR && prob == p) return;
+    if (R == nR && prob == p && prob_uid == p->uid) return;
     // buffers about to be replaced may still be read by queued work
     NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
+    drop_graphs();
     R = nR;
     prob = p;
+    prob_uid = p->uid;
     const int64_t nl = std::max<int64_t>(1, p->n_lambda), nu = std::max<int64_t>(1, p->n_u),
                   nv = std::max<int64_t>(1, p->sum_nk), nd = std::max<int64_t>(1, p->n_dofs_total);
     const int64_t nco = std::max(1, p->n_co);

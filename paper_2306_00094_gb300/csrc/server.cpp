@@ -53,7 +53,8 @@ struct nlfeti_server {
     void worker() {
         cudaStream_t st = nullptr;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return; }
-        SolveWS ws;
+        std::unique_ptr<SolveWS> wsp(new SolveWS());
+        SolveWS &ws = *wsp;
         ws.async_stream = st;
         for (;;) {
             std::shared_ptr<Request> rq;
@@ -116,7 +117,7 @@ struct nlfeti_server {
             cv_done.notify_all();
             cv_work.notify_all();
         }
-        ws = SolveWS();
+        wsp.reset();
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }

@@ -5,8 +5,19 @@
 
 namespace nlf {
 
+// An instantiated PCG loop of one pass (the body captured once and launched by every later
+// pass with the same problem, factorization, precision, tolerance and iteration limit).
+struct PcgGraph {
+    uint64_t factor_gen = 0;
+    int precision = 0, max_it = 0;
+    double tol = 0;
+    cudaGraphExec_t exec = nullptr;
+    int64_t body_launches = 0;      // kernels per loop iteration
+};
+
 struct SolveWS {
     nlfeti_problem *prob = nullptr;
+    uint64_t prob_uid = 0;
     int R = 0;
     DevMem lam, r, w, z, y, pv, q, d, cvec, dlam;      // Lambda space (FP64)
     DevMem fU, yU, uU, xU;                              // U space
@@ -18,7 +29,13 @@ struct SolveWS {
     DevMem in_rhs, in_g, out_u;                         // staging for host-array solves
     std::vector<int> host_flag;
     cudaStream_t async_stream = nullptr;   // set: stream-ordered allocations (server slots)
+    std::vector<PcgGraph> graphs;
     void ensure(nlfeti_problem *p, int R);
+    void drop_graphs();
+    SolveWS() = default;
+    SolveWS(const SolveWS &) = delete;
+    SolveWS &operator=(const SolveWS &) = delete;
+    ~SolveWS() { drop_graphs(); }
 };
 
 struct PassInfo {

@@ -1,0 +1,78 @@
+"""The three ways the PCG loop of a pass can run give the same solution.
+
+* batched, no profiling: the loop is one cached graph with a device-side WHILE node;
+* batched, profiling on: chunks of event-timed iterations with host checks in between;
+* not batched: one launch per subdomain per stage, no graphs.
+
+The arithmetic of every iteration is the same in all three (inactive right-hand sides are
+frozen by their flags), so the graph loop and the chunked loop must agree bit for bit, and
+the per-subdomain launches (same kernels on subsets of the work items) as well.  The cached
+graph must follow a refactorization and option changes.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    from paper_2306_00094_gb300 import binding
+    ctx = binding.Context()
+    w = W.cfg2_const_l2(N=24, k=3, nrhs=3, delta=0.1)
+    p = binding.Problem.from_workload(ctx, w)
+    p.factor(3)
+    yield binding, w, p
+    p.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_while_chunked_eager_agree(setup, precision):
+    binding, w, p = setup
+    p.set_options(binding.default_options(precision=precision, batched=1))
+    u_while, st_w = p.solve(w.rhs, w.rhs_kind)
+    u_again, _ = p.solve(w.rhs, w.rhs_kind)              # cached graph reused
+    assert np.array_equal(u_while, u_again)
+    p.profile()
+    p.set_profiling(True)
+    u_chunk, st_c = p.solve(w.rhs, w.rhs_kind)
+    p.set_profiling(False)
+    prof = p.profile()
+    assert prof["apply_launches"] > 0 and prof["apply_ms"] > 0 and prof["kernel_launches"] > 0
+    assert np.array_equal(u_while, u_chunk)
+    assert st_w["iterations"] == st_c["iterations"]
+    p.set_options(binding.default_options(precision=precision, batched=0))
+    u_eager, st_e = p.solve(w.rhs, w.rhs_kind)
+    assert np.array_equal(u_while, u_eager)
+    assert st_w["iterations"] == st_e["iterations"]
+
+
+def test_graph_follows_refactor_and_options(setup):
+    binding, w, p = setup
+    p.set_options(binding.default_options(precision=1, batched=1))
+    u1, _ = p.solve(w.rhs, w.rhs_kind)
+    p.factor(2)                                            # operator buffers are rebuilt
+    u2, _ = p.solve(w.rhs, w.rhs_kind)
+    assert np.array_equal(u1, u2)
+    loose = binding.default_options(precision=1, batched=1)
+    loose.inner_tol = 1e-2
+    p.set_options(loose)
+    u3, st3 = p.solve(w.rhs, w.rhs_kind)
+    scale = np.abs(u1).max()
+    assert np.abs(u3 - u1).max() <= 1e-8 * scale
+    p.set_options(binding.default_options(precision=1, batched=1))
+    u4, _ = p.solve(w.rhs, w.rhs_kind)
+    assert np.array_equal(u1, u4)
+
+
+def test_launch_count_of_graph_loop(setup):
+    binding, w, p = setup
+    p.set_options(binding.default_options(precision=1, batched=1))
+    p.solve(w.rhs, w.rhs_kind)
+    p.profile()
+    _, st = p.solve(w.rhs, w.rhs_kind)
+    n = p.profile()["kernel_launches"]
+    # at least the interface applies of every iteration (two per iteration) were counted
+    assert n >= 2 * st["iterations"]
