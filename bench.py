@@ -157,7 +157,7 @@ def run_ours(args):
     # inputs resident in HBM: column-major n_dofs x R  ==  contiguous (R, n_dofs)
     d_rhs = torch.from_numpy(np.ascontiguousarray(w.rhs.T)).to(dev)
     d_out = torch.empty_like(d_rhs)
-    mixed = binding.default_options(precision=1, batched=1)
+    mixed = binding.default_options(precision=1, batched=1, graph_loop=0 if args.host_loop else 1)
     plain = binding.default_options(precision=0, batched=0)
     plain_batched = binding.default_options(precision=0, batched=1)
 
@@ -382,6 +382,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true", help="setup, warm-up and the timed steps only (for ncu)")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="PCG loops as host-checked graph chunks instead of device-side WHILE graphs "
+                         "(ncu cannot profile kernels inside conditional graphs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

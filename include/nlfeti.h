@@ -91,7 +91,11 @@ typedef struct {
  *      the mixed path uses inner_tol per refinement sweep and refine_tol on the
  *      relative nodal correction.
  * batched: 1 = one launch per stage over all subdomains (graph-captured loop);
- *          0 = one launch per subdomain per stage, no graphs (baseline). */
+ *          0 = one launch per subdomain per stage, no graphs (baseline).
+ * graph_loop (batched only): 1 = each PCG loop runs on the device as one graph with a
+ *          WHILE node (no host round trips); 0 = graphs of 4 iterations with a host check
+ *          of convergence in between (for profilers that cannot look inside conditional
+ *          graphs).  Profiling (nlfeti_set_profiling) always uses the second form. */
 typedef struct {
     int precision;
     double tol;
@@ -101,6 +105,7 @@ typedef struct {
     double refine_tol;
     int batched;
     size_t hbm_budget;
+    int graph_loop;
 } nlfeti_options;
 
 typedef struct {
@@ -120,7 +125,7 @@ typedef struct {
 
 /* Default options: FP64 plain, tol 1e-10, max_it 1000, at most 10 refinement sweeps,
  * inner_tol 1e-3 (each sweep's contraction is limited by the FP32 operators to ~1e-4
- * anyway), refine_tol 1e-9, batched. */
+ * anyway), refine_tol 1e-9, batched, graph_loop 1. */
 void nlfeti_default_options(nlfeti_options *opt);
 
 /* Context on the given CUDA stream (cudaStream_t, NULL = the legacy stream).

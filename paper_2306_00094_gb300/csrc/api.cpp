@@ -316,6 +316,7 @@ void nlfeti_default_options(nlfeti_options *o) {
     o->refine_tol = 1e-9;
     o->batched = 1;
     o->hbm_budget = 0;
+    o->graph_loop = 1;
 }
 
 nlfeti_status nlfeti_create(nlfeti_ctx **out, const nlfeti_options *opt, void *cuda_stream,

@@ -303,7 +303,10 @@ __device__ __forceinline__ bool arrive_last(unsigned *counter) {
 //   BETA:  (y,w) and beta = (y,w)/(y,w)_old;    ETA:   (p,q) and eta = (y,w)/(p,q).
 template <int MODE>
 __device__ void finish_scalars(const double *partial, int nb, int R, PcgScalars s, double tol, int max_it) {
+    __shared__ int n_act;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) n_act = 0;
+    __syncthreads();
     for (int c = warp; c < R; c += RED_THREADS / 32) {
         double v = 0;
         for (int bl = lane; bl < nb; bl += 32) v += __ldcg(partial + (int64_t)bl * R + c);
@@ -317,8 +320,11 @@ __device__ void finish_scalars(const double *partial, int nb, int R, PcgScalars 
                 s.relres[c] = 1.0;
             } else if (MODE == FIN_CHECK) {
                 const double nw = sqrt(v), ref = s.nPd[c];
-                if (s.active[c]) s.relres[c] = ref > 0 ? nw / ref : 0.0;
-                if (s.active[c] && (nw <= tol * ref || s.iters[c] >= max_it)) s.active[c] = 0;
+                int act = s.active[c];
+                if (act) s.relres[c] = ref > 0 ? nw / ref : 0.0;
+                if (act && (nw <= tol * ref || s.iters[c] >= max_it)) act = 0;
+                s.active[c] = act;
+                if (act) atomicAdd(&n_act, 1);
             } else if (MODE == FIN_BETA) {
                 s.yw[c] = v;
                 s.beta[c] = (s.iters[c] == 0 || s.yw_old[c] == 0.0) ? 0.0 : v / s.yw_old[c];
@@ -332,11 +338,7 @@ __device__ void finish_scalars(const double *partial, int nb, int R, PcgScalars 
     __syncthreads();
     if (threadIdx.x == 0) {
         if (MODE == FIN_NPD) *s.n_active = R;
-        if (MODE == FIN_CHECK) {
-            int cnt = 0;
-            for (int c = 0; c < R; ++c) cnt += s.active[c] != 0;
-            *s.n_active = cnt;
-        }
+        if (MODE == FIN_CHECK) *s.n_active = n_act;
         *s.counter = 0u;
     }
 }
@@ -849,7 +851,7 @@ struct Runner {
             const int chunk = 4;
             int done = 0, n_active = R;
             cudaGraphExec_t exec = nullptr;
-            if (batched && !p->prof_on) {
+            if (batched && !p->prof_on && p->opt.graph_loop) {
                 // device-side loop: one launch, one read-back per pass
                 const PcgGraph &g = while_graph<T>(pool, tol, max_it);
                 NLF_CUDA(cudaMemsetAsync(S.loops, 0, sizeof(int), st));
@@ -860,8 +862,8 @@ struct Runner {
                 eager_launches += (int64_t)ws.host_flag[1] * g.body_launches;
                 done = max_it + 1;      // skip the chunked loop below
             } else if (batched) {
-                // profiling: chunks of iterations with event-timed applies (event nodes are not
-                // allowed inside a WHILE body), the host checks convergence between chunks
+                // host-checked chunks of iterations (profiling: with event-timed applies, as
+                // event nodes are not allowed inside a WHILE body)
                 cudaGraph_t graph;
                 capturing = true;
                 cap_launches = 0;

@@ -1,7 +1,8 @@
 """The three ways the PCG loop of a pass can run give the same solution.
 
 * batched, no profiling: the loop is one cached graph with a device-side WHILE node;
-* batched, profiling on: chunks of event-timed iterations with host checks in between;
+* batched, profiling on or graph_loop = 0: graphs of 4 iterations (event-timed applies when
+  profiling) with host checks in between;
 * not batched: one launch per subdomain per stage, no graphs.
 
 The arithmetic of every iteration is the same in all three (inactive right-hand sides are
@@ -43,6 +44,10 @@ def test_while_chunked_eager_agree(setup, precision):
     assert prof["apply_launches"] > 0 and prof["apply_ms"] > 0 and prof["kernel_launches"] > 0
     assert np.array_equal(u_while, u_chunk)
     assert st_w["iterations"] == st_c["iterations"]
+    p.set_options(binding.default_options(precision=precision, batched=1, graph_loop=0))
+    u_host, st_h = p.solve(w.rhs, w.rhs_kind)
+    assert np.array_equal(u_while, u_host)
+    assert st_w["iterations"] == st_h["iterations"]
     p.set_options(binding.default_options(precision=precision, batched=0))
     u_eager, st_e = p.solve(w.rhs, w.rhs_kind)
     assert np.array_equal(u_while, u_eager)
