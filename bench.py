@@ -109,7 +109,7 @@ def percentile(xs, q):
 def profile_traffic(kernel_src_hash):
     """DRAM bytes per launch of the apply kernel from the committed ncu summary, if it matches
     the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_rows_apply_cfg2.md")
+    path = os.path.join(ROOT, "profiles", "k_apply_tma_cfg2.md")
     try:
         txt = open(path).read()
     except OSError:
@@ -124,7 +124,7 @@ def profile_traffic(kernel_src_hash):
 
 
 def kernel_source_hash():
-    with open(os.path.join(ROOT, "paper_2306_00094_gb300", "csrc", "rows.cuh"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_2306_00094_gb300", "csrc", "apply_tma.cuh"), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
@@ -290,7 +290,7 @@ def run_ours(args):
                    "step": "warm solve request (operators resident), setup/factor excluded"},
         "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99)},
         "iterations": stats[-1]["iterations"], "refine_sweeps": stats[-1]["refine_sweeps"],
-        "roofline": {"kernel": "k_rows<float, 8, APPLY> (dense S_k^+ / S_k apply)", "bound": "hbm",
+        "roofline": {"kernel": "k_apply_tma<float, 8> (dense S_k^+ / S_k apply, tensor-copy pipeline)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "peak_source": peak_kind,
                      "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_s * 1e6 if avg_s else None,

@@ -268,6 +268,35 @@ void build_maps(nlfeti_problem *p) {
         p->item_off_o[k + 1] = (int)(items_o.size() / 2);
     }
     upload(c, p->d_items_o, items_o);
+    // persistent schedule of the bulk-copy apply: longest item first onto the least loaded CTA
+    // (cost = rows x streamed columns), then each CTA's list in (subdomain, row) order
+    {
+        const int G = std::max(1, std::min(apply_tma_ctas(), std::max(1, p->n_items)));
+        std::vector<std::pair<int64_t, int>> order;     // (cost, item)
+        for (int t = 0; t < p->n_items; ++t) {
+            const auto &s = p->sd[items[2 * t]];
+            const int rows = std::min(kApplyRows, s.nG - items[2 * t + 1]);
+            const int64_t cols = std::min<int64_t>(s.ldG, (s.nG + 7) / 8 * 8);
+            order.push_back({(int64_t)rows * cols + 256, t});
+        }
+        std::stable_sort(order.begin(), order.end(), [](auto a, auto b) { return a.first > b.first; });
+        std::vector<int64_t> load(G, 0);
+        std::vector<std::vector<int>> lists(G);
+        for (auto &o : order) {
+            const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            load[b] += o.first;
+            lists[b].push_back(o.second);
+        }
+        std::vector<int32_t> sptr(G + 1, 0), sitems;
+        for (int b = 0; b < G; ++b) {
+            std::sort(lists[b].begin(), lists[b].end());
+            for (int t : lists[b]) { sitems.push_back(items[2 * t]); sitems.push_back(items[2 * t + 1]); }
+            sptr[b + 1] = (int32_t)(sitems.size() / 2);
+        }
+        p->sched_ctas = G;
+        upload(c, p->d_sched_ptr, sptr);
+        upload(c, p->d_sched_items, sitems);
+    }
     std::vector<int32_t> items_a;
     for (int k = 0; k < K; ++k)
         for (int r0 = 0; r0 < p->sd[k].nk; r0 += kResidualRows) { items_a.push_back(k); items_a.push_back(r0); }

@@ -1,0 +1,200 @@
+// Interface apply y_U = M x_U (M = S_k^+ or S_k on every subdomain) with the operator rows
+// streamed by the bulk-copy engine.
+//
+// Persistent CTAs (a host-built schedule gives each CTA a list of 32-row work items, balanced
+// by their cost).  Warp 8 is the producer: for every item of the CTA and every chunk of
+// APPLY_CB bytes of columns it loads the 32 x APPLY_CB tile of the item's rows and the same
+// columns of RC right-hand sides of x with two 2-D tensor copies (tensor maps per subdomain
+// operator and per subdomain block of x in the apply layout; rows past n_gamma or past R
+// arrive as zeros) into a ring of NS shared-memory stages, each signalled by an mbarrier
+// with the byte count of its copies.  Warps 0..7 consume: warp w owns rows 4w..4w+3 of the item, each lane 4
+// (FP32) or 2 (FP64) consecutive columns per 128-/64-column step, in the same per-lane order
+// of operations as the register-streaming row kernel, so both give bitwise the same y.  A consumed stage is released to the producer
+// through a second mbarrier.  The producer runs ahead across item boundaries, so the copy
+// engine keeps up to NS * 32 KB per CTA in flight while the consumers compute.
+// With more than RC right-hand sides the rows of an item are streamed once per block of RC.
+//
+// Every wait is bounded: a wait that runs out sets *err (the workspace's error word, read by
+// the host after the solve), the consumers stop, the producer waits (again bounded) for the
+// copies it has issued and the CTA returns.
+#pragma once
+
+#include <cuda.h>
+
+constexpr int APPLY_CB = 1024;                      // bytes of one row (or one x column) per stage
+constexpr int APPLY_NS = 5;                         // stages (up to 200 KB of shared memory, one CTA per SM)
+// a stage: 32 operator rows, then RC columns of x
+__host__ __device__ constexpr int apply_stage_bytes(int rc) { return (32 + rc) * APPLY_CB; }
+// the ring is aligned to 1 KB inside the dynamic shared memory (tensor copies want 128 B)
+__host__ __device__ constexpr int apply_smem_bytes(int rc, int ns) { return ns * apply_stage_bytes(rc) + 1024; }
+constexpr int APPLY_THREADS = 9 * 32;               // 8 consumer warps + 1 producer warp
+constexpr long long APPLY_WAIT_TRIES = 1ll << 24;   // bounded mbarrier waits (seconds)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// true once the phase with the given parity has completed; false when the tries run out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long i = 0; i < APPLY_WAIT_TRIES; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 2-D tile (box of the tensor map) at coordinates (x = column, y = row) -> shared memory,
+// completing on an mbarrier; x * element size must be a multiple of 16 bytes
+__device__ __forceinline__ void tile_g2s(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// tensor map of a row-major block (n rows of ld entries, 16-byte aligned rows) for tiles of
+// box_rows rows x APPLY_CB bytes: an operator (box_rows 32) or the R columns of x of one
+// subdomain in the apply layout (box_rows RC); encode: the driver's cuTensorMapEncodeTiled
+template <typename Encode>
+inline CUresult encode_apply_map(Encode encode, CUtensorMap *map, const void *base, int ld, int n, int elem_size,
+                                 int box_rows = 32) {
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * (cuuint64_t)elem_size};
+    const cuuint32_t box[2] = {(cuuint32_t)(APPLY_CB / elem_size), (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return encode(map, elem_size == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2u,
+                  const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+template <typename T, int RC, int NS = APPLY_NS, int MINB = 1>
+__global__ void __launch_bounds__(APPLY_THREADS, MINB)
+    k_apply_tma(const CUtensorMap *maps, const CUtensorMap *xmaps, int use_sp, const SubdomainDesc *sd,
+                const int32_t *sched_ptr, const int32_t *sched_items, double *y, int R, const int *gate, int *err) {
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::W;
+    constexpr int CW = APPLY_CB / (int)sizeof(T);   // columns per stage row
+    constexpr int STAGE = apply_stage_bytes(RC);
+    extern __shared__ __align__(128) unsigned char ring_raw[];
+    unsigned char *ring = ring_raw + ((1024u - (smem_u32(ring_raw) & 1023u)) & 1023u);
+    __shared__ uint64_t full[NS], empty[NS];
+    __shared__ volatile int abort_flag;
+    if (gate && *gate == 0) return;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 8);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int it0 = sched_ptr[blockIdx.x], it1 = sched_ptr[blockIdx.x + 1];
+    if (warp == 8) {
+        // ------------------------------------------------------------------ producer
+        int q = 0;
+        bool ok = true;
+        for (int it = it0; it < it1 && ok; ++it) {
+            // descriptor fields in registers: the asm statements below clobber memory
+            const int k = sched_items[2 * it], i0 = sched_items[2 * it + 1];
+            const int n = sd[k].nG, ld = sd[k].ldG;
+            const int ncp = min(ld, (n + 7) / 8 * 8);
+            const CUtensorMap *map = maps + 2 * k + use_sp, *xmap = xmaps + k;
+            for (int c0 = 0; c0 < R && ok; c0 += RC)        // the rows again for every column block
+            for (int l0 = 0; l0 < ncp; l0 += CW, ++q) {
+                const int s = q % NS;
+                if (q >= NS && !mbar_wait(&empty[s], ((q / NS) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                if (abort_flag) { ok = false; break; }
+                // the tiles always land whole (out-of-range rows and columns as zeros)
+                if (lane == 0) {
+                    unsigned char *stg = ring + s * STAGE;
+                    mbar_arrive_expect_tx(&full[s], (32 + RC) * APPLY_CB);
+                    tile_g2s(stg, map, l0, i0, &full[s]);
+                    tile_g2s(stg + 32 * APPLY_CB, xmap, l0, c0, &full[s]);
+                }
+                __syncwarp();
+            }
+        }
+        if (!ok) {
+            if (lane == 0) { atomicExch(err, 1); abort_flag = 1; }
+            // let the copies already issued land before the CTA leaves
+            for (int t = max(0, q - NS); t < q; ++t) mbar_wait(&full[t % NS], (t / NS) & 1);
+        }
+        return;
+    }
+    // ---------------------------------------------------------------------- consumers
+    int q = 0;
+    for (int it = it0; it < it1; ++it) {
+        const int k = sched_items[2 * it], i0 = sched_items[2 * it + 1];
+        const int n = sd[k].nG, ld = sd[k].ldG;
+        const int64_t yoff = sd[k].offU;
+        const int ncp = min(ld, (n + 7) / 8 * 8);
+        const int ib = i0 + warp * 4;
+        for (int c0 = 0; c0 < R; c0 += RC) {
+            const int rc = min(RC, R - c0);
+            T acc[4][RC];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < RC; ++c) acc[r][c] = T(0);
+            for (int l0 = 0; l0 < ncp; l0 += CW, ++q) {
+                const int s = q % NS;
+                if (!mbar_wait(&full[s], (q / NS) & 1) || abort_flag) {
+                    if (lane == 0) { atomicExch(err, 1); abort_flag = 1; }
+                    return;
+                }
+                const int cw = min(CW, ncp - l0);
+                const T *st = reinterpret_cast<const T *>(ring + s * STAGE);
+                const T *xs = st + 32 * CW;
+                if (ib < n) {
+                    for (int l = lane * W; l < cw; l += 32 * W) {
+                        V mv[4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+                            mv[r] = *reinterpret_cast<const V *>(st + (warp * 4 + min(r, n - 1 - ib)) * CW + l);
+                        rows_step<T, RC>(mv, [&](int c) {
+                            return c < rc ? *reinterpret_cast<const V *>(xs + c * CW + l) : V{};
+                        }, acc);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
+            constexpr int NV = 4 * RC;
+            T v[NV];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < RC; ++c) v[r * RC + c] = acc[r][c];
+            const T tot = warp_reduce_scatter<T, NV>(v, lane);
+            constexpr int G = 32 / NV;
+            const int idx = lane / G, r = idx / RC, c = idx % RC, i = ib + r;
+            if (lane % G == 0 && c < rc && i < n) y[(yoff + i) * R + c0 + c] = (double)tot;
+        }
+    }
+}

@@ -128,6 +128,7 @@ constexpr int kResidualRows = 16;       // rows of a refinement-residual work it
 template <typename T> struct OpPool {   // operators of one precision
     nlf::DevMem M, S, Sp;                // swept matrices, Schur complements, pseudo-inverses
     nlf::DevMem scratch;                 // panel scratch of the sweeps
+    nlf::DevMem maps;                    // tensor maps of S_k and S_k^+ (2 per subdomain) for the apply
     nlf::DevMem Ahi, Alo;                // FP32 pool only: A^k = Ahi + Alo (FP32 pairs, swept-matrix layout),
                                          // for the double-single refinement residual
     bool ready = false;
@@ -182,6 +183,10 @@ struct nlfeti_problem {
     nlf::DevMem d_items_o;               // work items over Omega rows (back substitution)
     std::vector<int> item_off_o;         // K+1
     nlf::DevMem d_items_a;               // kResidualRows-row work items over all rows of A^k (residual)
+    // persistent schedule of the bulk-copy interface apply: CTA b runs the work items
+    // sched_items[sched_ptr[b] .. sched_ptr[b+1]) (pairs (k, first row)), balanced by cost
+    int sched_ctas = 0;
+    nlf::DevMem d_sched_ptr, d_sched_items;
     int n_items_a = 0;
     nlf::DevMem d_flag;                  // device status words
     OpPool<double> op64;
@@ -207,4 +212,8 @@ void stream_leave(nlfeti_ctx *c);
 // a live problem or server keeps its context alive
 void ctx_attach(nlfeti_ctx *c);
 void ctx_detach(nlfeti_ctx *c);
+// CTAs of the bulk-copy interface apply that fit on the device at once (all instantiations)
+int apply_tma_ctas();
+// tensor maps of a pool's S_k and S_k^+ for the bulk-copy apply (after the factorization)
+template <typename T> void encode_apply_maps(nlfeti_problem *p, OpPool<T> &pool);
 }  // namespace nlf

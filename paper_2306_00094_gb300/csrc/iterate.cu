@@ -19,6 +19,7 @@
 // correction is below refine_tol.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 
 #include "solve.hpp"
@@ -127,6 +128,7 @@ __global__ void k_gather_bd(const int64_t *ptr, const int64_t *col, const double
 }
 
 #include "rows.cuh"
+#include "apply_tma.cuh"
 
 __global__ void k_scatter_u(const int64_t *u2v, const double *uU, double *v, int64_t nu, int R) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
@@ -258,6 +260,7 @@ struct PcgScalars {
     double *nPd, *yw_old, *yw, *eta, *beta, *relres, *corr;
     int *active, *iters, *n_active;
     int *loops;            // PCG iterations run by the current graph loop
+    int *err;              // set by a device wait that ran out (checked after the solve)
     unsigned *counter;     // arrival counter of the fused reductions (reset by the last block)
 };
 
@@ -574,6 +577,7 @@ struct Runner {
         int *ib = reinterpret_cast<int *>(b + 7 * R);
         S.active = ib; S.iters = ib + R; S.n_active = ib + 2 * R; S.loops = ib + 2 * R + 1;
         S.counter = reinterpret_cast<unsigned *>(ib + 2 * R + 2);
+        S.err = ib + 2 * R + 3;
         sd = p->d_sd.as<SubdomainDesc>();
         set_attributes();
     }
@@ -591,6 +595,13 @@ struct Runner {
         p->prof.apply_launches += apply_launches;
         p->prof.apply_ms += apply_ms;
         p->prof.apply_bytes += apply_bytes;
+    }
+
+    // after a read-back of the scalar words n_active .. err into host_flag
+    void check_waits() {
+        if (ws.host_flag[3] == 0) return;
+        NLF_CUDA(cudaMemsetAsync(S.err, 0, sizeof(int), st));
+        fail(NLFETI_E_TIMEOUT, "a device-side wait of the interface apply ran out of time");
     }
 
     void note_launch() {
@@ -684,6 +695,26 @@ struct Runner {
 
     void set_attributes() {}
 
+    // the batched interface apply: persistent tensor-copy pipeline over the balanced schedule;
+    // x is read through the workspace's tensor maps of xU
+    template <typename T> int apply_tma(const OpPool<T> &pool, int use_sp, double *y) {
+        const int rc = R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1));
+        auto go = [&](auto rc_tag) {
+            constexpr int RCT = decltype(rc_tag)::value;
+            k_apply_tma<T, RCT><<<p->sched_ctas, APPLY_THREADS, apply_smem_bytes(RCT, APPLY_NS), st>>>(
+                pool.maps.template as<CUtensorMap>(), ws.xmaps[sizeof(T) == 8 ? 1 : 0].template as<CUtensorMap>(),
+                use_sp, sd, p->d_sched_ptr.as<int32_t>(), p->d_sched_items.as<int32_t>(), y, R, gate, S.err);
+        };
+        switch (rc) {
+            case 8: go(std::integral_constant<int, 8>{}); break;
+            case 4: go(std::integral_constant<int, 4>{}); break;
+            case 2: go(std::integral_constant<int, 2>{}); break;
+            default: go(std::integral_constant<int, 1>{}); break;
+        }
+        note_launch();
+        return 1;
+    }
+
     // y = S^+ x (use_sp = 1) or S x (use_sp = 0) on every subdomain
     template <typename T> void symv(const OpPool<T> &pool, int use_sp, const T *x, double *y) {
         if (p->n_u == 0) return;
@@ -697,7 +728,9 @@ struct Runner {
             NLF_CUDA(cudaEventCreate(&slot.b));
             NLF_CUDA(cudaEventRecordWithFlags(slot.a, st, rec_flags));
         }
-        const int launches = rows<T, ROWS_APPLY>(base, use_sp, x, nullptr, nullptr, y, p->d_items, p->item_off);
+        const int launches = (p->opt.batched && p->sched_ctas > 0)
+                                 ? apply_tma<T>(pool, use_sp, y)
+                                 : rows<T, ROWS_APPLY>(base, use_sp, x, nullptr, nullptr, y, p->d_items, p->item_off);
         if (timed) {
             NLF_CUDA(cudaEventRecordWithFlags(slot.b, st, rec_flags));
             double bytes = 0;
@@ -856,8 +889,9 @@ struct Runner {
                 const PcgGraph &g = while_graph<T>(pool, tol, max_it);
                 NLF_CUDA(cudaMemsetAsync(S.loops, 0, sizeof(int), st));
                 NLF_CUDA(cudaGraphLaunch(g.exec, st));
-                NLF_CUDA(cudaMemcpyAsync(ws.host_flag.data(), S.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                NLF_CUDA(cudaMemcpyAsync(ws.host_flag.data(), S.n_active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
                 NLF_CUDA(cudaStreamSynchronize(st));
+                check_waits();
                 n_active = ws.host_flag[0];
                 eager_launches += (int64_t)ws.host_flag[1] * g.body_launches;
                 done = max_it + 1;      // skip the chunked loop below
@@ -882,8 +916,9 @@ struct Runner {
                     for (int i = 0; i < chunk; ++i) iteration<T>(pool, tol, max_it);
                 }
                 done += chunk;
-                NLF_CUDA(cudaMemcpyAsync(ws.host_flag.data(), S.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+                NLF_CUDA(cudaMemcpyAsync(ws.host_flag.data(), S.n_active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
                 NLF_CUDA(cudaStreamSynchronize(st));
+                check_waits();
                 harvest(graph_slots, false);
                 harvest(eager_slots, true);
                 n_active = ws.host_flag[0];
@@ -939,6 +974,23 @@ struct Runner {
 
 }  // namespace
 
+namespace {
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        NLF_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q));
+        if (!f || q != cudaDriverEntryPointSuccess) fail(NLFETI_E_CUDA, "cuTensorMapEncodeTiled is not available");
+        fn = reinterpret_cast<EncodeTiledFn>(f);
+    }
+    return fn;
+}
+}  // namespace
+
 void SolveWS::drop_graphs() {
     if (graphs.empty()) return;
     // a graph may still run on the workspace's stream
@@ -970,6 +1022,27 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     A(fU, nu); A(yU, nu); A(uU, nu);
     A(xU, std::max<int64_t>(1, p->n_up));   // apply layout (padding zeroed by the gathers)
     NLF_CUDA(cudaMemsetAsync(xU.p, 0, xU.bytes, async_stream ? async_stream : c->stream));
+    // tensor maps of xU per subdomain (R rows of ld_gamma entries at offUp * R), read as FP32
+    // and as FP64, tiles of rc rows as the apply kernel of this R uses
+    {
+        const int rcb = R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1));
+        for (int e = 0; e < 2; ++e) {
+            const int es = e ? 8 : 4;
+            std::vector<CUtensorMap> maps(std::max(1, p->K));
+            std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+            for (int k = 0; k < p->K; ++k) {
+                const SubdomainDesc &d = p->sd[k];
+                if (d.nG == 0) continue;
+                const unsigned char *b = xU.as<unsigned char>() + d.offUp * R * es;
+                if (encode_apply_map(encode_tiled(), &maps[k], b, d.ldG, R, es, rcb) != CUDA_SUCCESS)
+                    fail(NLFETI_E_CUDA, "cuTensorMapEncodeTiled failed for the apply input");
+            }
+            alloc(xmaps[e], sizeof(CUtensorMap) * maps.size());
+            NLF_CUDA(cudaMemcpyAsync(xmaps[e].p, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                                     async_stream ? async_stream : c->stream));
+            NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
+        }
+    }
     A(ftil, nv); A(res, nv); A(u, nv); A(du, nv);
     alloc(uhl, sizeof(float) * 2 * std::max<int64_t>(1, p->n_vp) * R);
     A(F, nd);
@@ -1094,7 +1167,49 @@ void apply_operator(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int op, int
     if (precision == 0) go(p->op64, double{});
     else go(p->op32, float{});
     NLF_CUDA(cudaGetLastError());
+    NLF_CUDA(cudaMemcpyAsync(ws.host_flag.data(), run.S.n_active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     NLF_CUDA(cudaStreamSynchronize(st));
+    run.check_waits();
 }
+
+int apply_tma_ctas() {
+    int dev = 0, sms = 0;
+    NLF_CUDA(cudaGetDevice(&dev));
+    NLF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int per_sm = 1 << 20;
+    auto fit = [&](auto kern, int rc) {
+        const int smem = apply_smem_bytes(rc, APPLY_NS);
+        NLF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int b = 0;
+        NLF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, APPLY_THREADS, smem));
+        per_sm = std::min(per_sm, b);
+    };
+    fit(k_apply_tma<float, 1>, 1); fit(k_apply_tma<float, 2>, 2); fit(k_apply_tma<float, 4>, 4);
+    fit(k_apply_tma<float, 8>, 8); fit(k_apply_tma<double, 1>, 1); fit(k_apply_tma<double, 2>, 2);
+    fit(k_apply_tma<double, 4>, 4); fit(k_apply_tma<double, 8>, 8);
+    if (per_sm < 1) fail(NLFETI_E_CUDA, "the interface apply does not fit on an SM");
+    return sms * per_sm;
+}
+
+
+template <typename T> void encode_apply_maps(nlfeti_problem *p, OpPool<T> &pool) {
+    std::vector<CUtensorMap> maps(2 * std::max(1, p->K));
+    std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+    for (int k = 0; k < p->K; ++k) {
+        const SubdomainDesc &d = p->sd[k];
+        if (d.nG == 0) continue;                      // no work items
+        for (int sp = 0; sp < 2; ++sp) {
+            const T *m = (sp ? pool.Sp.template as<T>() + d.offSp : pool.S.template as<T>() + d.offS);
+            const CUresult r = encode_apply_map(encode_tiled(), &maps[2 * k + sp], m, d.ldG, d.nG, (int)sizeof(T));
+            if (r != CUDA_SUCCESS) fail(NLFETI_E_CUDA, "cuTensorMapEncodeTiled failed for an interface operator");
+        }
+    }
+    pool.maps.alloc(p->ctx, sizeof(CUtensorMap) * maps.size());
+    NLF_CUDA(cudaMemcpyAsync(pool.maps.p, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                             p->ctx->stream));
+    NLF_CUDA(cudaStreamSynchronize(p->ctx->stream));
+}
+template void encode_apply_maps<float>(nlfeti_problem *, OpPool<float> &);
+template void encode_apply_maps<double>(nlfeti_problem *, OpPool<double> &);
 
 }  // namespace nlf

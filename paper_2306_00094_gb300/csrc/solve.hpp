@@ -21,6 +21,7 @@ struct SolveWS {
     int R = 0;
     DevMem lam, r, w, z, y, pv, q, d, cvec, dlam;      // Lambda space (FP64)
     DevMem fU, yU, uU, xU;                              // U space
+    DevMem xmaps[2];                                    // tensor maps of xU per subdomain (FP32, FP64)
     DevMem ftil, res, u, du;                            // concatenated subdomain vectors
     DevMem uhl;                                         // u as FP32 hi / lo pairs, padded layout
     DevMem F;                                           // global load vector per dof

@@ -470,6 +470,7 @@ template <typename T> void factor_ops(nlfeti_problem *p, OpPool<T> &pool) {
     int flag = 0;
     NLF_CUDA(cudaMemcpy(&flag, p->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) fail(NLFETI_E_NOT_SPD, "a pivot block of a subdomain operator was not positive definite");
+    encode_apply_maps<T>(p, pool);
     pool.ready = true;
 }
 
