@@ -35,7 +35,8 @@ def _stale():
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(SRC, "*.hpp")) + glob.glob(os.path.join(HERE, "..", "include", "*.h"))
+    deps = (sources() + glob.glob(os.path.join(SRC, "*.hpp")) + glob.glob(os.path.join(SRC, "*.cuh"))
+            + glob.glob(os.path.join(HERE, "..", "include", "*.h")))
     return any(os.path.getmtime(f) > t for f in deps)
 
 
