@@ -178,6 +178,28 @@ nlfeti_status nlfeti_get_operator(const nlfeti_problem *p, int k, int which, int
  * 3 = S^+ (U -> U), 4 = S (U -> U). */
 nlfeti_status nlfeti_apply(nlfeti_problem *p, int op, int precision, int nrhs, const double *in, double *out);
 
+/* No-allocation interface apply (the paper has no counterpart: an integration entry point).
+ * d_out = blockdiag_k(M_k) d_in with M_k = S_k^+ (which 0) or S_k (which 1), the operators of
+ * the given precision (0 FP64, 1 FP32; factored before).  d_in, d_out: device arrays,
+ * column-major n_u x nrhs (FP64), U ordered as in nlfeti_apply; d_out is written, d_in only
+ * read.  For callers that must not allocate device memory during the call (a fixed memory
+ * plan frozen after warm-up, a framework that forbids allocations between its own, an
+ * allocator that would synchronise the device): the call makes no cudaMalloc, cudaFree or
+ * allocator-callback call.  It stages its input in a scratch array that is part of the
+ * library's device image, NLFETI_NOALLOC_SCRATCH_BYTES per device; it needs
+ * n_up * nrhs * (8 for precision 0, 4 for precision 1) bytes of it, n_up being the sum over
+ * subdomains of n_gamma rounded up to a multiple of 8.  Larger requests return
+ * NLFETI_E_INVALID (nothing launched; nlfeti_last_error gives the sizes).  All calls on a
+ * device share that scratch: calls that can overlap in time (other threads, other streams)
+ * race, so the caller serialises them.  Nothing in it has to start at zero.  The first call
+ * on a device resolves the scratch address with that device current (once); a caller that
+ * captures streams makes that first call before capturing.  Asynchronous on the context
+ * stream, ordered after the caller's stream and before its later work (as
+ * nlfeti_solve_device). */
+#define NLFETI_NOALLOC_SCRATCH_BYTES (8u << 20)
+nlfeti_status nlfeti_apply_schur_noalloc(nlfeti_problem *p, int which, int precision, int nrhs, const double *d_in,
+                                         double *d_out);
+
 /* Kernel accounting of a problem's solves (for roofline reporting).  With profiling on,
  * every launch of the dense interface apply (the per-iteration products with S_k^+ and
  * S_k) is bracketed by CUDA events on the library stream, also inside captured graphs.

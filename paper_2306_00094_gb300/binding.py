@@ -24,7 +24,7 @@ EXPORTED = ["nlfeti_default_options", "nlfeti_create", "nlfeti_destroy", "nlfeti
             "nlfeti_problem_destroy", "nlfeti_problem_info", "nlfeti_problem_set_options", "nlfeti_factor",
             "nlfeti_solve", "nlfeti_solve_device", "nlfeti_get_decomposition", "nlfeti_get_operator",
             "nlfeti_apply", "nlfeti_set_profiling", "nlfeti_get_profile", "nlfeti_server_create", "nlfeti_submit",
-            "nlfeti_wait", "nlfeti_server_destroy"]
+            "nlfeti_wait", "nlfeti_server_destroy", "nlfeti_apply_schur_noalloc"]
 
 
 class NlfetiError(RuntimeError):
@@ -113,6 +113,7 @@ def load(build_if_missing: bool = True):
         "nlfeti_submit": (i32, [vp, vp, i32, i32, vp, vp, C.POINTER(C.c_uint64)]),
         "nlfeti_wait": (i32, [vp, C.c_uint64, i32, vp, C.POINTER(Stats)]),
         "nlfeti_server_destroy": (None, [vp]),
+        "nlfeti_apply_schur_noalloc": (i32, [vp, i32, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -287,6 +288,16 @@ class Problem:
         out = np.zeros((n, n), np.float64)
         self.ctx.check(self.ctx.lib.nlfeti_get_operator(self.h, int(k), int(which), int(precision), out.ctypes.data))
         return out
+
+    def apply_schur_noalloc(self, which, precision, d_in, d_out, nrhs, raise_on_error=True):
+        """S^+ (which 0) or S (which 1) on device arrays (ints or torch tensors; column-major
+        n_u x nrhs = contiguous (nrhs, n_u)) without device allocation; returns the status."""
+        ptr = lambda t: t if isinstance(t, int) else t.data_ptr()
+        code = self.ctx.lib.nlfeti_apply_schur_noalloc(self.h, int(which), int(precision), int(nrhs), ptr(d_in),
+                                                       ptr(d_out))
+        if raise_on_error:
+            self.ctx.check(code)
+        return code
 
     def apply(self, op, precision, X):
         X = np.asfortranarray(X, dtype=np.float64)
