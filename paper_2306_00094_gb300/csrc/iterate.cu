@@ -40,11 +40,6 @@ inline unsigned grid_for(int64_t n, int threads = 256) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
-template <typename T> __global__ void k_cast(const double *a, T *b, int64_t n) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        b[t] = (T)a[t];
-}
-
 __global__ void k_sub(const double *a, const double *b, double *out, int64_t n) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
         out[t] = a[t] - b[t];
@@ -81,18 +76,6 @@ __global__ void k_gather_bt(const int64_t *ptr, const int64_t *row, const double
 }
 
 // x_U = B_D^T v (cast to T)
-template <typename T>
-__global__ void k_gather_bdt(const int64_t *ptr, const int64_t *row, const double *val, const double *v, T *x,
-                             int64_t nu, int R) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
-        int64_t u = t / R;
-        int c = (int)(t % R);
-        double s = 0;
-        for (int64_t q = ptr[u]; q < ptr[u + 1]; ++q) s += val[q] * v[row[q] * R + c];
-        x[t] = (T)s;
-    }
-}
-
 // out = B y - c (c optional)
 __global__ void k_gather_b(const int64_t *Bp, const int64_t *Bm, const double *y, const double *cvec, double *out,
                            int64_t nl, int R) {
