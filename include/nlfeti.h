@@ -88,8 +88,9 @@ typedef struct {
  * precision: 0 = FP64 operators throughout ("plain"); 1 = FP32 subdomain operators
  *            with FP64 PCG vectors, coarse problem and iterative refinement ("mixed").
  * tol: PCG stop when ||P r||_2 <= tol ||P d||_2 per right-hand side (FP64 path);
- *      the mixed path uses inner_tol per refinement sweep and refine_tol on the
- *      relative nodal correction.
+ *      the mixed path uses inner_tol per refinement sweep and stops refining a
+ *      right-hand side when its relative nodal correction, or the remaining error that
+ *      correction predicts from the observed contraction, is within refine_tol.
  * batched: 1 = one launch per stage over all subdomains (graph-captured loop);
  *          0 = one launch per subdomain per stage, no graphs (baseline).
  * graph_loop (batched only): 1 = each PCG loop runs on the device as one graph with a

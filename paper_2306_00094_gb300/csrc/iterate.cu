@@ -1083,6 +1083,7 @@ void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rh
         NLF_CUDA(cudaMemsetAsync(ws.u.p, 0, sizeof(double) * nv * R, st));
         if (nl > 0) NLF_CUDA(cudaMemsetAsync(ws.lam.p, 0, sizeof(double) * nl * R, st));
         bool ok = false;
+        std::vector<double> prev_corr;
         for (int sw = 0; sw < std::max(1, p->opt.max_refine); ++sw) {
             if (sw == 0) {
                 NLF_CUDA(cudaMemcpyAsync(ws.res.p, ws.ftil.p, sizeof(double) * nv * R, cudaMemcpyDeviceToDevice, st));
@@ -1108,7 +1109,17 @@ void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rh
             NLF_CUDA(cudaMemcpyAsync(corr.data(), run.S.corr, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
             NLF_CUDA(cudaStreamSynchronize(st));
             s.rel_correction = *std::max_element(corr.begin(), corr.end());
-            if (s.rel_correction <= p->opt.refine_tol) { ok = true; break; }
+            // stop when every column's correction, or its estimated remaining error, is within
+            // refine_tol: with the observed contraction rho = corr_k / corr_{k-1} < 1/2 the
+            // corrections still to come sum to about corr_k rho / (1 - rho)
+            bool done = true;
+            for (int c = 0; c < R; ++c) {
+                if (corr[c] <= p->opt.refine_tol) continue;
+                const double rho = prev_corr.empty() || prev_corr[c] <= 0 ? 1.0 : corr[c] / prev_corr[c];
+                if (!(rho < 0.5 && corr[c] * rho / (1.0 - rho) <= p->opt.refine_tol)) done = false;
+            }
+            prev_corr = corr;
+            if (done) { ok = true; break; }
         }
         if (!ok) {
             k_output<<<grid_for(ndof * R), 256, 0, st>>>(ws.u.as<double>(), p->d_cp_ptr.as<int64_t>(), p->d_cp_pos.as<int64_t>(),
