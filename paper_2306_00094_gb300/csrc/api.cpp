@@ -268,16 +268,16 @@ void build_maps(nlfeti_problem *p) {
         p->item_off_o[k + 1] = (int)(items_o.size() / 2);
     }
     upload(c, p->d_items_o, items_o);
-    // persistent schedule of the bulk-copy apply: longest item first onto the least loaded CTA
-    // (cost = rows x streamed columns), then each CTA's list in (subdomain, row) order
-    {
-        const int G = std::max(1, std::min(apply_tma_ctas(), std::max(1, p->n_items)));
+    // persistent schedules of the bulk-copy apply (items over Gamma rows) and of the residual
+    // (items over all rows of A^k): longest item first onto the least loaded CTA (cost = rows x
+    // streamed columns), then each CTA's list in (subdomain, row) order
+    auto schedule = [&](const std::vector<int32_t> &its, int ctas, auto rows_cols, DevMem &dptr, DevMem &ditems) {
+        const int n = (int)(its.size() / 2);
+        const int G = std::max(1, std::min(ctas, std::max(1, n)));
         std::vector<std::pair<int64_t, int>> order;     // (cost, item)
-        for (int t = 0; t < p->n_items; ++t) {
-            const auto &s = p->sd[items[2 * t]];
-            const int rows = std::min(kApplyRows, s.nG - items[2 * t + 1]);
-            const int64_t cols = std::min<int64_t>(s.ldG, (s.nG + 7) / 8 * 8);
-            order.push_back({(int64_t)rows * cols + 256, t});
+        for (int t = 0; t < n; ++t) {
+            const auto rc = rows_cols(p->sd[its[2 * t]], its[2 * t + 1]);
+            order.push_back({(int64_t)rc.first * rc.second + 256, t});
         }
         std::stable_sort(order.begin(), order.end(), [](auto a, auto b) { return a.first > b.first; });
         std::vector<int64_t> load(G, 0);
@@ -290,18 +290,24 @@ void build_maps(nlfeti_problem *p) {
         std::vector<int32_t> sptr(G + 1, 0), sitems;
         for (int b = 0; b < G; ++b) {
             std::sort(lists[b].begin(), lists[b].end());
-            for (int t : lists[b]) { sitems.push_back(items[2 * t]); sitems.push_back(items[2 * t + 1]); }
+            for (int t : lists[b]) { sitems.push_back(its[2 * t]); sitems.push_back(its[2 * t + 1]); }
             sptr[b + 1] = (int32_t)(sitems.size() / 2);
         }
-        p->sched_ctas = G;
-        upload(c, p->d_sched_ptr, sptr);
-        upload(c, p->d_sched_items, sitems);
+        upload(c, dptr, sptr);
+        upload(c, ditems, sitems);
+        return G;
+    };
+    p->sched_ctas = schedule(items, apply_tma_ctas(), [](const SubdomainDesc &s, int r0) {
+        return std::make_pair(std::min(kApplyRows, s.nG - r0), std::min<int64_t>(s.ldG, (s.nG + 7) / 8 * 8));
+    }, p->d_sched_ptr, p->d_sched_items);
+    {
+        std::vector<int32_t> items_a;
+        for (int k = 0; k < K; ++k)
+            for (int r0 = 0; r0 < p->sd[k].nk; r0 += 32) { items_a.push_back(k); items_a.push_back(r0); }
+        p->rsched_ctas = items_a.empty() ? 0 : schedule(items_a, residual_tma_ctas(), [](const SubdomainDesc &s, int r0) {
+            return std::make_pair(std::min(32, s.nk - r0), (int64_t)s.ldM);
+        }, p->d_rsched_ptr, p->d_rsched_items);
     }
-    std::vector<int32_t> items_a;
-    for (int k = 0; k < K; ++k)
-        for (int r0 = 0; r0 < p->sd[k].nk; r0 += kResidualRows) { items_a.push_back(k); items_a.push_back(r0); }
-    p->n_items_a = (int)(items_a.size() / 2);
-    upload(c, p->d_items_a, items_a);
     std::vector<uint64_t> mask = d.elem_mask;
     upload(c, p->d_sd, p->sd);
     upload(c, p->d_xy, m.xy);

@@ -74,14 +74,14 @@ __device__ __forceinline__ void tile_g2s(void *dst, const CUtensorMap *map, int 
 }
 
 // tensor map of a row-major block (n rows of ld entries, 16-byte aligned rows) for tiles of
-// box_rows rows x APPLY_CB bytes: an operator (box_rows 32) or the R columns of x of one
+// box_rows rows x box_bytes bytes: an operator (box_rows 32) or the R columns of x of one
 // subdomain in the apply layout (box_rows RC); encode: the driver's cuTensorMapEncodeTiled
 template <typename Encode>
 inline CUresult encode_apply_map(Encode encode, CUtensorMap *map, const void *base, int ld, int n, int elem_size,
-                                 int box_rows = 32) {
+                                 int box_rows = 32, int box_bytes = APPLY_CB) {
     const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)n};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * (cuuint64_t)elem_size};
-    const cuuint32_t box[2] = {(cuuint32_t)(APPLY_CB / elem_size), (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)(box_bytes / elem_size), (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1u, 1u};
     return encode(map, elem_size == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2u,
                   const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

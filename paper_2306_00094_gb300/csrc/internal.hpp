@@ -123,7 +123,6 @@ struct SubdomainDesc {      // per subdomain, device resident (POD)
 };
 
 constexpr int kApplyRows = 32;          // rows of an interface-apply work item
-constexpr int kResidualRows = 16;       // rows of a refinement-residual work item
 
 template <typename T> struct OpPool {   // operators of one precision
     nlf::DevMem M, S, Sp;                // swept matrices, Schur complements, pseudo-inverses
@@ -131,6 +130,7 @@ template <typename T> struct OpPool {   // operators of one precision
     nlf::DevMem maps;                    // tensor maps of S_k and S_k^+ (2 per subdomain) for the apply
     nlf::DevMem Ahi, Alo;                // FP32 pool only: A^k = Ahi + Alo (FP32 pairs, swept-matrix layout),
                                          // for the double-single refinement residual
+    nlf::DevMem amaps;                   // FP32 pool only: tensor maps of Ahi and Alo (2 per subdomain)
     bool ready = false;
 };
 
@@ -182,12 +182,13 @@ struct nlfeti_problem {
     std::vector<int> item_off;           // K+1
     nlf::DevMem d_items_o;               // work items over Omega rows (back substitution)
     std::vector<int> item_off_o;         // K+1
-    nlf::DevMem d_items_a;               // kResidualRows-row work items over all rows of A^k (residual)
+    // persistent schedule of the refinement residual: 32-row items over all rows of A^k
+    int rsched_ctas = 0;
+    nlf::DevMem d_rsched_ptr, d_rsched_items;
     // persistent schedule of the bulk-copy interface apply: CTA b runs the work items
     // sched_items[sched_ptr[b] .. sched_ptr[b+1]) (pairs (k, first row)), balanced by cost
     int sched_ctas = 0;
     nlf::DevMem d_sched_ptr, d_sched_items;
-    int n_items_a = 0;
     nlf::DevMem d_flag;                  // device status words
     OpPool<double> op64;
     OpPool<float> op32;
@@ -212,8 +213,9 @@ void stream_leave(nlfeti_ctx *c);
 // a live problem or server keeps its context alive
 void ctx_attach(nlfeti_ctx *c);
 void ctx_detach(nlfeti_ctx *c);
-// CTAs of the bulk-copy interface apply that fit on the device at once (all instantiations)
+// CTAs of the bulk-copy interface apply / refinement residual that fit on the device at once
 int apply_tma_ctas();
+int residual_tma_ctas();
 // tensor maps of a pool's S_k and S_k^+ for the bulk-copy apply (after the factorization)
 template <typename T> void encode_apply_maps(nlfeti_problem *p, OpPool<T> &pool);
 }  // namespace nlf

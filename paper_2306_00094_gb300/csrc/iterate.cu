@@ -112,6 +112,7 @@ __global__ void k_gather_bd(const int64_t *ptr, const int64_t *col, const double
 
 #include "rows.cuh"
 #include "apply_tma.cuh"
+#include "residual_tma.cuh"
 
 __global__ void k_scatter_u(const int64_t *u2v, const double *uU, double *v, int64_t nu, int R) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
@@ -506,19 +507,22 @@ __global__ void k_update_lr(const double *p, const double *q, const double *eta,
 
 // ====================================================================== host orchestration
 
+// the workspace's error word (set by a device wait that ran out)
+inline int *ws_err(SolveWS &ws, int R) { return reinterpret_cast<int *>(ws.scal.as<double>() + 7 * R) + 2 * R + 3; }
+
 // ws.res = ftil - A^k u - [0; B^T lambda] on every subdomain (double-single, FP32 pool pairs):
-// u is first split into FP32 hi / lo pairs in the padded layout, then the row kernel runs
+// u is first split into FP32 hi / lo pairs in the padded layout, then the pipeline kernel runs
 void residual_ds(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, const double *lam) {
-    if (p->n_items_a == 0) return;
+    if (p->rsched_ctas == 0) return;
     const OpPool<float> &pool = p->op32;
     float *uh = ws.uhl.as<float>(), *ul = uh + p->n_vp * R;
     k_split_u<<<dim3(p->K, R), 256, 0, st>>>(ws.u.as<double>(), p->d_sd.as<SubdomainDesc>(), uh, ul, R);
     auto go = [&](auto rc_tag) {
         constexpr int RC = decltype(rc_tag)::value;
-        k_residual_ds<RC><<<p->n_items_a, 256, 0, st>>>(pool.Ahi.as<float>(), pool.Alo.as<float>(),
-                                                       p->d_sd.as<SubdomainDesc>(), p->d_items_a.as<int32_t>(),
-                                                       ws.ftil.as<double>(), uh, ul, p->d_Bt_ptr.as<int64_t>(),
-                                                       p->d_Bt_row.as<int64_t>(), lam, ws.res.as<double>(), R);
+        k_residual_tma<RC><<<p->rsched_ctas, RES_THREADS, res_smem_bytes(RC), st>>>(
+            pool.amaps.as<CUtensorMap>(), ws.umaps.as<CUtensorMap>(), p->d_sd.as<SubdomainDesc>(),
+            p->d_rsched_ptr.as<int32_t>(), p->d_rsched_items.as<int32_t>(), ws.ftil.as<double>(),
+            p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), lam, ws.res.as<double>(), R, ws_err(ws, R));
     };
     if (R >= 8) go(std::integral_constant<int, 8>{});
     else if (R >= 4) go(std::integral_constant<int, 4>{});
@@ -1004,6 +1008,7 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     A(lam, nl); A(r, nl); A(w, nl); A(z, nl); A(y, nl); A(pv, nl); A(q, nl); A(d, nl); A(cvec, nl); A(dlam, nl);
     A(fU, nu); A(yU, nu); A(uU, nu);
     A(xU, std::max<int64_t>(1, p->n_up));   // apply layout (padding zeroed by the gathers)
+    alloc(uhl, sizeof(float) * 2 * std::max<int64_t>(1, p->n_vp) * R);
     NLF_CUDA(cudaMemsetAsync(xU.p, 0, xU.bytes, async_stream ? async_stream : c->stream));
     // tensor maps of xU per subdomain (R rows of ld_gamma entries at offUp * R), read as FP32
     // and as FP64, tiles of rc rows as the apply kernel of this R uses
@@ -1025,9 +1030,23 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
                                      async_stream ? async_stream : c->stream));
             NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
         }
+        // uh and ul (FP32, R rows of ld_M entries at offVp * R each) for the refinement residual
+        std::vector<CUtensorMap> um(2 * std::max(1, p->K));
+        std::memset(um.data(), 0, sizeof(CUtensorMap) * um.size());
+        const float *uh = uhl.as<float>(), *ul = uh + std::max<int64_t>(1, p->n_vp) * R;
+        for (int k = 0; k < p->K; ++k) {
+            const SubdomainDesc &d = p->sd[k];
+            if (d.nk == 0) continue;
+            if (encode_apply_map(encode_tiled(), &um[2 * k], uh + d.offVp * R, d.ldM, R, 4, rcb, RES_CB) != CUDA_SUCCESS ||
+                encode_apply_map(encode_tiled(), &um[2 * k + 1], ul + d.offVp * R, d.ldM, R, 4, rcb, RES_CB) != CUDA_SUCCESS)
+                fail(NLFETI_E_CUDA, "cuTensorMapEncodeTiled failed for the residual input");
+        }
+        alloc(umaps, sizeof(CUtensorMap) * um.size());
+        NLF_CUDA(cudaMemcpyAsync(umaps.p, um.data(), sizeof(CUtensorMap) * um.size(), cudaMemcpyHostToDevice,
+                                 async_stream ? async_stream : c->stream));
+        NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
     }
     A(ftil, nv); A(res, nv); A(u, nv); A(du, nv);
-    alloc(uhl, sizeof(float) * 2 * std::max<int64_t>(1, p->n_vp) * R);
     A(F, nd);
     A(gco, nco * PSPLIT); A(gsum, nco); A(alpha, nco);
     alloc(partial, sizeof(double) * RED_BLOCKS * R);
@@ -1185,6 +1204,23 @@ int apply_tma_ctas() {
     return sms * per_sm;
 }
 
+int residual_tma_ctas() {
+    int dev = 0, sms = 0;
+    NLF_CUDA(cudaGetDevice(&dev));
+    NLF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int per_sm = 1 << 20;
+    auto fit = [&](auto kern, int rc) {
+        const int smem = res_smem_bytes(rc);
+        NLF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int b = 0;
+        NLF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, RES_THREADS, smem));
+        per_sm = std::min(per_sm, b);
+    };
+    fit(k_residual_tma<1>, 1); fit(k_residual_tma<2>, 2); fit(k_residual_tma<4>, 4); fit(k_residual_tma<8>, 8);
+    if (per_sm < 1) fail(NLFETI_E_CUDA, "the refinement residual does not fit on an SM");
+    return sms * per_sm;
+}
+
 
 template <typename T> void encode_apply_maps(nlfeti_problem *p, OpPool<T> &pool) {
     std::vector<CUtensorMap> maps(2 * std::max(1, p->K));
@@ -1201,6 +1237,23 @@ template <typename T> void encode_apply_maps(nlfeti_problem *p, OpPool<T> &pool)
     pool.maps.alloc(p->ctx, sizeof(CUtensorMap) * maps.size());
     NLF_CUDA(cudaMemcpyAsync(pool.maps.p, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
                              p->ctx->stream));
+    if constexpr (std::is_same<T, float>::value) {
+        // A^k as FP32 pairs (n_k rows of ld_M) for the refinement residual
+        std::vector<CUtensorMap> am(2 * std::max(1, p->K));
+        std::memset(am.data(), 0, sizeof(CUtensorMap) * am.size());
+        for (int k = 0; k < p->K; ++k) {
+            const SubdomainDesc &d = p->sd[k];
+            if (d.nk == 0) continue;
+            if (encode_apply_map(encode_tiled(), &am[2 * k], pool.Ahi.template as<float>() + d.offM, d.ldM, d.nk, 4, 32,
+                                 RES_CB) != CUDA_SUCCESS ||
+                encode_apply_map(encode_tiled(), &am[2 * k + 1], pool.Alo.template as<float>() + d.offM, d.ldM, d.nk, 4, 32,
+                                 RES_CB) != CUDA_SUCCESS)
+                fail(NLFETI_E_CUDA, "cuTensorMapEncodeTiled failed for the residual operator");
+        }
+        pool.amaps.alloc(p->ctx, sizeof(CUtensorMap) * am.size());
+        NLF_CUDA(cudaMemcpyAsync(pool.amaps.p, am.data(), sizeof(CUtensorMap) * am.size(), cudaMemcpyHostToDevice,
+                                 p->ctx->stream));
+    }
     NLF_CUDA(cudaStreamSynchronize(p->ctx->stream));
 }
 template void encode_apply_maps<float>(nlfeti_problem *, OpPool<float> &);

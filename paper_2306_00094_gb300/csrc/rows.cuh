@@ -230,89 +230,3 @@ __global__ void k_split_u(const double *u, const SubdomainDesc *sd, float *uh, f
         ul[o] = (float)(v - (double)h);
     }
 }
-
-// Refinement residual of the torn system (eq. discreteKKT) with FP64 accuracy on the FP32
-// pipes: r = f~ - A^k u - [0; B_k^T lambda] per subdomain.  A^k is read as FP32 pairs
-// (hi + lo) and u as FP32 pairs (uh + ul, from k_split_u).  For each product the lane keeps
-// hi*uh rounded (p) and its exact rounding error (fma), adds p to a running FP32 sum with
-// TwoSum (exact error), and gathers the errors and the cross terms hi*ul + lo*uh in a second
-// FP32 sum; lo*ul (2^-48 relative) is dropped.  The two sums of each lane are added in FP64
-// and reduced across the warp in FP64.  Relative to sum_j |a_ij u_j| the result is accurate
-// to a few 1e-13, the limit being the FP32 sum of the small terms over a lane's columns.
-// Work item = (subdomain, kResidualRows rows of A^k); warp w owns rows 2w, 2w + 1 and
-// streams their columns with 16-byte loads; u is read in place (L1).
-template <int RC>
-__global__ void __launch_bounds__(256, 3) k_residual_ds(const float *Ahi, const float *Alo, const SubdomainDesc *sd,
-                                                        const int32_t *items, const double *f, const float *uh,
-                                                        const float *ul, const int64_t *bt_ptr,
-                                                        const int64_t *bt_row, const double *lam, double *r, int R) {
-    static_assert(kResidualRows == 16, "8 warps x 2 rows");
-    const int k = items[2 * blockIdx.x], row0 = items[2 * blockIdx.x + 1];
-    const SubdomainDesc d = sd[k];
-    const int n = d.nk, ld = d.ldM;
-    const int ncp = min(ld, (n + 7) / 8 * 8);
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int ib = row0 + warp * 2;
-    const int64_t roff0 = d.offM + (int64_t)min(ib, n - 1) * ld, roff1 = d.offM + (int64_t)min(ib + 1, n - 1) * ld;
-    for (int c0 = 0; c0 < R; c0 += RC) {
-        const int rc = min(RC, R - c0);
-        const int64_t xo = d.offVp * R + (int64_t)c0 * ld;
-        float sh[2][RC], sl[2][RC];
-#pragma unroll
-        for (int q = 0; q < 2; ++q)
-#pragma unroll
-            for (int c = 0; c < RC; ++c) { sh[q][c] = 0.f; sl[q][c] = 0.f; }
-        if (ib < n) {
-            for (int l = lane * 4; l < ncp; l += 128) {
-                const float4 mh[2] = {__ldcs(reinterpret_cast<const float4 *>(Ahi + roff0 + l)),
-                                      __ldcs(reinterpret_cast<const float4 *>(Ahi + roff1 + l))};
-                const float4 ml[2] = {__ldcs(reinterpret_cast<const float4 *>(Alo + roff0 + l)),
-                                      __ldcs(reinterpret_cast<const float4 *>(Alo + roff1 + l))};
-#pragma unroll
-                for (int c = 0; c < RC; ++c) {
-                    if (c >= rc) continue;
-                    const float4 a4 = __ldg(reinterpret_cast<const float4 *>(uh + xo + (int64_t)c * ld + l));
-                    const float4 b4 = __ldg(reinterpret_cast<const float4 *>(ul + xo + (int64_t)c * ld + l));
-                    const float xh[4] = {a4.x, a4.y, a4.z, a4.w}, xl[4] = {b4.x, b4.y, b4.z, b4.w};
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const float ah[4] = {mh[q].x, mh[q].y, mh[q].z, mh[q].w};
-                        const float al[4] = {ml[q].x, ml[q].y, ml[q].z, ml[q].w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            // explicit round-to-nearest intrinsics: no contraction into fma
-                            const float p = __fmul_rn(ah[e], xh[e]);
-                            const float pe = fmaf(ah[e], xh[e], -p);            // hi*uh - p exactly
-                            const float s = __fadd_rn(sh[q][c], p);            // TwoSum(sh, p)
-                            const float bb = __fsub_rn(s, sh[q][c]);
-                            const float se = __fadd_rn(__fsub_rn(sh[q][c], __fsub_rn(s, bb)), __fsub_rn(p, bb));
-                            sh[q][c] = s;
-                            sl[q][c] = __fadd_rn(sl[q][c], __fadd_rn(se, fmaf(ah[e], xl[e], fmaf(al[e], xh[e], pe))));
-                        }
-                    }
-                }
-            }
-        }
-        constexpr int V = 2 * RC;
-        double v[V];
-#pragma unroll
-        for (int q = 0; q < 2; ++q)
-#pragma unroll
-            for (int c = 0; c < RC; ++c) v[q * RC + c] = (double)sh[q][c] + (double)sl[q][c];
-        const double tot = warp_reduce_scatter<double, V>(v, lane);
-        constexpr int G = 32 / V;
-        const int idx = lane / G, q = idx / RC, c = idx % RC, i = ib + q;
-        if (lane % G == 0 && c < rc && i < n) {
-            const int cc = c0 + c;
-            double res = f[(d.offV + i) * R + cc] - tot;
-            if (i >= d.nO && lam) {
-                const int64_t ui = d.offU + (i - d.nO);
-                for (int64_t t = bt_ptr[ui]; t < bt_ptr[ui + 1]; ++t) {
-                    const int64_t rr = bt_row[t];
-                    res -= rr > 0 ? lam[(rr - 1) * R + cc] : -lam[(-rr - 1) * R + cc];
-                }
-            }
-            r[(d.offV + i) * R + cc] = res;
-        }
-    }
-}

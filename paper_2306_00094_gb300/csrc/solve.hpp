@@ -24,6 +24,7 @@ struct SolveWS {
     DevMem xmaps[2];                                    // tensor maps of xU per subdomain (FP32, FP64)
     DevMem ftil, res, u, du;                            // concatenated subdomain vectors
     DevMem uhl;                                         // u as FP32 hi / lo pairs, padded layout
+    DevMem umaps;                                       // tensor maps of uh and ul per subdomain
     DevMem F;                                           // global load vector per dof
     DevMem gco, gsum, alpha;                            // coarse space
     DevMem partial, partial2, scal;                     // reductions and PCG scalars
