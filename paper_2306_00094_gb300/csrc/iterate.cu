@@ -436,47 +436,46 @@ __global__ void __launch_bounds__(256) k_proj_g(const SubdomainDesc *sd, const i
     if (threadIdx.x == 0) *counter = 0u;
 }
 
-// max |a| and max |b| per column into partials
-__global__ void __launch_bounds__(RED_THREADS) k_absmax_partial(const double *a, const double *b, int64_t n, int R,
-                                                                 double *pa, double *pb) {
+// refinement update u += du with corr = max |du| / max |u| per column: grid (row blocks,
+// right-hand sides), per-block maxima, the last block to arrive writes corr (maxima do not
+// depend on the order)
+__global__ void __launch_bounds__(RED_THREADS) k_refine_update(double *u, const double *du, int64_t n, int R,
+                                                                double *pa, double *pb, PcgScalars s) {
     __shared__ double ra[RED_THREADS / 32], rb[RED_THREADS / 32];
-    for (int c = 0; c < R; ++c) {
-        double ma = 0, mb = 0;
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-            ma = fmax(ma, fabs(a[i * R + c]));
-            mb = fmax(mb, fabs(b[i * R + c]));
+    const int c = blockIdx.y, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    double ma = 0, mb = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = du[i * R + c], v = u[i * R + c] + d;
+        u[i * R + c] = v;
+        ma = fmax(ma, fabs(d));
+        mb = fmax(mb, fabs(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ma = fmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+        mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    }
+    if (lane == 0) { ra[warp] = ma; rb[warp] = mb; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0, y = 0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) { x = fmax(x, ra[w]); y = fmax(y, rb[w]); }
+        pa[(int64_t)blockIdx.x * R + c] = x;
+        pb[(int64_t)blockIdx.x * R + c] = y;
+    }
+    if (!arrive_last(s.counter)) return;
+    for (int cc = warp; cc < R; cc += RED_THREADS / 32) {
+        double x = 0, y = 0;
+        for (int bl = lane; bl < (int)gridDim.x; bl += 32) {
+            x = fmax(x, __ldcg(pa + (int64_t)bl * R + cc));
+            y = fmax(y, __ldcg(pb + (int64_t)bl * R + cc));
         }
         for (int o = 16; o > 0; o >>= 1) {
-            ma = fmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
-            mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+            x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+            y = fmax(y, __shfl_xor_sync(0xffffffffu, y, o));
         }
-        __syncthreads();
-        if (threadIdx.x % 32 == 0) { ra[threadIdx.x / 32] = ma; rb[threadIdx.x / 32] = mb; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double x = 0, y = 0;
-            for (int w = 0; w < RED_THREADS / 32; ++w) { x = fmax(x, ra[w]); y = fmax(y, rb[w]); }
-            pa[(int64_t)blockIdx.x * R + c] = x;
-            pb[(int64_t)blockIdx.x * R + c] = y;
-        }
+        if (lane == 0) s.corr[cc] = y > 0 ? x / y : (x > 0 ? 1.0 : 0.0);
     }
-}
-
-// corr = max |du| / max |u| per column from the RED_BLOCKS partial maxima (warp per column)
-__global__ void k_rel_correction(const double *pa, const double *pb, int R, PcgScalars s) {
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int c = warp; c < R; c += blockDim.x / 32) {
-        double a = 0, b = 0;
-        for (int bl = lane; bl < RED_BLOCKS; bl += 32) {
-            a = fmax(a, pa[(int64_t)bl * R + c]);
-            b = fmax(b, pb[(int64_t)bl * R + c]);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
-            b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
-        }
-        if (lane == 0) s.corr[c] = b > 0 ? a / b : (a > 0 ? 1.0 : 0.0);
-    }
+    if (threadIdx.x == 0) *s.counter = 0u;
 }
 
 __global__ void k_update_p(const double *y, const double *beta, const int *active, double *p, int64_t n, int R) {
@@ -551,6 +550,7 @@ struct Runner {
     // inside PCG iterations: the interface applies and their gathers return at once when no
     // right-hand side is active any more (every later update is masked by the active flags)
     const int *gate = nullptr;
+    int64_t loop_body_launches = 0;     // kernels per iteration of the last device-side loop
     // the WHILE node of the graph loop being captured (set by k_update_lr)
     cudaGraphConditionalHandle cond = 0;
     bool use_cond = false;
@@ -837,8 +837,7 @@ struct Runner {
 
     // one FETI pass on subdomain loads ws.res; constraint right-hand side ws.cvec when with_c.
     // Output: ws.du (subdomain vectors) and ws.dlam.
-    template <typename T> PassInfo pass(const OpPool<T> &pool, double tol, int max_it, bool with_c) {
-        PassInfo info;
+    template <typename T> void pass(const OpPool<T> &pool, double tol, int max_it, bool with_c) {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         const double *f = ws.res.as<double>();
         const bool batched = p->opt.batched != 0;
@@ -876,12 +875,8 @@ struct Runner {
                 const PcgGraph &g = while_graph<T>(pool, tol, max_it);
                 NLF_CUDA(cudaMemsetAsync(S.loops, 0, sizeof(int), st));
                 NLF_CUDA(cudaGraphLaunch(g.exec, st));
-                NLF_CUDA(cudaMemcpyAsync(ws.host_flag.data(), S.n_active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-                NLF_CUDA(cudaStreamSynchronize(st));
-                check_waits();
-                n_active = ws.host_flag[0];
-                eager_launches += (int64_t)ws.host_flag[1] * g.body_launches;
-                done = max_it + 1;      // skip the chunked loop below
+                loop_body_launches = g.body_launches;   // counted when the scalars are read back
+                done = max_it + 1;                      // skip the chunked loop below
             } else if (batched) {
                 // host-checked chunks of iterations (profiling: with event-timed applies, as
                 // event nodes are not allowed inside a WHILE body)
@@ -913,35 +908,19 @@ struct Runner {
             }
             if (exec) NLF_CUDA(cudaGraphExecDestroy(exec));
             drop(graph_slots);
-            // alpha from a fresh residual d - F lambda (eq. forAlpha)
-            applyF<T>(pool, lam, ws.q.as<double>());
-            k_sub<<<grid_for(nl * R), 256, 0, st>>>(ws.d.as<double>(), ws.q.as<double>(), ws.r.as<double>(), nl * R);
-            note_launch();
-            // u_G = S^+ (fU - B^T lambda) - Z alpha  (eq. forU)
-            k_gather_bt<double><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(),
-                                                                  lam, ws.uU.as<double>(), nu, R);
-                                                                  note_launch();
-            k_sub<<<grid_for(nu * R), 256, 0, st>>>(ws.fU.as<double>(), ws.uU.as<double>(), ws.uU.as<double>(), nu * R);
-            note_launch();
-            k_to_apply<T><<<grid_for(nu * R), 256, 0, st>>>(ws.uU.as<double>(), x, sd, p->d_u2sub.as<int32_t>(), nu, R);
+            // alpha from the PCG residual r = d - F lambda, kept current by the recurrence
+            // (eq. forAlpha); u_G = S^+ (fU - B^T lambda) - Z alpha  (eq. forU)
+            k_gather_sub_apply<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(),
+                                                                   lam, ws.fU.as<double>(), x, sd,
+                                                                   p->d_u2sub.as<int32_t>(), nu, R);
             note_launch();
             symv<T>(pool, 1, x, ws.uU.as<double>());
             if (p->n_co > 0) {
                 coarse_alpha(ws.r.as<double>(), 0);
                 k_apply_zalpha<<<grid_for(nu * R), 256, 0, st>>>(sd, p->d_u2sub.as<int32_t>(), p->d_Z.as<double>(),
                                                                  ws.alpha.as<double>(), -1.0, ws.uU.as<double>(), nu, R);
-                                                                 note_launch();
+                note_launch();
             }
-            std::vector<int> it(R);
-            std::vector<double> rr(R);
-            NLF_CUDA(cudaMemcpyAsync(it.data(), S.iters, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
-            NLF_CUDA(cudaMemcpyAsync(rr.data(), S.relres, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
-            NLF_CUDA(cudaStreamSynchronize(st));
-            info.iterations = *std::max_element(it.begin(), it.end());
-            info.relres = *std::max_element(rr.begin(), rr.end());
-            info.converged = info.relres <= tol || n_active == 0;
-            for (int c = 0; c < R; ++c)
-                if (!(rr[c] <= tol)) info.converged = false;
         } else if (nu > 0) {
             k_to_apply<T><<<grid_for(nu * R), 256, 0, st>>>(ws.fU.as<double>(), x, sd, p->d_u2sub.as<int32_t>(), nu, R);
             note_launch();
@@ -955,7 +934,37 @@ struct Runner {
             note_launch();
         }
         NLF_CUDA(cudaGetLastError());
-        return info;
+    }
+
+    // One read-back of the scalar block (doubles nPd .. corr, then active, iters, n_active,
+    // loops, counter, err) after the work of a sweep; checks the error word and counts the
+    // kernels of the last device-side loop.
+    struct State {
+        int iterations = 0, n_active = 0;
+        double relres = 0;
+        bool all_within = true;
+        std::vector<double> corr;
+    };
+    State read_state(double tol) {
+        const size_t nd = 7 * (size_t)R, ni = 2 * (size_t)R + 4;
+        std::vector<unsigned char> buf(nd * sizeof(double) + ni * sizeof(int));
+        NLF_CUDA(cudaMemcpyAsync(buf.data(), ws.scal.p, buf.size(), cudaMemcpyDeviceToHost, st));
+        NLF_CUDA(cudaStreamSynchronize(st));
+        const double *d = reinterpret_cast<const double *>(buf.data());
+        const int *iv = reinterpret_cast<const int *>(buf.data() + nd * sizeof(double));
+        for (int k = 0; k < 4; ++k) ws.host_flag[k] = iv[2 * R + k];
+        check_waits();
+        eager_launches += (int64_t)iv[2 * R + 1] * loop_body_launches;
+        loop_body_launches = 0;
+        State out;
+        out.n_active = iv[2 * R];
+        out.corr.assign(d + 6 * R, d + 7 * R);
+        for (int c = 0; c < R; ++c) {
+            out.iterations = std::max(out.iterations, iv[R + c]);
+            out.relres = std::max(out.relres, d[5 * R + c]);
+            if (!(d[5 * R + c] <= tol)) out.all_within = false;
+        }
+        return out;
     }
 };
 
@@ -1086,12 +1095,13 @@ void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rh
     if (!mixed) {
         if (!p->op64.ready) fail(NLFETI_E_INVALID, "FP64 operators not factored");
         NLF_CUDA(cudaMemcpyAsync(ws.res.p, ws.ftil.p, sizeof(double) * nv * R, cudaMemcpyDeviceToDevice, st));
-        PassInfo pi = run.pass<double>(p->op64, p->opt.tol, p->opt.max_it, false);
+        run.pass<double>(p->op64, p->opt.tol, p->opt.max_it, false);
         NLF_CUDA(cudaMemcpyAsync(ws.u.p, ws.du.p, sizeof(double) * nv * R, cudaMemcpyDeviceToDevice, st));
-        s.iterations = pi.iterations;
+        const auto state = run.read_state(p->opt.tol);
+        s.iterations = state.iterations;
         s.refine_sweeps = 1;
-        s.final_rel_residual = pi.relres;
-        if (!pi.converged) {
+        s.final_rel_residual = state.relres;
+        if (nl > 0 && !state.all_within) {
             k_output<<<grid_for(ndof * R), 256, 0, st>>>(ws.u.as<double>(), p->d_cp_ptr.as<int64_t>(), p->d_cp_pos.as<int64_t>(),
                                                          p->d_node_dir.as<int8_t>(), p->nc, d_g, ndof, R, d_out);
             if (stats) *stats = s;
@@ -1114,19 +1124,19 @@ void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rh
                                                                             ws.cvec.as<double>(), nl, R);
                 run.eager_launches += 1 + (nl > 0);
             }
-            PassInfo pi = run.pass<float>(p->op32, p->opt.inner_tol, p->opt.max_it, sw > 0);
-            s.iterations += pi.iterations;
-            s.refine_sweeps = sw + 1;
-            s.final_rel_residual = pi.relres;
-            k_axpy<<<grid_for(nv * R), 256, 0, st>>>(ws.u.as<double>(), ws.du.as<double>(), 1.0, nv * R);
+            run.pass<float>(p->op32, p->opt.inner_tol, p->opt.max_it, sw > 0);
             if (nl > 0) k_axpy<<<grid_for(nl * R), 256, 0, st>>>(ws.lam.as<double>(), ws.dlam.as<double>(), 1.0, nl * R);
-            k_absmax_partial<<<RED_BLOCKS, RED_THREADS, 0, st>>>(ws.du.as<double>(), ws.u.as<double>(), nv, R,
-                                                                 ws.partial.as<double>(), ws.partial2.as<double>());
-            k_rel_correction<<<1, 256, 0, st>>>(ws.partial.as<double>(), ws.partial2.as<double>(), R, run.S);
-            run.eager_launches += 3 + (nl > 0);
-            std::vector<double> corr(R);
-            NLF_CUDA(cudaMemcpyAsync(corr.data(), run.S.corr, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
-            NLF_CUDA(cudaStreamSynchronize(st));
+            k_refine_update<<<red_grid(nv, R), RED_THREADS, 0, st>>>(ws.u.as<double>(), ws.du.as<double>(), nv, R,
+                                                                     ws.partial.as<double>(), ws.partial2.as<double>(),
+                                                                     run.S);
+            run.eager_launches += 1 + (nl > 0);
+            const auto state = run.read_state(p->opt.inner_tol);
+            if (nl > 0) {
+                s.iterations += state.iterations;
+                s.final_rel_residual = state.relres;
+            }
+            s.refine_sweeps = sw + 1;
+            const std::vector<double> &corr = state.corr;
             s.rel_correction = *std::max_element(corr.begin(), corr.end());
             // stop when every column's correction, or its estimated remaining error, is within
             // refine_tol: with the observed contraction rho = corr_k / corr_{k-1} < 1/2 the

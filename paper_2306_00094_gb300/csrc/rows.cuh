@@ -207,6 +207,22 @@ __global__ void k_gather_apply(const int64_t *ptr, const int64_t *row, const dou
     }
 }
 
+// x (apply layout) = base - B^T v (B^T rows signed r+1 / -(r+1)), the apply input of u_G
+template <typename T>
+__global__ void k_gather_sub_apply(const int64_t *ptr, const int64_t *row, const double *v, const double *base, T *x,
+                                   const SubdomainDesc *sd, const int32_t *u2sub, int64_t nu, int R) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t / nu);
+        const int64_t u = t % nu;
+        double s = 0;
+        for (int64_t q = ptr[u]; q < ptr[u + 1]; ++q) {
+            const int64_t r = row[q];
+            s += r > 0 ? v[(r - 1) * R + c] : -v[(-r - 1) * R + c];
+        }
+        apply_store<T>(x, sd, u2sub, u, c, R, (T)(base[u * R + c] - s));
+    }
+}
+
 // x (apply layout) = uU (interleaved U vector) cast to T
 template <typename T>
 __global__ void k_to_apply(const double *uU, T *x, const SubdomainDesc *sd, const int32_t *u2sub, int64_t nu, int R) {

@@ -40,12 +40,6 @@ struct SolveWS {
     ~SolveWS() { drop_graphs(); }
 };
 
-struct PassInfo {
-    int iterations = 0;
-    double relres = 0.0;
-    bool converged = true;
-};
-
 // Full solve on device arrays: rhs / g column-major (n_dofs x R), out column-major.
 void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rhs_kind, const double *d_rhs,
                   const double *d_g, double *d_out, nlfeti_stats *stats);
