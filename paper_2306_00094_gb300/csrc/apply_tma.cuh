@@ -125,11 +125,11 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
             for (int c0 = 0; c0 < R && ok; c0 += RC)        // the rows again for every column block
             for (int l0 = 0; l0 < ncp; l0 += CW, ++q) {
                 const int s = q % NS;
-                if (q >= NS && !mbar_wait(&empty[s], ((q / NS) - 1) & 1)) {
+                // warp-uniform decisions: every lane takes the same branch
+                if (__any_sync(0xffffffffu, (q >= NS && !mbar_wait(&empty[s], ((q / NS) - 1) & 1)) || abort_flag)) {
                     ok = false;
                     break;
                 }
-                if (abort_flag) { ok = false; break; }
                 // the tiles always land whole (out-of-range rows and columns as zeros)
                 if (lane == 0) {
                     unsigned char *stg = ring + s * STAGE;
@@ -164,9 +164,9 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
                 for (int c = 0; c < RC; ++c) acc[r][c] = T(0);
             for (int l0 = 0; l0 < ncp; l0 += CW, ++q) {
                 const int s = q % NS;
-                if (!mbar_wait(&full[s], (q / NS) & 1) || abort_flag) {
+                if (__any_sync(0xffffffffu, !mbar_wait(&full[s], (q / NS) & 1) || abort_flag)) {
                     if (lane == 0) { atomicExch(err, 1); abort_flag = 1; }
-                    return;
+                    return;                           // the whole warp (the vote is uniform)
                 }
                 const int cw = min(CW, ncp - l0);
                 const T *st = reinterpret_cast<const T *>(ring + s * STAGE);

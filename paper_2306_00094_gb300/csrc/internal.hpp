@@ -170,6 +170,10 @@ struct nlfeti_problem {
     int gw = 0;
     nlf::DevMem d_Gcol, d_Gval;
     nlf::DevMem d_float_ids;             // floating subdomains (int32)
+    // G^T gathers per floating subdomain f: entry ranges (4 int64: Lambda-mode e0, e1 into the
+    // B^T entries, U-mode u0, u1), (co_off, n_co), and per B^T entry its Lambda row and the
+    // weights sign * Z[u] (3 doubles)
+    nlf::DevMem d_gt_range, d_gt_co, d_gt_rows, d_gt_w;
     nlf::DevMem d_u2sub;                 // per U dof: subdomain (int32)
     nlf::DevMem d_u2v;                   // per U dof: position in the subdomain vectors (int64)
     nlf::DevMem d_vdofs;                 // per subdomain-vector entry: global dof (int32)

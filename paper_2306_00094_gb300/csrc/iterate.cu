@@ -378,36 +378,30 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_b_eta(const int64_t *Bp,
     if (arrive_last(s.counter)) finish_scalars<FIN_ETA>(partial, gridDim.x, R, s, 0.0, 0);
 }
 
-// alpha = (G^T G)^-1 G^T v with G^T v = Z^T B^T v (or Z^T v for v in U).  Grid (floating
-// subdomains, PSPLIT slices, right-hand sides): block (f, j, c) sums slice j of floating
-// subdomain f's Gamma dofs for column c into gpart; the last block to arrive adds the slices
-// in order (gsum) and applies (G^T G)^-1.
+// alpha = (G^T G)^-1 G^T v.  G^T v is gathered from flat entry lists per floating subdomain
+// f: for v on Lambda, entry e of B^T restricted to Gamma_f is (Lambda row rows[e], weights
+// w[e][q] = sign(e) Z[u(e)][q]); for v on U, the entries are the U dofs of Gamma_f with
+// weights Z.  Grid (floating subdomains, PSPLIT slices of the entry range, right-hand sides):
+// block (f, j, c) sums slice j into gpart; the last block to arrive adds the slices in order
+// (into shared memory when they fit, else gsum) and applies (G^T G)^-1.
 constexpr int PSPLIT = 8;
-__global__ void __launch_bounds__(256) k_proj_g(const SubdomainDesc *sd, const int32_t *float_ids,
-                                                const int64_t *bt_ptr, const int64_t *bt_row, const double *v,
-                                                int v_is_u, const double *Z, double *gpart, double *gsum,
-                                                const double *GtGinv, int nco, double *alpha, int R,
-                                                unsigned *counter) {
+__global__ void __launch_bounds__(256) k_proj_g(const int64_t *range, const int32_t *fco, int lam_mode,
+                                                const int64_t *rows, const double *w, const double *v,
+                                                double *gpart, double *gsum, const double *GtGinv, int nco,
+                                                double *alpha, int R, unsigned *counter) {
+    extern __shared__ double gs_dyn[];
     __shared__ double red[8][3];
-    const SubdomainDesc d = sd[float_ids[blockIdx.x]];
-    const int nq = d.n_co, c = blockIdx.z;
+    const int f = blockIdx.x, c = blockIdx.z;
+    const int64_t e0 = range[4 * f + (lam_mode ? 0 : 2)], e1 = range[4 * f + (lam_mode ? 1 : 3)];
+    const int co_off = fco[2 * f], nq = fco[2 * f + 1];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int64_t chunk = (d.nG + PSPLIT - 1) / PSPLIT;
-    const int64_t l0 = blockIdx.y * chunk, l1 = min((int64_t)d.nG, l0 + chunk);
+    const int64_t chunk = (e1 - e0 + PSPLIT - 1) / PSPLIT;
+    const int64_t l0 = e0 + blockIdx.y * chunk, l1 = min(e1, l0 + chunk);
     double acc[3] = {0, 0, 0};
-    for (int64_t l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
-        const int64_t ui = d.offU + l;
-        double bt;
-        if (v_is_u) bt = v[ui * R + c];
-        else {
-            bt = 0;
-            for (int64_t q = bt_ptr[ui]; q < bt_ptr[ui + 1]; ++q) {
-                const int64_t rr = bt_row[q];
-                bt += rr > 0 ? v[(rr - 1) * R + c] : -v[(-rr - 1) * R + c];
-            }
-        }
+    for (int64_t e = l0 + threadIdx.x; e < l1; e += blockDim.x) {
+        const double x = v[(lam_mode ? rows[e] : e) * R + c];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) acc[q] += (q < nq ? Z[ui * 3 + q] : 0.0) * bt;
+        for (int q = 0; q < 3; ++q) acc[q] += w[e * 3 + q] * x;
     }
 #pragma unroll
     for (int q = 0; q < 3; ++q) acc[q] = warp_sum(acc[q]);
@@ -416,21 +410,22 @@ __global__ void __launch_bounds__(256) k_proj_g(const SubdomainDesc *sd, const i
     __syncthreads();
     if (threadIdx.x < nq) {
         double x = 0;
-        for (int w = 0; w < 8; ++w) x += red[w][threadIdx.x];
-        gpart[((int64_t)(d.co_off + threadIdx.x) * PSPLIT + blockIdx.y) * R + c] = x;
+        for (int ww = 0; ww < 8; ++ww) x += red[ww][threadIdx.x];
+        gpart[((int64_t)(co_off + threadIdx.x) * PSPLIT + blockIdx.y) * R + c] = x;
     }
     if (!arrive_last(counter)) return;
+    double *gs = gsum ? gsum : gs_dyn;
     for (int t = threadIdx.x; t < nco * R; t += blockDim.x) {
         const int i = t / R, cc = t % R;
         double g = 0;
         for (int j = 0; j < PSPLIT; ++j) g += __ldcg(gpart + ((int64_t)i * PSPLIT + j) * R + cc);
-        gsum[t] = g;
+        gs[t] = g;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < nco * R; t += blockDim.x) {
         const int i = t / R, cc = t % R;
         double a = 0;
-        for (int j = 0; j < nco; ++j) a += GtGinv[(int64_t)i * nco + j] * gsum[(int64_t)j * R + cc];
+        for (int j = 0; j < nco; ++j) a += GtGinv[(int64_t)i * nco + j] * gs[(int64_t)j * R + cc];
         alpha[t] = a;
     }
     if (threadIdx.x == 0) *counter = 0u;
@@ -618,11 +613,13 @@ struct Runner {
 
     // alpha = (G^T G)^-1 Z^T B^T v  (or (G^T G)^-1 Z^T v for v in U)
     void coarse_alpha(const double *v, int v_is_u) {
-        k_proj_g<<<dim3(p->n_floating, PSPLIT, R), 256, 0, st>>>(sd, p->d_float_ids.as<int32_t>(),
-                                                                  p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), v, v_is_u,
-                                                      p->d_Z.as<double>(), ws.gco.as<double>(), ws.gsum.as<double>(),
-                                                      p->d_GtGinv.as<double>(), p->n_co, ws.alpha.as<double>(), R,
-                                                      S.counter);
+        const size_t gs_bytes = sizeof(double) * (size_t)p->n_co * R;
+        const bool in_smem = gs_bytes <= 32768;
+        k_proj_g<<<dim3(p->n_floating, PSPLIT, R), 256, in_smem ? gs_bytes : 0, st>>>(
+            p->d_gt_range.as<int64_t>(), p->d_gt_co.as<int32_t>(), v_is_u ? 0 : 1, p->d_gt_rows.as<int64_t>(),
+            v_is_u ? p->d_Z.as<double>() : p->d_gt_w.as<double>(), v, ws.gco.as<double>(),
+            in_smem ? nullptr : ws.gsum.as<double>(), p->d_GtGinv.as<double>(), p->n_co, ws.alpha.as<double>(), R,
+            S.counter);
         note_launch();
     }
 

@@ -59,11 +59,11 @@ __global__ void __launch_bounds__(RES_THREADS)
             for (int c0 = 0; c0 < R && ok; c0 += RC)
                 for (int l0 = 0; l0 < ncp; l0 += CW, ++q) {
                     const int s = q % RES_NS;
-                    if (q >= RES_NS && !mbar_wait(&empty[s], ((q / RES_NS) - 1) & 1)) {
+                    // warp-uniform decisions: every lane takes the same branch
+                    if (__any_sync(0xffffffffu, (q >= RES_NS && !mbar_wait(&empty[s], ((q / RES_NS) - 1) & 1)) || abort_flag)) {
                         ok = false;
                         break;
                     }
-                    if (abort_flag) { ok = false; break; }
                     if (lane == 0) {
                         unsigned char *stg = ring + s * STAGE;
                         mbar_arrive_expect_tx(&full[s], STAGE);
@@ -98,9 +98,9 @@ __global__ void __launch_bounds__(RES_THREADS)
                 for (int c = 0; c < RC; ++c) { sh[a][c] = 0.f; sl[a][c] = 0.f; }
             for (int l0 = 0; l0 < ncp; l0 += CW, ++q) {
                 const int s = q % RES_NS;
-                if (!mbar_wait(&full[s], (q / RES_NS) & 1) || abort_flag) {
+                if (__any_sync(0xffffffffu, !mbar_wait(&full[s], (q / RES_NS) & 1) || abort_flag)) {
                     if (lane == 0) { atomicExch(err, 1); abort_flag = 1; }
-                    return;
+                    return;                           // the whole warp (the vote is uniform)
                 }
                 const float *st = reinterpret_cast<const float *>(ring + s * STAGE);
                 const float *sth = st, *stl = st + 32 * CW, *xh = st + 64 * CW, *xl = st + (64 + RC) * CW;

@@ -499,6 +499,18 @@ __global__ void k_gtg(const int64_t *Bp, const int64_t *Bm, int64_t nl, const in
     }
 }
 
+// per B^T entry e of U dof u: its Lambda row and sign(e) Z[u][0..2]
+__global__ void k_gt_entries(const int64_t *bt_ptr, const int64_t *bt_row, const double *Z, int64_t nu, int64_t *rows,
+                             double *w) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t e = bt_ptr[u]; e < bt_ptr[u + 1]; ++e) {
+            const int64_t r = bt_row[e];
+            const double sg = r > 0 ? 1.0 : -1.0;
+            rows[e] = (r > 0 ? r : -r) - 1;
+            for (int q = 0; q < 3; ++q) w[e * 3 + q] = sg * Z[u * 3 + q];
+        }
+}
+
 // slots of the rows of G = B Z (see nlfeti_problem::gw)
 __global__ void k_g_rows(const int64_t *Bp, const int64_t *Bm, int64_t nl, const int32_t *u2sub,
                          const SubdomainDesc *sd, const double *Z, int gw, int32_t *gcol, double *gval) {
@@ -601,6 +613,33 @@ void setup_coarse(nlfeti_problem *p) {
         if (p->sd[k].n_co > 0) fl.push_back(k);
     }
     upload(c, p->d_float_ids, fl);
+    {
+        // G^T entry ranges of the floating subdomains (B^T entries of Gamma_f are contiguous)
+        std::vector<int64_t> bt_ptr(p->n_u + 1, 0);
+        NLF_CUDA(cudaMemcpyAsync(bt_ptr.data(), p->d_Bt_ptr.p, sizeof(int64_t) * (p->n_u + 1), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        NLF_CUDA(cudaStreamSynchronize(c->stream));
+        std::vector<int64_t> range;
+        std::vector<int32_t> co;
+        for (int k : fl) {
+            const SubdomainDesc &d = p->sd[k];
+            range.push_back(bt_ptr[d.offU]);
+            range.push_back(bt_ptr[d.offU + d.nG]);
+            range.push_back(d.offU);
+            range.push_back(d.offU + d.nG);
+            co.push_back(d.co_off);
+            co.push_back(d.n_co);
+        }
+        upload(c, p->d_gt_range, range);
+        upload(c, p->d_gt_co, co);
+        const int64_t ne = std::max<int64_t>(1, bt_ptr[p->n_u]);
+        p->d_gt_rows.alloc(c, sizeof(int64_t) * ne);
+        p->d_gt_w.alloc(c, sizeof(double) * 3 * ne);
+        if (p->n_u > 0)
+            k_gt_entries<<<256, 256, 0, c->stream>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(),
+                                                     p->d_Z.as<double>(), p->n_u, p->d_gt_rows.as<int64_t>(),
+                                                     p->d_gt_w.as<double>());
+    }
     p->gw = 2 * max_nco;
     p->d_Gcol.alloc(c, sizeof(int32_t) * std::max<int64_t>(1, p->n_lambda * p->gw));
     p->d_Gval.alloc(c, sizeof(double) * std::max<int64_t>(1, p->n_lambda * p->gw));
