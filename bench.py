@@ -8,13 +8,19 @@ i.i.d. N(0,1) nodal loads.  A step is one FETI solve request of the 8 right-hand
 with the subdomain operators resident (setup and factorization excluded, the protocol of
 the paper's timings; both are reported under "cold"): reduced forcing, projected PCG with
 the scaled Dirichlet preconditioner, FP64 refinement of the FP32 operators until the
-relative nodal correction is below 1e-10, back substitution and nodal output.  "value" is
+relative nodal correction (or the remaining error it predicts) is below 1e-9, back
+substitution and nodal output.  "value" is
 right-hand-side solves per second with the loads resident in HBM; "e2e" is the same
 through the C ABI with pinned host buffers (host<->device copies inside the timed region).
 
 --impl reference times the FP64 CPU oracle (one-level FETI in numpy, Algorithm 1) on the
 same workload on the host cores; each step is one oracle solve of the 8 right-hand sides.
 Under torchrun (N > 1) every rank solves its own replica (no collective in the data path).
+
+--serving runs the serving scenario instead: requests drawn from a pool of factored problems
+(kernels, mesh sizes, horizons and decompositions sampled from a grid) arrive as a Poisson
+process at the server; it reports solves/s, arrival -> result latency p50/p99 and a sweep of
+the arrival rate.
 """
 from __future__ import annotations
 
@@ -374,6 +380,138 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------------------ serving
+
+def serving_pool(rng, size, budget_bytes, cost_cap):
+    """Problem configurations of the serving scenario, sampled uniformly from the grid
+    kernel x h x delta x K, rejecting those whose subdomains exceed 8k dofs, whose footprint
+    exceeds the budget or whose assembly would cost more than cost_cap (element pairs)."""
+    kinds = ["1d_const", "2d_const_l2", "2d_fractional"]
+    pool, seen, tried, rejected = [], set(), 0, 0
+    while len(pool) < size and tried < 5000:
+        tried += 1
+        kind = kinds[rng.integers(3)]
+        N = [64, 128, 256][rng.integers(3)]
+        di, ki = int(rng.integers(3)), int(rng.integers(5))
+        if kind == "1d_const":
+            N *= 10
+            K = [4, 8, 16, 32, 64][ki]
+            h = 1.0 / N
+            delta = [2 * h, 3 * h, 0.1][di]
+            e = int(np.ceil(delta / (2 * h) - 1e-9))
+            nk = N // K + 2 * e + 1
+            foot = K * nk * nk * 28
+            cost = N * 2 * delta / h
+        else:
+            k = [2, 3, 4, 6, 8][ki]
+            K = k * k
+            h = 1.0 / N
+            delta = [2 * h, 3 * h, 0.1][di]
+            e = int(np.ceil(delta / (2 * h) - 1e-9))
+            nk = (N // k + 2 * e + 1) ** 2
+            foot = K * nk * nk * 28
+            cost = 2 * (N + 2 * W.collar_cells(delta, N)) ** 2 * np.pi * (delta / h) ** 2
+        key = (kind, N, di, K)
+        if nk > 8000 or foot > budget_bytes or cost > cost_cap:
+            rejected += 1
+            continue
+        if key in seen:
+            continue
+        seen.add(key)
+        pool.append({"kernel": kind, "N": N, "delta": delta, "K": K, "n_k_est": int(nk)})
+    return pool, rejected / max(1, tried)
+
+
+def serving_workload(cfg, nrhs):
+    if cfg["kernel"] == "1d_const":
+        return W.cfg1_1d(N=cfg["N"], K=cfg["K"], delta=cfg["delta"], nrhs=nrhs)
+    k = int(round(np.sqrt(cfg["K"])))
+    if cfg["kernel"] == "2d_const_l2":
+        return W.cfg2_const_l2(N=cfg["N"], k=k, nrhs=nrhs, delta=cfg["delta"])
+    return W.cfg3_fractional(N=cfg["N"], k=k, nrhs=nrhs, delta=cfg["delta"])
+
+
+def run_serving(args):
+    """Serving scenario: Poisson arrivals of requests (a problem from a pool of factored
+    problems, R in [1, 32] right-hand sides) to the continuous-batching server; latency is
+    arrival -> result on the host (submission lag + queue wait + solve incl. copies)."""
+    import threading
+    import torch  # noqa: F401  (device memory and the caller stream of the context)
+    from paper_2306_00094_gb300 import binding
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    rng = np.random.default_rng(6)
+    budget = 16 << 30
+    pool_cfg, rejected = serving_pool(rng, args.pool, budget, cost_cap=2.0e7)
+    ctx = binding.Context()
+    t0 = time.perf_counter()
+    probs = []
+    for cfg in pool_cfg:
+        w = serving_workload(cfg, 32)
+        p = binding.Problem.from_workload(ctx, w)
+        p.factor(2)
+        p.set_options(binding.default_options(precision=1, batched=1))
+        rhs = np.asfortranarray(w.rhs)
+        probs.append((p, rhs, w.rhs_kind))
+        cfg["dofs"] = int(rhs.shape[0])
+    setup_s = time.perf_counter() - t0
+    server = binding.Server(ctx, hbm_budget=budget, max_slots=args.slots)
+
+    def run(rate, n_req, n_warm):
+        arr = np.cumsum(rng.exponential(1.0 / rate, n_warm + n_req))
+        pick = rng.integers(len(probs), size=n_warm + n_req)
+        nr = rng.integers(1, 33, size=n_warm + n_req)
+        tickets = [None] * len(arr)
+        lags = [0.0] * len(arr)
+        lat = [None] * len(arr)
+        done_at = [0.0] * len(arr)
+        submitted = threading.Semaphore(0)
+        start = time.perf_counter() + 0.05
+
+        def collect():
+            for i in range(len(arr)):
+                submitted.acquire()
+                _, st = server.wait(tickets[i])
+                done_at[i] = time.perf_counter()
+                lat[i] = lags[i] + 1e-3 * (st["ms_queue"] + st["ms_solve"])
+        th = threading.Thread(target=collect)
+        th.start()
+        for i in range(len(arr)):
+            tgt = start + arr[i]
+            now = time.perf_counter()
+            if tgt > now:
+                time.sleep(tgt - now)
+            p, rhs, kind = probs[pick[i]]
+            tickets[i] = server.submit(p, rhs[:, :nr[i]], kind)
+            lags[i] = time.perf_counter() - tgt
+            submitted.release()
+        th.join()
+        meas = range(n_warm, len(arr))
+        t_first, t_last = start + arr[n_warm], max(done_at[i] for i in meas)
+        span = t_last - t_first
+        ls = [1e3 * lat[i] for i in meas]
+        return {"offered_rate": rate, "requests": n_req, "requests_per_s": n_req / span,
+                "solves_per_s": float(sum(nr[i] for i in meas)) / span,
+                "p50_ms": percentile(ls, 0.5), "p99_ms": percentile(ls, 0.99),
+                "mean_submit_lag_ms": 1e3 * float(np.mean([lags[i] for i in meas]))}
+
+    main_run = run(args.rate, args.requests, args.requests // 10)
+    sweep = [run(r, 300, 30) for r in (50, 100, 200, 400, 800)]
+    sustainable = max([s["offered_rate"] for s in sweep if s["requests_per_s"] >= 0.9 * s["offered_rate"]], default=None)
+    server.close()
+    line = {"metric": "serving: FETI requests (mixed kernels, h, delta, K; R in [1, 32]) under Poisson arrivals, "
+                      "arrival -> host result latency, 1 GB300",
+            "mode": "serving", "value": main_run["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "dtype": "f32 operators + f64 vectors/refinement",
+            "config": {"workload": "serving pool of factored problems sampled from the grid (seed 6)",
+                       "pool": pool_cfg, "slots": args.slots, "hbm_budget_bytes": budget,
+                       "rejected_fraction_of_grid_draws": rejected},
+            "setup_and_factor_s": setup_s, "run": main_run, "rate_sweep": sweep,
+            "max_sustained_rate": sustainable}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -385,10 +523,18 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="PCG loops as host-checked graph chunks instead of device-side WHILE graphs "
                          "(ncu cannot profile kernels inside conditional graphs)")
+    ap.add_argument("--serving", action="store_true",
+                    help="serving scenario: Poisson arrivals of mixed requests to the server (one JSON line)")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: offered requests per second")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: measured requests")
+    ap.add_argument("--pool", type=int, default=6, help="serving: distinct factored problems")
+    ap.add_argument("--slots", type=int, default=4, help="serving: server slots")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.serving:
+        run_serving(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -115,6 +115,8 @@ typedef struct {
     double final_rel_residual; /* last ||P r|| / ||P d|| (max over RHS) */
     double rel_correction;     /* last relative nodal correction (mixed path) */
     double ms_setup, ms_factor, ms_solve;
+    double ms_queue;           /* server requests: time from nlfeti_submit until a slot took the
+                                  request (ms_solve then runs to its result on the host side) */
 } nlfeti_stats;
 
 /* Sizes of a created problem. */

@@ -42,7 +42,7 @@ class Options(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("refine_sweeps", C.c_int), ("final_rel_residual", C.c_double),
                 ("rel_correction", C.c_double), ("ms_setup", C.c_double), ("ms_factor", C.c_double),
-                ("ms_solve", C.c_double)]
+                ("ms_solve", C.c_double), ("ms_queue", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

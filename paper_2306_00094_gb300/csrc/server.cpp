@@ -200,7 +200,7 @@ nlfeti_status nlfeti_wait(nlfeti_server *s, nlfeti_ticket t, int timeout_ms, dou
     if (u_out && !rq->out.empty()) std::copy(rq->out.begin(), rq->out.end(), u_out);
     if (stats) {
         *stats = rq->stats;
-        stats->ms_setup = std::chrono::duration<double, std::milli>(rq->t_start - rq->t_submit).count();  // queue wait
+        stats->ms_queue = std::chrono::duration<double, std::milli>(rq->t_start - rq->t_submit).count();
     }
     if (rq->status != NLFETI_OK) set_error(s->ctx, rq->err);
     return rq->status;
