@@ -4,6 +4,7 @@
 // admitted when a slot is free and its predicted device footprint fits the HBM budget;
 // otherwise it waits in the queue.  Factorizations stay resident on the device in their
 // problems (setup is paid once per problem and amortized over the requests).
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -36,6 +37,55 @@ size_t predict_bytes(const nlfeti_problem *p, int R) {
     return sizeof(double) * (size_t)R * (10 * nl + 4 * nu + 4 * nv + 4 * nd) + (1 << 20);
 }
 
+// Right-hand-side counts are rounded up to a few bucket sizes (the extra columns are zero and
+// converge at once), so that a slot meets the same (problem, count) pairs again and reuses
+// their workspaces and captured PCG graphs.
+int rhs_bucket(int R) {
+    static const int b[] = {1, 2, 4, 8, 12, 16, 24, 32};
+    for (int v : b)
+        if (R <= v) return v;
+    return (R + 15) / 16 * 16;
+}
+
+// Recently used workspaces of one slot, keyed by (problem, right-hand-side count), bounded
+// in bytes (least recently used first out).
+struct WsCache {
+    struct Entry {
+        uint64_t uid = 0;
+        int R = 0;
+        size_t bytes = 0;
+        uint64_t stamp = 0;
+        std::unique_ptr<SolveWS> ws;
+    };
+    std::vector<Entry> entries;
+    size_t bytes = 0, cap = 0;
+    uint64_t clock = 0;
+    SolveWS &get(nlfeti_problem *p, int R, cudaStream_t st) {
+        for (auto &e : entries)
+            if (e.uid == p->uid && e.R == R) {
+                e.stamp = ++clock;
+                return *e.ws;
+            }
+        const size_t need = predict_bytes(p, R);
+        while (!entries.empty() && bytes + need > cap) {
+            auto lru = std::min_element(entries.begin(), entries.end(),
+                                        [](const Entry &a, const Entry &b) { return a.stamp < b.stamp; });
+            bytes -= lru->bytes;
+            entries.erase(lru);
+        }
+        Entry e;
+        e.uid = p->uid;
+        e.R = R;
+        e.bytes = need;
+        e.stamp = ++clock;
+        e.ws.reset(new SolveWS());
+        e.ws->async_stream = st;
+        bytes += need;
+        entries.push_back(std::move(e));
+        return *entries.back().ws;
+    }
+};
+
 }  // namespace
 
 struct nlfeti_server {
@@ -53,9 +103,10 @@ struct nlfeti_server {
     void worker() {
         cudaStream_t st = nullptr;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); return; }
-        std::unique_ptr<SolveWS> wsp(new SolveWS());
-        SolveWS &ws = *wsp;
-        ws.async_stream = st;
+        // each slot keeps recently used workspaces besides the admission budget: a share of
+        // the budget (half of it over all slots), or 2 GiB without a budget
+        WsCache cache;
+        cache.cap = budget ? std::max<size_t>(size_t(256) << 20, budget / (2 * (size_t)slots)) : size_t(2) << 30;
         for (;;) {
             std::shared_ptr<Request> rq;
             {
@@ -78,15 +129,24 @@ struct nlfeti_server {
             std::string msg;
             try {
                 nlfeti_problem *p = rq->prob;
+                const int Rb = rhs_bucket(rq->R);
+                SolveWS &ws = cache.get(p, Rb, st);
                 const size_t bytes = sizeof(double) * (size_t)p->n_dofs_total * rq->R;
-                if (ws.in_rhs.bytes < bytes) ws.in_rhs.alloc_async(st, bytes);
-                if (ws.out_u.bytes < bytes) ws.out_u.alloc_async(st, bytes);
-                if (rq->has_g && ws.in_g.bytes < bytes) ws.in_g.alloc_async(st, bytes);
+                const size_t bytes_b = sizeof(double) * (size_t)p->n_dofs_total * Rb;
+                if (ws.in_rhs.bytes < bytes_b) ws.in_rhs.alloc_async(st, bytes_b);
+                if (ws.out_u.bytes < bytes_b) ws.out_u.alloc_async(st, bytes_b);
+                if (rq->has_g && ws.in_g.bytes < bytes_b) ws.in_g.alloc_async(st, bytes_b);
                 NLF_CUDA(cudaMemcpyAsync(ws.in_rhs.p, rq->rhs.data(), bytes, cudaMemcpyHostToDevice, st));
-                if (rq->has_g) NLF_CUDA(cudaMemcpyAsync(ws.in_g.p, rq->g.data(), bytes, cudaMemcpyHostToDevice, st));
+                if (bytes_b > bytes)
+                    NLF_CUDA(cudaMemsetAsync(ws.in_rhs.as<unsigned char>() + bytes, 0, bytes_b - bytes, st));
+                if (rq->has_g) {
+                    NLF_CUDA(cudaMemcpyAsync(ws.in_g.p, rq->g.data(), bytes, cudaMemcpyHostToDevice, st));
+                    if (bytes_b > bytes)
+                        NLF_CUDA(cudaMemsetAsync(ws.in_g.as<unsigned char>() + bytes, 0, bytes_b - bytes, st));
+                }
                 rq->out.resize((size_t)p->n_dofs_total * rq->R);
                 try {
-                    solve_device(p, ws, st, rq->R, rq->kind, ws.in_rhs.as<double>(),
+                    solve_device(p, ws, st, Rb, rq->kind, ws.in_rhs.as<double>(),
                                  rq->has_g ? ws.in_g.as<double>() : nullptr, ws.out_u.as<double>(), &rq->stats);
                 } catch (const Error &e) {
                     if (e.st != NLFETI_E_NOT_CONVERGED) throw;
@@ -117,7 +177,7 @@ struct nlfeti_server {
             cv_done.notify_all();
             cv_work.notify_all();
         }
-        wsp.reset();
+        cache.entries.clear();
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }

@@ -70,3 +70,20 @@ def test_wait_times_out_then_completes(setup):
     u2, _ = srv.wait(t2)
     assert np.array_equal(u1, u2)
     srv.close()
+
+
+def test_server_matches_direct_solve_for_odd_rhs_counts(setup):
+    """The server rounds right-hand-side counts up to bucket sizes (zero columns) and keeps
+    workspaces per (problem, count); results equal the direct solve of the same columns."""
+    from paper_2306_00094_gb300 import binding
+    ctx, work, probs = setup
+    w, p = work[1], probs[1]
+    srv = binding.Server(ctx, max_slots=2)
+    for R in (1, 3, 5, 3, 5):
+        rhs = np.asfortranarray(np.tile(w.rhs, (1, 2))[:, :R])
+        u_direct, _ = p.solve(rhs, w.rhs_kind)
+        u_srv, st = srv.wait(srv.submit(p, rhs, w.rhs_kind), timeout_ms=120000)
+        assert u_srv.shape == u_direct.shape
+        assert np.abs(u_srv - u_direct).max() <= 1e-12 * np.abs(u_direct).max()
+        assert st["ms_queue"] >= 0.0
+    srv.close()
