@@ -305,6 +305,8 @@ __device__ void finish_scalars(const double *partial, int nb, int R, PcgScalars 
                 s.iters[c] = 0;
                 s.yw_old[c] = 1.0;
                 s.relres[c] = 1.0;
+                s.eta[c] = 0.0;
+                s.beta[c] = 0.0;
             } else if (MODE == FIN_CHECK) {
                 const double nw = sqrt(v), ref = s.nPd[c];
                 int act = s.active[c];
@@ -342,6 +344,16 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot_final(const double *a, cons
     if (arrive_last(s.counter)) finish_scalars<MODE>(partial, gridDim.x, R, s, tol, max_it);
 }
 
+// The updates of p, lambda and r are stored one iteration late, by the kernel that starts the
+// next iteration; until then the kernels that read p_new or r_new form them per row with these
+// (the same bits everywhere):
+//   p_new = y + beta p on active columns (p unchanged on converged ones),
+//   r_new = r - eta q (eta = 0 on converged columns and before the first iteration).
+__device__ __forceinline__ double p_next(double p, double y, double beta, bool active) {
+    return active ? __fma_rn(beta, p, y) : p;
+}
+__device__ __forceinline__ double r_next(double r, double q, double eta) { return __fma_rn(-eta, q, r); }
+
 // out = P v = v - G alpha (alpha from k_proj_g; NULL when there is no coarse space), with the
 // dot product of MODE: CHECK (out, out), BETA (out, other)
 template <int MODE>
@@ -362,20 +374,87 @@ __global__ void __launch_bounds__(RED_THREADS) k_project_dot(const int32_t *gcol
     if (arrive_last(s.counter)) finish_scalars<MODE>(partial, gridDim.x, R, s, tol, max_it);
 }
 
-// q = B y (y on U) with (p, q) and the ETA update
-__global__ void __launch_bounds__(RED_THREADS) k_gather_b_eta(const int64_t *Bp, const int64_t *Bm, const double *y,
-                                                               const double *pv, double *q, int64_t nl, int R,
-                                                               double *partial, PcgScalars s) {
+// q = B y_U with (p_new, q) and the ETA update (p_new formed per row, stored by the next
+// iteration's k_check_update)
+__global__ void __launch_bounds__(RED_THREADS) k_gather_b_eta(const int64_t *Bp, const int64_t *Bm, const double *yU,
+                                                               const double *pv, const double *y, double *q,
+                                                               int64_t nl, int R, double *partial, PcgScalars s) {
     const int c = blockIdx.y;
+    const bool act = s.active[c] != 0;
+    const double be = s.beta[c];
     double acc = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t t = i * R + c;
-        const double x = y[Bp[i] * R + c] - y[Bm[i] * R + c];
+        const double x = yU[Bp[i] * R + c] - yU[Bm[i] * R + c];
         q[t] = x;
-        acc += pv[t] * x;
+        acc += p_next(pv[t], y[t], be, act) * x;
     }
     block_partial(acc, partial, R);
     if (arrive_last(s.counter)) finish_scalars<FIN_ETA>(partial, gridDim.x, R, s, 0.0, 0);
+}
+
+// Start of a PCG iteration (after k_proj_g formed alpha from G^T r_new): the previous
+// iteration's updates p = p_new, lambda += eta p, r = r_new, then w = P r = r - G alpha,
+// (w, w) and the stop test.  The active flags read here are those p_new was formed with: the
+// last block changes them only after every block has arrived.  COND: the last block also
+// counts the iteration and sets the condition of the WHILE loop (continue while a
+// right-hand side is active and fewer than limit iterations have run, so the loop ends
+// whatever the scalars hold); a separate instantiation, as profilers skip kernels that set
+// graph conditions.
+template <int COND>
+__global__ void __launch_bounds__(RED_THREADS) k_check_update(const int32_t *gcol, const double *gval, int gw,
+                                                               const double *alpha, const double *y, double *pv,
+                                                               double *lam, double *r, const double *q, double *w,
+                                                               int64_t nl, int R, double *partial, PcgScalars s,
+                                                               double tol, int max_it, cudaGraphConditionalHandle cond,
+                                                               int limit) {
+    const int c = blockIdx.y;
+    const bool act = s.active[c] != 0;
+    const double be = s.beta[c], e = s.eta[c];
+    double acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i * R + c;
+        const double pn = p_next(pv[t], y[t], be, act);
+        pv[t] = pn;
+        lam[t] = __fma_rn(e, pn, lam[t]);
+        const double rn = r_next(r[t], q[t], e);
+        r[t] = rn;
+        double x = rn;
+        if (alpha) x += -1.0 * g_alpha(gcol, gval, gw, alpha, i, c, R);
+        w[t] = x;
+        acc += x * x;
+    }
+    block_partial(acc, partial, R);
+    if (arrive_last(s.counter)) {
+        finish_scalars<FIN_CHECK>(partial, gridDim.x, R, s, tol, max_it);
+        if (COND && threadIdx.x == 0) {
+            const int l = *s.loops + 1;
+            *s.loops = l;
+            cudaGraphSetConditional(cond, (*s.n_active > 0 && l < limit) ? 1u : 0u);
+        }
+    }
+}
+
+// x (apply layout) = B^T p_new (B^T rows signed r+1 / -(r+1)), p_new formed per row: the input
+// of the S^+ apply of a PCG iteration
+template <typename T>
+__global__ void k_gather_apply_p(const int64_t *ptr, const int64_t *row, const double *pv, const double *y,
+                                 const double *beta, const int *active, T *x, const SubdomainDesc *sd,
+                                 const int32_t *u2sub, int64_t nu, int R, const int *gate) {
+    if (gate && *gate == 0) return;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t / nu);
+        const int64_t u = t % nu;
+        const bool act = active[c] != 0;
+        const double be = beta[c];
+        double s = 0;
+        for (int64_t q = ptr[u]; q < ptr[u + 1]; ++q) {
+            const int64_t r = row[q], i = r > 0 ? r - 1 : -r - 1;
+            const double pn = p_next(pv[i * R + c], y[i * R + c], be, act);
+            s += r > 0 ? pn : -pn;
+        }
+        apply_store<T>(x, sd, u2sub, u, c, R, (T)s);
+    }
 }
 
 // alpha = (G^T G)^-1 G^T v.  G^T v is gathered from flat entry lists per floating subdomain
@@ -384,11 +463,15 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_b_eta(const int64_t *Bp,
 // weights Z.  Grid (floating subdomains, PSPLIT slices of the entry range, right-hand sides):
 // block (f, j, c) sums slice j into gpart; the last block to arrive adds the slices in order
 // (into shared memory when they fit, else gsum) and applies (G^T G)^-1.
+// v_mode: PG_U v on U; PG_LAM v on Lambda; PG_LAM_R r_new = r - eta q on Lambda (v = r)
 constexpr int PSPLIT = 8;
-__global__ void __launch_bounds__(256) k_proj_g(const int64_t *range, const int32_t *fco, int lam_mode,
-                                                const int64_t *rows, const double *w, const double *v,
-                                                double *gpart, double *gsum, const double *GtGinv, int nco,
-                                                double *alpha, int R, unsigned *counter) {
+enum { PG_U = 0, PG_LAM = 1, PG_LAM_R = 2 };
+template <int VMODE>
+__global__ void __launch_bounds__(256) k_proj_g(const int64_t *range, const int32_t *fco, const int64_t *rows,
+                                                const double *w, const double *v, const double *q,
+                                                const double *eta, double *gpart, double *gsum, const double *GtGinv,
+                                                int nco, double *alpha, int R, unsigned *counter) {
+    constexpr int lam_mode = VMODE != PG_U;
     extern __shared__ double gs_dyn[];
     __shared__ double red[8][3];
     const int f = blockIdx.x, c = blockIdx.z;
@@ -398,8 +481,12 @@ __global__ void __launch_bounds__(256) k_proj_g(const int64_t *range, const int3
     const int64_t chunk = (e1 - e0 + PSPLIT - 1) / PSPLIT;
     const int64_t l0 = e0 + blockIdx.y * chunk, l1 = min(e1, l0 + chunk);
     double acc[3] = {0, 0, 0};
+    const double eta_c = VMODE == PG_LAM_R ? eta[c] : 0.0;
     for (int64_t e = l0 + threadIdx.x; e < l1; e += blockDim.x) {
-        const double x = v[(lam_mode ? rows[e] : e) * R + c];
+        double x;
+        if (VMODE == PG_U) x = v[e * R + c];
+        else if (VMODE == PG_LAM) x = v[rows[e] * R + c];
+        else x = r_next(v[rows[e] * R + c], q[rows[e] * R + c], eta_c);
 #pragma unroll
         for (int q = 0; q < 3; ++q) acc[q] += w[e * 3 + q] * x;
     }
@@ -473,32 +560,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_refine_update(double *u, const 
     if (threadIdx.x == 0) *s.counter = 0u;
 }
 
-__global__ void k_update_p(const double *y, const double *beta, const int *active, double *p, int64_t n, int R) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * R; t += (int64_t)gridDim.x * blockDim.x) {
-        int c = (int)(t % R);
-        if (active[c]) p[t] = y[t] + beta[c] * p[t];
-    }
-}
-
-// lambda += eta p, r -= eta q.  Inside a graph loop (use_cond) the first thread also counts
-// the iteration and sets the loop condition: continue while a right-hand side is active and
-// fewer than limit iterations have run (the count bounds the loop whatever the scalars hold).
-__global__ void k_update_lr(const double *p, const double *q, const double *eta, double *lam, double *r, int64_t n,
-                            int R, cudaGraphConditionalHandle cond, int use_cond, const int *n_active, int *loops,
-                            int limit) {
-    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) {
-        const int l = *loops + 1;
-        *loops = l;
-        cudaGraphSetConditional(cond, (*n_active > 0 && l < limit) ? 1u : 0u);
-    }
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * R; t += (int64_t)gridDim.x * blockDim.x) {
-        int c = (int)(t % R);
-        double e = eta[c];
-        lam[t] += e * p[t];
-        r[t] -= e * q[t];
-    }
-}
-
 // ====================================================================== host orchestration
 
 // the workspace's error word (set by a device wait that ran out)
@@ -546,7 +607,7 @@ struct Runner {
     // right-hand side is active any more (every later update is masked by the active flags)
     const int *gate = nullptr;
     int64_t loop_body_launches = 0;     // kernels per iteration of the last device-side loop
-    // the WHILE node of the graph loop being captured (set by k_update_lr)
+    // the WHILE node of the graph loop being captured (set by k_check_update)
     cudaGraphConditionalHandle cond = 0;
     bool use_cond = false;
     int64_t apply_launches = 0;
@@ -612,14 +673,20 @@ struct Runner {
     }
 
     // alpha = (G^T G)^-1 Z^T B^T v  (or (G^T G)^-1 Z^T v for v in U)
-    void coarse_alpha(const double *v, int v_is_u) {
+    // alpha = (G^T G)^-1 G^T v: v on U (PG_U), on Lambda (PG_LAM) or r_new = v - eta q (PG_LAM_R)
+    void coarse_alpha(const double *v, int vmode, const double *q = nullptr) {
         const size_t gs_bytes = sizeof(double) * (size_t)p->n_co * R;
         const bool in_smem = gs_bytes <= 32768;
-        k_proj_g<<<dim3(p->n_floating, PSPLIT, R), 256, in_smem ? gs_bytes : 0, st>>>(
-            p->d_gt_range.as<int64_t>(), p->d_gt_co.as<int32_t>(), v_is_u ? 0 : 1, p->d_gt_rows.as<int64_t>(),
-            v_is_u ? p->d_Z.as<double>() : p->d_gt_w.as<double>(), v, ws.gco.as<double>(),
-            in_smem ? nullptr : ws.gsum.as<double>(), p->d_GtGinv.as<double>(), p->n_co, ws.alpha.as<double>(), R,
-            S.counter);
+        auto go = [&](auto kern) {
+            kern<<<dim3(p->n_floating, PSPLIT, R), 256, in_smem ? gs_bytes : 0, st>>>(
+                p->d_gt_range.as<int64_t>(), p->d_gt_co.as<int32_t>(), p->d_gt_rows.as<int64_t>(),
+                vmode == PG_U ? p->d_Z.as<double>() : p->d_gt_w.as<double>(), v, q, S.eta, ws.gco.as<double>(),
+                in_smem ? nullptr : ws.gsum.as<double>(), p->d_GtGinv.as<double>(), p->n_co, ws.alpha.as<double>(), R,
+                S.counter);
+        };
+        if (vmode == PG_U) go(k_proj_g<PG_U>);
+        else if (vmode == PG_LAM) go(k_proj_g<PG_LAM>);
+        else go(k_proj_g<PG_LAM_R>);
         note_launch();
     }
 
@@ -630,7 +697,7 @@ struct Runner {
             if (out != v) NLF_CUDA(cudaMemcpyAsync(out, v, sizeof(double) * nl * R, cudaMemcpyDeviceToDevice, st));
             return;
         }
-        coarse_alpha(v, 0);
+        coarse_alpha(v, PG_LAM);
         k_apply_galpha<<<grid_for(nl * R), 256, 0, st>>>(p->d_Gcol.as<int32_t>(), p->d_Gval.as<double>(), p->gw,
                                                          ws.alpha.as<double>(), v, -1.0, out, nl, R);
         note_launch();
@@ -640,7 +707,7 @@ struct Runner {
     template <int MODE> void project_dot(const double *v, const double *other, double *out, double tol = 0,
                                          int max_it = 0) {
         const int64_t nl = p->n_lambda;
-        if (p->n_co > 0) coarse_alpha(v, 0);
+        if (p->n_co > 0) coarse_alpha(v, PG_LAM);
         k_project_dot<MODE><<<red_grid(nl, R), RED_THREADS, 0, st>>>(
             p->d_Gcol.as<int32_t>(), p->d_Gval.as<double>(), p->gw, p->n_co > 0 ? ws.alpha.as<double>() : nullptr, v,
             other, out, nl, R, ws.partial.as<double>(), S, tol, max_it);
@@ -738,20 +805,6 @@ struct Runner {
                                                      note_launch();
     }
 
-    // q = F pv with (pv, q) and the ETA update fused into the final gather
-    template <typename T> void applyF_eta(const OpPool<T> &pool, const double *pv, double *q) {
-        const int64_t nl = p->n_lambda, nu = p->n_u;
-        T *x = ws.xU.as<T>();
-        k_gather_apply<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(),
-                                                            nullptr, pv, x, sd, p->d_u2sub.as<int32_t>(), nu, R, gate);
-        note_launch();
-        symv<T>(pool, 1, x, ws.yU.as<double>());
-        k_gather_b_eta<<<red_grid(nl, R), RED_THREADS, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(),
-                                                               ws.yU.as<double>(), pv, q, nl, R,
-                                                               ws.partial.as<double>(), S);
-        note_launch();
-    }
-
     template <typename T> void applyMinv(const OpPool<T> &pool, const double *v, double *out) {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         T *x = ws.xU.as<T>();
@@ -765,21 +818,38 @@ struct Runner {
                                                       note_launch();
     }
 
+    // One PCG iteration, ten kernels.  The updates of p, lambda and r are stored by the next
+    // iteration's k_check_update (kernels before it form p_new and r_new per row), and
+    // k_check_update sets the loop condition inside a graph loop.
     template <typename T> void iteration(const OpPool<T> &pool, double tol, int max_it) {
-        const int64_t nl = p->n_lambda;
+        const int64_t nl = p->n_lambda, nu = p->n_u;
         double *r = ws.r.as<double>(), *w = ws.w.as<double>(), *z = ws.z.as<double>(), *y = ws.y.as<double>(),
-               *pv = ws.pv.as<double>(), *q = ws.q.as<double>(), *lam = ws.dlam.as<double>();
-        project_dot<FIN_CHECK>(r, nullptr, w, tol, max_it);     // w = P r, ||w||, stop test
+               *pv = ws.pv.as<double>(), *q = ws.q.as<double>(), *lam = ws.dlam.as<double>(), *yU = ws.yU.as<double>();
+        T *x = ws.xU.as<T>();
+        const double *alpha = p->n_co > 0 ? ws.alpha.as<double>() : nullptr;
+        // p, lambda, r updated; w = P r, ||w||, stop test
+        if (p->n_co > 0) coarse_alpha(r, PG_LAM_R, q);
+        auto check = [&](auto kern) {
+            kern<<<red_grid(nl, R), RED_THREADS, 0, st>>>(p->d_Gcol.as<int32_t>(), p->d_Gval.as<double>(), p->gw, alpha, y,
+                                                          pv, lam, r, q, w, nl, R, ws.partial.as<double>(), S, tol,
+                                                          max_it, cond, max_it + 1);
+        };
+        if (use_cond) check(k_check_update<1>);
+        else check(k_check_update<0>);
+        note_launch();
         gate = S.n_active;
         applyMinv<T>(pool, w, z);                                // z = M^-1 w
         project_dot<FIN_BETA>(z, w, y);                          // y = P z, (y, w), beta
-        k_update_p<<<grid_for(nl * R), 256, 0, st>>>(y, S.beta, S.active, pv, nl, R);
+        // q = F p_new, (p_new, q), eta
+        k_gather_apply_p<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), pv,
+                                                              y, S.beta, S.active, x, sd, p->d_u2sub.as<int32_t>(),
+                                                              nu, R, gate);
         note_launch();
-        applyF_eta<T>(pool, pv, q);                              // q = F p, (p, q), eta
+        symv<T>(pool, 1, x, yU);
+        k_gather_b_eta<<<red_grid(nl, R), RED_THREADS, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), yU, pv, y,
+                                                               q, nl, R, ws.partial.as<double>(), S);
+        note_launch();
         gate = nullptr;
-        k_update_lr<<<grid_for(nl * R), 256, 0, st>>>(pv, q, S.eta, lam, r, nl, R, cond, use_cond ? 1 : 0,
-                                                      S.n_active, S.loops, max_it + 1);
-        note_launch();
     }
 
     // The PCG loop of a pass as one graph: a WHILE node whose body is one iteration; cached
@@ -851,7 +921,7 @@ struct Runner {
                                                          with_c ? ws.cvec.as<double>() : nullptr, ws.d.as<double>(), nl, R);
                                                          note_launch();
             if (p->n_co > 0) {
-                coarse_alpha(ws.fU.as<double>(), 1);
+                coarse_alpha(ws.fU.as<double>(), PG_U);
                 k_apply_galpha<<<grid_for(nl * R), 256, 0, st>>>(p->d_Gcol.as<int32_t>(), p->d_Gval.as<double>(),
                                                                  p->gw, ws.alpha.as<double>(), nullptr, 1.0, lam, nl, R);
                                                                  note_launch();
@@ -863,7 +933,11 @@ struct Runner {
             note_launch();
             project(ws.d.as<double>(), ws.w.as<double>());
             dot_final<FIN_NPD>(ws.w.as<double>(), ws.w.as<double>(), nl);
+            // p, y and q start at zero and FIN_NPD set eta = beta = 0: the updates the first
+            // iteration stores are empty
             NLF_CUDA(cudaMemsetAsync(ws.pv.p, 0, sizeof(double) * nl * R, st));
+            NLF_CUDA(cudaMemsetAsync(ws.y.p, 0, sizeof(double) * nl * R, st));
+            NLF_CUDA(cudaMemsetAsync(ws.q.p, 0, sizeof(double) * nl * R, st));
             const int chunk = 4;
             int done = 0, n_active = R;
             cudaGraphExec_t exec = nullptr;
@@ -913,7 +987,7 @@ struct Runner {
             note_launch();
             symv<T>(pool, 1, x, ws.uU.as<double>());
             if (p->n_co > 0) {
-                coarse_alpha(ws.r.as<double>(), 0);
+                coarse_alpha(ws.r.as<double>(), PG_LAM);
                 k_apply_zalpha<<<grid_for(nu * R), 256, 0, st>>>(sd, p->d_u2sub.as<int32_t>(), p->d_Z.as<double>(),
                                                                  ws.alpha.as<double>(), -1.0, ws.uU.as<double>(), nu, R);
                 note_launch();
