@@ -96,7 +96,11 @@ typedef struct {
  * graph_loop (batched only): 1 = each PCG loop runs on the device as one graph with a
  *          WHILE node (no host round trips); 0 = graphs of 4 iterations with a host check
  *          of convergence in between (for profilers that cannot look inside conditional
- *          graphs).  Profiling (nlfeti_set_profiling) always uses the second form. */
+ *          graphs).  Profiling (nlfeti_set_profiling) always uses the second form.
+ * precond_fp16 (mixed path): 1 = the scaled Dirichlet preconditioner applies S_k from an
+ *          FP16 copy scaled by one power of two (half the bytes of the preconditioner apply;
+ *          the preconditioner only steers the PCG, the accuracy reached is set by F and the
+ *          FP64 refinement); 0 = from the FP32 S_k.  nlfeti_apply always uses the FP32 S_k. */
 typedef struct {
     int precision;
     double tol;
@@ -107,6 +111,7 @@ typedef struct {
     int batched;
     size_t hbm_budget;
     int graph_loop;
+    int precond_fp16;
 } nlfeti_options;
 
 typedef struct {

@@ -36,7 +36,8 @@ class NlfetiError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_it", C.c_int), ("max_refine", C.c_int),
                 ("inner_tol", C.c_double), ("refine_tol", C.c_double), ("batched", C.c_int),
-                ("hbm_budget", C.c_size_t), ("graph_loop", C.c_int)]
+                ("hbm_budget", C.c_size_t), ("graph_loop", C.c_int),
+                ("precond_fp16", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -352,6 +352,7 @@ void nlfeti_default_options(nlfeti_options *o) {
     o->batched = 1;
     o->hbm_budget = 0;
     o->graph_loop = 1;
+    o->precond_fp16 = 1;
 }
 
 nlfeti_status nlfeti_create(nlfeti_ctx **out, const nlfeti_options *opt, void *cuda_stream,

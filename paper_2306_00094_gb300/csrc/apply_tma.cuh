@@ -13,6 +13,10 @@
 // through a second mbarrier.  The producer runs ahead across item boundaries, so the copy
 // engine keeps up to NS * 32 KB per CTA in flight while the consumers compute.
 // With more than RC right-hand sides the rows of an item are streamed once per block of RC.
+// The operator may be stored in a narrower type MT than the arithmetic type T (FP16 copy of
+// S_k for the preconditioner of the mixed path): a stage then holds the same columns with
+// rows of CW * sizeof(MT) bytes, the consumers widen each 4-entry group to T before the same
+// row step, and the result is multiplied by oscale (the power of two the copy was scaled by).
 //
 // Every wait is bounded: a wait that runs out sets *err (the workspace's error word, read by
 // the host after the solve), the consumers stop, the producer waits (again bounded) for the
@@ -23,10 +27,13 @@
 
 constexpr int APPLY_CB = 1024;                      // bytes of one row (or one x column) per stage
 constexpr int APPLY_NS = 5;                         // stages (up to 200 KB of shared memory, one CTA per SM)
-// a stage: 32 operator rows, then RC columns of x
-__host__ __device__ constexpr int apply_stage_bytes(int rc) { return (32 + rc) * APPLY_CB; }
+constexpr int APPLY_NS_H = 8;                       // stages with an FP16 operator (24 KB each at RC = 8)
+// a stage: 32 operator rows of mrow bytes, then RC columns of x (APPLY_CB bytes each)
+__host__ __device__ constexpr int apply_stage_bytes(int rc, int mrow = APPLY_CB) { return 32 * mrow + rc * APPLY_CB; }
 // the ring is aligned to 1 KB inside the dynamic shared memory (tensor copies want 128 B)
-__host__ __device__ constexpr int apply_smem_bytes(int rc, int ns) { return ns * apply_stage_bytes(rc) + 1024; }
+__host__ __device__ constexpr int apply_smem_bytes(int rc, int ns, int mrow = APPLY_CB) {
+    return ns * apply_stage_bytes(rc, mrow) + 1024;
+}
 constexpr int APPLY_THREADS = 9 * 32;               // 8 consumer warps + 1 producer warp
 constexpr long long APPLY_WAIT_TRIES = 1ll << 24;   // bounded mbarrier waits (seconds)
 
@@ -83,19 +90,24 @@ inline CUresult encode_apply_map(Encode encode, CUtensorMap *map, const void *ba
     const cuuint64_t strides[1] = {(cuuint64_t)ld * (cuuint64_t)elem_size};
     const cuuint32_t box[2] = {(cuuint32_t)(box_bytes / elem_size), (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1u, 1u};
-    return encode(map, elem_size == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2u,
+    const CUtensorMapDataType dt = elem_size == 2   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : elem_size == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    return encode(map, dt, 2u,
                   const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
-template <typename T, int RC, int NS = APPLY_NS, int MINB = 1>
+template <typename T, int RC, int NS = APPLY_NS, int MINB = 1, typename MT = T>
 __global__ void __launch_bounds__(APPLY_THREADS, MINB)
     k_apply_tma(const CUtensorMap *maps, const CUtensorMap *xmaps, int use_sp, const SubdomainDesc *sd,
-                const int32_t *sched_ptr, const int32_t *sched_items, double *y, int R, const int *gate, int *err) {
+                const int32_t *sched_ptr, const int32_t *sched_items, double *y, int R, const int *gate, int *err,
+                double oscale = 1.0) {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
     constexpr int CW = APPLY_CB / (int)sizeof(T);   // columns per stage row
-    constexpr int STAGE = apply_stage_bytes(RC);
+    constexpr int MROW = CW * (int)sizeof(MT);      // operator bytes per stage row
+    constexpr int STAGE = apply_stage_bytes(RC, MROW);
     extern __shared__ __align__(128) unsigned char ring_raw[];
     unsigned char *ring = ring_raw + ((1024u - (smem_u32(ring_raw) & 1023u)) & 1023u);
     __shared__ uint64_t full[NS], empty[NS];
@@ -133,9 +145,9 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
                 // the tiles always land whole (out-of-range rows and columns as zeros)
                 if (lane == 0) {
                     unsigned char *stg = ring + s * STAGE;
-                    mbar_arrive_expect_tx(&full[s], (32 + RC) * APPLY_CB);
+                    mbar_arrive_expect_tx(&full[s], STAGE);
                     tile_g2s(stg, map, l0, i0, &full[s]);
-                    tile_g2s(stg + 32 * APPLY_CB, xmap, l0, c0, &full[s]);
+                    tile_g2s(stg + 32 * MROW, xmap, l0, c0, &full[s]);
                 }
                 __syncwarp();
             }
@@ -169,14 +181,14 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
                     return;                           // the whole warp (the vote is uniform)
                 }
                 const int cw = min(CW, ncp - l0);
-                const T *st = reinterpret_cast<const T *>(ring + s * STAGE);
-                const T *xs = st + 32 * CW;
+                const MT *st = reinterpret_cast<const MT *>(ring + s * STAGE);
+                const T *xs = reinterpret_cast<const T *>(ring + s * STAGE + 32 * MROW);
                 if (ib < n) {
                     for (int l = lane * W; l < cw; l += 32 * W) {
                         V mv[4];
 #pragma unroll
                         for (int r = 0; r < 4; ++r)
-                            mv[r] = *reinterpret_cast<const V *>(st + (warp * 4 + min(r, n - 1 - ib)) * CW + l);
+                            mv[r] = load_widen<T, MT>(st + (warp * 4 + min(r, n - 1 - ib)) * CW + l);
                         rows_step<T, RC>(mv, [&](int c) {
                             return c < rc ? *reinterpret_cast<const V *>(xs + c * CW + l) : V{};
                         }, acc);
@@ -194,7 +206,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
             const T tot = warp_reduce_scatter<T, NV>(v, lane);
             constexpr int G = 32 / NV;
             const int idx = lane / G, r = idx / RC, c = idx % RC, i = ib + r;
-            if (lane % G == 0 && c < rc && i < n) y[(yoff + i) * R + c0 + c] = (double)tot;
+            if (lane % G == 0 && c < rc && i < n) y[(yoff + i) * R + c0 + c] = (double)tot * oscale;
         }
     }
 }

@@ -131,6 +131,9 @@ template <typename T> struct OpPool {   // operators of one precision
     nlf::DevMem Ahi, Alo;                // FP32 pool only: A^k = Ahi + Alo (FP32 pairs, swept-matrix layout),
                                          // for the double-single refinement residual
     nlf::DevMem amaps;                   // FP32 pool only: tensor maps of Ahi and Alo (2 per subdomain)
+    nlf::DevMem Sh;                      // FP32 pool only: S_k * hscale in FP16 (preconditioner of the PCG)
+    nlf::DevMem hmaps;                   // FP32 pool only: tensor maps of Sh (slot 2k per subdomain)
+    double hscale = 1.0;                 // power of two: largest |S_k| entry * hscale in [2^13, 2^14)
     bool ready = false;
 };
 

@@ -22,6 +22,8 @@
 #include <cstring>
 #include <type_traits>
 
+#include <cuda_fp16.h>
+
 #include "solve.hpp"
 
 namespace nlf {
@@ -714,25 +716,28 @@ struct Runner {
         note_launch();
     }
 
-    template <typename T, int RC, int MODE> void rows_launch(const T *base, int use_sp, const int32_t *it, int nitems,
-                                                            const T *x, const double *xa, const double *xb, double *y) {
-        k_rows<T, RC, MODE><<<nitems, 256, 0, st>>>(base, use_sp, sd, it, x, xa, xb, y, R,
-                                                    MODE == ROWS_APPLY ? gate : nullptr);
+    template <typename T, int RC, int MODE, typename MT> void rows_launch(const MT *base, int use_sp, const int32_t *it,
+                                                                         int nitems, const T *x, const double *xa,
+                                                                         const double *xb, double *y, double oscale) {
+        k_rows<T, RC, MODE, MT><<<nitems, 256, 0, st>>>(base, use_sp, sd, it, x, xa, xb, y, R,
+                                                        MODE == ROWS_APPLY ? gate : nullptr, oscale);
         note_launch();
     }
 
     // one row-product stage over every subdomain: one launch (batched) or one per subdomain;
-    // returns the number of launches
-    template <typename T, int MODE> int rows(const T *base, int use_sp, const T *x, const double *xa, const double *xb,
-                                             double *y, const DevMem &items, const std::vector<int> &off) {
+    // returns the number of launches.  MT: stored operator type (FP16 copy of S_k, result
+    // scaled by oscale)
+    template <typename T, int MODE, typename MT = T>
+    int rows(const MT *base, int use_sp, const T *x, const double *xa, const double *xb, double *y, const DevMem &items,
+             const std::vector<int> &off, double oscale = 1.0) {
         const int rc = R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1));
         auto go = [&](const int32_t *it, int nitems) {
             if (nitems <= 0) return 0;
             switch (rc) {
-                case 8: rows_launch<T, 8, MODE>(base, use_sp, it, nitems, x, xa, xb, y); break;
-                case 4: rows_launch<T, 4, MODE>(base, use_sp, it, nitems, x, xa, xb, y); break;
-                case 2: rows_launch<T, 2, MODE>(base, use_sp, it, nitems, x, xa, xb, y); break;
-                default: rows_launch<T, 1, MODE>(base, use_sp, it, nitems, x, xa, xb, y); break;
+                case 8: rows_launch<T, 8, MODE, MT>(base, use_sp, it, nitems, x, xa, xb, y, oscale); break;
+                case 4: rows_launch<T, 4, MODE, MT>(base, use_sp, it, nitems, x, xa, xb, y, oscale); break;
+                case 2: rows_launch<T, 2, MODE, MT>(base, use_sp, it, nitems, x, xa, xb, y, oscale); break;
+                default: rows_launch<T, 1, MODE, MT>(base, use_sp, it, nitems, x, xa, xb, y, oscale); break;
             }
             return 1;
         };
@@ -748,10 +753,21 @@ struct Runner {
 
     // the batched interface apply: persistent tensor-copy pipeline over the balanced schedule;
     // x is read through the workspace's tensor maps of xU
-    template <typename T> int apply_tma(const OpPool<T> &pool, int use_sp, double *y) {
+    // half: S_k from the FP16 copy (FP32 pool, use_sp = 0)
+    template <typename T> int apply_tma(const OpPool<T> &pool, int use_sp, double *y, bool half = false) {
         const int rc = R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1));
         auto go = [&](auto rc_tag) {
             constexpr int RCT = decltype(rc_tag)::value;
+            if constexpr (std::is_same<T, float>::value) {
+                if (half) {
+                    k_apply_tma<float, RCT, APPLY_NS_H, 1, __half>
+                        <<<p->sched_ctas, APPLY_THREADS, apply_smem_bytes(RCT, APPLY_NS_H, APPLY_CB / 2), st>>>(
+                            pool.hmaps.template as<CUtensorMap>(), ws.xmaps[0].template as<CUtensorMap>(), 0, sd,
+                            p->d_sched_ptr.as<int32_t>(), p->d_sched_items.as<int32_t>(), y, R, gate, S.err,
+                            1.0 / pool.hscale);
+                    return;
+                }
+            }
             k_apply_tma<T, RCT><<<p->sched_ctas, APPLY_THREADS, apply_smem_bytes(RCT, APPLY_NS), st>>>(
                 pool.maps.template as<CUtensorMap>(), ws.xmaps[sizeof(T) == 8 ? 1 : 0].template as<CUtensorMap>(),
                 use_sp, sd, p->d_sched_ptr.as<int32_t>(), p->d_sched_items.as<int32_t>(), y, R, gate, S.err);
@@ -766,9 +782,11 @@ struct Runner {
         return 1;
     }
 
-    // y = S^+ x (use_sp = 1) or S x (use_sp = 0) on every subdomain
-    template <typename T> void symv(const OpPool<T> &pool, int use_sp, const T *x, double *y) {
+    // y = S^+ x (use_sp = 1) or S x (use_sp = 0) on every subdomain.  precond: the apply is
+    // the preconditioner's, which takes S_k from its FP16 copy in the mixed path (when enabled)
+    template <typename T> void symv(const OpPool<T> &pool, int use_sp, const T *x, double *y, bool precond = false) {
         if (p->n_u == 0) return;
+        const bool half = std::is_same<T, float>::value && precond && !use_sp && p->opt.precond_fp16 && pool.Sh.p;
         const T *base = use_sp ? pool.Sp.template as<T>() : pool.S.template as<T>();
         Slot slot{};
         const bool timed = p->prof_on;
@@ -779,14 +797,22 @@ struct Runner {
             NLF_CUDA(cudaEventCreate(&slot.b));
             NLF_CUDA(cudaEventRecordWithFlags(slot.a, st, rec_flags));
         }
-        const int launches = (p->opt.batched && p->sched_ctas > 0)
-                                 ? apply_tma<T>(pool, use_sp, y)
-                                 : rows<T, ROWS_APPLY>(base, use_sp, x, nullptr, nullptr, y, p->d_items, p->item_off);
+        int launches = 0;
+        if (p->opt.batched && p->sched_ctas > 0) {
+            launches = apply_tma<T>(pool, use_sp, y, half);
+        } else if (half) {
+            if constexpr (std::is_same<T, float>::value)
+                launches = rows<T, ROWS_APPLY, __half>(pool.Sh.template as<__half>(), 0, x, nullptr, nullptr, y,
+                                                       p->d_items, p->item_off, 1.0 / pool.hscale);
+        } else {
+            launches = rows<T, ROWS_APPLY>(base, use_sp, x, nullptr, nullptr, y, p->d_items, p->item_off);
+        }
         if (timed) {
             NLF_CUDA(cudaEventRecordWithFlags(slot.b, st, rec_flags));
             double bytes = 0;
+            const double me = half ? 2.0 : (double)sizeof(T);
             for (const auto &d : p->sd)
-                bytes += (double)d.nG * d.ldG * sizeof(T) + (double)d.nG * R * (sizeof(T) + sizeof(double));
+                bytes += (double)d.nG * d.ldG * me + (double)d.nG * R * (sizeof(T) + sizeof(double));
             slot.launches = launches;
             slot.bytes = bytes;
             (capturing ? graph_slots : eager_slots).push_back(slot);
@@ -805,14 +831,14 @@ struct Runner {
                                                      note_launch();
     }
 
-    template <typename T> void applyMinv(const OpPool<T> &pool, const double *v, double *out) {
+    template <typename T> void applyMinv(const OpPool<T> &pool, const double *v, double *out, bool precond = false) {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         T *x = ws.xU.as<T>();
         k_gather_apply<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_BDt_ptr.as<int64_t>(), p->d_BDt_row.as<int64_t>(),
                                                             p->d_BDt_val.as<double>(), v, x, sd,
                                                             p->d_u2sub.as<int32_t>(), nu, R, gate);
         note_launch();
-        symv<T>(pool, 0, x, ws.yU.as<double>());
+        symv<T>(pool, 0, x, ws.yU.as<double>(), precond);
         k_gather_bd<<<grid_for(nl * R), 256, 0, st>>>(p->d_BD_ptr.as<int64_t>(), p->d_BD_col.as<int64_t>(),
                                                       p->d_BD_val.as<double>(), ws.yU.as<double>(), out, nl, R);
                                                       note_launch();
@@ -838,7 +864,7 @@ struct Runner {
         else check(k_check_update<0>);
         note_launch();
         gate = S.n_active;
-        applyMinv<T>(pool, w, z);                                // z = M^-1 w
+        applyMinv<T>(pool, w, z, true);                          // z = M^-1 w
         project_dot<FIN_BETA>(z, w, y);                          // y = P z, (y, w), beta
         // q = F p_new, (p_new, q), eta
         k_gather_apply_p<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), pv,
@@ -857,8 +883,11 @@ struct Runner {
     template <typename T> const PcgGraph &while_graph(const OpPool<T> &pool, double tol, int max_it) {
         const int prec = std::is_same<T, float>::value ? 1 : 0;
         for (const auto &g : ws.graphs)
-            if (g.factor_gen == p->factor_gen && g.precision == prec && g.tol == tol && g.max_it == max_it) return g;
+            if (g.factor_gen == p->factor_gen && g.precision == prec && g.tol == tol && g.max_it == max_it &&
+                g.precond_fp16 == p->opt.precond_fp16)
+                return g;
         PcgGraph g;
+        g.precond_fp16 = p->opt.precond_fp16;
         g.factor_gen = p->factor_gen;
         g.precision = prec;
         g.tol = tol;
@@ -1281,6 +1310,15 @@ int apply_tma_ctas() {
     fit(k_apply_tma<float, 1>, 1); fit(k_apply_tma<float, 2>, 2); fit(k_apply_tma<float, 4>, 4);
     fit(k_apply_tma<float, 8>, 8); fit(k_apply_tma<double, 1>, 1); fit(k_apply_tma<double, 2>, 2);
     fit(k_apply_tma<double, 4>, 4); fit(k_apply_tma<double, 8>, 8);
+    auto fit_h = [&](auto kern, int rc) {
+        const int smem = apply_smem_bytes(rc, APPLY_NS_H, APPLY_CB / 2);
+        NLF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int b = 0;
+        NLF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, APPLY_THREADS, smem));
+        per_sm = std::min(per_sm, b);
+    };
+    fit_h(k_apply_tma<float, 1, APPLY_NS_H, 1, __half>, 1); fit_h(k_apply_tma<float, 2, APPLY_NS_H, 1, __half>, 2);
+    fit_h(k_apply_tma<float, 4, APPLY_NS_H, 1, __half>, 4); fit_h(k_apply_tma<float, 8, APPLY_NS_H, 1, __half>, 8);
     if (per_sm < 1) fail(NLFETI_E_CUDA, "the interface apply does not fit on an SM");
     return sms * per_sm;
 }
@@ -1333,6 +1371,20 @@ template <typename T> void encode_apply_maps(nlfeti_problem *p, OpPool<T> &pool)
         }
         pool.amaps.alloc(p->ctx, sizeof(CUtensorMap) * am.size());
         NLF_CUDA(cudaMemcpyAsync(pool.amaps.p, am.data(), sizeof(CUtensorMap) * am.size(), cudaMemcpyHostToDevice,
+                                 p->ctx->stream));
+        // the FP16 copy of S_k: tiles of 32 rows x 256 entries (512 bytes), the columns of a
+        // stage of the FP32 x tiles
+        std::vector<CUtensorMap> hm(2 * std::max(1, p->K));
+        std::memset(hm.data(), 0, sizeof(CUtensorMap) * hm.size());
+        for (int k = 0; k < p->K; ++k) {
+            const SubdomainDesc &d = p->sd[k];
+            if (d.nG == 0) continue;
+            if (encode_apply_map(encode_tiled(), &hm[2 * k], pool.Sh.template as<__half>() + d.offS, d.ldG, d.nG, 2, 32,
+                                 APPLY_CB / 2) != CUDA_SUCCESS)
+                fail(NLFETI_E_CUDA, "cuTensorMapEncodeTiled failed for the FP16 preconditioner operator");
+        }
+        pool.hmaps.alloc(p->ctx, sizeof(CUtensorMap) * hm.size());
+        NLF_CUDA(cudaMemcpyAsync(pool.hmaps.p, hm.data(), sizeof(CUtensorMap) * hm.size(), cudaMemcpyHostToDevice,
                                  p->ctx->stream));
     }
     NLF_CUDA(cudaStreamSynchronize(p->ctx->stream));

@@ -23,6 +23,8 @@
 #include <string>
 #include <type_traits>
 
+#include <cuda_fp16.h>
+
 #include "internal.hpp"
 
 constexpr size_t kNoallocScratchBytes = NLFETI_NOALLOC_SCRATCH_BYTES;

@@ -18,9 +18,38 @@
 //   chunks of ROWS_CW columns ([c][column], row stride padded by 4 against bank conflicts).
 #pragma once
 
+// needs <cuda_fp16.h> and <type_traits>, included before the enclosing namespace
+
 template <typename T> struct Vec;
 template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
 template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
+
+// W consecutive operator entries of type MT at p (16-byte aligned for MT = T, 8-byte for an
+// FP16 copy) as the arithmetic vector of T; widening FP16 to FP32 is exact
+template <typename T, typename MT>
+__device__ __forceinline__ typename Vec<T>::type load_widen(const MT *p) {
+    if constexpr (std::is_same<MT, T>::value) {
+        return *reinterpret_cast<const typename Vec<T>::type *>(p);
+    } else {
+        static_assert(std::is_same<T, float>::value && std::is_same<MT, __half>::value, "FP16 copies widen to FP32");
+        const uint2 raw = *reinterpret_cast<const uint2 *>(p);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+// the same from global memory, streamed (not kept in L1)
+template <typename T, typename MT>
+__device__ __forceinline__ typename Vec<T>::type ldcs_widen(const MT *p) {
+    if constexpr (std::is_same<MT, T>::value) {
+        return __ldcs(reinterpret_cast<const typename Vec<T>::type *>(p));
+    } else {
+        const uint2 raw = __ldcs(reinterpret_cast<const uint2 *>(p));
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+}
 
 static_assert(kApplyRows == 32, "the row kernel owns 32 rows per CTA (8 warps x 4)");
 constexpr int ROWS_CW = 512;      // staged columns per chunk (forcing / back substitution)
@@ -85,10 +114,12 @@ __device__ __forceinline__ T warp_reduce_scatter(T (&v)[V], int lane) {
     return t;
 }
 
-template <typename T, int RC, int MODE>
-__global__ void __launch_bounds__(256, 2) k_rows(const T *base, int use_sp, const SubdomainDesc *sd, const int32_t *items,
+// MT: type of the stored operator (APPLY with the FP16 copy of S_k: __half, the result scaled by
+// oscale); T otherwise
+template <typename T, int RC, int MODE, typename MT = T>
+__global__ void __launch_bounds__(256, 2) k_rows(const MT *base, int use_sp, const SubdomainDesc *sd, const int32_t *items,
                                                  const T *x, const double *xa, const double *xb, double *y, int R,
-                                                 const int *gate) {
+                                                 const int *gate, double oscale = 1.0) {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
     constexpr int XS = ROWS_CW + 4;
@@ -101,10 +132,10 @@ __global__ void __launch_bounds__(256, 2) k_rows(const T *base, int use_sp, cons
     const int ld = MODE == ROWS_APPLY ? d.ldG : d.ldM;
     const int ncp = min(ld, (ncols + 7) / 8 * 8);                           // padded columns
     const int rbase = MODE == ROWS_FORCING ? d.nO : 0;                      // first matrix row
-    const T *M = base + (MODE == ROWS_APPLY ? (use_sp ? d.offSp : d.offS) : d.offM);
+    const MT *M = base + (MODE == ROWS_APPLY ? (use_sp ? d.offSp : d.offS) : d.offM);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int ib = row0 + warp * 4;
-    const T *Mr[4];
+    const MT *Mr[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) Mr[r] = M + (int64_t)(rbase + min(ib + r, n - 1)) * ld;
     for (int c0 = 0; c0 < R; c0 += RC) {
@@ -123,7 +154,7 @@ __global__ void __launch_bounds__(256, 2) k_rows(const T *base, int use_sp, cons
 #pragma unroll
                     for (int u = 0; u < 2; ++u)
 #pragma unroll
-                        for (int r = 0; r < 4; ++r) mv[u][r] = __ldcs(reinterpret_cast<const V *>(Mr[r] + l + u * 32 * W));
+                        for (int r = 0; r < 4; ++r) mv[u][r] = ldcs_widen<T, MT>(Mr[r] + l + u * 32 * W);
 #pragma unroll
                     for (int u = 0; u < 2; ++u)
                         rows_step<T, RC>(mv[u], [&](int c) {
@@ -133,7 +164,7 @@ __global__ void __launch_bounds__(256, 2) k_rows(const T *base, int use_sp, cons
                 for (; l < ncp; l += 32 * W) {
                     V mv[4];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) mv[r] = __ldcs(reinterpret_cast<const V *>(Mr[r] + l));
+                    for (int r = 0; r < 4; ++r) mv[r] = ldcs_widen<T, MT>(Mr[r] + l);
                     rows_step<T, RC>(mv, [&](int c) {
                         return c < rc ? __ldg(reinterpret_cast<const V *>(xk + (int64_t)c * ld + l)) : V{};
                     }, acc);
@@ -157,7 +188,7 @@ __global__ void __launch_bounds__(256, 2) k_rows(const T *base, int use_sp, cons
                     for (int l = lane * W; l < cw; l += 32 * W) {
                         V mv[4];
 #pragma unroll
-                        for (int r = 0; r < 4; ++r) mv[r] = __ldcs(reinterpret_cast<const V *>(Mr[r] + l0 + l));
+                        for (int r = 0; r < 4; ++r) mv[r] = ldcs_widen<T, MT>(Mr[r] + l0 + l);
                         rows_step<T, RC>(mv, [&](int c) { return *reinterpret_cast<const V *>(xs + c * XS + l); },
                                          acc);
                     }
@@ -177,7 +208,7 @@ __global__ void __launch_bounds__(256, 2) k_rows(const T *base, int use_sp, cons
         const int idx = lane / G, r = idx / RC, c = idx % RC;
         const int i = ib + r;
         if (lane % G == 0 && c < rc && i < n) {
-            if (MODE == ROWS_APPLY) y[(d.offU + i) * R + c0 + c] = (double)tot;
+            if (MODE == ROWS_APPLY) y[(d.offU + i) * R + c0 + c] = (double)tot * oscale;
             else if (MODE == ROWS_FORCING)
                 y[(d.offU + i) * R + c0 + c] = xa[(d.offV + d.nO + i) * R + c0 + c] - (double)tot;
             else y[(d.offV + i) * R + c0 + c] = -(double)tot;

@@ -13,6 +13,7 @@ struct PcgGraph {
     double tol = 0;
     cudaGraphExec_t exec = nullptr;
     int64_t body_launches = 0;      // kernels per loop iteration
+    int precond_fp16 = 0;           // the preconditioner apply it was captured with
 };
 
 struct SolveWS {

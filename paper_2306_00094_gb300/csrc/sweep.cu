@@ -19,6 +19,9 @@
 #include <algorithm>
 #include <type_traits>
 #include <cmath>
+#include <cstring>
+
+#include <cuda_fp16.h>
 
 #include "internal.hpp"
 
@@ -201,6 +204,21 @@ __global__ void k_split_ds(const double *A, float *hi, float *lo, const Subdomai
 }
 
 // copy the Gamma block of the swept matrix into S (and into Sp with pinning)
+// largest |entry| of an FP32 array into *mx (bits of a non-negative float order as unsigned)
+__global__ void k_absmax(const float *a, int64_t n, unsigned *mx) {
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(a[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(mx, __float_as_uint(m));
+}
+
+// h = half(a * scale), scale a power of two (the product is exact)
+__global__ void k_to_half(const float *a, int64_t n, float scale, __half *h) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        h[i] = __float2half_rn(a[i] * scale);
+}
+
 template <typename T> __global__ void k_extract(const T *Mpool, T *Spool, T *Sppool, const SubdomainDesc *sd) {
     const SubdomainDesc d = sd[blockIdx.y];
     const int64_t nG = d.nG, ld = d.ldG;
@@ -470,6 +488,25 @@ template <typename T> void factor_ops(nlfeti_problem *p, OpPool<T> &pool) {
     int flag = 0;
     NLF_CUDA(cudaMemcpy(&flag, p->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) fail(NLFETI_E_NOT_SPD, "a pivot block of a subdomain operator was not positive definite");
+    if constexpr (std::is_same<T, float>::value) {
+        // FP16 copy of S_k for the preconditioner, scaled by one power of two so that the
+        // largest entry lies in [2^13, 2^14) (FP16 keeps 11 bits from 2^-14 up to 65504)
+        DevMem mx;
+        mx.alloc(c, sizeof(unsigned));
+        NLF_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned), c->stream));
+        const int64_t n = std::max<int64_t>(poolG, 1);
+        k_absmax<<<256, 256, 0, c->stream>>>(pool.S.template as<float>(), n, mx.as<unsigned>());
+        unsigned bits = 0;
+        NLF_CUDA(cudaMemcpyAsync(&bits, mx.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+        NLF_CUDA(cudaStreamSynchronize(c->stream));
+        float m;
+        std::memcpy(&m, &bits, sizeof(m));
+        pool.hscale = (m > 0.f && std::isfinite(m)) ? std::ldexp(1.0, 13 - std::ilogb(m)) : 1.0;
+        pool.Sh.alloc(c, sizeof(__half) * n);
+        k_to_half<<<512, 256, 0, c->stream>>>(pool.S.template as<float>(), n, (float)pool.hscale,
+                                              pool.Sh.template as<__half>());
+        NLF_CUDA(cudaGetLastError());
+    }
     encode_apply_maps<T>(p, pool);
     pool.ready = true;
 }

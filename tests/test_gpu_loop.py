@@ -81,3 +81,20 @@ def test_launch_count_of_graph_loop(setup):
     n = p.profile()["kernel_launches"]
     # at least the interface applies of every iteration (two per iteration) were counted
     assert n >= 2 * st["iterations"]
+
+
+def test_fp16_preconditioner_reaches_the_same_accuracy(setup):
+    """The FP16 copy of S_k only steers the PCG: with it and without it the mixed path reaches
+    the oracle's solution to the same tolerance (the refinement fixes the fixed point)."""
+    from oracle import problem as oprob
+    binding, w, p = setup
+    ref = oprob.Monolithic(w.mesh, w.kernel).solve(w.rhs, w.rhs_kind)
+    out = {}
+    for fp16 in (0, 1):
+        p.set_options(binding.default_options(precision=1, precond_fp16=fp16))
+        u, st = p.solve(w.rhs, w.rhs_kind)
+        assert (oprob.rel_nodal_error(u, ref, w.mesh, w.kernel.ncomp) <= 1e-8).all()
+        out[fp16] = (u, st)
+    scale = np.abs(out[0][0]).max()
+    assert np.abs(out[1][0] - out[0][0]).max() <= 1e-8 * scale
+    assert abs(out[1][1]["iterations"] - out[0][1]["iterations"]) <= max(3, out[0][1]["iterations"] // 5)
