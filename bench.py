@@ -112,10 +112,10 @@ def percentile(xs, q):
     return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
 
 
-def profile_traffic(kernel_src_hash):
-    """DRAM bytes per launch of the apply kernel from the committed ncu summary, if it matches
+def profile_traffic(kernel_src_hash, name="k_apply_tma_cfg2.md"):
+    """DRAM bytes per launch of an apply kernel from the committed ncu summary, if it matches
     the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_apply_tma_cfg2.md")
+    path = os.path.join(ROOT, "profiles", name)
     try:
         txt = open(path).read()
     except OSError:
@@ -217,14 +217,17 @@ def run_ours(args):
         prob.set_profiling(False)
     prof = prob.profile()
     hbm, peak_kind = peaks()
-    achieved = None
-    if prof["apply_launches"] > 0 and prof["apply_ms"] > 0:
-        bytes_per_launch = prof["apply_bytes"] / prof["apply_launches"]
-        avg_s = prof["apply_ms"] / prof["apply_launches"] / 1e3
-        achieved = bytes_per_launch / avg_s / 1e9
-    else:
-        bytes_per_launch, avg_s = None, None
-    apply_share = prof["apply_ms"] / prof_ms if prof_ms else None
+
+    def apply_roofline(key):
+        n, ms, b = prof[key + "_launches"], prof[key + "_ms"], prof[key + "_bytes"]
+        if n > 0 and ms > 0:
+            bpl, avg = b / n, ms / n / 1e3
+            return bpl / avg / 1e9, bpl, avg, n, ms / prof_ms if prof_ms else None
+        return None, None, None, n, None
+
+    # the S_k^+ applies (FP32 operator) and the preconditioner's applies (FP16 copy of S_k)
+    achieved, bytes_per_launch, avg_s, n_apply, apply_share = apply_roofline("apply")
+    h_ach, h_bpl, h_avg, n_half, h_share = apply_roofline("half_apply")
 
     if args.only_timed:
         if rank == 0:
@@ -296,14 +299,20 @@ def run_ours(args):
                    "step": "warm solve request (operators resident), setup/factor excluded"},
         "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99)},
         "iterations": stats[-1]["iterations"], "refine_sweeps": stats[-1]["refine_sweeps"],
-        "roofline": {"kernel": "k_apply_tma<float, 8> (dense S_k^+ / S_k apply, tensor-copy pipeline)", "bound": "hbm",
-                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "roofline": {"kernel": "k_apply_tma<float, 8, 2, 2, float> (dense S_k^+ apply, FP32, tensor-copy pipeline)",
+                     "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "peak_source": peak_kind,
                      "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_s * 1e6 if avg_s else None,
-                     "launches": prof["apply_launches"], "share_of_step_time": apply_share,
+                     "launches": n_apply, "share_of_step_time": apply_share,
                      "timing": "CUDA events around each apply launch over a second timed region of the same "
                                f"{args.steps} steps",
                      "traffic": profile_traffic(kernel_source_hash())},
+        "roofline_precond": {"kernel": "k_apply_tma<float, 8, 4, 2, __half> (preconditioner S_k apply, FP16 copy)",
+                             "bound": "hbm", "achieved": h_ach, "peak": hbm, "unit": "GB/s",
+                             "frac": (h_ach / hbm) if h_ach else None, "peak_source": peak_kind,
+                             "bytes_per_launch": h_bpl, "avg_launch_us": h_avg * 1e6 if h_avg else None,
+                             "launches": n_half, "share_of_step_time": h_share,
+                             "traffic": profile_traffic(kernel_source_hash(), "k_apply_tma_fp16_cfg2.md")},
         "gpu_launches": launches,
         "e2e": e2e,
         "plain_fp64_per_subdomain": plain_res,

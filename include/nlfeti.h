@@ -212,13 +212,18 @@ nlfeti_status nlfeti_apply_schur_noalloc(nlfeti_problem *p, int which, int preci
  * every launch of the dense interface apply (the per-iteration products with S_k^+ and
  * S_k) is bracketed by CUDA events on the library stream, also inside captured graphs.
  * kernel_launches counts every kernel of the library launched by solves (graph kernel
- * nodes included).  apply_bytes: operator bytes read by those launches (sum over
- * launches of sum_k n_gamma_k * ld_k * sizeof(element)).  Reading resets the counters. */
+ * nodes included).  apply_*: launches, milliseconds and bytes read (operator entries plus
+ * x and y per launch) of the applies with the operators in their stored precision;
+ * half_apply_*: the same for the preconditioner's applies of the FP16 copy of S_k (mixed
+ * path with precond_fp16).  Reading resets the counters. */
 typedef struct {
     int64_t kernel_launches;
     int64_t apply_launches;
     double apply_ms;
     double apply_bytes;
+    int64_t half_apply_launches;
+    double half_apply_ms;
+    double half_apply_bytes;
 } nlfeti_profile;
 nlfeti_status nlfeti_set_profiling(nlfeti_problem *p, int on);
 nlfeti_status nlfeti_get_profile(nlfeti_problem *p, nlfeti_profile *out);

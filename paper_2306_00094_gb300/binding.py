@@ -57,7 +57,8 @@ class Info(C.Structure):
 
 class Profile(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("apply_launches", C.c_int64), ("apply_ms", C.c_double),
-                ("apply_bytes", C.c_double)]
+                ("apply_bytes", C.c_double), ("half_apply_launches", C.c_int64), ("half_apply_ms", C.c_double),
+                ("half_apply_bytes", C.c_double)]
 
 
 class Mesh(C.Structure):

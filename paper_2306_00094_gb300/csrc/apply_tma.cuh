@@ -26,8 +26,12 @@
 #include <cuda.h>
 
 constexpr int APPLY_CB = 1024;                      // bytes of one row (or one x column) per stage
-constexpr int APPLY_NS = 5;                         // stages (up to 200 KB of shared memory, one CTA per SM)
-constexpr int APPLY_NS_H = 8;                       // stages with an FP16 operator (24 KB each at RC = 8)
+// Two CTAs per SM (18 warps): the consumers of one CTA wait on shared-memory loads and on
+// their stage barrier often enough that a second CTA's warps are needed to keep the FMA
+// pipes and the copy engine busy; the ring per CTA is smaller accordingly.
+constexpr int APPLY_MINB = 2;                       // CTAs per SM
+constexpr int APPLY_NS = 2;                         // stages per CTA (40 KB each at RC = 8)
+constexpr int APPLY_NS_H = 4;                       // stages with an FP16 operator (24 KB each at RC = 8)
 // a stage: 32 operator rows of mrow bytes, then RC columns of x (APPLY_CB bytes each)
 __host__ __device__ constexpr int apply_stage_bytes(int rc, int mrow = APPLY_CB) { return 32 * mrow + rc * APPLY_CB; }
 // the ring is aligned to 1 KB inside the dynamic shared memory (tensor copies want 128 B)
@@ -98,7 +102,7 @@ inline CUresult encode_apply_map(Encode encode, CUtensorMap *map, const void *ba
                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
-template <typename T, int RC, int NS = APPLY_NS, int MINB = 1, typename MT = T>
+template <typename T, int RC, int NS = APPLY_NS, int MINB = APPLY_MINB, typename MT = T>
 __global__ void __launch_bounds__(APPLY_THREADS, MINB)
     k_apply_tma(const CUtensorMap *maps, const CUtensorMap *xmaps, int use_sp, const SubdomainDesc *sd,
                 const int32_t *sched_ptr, const int32_t *sched_items, double *y, int R, const int *gate, int *err,

@@ -603,6 +603,7 @@ struct Runner {
         cudaEvent_t a, b;
         int launches;
         double bytes;
+        bool half;          // an apply of the FP16 preconditioner copy
     };
     std::vector<Slot> graph_slots, eager_slots;
     // inside PCG iterations: the interface applies and their gathers return at once when no
@@ -612,8 +613,8 @@ struct Runner {
     // the WHILE node of the graph loop being captured (set by k_check_update)
     cudaGraphConditionalHandle cond = 0;
     bool use_cond = false;
-    int64_t apply_launches = 0;
-    double apply_ms = 0, apply_bytes = 0;
+    int64_t apply_launches = 0, half_launches = 0;
+    double apply_ms = 0, apply_bytes = 0, half_ms = 0, half_bytes = 0;
 
     Runner(nlfeti_problem *pp, SolveWS &w, cudaStream_t s) : p(pp), ws(w), st(s), R(w.R) {
         double *b = ws.scal.as<double>();
@@ -640,6 +641,9 @@ struct Runner {
         p->prof.apply_launches += apply_launches;
         p->prof.apply_ms += apply_ms;
         p->prof.apply_bytes += apply_bytes;
+        p->prof.half_apply_launches += half_launches;
+        p->prof.half_apply_ms += half_ms;
+        p->prof.half_apply_bytes += half_bytes;
     }
 
     // after a read-back of the scalar words n_active .. err into host_flag
@@ -664,9 +668,9 @@ struct Runner {
         for (auto &s : v) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, s.a, s.b) == cudaSuccess) {
-                apply_ms += ms;
-                apply_launches += s.launches;
-                apply_bytes += s.bytes;
+                (s.half ? half_ms : apply_ms) += ms;
+                (s.half ? half_launches : apply_launches) += s.launches;
+                (s.half ? half_bytes : apply_bytes) += s.bytes;
             } else {
                 cudaGetLastError();
             }
@@ -760,7 +764,7 @@ struct Runner {
             constexpr int RCT = decltype(rc_tag)::value;
             if constexpr (std::is_same<T, float>::value) {
                 if (half) {
-                    k_apply_tma<float, RCT, APPLY_NS_H, 1, __half>
+                    k_apply_tma<float, RCT, APPLY_NS_H, APPLY_MINB, __half>
                         <<<p->sched_ctas, APPLY_THREADS, apply_smem_bytes(RCT, APPLY_NS_H, APPLY_CB / 2), st>>>(
                             pool.hmaps.template as<CUtensorMap>(), ws.xmaps[0].template as<CUtensorMap>(), 0, sd,
                             p->d_sched_ptr.as<int32_t>(), p->d_sched_items.as<int32_t>(), y, R, gate, S.err,
@@ -815,6 +819,7 @@ struct Runner {
                 bytes += (double)d.nG * d.ldG * me + (double)d.nG * R * (sizeof(T) + sizeof(double));
             slot.launches = launches;
             slot.bytes = bytes;
+            slot.half = half;
             (capturing ? graph_slots : eager_slots).push_back(slot);
         }
     }
@@ -1317,8 +1322,8 @@ int apply_tma_ctas() {
         NLF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, APPLY_THREADS, smem));
         per_sm = std::min(per_sm, b);
     };
-    fit_h(k_apply_tma<float, 1, APPLY_NS_H, 1, __half>, 1); fit_h(k_apply_tma<float, 2, APPLY_NS_H, 1, __half>, 2);
-    fit_h(k_apply_tma<float, 4, APPLY_NS_H, 1, __half>, 4); fit_h(k_apply_tma<float, 8, APPLY_NS_H, 1, __half>, 8);
+    fit_h(k_apply_tma<float, 1, APPLY_NS_H, APPLY_MINB, __half>, 1); fit_h(k_apply_tma<float, 2, APPLY_NS_H, APPLY_MINB, __half>, 2);
+    fit_h(k_apply_tma<float, 4, APPLY_NS_H, APPLY_MINB, __half>, 4); fit_h(k_apply_tma<float, 8, APPLY_NS_H, APPLY_MINB, __half>, 8);
     if (per_sm < 1) fail(NLFETI_E_CUDA, "the interface apply does not fit on an SM");
     return sms * per_sm;
 }
