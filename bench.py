@@ -275,6 +275,29 @@ def run_ours(args):
     plain_res = time_variant(plain, ksteps)
     plain_b_res = time_variant(plain_batched, ksteps)
     u_plain = d_out.cpu().numpy().T.copy()
+
+    # the paper's baseline solver on the same GPU and inputs: diagonally preconditioned CG on
+    # the single-domain system (FP64-accurate products), tol 1e-10 (nodal error ~1e-10)
+    t0 = time.perf_counter()
+    prob.cg_prepare()
+    cg_prep_s = time.perf_counter() - t0
+    d_cg = torch.empty_like(d_rhs)
+    prob.set_options(binding.default_options(tol=1e-10, max_it=20000))
+    prob.solve_cg_device(d_rhs, w.rhs_kind, d_cg, nrhs=R)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(ksteps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        s_cg = prob.solve_cg_device(d_rhs, w.rhs_kind, d_cg, nrhs=R)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    u_cg = d_cg.cpu().numpy().T.copy()
+    cg_res = {"value": R * len(ts) / (sum(ts) / 1e3), "unit": "solves/s", "ms_per_step": statistics.mean(ts),
+              "iterations": s_cg["iterations"], "tol": 1e-10, "prepare_s": cg_prep_s,
+              "rel_diff_vs_fp64_feti": rel_diff(u_cg, u_plain, w)}
     prob.set_options(mixed)
 
     # cold: setup + assembly + FP32 factorization + one solve
@@ -317,12 +340,13 @@ def run_ours(args):
         "e2e": e2e,
         "plain_fp64_per_subdomain": plain_res,
         "fp64_batched": plain_b_res,
+        "cg_single_domain": cg_res,
         "cold": {"setup_assembly_s": t_setup, "factor_fp32_s": t_factor32, "factor_fp64_s": t_factor64,
                  "setup_factor_solve_s": cold_s},
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"], accuracy = cpu_baseline(w, args, u_gpu, u_plain)
+        line["cpu_baseline"], accuracy = cpu_baseline(w, args, u_gpu, u_plain, u_cg)
         line["rel_err_vs_oracle"] = accuracy
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -337,7 +361,15 @@ def oracle_setup(w):
     return feti.Feti(w.mesh, w.kernel, w.labels, w.K)
 
 
-def cpu_baseline(w, args, u_gpu, u_plain):
+def rel_diff(u, v, w):
+    """max over right-hand sides of max |u - v| / max |v| on the non-Dirichlet dofs"""
+    free = w.mesh.node_is_dirichlet == 0
+    d = np.abs(u[free] - v[free]).max(axis=0)
+    s = np.abs(v[free]).max(axis=0)
+    return float((d / np.where(s > 0, s, 1.0)).max())
+
+
+def cpu_baseline(w, args, u_gpu, u_plain, u_cg=None):
     """The FP64 oracle as it stands, on the host cores: warm solves of the same workload
     (its setup excluded like the GPU's), bounded to ~10-30 s; also the accuracy of the GPU
     results against it."""
@@ -358,6 +390,8 @@ def cpu_baseline(w, args, u_gpu, u_plain):
                       f"numpy/LAPACK FP64 on {cores} host threads"}
     acc = {"mixed": float(oprob.rel_nodal_error(u_gpu, u_ref, w.mesh, 1).max()),
            "plain_fp64": float(oprob.rel_nodal_error(u_plain, u_ref, w.mesh, 1).max())}
+    if u_cg is not None:
+        acc["cg_single_domain"] = float(oprob.rel_nodal_error(u_cg, u_ref, w.mesh, 1).max())
     return base, acc
 
 

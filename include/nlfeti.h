@@ -170,6 +170,25 @@ nlfeti_status nlfeti_solve(nlfeti_problem *p, int nrhs, int rhs_kind, const doub
 nlfeti_status nlfeti_solve_device(nlfeti_problem *p, int nrhs, int rhs_kind, const double *d_rhs,
                                   const double *d_g, double *d_u_out, nlfeti_stats *stats);
 
+/* The paper's baseline solver (section "Considered solver strategies"): conjugate gradients
+ * with the diagonal preconditioner on the single-domain system A u = F - A_D g, FP64, on the
+ * same mesh, kernel, loads and Dirichlet data as nlfeti_solve, for comparing the two solvers
+ * on one GPU.  A is assembled once per problem as CSR over the global dofs from the subdomain
+ * matrices (which sum to A through the zeta weights; Dirichlet dofs get identity rows):
+ * nlfeti_cg_prepare does it explicitly (host work and a device upload, synchronous),
+ * otherwise the first CG solve does.  The CG stops per right-hand side at
+ * ||r||_2 <= opt.tol ||b||_2 or after opt.max_it iterations (NLFETI_E_NOT_CONVERGED, output
+ * still written); stats.iterations is the largest count over the right-hand sides and
+ * stats.final_rel_residual the largest ||r|| / ||b||.  At most 32 right-hand sides per call
+ * (NLFETI_E_INVALID beyond).  Arguments, layouts and stream behaviour as nlfeti_solve /
+ * nlfeti_solve_device.  The options precision, precond_fp16 and refinement fields do not
+ * apply; batched = 0 runs the loop without graphs. */
+nlfeti_status nlfeti_cg_prepare(nlfeti_problem *p);
+nlfeti_status nlfeti_solve_cg(nlfeti_problem *p, int nrhs, int rhs_kind, const double *rhs, const double *g,
+                              double *u_out, nlfeti_stats *stats);
+nlfeti_status nlfeti_solve_cg_device(nlfeti_problem *p, int nrhs, int rhs_kind, const double *d_rhs,
+                                     const double *d_g, double *d_u_out, nlfeti_stats *stats);
+
 /* Introspection for bit-exact tests (host arrays, caller-sized from nlfeti_info):
  * n_k[K], n_gamma[K], node lists (sum n_k / ncomp node ids, Omega first then
  * Gamma per subdomain), B rows as U indices (n_lambda each), floating[K]. */

@@ -24,7 +24,8 @@ EXPORTED = ["nlfeti_default_options", "nlfeti_create", "nlfeti_destroy", "nlfeti
             "nlfeti_problem_destroy", "nlfeti_problem_info", "nlfeti_problem_set_options", "nlfeti_factor",
             "nlfeti_solve", "nlfeti_solve_device", "nlfeti_get_decomposition", "nlfeti_get_operator",
             "nlfeti_apply", "nlfeti_set_profiling", "nlfeti_get_profile", "nlfeti_server_create", "nlfeti_submit",
-            "nlfeti_wait", "nlfeti_server_destroy", "nlfeti_apply_schur_noalloc"]
+            "nlfeti_wait", "nlfeti_server_destroy", "nlfeti_apply_schur_noalloc", "nlfeti_cg_prepare",
+            "nlfeti_solve_cg", "nlfeti_solve_cg_device"]
 
 
 class NlfetiError(RuntimeError):
@@ -106,6 +107,9 @@ def load(build_if_missing: bool = True):
         "nlfeti_factor": (i32, [vp, i32]),
         "nlfeti_solve": (i32, [vp, i32, i32, vp, vp, vp, C.POINTER(Stats)]),
         "nlfeti_solve_device": (i32, [vp, i32, i32, vp, vp, vp, C.POINTER(Stats)]),
+        "nlfeti_cg_prepare": (i32, [vp]),
+        "nlfeti_solve_cg": (i32, [vp, i32, i32, vp, vp, vp, C.POINTER(Stats)]),
+        "nlfeti_solve_cg_device": (i32, [vp, i32, i32, vp, vp, vp, C.POINTER(Stats)]),
         "nlfeti_get_decomposition": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "nlfeti_get_operator": (i32, [vp, i32, i32, i32, vp]),
         "nlfeti_apply": (i32, [vp, i32, i32, i32, vp, vp]),
@@ -244,6 +248,35 @@ class Problem:
         if raise_on_error:
             self.ctx.check(code)
         return out, st.as_dict()
+
+    def cg_prepare(self):
+        """Assemble the single-domain matrix for the CG baseline (once per problem)."""
+        self.ctx.check(self.ctx.lib.nlfeti_cg_prepare(self.h))
+
+    def solve_cg(self, rhs, rhs_kind, g=None, raise_on_error=True):
+        """The paper's baseline: diagonally preconditioned CG on the single-domain system."""
+        rhs = np.asfortranarray(rhs, dtype=np.float64)
+        if rhs.ndim == 1:
+            rhs = rhs.reshape(-1, 1, order="F")
+        nrhs = rhs.shape[1]
+        gg = None if g is None else np.asfortranarray(np.broadcast_to(np.asarray(g, np.float64).reshape(rhs.shape[0], -1), rhs.shape))
+        out = np.zeros(rhs.shape, dtype=np.float64, order="F")
+        st = Stats()
+        code = self.ctx.lib.nlfeti_solve_cg(self.h, nrhs, int(rhs_kind), rhs.ctypes.data, _ptr(gg), out.ctypes.data,
+                                            C.byref(st))
+        if raise_on_error:
+            self.ctx.check(code)
+        return out, st.as_dict()
+
+    def solve_cg_device(self, d_rhs, rhs_kind, d_out, d_g=None, nrhs=None):
+        """CG baseline on device arrays (as solve_device)."""
+        ptr = lambda t: None if t is None else (t if isinstance(t, int) else t.data_ptr())
+        if nrhs is None:
+            nrhs = d_rhs.shape[0]
+        st = Stats()
+        self.ctx.check(self.ctx.lib.nlfeti_solve_cg_device(self.h, int(nrhs), int(rhs_kind), ptr(d_rhs), ptr(d_g),
+                                                           ptr(d_out), C.byref(st)))
+        return st.as_dict()
 
     def solve_host_ptr(self, rhs_ptr, rhs_kind, out_ptr, nrhs, g_ptr=None):
         """Host arrays given by address (e.g. pinned torch tensors), column-major n_dofs x nrhs."""

@@ -524,8 +524,14 @@ nlfeti_status nlfeti_factor(nlfeti_problem *p, int mask) {
     });
 }
 
-nlfeti_status nlfeti_solve_device(nlfeti_problem *p, int nrhs, int rhs_kind, const double *d_rhs, const double *d_g,
-                                  double *d_u_out, nlfeti_stats *stats) {
+}  // extern "C"
+
+namespace {
+using SolveFn = void (*)(nlfeti_problem *, SolveWS &, cudaStream_t, int, int, const double *, const double *, double *,
+                         nlfeti_stats *);
+
+nlfeti_status solve_on_device(nlfeti_problem *p, SolveFn fn, int nrhs, int rhs_kind, const double *d_rhs,
+                              const double *d_g, double *d_u_out, nlfeti_stats *stats) {
     if (!p) return NLFETI_E_INVALID;
     return guarded(p->ctx, [&] {
         if (nrhs < 1 || (rhs_kind != 0 && rhs_kind != 1) || !d_rhs || !d_u_out) fail(NLFETI_E_INVALID, "bad solve arguments");
@@ -534,7 +540,7 @@ nlfeti_status nlfeti_solve_device(nlfeti_problem *p, int nrhs, int rhs_kind, con
         nlfeti_stats s{};
         stream_enter(p->ctx);
         try {
-            solve_device(p, *p->ws, p->ctx->stream, nrhs, rhs_kind, d_rhs, d_g, d_u_out, &s);
+            fn(p, *p->ws, p->ctx->stream, nrhs, rhs_kind, d_rhs, d_g, d_u_out, &s);
         } catch (...) {
             if (stats) *stats = s;
             stream_leave(p->ctx);
@@ -548,11 +554,11 @@ nlfeti_status nlfeti_solve_device(nlfeti_problem *p, int nrhs, int rhs_kind, con
     });
 }
 
-nlfeti_status nlfeti_solve(nlfeti_problem *p, int nrhs, int rhs_kind, const double *rhs, const double *g,
-                           double *u_out, nlfeti_stats *stats) {
+nlfeti_status solve_on_host(nlfeti_problem *p, SolveFn fn, int nrhs, int rhs_kind, const double *rhs, const double *g,
+                            double *u_out, nlfeti_stats *stats) {
     if (!p) return NLFETI_E_INVALID;
     return guarded(p->ctx, [&] {
-        if (nrhs < 1 || !rhs || !u_out) fail(NLFETI_E_INVALID, "bad solve arguments");
+        if (nrhs < 1 || (rhs_kind != 0 && rhs_kind != 1) || !rhs || !u_out) fail(NLFETI_E_INVALID, "bad solve arguments");
         if (!p->ws) p->ws.reset(new SolveWS());
         SolveWS &ws = *p->ws;
         cudaStream_t st = p->ctx->stream;
@@ -566,8 +572,8 @@ nlfeti_status nlfeti_solve(nlfeti_problem *p, int nrhs, int rhs_kind, const doub
         nlfeti_stats s{};
         nlfeti_status inner = NLFETI_OK;
         try {
-            solve_device(p, ws, st, nrhs, rhs_kind, ws.in_rhs.as<double>(), g ? ws.in_g.as<double>() : nullptr,
-                         ws.out_u.as<double>(), &s);
+            fn(p, ws, st, nrhs, rhs_kind, ws.in_rhs.as<double>(), g ? ws.in_g.as<double>() : nullptr,
+               ws.out_u.as<double>(), &s);
         } catch (const Error &e) {
             if (e.st != NLFETI_E_NOT_CONVERGED) throw;
             inner = e.st;
@@ -581,6 +587,34 @@ nlfeti_status nlfeti_solve(nlfeti_problem *p, int nrhs, int rhs_kind, const doub
         if (stats) *stats = s;
         if (inner != NLFETI_OK) fail(inner, p->ctx->err);
     });
+}
+}  // namespace
+
+extern "C" {
+
+nlfeti_status nlfeti_solve_device(nlfeti_problem *p, int nrhs, int rhs_kind, const double *d_rhs, const double *d_g,
+                                  double *d_u_out, nlfeti_stats *stats) {
+    return solve_on_device(p, solve_device, nrhs, rhs_kind, d_rhs, d_g, d_u_out, stats);
+}
+
+nlfeti_status nlfeti_solve(nlfeti_problem *p, int nrhs, int rhs_kind, const double *rhs, const double *g,
+                           double *u_out, nlfeti_stats *stats) {
+    return solve_on_host(p, solve_device, nrhs, rhs_kind, rhs, g, u_out, stats);
+}
+
+nlfeti_status nlfeti_cg_prepare(nlfeti_problem *p) {
+    if (!p) return NLFETI_E_INVALID;
+    return guarded(p->ctx, [&] { cg_prepare(p); });
+}
+
+nlfeti_status nlfeti_solve_cg_device(nlfeti_problem *p, int nrhs, int rhs_kind, const double *d_rhs, const double *d_g,
+                                     double *d_u_out, nlfeti_stats *stats) {
+    return solve_on_device(p, cg_solve_device, nrhs, rhs_kind, d_rhs, d_g, d_u_out, stats);
+}
+
+nlfeti_status nlfeti_solve_cg(nlfeti_problem *p, int nrhs, int rhs_kind, const double *rhs, const double *g,
+                              double *u_out, nlfeti_stats *stats) {
+    return solve_on_host(p, cg_solve_device, nrhs, rhs_kind, rhs, g, u_out, stats);
 }
 
 nlfeti_status nlfeti_set_profiling(nlfeti_problem *p, int on) {

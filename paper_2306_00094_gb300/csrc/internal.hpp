@@ -200,6 +200,13 @@ struct nlfeti_problem {
     OpPool<double> op64;
     OpPool<float> op32;
     std::unique_ptr<nlf::SolveWS> ws;
+    // Diagonally preconditioned CG on the single-domain system (the paper's comparison
+    // solver): the global FP64 matrix as CSR over the n_dofs_total dofs (int64 row pointers,
+    // int32 columns, values as FP32 hi / lo pairs), assembled from the A^k by
+    // nlfeti_cg_prepare or the first CG solve, and the inverse of its diagonal
+    nlf::DevMem d_cg_ptr, d_cg_col, d_cg_vhi, d_cg_vlo, d_cg_dinv;
+    int64_t cg_nnz = 0;
+    bool cg_ready = false;
     double ms_setup = 0, ms_factor = 0;
     bool prof_on = false;
     std::mutex prof_mu;
@@ -225,4 +232,6 @@ int apply_tma_ctas();
 int residual_tma_ctas();
 // tensor maps of a pool's S_k and S_k^+ for the bulk-copy apply (after the factorization)
 template <typename T> void encode_apply_maps(nlfeti_problem *p, OpPool<T> &pool);
+// global CSR of the single-domain matrix for the CG baseline (once per problem; host sync)
+void cg_prepare(nlfeti_problem *p);
 }  // namespace nlf

@@ -562,6 +562,279 @@ __global__ void __launch_bounds__(RED_THREADS) k_refine_update(double *u, const 
     if (threadIdx.x == 0) *s.counter = 0u;
 }
 
+// ====================================================================== single-domain CG
+//
+// Diagonally preconditioned CG on A u = b over the global dofs: the performance baseline of
+// the paper's experiments (section "Considered solver strategies"), FP64, R right-hand sides
+// interleaved (entry g of column c at g*R + c), each column frozen once ||r|| <= tol ||b|| or
+// after max_it iterations:
+//   q = A p;  alpha = (r, z) / (p, q);  u += alpha p;  r -= alpha q;  z = D^-1 r;
+//   beta = (r, z)_new / (r, z)_old;  p = z + beta p.
+// A is the CSR of cg_prepare; b = sum over the subdomain copies of each dof of the split
+// loads (they sum to F - A_D g).  FP64 has a small share of this GPU's arithmetic, so the
+// SpMV runs in double-single arithmetic on the FP32 pipes: A and p as FP32 pairs (hi + lo,
+// 2^-48 relative), each product's rounding error kept exactly (fma), sums by TwoSum per lane
+// (the scheme of the refinement residual), lane sums in FP64.  The scalar block holds the CG state in the PCG's slots:
+// nPd = ||b||, yw = (r, z), eta = alpha, beta, relres = ||r|| / ||b||, active, iters,
+// n_active, loops.  Every reduction has a fixed order that does not depend on R.
+
+constexpr int CG_WARPS = 8;                   // warps (rows at a time) of a SpMV block
+constexpr int CG_BLOCKS = 8 * 152;            // SpMV blocks (rows strided over them; 64 warps per SM)
+constexpr int CG_MAX_R = 32;                  // right-hand sides per CG call
+constexpr int CG_U = 8;                       // nonzeros per SpMV slot loaded at a time
+
+// b[g] = sum of f~ over the copies of dof g
+__global__ void k_cg_rhs(const double *ftil, const int64_t *cp_ptr, const int64_t *cp_pos, int64_t n, int R,
+                         double *b) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * R; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = t / R;
+        const int c = (int)(t % R);
+        double s = 0;
+        for (int64_t q = cp_ptr[g]; q < cp_ptr[g + 1]; ++q) s += ftil[cp_pos[q] * R + c];
+        b[t] = s;
+    }
+}
+
+// p as FP32 pairs for the SpMV: hi = fl32(p), lo = fl32(p - hi)
+__device__ __forceinline__ void split_f2(double v, float *hi, float *lo, int64_t t) {
+    const float h = __double2float_rn(v);
+    hi[t] = h;
+    lo[t] = __double2float_rn(v - (double)h);
+}
+
+// u = 0, r = b, z = D^-1 b, p = z; (r, z) and (b, b); the initial state
+__global__ void __launch_bounds__(RED_THREADS) k_cg_init(const double *b, const double *dinv, double *u, double *r,
+                                                          double *z, double *p, float *ph, float *pl, int64_t n, int R,
+                                                          double *pa, double *pb, PcgScalars s) {
+    const int c = blockIdx.y;
+    double a1 = 0, a2 = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i * R + c;
+        const double bv = b[t], zv = dinv[i] * bv;
+        u[t] = 0.0;
+        r[t] = bv;
+        z[t] = zv;
+        p[t] = zv;
+        split_f2(zv, ph, pl, t);
+        a1 += bv * zv;
+        a2 += bv * bv;
+    }
+    block_partial(a1, pa, R);
+    __syncthreads();
+    block_partial(a2, pb, R);
+    if (!arrive_last(s.counter)) return;
+    __shared__ int n_act;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) n_act = 0;
+    __syncthreads();
+    for (int cc = warp; cc < R; cc += RED_THREADS / 32) {
+        double rz = 0, bb = 0;
+        for (int bl = lane; bl < (int)gridDim.x; bl += 32) {
+            rz += __ldcg(pa + (int64_t)bl * R + cc);
+            bb += __ldcg(pb + (int64_t)bl * R + cc);
+        }
+        rz = warp_sum(rz);
+        bb = warp_sum(bb);
+        if (lane == 0) {
+            const int act = bb > 0.0 ? 1 : 0;
+            s.nPd[cc] = sqrt(bb);
+            s.yw[cc] = rz;
+            s.eta[cc] = 0.0;
+            s.beta[cc] = 0.0;
+            s.relres[cc] = act ? 1.0 : 0.0;
+            s.iters[cc] = 0;
+            s.active[cc] = act;
+            if (act) atomicAdd(&n_act, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *s.n_active = n_act;
+        *s.counter = 0u;
+    }
+}
+
+// q = A p (warp per row, double-single products), (p, q) per column, alpha for the active
+// columns.  Lanes are (nonzero slot kg = lane / 8, column cl = lane % 8): the 8 lanes of a slot
+// read one nonzero and the 8 consecutive p entries of its column index (one 32-byte segment
+// of hi and one of lo), the 4 slots take every 4th nonzero of the row; the slots are summed by
+// two shuffles.  Columns come in blocks of 8; each column's arithmetic is the same whatever R.
+__global__ void __launch_bounds__(CG_WARPS * 32) k_cg_spmv(const int64_t *ptr, const int32_t *col, const float *vhi,
+                                                           const float *vlo, const float *ph, const float *pl,
+                                                           const double *p, double *q, int64_t n, int R, double *part,
+                                                           PcgScalars s) {
+    __shared__ double red[CG_WARPS][CG_MAX_R];
+    if (*s.n_active == 0) return;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, kg = lane >> 3, cl = lane & 7;
+    constexpr int NCB = CG_MAX_R / 8;
+    double dacc[NCB];
+#pragma unroll
+    for (int cb = 0; cb < NCB; ++cb) dacc[cb] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * CG_WARPS + warp; i < n; i += (int64_t)gridDim.x * CG_WARPS) {
+        const int64_t a = ptr[i], e = ptr[i + 1];
+#pragma unroll
+        for (int cb = 0; cb < NCB; ++cb) {
+            const int c = cb * 8 + cl;
+            if (cb * 8 < R) {
+                const bool on = c < R;
+                float sh = 0.f, sl = 0.f;
+                // CG_U nonzeros per slot at a time: their matrix loads first, then their p
+                // gathers, then the products in order (loads in flight cover DRAM latency)
+                for (int64_t k0 = a + kg; k0 < e; k0 += 4 * CG_U) {
+                    float ahv[CG_U], alv[CG_U];
+                    int64_t jv[CG_U];
+#pragma unroll
+                    for (int u = 0; u < CG_U; ++u) {
+                        const int64_t k = k0 + 4 * u;
+                        const bool in = k < e;
+                        ahv[u] = in ? __ldg(vhi + k) : 0.f;
+                        alv[u] = in ? __ldg(vlo + k) : 0.f;
+                        jv[u] = in ? (int64_t)__ldg(col + k) : -1;
+                    }
+                    float xhv[CG_U], xlv[CG_U];
+#pragma unroll
+                    for (int u = 0; u < CG_U; ++u) {
+                        const bool in = on && jv[u] >= 0;
+                        xhv[u] = in ? __ldg(ph + jv[u] * R + c) : 0.f;
+                        xlv[u] = in ? __ldg(pl + jv[u] * R + c) : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < CG_U; ++u) {
+                        if (!on || jv[u] < 0) continue;
+                        const float ah = ahv[u], al = alv[u], xh = xhv[u], xl = xlv[u];
+                        // explicit round-to-nearest intrinsics: no contraction into fma
+                        const float pr = __fmul_rn(ah, xh);
+                        const float pe = fmaf(ah, xh, -pr);              // ah*xh - pr exactly
+                        const float sum = __fadd_rn(sh, pr);             // TwoSum(sh, pr)
+                        const float bb = __fsub_rn(sum, sh);
+                        const float se = __fadd_rn(__fsub_rn(sh, __fsub_rn(sum, bb)), __fsub_rn(pr, bb));
+                        sh = sum;
+                        sl = __fadd_rn(sl, __fadd_rn(se, fmaf(ah, xl, fmaf(al, xh, pe))));
+                    }
+                }
+                double acc = (double)sh + (double)sl;
+                acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+                if (kg == 0 && on) {
+                    q[i * R + c] = acc;
+                    dacc[cb] += p[i * R + c] * acc;
+                }
+            }
+        }
+    }
+    // block sums per column, warps in order
+#pragma unroll
+    for (int cb = 0; cb < NCB; ++cb) {
+        const int c = cb * 8 + cl;
+        if (kg == 0 && c < R) red[warp][c] = dacc[cb];
+    }
+    __syncthreads();
+    if (threadIdx.x < R) {
+        double x = 0;
+        for (int w = 0; w < CG_WARPS; ++w) x += red[w][threadIdx.x];
+        part[(int64_t)blockIdx.x * R + threadIdx.x] = x;
+    }
+    if (!arrive_last(s.counter)) return;
+    for (int cc = warp; cc < R; cc += CG_WARPS) {
+        double pq = 0;
+        for (int bl = lane; bl < (int)gridDim.x; bl += 32) pq += __ldcg(part + (int64_t)bl * R + cc);
+        pq = warp_sum(pq);
+        if (lane == 0) s.eta[cc] = (s.active[cc] && pq != 0.0) ? s.yw[cc] / pq : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *s.counter = 0u;
+}
+
+// u += alpha p, r -= alpha q, z = D^-1 r; (r, z), (r, r); beta and the stop test.  COND: the
+// last block also counts the iteration and sets the WHILE condition (continue while a column
+// is active and fewer than limit iterations have run)
+template <int COND>
+__global__ void __launch_bounds__(RED_THREADS) k_cg_update(const double *dinv, const double *p, const double *q,
+                                                            double *u, double *r, double *z, int64_t n, int R,
+                                                            double *pa, double *pb, PcgScalars s, double tol,
+                                                            int max_it, cudaGraphConditionalHandle cond, int limit) {
+    if (*s.n_active == 0) {
+        if (COND && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
+    const int c = blockIdx.y;
+    const double al = s.eta[c];
+    double a1 = 0, a2 = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i * R + c;
+        u[t] = __fma_rn(al, p[t], u[t]);
+        const double rn = __fma_rn(-al, q[t], r[t]), zn = dinv[i] * rn;
+        r[t] = rn;
+        z[t] = zn;
+        a1 += rn * zn;
+        a2 += rn * rn;
+    }
+    block_partial(a1, pa, R);
+    __syncthreads();
+    block_partial(a2, pb, R);
+    if (!arrive_last(s.counter)) return;
+    __shared__ int n_act;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) n_act = 0;
+    __syncthreads();
+    for (int cc = warp; cc < R; cc += RED_THREADS / 32) {
+        double rz = 0, rr = 0;
+        for (int bl = lane; bl < (int)gridDim.x; bl += 32) {
+            rz += __ldcg(pa + (int64_t)bl * R + cc);
+            rr += __ldcg(pb + (int64_t)bl * R + cc);
+        }
+        rz = warp_sum(rz);
+        rr = warp_sum(rr);
+        if (lane == 0) {
+            int act = s.active[cc];
+            if (act) {
+                const int it = s.iters[cc] + 1;
+                s.iters[cc] = it;
+                const double nb = s.nPd[cc], rel = nb > 0 ? sqrt(rr) / nb : 0.0;
+                s.relres[cc] = rel;
+                s.beta[cc] = s.yw[cc] != 0.0 ? rz / s.yw[cc] : 0.0;
+                s.yw[cc] = rz;
+                if (rel <= tol || it >= max_it) act = 0;
+                s.active[cc] = act;
+            }
+            if (act) atomicAdd(&n_act, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *s.n_active = n_act;
+        *s.counter = 0u;
+        if (COND) {
+            const int l = *s.loops + 1;
+            *s.loops = l;
+            cudaGraphSetConditional(cond, (n_act > 0 && l < limit) ? 1u : 0u);
+        }
+    }
+}
+
+// p = z + beta p on the active columns (and its FP32 pair)
+__global__ void k_cg_p(const double *z, double *p, float *ph, float *pl, int64_t n, int R, PcgScalars s) {
+    if (*s.n_active == 0) return;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * R; t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t % R);
+        if (s.active[c]) {
+            const double v = __fma_rn(s.beta[c], p[t], z[t]);
+            p[t] = v;
+            split_f2(v, ph, pl, t);
+        }
+    }
+}
+
+// nodal output of the CG solution: u on the free dofs, g (or 0) on the Dirichlet dofs
+__global__ void k_cg_output(const double *u, const int8_t *node_dir, int nc, const double *g, int64_t ndof, int R,
+                            double *out) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ndof * R; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t gd = t % ndof;
+        const int c = (int)(t / ndof);
+        out[t] = node_dir[gd / nc] ? (g ? g[(int64_t)c * ndof + gd] : 0.0) : u[gd * R + c];
+    }
+}
+
 // ====================================================================== host orchestration
 
 // the workspace's error word (set by a device wait that ran out)
@@ -888,8 +1161,8 @@ struct Runner {
     template <typename T> const PcgGraph &while_graph(const OpPool<T> &pool, double tol, int max_it) {
         const int prec = std::is_same<T, float>::value ? 1 : 0;
         for (const auto &g : ws.graphs)
-            if (g.factor_gen == p->factor_gen && g.precision == prec && g.tol == tol && g.max_it == max_it &&
-                g.precond_fp16 == p->opt.precond_fp16)
+            if (g.kind == 0 && g.factor_gen == p->factor_gen && g.precision == prec && g.tol == tol &&
+                g.max_it == max_it && g.precond_fp16 == p->opt.precond_fp16)
                 return g;
         PcgGraph g;
         g.precond_fp16 = p->opt.precond_fp16;
@@ -934,6 +1207,113 @@ struct Runner {
         g.body_launches = cap_launches;
         ws.graphs.push_back(g);
         return ws.graphs.back();
+    }
+
+    // ---------------------------------------------------------------- single-domain CG
+    void cg_iteration(double tol, int max_it) {
+        const int64_t n = p->n_dofs_total;
+        double *u = ws.cg_u.as<double>(), *r = ws.cg_r.as<double>(), *z = ws.cg_z.as<double>(),
+               *pv = ws.cg_p.as<double>(), *q = ws.cg_q.as<double>();
+        k_cg_spmv<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(CG_BLOCKS, (n + CG_WARPS - 1) / CG_WARPS)),
+                    CG_WARPS * 32, 0, st>>>(p->d_cg_ptr.as<int64_t>(), p->d_cg_col.as<int32_t>(),
+                                            p->d_cg_vhi.as<float>(), p->d_cg_vlo.as<float>(), ws.cg_ph.as<float>(),
+                                            ws.cg_pl.as<float>(), pv, q, n, R, ws.cg_part.as<double>(), S);
+        note_launch();
+        auto upd = [&](auto kern) {
+            kern<<<red_grid(n, R), RED_THREADS, 0, st>>>(p->d_cg_dinv.as<double>(), pv, q, u, r, z, n, R,
+                                                         ws.partial.as<double>(), ws.partial2.as<double>(), S, tol,
+                                                         max_it, cond, max_it + 1);
+        };
+        if (use_cond) upd(k_cg_update<1>);
+        else upd(k_cg_update<0>);
+        note_launch();
+        k_cg_p<<<grid_for(n * R), 256, 0, st>>>(z, pv, ws.cg_ph.as<float>(), ws.cg_pl.as<float>(), n, R, S);
+        note_launch();
+    }
+
+    // the CG loop: one cached WHILE graph (batched, no profiling), else chunks of 4
+    // iterations with a host check (graphs when batched, plain launches otherwise)
+    void cg_loop(double tol, int max_it) {
+        const bool batched = p->opt.batched != 0;
+        if (batched && !p->prof_on && p->opt.graph_loop) {
+            const PcgGraph *found = nullptr;
+            for (const auto &g : ws.graphs)
+                if (g.kind == 1 && g.tol == tol && g.max_it == max_it) found = &g;
+            if (!found) {
+                PcgGraph g;
+                g.kind = 1;
+                g.tol = tol;
+                g.max_it = max_it;
+                cudaGraph_t graph = nullptr;
+                NLF_CUDA(cudaGraphCreate(&graph, 0));
+                try {
+                    NLF_CUDA(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+                    cudaGraphNodeParams np = {};
+                    np.type = cudaGraphNodeTypeConditional;
+                    np.conditional.handle = cond;
+                    np.conditional.type = cudaGraphCondTypeWhile;
+                    np.conditional.size = 1;
+                    cudaGraphNode_t node;
+                    NLF_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np));
+                    cudaGraph_t body = np.conditional.phGraph_out[0];
+                    capturing = true;
+                    use_cond = true;
+                    cap_launches = 0;
+                    NLF_CUDA(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0,
+                                                           cudaStreamCaptureModeThreadLocal));
+                    cg_iteration(tol, max_it);
+                    cudaGraph_t captured = nullptr;
+                    capturing = false;
+                    use_cond = false;
+                    NLF_CUDA(cudaStreamEndCapture(st, &captured));
+                    NLF_CUDA(cudaGraphInstantiate(&g.exec, graph, 0));
+                } catch (...) {
+                    if (capturing) {
+                        cudaGraph_t junk = nullptr;
+                        cudaStreamEndCapture(st, &junk);
+                        capturing = false;
+                        use_cond = false;
+                    }
+                    cudaGetLastError();
+                    cudaGraphDestroy(graph);
+                    throw;
+                }
+                cudaGraphDestroy(graph);
+                g.body_launches = cap_launches;
+                ws.graphs.push_back(g);
+                found = &ws.graphs.back();
+            }
+            NLF_CUDA(cudaMemsetAsync(S.loops, 0, sizeof(int), st));
+            NLF_CUDA(cudaGraphLaunch(found->exec, st));
+            loop_body_launches = found->body_launches;
+            return;
+        }
+        const int chunk = 4;
+        cudaGraphExec_t exec = nullptr;
+        if (batched) {
+            cudaGraph_t graph;
+            capturing = true;
+            cap_launches = 0;
+            NLF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            for (int i = 0; i < chunk; ++i) cg_iteration(tol, max_it);
+            NLF_CUDA(cudaStreamEndCapture(st, &graph));
+            capturing = false;
+            NLF_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+            NLF_CUDA(cudaGraphDestroy(graph));
+        }
+        for (int done = 0; done <= max_it; done += chunk) {
+            if (batched) {
+                NLF_CUDA(cudaGraphLaunch(exec, st));
+                eager_launches += cap_launches;
+            } else {
+                for (int i = 0; i < chunk; ++i) cg_iteration(tol, max_it);
+            }
+            NLF_CUDA(cudaMemcpyAsync(ws.host_flag.data(), S.n_active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            NLF_CUDA(cudaStreamSynchronize(st));
+            check_waits();
+            if (ws.host_flag[0] == 0) break;
+        }
+        if (exec) NLF_CUDA(cudaGraphExecDestroy(exec));
     }
 
     // one FETI pass on subdomain loads ws.res; constraint right-hand side ws.cvec when with_c.
@@ -1298,6 +1678,56 @@ void apply_operator(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int op, int
     NLF_CUDA(cudaMemcpyAsync(ws.host_flag.data(), run.S.n_active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     NLF_CUDA(cudaStreamSynchronize(st));
     run.check_waits();
+}
+
+void cg_solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rhs_kind, const double *d_rhs,
+                     const double *d_g, double *d_out, nlfeti_stats *stats) {
+    if (R > CG_MAX_R) fail(NLFETI_E_INVALID, "the CG solve takes at most 32 right-hand sides per call");
+    cg_prepare(p);
+    ws.ensure(p, R);
+    const int64_t n = p->n_dofs_total, nv = p->sum_nk;
+    auto need = [&](DevMem &m, size_t bytes) {
+        if (m.bytes >= bytes) return;
+        if (ws.async_stream) m.alloc_async(ws.async_stream, bytes);
+        else m.alloc(p->ctx, bytes);
+    };
+    const size_t vb = sizeof(double) * (size_t)std::max<int64_t>(1, n) * R;
+    need(ws.cg_u, vb); need(ws.cg_r, vb); need(ws.cg_z, vb); need(ws.cg_p, vb); need(ws.cg_q, vb); need(ws.cg_b, vb);
+    need(ws.cg_part, sizeof(double) * CG_BLOCKS * (size_t)R);
+    need(ws.cg_ph, vb / 2);
+    need(ws.cg_pl, vb / 2);
+    Runner run(p, ws, st);
+    const MeshHost &m = p->mesh;
+    // loads, split per subdomain as for FETI (eq. bilinear-multi5), with the Dirichlet coupling
+    k_load_vector<<<grid_for(n * R), 256, 0, st>>>(d_rhs, rhs_kind, p->d_xy.as<double>(), p->d_elems.as<int32_t>(),
+                                                   m.dim, p->d_nodeinc_ptr.as<int64_t>(), p->d_nodeinc_el.as<int32_t>(),
+                                                   p->nc, n, R, ws.F.as<double>());
+    k_split_loads<<<grid_for(nv * R), 256, 0, st>>>(ws.F.as<double>(), p->d_vdofs.as<int32_t>(),
+                                                    p->d_zeta_dof.as<double>(), nv, R, ws.ftil.as<double>());
+    if (d_g)
+        k_dirichlet<<<dim3(32, p->K), 256, 0, st>>>(p->d_AD.as<double>(), p->d_sd.as<SubdomainDesc>(),
+                                                    p->d_ddofs.as<int32_t>(), p->d_doff.as<int64_t>(), d_g, n,
+                                                    ws.ftil.as<double>(), R);
+    k_cg_rhs<<<grid_for(n * R), 256, 0, st>>>(ws.ftil.as<double>(), p->d_cp_ptr.as<int64_t>(),
+                                              p->d_cp_pos.as<int64_t>(), n, R, ws.cg_b.as<double>());
+    k_cg_init<<<red_grid(n, R), RED_THREADS, 0, st>>>(ws.cg_b.as<double>(), p->d_cg_dinv.as<double>(),
+                                                      ws.cg_u.as<double>(), ws.cg_r.as<double>(),
+                                                      ws.cg_z.as<double>(), ws.cg_p.as<double>(), ws.cg_ph.as<float>(),
+                                                      ws.cg_pl.as<float>(), n, R, ws.partial.as<double>(),
+                                                      ws.partial2.as<double>(), run.S);
+    NLF_CUDA(cudaGetLastError());
+    run.eager_launches += 4 + (d_g ? 1 : 0);
+    run.cg_loop(p->opt.tol, p->opt.max_it);
+    const auto state = run.read_state(p->opt.tol);
+    k_cg_output<<<grid_for(n * R), 256, 0, st>>>(ws.cg_u.as<double>(), p->d_node_dir.as<int8_t>(), p->nc, d_g, n, R,
+                                                 d_out);
+    NLF_CUDA(cudaGetLastError());
+    run.eager_launches += 1;
+    nlfeti_stats s{};
+    s.iterations = state.iterations;
+    s.final_rel_residual = state.relres;
+    if (stats) *stats = s;
+    if (!state.all_within) fail(NLFETI_E_NOT_CONVERGED, "CG did not reach the tolerance within max_it");
 }
 
 int apply_tma_ctas() {

@@ -14,6 +14,7 @@ struct PcgGraph {
     cudaGraphExec_t exec = nullptr;
     int64_t body_launches = 0;      // kernels per loop iteration
     int precond_fp16 = 0;           // the preconditioner apply it was captured with
+    int kind = 0;                   // 0: FETI PCG loop, 1: single-domain CG loop
 };
 
 struct SolveWS {
@@ -30,6 +31,8 @@ struct SolveWS {
     DevMem gco, gsum, alpha;                            // coarse space
     DevMem partial, partial2, scal;                     // reductions and PCG scalars
     DevMem in_rhs, in_g, out_u;                         // staging for host-array solves
+    DevMem cg_u, cg_r, cg_z, cg_p, cg_q, cg_b, cg_part;  // single-domain CG (global dofs x R)
+    DevMem cg_ph, cg_pl;                                // p as FP32 hi / lo pairs (SpMV operand)
     std::vector<int> host_flag;
     cudaStream_t async_stream = nullptr;   // set: stream-ordered allocations (server slots)
     std::vector<PcgGraph> graphs;
@@ -44,6 +47,11 @@ struct SolveWS {
 // Full solve on device arrays: rhs / g column-major (n_dofs x R), out column-major.
 void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rhs_kind, const double *d_rhs,
                   const double *d_g, double *d_out, nlfeti_stats *stats);
+
+// Single-domain diagonally preconditioned CG (the paper's baseline solver) on device arrays,
+// same arguments as solve_device; at most 32 right-hand sides.
+void cg_solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rhs_kind, const double *d_rhs,
+                     const double *d_g, double *d_out, nlfeti_stats *stats);
 
 // Apply one operator (0 F, 1 M^-1, 2 P, 3 S^+, 4 S) to device vectors in the interleaved layout.
 void apply_operator(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int op, int precision, int R, const double *in,
