@@ -8,7 +8,8 @@
 * end to end: relative nodal error vs the oracle's single-domain solve <= 1e-8 for the
   FP64 path and for the mixed path after refinement (the tolerance of the paper's solver
   target), on small workloads spanning several tiles with ragged tails, floating
-  subdomains, the Omega_k = empty degeneracy, the vector kernel and K = 1.
+  subdomains, the Omega_k = empty degeneracy, the vector kernel, K = 1, and unstructured
+  meshes (irregular nodes and diagonals) with graph-grown local parts.
 """
 import numpy as np
 import pytest
@@ -27,6 +28,8 @@ CASES = {
     "frac_deg": lambda: W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.25),
     "pd_3x3_jit": lambda: W.cfg4_peridynamic(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2),
     "k1": lambda: W.cfg2_const_l2(N=16, k=1, nrhs=2),
+    "l2_unstructured": lambda: W.unstructured_l2(N=24, K=5, nrhs=2),
+    "pd_unstructured": lambda: W.unstructured_pd(N=24, K=4, nrhs=2),
 }
 
 

@@ -28,6 +28,8 @@ CASES = {
     "frac_3x3": lambda: W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.1),
     "frac_deg": lambda: W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.25),   # Omega_k empty
     "pd_3x3_jit": lambda: W.cfg4_peridynamic(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2),
+    "l2_unstructured": lambda: W.unstructured_l2(N=20, K=5, nrhs=2),      # irregular mesh, graph parts
+    "pd_unstructured": lambda: W.unstructured_pd(N=20, K=4, nrhs=2),
 }
 
 

@@ -19,9 +19,14 @@ is a k1 x k2 grid of rectangles.  Mesh conventions:
   2 * (cj * (N + 2m) + ci) + (0 lower | 1 upper);
 * a node is Dirichlet when it lies on the boundary of the unit square or
   outside it; an element is Dirichlet when its cell lies outside the square.
+
+Unstructured variants (`unstructured_mesh`, `graph_labels`): irregular node positions and
+cell diagonals with the same collar, and local parts grown on the element graph instead of
+rectangles (the paper's general setting, Sec. 5.1: Omega-tilde_k from a graph partitioner).
 """
 from __future__ import annotations
 
+import heapq
 import math
 from dataclasses import dataclass, field
 
@@ -163,6 +168,117 @@ def rect_labels(mesh: Mesh, kx: int, ky: int = 1, jitter: float = 0.0, seed: int
     lab = iy * kx + ix
     labels[inside] = lab[inside].astype(np.int32)
     return labels
+
+
+def unstructured_mesh(N: int, m: int, amp: float = 0.15, seed: int = 7) -> Mesh:
+    """2-D P1 mesh of [-m h, 1 + m h]^2 with irregular geometry and connectivity: the grid
+    nodes strictly inside the unit square move by U(-amp, amp) h in each coordinate
+    (amp <= 0.15 keeps every triangle counter-clockwise: a vertex moves less than 0.22 h,
+    its distance to the opposite edge is at least 0.7 h), and each cell takes one of its two
+    diagonals at random.  Nodes on the boundary of the unit square and outside it stay on
+    the grid, so the Dirichlet nodes and elements are those of make_mesh(2, N, m)."""
+    base = make_mesh(2, N, m)
+    rng = np.random.default_rng(seed)
+    xy = base.xy.copy()
+    eps = 1e-12
+    inside = (xy[:, 0] > eps) & (xy[:, 0] < 1 - eps) & (xy[:, 1] > eps) & (xy[:, 1] < 1 - eps)
+    xy[inside] += rng.uniform(-amp, amp, size=(int(inside.sum()), 2)) / N
+    M = N + 2 * m
+    n1 = M + 1
+    cj, ci = np.meshgrid(np.arange(M), np.arange(M), indexing="ij")
+    v00 = (cj * n1 + ci).ravel()
+    v10, v11, v01 = v00 + 1, v00 + n1 + 1, v00 + n1
+    anti = rng.random(M * M) < 0.5
+    t0 = np.where(anti[:, None], np.stack([v00, v10, v01], 1), np.stack([v00, v10, v11], 1))
+    t1 = np.where(anti[:, None], np.stack([v10, v11, v01], 1), np.stack([v00, v11, v01], 1))
+    elems = np.empty((2 * M * M, 3), dtype=np.int32)
+    elems[0::2] = t0
+    elems[1::2] = t1
+    return Mesh(2, N, m, xy, elems, base.node_is_dirichlet.copy(), base.elem_is_dirichlet.copy())
+
+
+def graph_labels(mesh: Mesh, K: int, seed: int = 0) -> np.ndarray:
+    """Local parts grown on the graph of non-Dirichlet elements (edges between elements that
+    share a mesh edge): K seeds by farthest-point sampling of the barycenters (the first one
+    at random), then the part with the fewest elements takes, one at a time, the unassigned
+    neighbour of its region nearest to its seed (a greedy graph-growing partition; every part
+    is connected).  Labels -1 on Dirichlet elements."""
+    rng = np.random.default_rng(seed)
+    inside = np.flatnonzero(mesh.elem_is_dirichlet == 0)
+    pos = {int(e): i for i, e in enumerate(inside)}
+    nv = mesh.elems.shape[1]
+    edge_owner: dict = {}
+    nbr = [[] for _ in inside]
+    for i, e in enumerate(inside):
+        vs = mesh.elems[e]
+        for a in range(nv):
+            for b in range(a + 1, nv):
+                key = (min(vs[a], vs[b]), max(vs[a], vs[b]))
+                if key in edge_owner:
+                    j = edge_owner[key]
+                    nbr[i].append(j)
+                    nbr[j].append(i)
+                else:
+                    edge_owner[key] = i
+    bary = mesh.xy[mesh.elems[inside]].mean(axis=1)
+    seeds = [int(rng.integers(len(inside)))]
+    dmin = np.linalg.norm(bary - bary[seeds[0]], axis=1)
+    while len(seeds) < K:
+        s = int(np.argmax(dmin))
+        seeds.append(s)
+        dmin = np.minimum(dmin, np.linalg.norm(bary - bary[s], axis=1))
+    lab = np.full(len(inside), -1, dtype=np.int32)
+    size = np.zeros(K, dtype=np.int64)
+    heaps = [[] for _ in range(K)]
+    for k, s in enumerate(seeds):
+        lab[s] = k
+        size[k] = 1
+        for j in nbr[s]:
+            heapq.heappush(heaps[k], (float(np.linalg.norm(bary[j] - bary[s])), j))
+    left = len(inside) - K
+    while left > 0:
+        for k in np.argsort(size, kind="stable"):
+            h = heaps[k]
+            while h and lab[h[0][1]] >= 0:
+                heapq.heappop(h)
+            if h:
+                break
+        else:
+            raise RuntimeError("graph partition: unreachable elements")
+        _, j = heapq.heappop(heaps[k])
+        lab[j] = k
+        size[k] += 1
+        left -= 1
+        for i in nbr[j]:
+            if lab[i] < 0:
+                heapq.heappush(heaps[k], (float(np.linalg.norm(bary[i] - bary[seeds[k]])), i))
+    labels = np.full(mesh.n_elems, -1, dtype=np.int32)
+    labels[inside] = lab
+    return labels
+
+
+def unstructured_l2(N: int = 24, K: int = 5, nrhs: int = 2, delta: float = 0.1, seed: int = 7) -> Workload:
+    """Constant l2 kernel on an unstructured mesh with graph-grown local parts, N(0,1) loads."""
+    m = collar_cells(delta, N)
+    mesh = unstructured_mesh(N, m, seed=seed)
+    kern = Kernel(KERNEL_CONST_L2, delta)
+    kern.scale = default_scale(kern, 2)
+    labels = graph_labels(mesh, K, seed=seed)
+    rhs = nodal_loads(mesh, 1, nrhs, seed + 1, "normal")
+    return Workload("unstructured_l2", mesh, kern, labels, K, rhs, 1, meta=dict(N=N, delta=delta, K=K))
+
+
+def unstructured_pd(N: int = 24, K: int = 4, nrhs: int = 2, delta_cells: int = 3, seed: int = 9) -> Workload:
+    """Bond-based peridynamic kernel (2 dofs per node) on an unstructured mesh with graph-grown
+    local parts, N(0,1) loads per dof."""
+    delta = delta_cells / N
+    m = collar_cells(delta, N)
+    mesh = unstructured_mesh(N, m, seed=seed)
+    kern = Kernel(KERNEL_PERIDYNAMIC, delta)
+    kern.scale = default_scale(kern, 2)
+    labels = graph_labels(mesh, K, seed=seed)
+    rhs = nodal_loads(mesh, 2, nrhs, seed + 1, "normal")
+    return Workload("unstructured_pd", mesh, kern, labels, K, rhs, 1, meta=dict(N=N, delta=delta, K=K))
 
 
 def nodal_loads(mesh: Mesh, ncomp: int, nrhs: int, seed: int, dist: str) -> np.ndarray:
