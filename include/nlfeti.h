@@ -69,12 +69,19 @@ typedef struct {
 } nlfeti_mesh;
 
 /* Kernel: type, horizon delta, fractional order s (type 2 only) and constant c
- * (scale > 0 required; the library does not pick a default). */
+ * (scale > 0 required; the library does not pick a default).
+ * ball: the approximate interaction ball of the 2-D l2 kernels (types 1-3; Sec. 2.3,
+ * Fig. approximate-ball): 0 = "nocaps" (E' clipped to the polygon of its vertices in the
+ * closed disc and the edge/circle crossings); whole elements E' selected when
+ * 1 = its barycenter, 2 = at least one vertex ("123vertices"), 3 = at least two vertices
+ * ("23vertices") lie in the closed disc about the outer quadrature point.  Must be 0 for
+ * the l-infinity constant kernel (type 0, exact square) and in 1-D (exact interval). */
 typedef struct {
     int type;
     double delta;
     double s;
     double scale;
+    int ball;
 } nlfeti_kernel;
 
 /* Local decomposition (Sec. 5.1): K parts, one label in [0, K) per non-Dirichlet

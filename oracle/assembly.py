@@ -36,7 +36,7 @@ class _Mesh(C.Structure):
 
 
 class _Kernel(C.Structure):
-    _fields_ = [("type", C.c_int), ("delta", C.c_double), ("s", C.c_double), ("c", C.c_double)]
+    _fields_ = [("type", C.c_int), ("delta", C.c_double), ("s", C.c_double), ("c", C.c_double), ("ball", C.c_int)]
 
 
 def _load():
@@ -77,7 +77,7 @@ class _Ctx:
         self.ed = np.ascontiguousarray(mesh.elem_is_dirichlet, dtype=np.int8)
         self.m = _Mesh(mesh.dim, mesh.n_nodes, self.xy.ctypes.data, mesh.n_elems, self.el.ctypes.data,
                        self.nd.ctypes.data, self.ed.ctypes.data)
-        self.k = _Kernel(kernel.type, kernel.delta, kernel.s, scale)
+        self.k = _Kernel(kernel.type, kernel.delta, kernel.s, scale, int(getattr(kernel, "ball", 0)))
 
 
 def pair_matrix(mesh, kernel, scale, e, ep):

@@ -22,7 +22,11 @@
  *   2-D l-infinity: E' clipped by the square of half-width delta (exact);
  *   2-D l2: the "nocaps" polygon of Fig. approximate-ball (e): the vertices
  *           of E' inside the closed disc plus the edge/circle crossings, in
- *           boundary order (the circular caps are left out).
+ *           boundary order (the circular caps are left out);
+ *   2-D l2, whole-element approximate balls of Fig. approximate-ball (ball != 0):
+ *           all of E' when its barycenter lies in the closed disc (c), when at
+ *           least one of its vertices does (a, b: "123vertices"), or when at
+ *           least two of them do (d: "23vertices"); nothing otherwise.
  * Outer rules: 1-D 4-point Gauss-Legendre; 2-D 7-point degree-5 rule.
  * Inner integral:
  *   constant kernels: the integrand is a quadratic polynomial in y, integrated
@@ -62,6 +66,7 @@ typedef struct {
     double delta;
     double s;
     double c;                  /* kernel constant (already resolved) */
+    int ball;                  /* 2-D l2 kernels: 0 nocaps, 1 barycenter, 2 123vertices, 3 23vertices */
 } om_kernel;
 
 #define MAXP 16                /* max polygon vertices */
@@ -299,7 +304,25 @@ static void inner_2d(const om_kernel *K, const double w[3][2], const double x[2]
     double P[MAXP][2];
     int np;
     if (K->type == K_CONST_LINF) np = clip_square(w, x, K->delta, P);
-    else np = clip_disc_nocaps(w, x, K->delta, P);
+    else if (K->ball == 0) np = clip_disc_nocaps(w, x, K->delta, P);
+    else {
+        /* whole-element ball: E' itself or nothing */
+        int inside = 0;
+        double bx = 0.0, by = 0.0;
+        for (int v = 0; v < 3; ++v) {
+            double dx = w[v][0] - x[0], dy = w[v][1] - x[1];
+            if (dx * dx + dy * dy <= K->delta * K->delta) ++inside;
+            bx += w[v][0] / 3.0;
+            by += w[v][1] / 3.0;
+        }
+        int take;
+        if (K->ball == 1) take = (bx - x[0]) * (bx - x[0]) + (by - x[1]) * (by - x[1]) <= K->delta * K->delta;
+        else if (K->ball == 2) take = inside >= 1;
+        else take = inside >= 2;
+        np = 0;
+        if (take)
+            for (int v = 0; v < 3; ++v) { P[v][0] = w[v][0]; P[v][1] = w[v][1]; np = 3; }
+    }
     if (np < 3) return;
     if (K->type == K_CONST_LINF || K->type == K_CONST_L2) {
         /* fan triangulation + edge-midpoint rule (exact for quadratics) */

@@ -68,7 +68,7 @@ class Mesh(C.Structure):
 
 
 class Kernel(C.Structure):
-    _fields_ = [("type", C.c_int), ("delta", C.c_double), ("s", C.c_double), ("scale", C.c_double)]
+    _fields_ = [("type", C.c_int), ("delta", C.c_double), ("s", C.c_double), ("scale", C.c_double), ("ball", C.c_int)]
 
 
 class Decomp(C.Structure):
@@ -198,7 +198,7 @@ class Problem:
     """A nonlocal FETI problem: setup and GPU assembly on construction."""
 
     def __init__(self, ctx: Context, dim, xy, elems, node_is_dirichlet, elem_is_dirichlet, kernel_type, delta, s,
-                 scale, labels, K):
+                 scale, labels, K, ball=0):
         self.ctx = ctx
         lib = ctx.lib
         self._xy = np.ascontiguousarray(xy, dtype=np.float64)
@@ -208,7 +208,7 @@ class Problem:
         self._lab = np.ascontiguousarray(labels, dtype=np.int32)
         mesh = Mesh(dim, self._nd.size, self._xy.ctypes.data, self._ed.size, self._el.ctypes.data,
                     self._nd.ctypes.data, self._ed.ctypes.data)
-        kern = Kernel(int(kernel_type), float(delta), float(s), float(scale))
+        kern = Kernel(int(kernel_type), float(delta), float(s), float(scale), int(ball))
         dec = Decomp(int(K), self._lab.ctypes.data)
         h = C.c_void_p()
         ctx.check(lib.nlfeti_problem_create(ctx.h, C.byref(mesh), C.byref(kern), C.byref(dec), C.byref(h)))
@@ -222,7 +222,7 @@ class Problem:
     def from_workload(cls, ctx, w):
         m, k = w.mesh, w.kernel
         return cls(ctx, m.dim, m.xy, m.elems, m.node_is_dirichlet, m.elem_is_dirichlet, k.type, k.delta, k.s,
-                   k.scale, w.labels, w.K)
+                   k.scale, w.labels, w.K, getattr(k, "ball", 0))
 
     def info(self):
         i = Info()

@@ -147,6 +147,9 @@ void validate_kernel(const nlfeti_kernel *k, int dim) {
     if (!(k->scale > 0)) fail(NLFETI_E_INVALID, "kernel scale must be positive");
     if (k->type == NLFETI_K_FRACTIONAL && !(k->s > 0 && k->s < 1)) fail(NLFETI_E_INVALID, "fractional s must be in (0,1)");
     if (dim == 1 && k->type != NLFETI_K_CONST_LINF) fail(NLFETI_E_INVALID, "1-D meshes support the constant kernel only");
+    if (k->ball < 0 || k->ball > 3) fail(NLFETI_E_INVALID, "unknown approximate ball");
+    if (k->ball != 0 && (dim == 1 || k->type == NLFETI_K_CONST_LINF))
+        fail(NLFETI_E_INVALID, "approximate balls apply to the 2-D l2 kernels only");
 }
 
 void build_maps(nlfeti_problem *p) {

@@ -6,7 +6,9 @@
 // the single-domain reference, implemented here from its definition):
 //   outer points: 1-D 4-point Gauss-Legendre, 2-D 7-point degree-5 rule on E;
 //   inner region: 1-D interval, 2-D l-infinity square clip, or the l2 "nocaps" polygon
-//     (vertices of E' in the closed disc plus edge/circle crossings, Fig. approximate-ball e);
+//     (vertices of E' in the closed disc plus edge/circle crossings, Fig. approximate-ball e),
+//     or, for the whole-element approximate balls (Fig. approximate-ball a-d), all of E'
+//     when its barycenter / at least one vertex / at least two vertices lie in the disc;
 //   constant kernels: exact polygon moments;
 //   fractional / peridynamic kernels: if the bounding boxes of E and E' touch, polar
 //     coordinates about x_q with the radial integral in closed form and 8-point
@@ -44,6 +46,7 @@ struct AsmArgs {
     double *AD;
     int dim, type, nc;
     double delta, s, c;
+    int ball;                 // 0 nocaps, 1 barycenter, 2 123vertices, 3 23vertices (2-D l2 kernels)
 };
 
 __device__ const double kGLt8[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290,
@@ -138,6 +141,29 @@ __device__ int region_square(const double (*T)[2], double x0, double x1, double 
     if (n) n = clip_axis(P, n, 1, x1 + d, 1.0);
     if (n) n = clip_axis(P, n, 1, x1 - d, -1.0);
     return n >= 3 ? n : 0;
+}
+
+// whole-element approximate ball: T itself when selected by the rule, else nothing
+__device__ int region_whole(const double (*T)[2], double x0, double x1, double d, int ball, double (*P)[2]) {
+    const double rr = d * d;
+    int in = 0;
+    for (int k = 0; k < 3; ++k) {
+        const double dx = T[k][0] - x0, dy = T[k][1] - x1;
+        if (dx * dx + dy * dy <= rr) ++in;
+    }
+    bool take;
+    if (ball == 1) {
+        const double bx = (T[0][0] + T[1][0] + T[2][0]) / 3.0 - x0, by = (T[0][1] + T[1][1] + T[2][1]) / 3.0 - x1;
+        take = bx * bx + by * by <= rr;
+    } else {
+        take = in >= (ball == 2 ? 1 : 2);
+    }
+    if (!take) return 0;
+    for (int k = 0; k < 3; ++k) {
+        P[k][0] = T[k][0];
+        P[k][1] = T[k][1];
+    }
+    return 3;
 }
 
 __device__ int region_disc(const double (*T)[2], double x0, double x1, double d, double (*P)[2]) {
@@ -399,7 +425,8 @@ __global__ void __launch_bounds__(64) k_assemble(AsmArgs a) {
             double x1 = R.b[q][0] * To[0][1] + R.b[q][1] * To[1][1] + R.b[q][2] * To[2][1];
             double P[MAXV][2];
             int np = (a.type == NLFETI_K_CONST_LINF) ? region_square(Ti, x0, x1, a.delta, P)
-                                                     : region_disc(Ti, x0, x1, a.delta, P);
+                     : a.ball != 0                    ? region_whole(Ti, x0, x1, a.delta, a.ball, P)
+                                                      : region_disc(Ti, x0, x1, a.delta, P);
             if (np == 0) continue;
             double av[6];
             for (int i = 0; i < nl; ++i) {
@@ -541,6 +568,7 @@ void assemble_all(nlfeti_problem *p) {
     a.type = p->kern.type;
     a.nc = p->nc;
     a.delta = p->kern.delta;
+    a.ball = p->kern.ball;
     a.s = p->kern.s;
     a.c = p->kern.scale;
     const int threads = 64;

@@ -8,8 +8,9 @@
 * end to end: relative nodal error vs the oracle's single-domain solve <= 1e-8 for the
   FP64 path and for the mixed path after refinement (the tolerance of the paper's solver
   target), on small workloads spanning several tiles with ragged tails, floating
-  subdomains, the Omega_k = empty degeneracy, the vector kernel, K = 1, and unstructured
-  meshes (irregular nodes and diagonals) with graph-grown local parts.
+  subdomains, the Omega_k = empty degeneracy, the vector kernel, K = 1, unstructured
+  meshes (irregular nodes and diagonals) with graph-grown local parts, and the
+  whole-element approximate balls (barycenter, 123vertices, 23vertices).
 """
 import numpy as np
 import pytest
@@ -30,7 +31,15 @@ CASES = {
     "k1": lambda: W.cfg2_const_l2(N=16, k=1, nrhs=2),
     "l2_unstructured": lambda: W.unstructured_l2(N=24, K=5, nrhs=2),
     "pd_unstructured": lambda: W.unstructured_pd(N=24, K=4, nrhs=2),
+    "l2_ball_barycenter": lambda: _ball(W.cfg2_const_l2(N=24, k=3, nrhs=2, delta=0.1), 1),
+    "frac_ball_123v": lambda: _ball(W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.1), 2),
+    "pd_ball_23v": lambda: _ball(W.cfg4_peridynamic(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2), 3),
 }
+
+
+def _ball(w, ball):
+    w.kernel.ball = ball
+    return w
 
 
 def _linf(N, k):
