@@ -24,6 +24,7 @@ CASES = {
     "pd_3x3_jit": lambda: W.cfg4_peridynamic(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2),
     "k1": lambda: W.cfg2_const_l2(N=16, k=1, nrhs=2),
     "l2_unstructured": lambda: W.unstructured_l2(N=24, K=5, nrhs=2),
+    "l2_neumann": lambda: W.neumann_l2(N=24, k=3, nrhs=2),
 }
 
 

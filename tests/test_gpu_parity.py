@@ -9,8 +9,9 @@
   FP64 path and for the mixed path after refinement (the tolerance of the paper's solver
   target), on small workloads spanning several tiles with ragged tails, floating
   subdomains, the Omega_k = empty degeneracy, the vector kernel, K = 1, unstructured
-  meshes (irregular nodes and diagonals) with graph-grown local parts, and the
-  whole-element approximate balls (barycenter, 123vertices, 23vertices).
+  meshes (irregular nodes and diagonals) with graph-grown local parts, the whole-element
+  approximate balls (barycenter, 123vertices, 23vertices), and Neumann volume constraints
+  (a free, loaded collar region on two sides).
 """
 import numpy as np
 import pytest
@@ -34,6 +35,8 @@ CASES = {
     "l2_ball_barycenter": lambda: _ball(W.cfg2_const_l2(N=24, k=3, nrhs=2, delta=0.1), 1),
     "frac_ball_123v": lambda: _ball(W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.1), 2),
     "pd_ball_23v": lambda: _ball(W.cfg4_peridynamic(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2), 3),
+    "l2_neumann": lambda: W.neumann_l2(N=24, k=3, nrhs=2),
+    "pd_neumann": lambda: W.neumann_pd(N=30, k=3, nrhs=2),
 }
 
 

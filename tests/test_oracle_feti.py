@@ -30,6 +30,8 @@ CASES = {
     "pd_3x3_jit": lambda: W.cfg4_peridynamic(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2),
     "l2_unstructured": lambda: W.unstructured_l2(N=20, K=5, nrhs=2),      # irregular mesh, graph parts
     "pd_unstructured": lambda: W.unstructured_pd(N=20, K=4, nrhs=2),
+    "l2_neumann": lambda: W.neumann_l2(N=20, k=3, nrhs=2),                # Neumann region on two sides
+    "pd_neumann": lambda: W.neumann_pd(N=24, k=3, nrhs=2),
 }
 
 

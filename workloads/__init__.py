@@ -282,6 +282,56 @@ def unstructured_pd(N: int = 24, K: int = 4, nrhs: int = 2, delta_cells: int = 3
     return Workload("unstructured_pd", mesh, kern, labels, K, rhs, 1, meta=dict(N=N, delta=delta, K=K))
 
 
+def neumann_sides(mesh: Mesh) -> Mesh:
+    """The same mesh with the Dirichlet volume constraint kept only on the left (x < 0) and
+    bottom (y < 0) parts of the collar; the rest of the collar (x > 1 or y > 1, corners
+    included) becomes a Neumann region Gamma^N: free nodes and elements that belong to
+    Omega_h = Omega u Gamma^N (Sec. 2.1), loaded like the interior.  Nodes on x = 0 or
+    y = 0 stay Dirichlet."""
+    x, y = mesh.xy[:, 0], mesh.xy[:, 1]
+    eps = 1e-12
+    nd = ((x <= eps) | (y <= eps)).astype(np.int8)
+    cen = mesh.xy[mesh.elems].mean(axis=1)
+    ed = ((cen[:, 0] < 0) | (cen[:, 1] < 0)).astype(np.int8)
+    return Mesh(mesh.dim, mesh.N, mesh.m, mesh.xy, mesh.elems, nd, ed)
+
+
+def clamped_rect_labels(mesh: Mesh, kx: int, ky: int) -> np.ndarray:
+    """rect_labels with the barycenters clamped into the unit square first, so that free
+    collar elements (a Neumann region) join the nearest rectangle."""
+    cx = rect_cuts(mesh.N, kx)
+    cy = rect_cuts(mesh.N, ky)
+    bary = np.clip(mesh.xy[mesh.elems].mean(axis=1) * mesh.N, 1e-9, mesh.N - 1e-9)
+    ix = np.searchsorted(cx, bary[:, 0], side="right") - 1
+    iy = np.searchsorted(cy, bary[:, 1], side="right") - 1
+    labels = np.full(mesh.n_elems, -1, dtype=np.int32)
+    free = mesh.elem_is_dirichlet == 0
+    labels[free] = (iy * kx + ix)[free].astype(np.int32)
+    return labels
+
+
+def neumann_l2(N: int = 24, k: int = 3, nrhs: int = 2, delta: float = 0.1, seed: int = 13) -> Workload:
+    """Constant l2 kernel with Dirichlet constraint on the left and bottom collar and a
+    Neumann region on the rest, k x k rectangles (clamped labels), N(0,1) loads."""
+    mesh = neumann_sides(make_mesh(2, N, collar_cells(delta, N)))
+    kern = Kernel(KERNEL_CONST_L2, delta)
+    kern.scale = default_scale(kern, 2)
+    labels = clamped_rect_labels(mesh, k, k)
+    rhs = nodal_loads(mesh, 1, nrhs, seed, "normal")
+    return Workload("neumann_l2", mesh, kern, labels, k * k, rhs, 1, meta=dict(N=N, delta=delta, k=k))
+
+
+def neumann_pd(N: int = 30, k: int = 3, nrhs: int = 2, delta_cells: int = 3, seed: int = 15) -> Workload:
+    """Bond-based peridynamics with the same mixed volume constraints (2 dofs per node)."""
+    delta = delta_cells / N
+    mesh = neumann_sides(make_mesh(2, N, collar_cells(delta, N)))
+    kern = Kernel(KERNEL_PERIDYNAMIC, delta)
+    kern.scale = default_scale(kern, 2)
+    labels = clamped_rect_labels(mesh, k, k)
+    rhs = nodal_loads(mesh, 2, nrhs, seed, "normal")
+    return Workload("neumann_pd", mesh, kern, labels, k * k, rhs, 1, meta=dict(N=N, delta=delta, k=k))
+
+
 def nodal_loads(mesh: Mesh, ncomp: int, nrhs: int, seed: int, dist: str) -> np.ndarray:
     rng = np.random.default_rng(seed)
     n = mesh.n_nodes * ncomp
