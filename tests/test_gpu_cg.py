@@ -25,6 +25,7 @@ CASES = {
     "k1": lambda: W.cfg2_const_l2(N=16, k=1, nrhs=2),
     "l2_unstructured": lambda: W.unstructured_l2(N=24, K=5, nrhs=2),
     "l2_neumann": lambda: W.neumann_l2(N=24, k=3, nrhs=2),
+    "l2_rounded_collar": lambda: W.l2_collar_const(N=24, k=3, nrhs=2, delta=0.15),
 }
 
 

@@ -10,8 +10,8 @@
   target), on small workloads spanning several tiles with ragged tails, floating
   subdomains, the Omega_k = empty degeneracy, the vector kernel, K = 1, unstructured
   meshes (irregular nodes and diagonals) with graph-grown local parts, the whole-element
-  approximate balls (barycenter, 123vertices, 23vertices), and Neumann volume constraints
-  (a free, loaded collar region on two sides).
+  approximate balls (barycenter, 123vertices, 23vertices), Neumann volume constraints
+  (a free, loaded collar region on two sides) and the l2 (rounded-corner) collar.
 """
 import numpy as np
 import pytest
@@ -37,6 +37,7 @@ CASES = {
     "pd_ball_23v": lambda: _ball(W.cfg4_peridynamic(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2), 3),
     "l2_neumann": lambda: W.neumann_l2(N=24, k=3, nrhs=2),
     "pd_neumann": lambda: W.neumann_pd(N=30, k=3, nrhs=2),
+    "l2_rounded_collar": lambda: W.l2_collar_const(N=24, k=3, nrhs=2, delta=0.15),
 }
 
 

@@ -32,6 +32,7 @@ CASES = {
     "pd_unstructured": lambda: W.unstructured_pd(N=20, K=4, nrhs=2),
     "l2_neumann": lambda: W.neumann_l2(N=20, k=3, nrhs=2),                # Neumann region on two sides
     "pd_neumann": lambda: W.neumann_pd(N=24, k=3, nrhs=2),
+    "l2_rounded_collar": lambda: W.l2_collar_const(N=20, k=3, nrhs=2, delta=0.15),
 }
 
 

@@ -53,3 +53,31 @@ def test_graph_labels_cover_and_connect():
                     stack.append(j)
         assert seen == part
     assert np.array_equal(w.labels, W.unstructured_l2(N=20, K=5).labels)   # seeded
+
+
+def test_l2_collar_keeps_exactly_the_elements_meeting_the_disc_neighbourhood():
+    N, delta = 24, 0.15
+    base = W.make_mesh(2, N, W.collar_cells(delta, N))
+    mesh = W.l2_collar(base, delta)
+    # distance of a triangle to the unit square by dense barycentric sampling (resolution h / 40)
+    t = np.linspace(0.0, 1.0, 41)
+    a, b = np.meshgrid(t, t, indexing="ij")
+    ok = (a + b) <= 1.0
+    lam = np.stack([a[ok], b[ok], 1.0 - a[ok] - b[ok]], axis=1)
+
+    def dist(P):
+        pts = lam @ P
+        return np.linalg.norm(pts - np.clip(pts, 0.0, 1.0), axis=1).min()
+
+    kept = {tuple(np.round(mesh.xy[e].mean(axis=0), 12)) for e in mesh.elems}
+    for e in range(base.n_elems):
+        if base.elem_is_dirichlet[e] == 0:
+            continue
+        P = base.xy[base.elems[e]]
+        d = dist(P)
+        key = tuple(np.round(P.mean(axis=0), 12))
+        if d <= delta - 1.0 / (40 * N):
+            assert key in kept
+        elif d > delta + 1e-12:
+            assert key not in kept
+    assert mesh.n_elems < base.n_elems and (mesh.elem_is_dirichlet == 0).sum() == (base.elem_is_dirichlet == 0).sum()

@@ -282,6 +282,56 @@ def unstructured_pd(N: int = 24, K: int = 4, nrhs: int = 2, delta_cells: int = 3
     return Workload("unstructured_pd", mesh, kern, labels, K, rhs, 1, meta=dict(N=N, delta=delta, K=K))
 
 
+def l2_collar(mesh: Mesh, delta: float) -> Mesh:
+    """Keep only the collar elements that meet the l2 delta-neighbourhood of the unit square
+    (the Dirichlet region of an l2 ball has rounded corners; the simplest discretization of
+    it takes every triangle that meets it, Sec. 2.3.1), then drop unused nodes.  The distance
+    between a triangle and the square (both convex) is the smallest distance from a vertex of
+    one of them to the other."""
+    P = mesh.xy[mesh.elems]                              # (n_elems, 3, 2)
+    nE = P.shape[0]
+    # vertex of a triangle to the square
+    dv = np.linalg.norm(P - np.clip(P, 0.0, 1.0), axis=2).min(axis=1)
+    # corner of the square to a triangle (zero when inside)
+    dc = np.full(nE, np.inf)
+    for cx, cy in ((0.0, 0.0), (1.0, 0.0), (0.0, 1.0), (1.0, 1.0)):
+        q = np.array([cx, cy])
+        d = np.minimum(np.minimum(_seg_dist_many(q, P[:, 0], P[:, 1]), _seg_dist_many(q, P[:, 1], P[:, 2])),
+                       _seg_dist_many(q, P[:, 2], P[:, 0]))
+        v0, v1, v2 = P[:, 0] - q, P[:, 1] - q, P[:, 2] - q
+        c0 = v0[:, 0] * v1[:, 1] - v0[:, 1] * v1[:, 0]
+        c1 = v1[:, 0] * v2[:, 1] - v1[:, 1] * v2[:, 0]
+        c2 = v2[:, 0] * v0[:, 1] - v2[:, 1] * v0[:, 0]
+        inside = (c0 >= 0) & (c1 >= 0) & (c2 >= 0)
+        dc = np.minimum(dc, np.where(inside, 0.0, d))
+    keep = (mesh.elem_is_dirichlet == 0) | (np.minimum(dv, dc) <= delta * (1 + 1e-12))
+    elems = mesh.elems[keep]
+    used = np.zeros(mesh.n_nodes, dtype=bool)
+    used[elems.ravel()] = True
+    new_id = np.full(mesh.n_nodes, -1, dtype=np.int64)
+    new_id[used] = np.arange(int(used.sum()))
+    return Mesh(mesh.dim, mesh.N, mesh.m, mesh.xy[used].copy(), new_id[elems].astype(np.int32),
+                mesh.node_is_dirichlet[used].copy(), mesh.elem_is_dirichlet[keep].copy())
+
+
+def _seg_dist_many(q, a, b):
+    """distance from the point q to each segment [a_i, b_i]"""
+    ab = b - a
+    t = np.clip(np.einsum("ij,ij->i", q - a, ab) / np.maximum(np.einsum("ij,ij->i", ab, ab), 1e-300), 0.0, 1.0)
+    return np.linalg.norm(q - (a + t[:, None] * ab), axis=1)
+
+
+def l2_collar_const(N: int = 24, k: int = 3, nrhs: int = 2, delta: float = 0.15, seed: int = 17) -> Workload:
+    """Constant l2 kernel on a mesh whose Dirichlet collar is the l2 delta-neighbourhood of
+    the square (rounded corners), k x k rectangles, N(0,1) loads."""
+    mesh = l2_collar(make_mesh(2, N, collar_cells(delta, N)), delta)
+    kern = Kernel(KERNEL_CONST_L2, delta)
+    kern.scale = default_scale(kern, 2)
+    labels = rect_labels(mesh, k, k)
+    rhs = nodal_loads(mesh, 1, nrhs, seed, "normal")
+    return Workload("l2_collar", mesh, kern, labels, k * k, rhs, 1, meta=dict(N=N, delta=delta, k=k))
+
+
 def neumann_sides(mesh: Mesh) -> Mesh:
     """The same mesh with the Dirichlet volume constraint kept only on the left (x < 0) and
     bottom (y < 0) parts of the collar; the rest of the collar (x > 1 or y > 1, corners
