@@ -584,6 +584,82 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+PAPER_ROWS = [
+    # (table, kernel, N, delta, k): the rows of the paper's Tables fixedHorizon and fixedRatio
+    # that fit this implementation (K <= 64 subdomains, dense subdomain matrices; the
+    # peridynamic fixed-ratio row would need about 200 GB of dense matrices and is left out)
+    ("fixedHorizon", "constant", 250, 0.008, 6),
+    ("fixedHorizon", "fractional", 250, 0.008, 6),
+    ("fixedHorizon", "peridynamic", 250, 0.008, 6),
+    ("fixedRatio", "constant", 500, 0.008, 6),
+    ("fixedRatio", "fractional", 500, 0.008, 6),
+]
+
+
+def run_paper_rows(args):
+    """The paper's table rows that fit one GB300 with dense subdomain matrices (6 x 6
+    subdomains): its manufactured problem (u = x1^2 x2 + x2^2, g = u on the collar,
+    f = -2 (1 + x2) for every kernel; the peridynamic u = (u, u)), FETI in FP64 at the
+    paper's tolerance 1e-10 and in the mixed mode, and the diagonally preconditioned CG;
+    iteration counts beside the paper's.  One JSON line."""
+    import torch
+    from paper_2306_00094_gb300 import binding
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    golden = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "paper_table_fixed_horizon.txt")):
+        f = line.split()
+        if f and not f[0].startswith("#"):
+            golden[("fixedHorizon", f[0], f[1])] = {"cg_its": int(f[3]), "feti_its": int(f[5]), "l2": float(f[7])}
+    for line in open(os.path.join(ROOT, "tests", "golden", "paper_table_fixed_ratio.txt")):
+        f = line.split()
+        if f and not f[0].startswith("#"):
+            golden[("fixedRatio", f[0], f[1])] = {"cg_its": int(f[4]), "feti_its": int(f[6])}
+    kinds = {"constant": W.KERNEL_CONST_LINF, "fractional": W.KERNEL_FRACTIONAL, "peridynamic": W.KERNEL_PERIDYNAMIC}
+    ctx = binding.Context()
+    rows = []
+    for table, kname, N, delta, k in PAPER_ROWS:
+        mesh = W.make_mesh(2, N, W.collar_cells(delta, N))
+        kern = W.Kernel(kinds[kname], delta, s=0.4 if kname == "fractional" else 0.0)
+        kern.scale = W.default_scale(kern, 2)
+        nc = kern.ncomp
+        x, y = mesh.xy[:, 0], mesh.xy[:, 1]
+        uex = x * x * y + y * y
+        fval = -2.0 * (1.0 + y)
+        u = np.repeat(uex, nc).reshape(-1, 1)
+        f = np.repeat(fval, nc).reshape(-1, 1)
+        w = W.Workload(f"{table}_{kname}", mesh, kern, W.rect_labels(mesh, k, k), k * k, np.asfortranarray(f), 0,
+                       g=np.asfortranarray(u))
+        t0 = time.perf_counter()
+        p = binding.Problem.from_workload(ctx, w)
+        t_setup = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        p.factor(3)
+        t_factor = time.perf_counter() - t0
+        free = np.repeat(mesh.node_is_dirichlet == 0, nc)
+        res = {"table": table, "kernel": kname, "K": f"{k}x{k}", "h": 1.0 / N, "delta": delta,
+               "dofs": int(free.sum()), "setup_s": t_setup, "factor_fp64_fp32_s": t_factor}
+        for mode, opt in (("feti_fp64", binding.default_options(precision=0, tol=1e-10)),
+                          ("feti_mixed", binding.default_options(precision=1)),
+                          ("cg", binding.default_options(tol=1e-10, max_it=20000))):
+            p.set_options(opt)
+            solve = p.solve_cg if mode == "cg" else p.solve
+            uh, st = solve(w.rhs, 0, w.g)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            uh, st = solve(w.rhs, 0, w.g)
+            dt = time.perf_counter() - t0
+            res[mode] = {"iterations": st["iterations"], "refine_sweeps": st["refine_sweeps"], "solve_s": dt,
+                         "max_nodal_err_vs_u": float(np.abs(uh[:, 0] - u[:, 0])[free].max())}
+        gold = golden.get((table, kname, f"{k}x{k}"))
+        if gold:
+            res["paper"] = gold
+        rows.append(res)
+        p.close()
+    print(json.dumps({"mode": "paper_rows", "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -601,11 +677,15 @@ def main():
     ap.add_argument("--requests", type=int, default=2000, help="serving: measured requests")
     ap.add_argument("--pool", type=int, default=6, help="serving: distinct factored problems")
     ap.add_argument("--slots", type=int, default=4, help="serving: server slots")
+    ap.add_argument("--paper-rows", action="store_true",
+                    help="the paper's table rows that fit one GPU (6 x 6 subdomains, 62.5k / 250k dofs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.serving:
         run_serving(args)
+    elif args.paper_rows:
+        run_paper_rows(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

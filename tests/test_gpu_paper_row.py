@@ -1,0 +1,48 @@
+"""The paper's Table fixedHorizon, constant kernel, 6 x 6 row on the GPU (h = 0.004,
+delta = 0.008, 62001 dofs, 36 subdomains), with the manufactured problem of Sec. 6.2:
+
+* the diagonally preconditioned CG on the single-domain system takes the paper's printed
+  iteration count (343 at tolerance 1e-10; `tests/golden/paper_table_fixed_horizon.txt`):
+  the count depends only on the matrix, the right-hand side and the tolerance, so this
+  pins the assembled system (kernel constant, quadrature, mesh, loads) at the paper's size;
+* FETI in FP64 reaches the nodal values of u (delta / h = 2: exact at the nodes) and needs
+  no more iterations than the paper's 40 (the paper does not state its stopping norm).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_table_fixed_horizon.txt")
+
+
+def test_constant_6x6_row_cg_iterations_and_feti():
+    from paper_2306_00094_gb300 import binding
+    row = next(l.split() for l in open(GOLDEN) if l.startswith("constant 6x6"))
+    cg_its, feti_its = int(row[3]), int(row[5])
+    N, delta = int(round(1.0 / float(row[2]))), 0.008
+    mesh = W.make_mesh(2, N, W.collar_cells(delta, N))
+    kern = W.Kernel(W.KERNEL_CONST_LINF, delta)
+    kern.scale = W.default_scale(kern, 2)
+    x, y = mesh.xy[:, 0], mesh.xy[:, 1]
+    u = (x * x * y + y * y).reshape(-1, 1)
+    f = (-2.0 * (1.0 + y)).reshape(-1, 1)
+    w = W.Workload("paper_6x6", mesh, kern, W.rect_labels(mesh, 6, 6), 36, np.asfortranarray(f), 0,
+                   g=np.asfortranarray(u))
+    ctx = binding.Context()
+    p = binding.Problem.from_workload(ctx, w)
+    p.factor(1)
+    free = mesh.node_is_dirichlet == 0
+    p.set_options(binding.default_options(tol=1e-10, max_it=20000))
+    uc, st = p.solve_cg(w.rhs, 0, w.g)
+    assert st["iterations"] == cg_its, st
+    p.set_options(binding.default_options(precision=0, tol=1e-10))
+    uf, st = p.solve(w.rhs, 0, w.g)
+    assert np.abs(uf[:, 0] - u[:, 0])[free].max() < 1e-9
+    assert st["iterations"] <= feti_its, st
+    p.close()
+    ctx.close()
