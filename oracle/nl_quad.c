@@ -23,7 +23,12 @@
  *   2-D l2: the "nocaps" polygon of Fig. approximate-ball (e): the vertices
  *           of E' inside the closed disc plus the edge/circle crossings, in
  *           boundary order (the circular caps are left out);
- *   2-D l2, whole-element approximate balls of Fig. approximate-ball (ball != 0):
+ *   2-D l2, "approxcaps" (ball 4, Fig. approximate-ball f): the nocaps polygon with
+ *           each circular cap it leaves out (beyond the chord from a point where the
+ *           boundary of E' leaves the disc to the next polygon point) filled by the
+ *           triangle on that chord and the midpoint of its arc, a sub-triangle of E'
+ *           when 2 delta exceeds the diameter of E' (the arc is then a minor arc);
+ *   2-D l2, whole-element approximate balls of Fig. approximate-ball (ball 1-3):
  *           all of E' when its barycenter lies in the closed disc (c), when at
  *           least one of its vertices does (a, b: "123vertices"), or when at
  *           least two of them do (d: "23vertices"); nothing otherwise.
@@ -66,7 +71,8 @@ typedef struct {
     double delta;
     double s;
     double c;                  /* kernel constant (already resolved) */
-    int ball;                  /* 2-D l2 kernels: 0 nocaps, 1 barycenter, 2 123vertices, 3 23vertices */
+    int ball;                  /* 2-D l2 kernels: 0 nocaps, 1 barycenter, 2 123vertices, 3 23vertices,
+                                  4 approxcaps */
 } om_kernel;
 
 #define MAXP 16                /* max polygon vertices */
@@ -158,15 +164,17 @@ static int clip_square(const double tri[3][2], const double x[2], double d, doub
     return n < 3 ? 0 : n;
 }
 
-/* nocaps polygon: vertices inside the closed disc plus edge/circle crossings, in order */
-static int clip_disc_nocaps(const double tri[3][2], const double x[2], double d, double P[MAXP][2]) {
+/* Walk the boundary of the triangle in order and list the vertices inside the closed disc
+ * and the edge/circle crossings strictly inside the edges.  exit_[k] = 1 marks a crossing
+ * where the boundary leaves the disc (the larger root on its edge). */
+static int disc_walk(const double tri[3][2], const double x[2], double d, double P[MAXP][2], int exit_[MAXP]) {
     int n = 0;
     double d2 = d * d;
     for (int k = 0; k < 3; ++k) {
         const double *A = tri[k], *B = tri[(k + 1) % 3];
         double ax = A[0] - x[0], ay = A[1] - x[1];
         double ex = B[0] - A[0], ey = B[1] - A[1];
-        if (ax * ax + ay * ay <= d2) { P[n][0] = A[0]; P[n][1] = A[1]; ++n; }
+        if (ax * ax + ay * ay <= d2) { P[n][0] = A[0]; P[n][1] = A[1]; exit_[n] = 0; ++n; }
         double qa = ex * ex + ey * ey;
         double qb = ax * ex + ay * ey;
         double qc = ax * ax + ay * ay - d2;
@@ -174,11 +182,39 @@ static int clip_disc_nocaps(const double tri[3][2], const double x[2], double d,
         if (disc > 0.0) {
             double sq = sqrt(disc);
             double t1 = (-qb - sq) / qa, t2 = (-qb + sq) / qa;
-            if (t1 > 0.0 && t1 < 1.0) { P[n][0] = A[0] + t1 * ex; P[n][1] = A[1] + t1 * ey; ++n; }
-            if (t2 > 0.0 && t2 < 1.0) { P[n][0] = A[0] + t2 * ex; P[n][1] = A[1] + t2 * ey; ++n; }
+            if (t1 > 0.0 && t1 < 1.0) { P[n][0] = A[0] + t1 * ex; P[n][1] = A[1] + t1 * ey; exit_[n] = 0; ++n; }
+            if (t2 > 0.0 && t2 < 1.0) { P[n][0] = A[0] + t2 * ex; P[n][1] = A[1] + t2 * ey; exit_[n] = 1; ++n; }
         }
     }
+    return n;
+}
+
+/* nocaps polygon: vertices inside the closed disc plus edge/circle crossings, in order */
+static int clip_disc_nocaps(const double tri[3][2], const double x[2], double d, double P[MAXP][2]) {
+    int exit_[MAXP];
+    int n = disc_walk(tri, x, d, P, exit_);
     return n < 3 ? 0 : n;
+}
+
+/* approxcaps polygon: the nocaps walk, and after every exit crossing the point of the circle
+ * half-way along the arc to the next listed point (x + d (m - x) / |m - x|, m the chord
+ * midpoint), so that each left-out cap is replaced by the triangle on its chord and arc
+ * midpoint.  A circle entering and leaving E' through one edge yields that triangle alone. */
+static int clip_disc_approxcaps(const double tri[3][2], const double x[2], double d, double P[MAXP][2]) {
+    double W[MAXP][2];
+    int exit_[MAXP];
+    int n = disc_walk(tri, x, d, W, exit_);
+    if (n < 2) return 0;
+    int m = 0;
+    for (int k = 0; k < n; ++k) {
+        P[m][0] = W[k][0]; P[m][1] = W[k][1]; ++m;
+        if (!exit_[k]) continue;
+        const double *Q = W[(k + 1) % n];
+        double mx = 0.5 * (W[k][0] + Q[0]) - x[0], my = 0.5 * (W[k][1] + Q[1]) - x[1];
+        double r = sqrt(mx * mx + my * my);
+        if (r > 0.0) { P[m][0] = x[0] + d * mx / r; P[m][1] = x[1] + d * my / r; ++m; }
+    }
+    return m < 3 ? 0 : m;
 }
 
 /* ------------------------------------------------------- local pair structure */
@@ -305,6 +341,7 @@ static void inner_2d(const om_kernel *K, const double w[3][2], const double x[2]
     int np;
     if (K->type == K_CONST_LINF) np = clip_square(w, x, K->delta, P);
     else if (K->ball == 0) np = clip_disc_nocaps(w, x, K->delta, P);
+    else if (K->ball == 4) np = clip_disc_approxcaps(w, x, K->delta, P);
     else {
         /* whole-element ball: E' itself or nothing */
         int inside = 0;

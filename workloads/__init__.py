@@ -67,7 +67,7 @@ class Kernel:
     delta: float
     s: float = 0.0
     scale: float = 0.0      # <= 0 selects the default constant for the type
-    ball: int = 0           # 2-D l2 kernels: 0 nocaps, 1 barycenter, 2 123vertices, 3 23vertices
+    ball: int = 0           # 2-D l2 kernels: 0 nocaps, 1 barycenter, 2 123vertices, 3 23vertices, 4 approxcaps
 
     @property
     def ncomp(self) -> int:
