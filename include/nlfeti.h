@@ -74,8 +74,11 @@ typedef struct {
  * Fig. approximate-ball): 0 = "nocaps" (E' clipped to the polygon of its vertices in the
  * closed disc and the edge/circle crossings); whole elements E' selected when
  * 1 = its barycenter, 2 = at least one vertex ("123vertices"), 3 = at least two vertices
- * ("23vertices") lie in the closed disc about the outer quadrature point.  Must be 0 for
- * the l-infinity constant kernel (type 0, exact square) and in 1-D (exact interval). */
+ * ("23vertices") lie in the closed disc about the outer quadrature point; 4 = "approxcaps"
+ * (Fig. approximate-ball f): the nocaps polygon with each circular cap it leaves out
+ * replaced by the triangle on the cap's chord and the midpoint of its arc (requires
+ * 2 delta > the longest element edge, else NLFETI_E_INVALID).  Must be 0 for the
+ * l-infinity constant kernel (type 0, exact square) and in 1-D (exact interval). */
 typedef struct {
     int type;
     double delta;

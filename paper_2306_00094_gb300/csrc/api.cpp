@@ -147,9 +147,24 @@ void validate_kernel(const nlfeti_kernel *k, int dim) {
     if (!(k->scale > 0)) fail(NLFETI_E_INVALID, "kernel scale must be positive");
     if (k->type == NLFETI_K_FRACTIONAL && !(k->s > 0 && k->s < 1)) fail(NLFETI_E_INVALID, "fractional s must be in (0,1)");
     if (dim == 1 && k->type != NLFETI_K_CONST_LINF) fail(NLFETI_E_INVALID, "1-D meshes support the constant kernel only");
-    if (k->ball < 0 || k->ball > 3) fail(NLFETI_E_INVALID, "unknown approximate ball");
+    if (k->ball < 0 || k->ball > 4) fail(NLFETI_E_INVALID, "unknown approximate ball");
     if (k->ball != 0 && (dim == 1 || k->type == NLFETI_K_CONST_LINF))
         fail(NLFETI_E_INVALID, "approximate balls apply to the 2-D l2 kernels only");
+}
+
+// approxcaps fills each cap with the triangle on its chord and the midpoint of its arc, which
+// lies in E' when the arc is a minor arc; that holds for every element when 2 delta exceeds
+// the longest element edge (an arc of at least half the circle inside E' would put two
+// antipodal points, 2 delta apart, in E').
+void validate_ball_mesh(const nlfeti_kernel *k, const nlfeti_mesh *m) {
+    if (k->ball != 4) return;
+    double longest = 0.0;
+    for (int64_t e = 0; e < m->n_elems; ++e)
+        for (int i = 0; i < 3; ++i) {
+            const int32_t a = m->elems[3 * e + i], b = m->elems[3 * e + (i + 1) % 3];
+            longest = std::max(longest, std::hypot(m->xy[2 * a] - m->xy[2 * b], m->xy[2 * a + 1] - m->xy[2 * b + 1]));
+        }
+    if (!(2.0 * k->delta > longest)) fail(NLFETI_E_INVALID, "approxcaps needs 2 delta above the longest element edge");
 }
 
 void build_maps(nlfeti_problem *p) {
@@ -441,6 +456,7 @@ nlfeti_status nlfeti_problem_create(nlfeti_ctx *ctx, const nlfeti_mesh *mesh, co
         double t0 = now_ms();
         validate_mesh(mesh);
         validate_kernel(kernel, mesh->dim);
+        validate_ball_mesh(kernel, mesh);
         if (!decomp || !decomp->elem_subdomain) fail(NLFETI_E_INVALID, "null decomposition");
         std::unique_ptr<nlfeti_problem> q(new nlfeti_problem());
         static std::atomic<uint64_t> next_uid{1};

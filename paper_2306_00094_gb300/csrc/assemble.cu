@@ -7,7 +7,8 @@
 //   outer points: 1-D 4-point Gauss-Legendre, 2-D 7-point degree-5 rule on E;
 //   inner region: 1-D interval, 2-D l-infinity square clip, or the l2 "nocaps" polygon
 //     (vertices of E' in the closed disc plus edge/circle crossings, Fig. approximate-ball e),
-//     or, for the whole-element approximate balls (Fig. approximate-ball a-d), all of E'
+//     the "approxcaps" polygon (nocaps plus a chord/arc-midpoint triangle per left-out cap,
+//     Fig. approximate-ball f), or, for the whole-element approximate balls (Fig. approximate-ball a-d), all of E'
 //     when its barycenter / at least one vertex / at least two vertices lie in the disc;
 //   constant kernels: exact polygon moments;
 //   fractional / peridynamic kernels: if the bounding boxes of E and E' touch, polar
@@ -46,7 +47,7 @@ struct AsmArgs {
     double *AD;
     int dim, type, nc;
     double delta, s, c;
-    int ball;                 // 0 nocaps, 1 barycenter, 2 123vertices, 3 23vertices (2-D l2 kernels)
+    int ball;                 // 0 nocaps, 1 barycenter, 2 123vertices, 3 23vertices, 4 approxcaps (2-D l2)
 };
 
 __device__ const double kGLt8[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290,
@@ -166,24 +167,59 @@ __device__ int region_whole(const double (*T)[2], double x0, double x1, double d
     return 3;
 }
 
-__device__ int region_disc(const double (*T)[2], double x0, double x1, double d, double (*P)[2]) {
+// l2 disc: the vertices of T in the closed disc and the edge/circle crossings strictly
+// inside the edges, in boundary order ("nocaps").  With caps, every crossing where the
+// boundary leaves the disc (the larger root on its edge) is followed by the point of the
+// circle half-way along the arc to the next listed point, x + d (m - x) / |m - x| with m the
+// chord midpoint ("approxcaps": each left-out cap becomes the triangle on its chord and arc
+// midpoint; a minor arc, inside T, when 2 d exceeds the diameter of T).  At most 9 points:
+// an edge adds its start vertex and one crossing, or two crossings, plus one arc point.
+__device__ int region_disc(const double (*T)[2], double x0, double x1, double d, bool caps, double (*P)[2]) {
     int n = 0;
     const double rr = d * d;
+    bool ex[MAXV];
     for (int k = 0; k < 3; ++k) {
         const double *A = T[k], *B = T[(k + 1) % 3];
-        double px = A[0] - x0, py = A[1] - x1, ex = B[0] - A[0], ey = B[1] - A[1];
+        double px = A[0] - x0, py = A[1] - x1, ex_ = B[0] - A[0], ey = B[1] - A[1];
         double aa = px * px + py * py;
-        if (aa <= rr) { P[n][0] = A[0]; P[n][1] = A[1]; ++n; }
-        double qa = ex * ex + ey * ey, qb = px * ex + py * ey, qc = aa - rr;
+        if (aa <= rr) { P[n][0] = A[0]; P[n][1] = A[1]; ex[n] = false; ++n; }
+        double qa = ex_ * ex_ + ey * ey, qb = px * ex_ + py * ey, qc = aa - rr;
         double disc = qb * qb - qa * qc;
         if (disc > 0.0) {
             double sq = sqrt(disc);
             double ta = (-qb - sq) / qa, tb = (-qb + sq) / qa;
-            if (ta > 0.0 && ta < 1.0) { P[n][0] = A[0] + ta * ex; P[n][1] = A[1] + ta * ey; ++n; }
-            if (tb > 0.0 && tb < 1.0) { P[n][0] = A[0] + tb * ex; P[n][1] = A[1] + tb * ey; ++n; }
+            if (ta > 0.0 && ta < 1.0) { P[n][0] = A[0] + ta * ex_; P[n][1] = A[1] + ta * ey; ex[n] = false; ++n; }
+            if (tb > 0.0 && tb < 1.0) { P[n][0] = A[0] + tb * ex_; P[n][1] = A[1] + tb * ey; ex[n] = true; ++n; }
         }
     }
-    return n >= 3 ? n : 0;
+    if (!caps) return n >= 3 ? n : 0;
+    if (n < 2) return 0;
+    // insert the arc points from the back, so that each lands after its exit crossing
+    int m = n;
+    for (int k = 0; k < n; ++k) m += ex[k] ? 1 : 0;
+    const double qx = P[0][0], qy = P[0][1];      // the point after the last one
+    int w = m;
+    for (int k = n - 1; k >= 0; --k) {
+        if (ex[k]) {
+            const double nx = (k + 1 < n) ? P[k + 1][0] : qx, ny = (k + 1 < n) ? P[k + 1][1] : qy;
+            double mx = 0.5 * (P[k][0] + nx) - x0, my = 0.5 * (P[k][1] + ny) - x1;
+            double r = sqrt(mx * mx + my * my);
+            if (r > 0.0) {
+                --w;
+                P[w][0] = x0 + d * mx / r;
+                P[w][1] = x1 + d * my / r;
+            } else {
+                --m;            // a chord through x (not possible when 2 d > diam T): no arc point
+            }
+        }
+        --w;
+        P[w][0] = P[k][0];
+        P[w][1] = P[k][1];
+    }
+    // w is 0 unless arc points were dropped; close the gap
+    if (w > 0)
+        for (int k = 0; k < m; ++k) { P[k][0] = P[k + w][0]; P[k][1] = P[k + w][1]; }
+    return m >= 3 ? m : 0;
 }
 
 // exact moments of a polygon about x (constant kernel), by fan triangles:
@@ -425,8 +461,8 @@ __global__ void __launch_bounds__(64) k_assemble(AsmArgs a) {
             double x1 = R.b[q][0] * To[0][1] + R.b[q][1] * To[1][1] + R.b[q][2] * To[2][1];
             double P[MAXV][2];
             int np = (a.type == NLFETI_K_CONST_LINF) ? region_square(Ti, x0, x1, a.delta, P)
-                     : a.ball != 0                    ? region_whole(Ti, x0, x1, a.delta, a.ball, P)
-                                                      : region_disc(Ti, x0, x1, a.delta, P);
+                     : (a.ball != 0 && a.ball != 4)   ? region_whole(Ti, x0, x1, a.delta, a.ball, P)
+                                                      : region_disc(Ti, x0, x1, a.delta, a.ball == 4, P);
             if (np == 0) continue;
             double av[6];
             for (int i = 0; i < nl; ++i) {

@@ -3,7 +3,8 @@ system, through the C ABI (nlfeti_solve_cg).
 
 * the CG solution equals the oracle's single-domain FP64 Cholesky solve to the parity
   tolerance (relative nodal error <= 1e-8) on small workloads: 1-D, 2-D l2 constant, the
-  Omega_k = empty fractional case, the vector peridynamic kernel (jittered parts), K = 1;
+  Omega_k = empty fractional case, the vector peridynamic kernel (jittered parts), K = 1,
+  unstructured meshes, Neumann regions, the rounded collar, the approxcaps ball;
 * the 1-D quadratic with Dirichlet data is reproduced (closed form, |u - x^2/2| <= 1e-10);
 * graph loop and plain launches agree bit for bit, and a column gives bitwise the same
   result alone or batched (reductions in an order independent of the batch);
@@ -26,7 +27,13 @@ CASES = {
     "l2_unstructured": lambda: W.unstructured_l2(N=24, K=5, nrhs=2),
     "l2_neumann": lambda: W.neumann_l2(N=24, k=3, nrhs=2),
     "l2_rounded_collar": lambda: W.l2_collar_const(N=24, k=3, nrhs=2, delta=0.15),
+    "frac_approxcaps": lambda: _approxcaps(W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.1)),
 }
+
+
+def _approxcaps(w):
+    w.kernel.ball = 4
+    return w
 
 
 @pytest.fixture(scope="module")

@@ -10,7 +10,8 @@
   target), on small workloads spanning several tiles with ragged tails, floating
   subdomains, the Omega_k = empty degeneracy, the vector kernel, K = 1, unstructured
   meshes (irregular nodes and diagonals) with graph-grown local parts, the whole-element
-  approximate balls (barycenter, 123vertices, 23vertices), Neumann volume constraints
+  approximate balls (barycenter, 123vertices, 23vertices), the approxcaps ball (cap
+  triangles on the nocaps polygon; structured and unstructured), Neumann volume constraints
   (a free, loaded collar region on two sides) and the l2 (rounded-corner) collar.
 """
 import numpy as np
@@ -35,6 +36,10 @@ CASES = {
     "l2_ball_barycenter": lambda: _ball(W.cfg2_const_l2(N=24, k=3, nrhs=2, delta=0.1), 1),
     "frac_ball_123v": lambda: _ball(W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.1), 2),
     "pd_ball_23v": lambda: _ball(W.cfg4_peridynamic(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2), 3),
+    "l2_approxcaps": lambda: _ball(W.cfg2_const_l2(N=24, k=3, nrhs=2, delta=0.1), 4),
+    "frac_approxcaps": lambda: _ball(W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.1), 4),
+    "pd_approxcaps": lambda: _ball(W.cfg4_peridynamic(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2), 4),
+    "l2_unstructured_approxcaps": lambda: _ball(W.unstructured_l2(N=24, K=5, nrhs=2), 4),
     "l2_neumann": lambda: W.neumann_l2(N=24, k=3, nrhs=2),
     "pd_neumann": lambda: W.neumann_pd(N=30, k=3, nrhs=2),
     "l2_rounded_collar": lambda: W.l2_collar_const(N=24, k=3, nrhs=2, delta=0.15),
@@ -146,3 +151,11 @@ def test_quadratic_closed_form_1d_on_gpu(ctx):
     u, st = p.solve(w.rhs, w.rhs_kind, w.g)
     x = w.mesh.xy[:, 0]
     assert np.abs(u[:, 0] - 0.5 * x * x).max() < 1e-10
+
+
+def test_approxcaps_rejects_short_horizon(ctx):
+    from paper_2306_00094_gb300 import binding
+    w = _ball(W.cfg2_const_l2(N=24, k=2, nrhs=1, delta=0.02), 4)     # 2 delta < the diagonal h sqrt(2)
+    with pytest.raises(binding.NlfetiError) as e:
+        binding.Problem.from_workload(ctx, w)
+    assert e.value.status == binding.E_INVALID
