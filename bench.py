@@ -129,8 +129,8 @@ def profile_traffic(kernel_src_hash, name="k_apply_tma_cfg2.md"):
     return val if (val is not None and h == kernel_src_hash) else None
 
 
-def kernel_source_hash():
-    with open(os.path.join(ROOT, "paper_2306_00094_gb300", "csrc", "apply_tma.cuh"), "rb") as f:
+def kernel_source_hash(name="apply_tma.cuh"):
+    with open(os.path.join(ROOT, "paper_2306_00094_gb300", "csrc", name), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
@@ -163,7 +163,8 @@ def run_ours(args):
     # inputs resident in HBM: column-major n_dofs x R  ==  contiguous (R, n_dofs)
     d_rhs = torch.from_numpy(np.ascontiguousarray(w.rhs.T)).to(dev)
     d_out = torch.empty_like(d_rhs)
-    mixed = binding.default_options(precision=1, batched=1, graph_loop=0 if args.host_loop else 1)
+    mixed = binding.default_options(precision=1, batched=1, graph_loop=0 if args.host_loop else 1,
+                                    precond_fp16=2 if args.tensor_core_precond else 1)
     plain = binding.default_options(precision=0, batched=0)
     plain_batched = binding.default_options(precision=0, batched=1)
 
@@ -274,6 +275,23 @@ def run_ours(args):
     ksteps = max(3, min(args.steps, 5))
     plain_res = time_variant(plain, ksteps)
     plain_b_res = time_variant(plain_batched, ksteps)
+    # the mixed solve with the preconditioner's S_k apply on the tensor cores (tcgen05 MMAs on
+    # the FP16 copy and FP16 x, FP32 accumulators in tensor memory): solves/s, and the apply's
+    # own CUDA-event time from a profiled pass of the same steps
+    tc_opt = binding.default_options(precision=1, batched=1, precond_fp16=2)
+    tc_res = time_variant(tc_opt, ksteps)
+    prob.profile()
+    prob.set_profiling(True)
+    for _ in range(ksteps):
+        step()
+    torch.cuda.synchronize()
+    prob.set_profiling(False)
+    tp = prob.profile()
+    if tp["half_apply_launches"] > 0 and tp["half_apply_ms"] > 0:
+        tc_avg = tp["half_apply_ms"] / tp["half_apply_launches"] / 1e3
+        tc_bpl = tp["half_apply_bytes"] / tp["half_apply_launches"]
+        tc_res.update({"kernel": "k_apply_mma<16>", "avg_launch_us": tc_avg * 1e6, "bytes_per_launch": tc_bpl,
+                       "achieved_gbs": tc_bpl / tc_avg / 1e9, "frac": tc_bpl / tc_avg / 1e9 / hbm})
     u_plain = d_out.cpu().numpy().T.copy()
 
     # the paper's baseline solver on the same GPU and inputs: diagonally preconditioned CG on
@@ -364,6 +382,7 @@ def run_ours(args):
                              "bytes_per_launch": h_bpl, "avg_launch_us": h_avg * 1e6 if h_avg else None,
                              "launches": n_half, "share_of_step_time": h_share,
                              "traffic": profile_traffic(kernel_source_hash(), "k_apply_tma_fp16_cfg2.md")},
+        "precond_tensor_cores": tc_res,
         "gpu_launches": launches,
         "e2e": e2e,
         "plain_fp64_per_subdomain": plain_res,
@@ -668,6 +687,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true", help="setup, warm-up and the timed steps only (for ncu)")
+    ap.add_argument("--tensor-core-precond", action="store_true",
+                    help="the timed mixed solve applies the preconditioner's S_k on the tensor cores "
+                         "(precond_fp16 = 2; default: the FP16 copy on the FP32 pipes)")
     ap.add_argument("--host-loop", action="store_true",
                     help="PCG loops as host-checked graph chunks instead of device-side WHILE graphs "
                          "(ncu cannot profile kernels inside conditional graphs)")

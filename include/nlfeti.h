@@ -107,10 +107,13 @@ typedef struct {
  *          WHILE node (no host round trips); 0 = graphs of 4 iterations with a host check
  *          of convergence in between (for profilers that cannot look inside conditional
  *          graphs).  Profiling (nlfeti_set_profiling) always uses the second form.
- * precond_fp16 (mixed path): 1 = the scaled Dirichlet preconditioner applies S_k from an
- *          FP16 copy scaled by one power of two (half the bytes of the preconditioner apply;
- *          the preconditioner only steers the PCG, the accuracy reached is set by F and the
- *          FP64 refinement); 0 = from the FP32 S_k.  nlfeti_apply always uses the FP32 S_k. */
+ * precond_fp16 (mixed path): the scaled Dirichlet preconditioner applies S_k from an FP16
+ *          copy scaled by one power of two (half the bytes of the preconditioner apply; the
+ *          preconditioner only steers the PCG, the accuracy reached is set by F and the FP64
+ *          refinement).  1 = on the FP32 pipes (x in FP32; the default); 2 = on the tensor
+ *          cores (x in FP16, scaled per column by a power of two from its norm; FP32
+ *          accumulation) for at most 64 right-hand sides, else as 1; 0 = the FP32 S_k.
+ *          nlfeti_apply ops 0-4 always use the FP32 S_k. */
 typedef struct {
     int precision;
     double tol;
@@ -212,7 +215,10 @@ nlfeti_status nlfeti_get_operator(const nlfeti_problem *p, int k, int which, int
 
 /* Apply one FETI operator to host vectors (nrhs columns, column-major):
  * op 0 = F = B S^+ B^T (Lambda -> Lambda), 1 = M^-1 = B_D S B_D^T, 2 = P (eq. P),
- * 3 = S^+ (U -> U), 4 = S (U -> U). */
+ * 3 = S^+ (U -> U), 4 = S (U -> U), 5 = S (U -> U) through the copy the preconditioner of
+ * the mixed path applies (precision 1 and the options' precond_fp16: FP16 on the FP32 pipes,
+ * FP16 on the tensor cores with x scaled per column by a power of two from its largest
+ * entry, or FP32; precision 0: the FP64 S). */
 nlfeti_status nlfeti_apply(nlfeti_problem *p, int op, int precision, int nrhs, const double *in, double *out);
 
 /* No-allocation interface apply (the paper has no counterpart: an integration entry point).

@@ -179,7 +179,7 @@ void build_maps(nlfeti_problem *p) {
     p->n_u = d.u_off[K];
     p->n_co = d.co_off[K];
     p->sd.assign(K, SubdomainDesc{});
-    int64_t offA = 0, offAD = 0, offM = 0, offG = 0, offV = 0, offUp = 0, offVp = 0;
+    int64_t offA = 0, offAD = 0, offM = 0, offG = 0, offV = 0, offUp = 0, offVp = 0, offT = 0;
     p->n_floating = 0;
     p->max_ldG = 8;
     for (int k = 0; k < K; ++k) {
@@ -195,6 +195,7 @@ void build_maps(nlfeti_problem *p) {
         s.offAD = offAD; offAD += (int64_t)s.nk * s.nD;
         s.offM = offM; offM += (int64_t)s.nk * s.ldM;
         s.offS = offG; s.offSp = offG; offG += (int64_t)s.nG * s.ldG;
+        s.offT = offT; offT += s.nG > 0 ? (int64_t)((s.nG + 127) / 128) * mma_ktiles(s.nG, s.ldG) : 0;
         s.offU = d.u_off[k];
         s.offUp = offUp; offUp += s.ldG;
         s.offVp = offVp; offVp += s.ldM;
@@ -207,7 +208,7 @@ void build_maps(nlfeti_problem *p) {
         if (s.floating) p->n_floating++;
         p->max_ldG = std::max(p->max_ldG, s.ldG);
     }
-    p->poolA = offA; p->poolAD = offAD; p->poolM = offM; p->poolG = offG;
+    p->poolA = offA; p->poolAD = offAD; p->poolM = offM; p->poolG = offG; p->poolT = offT;
     p->sum_nk = offV;
     p->n_up = offUp;
     p->n_vp = offVp;
@@ -318,6 +319,26 @@ void build_maps(nlfeti_problem *p) {
     p->sched_ctas = schedule(items, apply_tma_ctas(), [](const SubdomainDesc &s, int r0) {
         return std::make_pair(std::min(kApplyRows, s.nG - r0), std::min<int64_t>(s.ldG, (s.nG + 7) / 8 * 8));
     }, p->d_sched_ptr, p->d_sched_items);
+    {
+        // tensor-core preconditioner apply: 128-row items, 64-column stages
+        std::vector<int32_t> items_m;
+        for (int k = 0; k < K; ++k)
+            for (int r0 = 0; r0 < p->sd[k].nG; r0 += 128) { items_m.push_back(k); items_m.push_back(r0); }
+        p->msched_ctas = items_m.empty() ? 0 : schedule(items_m, apply_mma_ctas(), [](const SubdomainDesc &s, int) {
+            return std::make_pair(128, (std::min<int64_t>(s.ldG, (s.nG + 7) / 8 * 8) + 63) / 64 * 64);
+        }, p->d_msched_ptr, p->d_msched_items);
+        p->mitem_off.assign(K + 1, 0);
+        int most = 1;
+        for (int k = 0; k < K; ++k) {
+            const int nk_items = (p->sd[k].nG + 127) / 128;
+            p->mitem_off[k + 1] = p->mitem_off[k] + nk_items;
+            most = std::max(most, nk_items);
+        }
+        std::vector<int32_t> iota(most + 1);
+        for (int i = 0; i <= most; ++i) iota[i] = i;
+        if (!items_m.empty()) upload(c, p->d_mitems, items_m);
+        upload(c, p->d_iota, iota);
+    }
     {
         std::vector<int32_t> items_a;
         for (int k = 0; k < K; ++k)
@@ -699,7 +720,7 @@ nlfeti_status nlfeti_get_operator(const nlfeti_problem *p, int k, int which, int
 nlfeti_status nlfeti_apply(nlfeti_problem *p, int op, int precision, int nrhs, const double *in, double *out) {
     if (!p || !in || !out || nrhs < 1) return NLFETI_E_INVALID;
     return guarded(p->ctx, [&] {
-        if (op < 0 || op > 4) fail(NLFETI_E_INVALID, "unknown operator");
+        if (op < 0 || op > 5) fail(NLFETI_E_INVALID, "unknown operator");
         const int64_t n = (op <= 2) ? p->n_lambda : p->n_u;
         if (n == 0) return;
         cudaStream_t st = p->ctx->stream;

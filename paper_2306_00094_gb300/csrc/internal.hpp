@@ -120,7 +120,16 @@ struct SubdomainDesc {      // per subdomain, device resident (POD)
                             // for R right-hand sides sits at offUp*R as R columns of ldG entries
     int64_t offVp;          // start of the subdomain in the padded subdomain-vector layout (sum of
                             // ldM): R columns of ldM entries at offVp*R (refinement residual input)
+    int64_t offT;           // first tile of S_k in the tiled FP16 copy (tensor-core apply): tiles of
+                            // 128 rows x 64 columns, ceil(nG/128) row tiles x mma_ktiles(nG, ldG)
 };
+
+// column tiles of 64 of an operator in the tiled FP16 copy: the streamed columns, min(ldG,
+// nG rounded up to 8), in 64-column tiles
+__host__ __device__ inline int mma_ktiles(int nG, int ldG) {
+    const int ncp = ldG < (nG + 7) / 8 * 8 ? ldG : (nG + 7) / 8 * 8;
+    return (ncp + 63) / 64;
+}
 
 constexpr int kApplyRows = 32;          // rows of an interface-apply work item
 
@@ -134,6 +143,9 @@ template <typename T> struct OpPool {   // operators of one precision
     nlf::DevMem Sh;                      // FP32 pool only: S_k * hscale in FP16 (preconditioner of the PCG)
     nlf::DevMem hmaps;                   // FP32 pool only: tensor maps of Sh (slot 2k per subdomain)
     double hscale = 1.0;                 // power of two: largest |S_k| entry * hscale in [2^13, 2^14)
+    nlf::DevMem St;                      // FP32 pool only: Sh tiled for the tensor-core apply: 128 x 64 tiles
+                                         // of 16 KB, each in the 128-byte swizzled K-major order of the MMA
+                                         // operand (zeros past n_gamma and ld_gamma)
     bool ready = false;
 };
 
@@ -159,7 +171,7 @@ struct nlfeti_problem {
     nlf::DevMem d_nodemap;
     // assembled FP64 matrices
     nlf::DevMem d_A, d_AD;
-    int64_t poolA = 0, poolAD = 0, poolM = 0, poolG = 0;
+    int64_t poolA = 0, poolAD = 0, poolM = 0, poolG = 0, poolT = 0;
     // jump operators
     nlf::DevMem d_Bp, d_Bm;              // int64 U index per Lambda row
     nlf::DevMem d_Bt_ptr, d_Bt_row;      // per U dof: rows, signed (r+1 for +1, -(r+1) for -1)
@@ -196,6 +208,13 @@ struct nlfeti_problem {
     // sched_items[sched_ptr[b] .. sched_ptr[b+1]) (pairs (k, first row)), balanced by cost
     int sched_ctas = 0;
     nlf::DevMem d_sched_ptr, d_sched_items;
+    // the same for the tensor-core preconditioner apply: 128-row items; and, for the launches
+    // per subdomain, the items in subdomain order (subdomain k: mitem_off[k] .. mitem_off[k+1])
+    // with the identity schedule 0, 1, 2, ... (one item per CTA)
+    int msched_ctas = 0;
+    nlf::DevMem d_msched_ptr, d_msched_items;
+    nlf::DevMem d_mitems, d_iota;
+    std::vector<int> mitem_off;
     nlf::DevMem d_flag;                  // device status words
     OpPool<double> op64;
     OpPool<float> op32;
@@ -229,6 +248,7 @@ void ctx_attach(nlfeti_ctx *c);
 void ctx_detach(nlfeti_ctx *c);
 // CTAs of the bulk-copy interface apply / refinement residual that fit on the device at once
 int apply_tma_ctas();
+int apply_mma_ctas();
 int residual_tma_ctas();
 // tensor maps of a pool's S_k and S_k^+ for the bulk-copy apply (after the factorization)
 template <typename T> void encode_apply_maps(nlfeti_problem *p, OpPool<T> &pool);

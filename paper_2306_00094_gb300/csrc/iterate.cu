@@ -114,6 +114,7 @@ __global__ void k_gather_bd(const int64_t *ptr, const int64_t *col, const double
 
 #include "rows.cuh"
 #include "apply_tma.cuh"
+#include "apply_mma.cuh"
 #include "residual_tma.cuh"
 
 __global__ void k_scatter_u(const int64_t *u2v, const double *uU, double *v, int64_t nu, int R) {
@@ -244,6 +245,7 @@ __global__ void k_apply_zalpha(const SubdomainDesc *sd, const int32_t *u2sub, co
 // PCG scalar state, per right-hand side
 struct PcgScalars {
     double *nPd, *yw_old, *yw, *eta, *beta, *relres, *corr;
+    double *xscale;        // per column: 2^-floor(log2 ||w||) (FP16 input of the tensor-core apply)
     int *active, *iters, *n_active;
     int *loops;            // PCG iterations run by the current graph loop
     int *err;              // set by a device wait that ran out (checked after the solve)
@@ -311,6 +313,7 @@ __device__ void finish_scalars(const double *partial, int nb, int R, PcgScalars 
                 s.beta[c] = 0.0;
             } else if (MODE == FIN_CHECK) {
                 const double nw = sqrt(v), ref = s.nPd[c];
+                s.xscale[c] = (nw > 0.0 && nw < INFINITY) ? ldexp(1.0, -ilogb(nw)) : 1.0;
                 int act = s.active[c];
                 if (act) s.relres[c] = ref > 0 ? nw / ref : 0.0;
                 if (act && (nw <= tol * ref || s.iters[c] >= max_it)) act = 0;
@@ -456,6 +459,59 @@ __global__ void k_gather_apply_p(const int64_t *ptr, const int64_t *row, const d
             s += r > 0 ? pn : -pn;
         }
         apply_store<T>(x, sd, u2sub, u, c, R, (T)s);
+    }
+}
+
+// store v * xscale (a power of two), rounded once to FP16, at (U dof u, column c) of the
+// apply layout; the thread of the last Gamma dof of a subdomain zeroes the column's padding
+__device__ __forceinline__ void store_f16(__half *x, const SubdomainDesc *sd, const int32_t *u2sub, int64_t u, int c,
+                                          int R, double v) {
+    const SubdomainDesc &d = sd[u2sub[u]];
+    const int64_t col = d.offUp * R + (int64_t)c * d.ldG;
+    const int j = (int)(u - d.offU);
+    x[col + j] = __double2half(v);
+    if (j == d.nG - 1)
+        for (int q = d.nG; q < d.ldG; ++q) x[col + q] = __float2half(0.0f);
+}
+
+// x (apply layout, FP16) = xscale B_D^T v for the tensor-core preconditioner apply (the sums
+// of k_gather_apply in FP64, scaled exactly, rounded once)
+__global__ void k_gather_apply_f16(const int64_t *ptr, const int64_t *row, const double *val, const double *v,
+                                   const double *xscale, __half *x, const SubdomainDesc *sd, const int32_t *u2sub,
+                                   int64_t nu, int R, const int *gate) {
+    if (gate && *gate == 0) return;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t / nu);
+        const int64_t u = t % nu;
+        double s = 0;
+        for (int64_t q = ptr[u]; q < ptr[u + 1]; ++q) s += val[q] * v[row[q] * R + c];
+        store_f16(x, sd, u2sub, u, c, R, s * xscale[c]);
+    }
+}
+
+// xscale[c] = 2^-floor(log2 max_u |v[u][c]|) (1 for a zero column); grid R blocks
+__global__ void __launch_bounds__(256) k_col_scale(const double *v, int64_t n, int R, double *xscale) {
+    __shared__ double red[8];
+    const int c = blockIdx.x;
+    double m = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(v[i * R + c]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmax(m, red[w]);
+        m = fmax(m, red[0]);
+        xscale[c] = (m > 0.0 && m < INFINITY) ? ldexp(1.0, -ilogb(m)) : 1.0;
+    }
+}
+
+// U vectors (interleaved, FP64) -> FP16 apply layout, column c scaled by xscale[c]
+__global__ void k_to_apply_f16(const double *uU, const double *xscale, __half *x, const SubdomainDesc *sd,
+                               const int32_t *u2sub, int64_t nu, int R) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t / nu);
+        const int64_t u = t % nu;
+        store_f16(x, sd, u2sub, u, c, R, uU[u * R + c] * xscale[c]);
     }
 }
 
@@ -893,6 +949,7 @@ struct Runner {
         double *b = ws.scal.as<double>();
         S.nPd = b; S.yw_old = b + R; S.yw = b + 2 * R; S.eta = b + 3 * R; S.beta = b + 4 * R; S.relres = b + 5 * R;
         S.corr = b + 6 * R;
+        S.xscale = ws.xscale.as<double>();
         int *ib = reinterpret_cast<int *>(b + 7 * R);
         S.active = ib; S.iters = ib + R; S.n_active = ib + 2 * R; S.loops = ib + 2 * R + 1;
         S.counter = reinterpret_cast<unsigned *>(ib + 2 * R + 2);
@@ -1063,7 +1120,7 @@ struct Runner {
     // the preconditioner's, which takes S_k from its FP16 copy in the mixed path (when enabled)
     template <typename T> void symv(const OpPool<T> &pool, int use_sp, const T *x, double *y, bool precond = false) {
         if (p->n_u == 0) return;
-        const bool half = std::is_same<T, float>::value && precond && !use_sp && p->opt.precond_fp16 && pool.Sh.p;
+        const bool half = std::is_same<T, float>::value && precond && !use_sp && p->opt.precond_fp16 != 0 && pool.Sh.p;
         const T *base = use_sp ? pool.Sp.template as<T>() : pool.S.template as<T>();
         Slot slot{};
         const bool timed = p->prof_on;
@@ -1097,6 +1154,61 @@ struct Runner {
         }
     }
 
+    // y = S x on every subdomain on the tensor cores (FP16 S_k and x in xU, x scaled per column
+    // by xscale, FP32 accumulators), timed like the other preconditioner applies
+    template <typename T> void symv_mma(const OpPool<T> &pool, double *y) {
+        Slot slot{};
+        const bool timed = p->prof_on;
+        const unsigned rec_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+        if (timed) {
+            NLF_CUDA(cudaEventCreate(&slot.a));
+            NLF_CUDA(cudaEventCreate(&slot.b));
+            NLF_CUDA(cudaEventRecordWithFlags(slot.a, st, rec_flags));
+        }
+        const __half *am = pool.St.template as<__half>();
+        const CUtensorMap *xm = ws.xhmaps.as<CUtensorMap>();
+        const double osc = 1.0 / pool.hscale;
+        const double *xs = ws.xscale.as<double>();
+        auto go = [&](int ctas, const int32_t *sp, const int32_t *si) {
+            if (ctas <= 0) return 0;
+            switch (mma_np(R)) {
+                case 16:
+                    k_apply_mma<16><<<ctas, MMA_THREADS, mma_smem_bytes(16), st>>>(am, xm, sd, sp, si, y, R, gate, S.err,
+                                                                                    osc, xs);
+                    break;
+                case 32:
+                    k_apply_mma<32><<<ctas, MMA_THREADS, mma_smem_bytes(32), st>>>(am, xm, sd, sp, si, y, R, gate, S.err,
+                                                                                    osc, xs);
+                    break;
+                default:
+                    k_apply_mma<64><<<ctas, MMA_THREADS, mma_smem_bytes(64), st>>>(am, xm, sd, sp, si, y, R, gate, S.err,
+                                                                                    osc, xs);
+                    break;
+            }
+            note_launch();
+            return 1;
+        };
+        // batched: the balanced persistent schedule; else one launch per subdomain, one item per
+        // CTA (every item runs the same MMA sequence either way: the same bits)
+        int launches = 0;
+        if (p->opt.batched) {
+            launches = go(p->msched_ctas, p->d_msched_ptr.as<int32_t>(), p->d_msched_items.as<int32_t>());
+        } else {
+            for (int k = 0; k < p->K; ++k)
+                launches += go(p->mitem_off[k + 1] - p->mitem_off[k], p->d_iota.as<int32_t>(),
+                               p->d_mitems.as<int32_t>() + 2 * p->mitem_off[k]);
+        }
+        if (timed) {
+            NLF_CUDA(cudaEventRecordWithFlags(slot.b, st, rec_flags));
+            double bytes = 0;
+            for (const auto &d : p->sd) bytes += (double)d.nG * d.ldG * 2.0 + (double)d.nG * R * (2.0 + sizeof(double));
+            slot.launches = launches;
+            slot.bytes = bytes;
+            slot.half = true;
+            (capturing ? graph_slots : eager_slots).push_back(slot);
+        }
+    }
+
     template <typename T> void applyF(const OpPool<T> &pool, const double *v, double *out, const double *cvec = nullptr) {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         T *x = ws.xU.as<T>();
@@ -1109,14 +1221,31 @@ struct Runner {
                                                      note_launch();
     }
 
+    // the preconditioner's S_k apply runs on the tensor cores (FP16 copy, FP16 x): mixed path
+    // with precond_fp16 = 2, at most MMA_MAX_R right-hand sides
+    template <typename T> bool use_mma(const OpPool<T> &pool, bool precond) const {
+        return std::is_same<T, float>::value && precond && p->opt.precond_fp16 == 2 && p->msched_ctas > 0 &&
+               R <= MMA_MAX_R && pool.St.p && ws.xhmaps.p;
+    }
+
     template <typename T> void applyMinv(const OpPool<T> &pool, const double *v, double *out, bool precond = false) {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         T *x = ws.xU.as<T>();
-        k_gather_apply<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_BDt_ptr.as<int64_t>(), p->d_BDt_row.as<int64_t>(),
-                                                            p->d_BDt_val.as<double>(), v, x, sd,
-                                                            p->d_u2sub.as<int32_t>(), nu, R, gate);
-        note_launch();
-        symv<T>(pool, 0, x, ws.yU.as<double>(), precond);
+        if (use_mma(pool, precond)) {
+            if (nu > 0) {
+                k_gather_apply_f16<<<grid_for(nu * R), 256, 0, st>>>(
+                    p->d_BDt_ptr.as<int64_t>(), p->d_BDt_row.as<int64_t>(), p->d_BDt_val.as<double>(), v,
+                    ws.xscale.as<double>(), ws.xU.as<__half>(), sd, p->d_u2sub.as<int32_t>(), nu, R, gate);
+                note_launch();
+                symv_mma(pool, ws.yU.as<double>());
+            }
+        } else {
+            k_gather_apply<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_BDt_ptr.as<int64_t>(), p->d_BDt_row.as<int64_t>(),
+                                                                p->d_BDt_val.as<double>(), v, x, sd,
+                                                                p->d_u2sub.as<int32_t>(), nu, R, gate);
+            note_launch();
+            symv<T>(pool, 0, x, ws.yU.as<double>(), precond);
+        }
         k_gather_bd<<<grid_for(nl * R), 256, 0, st>>>(p->d_BD_ptr.as<int64_t>(), p->d_BD_col.as<int64_t>(),
                                                       p->d_BD_val.as<double>(), ws.yU.as<double>(), out, nl, R);
                                                       note_launch();
@@ -1503,6 +1632,13 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     A(fU, nu); A(yU, nu); A(uU, nu);
     A(xU, std::max<int64_t>(1, p->n_up));   // apply layout (padding zeroed by the gathers)
     alloc(uhl, sizeof(float) * 2 * std::max<int64_t>(1, p->n_vp) * R);
+    alloc(xscale, sizeof(double) * R);
+    {
+        const std::vector<double> ones(R, 1.0);
+        NLF_CUDA(cudaMemcpyAsync(xscale.p, ones.data(), sizeof(double) * R, cudaMemcpyHostToDevice,
+                                 async_stream ? async_stream : c->stream));
+        NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
+    }
     NLF_CUDA(cudaMemsetAsync(xU.p, 0, xU.bytes, async_stream ? async_stream : c->stream));
     // tensor maps of xU per subdomain (R rows of ld_gamma entries at offUp * R), read as FP32
     // and as FP64, tiles of rc rows as the apply kernel of this R uses
@@ -1521,6 +1657,23 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
             }
             alloc(xmaps[e], sizeof(CUtensorMap) * maps.size());
             NLF_CUDA(cudaMemcpyAsync(xmaps[e].p, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                                     async_stream ? async_stream : c->stream));
+            NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
+        }
+        // xU read as FP16 by the tensor-core apply: tiles of 64 columns x (R rounded up to 16)
+        // rows, 128-byte swizzle (rows past R arrive as zeros)
+        if (R <= MMA_MAX_R) {
+            std::vector<CUtensorMap> bm(std::max(1, p->K));
+            std::memset(bm.data(), 0, sizeof(CUtensorMap) * bm.size());
+            for (int k = 0; k < p->K; ++k) {
+                const SubdomainDesc &d = p->sd[k];
+                if (d.nG == 0) continue;
+                const unsigned char *b = xU.as<unsigned char>() + d.offUp * R * 2;
+                if (encode_mma_map(encode_tiled(), &bm[k], b, d.ldG, R, mma_np(R)) != CUDA_SUCCESS)
+                    fail(NLFETI_E_CUDA, "cuTensorMapEncodeTiled failed for the FP16 apply input");
+            }
+            alloc(xhmaps, sizeof(CUtensorMap) * bm.size());
+            NLF_CUDA(cudaMemcpyAsync(xhmaps.p, bm.data(), sizeof(CUtensorMap) * bm.size(), cudaMemcpyHostToDevice,
                                      async_stream ? async_stream : c->stream));
             NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
         }
@@ -1668,6 +1821,20 @@ void apply_operator(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int op, int
                 run.symv<T>(pool, op == 3 ? 1 : 0, x, out);
                 break;
             }
+            case 5: {    // S through the preconditioner's copy (the path precond_fp16 selects)
+                if (nu == 0) break;
+                if (run.use_mma(pool, true)) {
+                    k_col_scale<<<R, 256, 0, st>>>(in, nu, R, ws.xscale.as<double>());
+                    k_to_apply_f16<<<grid_for(nu * R), 256, 0, st>>>(in, ws.xscale.as<double>(), ws.xU.as<__half>(),
+                                                                     run.sd, p->d_u2sub.as<int32_t>(), nu, R);
+                    run.symv_mma(pool, out);
+                } else {
+                    T *x = ws.xU.as<T>();
+                    k_to_apply<T><<<grid_for(nu * R), 256, 0, st>>>(in, x, run.sd, p->d_u2sub.as<int32_t>(), nu, R);
+                    run.symv<T>(pool, 0, x, out, true);
+                }
+                break;
+            }
             default: fail(NLFETI_E_INVALID, "unknown operator");
         }
     };
@@ -1758,6 +1925,23 @@ int apply_tma_ctas() {
     return sms * per_sm;
 }
 
+int apply_mma_ctas() {
+    int dev = 0, sms = 0;
+    NLF_CUDA(cudaGetDevice(&dev));
+    NLF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int per_sm = 1 << 20;
+    auto fit = [&](auto kern, int np) {
+        const int smem = mma_smem_bytes(np);
+        NLF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int b = 0;
+        NLF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, MMA_THREADS, smem));
+        per_sm = std::min(per_sm, b);
+    };
+    fit(k_apply_mma<16>, 16); fit(k_apply_mma<32>, 32); fit(k_apply_mma<64>, 64);
+    if (per_sm < 1) fail(NLFETI_E_CUDA, "the tensor-core apply does not fit on an SM");
+    return sms * per_sm;
+}
+
 int residual_tma_ctas() {
     int dev = 0, sms = 0;
     NLF_CUDA(cudaGetDevice(&dev));
@@ -1821,6 +2005,7 @@ template <typename T> void encode_apply_maps(nlfeti_problem *p, OpPool<T> &pool)
         pool.hmaps.alloc(p->ctx, sizeof(CUtensorMap) * hm.size());
         NLF_CUDA(cudaMemcpyAsync(pool.hmaps.p, hm.data(), sizeof(CUtensorMap) * hm.size(), cudaMemcpyHostToDevice,
                                  p->ctx->stream));
+
     }
     NLF_CUDA(cudaStreamSynchronize(p->ctx->stream));
 }

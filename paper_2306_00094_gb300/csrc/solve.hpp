@@ -24,6 +24,8 @@ struct SolveWS {
     DevMem lam, r, w, z, y, pv, q, d, cvec, dlam;      // Lambda space (FP64)
     DevMem fU, yU, uU, xU;                              // U space
     DevMem xmaps[2];                                    // tensor maps of xU per subdomain (FP32, FP64)
+    DevMem xhmaps;                                      // xU read as FP16 (tensor-core apply; R <= 64)
+    DevMem xscale;                                      // per column: power of two x is scaled by (FP16 x)
     DevMem ftil, res, u, du;                            // concatenated subdomain vectors
     DevMem uhl;                                         // u as FP32 hi / lo pairs, padded layout
     DevMem umaps;                                       // tensor maps of uh and ul per subdomain

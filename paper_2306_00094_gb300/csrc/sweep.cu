@@ -219,6 +219,27 @@ __global__ void k_to_half(const float *a, int64_t n, float scale, __half *h) {
         h[i] = __float2half_rn(a[i] * scale);
 }
 
+// Sh tiled for the tensor-core apply: tile t of subdomain k (row tile t / kt, column tile
+// t % kt, kt = mma_ktiles) holds rows 128 (t / kt) .. +127 and columns 64 (t % kt) .. +63 of
+// S_k * scale in FP16 (zero past n_gamma or ld_gamma), row r at byte 128 r, its 16-byte chunk j
+// (columns 8j..8j+7) at chunk position j ^ (r mod 8): the order of a 1 KB-aligned 128-byte
+// swizzled K-major operand.  Grid (tiles of the largest subdomain / 4 blocks, K); 256 threads.
+__global__ void k_tile_half(const float *S, float scale, const SubdomainDesc *sd, __half *T) {
+    const SubdomainDesc d = sd[blockIdx.y];
+    if (d.nG == 0) return;
+    const int kt = mma_ktiles(d.nG, d.ldG);
+    const int64_t ntiles = (int64_t)((d.nG + 127) / 128) * kt;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ntiles * 8192;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = e / 8192;
+        const int w = (int)(e % 8192), r = w / 64, cl = w % 64;
+        const int64_t i = (t / kt) * 128 + r, l = (t % kt) * 64 + cl;
+        const float v = (i < d.nG && l < d.ldG) ? S[d.offS + i * d.ldG + l] * scale : 0.f;
+        const int j = cl / 8, pos = r * 64 + ((j ^ (r & 7)) * 8) + cl % 8;
+        T[(d.offT + t) * 8192 + pos] = __float2half_rn(v);
+    }
+}
+
 template <typename T> __global__ void k_extract(const T *Mpool, T *Spool, T *Sppool, const SubdomainDesc *sd) {
     const SubdomainDesc d = sd[blockIdx.y];
     const int64_t nG = d.nG, ld = d.ldG;
@@ -506,6 +527,12 @@ template <typename T> void factor_ops(nlfeti_problem *p, OpPool<T> &pool) {
         k_to_half<<<512, 256, 0, c->stream>>>(pool.S.template as<float>(), n, (float)pool.hscale,
                                               pool.Sh.template as<__half>());
         NLF_CUDA(cudaGetLastError());
+        pool.St.alloc(c, sizeof(__half) * 8192 * std::max<int64_t>(p->poolT, 1));
+        if (p->poolT > 0 && p->K > 0) {
+            k_tile_half<<<dim3(256, p->K), 256, 0, c->stream>>>(pool.S.template as<float>(), (float)pool.hscale,
+                                                                p->d_sd.as<SubdomainDesc>(), pool.St.template as<__half>());
+            NLF_CUDA(cudaGetLastError());
+        }
     }
     encode_apply_maps<T>(p, pool);
     pool.ready = true;

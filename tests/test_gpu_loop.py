@@ -84,17 +84,19 @@ def test_launch_count_of_graph_loop(setup):
 
 
 def test_fp16_preconditioner_reaches_the_same_accuracy(setup):
-    """The FP16 copy of S_k only steers the PCG: with it and without it the mixed path reaches
-    the oracle's solution to the same tolerance (the refinement fixes the fixed point)."""
+    """The 16-bit copies of S_k (BF16 on the tensor cores, FP16 on the FP32 pipes) only steer
+    the PCG: with them and without them the mixed path reaches the oracle's solution to the
+    same tolerance (the refinement fixes the fixed point) in about as many iterations."""
     from oracle import problem as oprob
     binding, w, p = setup
     ref = oprob.Monolithic(w.mesh, w.kernel).solve(w.rhs, w.rhs_kind)
     out = {}
-    for fp16 in (0, 1):
+    for fp16 in (0, 1, 2):
         p.set_options(binding.default_options(precision=1, precond_fp16=fp16))
         u, st = p.solve(w.rhs, w.rhs_kind)
         assert (oprob.rel_nodal_error(u, ref, w.mesh, w.kernel.ncomp) <= 1e-8).all()
         out[fp16] = (u, st)
     scale = np.abs(out[0][0]).max()
-    assert np.abs(out[1][0] - out[0][0]).max() <= 1e-8 * scale
-    assert abs(out[1][1]["iterations"] - out[0][1]["iterations"]) <= max(3, out[0][1]["iterations"] // 5)
+    for fp16 in (1, 2):
+        assert np.abs(out[fp16][0] - out[0][0]).max() <= 1e-8 * scale
+        assert abs(out[fp16][1]["iterations"] - out[0][1]["iterations"]) <= max(3, out[0][1]["iterations"] // 5)
