@@ -933,8 +933,10 @@ struct Runner {
         int launches;
         double bytes;
         bool half;          // an apply of the FP16 preconditioner copy
+        int flag = -1;      // word of ws.slot_flags holding the gate (active columns) the apply saw
     };
     std::vector<Slot> graph_slots, eager_slots;
+    int next_graph_flag = 0, next_eager_flag = 0;
     // inside PCG iterations: the interface applies and their gathers return at once when no
     // right-hand side is active any more (every later update is masked by the active flags)
     const int *gate = nullptr;
@@ -944,6 +946,7 @@ struct Runner {
     bool use_cond = false;
     int64_t apply_launches = 0, half_launches = 0;
     double apply_ms = 0, apply_bytes = 0, half_ms = 0, half_bytes = 0;
+    std::vector<int> slot_flags_host;
 
     Runner(nlfeti_problem *pp, SolveWS &w, cudaStream_t s) : p(pp), ws(w), st(s), R(w.R) {
         double *b = ws.scal.as<double>();
@@ -991,12 +994,37 @@ struct Runner {
     void drop(std::vector<Slot> &v) {
         for (auto &s : v) { cudaEventDestroy(s.a); cudaEventDestroy(s.b); }
         v.clear();
+        if (&v == &graph_slots) next_graph_flag = 0;
+        else next_eager_flag = 0;
     }
 
-    // add the elapsed times of completed slots (the stream has been synchronized)
+    // a timed apply inside the PCG loop copies its gate (the number of active columns) into a
+    // flag word, so that the harvest counts only the launches that did the work (a gated
+    // launch returns at once; the chunked loop runs up to chunk - 1 of them per pass)
+    int snapshot_gate() {
+        if (!gate) return -1;
+        int idx = -1;
+        if (capturing && next_graph_flag < kSlotFlags / 2) idx = next_graph_flag++;
+        if (!capturing && next_eager_flag < kSlotFlags / 2) idx = kSlotFlags / 2 + next_eager_flag++;
+        if (idx >= 0)
+            NLF_CUDA(cudaMemcpyAsync(ws.slot_flags.as<int>() + idx, gate, sizeof(int), cudaMemcpyDeviceToDevice, st));
+        return idx;
+    }
+
+    // add the elapsed times of completed slots (the stream has been synchronized); slots whose
+    // gate was zero (the apply returned at once) are left out
     void harvest(std::vector<Slot> &v, bool clear) {
+        bool any = false;
+        for (auto &s : v) any |= s.flag >= 0;
+        if (any) {
+            slot_flags_host.resize(kSlotFlags);
+            NLF_CUDA(cudaMemcpyAsync(slot_flags_host.data(), ws.slot_flags.p, sizeof(int) * kSlotFlags,
+                                     cudaMemcpyDeviceToHost, st));
+            NLF_CUDA(cudaStreamSynchronize(st));
+        }
         for (auto &s : v) {
             float ms = 0.f;
+            if (s.flag >= 0 && slot_flags_host[s.flag] == 0) continue;
             if (cudaEventElapsedTime(&ms, s.a, s.b) == cudaSuccess) {
                 (s.half ? half_ms : apply_ms) += ms;
                 (s.half ? half_launches : apply_launches) += s.launches;
@@ -1129,6 +1157,7 @@ struct Runner {
         if (timed) {
             NLF_CUDA(cudaEventCreate(&slot.a));
             NLF_CUDA(cudaEventCreate(&slot.b));
+            slot.flag = snapshot_gate();
             NLF_CUDA(cudaEventRecordWithFlags(slot.a, st, rec_flags));
         }
         int launches = 0;
@@ -1163,6 +1192,7 @@ struct Runner {
         if (timed) {
             NLF_CUDA(cudaEventCreate(&slot.a));
             NLF_CUDA(cudaEventCreate(&slot.b));
+            slot.flag = snapshot_gate();
             NLF_CUDA(cudaEventRecordWithFlags(slot.a, st, rec_flags));
         }
         const __half *am = pool.St.template as<__half>();
@@ -1699,6 +1729,7 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     alloc(partial, sizeof(double) * RED_BLOCKS * R);
     alloc(partial2, sizeof(double) * RED_BLOCKS * R);
     alloc(scal, sizeof(double) * R * 7 + sizeof(int) * (2 * R + 8));
+    alloc(slot_flags, sizeof(int) * kSlotFlags);
     NLF_CUDA(cudaMemsetAsync(scal.p, 0, scal.bytes, async_stream ? async_stream : c->stream));
     host_flag.assign(4, 0);
 }

@@ -17,6 +17,8 @@ struct PcgGraph {
     int kind = 0;                   // 0: FETI PCG loop, 1: single-domain CG loop
 };
 
+constexpr int kSlotFlags = 1024;   // flag words of the timed applies: half for graphs, half eager
+
 struct SolveWS {
     nlfeti_problem *prob = nullptr;
     uint64_t prob_uid = 0;
@@ -26,6 +28,7 @@ struct SolveWS {
     DevMem xmaps[2];                                    // tensor maps of xU per subdomain (FP32, FP64)
     DevMem xhmaps;                                      // xU read as FP16 (tensor-core apply; R <= 64)
     DevMem xscale;                                      // per column: power of two x is scaled by (FP16 x)
+    DevMem slot_flags;                                  // gates seen by the timed applies (profiling)
     DevMem ftil, res, u, du;                            // concatenated subdomain vectors
     DevMem uhl;                                         // u as FP32 hi / lo pairs, padded layout
     DevMem umaps;                                       // tensor maps of uh and ul per subdomain
