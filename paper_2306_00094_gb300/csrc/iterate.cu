@@ -901,8 +901,9 @@ inline int *ws_err(SolveWS &ws, int R) { return reinterpret_cast<int *>(ws.scal.
 void residual_ds(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, const double *lam) {
     if (p->rsched_ctas == 0) return;
     const OpPool<float> &pool = p->op32;
-    float *uh = ws.uhl.as<float>(), *ul = uh + p->n_vp * R;
-    k_split_u<<<dim3(p->K, R), 256, 0, st>>>(ws.u.as<double>(), p->d_sd.as<SubdomainDesc>(), uh, ul, R);
+    const int R2 = (R + 1) / 2 * 2;
+    float *uh = ws.uhl.as<float>(), *ul = uh + std::max<int64_t>(1, p->n_vp) * R2;
+    k_split_u<<<dim3(p->K, R2), 256, 0, st>>>(ws.u.as<double>(), p->d_sd.as<SubdomainDesc>(), uh, ul, R);
     auto go = [&](auto rc_tag) {
         constexpr int RC = decltype(rc_tag)::value;
         k_residual_tma<RC><<<p->rsched_ctas, RES_THREADS, res_smem_bytes(RC), st>>>(
@@ -1661,7 +1662,7 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     A(lam, nl); A(r, nl); A(w, nl); A(z, nl); A(y, nl); A(pv, nl); A(q, nl); A(d, nl); A(cvec, nl); A(dlam, nl);
     A(fU, nu); A(yU, nu); A(uU, nu);
     A(xU, std::max<int64_t>(1, p->n_up));   // apply layout (padding zeroed by the gathers)
-    alloc(uhl, sizeof(float) * 2 * std::max<int64_t>(1, p->n_vp) * R);
+    alloc(uhl, sizeof(float) * 2 * std::max<int64_t>(1, p->n_vp) * ((R + 1) / 2 * 2));
     alloc(xscale, sizeof(double) * R);
     {
         const std::vector<double> ones(R, 1.0);
@@ -1707,15 +1708,19 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
                                      async_stream ? async_stream : c->stream));
             NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
         }
-        // uh and ul (FP32, R rows of ld_M entries at offVp * R each) for the refinement residual
+        // uh and ul (FP32, column pairs: R2 / 2 rows of 2 ld_M entries at offVp * R2 each) for the
+        // refinement residual, tiles of (rc + 1) / 2 pair rows
         std::vector<CUtensorMap> um(2 * std::max(1, p->K));
         std::memset(um.data(), 0, sizeof(CUtensorMap) * um.size());
-        const float *uh = uhl.as<float>(), *ul = uh + std::max<int64_t>(1, p->n_vp) * R;
+        const int R2 = (R + 1) / 2 * 2;
+        const float *uh = uhl.as<float>(), *ul = uh + std::max<int64_t>(1, p->n_vp) * R2;
         for (int k = 0; k < p->K; ++k) {
             const SubdomainDesc &d = p->sd[k];
             if (d.nk == 0) continue;
-            if (encode_apply_map(encode_tiled(), &um[2 * k], uh + d.offVp * R, d.ldM, R, 4, rcb, RES_CB) != CUDA_SUCCESS ||
-                encode_apply_map(encode_tiled(), &um[2 * k + 1], ul + d.offVp * R, d.ldM, R, 4, rcb, RES_CB) != CUDA_SUCCESS)
+            if (encode_apply_map(encode_tiled(), &um[2 * k], uh + d.offVp * R2, 2 * d.ldM, R2 / 2, 4, (rcb + 1) / 2,
+                                 2 * RES_CB) != CUDA_SUCCESS ||
+                encode_apply_map(encode_tiled(), &um[2 * k + 1], ul + d.offVp * R2, 2 * d.ldM, R2 / 2, 4, (rcb + 1) / 2,
+                                 2 * RES_CB) != CUDA_SUCCESS)
                 fail(NLFETI_E_CUDA, "cuTensorMapEncodeTiled failed for the residual input");
         }
         alloc(umaps, sizeof(CUtensorMap) * um.size());

@@ -264,15 +264,17 @@ __global__ void k_to_apply(const double *uU, T *x, const SubdomainDesc *sd, cons
     }
 }
 
-// u (interleaved subdomain vectors, FP64) -> FP32 pairs uh + ul in the padded layout: for
-// subdomain k, R columns of ld_M entries at offVp * R, zero beyond n_k.  Grid (K, R).
+// u (interleaved subdomain vectors, FP64) -> FP32 pairs uh + ul in the padded layout, the
+// columns taken two at a time: for subdomain k, R2 / 2 rows (R2 = R rounded up to even) at
+// offVp * R2, row q holding columns 2q and 2q + 1 interleaved entry by entry (2 ld_M floats),
+// zero beyond n_k and in the pad column.  Grid (K, R2).
 __global__ void k_split_u(const double *u, const SubdomainDesc *sd, float *uh, float *ul, int R) {
     const SubdomainDesc d = sd[blockIdx.x];
-    const int c = blockIdx.y;
+    const int c = blockIdx.y, R2 = (R + 1) / 2 * 2;          // grid (K, R2): the pad column is zero
     for (int l = threadIdx.x; l < d.ldM; l += blockDim.x) {
-        const double v = l < d.nk ? u[(d.offV + l) * R + c] : 0.0;
+        const double v = (l < d.nk && c < R) ? u[(d.offV + l) * R + c] : 0.0;
         const float h = (float)v;
-        const int64_t o = d.offVp * R + (int64_t)c * d.ldM + l;
+        const int64_t o = d.offVp * R2 + (int64_t)(c / 2) * 2 * d.ldM + 2 * l + (c & 1);
         uh[o] = h;
         ul[o] = (float)(v - (double)h);
     }
