@@ -184,18 +184,20 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
                     if (lane == 0) { atomicExch(err, 1); abort_flag = 1; }
                     return;                           // the whole warp (the vote is uniform)
                 }
-                const int cw = min(CW, ncp - l0);
                 const MT *st = reinterpret_cast<const MT *>(ring + s * STAGE);
                 const T *xs = reinterpret_cast<const T *>(ring + s * STAGE + 32 * MROW);
+                // the tiles land whole, with zeros past n_gamma, ld_gamma and R (and the operator's
+                // padding columns and x's padding are zero), so every lane runs the full stage
+                // without bounds tests: the extra products are exact zeros and the rows and
+                // columns past the operator are never stored
                 if (ib < n) {
-                    for (int l = lane * W; l < cw; l += 32 * W) {
+#pragma unroll
+                    for (int j = 0; j < CW / (32 * W); ++j) {
+                        const int l = lane * W + j * 32 * W;
                         V mv[4];
 #pragma unroll
-                        for (int r = 0; r < 4; ++r)
-                            mv[r] = load_widen<T, MT>(st + (warp * 4 + min(r, n - 1 - ib)) * CW + l);
-                        rows_step<T, RC>(mv, [&](int c) {
-                            return c < rc ? *reinterpret_cast<const V *>(xs + c * CW + l) : V{};
-                        }, acc);
+                        for (int r = 0; r < 4; ++r) mv[r] = load_widen<T, MT>(st + (warp * 4 + r) * CW + l);
+                        rows_step<T, RC>(mv, [&](int c) { return *reinterpret_cast<const V *>(xs + c * CW + l); }, acc);
                     }
                 }
                 __syncwarp();
