@@ -100,3 +100,22 @@ def test_fp16_preconditioner_reaches_the_same_accuracy(setup):
     for fp16 in (1, 2):
         assert np.abs(out[fp16][0] - out[0][0]).max() <= 1e-8 * scale
         assert abs(out[fp16][1]["iterations"] - out[0][1]["iterations"]) <= max(3, out[0][1]["iterations"] // 5)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_columns_bitwise_independent_of_batch_size(setup, precision):
+    """Every kernel treats a column the same whatever batch it is part of; the Lambda
+    reductions sum it over the same rows in the same tree in the coalesced layout (up to 8
+    columns) and in the one-column-per-block layout (more columns).  So one right-hand side
+    solved alone, in a batch of 8 and in a batch of 9 identical columns (the same iterations
+    and sweeps) gives bitwise the same solution."""
+    binding, w, p = setup
+    p.set_options(binding.default_options(precision=precision))
+    col = np.asfortranarray(w.rhs[:, :1])
+    u1, s1 = p.solve(col, w.rhs_kind)
+    u8, s8 = p.solve(np.asfortranarray(np.tile(col, (1, 8))), w.rhs_kind)
+    u9, s9 = p.solve(np.asfortranarray(np.tile(col, (1, 9))), w.rhs_kind)
+    assert s1["iterations"] == s8["iterations"] == s9["iterations"]
+    for u in (u8, u9):
+        for c in range(u.shape[1]):
+            assert np.array_equal(u[:, c], u1[:, 0]), (u.shape[1], c, np.abs(u[:, c] - u1[:, 0]).max())
