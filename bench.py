@@ -59,6 +59,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x, world, device=None):
+    """The largest of a per-rank time (every rank gets it); the identity on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, slowest_s):
+    """Whole-job throughput of independent replicas: the units all ranks processed over the
+    time of the slowest rank."""
+    return world * units_per_rank / slowest_s
+
+
 class ClockSampler:
     """nvidia-smi clock and throttle samples during the timed region."""
 
@@ -192,12 +208,8 @@ def run_ours(args):
     clocks = sampler.stop()
     launches = prob.profile()["kernel_launches"]
     lat = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * R * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), world, dev)
+    value = replica_throughput(R * args.steps, world, total_ms / 1e3)
     u_gpu = d_out.cpu().numpy().T.copy()
 
     # roofline of the dominant kernel (dense interface apply, FP32): the same K steps again
@@ -247,12 +259,9 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         prob.solve_host_ptr(h_rhs.data_ptr(), w.rhs_kind, h_out.data_ptr(), R)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * R * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * R * ndof,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e = {"value": replica_throughput(R * args.steps, world, e2e_s), "unit": "solves/s",
+           "h2d_bytes_per_step": 8 * R * ndof,
            "d2h_bytes_per_step": 8 * R * ndof}
 
     # baselines on the GPU: plain FP64 one subdomain at a time (no graphs), and FP64 batched
