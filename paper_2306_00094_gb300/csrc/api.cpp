@@ -548,8 +548,11 @@ nlfeti_status nlfeti_problem_info(const nlfeti_problem *p, nlfeti_info *info) {
 nlfeti_status nlfeti_problem_set_options(nlfeti_problem *p, const nlfeti_options *opt) {
     if (!p || !opt) return NLFETI_E_INVALID;
     if (opt->precision != 0 && opt->precision != 1) return NLFETI_E_INVALID;
-    p->opt = *opt;
-    return NLFETI_OK;
+    if (opt->precond_fp16 < 0 || opt->precond_fp16 > 2) return NLFETI_E_INVALID;
+    return guarded(p->ctx, [&] {
+        p->opt = *opt;
+        if (p->opt.precond_fp16 == 2 && p->op32.ready) build_tiled_half(p);
+    });
 }
 
 nlfeti_status nlfeti_factor(nlfeti_problem *p, int mask) {

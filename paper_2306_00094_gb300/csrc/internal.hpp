@@ -237,6 +237,8 @@ struct nlfeti_problem {
 namespace nlf {
 void assemble_all(nlfeti_problem *p);
 template <typename T> void factor_ops(nlfeti_problem *p, OpPool<T> &pool);
+// the FP16 copy of S_k tiled for the tensor-core preconditioner apply (FP32 operators factored)
+void build_tiled_half(nlfeti_problem *p);
 void setup_coarse(nlfeti_problem *p);
 void setup_jump_weights(nlfeti_problem *p);
 void set_error(nlfeti_ctx *c, const std::string &msg);

@@ -447,6 +447,20 @@ template <typename T> void run_sweeps(nlfeti_problem *p, T *pool, const std::vec
 
 }  // namespace
 
+// the FP16 copy of S_k tiled for the tensor-core apply (after the FP32 factorization)
+void build_tiled_half(nlfeti_problem *p) {
+    nlfeti_ctx *c = p->ctx;
+    OpPool<float> &pool = p->op32;
+    if (!pool.S.p || pool.St.p) return;
+    pool.St.alloc(c, sizeof(__half) * 8192 * std::max<int64_t>(p->poolT, 1));
+    if (p->poolT > 0 && p->K > 0) {
+        k_tile_half<<<dim3(256, p->K), 256, 0, c->stream>>>(pool.S.as<float>(), (float)pool.hscale,
+                                                            p->d_sd.as<SubdomainDesc>(), pool.St.as<__half>());
+        NLF_CUDA(cudaGetLastError());
+    }
+    NLF_CUDA(cudaStreamSynchronize(c->stream));
+}
+
 template <typename T> void factor_ops(nlfeti_problem *p, OpPool<T> &pool) {
     nlfeti_ctx *c = p->ctx;
     const int K = p->K;
@@ -527,12 +541,10 @@ template <typename T> void factor_ops(nlfeti_problem *p, OpPool<T> &pool) {
         k_to_half<<<512, 256, 0, c->stream>>>(pool.S.template as<float>(), n, (float)pool.hscale,
                                               pool.Sh.template as<__half>());
         NLF_CUDA(cudaGetLastError());
-        pool.St.alloc(c, sizeof(__half) * 8192 * std::max<int64_t>(p->poolT, 1));
-        if (p->poolT > 0 && p->K > 0) {
-            k_tile_half<<<dim3(256, p->K), 256, 0, c->stream>>>(pool.S.template as<float>(), (float)pool.hscale,
-                                                                p->d_sd.as<SubdomainDesc>(), pool.St.template as<__half>());
-            NLF_CUDA(cudaGetLastError());
-        }
+        // the tiled copy for the tensor-core apply only when that apply is selected (else built
+        // by nlfeti_problem_set_options when it is)
+        pool.St.release();
+        if (p->opt.precond_fp16 == 2) build_tiled_half(p);
     }
     encode_apply_maps<T>(p, pool);
     pool.ready = true;
