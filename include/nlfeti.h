@@ -164,6 +164,9 @@ nlfeti_status nlfeti_problem_create(nlfeti_ctx *ctx, const nlfeti_mesh *mesh, co
                                     const nlfeti_decomp *decomp, nlfeti_problem **out);
 void nlfeti_problem_destroy(nlfeti_problem *p);
 nlfeti_status nlfeti_problem_info(const nlfeti_problem *p, nlfeti_info *info);
+/* Replace the problem's options (copied).  NLFETI_E_INVALID for a precision other than 0/1
+ * or precond_fp16 outside 0..2.  Selecting precond_fp16 = 2 once the FP32 operators are
+ * factored builds the tiled FP16 copy of S_k the tensor-core apply reads (synchronous). */
 nlfeti_status nlfeti_problem_set_options(nlfeti_problem *p, const nlfeti_options *opt);
 
 /* Factor the subdomain operators (eq. splittingBlockCholesky, eq. subSchurComplement,
