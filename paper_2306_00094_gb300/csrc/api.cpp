@@ -319,6 +319,12 @@ void build_maps(nlfeti_problem *p) {
     p->sched_ctas = schedule(items, apply_tma_ctas(), [](const SubdomainDesc &s, int r0) {
         return std::make_pair(std::min(kApplyRows, s.nG - r0), std::min<int64_t>(s.ldG, (s.nG + 7) / 8 * 8));
     }, p->d_sched_ptr, p->d_sched_items);
+    p->fsched_ctas = schedule(items, apply_tma_ctas(), [](const SubdomainDesc &s, int r0) {
+        return std::make_pair(std::min(kApplyRows, s.nG - r0), (int64_t)(s.nO + 7) / 8 * 8);
+    }, p->d_fsched_ptr, p->d_fsched_items);
+    p->osched_ctas = items_o.empty() ? 0 : schedule(items_o, apply_tma_ctas(), [](const SubdomainDesc &s, int r0) {
+        return std::make_pair(std::min(kApplyRows, s.nO - r0), std::min<int64_t>(s.ldM, (s.nk + 7) / 8 * 8));
+    }, p->d_osched_ptr, p->d_osched_items);
     {
         // tensor-core preconditioner apply: 128-row items, 64-column stages
         std::vector<int32_t> items_m;

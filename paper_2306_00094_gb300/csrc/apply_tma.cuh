@@ -102,11 +102,42 @@ inline CUresult encode_apply_map(Encode encode, CUtensorMap *map, const void *ba
                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
-template <typename T, int RC, int NS = APPLY_NS, int MINB = APPLY_MINB, typename MT = T>
+// tensor map of a block of a row-major matrix (rows of `stride` entries, 16-byte aligned; the
+// block cols x rows from base) for tiles of 32 rows x APPLY_CB bytes: the sub-blocks of the
+// swept matrix that the forcing and back-substitution modes stream
+template <typename Encode>
+inline CUresult encode_block_map(Encode encode, CUtensorMap *map, const void *base, int cols, int rows, int stride,
+                                 int elem_size) {
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)stride * (cuuint64_t)elem_size};
+    const cuuint32_t box[2] = {(cuuint32_t)(APPLY_CB / elem_size), 32u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUtensorMapDataType dt = elem_size == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    return encode(map, dt, 2u, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+// rows and streamed columns of an item's operator per mode: the interface apply (S_k or S_k^+,
+// n_gamma x n_gamma), the forcing (rows n_O.. of the swept matrix, columns 0..n_O-1: T_k) and
+// the back substitution (rows 0..n_O-1, all n_k columns)
+template <int MODE>
+__device__ __forceinline__ void apply_shape(const SubdomainDesc &d, int &n, int &ncp) {
+    if (MODE == ROWS_APPLY) { n = d.nG; ncp = min(d.ldG, (d.nG + 7) / 8 * 8); }
+    else if (MODE == ROWS_FORCING) { n = d.nG; ncp = (d.nO + 7) / 8 * 8; }
+    else { n = d.nO; ncp = min(d.ldM, (d.nk + 7) / 8 * 8); }
+}
+
+// MODE (ROWS_APPLY, ROWS_FORCING, ROWS_BACKSUB) selects the operator block (above), the tensor
+// maps (APPLY: 2 per subdomain, use_sp picks; else 1 per subdomain) and the output:
+//   APPLY     y[(offU + i) R + c] = acc * oscale;
+//   FORCING   y[(offU + i) R + c] = xa[(offV + n_O + i) R + c] - acc   (reduced forcing, f_G - T_k f_O);
+//   BACKSUB   y[(offV + i) R + c] = -acc                              (u_O from the swept -A_OO^-1 rows),
+// the same outputs, in the same order of operations per lane, as k_rows.
+template <typename T, int RC, int NS = APPLY_NS, int MINB = APPLY_MINB, typename MT = T, int MODE = ROWS_APPLY>
 __global__ void __launch_bounds__(APPLY_THREADS, MINB)
     k_apply_tma(const CUtensorMap *maps, const CUtensorMap *xmaps, int use_sp, const SubdomainDesc *sd,
                 const int32_t *sched_ptr, const int32_t *sched_items, double *y, int R, const int *gate, int *err,
-                double oscale = 1.0) {
+                double oscale = 1.0, const double *xa = nullptr) {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
     constexpr int CW = APPLY_CB / (int)sizeof(T);   // columns per stage row
@@ -135,9 +166,9 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
         for (int it = it0; it < it1 && ok; ++it) {
             // descriptor fields in registers: the asm statements below clobber memory
             const int k = sched_items[2 * it], i0 = sched_items[2 * it + 1];
-            const int n = sd[k].nG, ld = sd[k].ldG;
-            const int ncp = min(ld, (n + 7) / 8 * 8);
-            const CUtensorMap *map = maps + 2 * k + use_sp, *xmap = xmaps + k;
+            int n, ncp;
+            apply_shape<MODE>(sd[k], n, ncp);
+            const CUtensorMap *map = MODE == ROWS_APPLY ? maps + 2 * k + use_sp : maps + k, *xmap = xmaps + k;
             for (int c0 = 0; c0 < R && ok; c0 += RC)        // the rows again for every column block
             for (int l0 = 0; l0 < ncp; l0 += CW, ++q) {
                 const int s = q % NS;
@@ -167,9 +198,9 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
     int q = 0;
     for (int it = it0; it < it1; ++it) {
         const int k = sched_items[2 * it], i0 = sched_items[2 * it + 1];
-        const int n = sd[k].nG, ld = sd[k].ldG;
-        const int64_t yoff = sd[k].offU;
-        const int ncp = min(ld, (n + 7) / 8 * 8);
+        int n, ncp;
+        apply_shape<MODE>(sd[k], n, ncp);
+        const int64_t yoff = sd[k].offU, voff = sd[k].offV, nO = sd[k].nO;
         const int ib = i0 + warp * 4;
         for (int c0 = 0; c0 < R; c0 += RC) {
             const int rc = min(RC, R - c0);
@@ -212,7 +243,12 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
             const T tot = warp_reduce_scatter<T, NV>(v, lane);
             constexpr int G = 32 / NV;
             const int idx = lane / G, r = idx / RC, c = idx % RC, i = ib + r;
-            if (lane % G == 0 && c < rc && i < n) y[(yoff + i) * R + c0 + c] = (double)tot * oscale;
+            if (lane % G == 0 && c < rc && i < n) {
+                if (MODE == ROWS_APPLY) y[(yoff + i) * R + c0 + c] = (double)tot * oscale;
+                else if (MODE == ROWS_FORCING)
+                    y[(yoff + i) * R + c0 + c] = xa[(voff + nO + i) * R + c0 + c] - (double)tot;
+                else y[(voff + i) * R + c0 + c] = -(double)tot;
+            }
         }
     }
 }

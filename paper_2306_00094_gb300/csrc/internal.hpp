@@ -137,6 +137,8 @@ template <typename T> struct OpPool {   // operators of one precision
     nlf::DevMem M, S, Sp;                // swept matrices, Schur complements, pseudo-inverses
     nlf::DevMem scratch;                 // panel scratch of the sweeps
     nlf::DevMem maps;                    // tensor maps of S_k and S_k^+ (2 per subdomain) for the apply
+    nlf::DevMem fmaps, omaps;            // tensor maps of the swept matrix blocks the forcing (rows n_O..,
+                                         // columns ..n_O) and the back substitution (rows ..n_O) stream
     nlf::DevMem Ahi, Alo;                // FP32 pool only: A^k = Ahi + Alo (FP32 pairs, swept-matrix layout),
                                          // for the double-single refinement residual
     nlf::DevMem amaps;                   // FP32 pool only: tensor maps of Ahi and Alo (2 per subdomain)
@@ -213,6 +215,10 @@ struct nlfeti_problem {
     // with the identity schedule 0, 1, 2, ... (one item per CTA)
     int msched_ctas = 0;
     nlf::DevMem d_msched_ptr, d_msched_items;
+    // and for the forcing (items over Gamma rows, n_O columns) and the back substitution (items
+    // over Omega rows, n_k columns) on the same pipeline
+    int fsched_ctas = 0, osched_ctas = 0;
+    nlf::DevMem d_fsched_ptr, d_fsched_items, d_osched_ptr, d_osched_items;
     nlf::DevMem d_mitems, d_iota;
     std::vector<int> mitem_off;
     nlf::DevMem d_flag;                  // device status words

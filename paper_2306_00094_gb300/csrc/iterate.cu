@@ -515,6 +515,24 @@ __global__ void k_to_apply_f16(const double *uU, const double *xscale, __half *x
     }
 }
 
+// right-hand side of the forcing (MODE ROWS_FORCING: f_O) or of the back substitution
+// (ROWS_BACKSUB: [f_O; u_G]) per subdomain, R columns of ld_M entries at offVp * R, zero past
+// the block's columns: the values (and conversions) k_rows stages in shared memory.  Grid (K, R).
+template <typename T, int MODE>
+__global__ void k_stage_rows_x(const double *xa, const double *xb, const SubdomainDesc *sd, T *xs, int R) {
+    const SubdomainDesc d = sd[blockIdx.x];
+    const int c = blockIdx.y;
+    const int ncols = MODE == ROWS_FORCING ? d.nO : d.nk;
+    for (int l = threadIdx.x; l < d.ldM; l += blockDim.x) {
+        T v = T(0);
+        if (l < ncols) {
+            if (MODE == ROWS_FORCING || l < d.nO) v = (T)xa[(d.offV + l) * R + c];
+            else v = (T)xb[(d.offU + l - d.nO) * R + c];
+        }
+        xs[d.offVp * R + (int64_t)c * d.ldM + l] = v;
+    }
+}
+
 // alpha = (G^T G)^-1 G^T v.  G^T v is gathered from flat entry lists per floating subdomain
 // f: for v on Lambda, entry e of B^T restricted to Gamma_f is (Lambda row rows[e], weights
 // w[e][q] = sign(e) Z[u(e)][q]); for v on U, the entries are the U dofs of Gamma_f with
@@ -1114,6 +1132,33 @@ struct Runner {
 
     void set_attributes() {}
 
+    // forcing / back substitution on the bulk-copy pipeline (batched): the right-hand sides are
+    // staged once (k_stage_rows_x), then k_apply_tma in the row mode over its schedule
+    template <typename T, int MODE> void rows_tma(const OpPool<T> &pool, const double *xa, const double *xb, double *y) {
+        const int ctas = MODE == ROWS_FORCING ? p->fsched_ctas : p->osched_ctas;
+        if (ctas <= 0) return;
+        T *xs = ws.rxs.as<T>();
+        k_stage_rows_x<T, MODE><<<dim3(p->K, R), 256, 0, st>>>(xa, xb, sd, xs, R);
+        note_launch();
+        const CUtensorMap *om = (MODE == ROWS_FORCING ? pool.fmaps : pool.omaps).template as<CUtensorMap>();
+        const CUtensorMap *xm = ws.rxmaps[sizeof(T) == 8 ? 1 : 0].template as<CUtensorMap>();
+        const int32_t *sp = (MODE == ROWS_FORCING ? p->d_fsched_ptr : p->d_osched_ptr).template as<int32_t>();
+        const int32_t *si = (MODE == ROWS_FORCING ? p->d_fsched_items : p->d_osched_items).template as<int32_t>();
+        const int rc = R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1));
+        auto go = [&](auto rc_tag) {
+            constexpr int RCT = decltype(rc_tag)::value;
+            k_apply_tma<T, RCT, APPLY_NS, APPLY_MINB, T, MODE><<<ctas, APPLY_THREADS, apply_smem_bytes(RCT, APPLY_NS), st>>>(
+                om, xm, 0, sd, sp, si, y, R, nullptr, S.err, 1.0, xa);
+        };
+        switch (rc) {
+            case 8: go(std::integral_constant<int, 8>{}); break;
+            case 4: go(std::integral_constant<int, 4>{}); break;
+            case 2: go(std::integral_constant<int, 2>{}); break;
+            default: go(std::integral_constant<int, 1>{}); break;
+        }
+        note_launch();
+    }
+
     // the batched interface apply: persistent tensor-copy pipeline over the balanced schedule;
     // x is read through the workspace's tensor maps of xU
     // half: S_k from the FP16 copy (FP32 pool, use_sp = 0)
@@ -1482,9 +1527,11 @@ struct Runner {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         const double *f = ws.res.as<double>();
         const bool batched = p->opt.batched != 0;
-        if (nu > 0)
-            rows<T, ROWS_FORCING>(pool.M.template as<T>(), 0, nullptr, f, nullptr, ws.fU.as<double>(), p->d_items,
-                                  p->item_off);
+        if (nu > 0) {
+            if (batched && p->fsched_ctas > 0) rows_tma<T, ROWS_FORCING>(pool, f, nullptr, ws.fU.as<double>());
+            else rows<T, ROWS_FORCING>(pool.M.template as<T>(), 0, nullptr, f, nullptr, ws.fU.as<double>(), p->d_items,
+                                       p->item_off);
+        }
         double *lam = ws.dlam.as<double>();
         T *x = ws.xU.as<T>();
         if (nl > 0) {
@@ -1571,8 +1618,11 @@ struct Runner {
             note_launch();
             symv<T>(pool, 1, x, ws.uU.as<double>());
         }
-        rows<T, ROWS_BACKSUB>(pool.M.template as<T>(), 0, nullptr, f, ws.uU.as<double>(), ws.du.as<double>(),
-                              p->d_items_o, p->item_off_o);
+        if (batched && p->osched_ctas > 0)
+            rows_tma<T, ROWS_BACKSUB>(pool, f, ws.uU.as<double>(), ws.du.as<double>());
+        else
+            rows<T, ROWS_BACKSUB>(pool.M.template as<T>(), 0, nullptr, f, ws.uU.as<double>(), ws.du.as<double>(),
+                                  p->d_items_o, p->item_off_o);
         if (nu > 0) {
             k_scatter_u<<<grid_for(nu * R), 256, 0, st>>>(p->d_u2v.as<int64_t>(), ws.uU.as<double>(), ws.du.as<double>(),
                                                           nu, R);
@@ -1688,6 +1738,25 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
             }
             alloc(xmaps[e], sizeof(CUtensorMap) * maps.size());
             NLF_CUDA(cudaMemcpyAsync(xmaps[e].p, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                                     async_stream ? async_stream : c->stream));
+            NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
+        }
+        // the forcing / back-substitution right-hand sides (R rows of ld_M entries at offVp * R),
+        // read as FP32 and as FP64, tiles of rcb rows
+        alloc(rxs, sizeof(double) * std::max<int64_t>(1, p->n_vp) * R);
+        for (int e = 0; e < 2; ++e) {
+            const int es = e ? 8 : 4;
+            std::vector<CUtensorMap> rm(std::max(1, p->K));
+            std::memset(rm.data(), 0, sizeof(CUtensorMap) * rm.size());
+            for (int k = 0; k < p->K; ++k) {
+                const SubdomainDesc &d = p->sd[k];
+                if (d.nk == 0) continue;
+                const unsigned char *b = rxs.as<unsigned char>() + d.offVp * R * es;
+                if (encode_apply_map(encode_tiled(), &rm[k], b, d.ldM, R, es, rcb) != CUDA_SUCCESS)
+                    fail(NLFETI_E_CUDA, "cuTensorMapEncodeTiled failed for the forcing input");
+            }
+            alloc(rxmaps[e], sizeof(CUtensorMap) * rm.size());
+            NLF_CUDA(cudaMemcpyAsync(rxmaps[e].p, rm.data(), sizeof(CUtensorMap) * rm.size(), cudaMemcpyHostToDevice,
                                      async_stream ? async_stream : c->stream));
             NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
         }
@@ -1948,6 +2017,23 @@ int apply_tma_ctas() {
     fit(k_apply_tma<float, 1>, 1); fit(k_apply_tma<float, 2>, 2); fit(k_apply_tma<float, 4>, 4);
     fit(k_apply_tma<float, 8>, 8); fit(k_apply_tma<double, 1>, 1); fit(k_apply_tma<double, 2>, 2);
     fit(k_apply_tma<double, 4>, 4); fit(k_apply_tma<double, 8>, 8);
+    // the forcing and back-substitution modes (same pipeline and shared memory)
+    fit(k_apply_tma<float, 1, APPLY_NS, APPLY_MINB, float, ROWS_FORCING>, 1);
+    fit(k_apply_tma<float, 2, APPLY_NS, APPLY_MINB, float, ROWS_FORCING>, 2);
+    fit(k_apply_tma<float, 4, APPLY_NS, APPLY_MINB, float, ROWS_FORCING>, 4);
+    fit(k_apply_tma<float, 8, APPLY_NS, APPLY_MINB, float, ROWS_FORCING>, 8);
+    fit(k_apply_tma<float, 1, APPLY_NS, APPLY_MINB, float, ROWS_BACKSUB>, 1);
+    fit(k_apply_tma<float, 2, APPLY_NS, APPLY_MINB, float, ROWS_BACKSUB>, 2);
+    fit(k_apply_tma<float, 4, APPLY_NS, APPLY_MINB, float, ROWS_BACKSUB>, 4);
+    fit(k_apply_tma<float, 8, APPLY_NS, APPLY_MINB, float, ROWS_BACKSUB>, 8);
+    fit(k_apply_tma<double, 1, APPLY_NS, APPLY_MINB, double, ROWS_FORCING>, 1);
+    fit(k_apply_tma<double, 2, APPLY_NS, APPLY_MINB, double, ROWS_FORCING>, 2);
+    fit(k_apply_tma<double, 4, APPLY_NS, APPLY_MINB, double, ROWS_FORCING>, 4);
+    fit(k_apply_tma<double, 8, APPLY_NS, APPLY_MINB, double, ROWS_FORCING>, 8);
+    fit(k_apply_tma<double, 1, APPLY_NS, APPLY_MINB, double, ROWS_BACKSUB>, 1);
+    fit(k_apply_tma<double, 2, APPLY_NS, APPLY_MINB, double, ROWS_BACKSUB>, 2);
+    fit(k_apply_tma<double, 4, APPLY_NS, APPLY_MINB, double, ROWS_BACKSUB>, 4);
+    fit(k_apply_tma<double, 8, APPLY_NS, APPLY_MINB, double, ROWS_BACKSUB>, 8);
     auto fit_h = [&](auto kern, int rc) {
         const int smem = apply_smem_bytes(rc, APPLY_NS_H, APPLY_CB / 2);
         NLF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -2010,6 +2096,26 @@ template <typename T> void encode_apply_maps(nlfeti_problem *p, OpPool<T> &pool)
     }
     pool.maps.alloc(p->ctx, sizeof(CUtensorMap) * maps.size());
     NLF_CUDA(cudaMemcpyAsync(pool.maps.p, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                             p->ctx->stream));
+    // swept-matrix blocks of the forcing (rows n_O.., columns ..n_O) and of the back
+    // substitution (rows ..n_O, all columns)
+    std::vector<CUtensorMap> fm(std::max(1, p->K)), om(std::max(1, p->K));
+    std::memset(fm.data(), 0, sizeof(CUtensorMap) * fm.size());
+    std::memset(om.data(), 0, sizeof(CUtensorMap) * om.size());
+    for (int k = 0; k < p->K; ++k) {
+        const SubdomainDesc &d = p->sd[k];
+        if (d.nO == 0) continue;                      // nothing to stream
+        const T *m = pool.M.template as<T>() + d.offM;
+        if ((d.nG > 0 && encode_block_map(encode_tiled(), &fm[k], m + (int64_t)d.nO * d.ldM, d.nO, d.nG, d.ldM,
+                                          (int)sizeof(T)) != CUDA_SUCCESS) ||
+            encode_block_map(encode_tiled(), &om[k], m, d.nk, d.nO, d.ldM, (int)sizeof(T)) != CUDA_SUCCESS)
+            fail(NLFETI_E_CUDA, "cuTensorMapEncodeTiled failed for a swept-matrix block");
+    }
+    pool.fmaps.alloc(p->ctx, sizeof(CUtensorMap) * fm.size());
+    pool.omaps.alloc(p->ctx, sizeof(CUtensorMap) * om.size());
+    NLF_CUDA(cudaMemcpyAsync(pool.fmaps.p, fm.data(), sizeof(CUtensorMap) * fm.size(), cudaMemcpyHostToDevice,
+                             p->ctx->stream));
+    NLF_CUDA(cudaMemcpyAsync(pool.omaps.p, om.data(), sizeof(CUtensorMap) * om.size(), cudaMemcpyHostToDevice,
                              p->ctx->stream));
     if constexpr (std::is_same<T, float>::value) {
         // A^k as FP32 pairs (n_k rows of ld_M) for the refinement residual

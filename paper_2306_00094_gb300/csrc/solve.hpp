@@ -29,6 +29,9 @@ struct SolveWS {
     DevMem xhmaps;                                      // xU read as FP16 (tensor-core apply; R <= 64)
     DevMem xscale;                                      // per column: power of two x is scaled by (FP16 x)
     DevMem slot_flags;                                  // gates seen by the timed applies (profiling)
+    DevMem rxs;                                         // right-hand sides of the forcing / back substitution
+                                                        // (R columns of ld_M entries at offVp * R per subdomain)
+    DevMem rxmaps[2];                                   // tensor maps of rxs per subdomain (FP32, FP64)
     DevMem ftil, res, u, du;                            // concatenated subdomain vectors
     DevMem uhl;                                         // u as FP32 hi / lo pairs, padded layout
     DevMem umaps;                                       // tensor maps of uh and ul per subdomain
