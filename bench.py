@@ -128,7 +128,7 @@ def percentile(xs, q):
     return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
 
 
-def profile_traffic(kernel_src_hash, name="k_apply_tma_cfg2.md"):
+def profile_traffic(kernel_src_hash, name="k_apply_tma_const_l2_h128.md"):
     """DRAM bytes per launch of an apply kernel from the committed ncu summary, if it matches
     the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", name)
@@ -162,7 +162,7 @@ def run_ours(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
-    w = W.cfg2_const_l2()
+    w = W.const_l2_2d()
     R = w.nrhs
     ctx = binding.Context()
     t0 = time.perf_counter()
@@ -390,7 +390,7 @@ def run_ours(args):
                              "frac": (h_ach / hbm) if h_ach else None, "peak_source": peak_kind,
                              "bytes_per_launch": h_bpl, "avg_launch_us": h_avg * 1e6 if h_avg else None,
                              "launches": n_half, "share_of_step_time": h_share,
-                             "traffic": profile_traffic(kernel_source_hash(), "k_apply_tma_fp16_cfg2.md")},
+                             "traffic": profile_traffic(kernel_source_hash(), "k_apply_tma_fp16_const_l2_h128.md")},
         "precond_tensor_cores": tc_res,
         "gpu_launches": launches,
         "e2e": e2e,
@@ -456,7 +456,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = W.cfg2_const_l2()
+    w = W.const_l2_2d()
     fo = oracle_setup(w)
     for _ in range(min(args.warmup, 1)):
         fo.solve(w.rhs, w.rhs_kind)
@@ -524,11 +524,11 @@ def serving_pool(rng, size, budget_bytes, cost_cap):
 
 def serving_workload(cfg, nrhs):
     if cfg["kernel"] == "1d_const":
-        return W.cfg1_1d(N=cfg["N"], K=cfg["K"], delta=cfg["delta"], nrhs=nrhs)
+        return W.const_1d(N=cfg["N"], K=cfg["K"], delta=cfg["delta"], nrhs=nrhs)
     k = int(round(np.sqrt(cfg["K"])))
     if cfg["kernel"] == "2d_const_l2":
-        return W.cfg2_const_l2(N=cfg["N"], k=k, nrhs=nrhs, delta=cfg["delta"])
-    return W.cfg3_fractional(N=cfg["N"], k=k, nrhs=nrhs, delta=cfg["delta"])
+        return W.const_l2_2d(N=cfg["N"], k=k, nrhs=nrhs, delta=cfg["delta"])
+    return W.fractional_2d(N=cfg["N"], k=k, nrhs=nrhs, delta=cfg["delta"])
 
 
 def run_serving(args):

@@ -13,9 +13,11 @@
 // (N = NP, R rounded up to 16; rows past R of the x tile arrive as zeros).  The K loop streams
 // 64 columns per stage: the 128 x 64 tile of S_k, stored contiguously (16 KB) in the tiled
 // copy already in the 128-byte swizzled K-major order and loaded by one bulk copy (one
-// contiguous DRAM stream per stage instead of 128 rows of 128 bytes; on cfg2 both forms
-// measured the same), and the NP x 64 tile of x_k by a 2-D tensor copy with the same
-// swizzle; 8-row atoms of 1 KB, stage buffers 1 KB aligned, four MMAs of K = 16 per stage.  Rows and columns past the operator (n_gamma, ld_gamma) are zeros in the tiles.
+// contiguous DRAM stream per stage instead of 128 rows of 128 bytes; on the 2-D constant-kernel
+// workload with h = 1/128, 4 x 4 subdomains and 8 right-hand sides both forms measured the
+// same), and the NP x 64 tile of x_k by a 2-D tensor copy with the same swizzle; 8-row atoms
+// of 1 KB, stage buffers 1 KB aligned, four MMAs of K = 16 per stage.  Rows and columns past
+// the operator (n_gamma, ld_gamma) are zeros in the tiles.
 //
 // Persistent CTAs of six warps over a host-built schedule of items (longest first onto the
 // least loaded CTA):
@@ -49,7 +51,7 @@ __host__ __device__ constexpr int mma_stage_bytes(int np) { return MMA_A_BYTES +
 __host__ __device__ constexpr int mma_smem_bytes(int np) { return mma_ns(np) * mma_stage_bytes(np) + 1024; }
 // MMA_ACC accumulators per item (the k-th MMA of every stage adds into accumulator k), so
 // that no chain of dependent accumulations into one tile can set the pace of the small
-// 128 x 16 x 16 MMAs (on cfg2 one accumulator measured the same: the copies set it)
+// 128 x 16 x 16 MMAs (on that workload one accumulator measured the same: the copies set it)
 constexpr int MMA_ACC = 4;
 __host__ __device__ constexpr int mma_tmem_cols(int np) {
     return MMA_ACC * np <= 32 ? 32 : (MMA_ACC * np <= 64 ? 64 : (MMA_ACC * np <= 128 ? 128 : 256));

@@ -19,15 +19,15 @@ from oracle import problem as oprob
 pytestmark = pytest.mark.gpu
 
 CASES = {
-    "1d_k4": lambda: W.cfg1_1d(N=200, K=4, nrhs=2),
-    "l2_3x3": lambda: W.cfg2_const_l2(N=24, k=3, nrhs=3, delta=0.1),
-    "frac_deg": lambda: W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.25),
-    "pd_3x3_jit": lambda: W.cfg4_peridynamic(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2),
-    "k1": lambda: W.cfg2_const_l2(N=16, k=1, nrhs=2),
+    "1d_k4": lambda: W.const_1d(N=200, K=4, nrhs=2),
+    "l2_3x3": lambda: W.const_l2_2d(N=24, k=3, nrhs=3, delta=0.1),
+    "frac_deg": lambda: W.fractional_2d(N=24, k=3, nrhs=2, delta=0.25),
+    "pd_3x3_jit": lambda: W.peridynamic_2d(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2),
+    "k1": lambda: W.const_l2_2d(N=16, k=1, nrhs=2),
     "l2_unstructured": lambda: W.unstructured_l2(N=24, K=5, nrhs=2),
     "l2_neumann": lambda: W.neumann_l2(N=24, k=3, nrhs=2),
     "l2_rounded_collar": lambda: W.l2_collar_const(N=24, k=3, nrhs=2, delta=0.15),
-    "frac_approxcaps": lambda: _approxcaps(W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.1)),
+    "frac_approxcaps": lambda: _approxcaps(W.fractional_2d(N=24, k=3, nrhs=2, delta=0.1)),
 }
 
 

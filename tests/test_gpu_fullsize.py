@@ -20,10 +20,10 @@ from oracle import problem as oprob
 pytestmark = pytest.mark.gpu
 
 FULL = {
-    "cfg1": lambda: W.cfg1_1d(),
-    "cfg2": lambda: W.cfg2_const_l2(),
-    "cfg3": lambda: W.cfg3_fractional(nrhs=11),
-    "cfg4": lambda: W.cfg4_peridynamic(nrhs=1),
+    "const_1d": lambda: W.const_1d(),
+    "const_l2_2d": lambda: W.const_l2_2d(),
+    "fractional_2d": lambda: W.fractional_2d(nrhs=11),
+    "peridynamic_2d": lambda: W.peridynamic_2d(nrhs=1),
 }
 
 

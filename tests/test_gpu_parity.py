@@ -24,21 +24,21 @@ from oracle import problem as oprob
 pytestmark = pytest.mark.gpu
 
 CASES = {
-    "1d_k4": lambda: W.cfg1_1d(N=200, K=4, nrhs=2),
-    "l2_3x3": lambda: W.cfg2_const_l2(N=24, k=3, nrhs=3, delta=0.1),
+    "1d_k4": lambda: W.const_1d(N=200, K=4, nrhs=2),
+    "l2_3x3": lambda: W.const_l2_2d(N=24, k=3, nrhs=3, delta=0.1),
     "linf_2x2": lambda: W.Workload("linf", *_linf(20, 2)),
-    "frac_3x3": lambda: W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.1),
-    "frac_deg": lambda: W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.25),
-    "pd_3x3_jit": lambda: W.cfg4_peridynamic(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2),
-    "k1": lambda: W.cfg2_const_l2(N=16, k=1, nrhs=2),
+    "frac_3x3": lambda: W.fractional_2d(N=24, k=3, nrhs=2, delta=0.1),
+    "frac_deg": lambda: W.fractional_2d(N=24, k=3, nrhs=2, delta=0.25),
+    "pd_3x3_jit": lambda: W.peridynamic_2d(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2),
+    "k1": lambda: W.const_l2_2d(N=16, k=1, nrhs=2),
     "l2_unstructured": lambda: W.unstructured_l2(N=24, K=5, nrhs=2),
     "pd_unstructured": lambda: W.unstructured_pd(N=24, K=4, nrhs=2),
-    "l2_ball_barycenter": lambda: _ball(W.cfg2_const_l2(N=24, k=3, nrhs=2, delta=0.1), 1),
-    "frac_ball_123v": lambda: _ball(W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.1), 2),
-    "pd_ball_23v": lambda: _ball(W.cfg4_peridynamic(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2), 3),
-    "l2_approxcaps": lambda: _ball(W.cfg2_const_l2(N=24, k=3, nrhs=2, delta=0.1), 4),
-    "frac_approxcaps": lambda: _ball(W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.1), 4),
-    "pd_approxcaps": lambda: _ball(W.cfg4_peridynamic(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2), 4),
+    "l2_ball_barycenter": lambda: _ball(W.const_l2_2d(N=24, k=3, nrhs=2, delta=0.1), 1),
+    "frac_ball_123v": lambda: _ball(W.fractional_2d(N=24, k=3, nrhs=2, delta=0.1), 2),
+    "pd_ball_23v": lambda: _ball(W.peridynamic_2d(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2), 3),
+    "l2_approxcaps": lambda: _ball(W.const_l2_2d(N=24, k=3, nrhs=2, delta=0.1), 4),
+    "frac_approxcaps": lambda: _ball(W.fractional_2d(N=24, k=3, nrhs=2, delta=0.1), 4),
+    "pd_approxcaps": lambda: _ball(W.peridynamic_2d(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2), 4),
     "l2_unstructured_approxcaps": lambda: _ball(W.unstructured_l2(N=24, K=5, nrhs=2), 4),
     "l2_neumann": lambda: W.neumann_l2(N=24, k=3, nrhs=2),
     "pd_neumann": lambda: W.neumann_pd(N=30, k=3, nrhs=2),
@@ -155,7 +155,7 @@ def test_quadratic_closed_form_1d_on_gpu(ctx):
 
 def test_approxcaps_rejects_short_horizon(ctx):
     from paper_2306_00094_gb300 import binding
-    w = _ball(W.cfg2_const_l2(N=24, k=2, nrhs=1, delta=0.02), 4)     # 2 delta < the diagonal h sqrt(2)
+    w = _ball(W.const_l2_2d(N=24, k=2, nrhs=1, delta=0.02), 4)     # 2 delta < the diagonal h sqrt(2)
     with pytest.raises(binding.NlfetiError) as e:
         binding.Problem.from_workload(ctx, w)
     assert e.value.status == binding.E_INVALID

@@ -26,9 +26,9 @@ from oracle import feti as ofeti
 pytestmark = pytest.mark.gpu
 
 CASES = {
-    "l2_3x3": lambda: W.cfg2_const_l2(N=24, k=3, nrhs=1, delta=0.1),
-    "l2_2x2_big": lambda: W.cfg2_const_l2(N=64, k=2, nrhs=1, delta=0.1),
-    "pd_3x3": lambda: W.cfg4_peridynamic(N=30, k=3, nrhs=1, delta_cells=3, jitter=0.2),
+    "l2_3x3": lambda: W.const_l2_2d(N=24, k=3, nrhs=1, delta=0.1),
+    "l2_2x2_big": lambda: W.const_l2_2d(N=64, k=2, nrhs=1, delta=0.1),
+    "pd_3x3": lambda: W.peridynamic_2d(N=30, k=3, nrhs=1, delta_cells=3, jitter=0.2),
     "l2_unstructured": lambda: W.unstructured_l2(N=32, K=5, nrhs=1),
 }
 

@@ -14,8 +14,8 @@ pytestmark = pytest.mark.gpu
 def setup():
     from paper_2306_00094_gb300 import binding
     ctx = binding.Context()
-    work = [W.cfg1_1d(N=300, K=4, nrhs=3), W.cfg2_const_l2(N=32, k=4, nrhs=5, delta=0.1),
-            W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.1), W.cfg4_peridynamic(N=24, k=3, nrhs=1, jitter=0.2)]
+    work = [W.const_1d(N=300, K=4, nrhs=3), W.const_l2_2d(N=32, k=4, nrhs=5, delta=0.1),
+            W.fractional_2d(N=24, k=3, nrhs=2, delta=0.1), W.peridynamic_2d(N=24, k=3, nrhs=1, jitter=0.2)]
     probs = []
     for w in work:
         p = binding.Problem.from_workload(ctx, w)

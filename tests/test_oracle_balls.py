@@ -90,7 +90,7 @@ def test_local_limit_on_quadratics(ball):
 
 @pytest.mark.parametrize("ball", list(BALLS))
 def test_feti_equals_single_domain(ball):
-    w = W.cfg2_const_l2(N=16, k=3, nrhs=2, delta=0.15)
+    w = W.const_l2_2d(N=16, k=3, nrhs=2, delta=0.15)
     w.kernel.ball = BALLS[ball]
     ref = problem.Monolithic(w.mesh, w.kernel).solve(w.rhs, w.rhs_kind)
     u, _ = feti.Feti(w.mesh, w.kernel, w.labels, w.K).solve(w.rhs, w.rhs_kind)

@@ -23,11 +23,11 @@ from oracle import assembly, feti, problem
 from oracle.decomposition import build_decomposition
 
 CASES = {
-    "1d_k4": lambda: W.cfg1_1d(N=120, K=4, nrhs=2),
-    "l2_3x3": lambda: W.cfg2_const_l2(N=24, k=3, nrhs=2, delta=0.1),
-    "frac_3x3": lambda: W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.1),
-    "frac_deg": lambda: W.cfg3_fractional(N=24, k=3, nrhs=2, delta=0.25),   # Omega_k empty
-    "pd_3x3_jit": lambda: W.cfg4_peridynamic(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2),
+    "1d_k4": lambda: W.const_1d(N=120, K=4, nrhs=2),
+    "l2_3x3": lambda: W.const_l2_2d(N=24, k=3, nrhs=2, delta=0.1),
+    "frac_3x3": lambda: W.fractional_2d(N=24, k=3, nrhs=2, delta=0.1),
+    "frac_deg": lambda: W.fractional_2d(N=24, k=3, nrhs=2, delta=0.25),   # Omega_k empty
+    "pd_3x3_jit": lambda: W.peridynamic_2d(N=30, k=3, nrhs=2, delta_cells=3, jitter=0.2),
     "l2_unstructured": lambda: W.unstructured_l2(N=20, K=5, nrhs=2),      # irregular mesh, graph parts
     "pd_unstructured": lambda: W.unstructured_pd(N=20, K=4, nrhs=2),
     "l2_neumann": lambda: W.neumann_l2(N=20, k=3, nrhs=2),                # Neumann region on two sides
@@ -166,7 +166,7 @@ def test_feti_equals_monolithic(built, name):
 
 
 def test_single_subdomain_is_monolithic():
-    w = W.cfg2_const_l2(N=16, k=1, nrhs=2)
+    w = W.const_l2_2d(N=16, k=1, nrhs=2)
     f = feti.Feti(w.mesh, w.kernel, w.labels, w.K)
     assert f.dec.n_lambda == 0 and not f.dec.floating.any()
     mono = problem.Monolithic(w.mesh, w.kernel)

@@ -29,7 +29,7 @@ def _rows_free(mesh, kern):
 
 @pytest.mark.parametrize("N", [200, 250])
 def test_1d_quadratic_row_identity(N):
-    w = W.cfg1_1d(N=N, K=2)
+    w = W.const_1d(N=N, K=2)
     dofs, rows = _rows_free(w.mesh, w.kernel)
     x = w.mesh.xy[:, 0]
     h = 1.0 / N
@@ -135,9 +135,9 @@ def test_peridynamic_constant_navier_limit():
     assert abs(r[0] / (-0.5 * np.pi) - 1) < 0.01 and abs(r[1]) < 0.01
 
 
-@pytest.mark.parametrize("maker", [lambda: W.cfg2_const_l2(N=16, k=2, nrhs=1),
-                                   lambda: W.cfg3_fractional(N=12, k=2, nrhs=1),
-                                   lambda: W.cfg4_peridynamic(N=16, k=2, nrhs=1, jitter=0.0)])
+@pytest.mark.parametrize("maker", [lambda: W.const_l2_2d(N=16, k=2, nrhs=1),
+                                   lambda: W.fractional_2d(N=12, k=2, nrhs=1),
+                                   lambda: W.peridynamic_2d(N=16, k=2, nrhs=1, jitter=0.0)])
 def test_symmetric_positive_definite(maker):
     w = maker()
     mono = problem.Monolithic(w.mesh, w.kernel, dense=True)

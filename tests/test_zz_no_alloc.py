@@ -18,7 +18,7 @@ def setup():
     torch = pytest.importorskip("torch")
     from paper_2306_00094_gb300 import binding
     ctx = binding.Context()
-    w = W.cfg2_const_l2(N=24, k=3, nrhs=3, delta=0.1)
+    w = W.const_l2_2d(N=24, k=3, nrhs=3, delta=0.1)
     p = binding.Problem.from_workload(ctx, w)
     p.factor(3)
     yield torch, binding, p

@@ -412,7 +412,7 @@ def default_scale(kernel: Kernel, dim: int) -> float:
 # size and at reduced sizes that keep the same structure for fast parity runs.
 # --------------------------------------------------------------------------------------
 
-def cfg1_1d(N: int = 1000, K: int = 4, seed: int = 1, delta: float = 0.1, nrhs: int = 1) -> Workload:
+def const_1d(N: int = 1000, K: int = 4, seed: int = 1, delta: float = 0.1, nrhs: int = 1) -> Workload:
     """1-D constant kernel 3/delta^3 on |x-y|<delta, h=1/N, K equal subdomains, nodal f=-2+U(-0.1,0.1)."""
     m = collar_cells(delta, N)
     mesh = make_mesh(1, N, m)
@@ -421,11 +421,11 @@ def cfg1_1d(N: int = 1000, K: int = 4, seed: int = 1, delta: float = 0.1, nrhs: 
     labels = rect_labels(mesh, K)
     rng = np.random.default_rng(seed)
     f = -2.0 + rng.uniform(-0.1, 0.1, size=(mesh.n_nodes, nrhs))
-    return Workload("cfg1_1d_const", mesh, kern, labels, K, np.asfortranarray(f), 0,
+    return Workload("1d_const", mesh, kern, labels, K, np.asfortranarray(f), 0,
                     meta=dict(N=N, delta=delta, kx=K, ky=1))
 
 
-def cfg2_const_l2(N: int = 128, k: int = 4, nrhs: int = 8, seed: int = 2, delta: float = 0.1) -> Workload:
+def const_l2_2d(N: int = 128, k: int = 4, nrhs: int = 8, seed: int = 2, delta: float = 0.1) -> Workload:
     """2-D constant kernel 4/(pi delta^4) on the l2 ball (nocaps), h=1/N, k x k subdomains, N(0,1) loads."""
     m = collar_cells(delta, N)
     mesh = make_mesh(2, N, m)
@@ -433,11 +433,11 @@ def cfg2_const_l2(N: int = 128, k: int = 4, nrhs: int = 8, seed: int = 2, delta:
     kern.scale = default_scale(kern, 2)
     labels = rect_labels(mesh, k, k)
     rhs = nodal_loads(mesh, 1, nrhs, seed, "normal")
-    return Workload("cfg2_2d_const_l2", mesh, kern, labels, k * k, rhs, 1,
+    return Workload("2d_const_l2", mesh, kern, labels, k * k, rhs, 1,
                     meta=dict(N=N, delta=delta, kx=k, ky=k))
 
 
-def cfg3_fractional(N: int = 96, k: int = 6, nrhs: int = 64, seed: int = 3, delta: float = 0.2,
+def fractional_2d(N: int = 96, k: int = 6, nrhs: int = 64, seed: int = 3, delta: float = 0.2,
                     s: float = 0.5) -> Workload:
     """2-D fractional-type kernel (2-2s)/(pi delta^(2-2s)) |x-y|^-(2+2s), s=0.5, delta=0.2, h=1/N, k x k."""
     m = collar_cells(delta, N)
@@ -446,11 +446,11 @@ def cfg3_fractional(N: int = 96, k: int = 6, nrhs: int = 64, seed: int = 3, delt
     kern.scale = default_scale(kern, 2)
     labels = rect_labels(mesh, k, k)
     rhs = nodal_loads(mesh, 1, nrhs, seed, "normal")
-    return Workload("cfg3_2d_fractional", mesh, kern, labels, k * k, rhs, 1,
+    return Workload("2d_fractional", mesh, kern, labels, k * k, rhs, 1,
                     meta=dict(N=N, delta=delta, kx=k, ky=k, s=s))
 
 
-def cfg4_peridynamic(N: int = 256, k: int = 8, nrhs: int = 16, seed_cuts: int = 4, seed_rhs: int = 5,
+def peridynamic_2d(N: int = 256, k: int = 8, nrhs: int = 16, seed_cuts: int = 4, seed_rhs: int = 5,
                      delta_cells: int = 3, jitter: float = 0.2) -> Workload:
     """2-D bond-based peridynamics 3/delta^3 xi xi^T/|xi|^3, delta=3h, h=1/N, k x k jittered cuts."""
     delta = delta_cells / N
@@ -460,24 +460,24 @@ def cfg4_peridynamic(N: int = 256, k: int = 8, nrhs: int = 16, seed_cuts: int = 
     kern.scale = default_scale(kern, 2)
     labels = rect_labels(mesh, k, k, jitter=jitter, seed=seed_cuts)
     rhs = nodal_loads(mesh, 2, nrhs, seed_rhs, "normal")
-    return Workload("cfg4_2d_peridynamic", mesh, kern, labels, k * k, rhs, 1,
+    return Workload("2d_peridynamic", mesh, kern, labels, k * k, rhs, 1,
                     meta=dict(N=N, delta=delta, kx=k, ky=k, jitter=jitter))
 
 
 def manufactured_1d_quadratic(N: int = 1000, K: int = 4, delta: float = 0.1) -> Workload:
     """1-D closed-form case: c=3/delta^3, nodal f=-2, g = x^2/2 on the collar; the discrete
     solution is x^2/2 at every node (uniform mesh, delta/h integer)."""
-    w = cfg1_1d(N=N, K=K, delta=delta)
+    w = const_1d(N=N, K=K, delta=delta)
     x = w.mesh.xy[:, 0]
     w.rhs = np.asfortranarray(np.full((w.mesh.n_nodes, 1), -2.0))
     w.g = np.asfortranarray((0.5 * x * x).reshape(-1, 1))
-    w.name = "cfg1_1d_quadratic"
+    w.name = "1d_quadratic"
     return w
 
 
 WORKLOADS = {
-    "cfg1": cfg1_1d,
-    "cfg2": cfg2_const_l2,
-    "cfg3": cfg3_fractional,
-    "cfg4": cfg4_peridynamic,
+    "const_1d": const_1d,
+    "const_l2_2d": const_l2_2d,
+    "fractional_2d": fractional_2d,
+    "peridynamic_2d": peridynamic_2d,
 }
