@@ -159,3 +159,21 @@ def test_approxcaps_rejects_short_horizon(ctx):
     with pytest.raises(binding.NlfetiError) as e:
         binding.Problem.from_workload(ctx, w)
     assert e.value.status == binding.E_INVALID
+
+
+def test_empty_and_invalid_requests_rejected(ctx):
+    """Zero right-hand sides and an unknown load kind are refused with NLFETI_E_INVALID by the
+    FETI solve, the CG solve and the operator apply; the problem stays usable afterwards."""
+    from paper_2306_00094_gb300 import binding
+    w = W.const_l2_2d(N=16, k=2, nrhs=1)
+    p = binding.Problem.from_workload(ctx, w)
+    p.factor(3)
+    empty = np.zeros((w.rhs.shape[0], 0), order="F")
+    for call in (lambda: p.solve(empty, w.rhs_kind), lambda: p.solve(w.rhs, 2),
+                 lambda: p.solve_cg(empty, w.rhs_kind), lambda: p.apply(0, 0, np.zeros((p.info()["n_lambda"], 0)))):
+        with pytest.raises(binding.NlfetiError) as e:
+            call()
+        assert e.value.status == binding.E_INVALID
+    u, st = p.solve(w.rhs, w.rhs_kind)
+    assert np.isfinite(u).all() and st["iterations"] > 0
+    p.close()
