@@ -18,7 +18,7 @@
  * nlfeti_create (or cudaMalloc/cudaFree when they are NULL).
  *
  * Threads: a context and its problems are not thread-safe; a server is (one
- * submit/wait mutex, one worker thread).
+ * submit/wait mutex; its slots are worker threads with their own streams).
  */
 #ifndef NLFETI_H
 #define NLFETI_H
@@ -113,7 +113,13 @@ typedef struct {
  *          refinement).  1 = on the FP32 pipes (x in FP32; the default); 2 = on the tensor
  *          cores (x in FP16, scaled per column by a power of two from its norm; FP32
  *          accumulation) for at most 64 right-hand sides, else as 1; 0 = the FP32 S_k.
- *          nlfeti_apply ops 0-4 always use the FP32 S_k. */
+ *          nlfeti_apply ops 0-4 always use the FP32 S_k.
+ * factor_tc (FP32 operators): 1 = the rank-64 updates of the factorization sweeps run on the
+ *          tensor cores (tcgen05 kind::tf32, each FP32 panel entry split into three TF32 terms);
+ *          0 = on the FP32 pipes (the default).  The tensor cores accumulate with truncation, so
+ *          their FP32 operators carry a few times the rounding error of the FP32-pipe ones, which
+ *          can cost the mixed path's refinement an extra sweep; both meet the same tolerances.
+ *          Read by nlfeti_factor. */
 typedef struct {
     int precision;
     double tol;
@@ -125,6 +131,7 @@ typedef struct {
     size_t hbm_budget;
     int graph_loop;
     int precond_fp16;
+    int factor_tc;
 } nlfeti_options;
 
 typedef struct {
@@ -211,6 +218,53 @@ nlfeti_status nlfeti_solve_cg_device(nlfeti_problem *p, int nrhs, int rhs_kind, 
 nlfeti_status nlfeti_get_decomposition(const nlfeti_problem *p, int32_t *n_k, int32_t *n_gamma, int32_t *node_lists,
                                        int64_t *B_plus, int64_t *B_minus, int8_t *floating);
 
+/* Replace the assembled matrix A^k of subdomain k (n_k x n_k, row-major FP64 host array in
+ * the subdomain's dof order, Omega_k dofs first, as nlfeti_get_operator which 0 returns) with
+ * the caller's own, e.g. a matrix assembled by other quadrature (eq. bilinear-multi1 defines
+ * what it stands for; the Dirichlet coupling and the loads are unchanged).  Copied before the
+ * call returns.  The factorizations and the single-domain CG matrix of the problem are
+ * dropped: nlfeti_factor must run again before the next solve (solves return
+ * NLFETI_E_INVALID until then).  A matrix whose Omega block or pinned Neumann block is not
+ * positive definite makes that nlfeti_factor return NLFETI_E_NOT_SPD, after which the problem
+ * stays usable (set a valid matrix and factor again).  NLFETI_E_INVALID for k out of range or
+ * a non-finite entry. */
+nlfeti_status nlfeti_problem_set_matrix(nlfeti_problem *p, int k, const double *A);
+
+/* Autotuner of the batched interface apply (the persistent bulk-copy pipeline that applies
+ * S_k^+ and S_k in every PCG iteration; the paper has no counterpart, its subdomain solves run
+ * on CPUs).  Its shape for nrhs right-hand sides: rc, the right-hand sides per streamed pass
+ * over the operator (1, 2, 4, 8 or 16, at most nrhs; 8 for FP64: fewer passes read the operator
+ * fewer times but hold more accumulators), and ctas_per_sm (1 or 2) of its persistent grid.
+ * nlfeti_autotune times every candidate with CUDA events on the problem's factored operators
+ * for each operator kind it has -- 0 FP32 S_k^+ and S_k, 1 the FP16 copy of S_k the mixed
+ * path's preconditioner applies, 2 FP64 -- and keeps the fastest in the problem: later solves
+ * and applies with nrhs right-hand sides use it.  cache_path (nullable): a JSON file of earlier
+ * choices keyed by the device, the subdomain operator shapes, the kind and nrhs; a choice found
+ * there is used without timing (from_cache = 1), new ones are added (the file is rewritten).
+ * out: up to 3 entries (one per kind), *n_out their number.  Every shape gives bitwise the same
+ * results (each column is summed in the same order whatever the pass width and schedule).
+ * nlfeti_set_apply_choice pins a shape (rc 0 clears it, back to the default: the widest block
+ * up to nrhs, two CTAs per SM); NLFETI_E_INVALID for shapes outside the lists above. */
+typedef struct {
+    int32_t kind, nrhs, rc, ctas_per_sm;
+    double us;              /* mean time per apply launch of the chosen shape */
+    int32_t from_cache;
+} nlfeti_tune_entry;
+nlfeti_status nlfeti_autotune(nlfeti_problem *p, int nrhs, const char *cache_path, nlfeti_tune_entry *out,
+                              int *n_out);
+nlfeti_status nlfeti_set_apply_choice(nlfeti_problem *p, int kind, int nrhs, int rc, int ctas_per_sm);
+
+/* Fault injection for tests of the bounded device waits (not for production use; the paper has
+ * no counterpart).  The batched interface apply (a persistent bulk-copy pipeline) bounds every
+ * mbarrier wait: a wait that runs out sets the workspace's error word, the CTA lets the copies
+ * it issued land and returns, and the solve returns NLFETI_E_TIMEOUT with the context usable.
+ * wait_tries: polls of a stage barrier before the apply's consumers give up (0 = the default,
+ * 2^24 polls, seconds); withhold_copies = 1: the apply's producer issues no copies, so that the
+ * consumers' first wait runs out with nothing in flight.  Applies to the solves that follow
+ * (the batched path; the per-subdomain baseline has no waits).  NLFETI_E_INVALID for negative
+ * tries or withhold_copies outside 0/1. */
+nlfeti_status nlfeti_debug_apply_waits(nlfeti_problem *p, long long wait_tries, int withhold_copies);
+
 /* Copy one subdomain operator to the host (row-major, FP64):
  * which 0 = assembled A^k (n_k x n_k), 1 = S_k (n_g x n_g), 2 = S_k^+ (n_g x n_g);
  * precision 0 = FP64 operators, 1 = FP32 operators (widened). */
@@ -239,7 +293,8 @@ nlfeti_status nlfeti_apply(nlfeti_problem *p, int op, int precision, int nrhs, c
  * device share that scratch: calls that can overlap in time (other threads, other streams)
  * race, so the caller serialises them.  Nothing in it has to start at zero.  The first call
  * on a device resolves the scratch address with that device current (once); a caller that
- * captures streams makes that first call before capturing.  Asynchronous on the context
+ * captures streams makes that first call before capturing.  The call must be made with the
+ * device of the problem's context current (NLFETI_E_INVALID otherwise).  Asynchronous on the context
  * stream, ordered after the caller's stream and before its later work (as
  * nlfeti_solve_device). */
 #define NLFETI_NOALLOC_SCRATCH_BYTES (8u << 20)
@@ -266,13 +321,50 @@ typedef struct {
 nlfeti_status nlfeti_set_profiling(nlfeti_problem *p, int on);
 nlfeti_status nlfeti_get_profile(nlfeti_problem *p, nlfeti_profile *out);
 
-/* Continuous-batching server (one worker thread, its own streams).  Requests
- * that arrive while others run are admitted between PCG iterations as slots and
- * the HBM budget allow; their work shares the batched launches. */
+/* Serving (the paper's setup amortized over repeated solves, Sec. 6.4): a server takes solve
+ * requests as they arrive and runs them on max_slots slots, each a worker thread with its own
+ * CUDA stream, so the kernels of the batches in flight overlap on the device.  Continuous
+ * batching: when a slot starts the oldest admissible request it also takes the other queued
+ * requests on the same problem with the same rhs_kind (up to 64 right-hand sides in all) and
+ * runs them as one batched solve whose launches serve all of them; a request that arrives while
+ * a batch of its problem runs joins the next one.  Every column of a batched solve is computed
+ * in an order that does not depend on the other columns, so each request's result is bitwise
+ * the one it gets alone.  Right-hand-side counts are rounded up to buckets (zero columns) so
+ * that workspaces and their captured PCG loops are reused.
+ * Admission by device footprint: the server counts the bytes it holds -- its solve workspaces
+ * (in use or kept for reuse) and the problems it created for nlfeti_submit_mesh requests --
+ * against hbm_budget (0 = no limit), evicting idle ones least recently used first; a batch
+ * that does not fit waits.  Problems created by the caller (nlfeti_submit) are the caller's
+ * memory and are not counted.  The caller must not use the context or the problems passed to
+ * nlfeti_submit from other threads while the server runs requests on them.
+ * nlfeti_submit: a request on a factored problem (copies rhs and g: n_dofs x nrhs, column-major;
+ * 1 <= nrhs <= 64); NLFETI_E_NOMEM when the request alone exceeds the budget.
+ * nlfeti_submit_mesh: a request on the problem given by its inputs (as nlfeti_problem_create,
+ * with the options opt or the defaults; all copied): factorization cache keyed by a hash of
+ * the mesh, kernel, decomposition and options -- the first request of a key creates, assembles
+ * and factors the problem (stats ms_setup / ms_factor), later ones reuse it while it stays
+ * cached; invalid inputs fail the request with NLFETI_E_INVALID at nlfeti_wait.
+ * nlfeti_wait: the result (u_out as nlfeti_solve) and stats (ms_queue: submission to start,
+ * ms_solve: start to result); NLFETI_E_TIMEOUT if not done within timeout_ms (< 0: no limit),
+ * the request stays pending.  Submission never blocks on the GPU. */
 nlfeti_status nlfeti_server_create(nlfeti_ctx *ctx, size_t hbm_budget, int max_slots, nlfeti_server **out);
 nlfeti_status nlfeti_submit(nlfeti_server *s, nlfeti_problem *p, int nrhs, int rhs_kind, const double *rhs,
                             const double *g, nlfeti_ticket *out);
+nlfeti_status nlfeti_submit_mesh(nlfeti_server *s, const nlfeti_mesh *mesh, const nlfeti_kernel *kernel,
+                                 const nlfeti_decomp *decomp, const nlfeti_options *opt, int nrhs, int rhs_kind,
+                                 const double *rhs, const double *g, nlfeti_ticket *out);
 nlfeti_status nlfeti_wait(nlfeti_server *s, nlfeti_ticket t, int timeout_ms, double *u_out, nlfeti_stats *stats);
+
+/* Server counters: finished requests, batches run, requests that ran in a batch with others,
+ * factorization-cache hits / misses / evictions and problems cached, the most slots busy at
+ * once, requests queued, and the device bytes the server holds now and at most so far. */
+typedef struct {
+    int64_t requests_done, batches, merged_requests;
+    int64_t problem_hits, problem_misses, problems_evicted;
+    int32_t problems_cached, peak_active, queued;
+    size_t bytes_in_use, peak_bytes;
+} nlfeti_server_info;
+nlfeti_status nlfeti_server_get_info(nlfeti_server *s, nlfeti_server_info *out);
 void nlfeti_server_destroy(nlfeti_server *s);
 
 #ifdef __cplusplus

@@ -25,7 +25,9 @@ EXPORTED = ["nlfeti_default_options", "nlfeti_create", "nlfeti_destroy", "nlfeti
             "nlfeti_solve", "nlfeti_solve_device", "nlfeti_get_decomposition", "nlfeti_get_operator",
             "nlfeti_apply", "nlfeti_set_profiling", "nlfeti_get_profile", "nlfeti_server_create", "nlfeti_submit",
             "nlfeti_wait", "nlfeti_server_destroy", "nlfeti_apply_schur_noalloc", "nlfeti_cg_prepare",
-            "nlfeti_solve_cg", "nlfeti_solve_cg_device"]
+            "nlfeti_solve_cg", "nlfeti_solve_cg_device", "nlfeti_problem_set_matrix",
+            "nlfeti_debug_apply_waits", "nlfeti_submit_mesh", "nlfeti_server_get_info",
+            "nlfeti_autotune", "nlfeti_set_apply_choice"]
 
 
 class NlfetiError(RuntimeError):
@@ -38,7 +40,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_it", C.c_int), ("max_refine", C.c_int),
                 ("inner_tol", C.c_double), ("refine_tol", C.c_double), ("batched", C.c_int),
                 ("hbm_budget", C.c_size_t), ("graph_loop", C.c_int),
-                ("precond_fp16", C.c_int)]
+                ("precond_fp16", C.c_int), ("factor_tc", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -60,6 +62,18 @@ class Profile(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("apply_launches", C.c_int64), ("apply_ms", C.c_double),
                 ("apply_bytes", C.c_double), ("half_apply_launches", C.c_int64), ("half_apply_ms", C.c_double),
                 ("half_apply_bytes", C.c_double)]
+
+
+class ServerInfo(C.Structure):
+    _fields_ = [("requests_done", C.c_int64), ("batches", C.c_int64), ("merged_requests", C.c_int64),
+                ("problem_hits", C.c_int64), ("problem_misses", C.c_int64), ("problems_evicted", C.c_int64),
+                ("problems_cached", C.c_int32), ("peak_active", C.c_int32), ("queued", C.c_int32),
+                ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t)]
+
+
+class TuneEntry(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("nrhs", C.c_int32), ("rc", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("us", C.c_double), ("from_cache", C.c_int32)]
 
 
 class Mesh(C.Structure):
@@ -112,6 +126,10 @@ def load(build_if_missing: bool = True):
         "nlfeti_solve_cg_device": (i32, [vp, i32, i32, vp, vp, vp, C.POINTER(Stats)]),
         "nlfeti_get_decomposition": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "nlfeti_get_operator": (i32, [vp, i32, i32, i32, vp]),
+        "nlfeti_problem_set_matrix": (i32, [vp, i32, vp]),
+        "nlfeti_debug_apply_waits": (i32, [vp, C.c_longlong, i32]),
+        "nlfeti_autotune": (i32, [vp, i32, C.c_char_p, C.POINTER(TuneEntry), C.POINTER(C.c_int)]),
+        "nlfeti_set_apply_choice": (i32, [vp, i32, i32, i32, i32]),
         "nlfeti_apply": (i32, [vp, i32, i32, i32, vp, vp]),
         "nlfeti_set_profiling": (i32, [vp, i32]),
         "nlfeti_get_profile": (i32, [vp, C.POINTER(Profile)]),
@@ -119,6 +137,9 @@ def load(build_if_missing: bool = True):
         "nlfeti_submit": (i32, [vp, vp, i32, i32, vp, vp, C.POINTER(C.c_uint64)]),
         "nlfeti_wait": (i32, [vp, C.c_uint64, i32, vp, C.POINTER(Stats)]),
         "nlfeti_server_destroy": (None, [vp]),
+        "nlfeti_submit_mesh": (i32, [vp, C.POINTER(Mesh), C.POINTER(Kernel), C.POINTER(Decomp), C.POINTER(Options),
+                                     i32, i32, vp, vp, C.POINTER(C.c_uint64)]),
+        "nlfeti_server_get_info": (i32, [vp, C.POINTER(ServerInfo)]),
         "nlfeti_apply_schur_noalloc": (i32, [vp, i32, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -145,7 +166,9 @@ def _ptr(a):
 class Context:
     """A library context bound to torch's current CUDA stream and caching allocator."""
 
-    def __init__(self, options: Options | None = None, use_torch: bool = True):
+    def __init__(self, options: Options | None = None, use_torch: bool = True, alloc_filter=None):
+        """alloc_filter(nbytes) -> bool, optional: when it returns False the allocator callback
+        returns NULL for that request (the library then reports NLFETI_E_NOMEM)."""
         self.lib = load()
         self._keep = []
         stream = None
@@ -159,6 +182,8 @@ class Context:
                     stream = s.cuda_stream
 
                     def _alloc(n, user):
+                        if alloc_filter is not None and not alloc_filter(int(n)):
+                            return None
                         return torch.cuda.caching_allocator_alloc(int(n), dev, s)
 
                     def _free(p, user):
@@ -317,6 +342,33 @@ class Problem:
         n = inf["n_lambda"]
         return dict(n_k=nk, n_gamma=ng, nodes=nodes, B_plus=bp[:n], B_minus=bm[:n], floating=fl)
 
+    def autotune(self, nrhs, cache_path=None):
+        """Time the apply shapes for nrhs right-hand sides and keep the fastest (see nlfeti_autotune);
+        returns one dict per operator kind."""
+        arr = (TuneEntry * 3)()
+        n = C.c_int(0)
+        self.ctx.check(self.ctx.lib.nlfeti_autotune(self.h, int(nrhs), cache_path.encode() if cache_path else None,
+                                                    arr, C.byref(n)))
+        return [{k: getattr(arr[i], k) for k, _ in TuneEntry._fields_} for i in range(n.value)]
+
+    def set_apply_choice(self, kind, nrhs, rc, ctas_per_sm=2, raise_on_error=True):
+        code = self.ctx.lib.nlfeti_set_apply_choice(self.h, int(kind), int(nrhs), int(rc), int(ctas_per_sm))
+        if raise_on_error:
+            self.ctx.check(code)
+        return code
+
+    def debug_apply_waits(self, wait_tries=0, withhold_copies=0):
+        """Fault injection for tests of the apply's bounded waits (see nlfeti_debug_apply_waits)."""
+        self.ctx.check(self.ctx.lib.nlfeti_debug_apply_waits(self.h, int(wait_tries), int(withhold_copies)))
+
+    def set_matrix(self, k, A, raise_on_error=True):
+        """Replace the assembled subdomain matrix A^k (n_k x n_k); the factorizations are dropped."""
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        code = self.ctx.lib.nlfeti_problem_set_matrix(self.h, int(k), A.ctypes.data)
+        if raise_on_error:
+            self.ctx.check(code)
+        return code
+
     def operator(self, k, which, precision=0):
         d = self.decomposition()
         n = int(d["n_k"][k]) if which == 0 else int(d["n_gamma"][k])
@@ -360,7 +412,8 @@ class Problem:
 
 
 class Server:
-    """Continuous-batching server over a context (one worker per slot, own streams)."""
+    """Continuous-batching server over a context (one worker thread and stream per slot;
+    requests on the same problem share batched solves)."""
 
     def __init__(self, ctx: Context, hbm_budget: int = 0, max_slots: int = 4):
         self.ctx = ctx
@@ -379,6 +432,34 @@ class Server:
                                                   _ptr(gg), C.byref(t)))
         self._pending[t.value] = (rhs.shape, prob)
         return t.value
+
+    def submit_workload(self, w, rhs=None, opt: Options | None = None, g=None):
+        """A request on the problem given by a workload's inputs (the server's factorization
+        cache creates and factors it on first use)."""
+        m, k = w.mesh, w.kernel
+        xy = np.ascontiguousarray(m.xy, dtype=np.float64)
+        el = np.ascontiguousarray(m.elems, dtype=np.int32)
+        nd = np.ascontiguousarray(m.node_is_dirichlet, dtype=np.int8)
+        ed = np.ascontiguousarray(m.elem_is_dirichlet, dtype=np.int8)
+        lab = np.ascontiguousarray(w.labels, dtype=np.int32)
+        mesh = Mesh(m.dim, nd.size, xy.ctypes.data, ed.size, el.ctypes.data, nd.ctypes.data, ed.ctypes.data)
+        kern = Kernel(int(k.type), float(k.delta), float(k.s), float(k.scale), int(getattr(k, "ball", 0)))
+        dec = Decomp(int(w.K), lab.ctypes.data)
+        rhs = np.asfortranarray(w.rhs if rhs is None else rhs, dtype=np.float64)
+        if rhs.ndim == 1:
+            rhs = rhs.reshape(-1, 1, order="F")
+        gg = None if g is None else np.asfortranarray(np.broadcast_to(np.asarray(g, np.float64).reshape(rhs.shape[0], -1), rhs.shape))
+        t = C.c_uint64()
+        self.ctx.check(self.ctx.lib.nlfeti_submit_mesh(self.h, C.byref(mesh), C.byref(kern), C.byref(dec),
+                                                       C.byref(opt) if opt is not None else None, rhs.shape[1],
+                                                       int(w.rhs_kind), rhs.ctypes.data, _ptr(gg), C.byref(t)))
+        self._pending[t.value] = (rhs.shape, None)
+        return t.value
+
+    def info(self):
+        i = ServerInfo()
+        self.ctx.check(self.ctx.lib.nlfeti_server_get_info(self.h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in ServerInfo._fields_}
 
     def wait(self, ticket, timeout_ms=-1):
         shape, _ = self._pending[ticket]

@@ -319,6 +319,10 @@ void build_maps(nlfeti_problem *p) {
     p->sched_ctas = schedule(items, apply_tma_ctas(), [](const SubdomainDesc &s, int r0) {
         return std::make_pair(std::min(kApplyRows, s.nG - r0), std::min<int64_t>(s.ldG, (s.nG + 7) / 8 * 8));
     }, p->d_sched_ptr, p->d_sched_items);
+    p->sched1_ctas = items.empty() ? 0 : schedule(items, device_sms(),
+                                                 [](const SubdomainDesc &s, int r0) {
+        return std::make_pair(std::min(kApplyRows, s.nG - r0), std::min<int64_t>(s.ldG, (s.nG + 7) / 8 * 8));
+    }, p->d_sched1_ptr, p->d_sched1_items);
     p->fsched_ctas = schedule(items, apply_tma_ctas(), [](const SubdomainDesc &s, int r0) {
         return std::make_pair(std::min(kApplyRows, s.nG - r0), (int64_t)(s.nO + 7) / 8 * 8);
     }, p->d_fsched_ptr, p->d_fsched_items);
@@ -398,6 +402,7 @@ void nlfeti_default_options(nlfeti_options *o) {
     o->hbm_budget = 0;
     o->graph_loop = 1;
     o->precond_fp16 = 1;
+    o->factor_tc = 0;
 }
 
 nlfeti_status nlfeti_create(nlfeti_ctx **out, const nlfeti_options *opt, void *cuda_stream,
@@ -414,6 +419,11 @@ nlfeti_status nlfeti_create(nlfeti_ctx **out, const nlfeti_options *opt, void *c
     nlfeti_default_options(&c->opt);
     if (opt) c->opt = *opt;
     c->user_stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return NLFETI_E_CUDA;
+    }
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
@@ -469,6 +479,53 @@ void ctx_detach(nlfeti_ctx *c) {
     }
     if (free_now) ctx_free(c);
 }
+}  // namespace nlf
+
+namespace nlf {
+
+// Device bytes a problem holds once created and factored with the precisions of mask (bit 0
+// FP64, bit 1 FP32): the assembled matrices, the operator pools in the layout of build_maps,
+// the sweep scratch and the node maps, plus a margin for the index maps and tensor maps.
+size_t problem_bytes(const Decomp &d, int64_t n_nodes, int mask) {
+    const int K = d.K, nc = d.nc;
+    double b = 0, sum_nk = 0;
+    for (int k = 0; k < K; ++k) {
+        const double nk = (double)d.nodes[k].size() * nc, nG = (double)d.n_gamma_nodes[k] * nc;
+        const double nD = (double)d.dir_nodes[k].size() * nc;
+        const double ldM = (double)round8((int)nk), ldG = (double)round8(std::max((int)nG, 1));
+        sum_nk += nk;
+        b += 8.0 * nk * nk + 8.0 * nk * nD;                               // A^k and its Dirichlet block
+        if (mask & 1) b += 8.0 * nk * ldM + 2 * 8.0 * nG * ldG;           // FP64 swept matrix, S, S^+
+        if (mask & 2) b += 4.0 * nk * ldM * 3 + 2 * 4.0 * nG * ldG + 2.0 * nG * ldG;   // FP32 + A pairs, S, S^+, FP16 S
+    }
+    const double scr = sum_nk * 64 * 2 + (double)K * 64 * 64;              // sweep panels
+    if (mask & 1) b += 8.0 * scr;
+    if (mask & 2) b += 4.0 * scr;
+    b += 4.0 * (double)K * (double)n_nodes;                               // node -> subdomain-local maps
+    b += 64.0 * sum_nk;                                                   // index maps, vectors, tensor maps
+    return (size_t)(b * 1.05) + (size_t(16) << 20);
+}
+
+size_t predict_problem_bytes(const nlfeti_mesh *mesh, const nlfeti_kernel *kernel, const nlfeti_decomp *decomp,
+                             int mask) {
+    validate_mesh(mesh);
+    validate_kernel(kernel, mesh->dim);
+    validate_ball_mesh(kernel, mesh);
+    if (!decomp || !decomp->elem_subdomain) fail(NLFETI_E_INVALID, "null decomposition");
+    MeshHost m;
+    m.dim = mesh->dim;
+    m.n_nodes = mesh->n_nodes;
+    m.n_elems = mesh->n_elems;
+    m.xy.assign(mesh->xy, mesh->xy + mesh->n_nodes * mesh->dim);
+    m.elems.assign(mesh->elems, mesh->elems + mesh->n_elems * (mesh->dim + 1));
+    m.node_dir.assign(mesh->node_is_dirichlet, mesh->node_is_dirichlet + mesh->n_nodes);
+    m.elem_dir.assign(mesh->elem_is_dirichlet, mesh->elem_is_dirichlet + mesh->n_elems);
+    std::vector<int32_t> labels(decomp->elem_subdomain, decomp->elem_subdomain + mesh->n_elems);
+    Decomp d;
+    build_decomposition(m, *kernel, labels, decomp->K, d);
+    return problem_bytes(d, mesh->n_nodes, mask);
+}
+
 }  // namespace nlf
 
 extern "C" {
@@ -555,6 +612,7 @@ nlfeti_status nlfeti_problem_set_options(nlfeti_problem *p, const nlfeti_options
     if (!p || !opt) return NLFETI_E_INVALID;
     if (opt->precision != 0 && opt->precision != 1) return NLFETI_E_INVALID;
     if (opt->precond_fp16 < 0 || opt->precond_fp16 > 2) return NLFETI_E_INVALID;
+    if (opt->factor_tc != 0 && opt->factor_tc != 1) return NLFETI_E_INVALID;
     return guarded(p->ctx, [&] {
         p->opt = *opt;
         if (p->opt.precond_fp16 == 2 && p->op32.ready) build_tiled_half(p);
@@ -694,6 +752,64 @@ nlfeti_status nlfeti_get_decomposition(const nlfeti_problem *p, int32_t *n_k, in
     if (B_plus) std::copy(p->dec.B_plus.begin(), p->dec.B_plus.end(), B_plus);
     if (B_minus) std::copy(p->dec.B_minus.begin(), p->dec.B_minus.end(), B_minus);
     return NLFETI_OK;
+}
+
+nlfeti_status nlfeti_autotune(nlfeti_problem *p, int nrhs, const char *cache_path, nlfeti_tune_entry *out,
+                              int *n_out) {
+    if (!p || nrhs < 1) return NLFETI_E_INVALID;
+    return guarded(p->ctx, [&] {
+        std::vector<TuneEntry> res;
+        autotune_applies(p, nrhs, cache_path, res);
+        if (n_out) *n_out = (int)res.size();
+        if (out)
+            for (size_t i = 0; i < res.size() && i < 3; ++i) {
+                out[i].kind = res[i].kind;
+                out[i].nrhs = res[i].R;
+                out[i].rc = res[i].rc;
+                out[i].ctas_per_sm = res[i].per_sm;
+                out[i].us = res[i].us;
+                out[i].from_cache = res[i].from_cache ? 1 : 0;
+            }
+    });
+}
+
+nlfeti_status nlfeti_set_apply_choice(nlfeti_problem *p, int kind, int nrhs, int rc, int ctas_per_sm) {
+    if (!p || kind < 0 || kind > 2 || nrhs < 1) return NLFETI_E_INVALID;
+    return guarded(p->ctx, [&] {
+        if (rc == 0) {
+            p->tune.erase({kind, nrhs});
+        } else {
+            const bool pow2 = rc == 1 || rc == 2 || rc == 4 || rc == 8 || rc == 16;
+            if (!pow2 || (kind == 2 && rc > 8) || (rc > nrhs && rc > 1) || (ctas_per_sm != 1 && ctas_per_sm != 2))
+                fail(NLFETI_E_INVALID, "column block must be 1, 2, 4, 8 or 16 (8 for FP64) and at most nrhs; "
+                                       "CTAs per SM 1 or 2");
+            p->tune[{kind, nrhs}] = ApplyChoice{rc, ctas_per_sm};
+        }
+        ++p->tune_gen;
+    });
+}
+
+nlfeti_status nlfeti_debug_apply_waits(nlfeti_problem *p, long long wait_tries, int withhold_copies) {
+    if (!p || wait_tries < 0 || (withhold_copies != 0 && withhold_copies != 1)) return NLFETI_E_INVALID;
+    p->dbg_wait_tries = wait_tries;
+    p->dbg_withhold = withhold_copies;
+    return NLFETI_OK;
+}
+
+nlfeti_status nlfeti_problem_set_matrix(nlfeti_problem *p, int k, const double *A) {
+    if (!p || !A || k < 0 || k >= p->K) return NLFETI_E_INVALID;
+    return guarded(p->ctx, [&] {
+        const SubdomainDesc &d = p->sd[k];
+        const size_t n = (size_t)d.nk * (size_t)d.nk;
+        for (size_t t = 0; t < n; ++t)
+            if (!std::isfinite(A[t])) fail(NLFETI_E_INVALID, "the subdomain matrix has a non-finite entry");
+        if (n) NLF_CUDA(cudaMemcpy(p->d_A.as<double>() + d.offA, A, sizeof(double) * n, cudaMemcpyHostToDevice));
+        // every operator derived from A^k is stale: refactor before the next solve
+        p->op64.ready = false;
+        p->op32.ready = false;
+        p->cg_ready = false;
+        ++p->factor_gen;
+    });
 }
 
 nlfeti_status nlfeti_get_operator(const nlfeti_problem *p, int k, int which, int precision, double *out) {

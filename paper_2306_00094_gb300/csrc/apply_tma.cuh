@@ -19,8 +19,9 @@
 // row step, and the result is multiplied by oscale (the power of two the copy was scaled by).
 //
 // Every wait is bounded: a wait that runs out sets *err (the workspace's error word, read by
-// the host after the solve), the consumers stop, the producer waits (again bounded) for the
-// copies it has issued and the CTA returns.
+// the host after the solve), the consumers stop, the producer waits (again bounded, with the
+// default limit) for the copies it has issued and the CTA returns.  The consumers' stage waits
+// take their limit from wait_tries (the problem's setting; tests make it short).
 #pragma once
 
 #include <cuda.h>
@@ -32,6 +33,12 @@ constexpr int APPLY_CB = 1024;                      // bytes of one row (or one 
 constexpr int APPLY_MINB = 2;                       // CTAs per SM
 constexpr int APPLY_NS = 2;                         // stages per CTA (40 KB each at RC = 8)
 constexpr int APPLY_NS_H = 4;                       // stages with an FP16 operator (24 KB each at RC = 8)
+constexpr int APPLY_NS_H16 = 3;                     // ... at RC = 16 (32 KB each), two CTAs per SM
+// right-hand sides per streamed pass: the FP32 operators stream once for up to 16 columns (the
+// FP64 ones, whose accumulators take twice the registers, for up to 8)
+__host__ __device__ constexpr int apply_rc(int R, int elem_size) {
+    return (R >= 16 && elem_size == 4) ? 16 : (R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1)));
+}
 // a stage: 32 operator rows of mrow bytes, then RC columns of x (APPLY_CB bytes each)
 __host__ __device__ constexpr int apply_stage_bytes(int rc, int mrow = APPLY_CB) { return 32 * mrow + rc * APPLY_CB; }
 // the ring is aligned to 1 KB inside the dynamic shared memory (tensor copies want 128 B)
@@ -59,10 +66,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned by
                  : "memory");
 }
 
-// true once the phase with the given parity has completed; false when the tries run out
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+// true once the phase with the given parity has completed; false when the tries run out (or,
+// with an abort word, once another warp of the CTA has set it)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long tries = APPLY_WAIT_TRIES,
+                                          const volatile int *abort_word = nullptr) {
     const uint32_t a = smem_u32(bar);
-    for (long long i = 0; i < APPLY_WAIT_TRIES; ++i) {
+    for (long long i = 0; i < tries; ++i) {
+        if (abort_word && (i & 63) == 63 && *abort_word) return false;
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
@@ -137,7 +147,8 @@ template <typename T, int RC, int NS = APPLY_NS, int MINB = APPLY_MINB, typename
 __global__ void __launch_bounds__(APPLY_THREADS, MINB)
     k_apply_tma(const CUtensorMap *maps, const CUtensorMap *xmaps, int use_sp, const SubdomainDesc *sd,
                 const int32_t *sched_ptr, const int32_t *sched_items, double *y, int R, const int *gate, int *err,
-                double oscale = 1.0, const double *xa = nullptr) {
+                double oscale = 1.0, const double *xa = nullptr, long long wait_tries = APPLY_WAIT_TRIES,
+                int withhold = 0) {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
     constexpr int CW = APPLY_CB / (int)sizeof(T);   // columns per stage row
@@ -161,6 +172,9 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
     const int it0 = sched_ptr[blockIdx.x], it1 = sched_ptr[blockIdx.x + 1];
     if (warp == 8) {
         // ------------------------------------------------------------------ producer
+        // withhold (fault injection for tests of the bounded waits): issue nothing, so that the
+        // consumers' first stage wait runs out with no copy in flight
+        if (withhold) return;
         int q = 0;
         bool ok = true;
         for (int it = it0; it < it1 && ok; ++it) {
@@ -173,7 +187,9 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
             for (int l0 = 0; l0 < ncp; l0 += CW, ++q) {
                 const int s = q % NS;
                 // warp-uniform decisions: every lane takes the same branch
-                if (__any_sync(0xffffffffu, (q >= NS && !mbar_wait(&empty[s], ((q / NS) - 1) & 1)) || abort_flag)) {
+                if (__any_sync(0xffffffffu,
+                               (q >= NS && !mbar_wait(&empty[s], ((q / NS) - 1) & 1, APPLY_WAIT_TRIES, &abort_flag)) ||
+                                   abort_flag)) {
                     ok = false;
                     break;
                 }
@@ -211,7 +227,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
                 for (int c = 0; c < RC; ++c) acc[r][c] = T(0);
             for (int l0 = 0; l0 < ncp; l0 += CW, ++q) {
                 const int s = q % NS;
-                if (__any_sync(0xffffffffu, !mbar_wait(&full[s], (q / NS) & 1) || abort_flag)) {
+                if (__any_sync(0xffffffffu, !mbar_wait(&full[s], (q / NS) & 1, wait_tries, &abort_flag) || abort_flag)) {
                     if (lane == 0) { atomicExch(err, 1); abort_flag = 1; }
                     return;                           // the whole warp (the vote is uniform)
                 }
@@ -234,20 +250,26 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
             }
-            constexpr int NV = 4 * RC;
-            T v[NV];
+            // lane sums by reduce-scatter in groups of at most 8 columns (4 rows x 8 = 32 values,
+            // one per lane): every sum takes the same shuffle tree whatever RC is
+            constexpr int CG = RC < 8 ? RC : 8;
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int g0 = 0; g0 < RC; g0 += CG) {
+                constexpr int NV = 4 * CG;
+                T v[NV];
 #pragma unroll
-                for (int c = 0; c < RC; ++c) v[r * RC + c] = acc[r][c];
-            const T tot = warp_reduce_scatter<T, NV>(v, lane);
-            constexpr int G = 32 / NV;
-            const int idx = lane / G, r = idx / RC, c = idx % RC, i = ib + r;
-            if (lane % G == 0 && c < rc && i < n) {
-                if (MODE == ROWS_APPLY) y[(yoff + i) * R + c0 + c] = (double)tot * oscale;
-                else if (MODE == ROWS_FORCING)
-                    y[(yoff + i) * R + c0 + c] = xa[(voff + nO + i) * R + c0 + c] - (double)tot;
-                else y[(voff + i) * R + c0 + c] = -(double)tot;
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < CG; ++c) v[r * CG + c] = acc[r][g0 + c];
+                const T tot = warp_reduce_scatter<T, NV>(v, lane);
+                constexpr int G = 32 / NV;
+                const int idx = lane / G, r = idx / CG, c = g0 + idx % CG, i = ib + r;
+                if (lane % G == 0 && c < rc && i < n) {
+                    if (MODE == ROWS_APPLY) y[(yoff + i) * R + c0 + c] = (double)tot * oscale;
+                    else if (MODE == ROWS_FORCING)
+                        y[(yoff + i) * R + c0 + c] = xa[(voff + nO + i) * R + c0 + c] - (double)tot;
+                    else y[(voff + i) * R + c0 + c] = -(double)tot;
+                }
             }
         }
     }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -13,6 +14,7 @@
 
 struct nlfeti_ctx {
     nlfeti_options opt;
+    int device = 0;                       // the device current at nlfeti_create (its streams and memory)
     cudaStream_t stream = nullptr;        // the library's own non-blocking stream (capturable)
     cudaStream_t user_stream = nullptr;   // the caller's stream (may be the legacy stream)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -153,6 +155,13 @@ template <typename T> struct OpPool {   // operators of one precision
 
 namespace nlf { struct SolveWS; }
 
+// a configuration of the bulk-copy interface apply: right-hand sides per streamed pass (1, 2,
+// 4, 8 or 16) and CTAs per SM of its persistent grid (1 or 2)
+struct ApplyChoice {
+    int rc = 0;
+    int per_sm = 2;
+};
+
 struct nlfeti_problem {
     nlfeti_ctx *ctx = nullptr;
     uint64_t uid = 0;                   // unique per problem of the process (workspaces and graphs key on it)
@@ -210,6 +219,13 @@ struct nlfeti_problem {
     // sched_items[sched_ptr[b] .. sched_ptr[b+1]) (pairs (k, first row)), balanced by cost
     int sched_ctas = 0;
     nlf::DevMem d_sched_ptr, d_sched_items;
+    // the same items over one CTA per SM (an autotuner candidate)
+    int sched1_ctas = 0;
+    nlf::DevMem d_sched1_ptr, d_sched1_items;
+    // the autotuner's choices for the bulk-copy apply per (operator kind, right-hand sides):
+    // kind 0 = FP32 operators, 1 = the FP16 copy of S_k, 2 = FP64 operators
+    std::map<std::pair<int, int>, ApplyChoice> tune;
+    uint64_t tune_gen = 0;               // bumped by every change of tune (captured graphs key on it)
     // the same for the tensor-core preconditioner apply: 128-row items; and, for the launches
     // per subdomain, the items in subdomain order (subdomain k: mitem_off[k] .. mitem_off[k+1])
     // with the identity schedule 0, 1, 2, ... (one item per CTA)
@@ -233,6 +249,10 @@ struct nlfeti_problem {
     int64_t cg_nnz = 0;
     bool cg_ready = false;
     double ms_setup = 0, ms_factor = 0;
+    // fault injection for tests of the bounded waits of the interface apply (nlfeti_debug_apply_waits):
+    // the consumers' stage-wait limit (0 = the default) and whether the producer withholds its copies
+    long long dbg_wait_tries = 0;
+    int dbg_withhold = 0;
     bool prof_on = false;
     std::mutex prof_mu;
     nlfeti_profile prof{};
@@ -254,6 +274,11 @@ void stream_leave(nlfeti_ctx *c);
 // a live problem or server keeps its context alive
 void ctx_attach(nlfeti_ctx *c);
 void ctx_detach(nlfeti_ctx *c);
+// the apply configuration used for operator kind (0 FP32, 1 FP16 copy, 2 FP64) and R: the
+// autotuner's choice if one was made, else the default (apply_rc(R), two CTAs per SM)
+ApplyChoice apply_choice(const nlfeti_problem *p, int kind, int R);
+// streaming multiprocessors of the current device
+int device_sms();
 // CTAs of the bulk-copy interface apply / refinement residual that fit on the device at once
 int apply_tma_ctas();
 int apply_mma_ctas();
@@ -262,4 +287,8 @@ int residual_tma_ctas();
 template <typename T> void encode_apply_maps(nlfeti_problem *p, OpPool<T> &pool);
 // global CSR of the single-domain matrix for the CG baseline (once per problem; host sync)
 void cg_prepare(nlfeti_problem *p);
+// device bytes of a problem created from these inputs and factored in the precisions of mask
+// (bit 0 FP64, bit 1 FP32): validates the inputs and runs the host decomposition (throws Error)
+size_t predict_problem_bytes(const nlfeti_mesh *mesh, const nlfeti_kernel *kernel, const nlfeti_decomp *decomp,
+                             int mask);
 }  // namespace nlf

@@ -19,6 +19,7 @@
 // correction is below refine_tol.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <type_traits>
 
@@ -45,6 +46,12 @@ inline unsigned grid_for(int64_t n, int threads = 256) {
 __global__ void k_sub(const double *a, const double *b, double *out, int64_t n) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
         out[t] = a[t] - b[t];
+}
+
+// zero the columns c with frozen[c] != 0 of an interleaved n x R vector
+__global__ void k_zero_frozen(double *v, int64_t n, int R, const int *frozen) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * R; t += (int64_t)gridDim.x * blockDim.x)
+        if (frozen[t % R]) v[t] = 0.0;
 }
 
 __global__ void k_axpy(double *y, const double *x, double a, int64_t n) {
@@ -288,6 +295,69 @@ __device__ __forceinline__ bool arrive_last(unsigned *counter) {
     return last;
 }
 
+// Coalesced reductions over Lambda with R interleaved right-hand sides (entry (i, c) at
+// i R + c).  The rows are cut into tiles of RT = 8 rows; block b owns the contiguous tiles
+// [b tpb, (b + 1) tpb) (tpb from n and the grid only).  A (tile, chunk of cw columns) unit
+// takes 4 cw lanes: lane (h, j), h = 0..3, adds rows h and h + 4 of column c0 + j, and the
+// four lanes of a column are added as ((h0 + h2) + (h1 + h3)).  The block adds its tile sums
+// per column in tile order (rounds of up to RSMEM / R tiles through shared memory), and
+// finish_scalars adds the blocks' partials in block order.  cw = min(8, R rounded up to a
+// power of two) and the round size only decide which lanes run a unit and when, never the
+// order of the additions, so every column is summed in the same order whatever the batch it
+// is part of; the lanes of a unit read 4 rows x cw consecutive columns per step, and each lane
+// has two rows in flight.  f(i, c) is called once per entry (i < n, c < R) and returns its
+// addend.
+constexpr int RT = 8;
+constexpr int RSMEM = 2048;             // doubles of tile sums per round (16 KB)
+constexpr int RCOLS = RED_THREADS;      // columns per pass (one accumulating thread each)
+
+constexpr int TILE_MAX_BLOCKS = 608;    // four CTAs per SM
+inline int tile_blocks(int64_t n) {
+    const int64_t nt = (n + RT - 1) / RT;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(TILE_MAX_BLOCKS, (nt + 1) / 2));
+}
+
+template <typename F>
+__device__ __forceinline__ void tile_reduce(int64_t n, int R, double *partial, F &&f) {
+    __shared__ double ts[RSMEM];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int64_t ntiles = (n + RT - 1) / RT;
+    const int64_t tpb = (ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * tpb, t1 = min(ntiles, t0 + tpb);
+    const int cw = R >= 5 ? 8 : (R >= 3 ? 4 : (R == 2 ? 2 : 1));
+    const int ulanes = 4 * cw, upw = 32 / ulanes;
+    const int ju = lane / ulanes, jl = lane % ulanes, h = jl / cw, cj = jl % cw;
+    for (int cc0 = 0; cc0 < R; cc0 += RCOLS) {
+        const int ncol = min(RCOLS, R - cc0);
+        const int nchunk = (ncol + cw - 1) / cw;
+        const int rtiles = max(1, min(256, RSMEM / ncol));
+        double acc = 0;
+        for (int64_t tb = t0; tb < t1; tb += rtiles) {
+            const int ntl = (int)min((int64_t)rtiles, t1 - tb);
+            const int units = ntl * nchunk;
+            for (int ub = warp * upw; ub < units; ub += (RED_THREADS / 32) * upw) {
+                const int u = ub + ju;
+                const int tl = u / nchunk, cl = (u % nchunk) * cw + cj;
+                const bool ok = u < units && cl < ncol;
+                double v = 0;
+                if (ok) {
+                    const int64_t i0 = (tb + tl) * RT + h;
+                    if (i0 < n) v += f(i0, cc0 + cl);
+                    if (i0 + 4 < n) v += f(i0 + 4, cc0 + cl);
+                }
+                v += __shfl_down_sync(0xffffffffu, v, 2 * cw);
+                v += __shfl_down_sync(0xffffffffu, v, cw);
+                if (ok && h == 0) ts[tl * ncol + cl] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x < ncol)
+                for (int tl = 0; tl < ntl; ++tl) acc += ts[tl * ncol + threadIdx.x];
+            __syncthreads();
+        }
+        if (threadIdx.x < ncol) partial[(int64_t)blockIdx.x * R + cc0 + threadIdx.x] = acc;
+    }
+}
+
 // last block: column totals over the nb row-block partials (warp per column, fixed order)
 // and the PCG scalar update:
 //   NPD:   ||P d|| and the initial state;      CHECK: ||w|| and the active mask;
@@ -337,15 +407,12 @@ __device__ void finish_scalars(const double *partial, int nb, int R, PcgScalars 
     }
 }
 
-// (a, b) per column with the scalar update of MODE
+// (a, b) per column with the scalar update of MODE (grid tile_blocks(n))
 template <int MODE>
-__global__ void __launch_bounds__(RED_THREADS) k_dot_final(const double *a, const double *b, int64_t n, int R,
-                                                            double *partial, PcgScalars s, double tol, int max_it) {
-    const int c = blockIdx.y;
-    double acc = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        acc += a[i * R + c] * b[i * R + c];
-    block_partial(acc, partial, R);
+__global__ void __launch_bounds__(RED_THREADS) k_dot_final(const double *__restrict__ a, const double *__restrict__ b,
+                                                            int64_t n, int R, double *partial, PcgScalars s, double tol,
+                                                            int max_it) {
+    tile_reduce(n, R, partial, [&](int64_t i, int c) { return a[i * R + c] * b[i * R + c]; });
     if (arrive_last(s.counter)) finish_scalars<MODE>(partial, gridDim.x, R, s, tol, max_it);
 }
 
@@ -360,41 +427,39 @@ __device__ __forceinline__ double p_next(double p, double y, double beta, bool a
 __device__ __forceinline__ double r_next(double r, double q, double eta) { return __fma_rn(-eta, q, r); }
 
 // out = P v = v - G alpha (alpha from k_proj_g; NULL when there is no coarse space), with the
-// dot product of MODE: CHECK (out, out), BETA (out, other)
+// dot product of MODE: CHECK (out, out), BETA (out, other).  Grid tile_blocks(nl).
 template <int MODE>
-__global__ void __launch_bounds__(RED_THREADS) k_project_dot(const int32_t *gcol, const double *gval, int gw,
-                                                              const double *alpha, const double *v,
-                                                              const double *other, double *out, int64_t nl, int R,
+__global__ void __launch_bounds__(RED_THREADS) k_project_dot(const int32_t *__restrict__ gcol,
+                                                              const double *__restrict__ gval, int gw,
+                                                              const double *__restrict__ alpha,
+                                                              const double *__restrict__ v,
+                                                              const double *__restrict__ other,
+                                                              double *__restrict__ out, int64_t nl, int R,
                                                               double *partial, PcgScalars s, double tol, int max_it) {
-    const int c = blockIdx.y;
-    double acc = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += (int64_t)gridDim.x * blockDim.x) {
+    tile_reduce(nl, R, partial, [&](int64_t i, int c) {
         const int64_t t = i * R + c;
         double x = v[t];
         if (alpha) x += -1.0 * g_alpha(gcol, gval, gw, alpha, i, c, R);
         out[t] = x;
-        acc += x * (MODE == FIN_CHECK ? x : other[t]);
-    }
-    block_partial(acc, partial, R);
+        return x * (MODE == FIN_CHECK ? x : other[t]);
+    });
     if (arrive_last(s.counter)) finish_scalars<MODE>(partial, gridDim.x, R, s, tol, max_it);
 }
 
 // q = B y_U with (p_new, q) and the ETA update (p_new formed per row, stored by the next
-// iteration's k_check_update)
-__global__ void __launch_bounds__(RED_THREADS) k_gather_b_eta(const int64_t *Bp, const int64_t *Bm, const double *yU,
-                                                               const double *pv, const double *y, double *q,
+// iteration's k_check_update).  Grid tile_blocks(nl).
+__global__ void __launch_bounds__(RED_THREADS) k_gather_b_eta(const int64_t *__restrict__ Bp,
+                                                               const int64_t *__restrict__ Bm,
+                                                               const double *__restrict__ yU,
+                                                               const double *__restrict__ pv,
+                                                               const double *__restrict__ y, double *__restrict__ q,
                                                                int64_t nl, int R, double *partial, PcgScalars s) {
-    const int c = blockIdx.y;
-    const bool act = s.active[c] != 0;
-    const double be = s.beta[c];
-    double acc = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += (int64_t)gridDim.x * blockDim.x) {
+    tile_reduce(nl, R, partial, [&](int64_t i, int c) {
         const int64_t t = i * R + c;
         const double x = yU[Bp[i] * R + c] - yU[Bm[i] * R + c];
         q[t] = x;
-        acc += p_next(pv[t], y[t], be, act) * x;
-    }
-    block_partial(acc, partial, R);
+        return p_next(pv[t], y[t], s.beta[c], s.active[c] != 0) * x;
+    });
     if (arrive_last(s.counter)) finish_scalars<FIN_ETA>(partial, gridDim.x, R, s, 0.0, 0);
 }
 
@@ -407,19 +472,19 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_b_eta(const int64_t *Bp,
 // whatever the scalars hold); a separate instantiation, as profilers skip kernels that set
 // graph conditions.
 template <int COND>
-__global__ void __launch_bounds__(RED_THREADS) k_check_update(const int32_t *gcol, const double *gval, int gw,
-                                                               const double *alpha, const double *y, double *pv,
-                                                               double *lam, double *r, const double *q, double *w,
+__global__ void __launch_bounds__(RED_THREADS) k_check_update(const int32_t *__restrict__ gcol,
+                                                               const double *__restrict__ gval, int gw,
+                                                               const double *__restrict__ alpha,
+                                                               const double *__restrict__ y, double *__restrict__ pv,
+                                                               double *__restrict__ lam, double *__restrict__ r,
+                                                               const double *__restrict__ q, double *__restrict__ w,
                                                                int64_t nl, int R, double *partial, PcgScalars s,
                                                                double tol, int max_it, cudaGraphConditionalHandle cond,
                                                                int limit) {
-    const int c = blockIdx.y;
-    const bool act = s.active[c] != 0;
-    const double be = s.beta[c], e = s.eta[c];
-    double acc = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += (int64_t)gridDim.x * blockDim.x) {
+    tile_reduce(nl, R, partial, [&](int64_t i, int c) {
         const int64_t t = i * R + c;
-        const double pn = p_next(pv[t], y[t], be, act);
+        const double e = s.eta[c];
+        const double pn = p_next(pv[t], y[t], s.beta[c], s.active[c] != 0);
         pv[t] = pn;
         lam[t] = __fma_rn(e, pn, lam[t]);
         const double rn = r_next(r[t], q[t], e);
@@ -427,9 +492,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_check_update(const int32_t *gco
         double x = rn;
         if (alpha) x += -1.0 * g_alpha(gcol, gval, gw, alpha, i, c, R);
         w[t] = x;
-        acc += x * x;
-    }
-    block_partial(acc, partial, R);
+        return x * x;
+    });
     if (arrive_last(s.counter)) {
         finish_scalars<FIN_CHECK>(partial, gridDim.x, R, s, tol, max_it);
         if (COND && threadIdx.x == 0) {
@@ -460,6 +524,76 @@ __global__ void k_gather_apply_p(const int64_t *ptr, const int64_t *row, const d
         }
         apply_store<T>(x, sd, u2sub, u, c, R, (T)s);
     }
+}
+
+// Gathers into the apply layout through shared memory: a block takes GX_U consecutive U dofs
+// with all R columns; the sums are formed with the columns fastest (the R entries of a Lambda
+// row are consecutive: coalesced reads), staged as [c][u], and stored with the U dofs fastest
+// (coalesced stores into the per-subdomain columns).  Each sum runs over its CSR entries in the
+// same order as in the column-major kernels, so the stored values are the same bits.
+// Dynamic shared memory GX_U * R doubles (R <= GX_MAXR).
+constexpr int GX_U = 32;
+constexpr int GX_MAXR = 64;
+
+template <typename T, typename G>
+__device__ __forceinline__ void gather_x_block(T *x, const SubdomainDesc *sd, const int32_t *u2sub, int64_t nu, int R,
+                                               G &&g) {
+    extern __shared__ double gx_sm[];
+    const int64_t u0 = (int64_t)blockIdx.x * GX_U;
+    const int nuu = (int)min((int64_t)GX_U, nu - u0);
+    for (int t = threadIdx.x; t < nuu * R; t += blockDim.x) {
+        const int ul = t / R, c = t % R;
+        gx_sm[c * GX_U + ul] = g(u0 + ul, c);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nuu * R; t += blockDim.x) {
+        const int c = t / nuu, ul = t % nuu;
+        apply_store<T>(x, sd, u2sub, u0 + ul, c, R, (T)gx_sm[c * GX_U + ul]);
+    }
+}
+
+// x = B^T p_new (as k_gather_apply_p)
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather_apply_p_t(const int64_t *__restrict__ ptr,
+                                                          const int64_t *__restrict__ row,
+                                                          const double *__restrict__ pv, const double *__restrict__ y,
+                                                          const double *beta, const int *active, T *x,
+                                                          const SubdomainDesc *sd, const int32_t *u2sub, int64_t nu,
+                                                          int R, const int *gate) {
+    if (gate && *gate == 0) return;
+    gather_x_block<T>(x, sd, u2sub, nu, R, [&](int64_t u, int c) {
+        const bool act = active[c] != 0;
+        const double be = beta[c];
+        double s = 0;
+        for (int64_t q = ptr[u]; q < ptr[u + 1]; ++q) {
+            const int64_t r = row[q], i = r > 0 ? r - 1 : -r - 1;
+            const double pn = p_next(pv[i * R + c], y[i * R + c], be, act);
+            s += r > 0 ? pn : -pn;
+        }
+        return s;
+    });
+}
+
+// x = B^T v, or B_D^T v when val is given (as k_gather_apply)
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather_apply_t(const int64_t *__restrict__ ptr,
+                                                        const int64_t *__restrict__ row,
+                                                        const double *__restrict__ val,
+                                                        const double *__restrict__ v, T *x, const SubdomainDesc *sd,
+                                                        const int32_t *u2sub, int64_t nu, int R, const int *gate) {
+    if (gate && *gate == 0) return;
+    gather_x_block<T>(x, sd, u2sub, nu, R, [&](int64_t u, int c) {
+        double s = 0;
+        if (val) {
+            for (int64_t q = ptr[u]; q < ptr[u + 1]; ++q) s += val[q] * v[row[q] * R + c];
+        } else {
+            for (int64_t q = ptr[u]; q < ptr[u + 1]; ++q) {
+                const int64_t r = row[q];
+                s += r > 0 ? v[(r - 1) * R + c] : -v[(-r - 1) * R + c];
+            }
+        }
+        return s;
+    });
 }
 
 // store v * xscale (a power of two), rounded once to FP16, at (U dof u, column c) of the
@@ -536,17 +670,23 @@ __global__ void k_stage_rows_x(const double *xa, const double *xb, const Subdoma
 // alpha = (G^T G)^-1 G^T v.  G^T v is gathered from flat entry lists per floating subdomain
 // f: for v on Lambda, entry e of B^T restricted to Gamma_f is (Lambda row rows[e], weights
 // w[e][q] = sign(e) Z[u(e)][q]); for v on U, the entries are the U dofs of Gamma_f with
-// weights Z.  Grid (floating subdomains, PSPLIT slices of the entry range, right-hand sides):
-// block (f, j, c) sums slice j into gpart; the last block to arrive adds the slices in order
-// (into shared memory when they fit, else gsum) and applies (G^T G)^-1.
+// weights Z.  Grid (floating subdomains, psplit slices of the entry range, right-hand sides):
+// block (f, j, c) sums slice j into gpart.  Small coarse spaces (fused): the last block to
+// arrive adds the slices in order (into shared memory when they fit, else gsum) and applies
+// (G^T G)^-1.  Large ones: k_coarse_solve does that over many CTAs (FP64 runs at a small
+// fraction of the FP32 rate here, so one CTA would take ~100 us for n_co = 108 and 16
+// right-hand sides).  psplit and the choice depend on the problem only, so every column is
+// summed in the same order whatever batch it is part of.
 // v_mode: PG_U v on U; PG_LAM v on Lambda; PG_LAM_R r_new = r - eta q on Lambda (v = r)
 constexpr int PSPLIT = 8;
+constexpr int kCoarseFusedMax = 16;     // n_co up to which the last block of k_proj_g solves
 enum { PG_U = 0, PG_LAM = 1, PG_LAM_R = 2 };
 template <int VMODE>
 __global__ void __launch_bounds__(256) k_proj_g(const int64_t *range, const int32_t *fco, const int64_t *rows,
                                                 const double *w, const double *v, const double *q,
                                                 const double *eta, double *gpart, double *gsum, const double *GtGinv,
-                                                int nco, double *alpha, int R, unsigned *counter) {
+                                                int nco, double *alpha, int R, unsigned *counter, int psplit,
+                                                int fused) {
     constexpr int lam_mode = VMODE != PG_U;
     extern __shared__ double gs_dyn[];
     __shared__ double red[8][3];
@@ -554,7 +694,7 @@ __global__ void __launch_bounds__(256) k_proj_g(const int64_t *range, const int3
     const int64_t e0 = range[4 * f + (lam_mode ? 0 : 2)], e1 = range[4 * f + (lam_mode ? 1 : 3)];
     const int co_off = fco[2 * f], nq = fco[2 * f + 1];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int64_t chunk = (e1 - e0 + PSPLIT - 1) / PSPLIT;
+    const int64_t chunk = (e1 - e0 + psplit - 1) / psplit;
     const int64_t l0 = e0 + blockIdx.y * chunk, l1 = min(e1, l0 + chunk);
     double acc[3] = {0, 0, 0};
     const double eta_c = VMODE == PG_LAM_R ? eta[c] : 0.0;
@@ -574,14 +714,15 @@ __global__ void __launch_bounds__(256) k_proj_g(const int64_t *range, const int3
     if (threadIdx.x < nq) {
         double x = 0;
         for (int ww = 0; ww < 8; ++ww) x += red[ww][threadIdx.x];
-        gpart[((int64_t)(co_off + threadIdx.x) * PSPLIT + blockIdx.y) * R + c] = x;
+        gpart[((int64_t)(co_off + threadIdx.x) * psplit + blockIdx.y) * R + c] = x;
     }
+    if (!fused) return;
     if (!arrive_last(counter)) return;
     double *gs = gsum ? gsum : gs_dyn;
     for (int t = threadIdx.x; t < nco * R; t += blockDim.x) {
         const int i = t / R, cc = t % R;
         double g = 0;
-        for (int j = 0; j < PSPLIT; ++j) g += __ldcg(gpart + ((int64_t)i * PSPLIT + j) * R + cc);
+        for (int j = 0; j < psplit; ++j) g += __ldcg(gpart + ((int64_t)i * psplit + j) * R + cc);
         gs[t] = g;
     }
     __syncthreads();
@@ -592,6 +733,24 @@ __global__ void __launch_bounds__(256) k_proj_g(const int64_t *range, const int3
         alpha[t] = a;
     }
     if (threadIdx.x == 0) *counter = 0u;
+}
+
+// alpha[i][c] = sum_j (G^T G)^-1[i][j] (G^T v)[j][c], G^T v summed from the psplit slices of
+// k_proj_g: one warp per (i, c), lanes over j (fixed order: per lane ascending, then the warp
+// tree).  Grid (ceil(n_co / 8), R), 256 threads.
+__global__ void __launch_bounds__(256) k_coarse_solve(const double *gpart, int psplit, const double *GtGinv, int nco,
+                                                      double *alpha, int R) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int i = blockIdx.x * 8 + warp, c = blockIdx.y;
+    if (i >= nco) return;
+    double a = 0;
+    for (int j = lane; j < nco; j += 32) {
+        double g = 0;
+        for (int s = 0; s < psplit; ++s) g += __ldcg(gpart + ((int64_t)j * psplit + s) * R + c);
+        a += GtGinv[(int64_t)i * nco + j] * g;
+    }
+    a = warp_sum(a);
+    if (lane == 0) alpha[(int64_t)i * R + c] = a;
 }
 
 // refinement update u += du with corr = max |du| / max |u| per column: grid (row blocks,
@@ -981,7 +1140,7 @@ struct Runner {
     }
 
     template <int MODE> void dot_final(const double *a, const double *b, int64_t n, double tol = 0, int max_it = 0) {
-        k_dot_final<MODE><<<red_grid(n, R), RED_THREADS, 0, st>>>(a, b, n, R, ws.partial.as<double>(), S, tol, max_it);
+        k_dot_final<MODE><<<tile_blocks(n), RED_THREADS, 0, st>>>(a, b, n, R, ws.partial.as<double>(), S, tol, max_it);
         note_launch();
     }
 
@@ -996,6 +1155,13 @@ struct Runner {
         p->prof.half_apply_launches += half_launches;
         p->prof.half_apply_ms += half_ms;
         p->prof.half_apply_bytes += half_bytes;
+    }
+
+    // read the error word of the bounded waits and report a wait that ran out
+    void check_waits_now() {
+        NLF_CUDA(cudaMemcpyAsync(ws.host_flag.data(), S.n_active, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        NLF_CUDA(cudaStreamSynchronize(st));
+        check_waits();
     }
 
     // after a read-back of the scalar words n_active .. err into host_flag
@@ -1058,19 +1224,27 @@ struct Runner {
     // alpha = (G^T G)^-1 Z^T B^T v  (or (G^T G)^-1 Z^T v for v in U)
     // alpha = (G^T G)^-1 G^T v: v on U (PG_U), on Lambda (PG_LAM) or r_new = v - eta q (PG_LAM_R)
     void coarse_alpha(const double *v, int vmode, const double *q = nullptr) {
+        const bool fused = p->n_co <= kCoarseFusedMax;
+        const int psplit = fused ? PSPLIT : 1;
         const size_t gs_bytes = sizeof(double) * (size_t)p->n_co * R;
-        const bool in_smem = gs_bytes <= 32768;
+        const bool in_smem = fused && gs_bytes <= 32768;
         auto go = [&](auto kern) {
-            kern<<<dim3(p->n_floating, PSPLIT, R), 256, in_smem ? gs_bytes : 0, st>>>(
+            kern<<<dim3(p->n_floating, psplit, R), 256, in_smem ? gs_bytes : 0, st>>>(
                 p->d_gt_range.as<int64_t>(), p->d_gt_co.as<int32_t>(), p->d_gt_rows.as<int64_t>(),
                 vmode == PG_U ? p->d_Z.as<double>() : p->d_gt_w.as<double>(), v, q, S.eta, ws.gco.as<double>(),
                 in_smem ? nullptr : ws.gsum.as<double>(), p->d_GtGinv.as<double>(), p->n_co, ws.alpha.as<double>(), R,
-                S.counter);
+                S.counter, psplit, fused ? 1 : 0);
         };
         if (vmode == PG_U) go(k_proj_g<PG_U>);
         else if (vmode == PG_LAM) go(k_proj_g<PG_LAM>);
         else go(k_proj_g<PG_LAM_R>);
         note_launch();
+        if (!fused) {
+            k_coarse_solve<<<dim3((p->n_co + 7) / 8, R), 256, 0, st>>>(ws.gco.as<double>(), psplit,
+                                                                      p->d_GtGinv.as<double>(), p->n_co,
+                                                                      ws.alpha.as<double>(), R);
+            note_launch();
+        }
     }
 
     // out = P v (out may alias v)
@@ -1091,7 +1265,7 @@ struct Runner {
                                          int max_it = 0) {
         const int64_t nl = p->n_lambda;
         if (p->n_co > 0) coarse_alpha(v, PG_LAM);
-        k_project_dot<MODE><<<red_grid(nl, R), RED_THREADS, 0, st>>>(
+        k_project_dot<MODE><<<tile_blocks(nl), RED_THREADS, 0, st>>>(
             p->d_Gcol.as<int32_t>(), p->d_Gval.as<double>(), p->gw, p->n_co > 0 ? ws.alpha.as<double>() : nullptr, v,
             other, out, nl, R, ws.partial.as<double>(), S, tol, max_it);
         note_launch();
@@ -1144,13 +1318,16 @@ struct Runner {
         const CUtensorMap *xm = ws.rxmaps[sizeof(T) == 8 ? 1 : 0].template as<CUtensorMap>();
         const int32_t *sp = (MODE == ROWS_FORCING ? p->d_fsched_ptr : p->d_osched_ptr).template as<int32_t>();
         const int32_t *si = (MODE == ROWS_FORCING ? p->d_fsched_items : p->d_osched_items).template as<int32_t>();
-        const int rc = R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1));
+        const int rc = apply_rc(R, (int)sizeof(T));
         auto go = [&](auto rc_tag) {
             constexpr int RCT = decltype(rc_tag)::value;
             k_apply_tma<T, RCT, APPLY_NS, APPLY_MINB, T, MODE><<<ctas, APPLY_THREADS, apply_smem_bytes(RCT, APPLY_NS), st>>>(
                 om, xm, 0, sd, sp, si, y, R, nullptr, S.err, 1.0, xa);
         };
         switch (rc) {
+            case 16:
+                if constexpr (sizeof(T) == 4) go(std::integral_constant<int, 16>{});
+                break;
             case 8: go(std::integral_constant<int, 8>{}); break;
             case 4: go(std::integral_constant<int, 4>{}); break;
             case 2: go(std::integral_constant<int, 2>{}); break;
@@ -1162,25 +1339,40 @@ struct Runner {
     // the batched interface apply: persistent tensor-copy pipeline over the balanced schedule;
     // x is read through the workspace's tensor maps of xU
     // half: S_k from the FP16 copy (FP32 pool, use_sp = 0)
+    long long wait_tries() const { return p->dbg_wait_tries > 0 ? p->dbg_wait_tries : APPLY_WAIT_TRIES; }
+
     template <typename T> int apply_tma(const OpPool<T> &pool, int use_sp, double *y, bool half = false) {
-        const int rc = R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1));
+        // the autotuner's choice for this operator kind and R (column block, CTAs per SM), else
+        // the default block and two CTAs per SM
+        const ApplyChoice ch = apply_choice(p, half ? 1 : (sizeof(T) == 8 ? 2 : 0), R);
+        const int rc = ch.rc;
+        const int ri = rc >= 16 ? 4 : (rc >= 8 ? 3 : (rc >= 4 ? 2 : (rc >= 2 ? 1 : 0)));
+        const CUtensorMap *xm = ws.xmaps_rc[sizeof(T) == 8 ? 1 : 0][ri].template as<CUtensorMap>();
+        const bool one = ch.per_sm == 1 && p->sched1_ctas > 0;
+        const int ctas = one ? p->sched1_ctas : p->sched_ctas;
+        const int32_t *sptr = (one ? p->d_sched1_ptr : p->d_sched_ptr).as<int32_t>();
+        const int32_t *sitems = (one ? p->d_sched1_items : p->d_sched_items).as<int32_t>();
+        if (!xm) fail(NLFETI_E_INVALID, "no tensor maps for the chosen column block");
         auto go = [&](auto rc_tag) {
             constexpr int RCT = decltype(rc_tag)::value;
             if constexpr (std::is_same<T, float>::value) {
                 if (half) {
-                    k_apply_tma<float, RCT, APPLY_NS_H, APPLY_MINB, __half>
-                        <<<p->sched_ctas, APPLY_THREADS, apply_smem_bytes(RCT, APPLY_NS_H, APPLY_CB / 2), st>>>(
-                            pool.hmaps.template as<CUtensorMap>(), ws.xmaps[0].template as<CUtensorMap>(), 0, sd,
-                            p->d_sched_ptr.as<int32_t>(), p->d_sched_items.as<int32_t>(), y, R, gate, S.err,
-                            1.0 / pool.hscale);
+                    constexpr int NSH = RCT >= 16 ? APPLY_NS_H16 : APPLY_NS_H;
+                    k_apply_tma<float, RCT, NSH, APPLY_MINB, __half>
+                        <<<ctas, APPLY_THREADS, apply_smem_bytes(RCT, NSH, APPLY_CB / 2), st>>>(
+                            pool.hmaps.template as<CUtensorMap>(), xm, 0, sd, sptr, sitems, y, R, gate, S.err,
+                            1.0 / pool.hscale, nullptr, wait_tries(), p->dbg_withhold);
                     return;
                 }
             }
-            k_apply_tma<T, RCT><<<p->sched_ctas, APPLY_THREADS, apply_smem_bytes(RCT, APPLY_NS), st>>>(
-                pool.maps.template as<CUtensorMap>(), ws.xmaps[sizeof(T) == 8 ? 1 : 0].template as<CUtensorMap>(),
-                use_sp, sd, p->d_sched_ptr.as<int32_t>(), p->d_sched_items.as<int32_t>(), y, R, gate, S.err);
+            k_apply_tma<T, RCT><<<ctas, APPLY_THREADS, apply_smem_bytes(RCT, APPLY_NS), st>>>(
+                pool.maps.template as<CUtensorMap>(), xm, use_sp, sd, sptr, sitems, y, R, gate, S.err, 1.0, nullptr,
+                wait_tries(), p->dbg_withhold);
         };
         switch (rc) {
+            case 16:
+                if constexpr (sizeof(T) == 4) go(std::integral_constant<int, 16>{});
+                break;
             case 8: go(std::integral_constant<int, 8>{}); break;
             case 4: go(std::integral_constant<int, 4>{}); break;
             case 2: go(std::integral_constant<int, 2>{}); break;
@@ -1285,12 +1477,22 @@ struct Runner {
         }
     }
 
+    // x (apply layout) = B^T v, or B_D^T v with weights
+    template <typename T> void gather_x(const int64_t *ptr, const int64_t *row, const double *val, const double *v, T *x) {
+        const int64_t nu = p->n_u;
+        if (R <= GX_MAXR)
+            k_gather_apply_t<T><<<(unsigned)((nu + GX_U - 1) / GX_U), 256, sizeof(double) * GX_U * R, st>>>(
+                ptr, row, val, v, x, sd, p->d_u2sub.as<int32_t>(), nu, R, gate);
+        else
+            k_gather_apply<T><<<grid_for(nu * R), 256, 0, st>>>(ptr, row, val, v, x, sd, p->d_u2sub.as<int32_t>(), nu,
+                                                                R, gate);
+        note_launch();
+    }
+
     template <typename T> void applyF(const OpPool<T> &pool, const double *v, double *out, const double *cvec = nullptr) {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         T *x = ws.xU.as<T>();
-        k_gather_apply<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(),
-                                                            nullptr, v, x, sd, p->d_u2sub.as<int32_t>(), nu, R, gate);
-        note_launch();
+        if (nu > 0) gather_x<T>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), nullptr, v, x);
         symv<T>(pool, 1, x, ws.yU.as<double>());
         k_gather_b<<<grid_for(nl * R), 256, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), ws.yU.as<double>(),
                                                      cvec, out, nl, R);
@@ -1316,10 +1518,7 @@ struct Runner {
                 symv_mma(pool, ws.yU.as<double>());
             }
         } else {
-            k_gather_apply<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_BDt_ptr.as<int64_t>(), p->d_BDt_row.as<int64_t>(),
-                                                                p->d_BDt_val.as<double>(), v, x, sd,
-                                                                p->d_u2sub.as<int32_t>(), nu, R, gate);
-            note_launch();
+            if (nu > 0) gather_x<T>(p->d_BDt_ptr.as<int64_t>(), p->d_BDt_row.as<int64_t>(), p->d_BDt_val.as<double>(), v, x);
             symv<T>(pool, 0, x, ws.yU.as<double>(), precond);
         }
         k_gather_bd<<<grid_for(nl * R), 256, 0, st>>>(p->d_BD_ptr.as<int64_t>(), p->d_BD_col.as<int64_t>(),
@@ -1339,7 +1538,7 @@ struct Runner {
         // p, lambda, r updated; w = P r, ||w||, stop test
         if (p->n_co > 0) coarse_alpha(r, PG_LAM_R, q);
         auto check = [&](auto kern) {
-            kern<<<red_grid(nl, R), RED_THREADS, 0, st>>>(p->d_Gcol.as<int32_t>(), p->d_Gval.as<double>(), p->gw, alpha, y,
+            kern<<<tile_blocks(nl), RED_THREADS, 0, st>>>(p->d_Gcol.as<int32_t>(), p->d_Gval.as<double>(), p->gw, alpha, y,
                                                           pv, lam, r, q, w, nl, R, ws.partial.as<double>(), S, tol,
                                                           max_it, cond, max_it + 1);
         };
@@ -1350,12 +1549,17 @@ struct Runner {
         applyMinv<T>(pool, w, z, true);                          // z = M^-1 w
         project_dot<FIN_BETA>(z, w, y);                          // y = P z, (y, w), beta
         // q = F p_new, (p_new, q), eta
-        k_gather_apply_p<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), pv,
-                                                              y, S.beta, S.active, x, sd, p->d_u2sub.as<int32_t>(),
-                                                              nu, R, gate);
+        if (R <= GX_MAXR)
+            k_gather_apply_p_t<T><<<(unsigned)((nu + GX_U - 1) / GX_U), 256, sizeof(double) * GX_U * R, st>>>(
+                p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), pv, y, S.beta, S.active, x, sd,
+                p->d_u2sub.as<int32_t>(), nu, R, gate);
+        else
+            k_gather_apply_p<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(),
+                                                                  pv, y, S.beta, S.active, x, sd,
+                                                                  p->d_u2sub.as<int32_t>(), nu, R, gate);
         note_launch();
         symv<T>(pool, 1, x, yU);
-        k_gather_b_eta<<<red_grid(nl, R), RED_THREADS, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), yU, pv, y,
+        k_gather_b_eta<<<tile_blocks(nl), RED_THREADS, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), yU, pv, y,
                                                                q, nl, R, ws.partial.as<double>(), S);
         note_launch();
         gate = nullptr;
@@ -1367,9 +1571,13 @@ struct Runner {
         const int prec = std::is_same<T, float>::value ? 1 : 0;
         for (const auto &g : ws.graphs)
             if (g.kind == 0 && g.factor_gen == p->factor_gen && g.precision == prec && g.tol == tol &&
-                g.max_it == max_it && g.precond_fp16 == p->opt.precond_fp16)
+                g.max_it == max_it && g.precond_fp16 == p->opt.precond_fp16 && g.wait_tries == wait_tries() &&
+                g.withhold == p->dbg_withhold && g.tune_gen == p->tune_gen)
                 return g;
         PcgGraph g;
+        g.wait_tries = wait_tries();
+        g.withhold = p->dbg_withhold;
+        g.tune_gen = p->tune_gen;
         g.precond_fp16 = p->opt.precond_fp16;
         g.factor_gen = p->factor_gen;
         g.precision = prec;
@@ -1698,9 +1906,12 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     // buffers about to be replaced may still be read by queued work
     NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
     drop_graphs();
-    R = nR;
-    prob = p;
-    prob_uid = p->uid;
+    // marked complete only once every buffer below exists: a failed allocation leaves the
+    // workspace empty, so that the next call sizes it again
+    R = 0;
+    prob = nullptr;
+    prob_uid = 0;
+    const int R = nR;
     const int64_t nl = std::max<int64_t>(1, p->n_lambda), nu = std::max<int64_t>(1, p->n_u),
                   nv = std::max<int64_t>(1, p->sum_nk), nd = std::max<int64_t>(1, p->n_dofs_total);
     const int64_t nco = std::max(1, p->n_co);
@@ -1724,35 +1935,48 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     // tensor maps of xU per subdomain (R rows of ld_gamma entries at offUp * R), read as FP32
     // and as FP64, tiles of rc rows as the apply kernel of this R uses
     {
-        const int rcb = R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1));
+        const int rcb = apply_rc(R, 8);          // at most 8 (the FP64 pipeline and the residual)
         for (int e = 0; e < 2; ++e) {
             const int es = e ? 8 : 4;
-            std::vector<CUtensorMap> maps(std::max(1, p->K));
-            std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
-            for (int k = 0; k < p->K; ++k) {
-                const SubdomainDesc &d = p->sd[k];
-                if (d.nG == 0) continue;
-                const unsigned char *b = xU.as<unsigned char>() + d.offUp * R * es;
-                if (encode_apply_map(encode_tiled(), &maps[k], b, d.ldG, R, es, rcb) != CUDA_SUCCESS)
-                    fail(NLFETI_E_CUDA, "cuTensorMapEncodeTiled failed for the apply input");
+            for (int ri = 0; ri < 5; ++ri) {
+                const int rce = 1 << ri;
+                xmaps_rc[e][ri].release();
+                if (rce > R && rce > 1) continue;
+                if (e == 1 && rce > 8) continue;
+                std::vector<CUtensorMap> maps(std::max(1, p->K));
+                std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+                for (int k = 0; k < p->K; ++k) {
+                    const SubdomainDesc &d = p->sd[k];
+                    if (d.nG == 0) continue;
+                    const unsigned char *b = xU.as<unsigned char>() + d.offUp * R * es;
+                    if (encode_apply_map(encode_tiled(), &maps[k], b, d.ldG, R, es, rce) != CUDA_SUCCESS)
+                        fail(NLFETI_E_CUDA, "cuTensorMapEncodeTiled failed for the apply input");
+                }
+                alloc(xmaps_rc[e][ri], sizeof(CUtensorMap) * maps.size());
+                NLF_CUDA(cudaMemcpyAsync(xmaps_rc[e][ri].p, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                                         cudaMemcpyHostToDevice, async_stream ? async_stream : c->stream));
+                NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
+                if (rce == apply_rc(R, es)) {
+                    alloc(xmaps[e], sizeof(CUtensorMap) * maps.size());
+                    NLF_CUDA(cudaMemcpyAsync(xmaps[e].p, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                                             cudaMemcpyHostToDevice, async_stream ? async_stream : c->stream));
+                    NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
+                }
             }
-            alloc(xmaps[e], sizeof(CUtensorMap) * maps.size());
-            NLF_CUDA(cudaMemcpyAsync(xmaps[e].p, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
-                                     async_stream ? async_stream : c->stream));
-            NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
         }
         // the forcing / back-substitution right-hand sides (R rows of ld_M entries at offVp * R),
         // read as FP32 and as FP64, tiles of rcb rows
         alloc(rxs, sizeof(double) * std::max<int64_t>(1, p->n_vp) * R);
         for (int e = 0; e < 2; ++e) {
             const int es = e ? 8 : 4;
+            const int rce = apply_rc(R, es);
             std::vector<CUtensorMap> rm(std::max(1, p->K));
             std::memset(rm.data(), 0, sizeof(CUtensorMap) * rm.size());
             for (int k = 0; k < p->K; ++k) {
                 const SubdomainDesc &d = p->sd[k];
                 if (d.nk == 0) continue;
                 const unsigned char *b = rxs.as<unsigned char>() + d.offVp * R * es;
-                if (encode_apply_map(encode_tiled(), &rm[k], b, d.ldM, R, es, rcb) != CUDA_SUCCESS)
+                if (encode_apply_map(encode_tiled(), &rm[k], b, d.ldM, R, es, rce) != CUDA_SUCCESS)
                     fail(NLFETI_E_CUDA, "cuTensorMapEncodeTiled failed for the forcing input");
             }
             alloc(rxmaps[e], sizeof(CUtensorMap) * rm.size());
@@ -1800,12 +2024,16 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     A(ftil, nv); A(res, nv); A(u, nv); A(du, nv);
     A(F, nd);
     A(gco, nco * PSPLIT); A(gsum, nco); A(alpha, nco);
-    alloc(partial, sizeof(double) * RED_BLOCKS * R);
-    alloc(partial2, sizeof(double) * RED_BLOCKS * R);
+    alloc(partial, sizeof(double) * std::max(RED_BLOCKS, TILE_MAX_BLOCKS) * R);
+    alloc(partial2, sizeof(double) * std::max(RED_BLOCKS, TILE_MAX_BLOCKS) * R);
     alloc(scal, sizeof(double) * R * 7 + sizeof(int) * (2 * R + 8));
     alloc(slot_flags, sizeof(int) * kSlotFlags);
+    alloc(frozen, sizeof(int) * R);
     NLF_CUDA(cudaMemsetAsync(scal.p, 0, scal.bytes, async_stream ? async_stream : c->stream));
     host_flag.assign(4, 0);
+    this->R = nR;
+    prob = p;
+    prob_uid = p->uid;
 }
 
 void to_interleaved(const double *colmajor, double *inter, int64_t n, int R, cudaStream_t st) {
@@ -1856,6 +2084,11 @@ void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rh
         if (nl > 0) NLF_CUDA(cudaMemsetAsync(ws.lam.p, 0, sizeof(double) * nl * R, st));
         bool ok = false;
         std::vector<double> prev_corr;
+        // a right-hand side whose refinement has finished is frozen: its residual is zeroed
+        // before the later sweeps, so their corrections of it are exact zeros and its result
+        // is the one it would have alone (its sweeps depend on its own corrections only)
+        std::vector<int> frozen(R, 0);
+        bool any_frozen = false;
         for (int sw = 0; sw < std::max(1, p->opt.max_refine); ++sw) {
             if (sw == 0) {
                 NLF_CUDA(cudaMemcpyAsync(ws.res.p, ws.ftil.p, sizeof(double) * nv * R, cudaMemcpyDeviceToDevice, st));
@@ -1866,6 +2099,13 @@ void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rh
                                                                             p->d_u2v.as<int64_t>(), ws.u.as<double>(),
                                                                             ws.cvec.as<double>(), nl, R);
                 run.eager_launches += 1 + (nl > 0);
+                if (any_frozen) {
+                    NLF_CUDA(cudaMemcpyAsync(ws.frozen.p, frozen.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+                    k_zero_frozen<<<grid_for(nv * R), 256, 0, st>>>(ws.res.as<double>(), nv, R, ws.frozen.as<int>());
+                    if (nl > 0)
+                        k_zero_frozen<<<grid_for(nl * R), 256, 0, st>>>(ws.cvec.as<double>(), nl, R, ws.frozen.as<int>());
+                    run.eager_launches += 1 + (nl > 0);
+                }
             }
             run.pass<float>(p->op32, p->opt.inner_tol, p->opt.max_it, sw > 0);
             if (nl > 0) k_axpy<<<grid_for(nl * R), 256, 0, st>>>(ws.lam.as<double>(), ws.dlam.as<double>(), 1.0, nl * R);
@@ -1886,9 +2126,18 @@ void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rh
             // corrections still to come sum to about corr_k rho / (1 - rho)
             bool done = true;
             for (int c = 0; c < R; ++c) {
-                if (corr[c] <= p->opt.refine_tol) continue;
-                const double rho = prev_corr.empty() || prev_corr[c] <= 0 ? 1.0 : corr[c] / prev_corr[c];
-                if (!(rho < 0.5 && corr[c] * rho / (1.0 - rho) <= p->opt.refine_tol)) done = false;
+                if (frozen[c]) continue;
+                bool fin = corr[c] <= p->opt.refine_tol;
+                if (!fin) {
+                    const double rho = prev_corr.empty() || prev_corr[c] <= 0 ? 1.0 : corr[c] / prev_corr[c];
+                    fin = rho < 0.5 && corr[c] * rho / (1.0 - rho) <= p->opt.refine_tol;
+                }
+                if (fin) {
+                    frozen[c] = 1;
+                    any_frozen = true;
+                } else {
+                    done = false;
+                }
             }
             prev_corr = corr;
             if (done) { ok = true; break; }
@@ -1905,6 +2154,179 @@ void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rh
     NLF_CUDA(cudaGetLastError());
     run.eager_launches += 1;
     if (stats) *stats = s;
+}
+
+ApplyChoice apply_choice(const nlfeti_problem *p, int kind, int R) {
+    auto it = p->tune.find({kind, R});
+    if (it != p->tune.end()) return it->second;
+    ApplyChoice c;
+    c.rc = apply_rc(R, kind == 2 ? 8 : 4);
+    c.per_sm = 2;
+    return c;
+}
+
+int device_sms() {
+    int dev = 0, sms = 0;
+    NLF_CUDA(cudaGetDevice(&dev));
+    NLF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    return sms;
+}
+
+namespace {
+
+// key of a tuning result: the device, the subdomain operator shapes, the kind and R
+std::string tune_key(const nlfeti_problem *p, int kind, int R) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void *q, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(q);
+        for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+    };
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    mix(prop.name, strnlen(prop.name, sizeof(prop.name)));
+    mix(&prop.multiProcessorCount, sizeof(int));
+    mix(&kind, sizeof(kind));
+    mix(&R, sizeof(R));
+    for (const auto &d : p->sd) {
+        mix(&d.nG, sizeof(d.nG));
+        mix(&d.ldG, sizeof(d.ldG));
+    }
+    char buf[32];
+    snprintf(buf, sizeof(buf), "%016llx", (unsigned long long)h);
+    return buf;
+}
+
+struct CacheLine {
+    std::string key;
+    int kind = 0, R = 0, rc = 0, per_sm = 0;
+    double us = 0;
+};
+
+// the cache: {"entries": [ one object per line ]}
+std::vector<CacheLine> read_tune_cache(const char *path) {
+    std::vector<CacheLine> out;
+    FILE *f = path ? fopen(path, "r") : nullptr;
+    if (!f) return out;
+    char line[512];
+    while (fgets(line, sizeof(line), f)) {
+        CacheLine c;
+        char key[64] = {0};
+        if (sscanf(line, " {\"key\": \"%63[0-9a-f]\", \"kind\": %d, \"R\": %d, \"rc\": %d, \"ctas_per_sm\": %d, \"us\": %lf",
+                   key, &c.kind, &c.R, &c.rc, &c.per_sm, &c.us) == 6) {
+            c.key = key;
+            out.push_back(c);
+        }
+    }
+    fclose(f);
+    return out;
+}
+
+void write_tune_cache(const char *path, const std::vector<CacheLine> &v) {
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    fprintf(f, "{\"entries\": [\n");
+    for (size_t i = 0; i < v.size(); ++i)
+        fprintf(f, "  {\"key\": \"%s\", \"kind\": %d, \"R\": %d, \"rc\": %d, \"ctas_per_sm\": %d, \"us\": %.3f}%s\n",
+                v[i].key.c_str(), v[i].kind, v[i].R, v[i].rc, v[i].per_sm, v[i].us, i + 1 < v.size() ? "," : "");
+    fprintf(f, "]}\n");
+    fclose(f);
+    std::rename(tmp.c_str(), path);
+}
+
+}  // namespace
+
+void autotune_applies(nlfeti_problem *p, int R, const char *cache_path, std::vector<TuneEntry> &out) {
+    out.clear();
+    if (p->n_u == 0 || p->sched_ctas == 0) return;
+    if (!p->ws) p->ws.reset(new SolveWS());
+    SolveWS &ws = *p->ws;
+    cudaStream_t st = p->ctx->stream;
+    ws.ensure(p, R);
+    NLF_CUDA(cudaMemsetAsync(ws.xU.p, 0, ws.xU.bytes, st));
+    std::vector<CacheLine> cache = read_tune_cache(cache_path);
+    const int saved_batched = p->opt.batched, saved_fp16 = p->opt.precond_fp16;
+    p->opt.batched = 1;
+    bool changed = false;
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    NLF_CUDA(cudaEventCreate(&ea));
+    NLF_CUDA(cudaEventCreate(&eb));
+    try {
+        Runner run(p, ws, st);
+        for (int kind = 0; kind < 3; ++kind) {
+            if (kind < 2 && !p->op32.ready) continue;
+            if (kind == 1 && !p->op32.Sh.p) continue;
+            if (kind == 2 && !p->op64.ready) continue;
+            TuneEntry te;
+            te.kind = kind;
+            te.R = R;
+            const std::string key = tune_key(p, kind, R);
+            for (const auto &c : cache)
+                if (c.key == key && c.kind == kind && c.R == R) {
+                    te.rc = c.rc;
+                    te.per_sm = c.per_sm;
+                    te.us = c.us;
+                    te.from_cache = true;
+                }
+            if (!te.from_cache) {
+                p->opt.precond_fp16 = kind == 1 ? 1 : saved_fp16;
+                double best = 1e30;
+                for (int rc = 1; rc <= 16; rc *= 2) {
+                    if (rc > R && rc > 1) break;
+                    if (kind == 2 && rc > 8) break;
+                    for (int per_sm = 1; per_sm <= 2; ++per_sm) {
+                        p->tune[{kind, R}] = ApplyChoice{rc, per_sm};
+                        auto launch = [&] {
+                            if (kind == 0) run.symv<float>(p->op32, 1, ws.xU.as<float>(), ws.yU.as<double>());
+                            else if (kind == 1) run.symv<float>(p->op32, 0, ws.xU.as<float>(), ws.yU.as<double>(), true);
+                            else run.symv<double>(p->op64, 1, ws.xU.as<double>(), ws.yU.as<double>());
+                        };
+                        launch();
+                        NLF_CUDA(cudaEventRecord(ea, st));
+                        for (int r = 0; r < 3; ++r) launch();
+                        NLF_CUDA(cudaEventRecord(eb, st));
+                        NLF_CUDA(cudaEventSynchronize(eb));
+                        float ms = 0.f;
+                        NLF_CUDA(cudaEventElapsedTime(&ms, ea, eb));
+                        const double us = 1e3 * ms / 3.0;
+                        if (us < best) {
+                            best = us;
+                            te.rc = rc;
+                            te.per_sm = per_sm;
+                            te.us = us;
+                        }
+                    }
+                }
+                run.check_waits_now();
+                CacheLine c;
+                c.key = key;
+                c.kind = kind;
+                c.R = R;
+                c.rc = te.rc;
+                c.per_sm = te.per_sm;
+                c.us = te.us;
+                cache.push_back(c);
+                changed = true;
+            }
+            p->tune[{kind, R}] = ApplyChoice{te.rc, te.per_sm};
+            out.push_back(te);
+        }
+    } catch (...) {
+        p->opt.batched = saved_batched;
+        p->opt.precond_fp16 = saved_fp16;
+        ++p->tune_gen;
+        cudaEventDestroy(ea);
+        cudaEventDestroy(eb);
+        throw;
+    }
+    p->opt.batched = saved_batched;
+    p->opt.precond_fp16 = saved_fp16;
+    ++p->tune_gen;
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+    if (changed && cache_path) write_tune_cache(cache_path, cache);
 }
 
 void apply_operator(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int op, int precision, int R, const double *in,
@@ -2015,17 +2437,20 @@ int apply_tma_ctas() {
         per_sm = std::min(per_sm, b);
     };
     fit(k_apply_tma<float, 1>, 1); fit(k_apply_tma<float, 2>, 2); fit(k_apply_tma<float, 4>, 4);
-    fit(k_apply_tma<float, 8>, 8); fit(k_apply_tma<double, 1>, 1); fit(k_apply_tma<double, 2>, 2);
+    fit(k_apply_tma<float, 8>, 8); fit(k_apply_tma<float, 16>, 16);
+    fit(k_apply_tma<double, 1>, 1); fit(k_apply_tma<double, 2>, 2);
     fit(k_apply_tma<double, 4>, 4); fit(k_apply_tma<double, 8>, 8);
     // the forcing and back-substitution modes (same pipeline and shared memory)
     fit(k_apply_tma<float, 1, APPLY_NS, APPLY_MINB, float, ROWS_FORCING>, 1);
     fit(k_apply_tma<float, 2, APPLY_NS, APPLY_MINB, float, ROWS_FORCING>, 2);
     fit(k_apply_tma<float, 4, APPLY_NS, APPLY_MINB, float, ROWS_FORCING>, 4);
     fit(k_apply_tma<float, 8, APPLY_NS, APPLY_MINB, float, ROWS_FORCING>, 8);
+    fit(k_apply_tma<float, 16, APPLY_NS, APPLY_MINB, float, ROWS_FORCING>, 16);
     fit(k_apply_tma<float, 1, APPLY_NS, APPLY_MINB, float, ROWS_BACKSUB>, 1);
     fit(k_apply_tma<float, 2, APPLY_NS, APPLY_MINB, float, ROWS_BACKSUB>, 2);
     fit(k_apply_tma<float, 4, APPLY_NS, APPLY_MINB, float, ROWS_BACKSUB>, 4);
     fit(k_apply_tma<float, 8, APPLY_NS, APPLY_MINB, float, ROWS_BACKSUB>, 8);
+    fit(k_apply_tma<float, 16, APPLY_NS, APPLY_MINB, float, ROWS_BACKSUB>, 16);
     fit(k_apply_tma<double, 1, APPLY_NS, APPLY_MINB, double, ROWS_FORCING>, 1);
     fit(k_apply_tma<double, 2, APPLY_NS, APPLY_MINB, double, ROWS_FORCING>, 2);
     fit(k_apply_tma<double, 4, APPLY_NS, APPLY_MINB, double, ROWS_FORCING>, 4);
@@ -2043,6 +2468,14 @@ int apply_tma_ctas() {
     };
     fit_h(k_apply_tma<float, 1, APPLY_NS_H, APPLY_MINB, __half>, 1); fit_h(k_apply_tma<float, 2, APPLY_NS_H, APPLY_MINB, __half>, 2);
     fit_h(k_apply_tma<float, 4, APPLY_NS_H, APPLY_MINB, __half>, 4); fit_h(k_apply_tma<float, 8, APPLY_NS_H, APPLY_MINB, __half>, 8);
+    {
+        const int smem = apply_smem_bytes(16, APPLY_NS_H16, APPLY_CB / 2);
+        auto kern = k_apply_tma<float, 16, APPLY_NS_H16, APPLY_MINB, __half>;
+        NLF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int b = 0;
+        NLF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, APPLY_THREADS, smem));
+        per_sm = std::min(per_sm, b);
+    }
     if (per_sm < 1) fail(NLFETI_E_CUDA, "the interface apply does not fit on an SM");
     return sms * per_sm;
 }

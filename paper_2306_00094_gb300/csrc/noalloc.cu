@@ -18,7 +18,11 @@
 //
 // Set-up: the first call on a device, with that device current, resolves the array's address
 // with cudaGetSymbolAddress (once per device, under a lock) and every later call reuses it.
-// A caller that captures streams should make that first call before capturing.
+// A caller that captures streams should make that first call before capturing.  A call made
+// with another device current than the one the problem's context was created on is rejected
+// (NLFETI_E_INVALID): its operators live on that device.  The resolved address stays valid for
+// the life of the process's primary context on the device; a caller that resets the device
+// (cudaDeviceReset) has destroyed its problems with it and does not call this again.
 #include <mutex>
 #include <string>
 #include <type_traits>
@@ -42,10 +46,14 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 void *g_scratch_ptr[kMaxDevices] = {};
 
-// address of the scratch array on the current device (resolved once per device)
-void *scratch_for_current_device() {
+// address of the scratch array on the problem's device, which must be the current one (resolved
+// once per device)
+void *scratch_for_device(const nlfeti_problem *p) {
     int dev = 0;
     NLF_CUDA(cudaGetDevice(&dev));
+    if (dev != p->ctx->device)
+        fail(NLFETI_E_INVALID, "the no-allocation apply must be called with the problem's device current (device " +
+                                   std::to_string(p->ctx->device) + ", current " + std::to_string(dev) + ")");
     if (dev < 0 || dev >= kMaxDevices) fail(NLFETI_E_INVALID, "device ordinal out of range for the no-allocation apply");
     std::lock_guard<std::mutex> g(g_scratch_mu);
     if (!g_scratch_ptr[dev]) {
@@ -167,7 +175,7 @@ extern "C" nlfeti_status nlfeti_apply_schur_noalloc(nlfeti_problem *p, int which
         if ((precision == 0 && !p->op64.ready) || (precision == 1 && !p->op32.ready))
             fail(NLFETI_E_INVALID, "operators of the requested precision are not factored");
         if (p->n_u == 0 || p->n_items == 0) return NLFETI_OK;
-        void *scratch = scratch_for_current_device();
+        void *scratch = scratch_for_device(p);
         stream_enter(p->ctx);
         try {
             if (precision == 0) apply_noalloc<double>(p, p->op64, which == 0 ? 1 : 0, nrhs, d_in, d_out, scratch);

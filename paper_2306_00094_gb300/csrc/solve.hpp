@@ -15,6 +15,9 @@ struct PcgGraph {
     int64_t body_launches = 0;      // kernels per loop iteration
     int precond_fp16 = 0;           // the preconditioner apply it was captured with
     int kind = 0;                   // 0: FETI PCG loop, 1: single-domain CG loop
+    long long wait_tries = 0;       // the apply's stage-wait limit and withheld copies it was
+    int withhold = 0;               // captured with (fault injection for tests)
+    uint64_t tune_gen = 0;          // the apply configurations it was captured with
 };
 
 constexpr int kSlotFlags = 1024;   // flag words of the timed applies: half for graphs, half eager
@@ -25,7 +28,10 @@ struct SolveWS {
     int R = 0;
     DevMem lam, r, w, z, y, pv, q, d, cvec, dlam;      // Lambda space (FP64)
     DevMem fU, yU, uU, xU;                              // U space
-    DevMem xmaps[2];                                    // tensor maps of xU per subdomain (FP32, FP64)
+    DevMem xmaps[2];                                    // tensor maps of xU per subdomain (FP32, FP64),
+                                                        // tiles of the default column block apply_rc(R)
+    DevMem xmaps_rc[2][5];                              // the same for column blocks 1, 2, 4, 8, 16 (the
+                                                        // autotuner's choices; 16 for FP32 only)
     DevMem xhmaps;                                      // xU read as FP16 (tensor-core apply; R <= 64)
     DevMem xscale;                                      // per column: power of two x is scaled by (FP16 x)
     DevMem slot_flags;                                  // gates seen by the timed applies (profiling)
@@ -38,6 +44,7 @@ struct SolveWS {
     DevMem F;                                           // global load vector per dof
     DevMem gco, gsum, alpha;                            // coarse space
     DevMem partial, partial2, scal;                     // reductions and PCG scalars
+    DevMem frozen;                                      // per column: refinement finished (mixed path)
     DevMem in_rhs, in_g, out_u;                         // staging for host-array solves
     DevMem cg_u, cg_r, cg_z, cg_p, cg_q, cg_b, cg_part;  // single-domain CG (global dofs x R)
     DevMem cg_ph, cg_pl;                                // p as FP32 hi / lo pairs (SpMV operand)
@@ -64,6 +71,18 @@ void cg_solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int
 // Apply one operator (0 F, 1 M^-1, 2 P, 3 S^+, 4 S) to device vectors in the interleaved layout.
 void apply_operator(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int op, int precision, int R, const double *in,
                     double *out);
+
+// Autotuner of the bulk-copy interface apply for R right-hand sides: per operator kind the
+// problem has (FP32 S^+, FP16 copy of S_k, FP64 S^+), every column block 1..16 (<= R) and one or
+// two CTAs per SM, timed with CUDA events on the problem's operators; the fastest is kept in
+// the problem.  With a cache path, choices found there (same device, subdomain shapes, kind and
+// R) are used without timing, and new ones are written back (JSON).
+struct TuneEntry {
+    int kind = 0, R = 0, rc = 0, per_sm = 0;
+    double us = 0;
+    bool from_cache = false;
+};
+void autotune_applies(nlfeti_problem *p, int R, const char *cache_path, std::vector<TuneEntry> &out);
 
 // Interleaved <-> column-major conversions (device).
 void to_interleaved(const double *colmajor, double *inter, int64_t n, int R, cudaStream_t st);

@@ -14,7 +14,8 @@
 //
 // Pivot blocks are NB = 64 wide; a step is three launches over all subdomains: invert
 // the pivot block (one CTA per subdomain, in shared memory), form the pivot panels,
-// update all tiles (64x64 CTA tiles, 4x4 register blocking).  A non-positive pivot
+// update all tiles (FP32 operators: 128x128 tiles on the tensor cores, split-TF32, in
+// sweep_tc.cuh; FP64 operators: 64x64 CTA tiles, 4x4 register blocking).  A non-positive pivot
 // sets the device status word (NLFETI_E_NOT_SPD) instead of trapping.
 #include <algorithm>
 #include <type_traits>
@@ -178,6 +179,8 @@ template <typename T> __global__ void __launch_bounds__(256) k_update(SweepArgs<
         }
     }
 }
+
+#include "sweep_tc.cuh"
 
 // copy A^k (FP64, ld = nk) into the swept-matrix pool (type T, ld = ldM, zero padding)
 template <typename T> __global__ void k_load_matrix(const double *A, T *Mpool, const SubdomainDesc *sd) {
@@ -435,10 +438,20 @@ template <typename T> void run_sweeps(nlfeti_problem *p, T *pool, const std::vec
     const int nt = (maxn + TILE - 1) / TILE;
     const size_t smu = sizeof(T) * 2 * NB * TILE;
     NLF_CUDA(cudaFuncSetAttribute(k_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smu));
+    // FP32 operators with factor_tc: the rank-64 updates on the tensor cores (split-TF32)
+    const bool tc = std::is_same<T, float>::value && p->opt.factor_tc == 1;
+    const int ntc = (maxn + TC_TILE - 1) / TC_TILE;
+    if (tc) NLF_CUDA(cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     for (int j0 = 0; j0 < maxp; j0 += NB) {
         a.j0 = j0;
         k_pivot<T><<<K, 256, 0, c->stream>>>(a);
         k_panel<T><<<dim3((maxn + 3) / 4, K), 256, 0, c->stream>>>(a);
+        if constexpr (std::is_same<T, float>::value) {
+            if (tc) {
+                k_update_tc<<<dim3(ntc, ntc, K), TC_THREADS, TC_SMEM, c->stream>>>(a, p->d_flag.as<int>() + 2);
+                continue;
+            }
+        }
         k_update<T><<<dim3(nt, nt, K), 256, smu, c->stream>>>(a);
     }
     NLF_CUDA(cudaGetLastError());
@@ -464,6 +477,7 @@ void build_tiled_half(nlfeti_problem *p) {
 template <typename T> void factor_ops(nlfeti_problem *p, OpPool<T> &pool) {
     nlfeti_ctx *c = p->ctx;
     const int K = p->K;
+    pool.ready = false;          // until this factorization has succeeded
     int64_t poolM = p->poolM, poolG = p->poolG;
     pool.M.alloc(c, sizeof(T) * std::max<int64_t>(poolM, 1));
     pool.S.alloc(c, sizeof(T) * std::max<int64_t>(poolG, 1));
@@ -520,9 +534,13 @@ template <typename T> void factor_ops(nlfeti_problem *p, OpPool<T> &pool) {
         }
     }
     NLF_CUDA(cudaStreamSynchronize(c->stream));
-    int flag = 0;
-    NLF_CUDA(cudaMemcpy(&flag, p->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag) fail(NLFETI_E_NOT_SPD, "a pivot block of a subdomain operator was not positive definite");
+    int flag[3] = {0, 0, 0};
+    NLF_CUDA(cudaMemcpy(flag, p->d_flag.p, sizeof(flag), cudaMemcpyDeviceToHost));
+    if (flag[2]) {
+        NLF_CUDA(cudaMemset(p->d_flag.as<int>() + 2, 0, sizeof(int)));
+        fail(NLFETI_E_TIMEOUT, "a tensor-core update of the factorization did not complete in time");
+    }
+    if (flag[0]) fail(NLFETI_E_NOT_SPD, "a pivot block of a subdomain operator was not positive definite");
     if constexpr (std::is_same<T, float>::value) {
         // FP16 copy of S_k for the preconditioner, scaled by one power of two so that the
         // largest entry lies in [2^13, 2^14) (FP16 keeps 11 bits from 2^-14 up to 65504)

@@ -1,4 +1,6 @@
-"""The no-allocation interface apply (nlfeti_apply_schur_noalloc) against nlfeti_apply.
+"""The no-allocation interface apply (nlfeti_apply_schur_noalloc) against nlfeti_apply and
+against the FP64 oracle's S_k^+ (pinned Neumann solve, Sec. 5.3) and S_k (Dirichlet solve,
+eq. subSchurComplement) applied to the same vectors.
 
 The file name makes pytest collect it last: it has to pass in a fresh process and after every
 other GPU test, since all its calls on a device share the library's scratch array.  Each
@@ -9,6 +11,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from oracle import feti as ofeti
 
 pytestmark = pytest.mark.gpu
 
@@ -21,21 +24,25 @@ def setup():
     w = W.const_l2_2d(N=24, k=3, nrhs=3, delta=0.1)
     p = binding.Problem.from_workload(ctx, w)
     p.factor(3)
-    yield torch, binding, p
+    o = ofeti.Feti(w.mesh, w.kernel, w.labels, w.K)
+    yield torch, binding, p, o
     p.close()
 
 
 @pytest.mark.parametrize("R", [1, 3, 9])
 def test_noalloc_apply_matches_apply(setup, R):
-    torch, binding, p = setup
+    torch, binding, p, o = setup
     n_u = p.info()["n_u"]
     rng = np.random.default_rng(100 + R)
     X = rng.standard_normal((n_u, R))
     d_in = torch.from_numpy(np.ascontiguousarray(X.T)).cuda()      # column-major n_u x R
-    for precision, tol in ((0, 1e-12), (1, 1e-6)):
+    oracle_ref = {0: o.S_plus(X), 1: o.S(X)}
+    for precision, tol, otol in ((0, 1e-12, 1e-9), (1, 1e-6, 1e-3)):
         for which, op in ((0, 3), (1, 4)):                          # S^+ and S
             ref = p.apply(op, precision, X)
             scale = np.abs(ref).max()
+            oref = oracle_ref[which]
+            assert np.abs(ref - oref).max() <= otol * np.abs(oref).max()
             for _ in range(2):
                 d_out = torch.full_like(d_in, float("nan"))
                 p.apply_schur_noalloc(which, precision, d_in, d_out, R)
@@ -43,10 +50,11 @@ def test_noalloc_apply_matches_apply(setup, R):
                 got = d_out.cpu().numpy().T
                 assert np.isfinite(got).all()
                 assert np.abs(got - ref).max() <= tol * scale, (precision, which, R)
+                assert np.abs(got - oref).max() <= otol * np.abs(oref).max(), (precision, which, R)
 
 
 def test_noalloc_apply_rejects_oversize(setup):
-    torch, binding, p = setup
+    torch, binding, p, o = setup
     d = torch.zeros(8, dtype=torch.float64, device="cuda")
     code = p.apply_schur_noalloc(0, 0, d, d, 10 ** 6, raise_on_error=False)
     assert code == binding.E_INVALID
