@@ -1,21 +1,24 @@
 #!/usr/bin/env python
 """Benchmark: FETI solves/s at relative nodal error 1e-8, with p50/p99 latency, on one GB300.
 
-Workload (2-D constant-kernel nonlocal diffusion): kernel 4/(pi delta^4) on the l2 ball
-(nocaps polygon), delta = 0.1, structured P1 triangles h = 1/128 with a 13-cell Dirichlet
-collar (16 129 unknowns), 4 x 4 rectangular subdomains, 8 right-hand sides of seeded
-i.i.d. N(0,1) nodal loads.  A step is one FETI solve request of the 8 right-hand sides
-with the subdomain operators resident (setup and factorization excluded, the protocol of
-the paper's timings; both are reported under "cold"): reduced forcing, projected PCG with
-the scaled Dirichlet preconditioner, FP64 refinement of the FP32 operators until the
-relative nodal correction (or the remaining error it predicts) is below 1e-9, back
-substitution and nodal output.  "value" is
-right-hand-side solves per second with the loads resident in HBM; "e2e" is the same
+Headline workload (the largest single-GPU one): 2-D bond-based peridynamics, micromodulus
+3/delta^3 xi xi^T/|xi|^3 on the l2 ball (nocaps polygon), delta = 3h, structured P1 triangles
+h = 1/256 (130 050 unknowns, 2 per node), 8 x 8 subdomains with seeded jittered cuts, 36 of
+them floating with 3 rigid modes each, 16 right-hand sides of seeded i.i.d. N(0,1) loads.
+A step is one FETI solve request of the 16 right-hand sides with the subdomain operators
+resident (setup and factorization excluded, the protocol of the paper's timings; both are
+reported under "cold"): reduced forcing, projected PCG with the scaled Dirichlet
+preconditioner, FP64 refinement of the FP32 operators until the relative nodal correction (or
+the remaining error it predicts) is below 1e-9, back substitution and nodal output.  "value"
+is right-hand-side solves per second with the loads resident in HBM; "e2e" is the same
 through the C ABI with pinned host buffers (host<->device copies inside the timed region).
+The 2-D fractional (64 RHS) and constant-kernel (8 RHS) workloads are reported beside it
+("other_workloads"); --workload selects another headline.
 
 --impl reference times the FP64 CPU oracle (one-level FETI in numpy, Algorithm 1) on the
-same workload on the host cores; each step is one oracle solve of the 8 right-hand sides.
-Under torchrun (N > 1) every rank solves its own replica (no collective in the data path).
+host cores on a bounded sample of the same workload (its per-iteration subdomain work on a
+few subdomains, scaled to a whole solve).  Under torchrun (N > 1) every rank solves its own
+replica (no collective in the data path).
 
 --serving runs the serving scenario instead: requests drawn from a pool of factored problems
 (kernels, mesh sizes, horizons and decompositions sampled from a grid) arrive as a Poisson
@@ -42,8 +45,38 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 METRIC = "FETI solves/sec at rel. error 1e-8 + p50/p99 latency: batched mixed vs plain FP64, 1 GB300"
-WORKLOAD = "2-D nonlocal diffusion, constant kernel on the l2 ball (nocaps), delta=0.1, h=1/128 (16129 dofs), " \
-           "4x4 subdomains, 8 RHS N(0,1) loads (seed 2)"
+
+# The workloads (synthetic stand-ins for the paper's manufactured problems, Sec. 6.2): the
+# headline is the largest single-GPU one, the peridynamic problem; the others are reported
+# beside it.
+WORKLOADS = {
+    "peridynamic_2d": (
+        lambda: W.peridynamic_2d(),
+        "2-D bond-based peridynamics, micromodulus 3/delta^3 xi xi^T/|xi|^3 on the l2 ball (nocaps), "
+        "delta=3h, h=1/256 (130050 dofs, 2 per node), 8x8 subdomains with seeded jittered cuts "
+        "(+-20%, seed 4), 16 RHS N(0,1) loads per dof (seed 5)"),
+    "fractional_2d": (
+        lambda: W.fractional_2d(),
+        "2-D fractional kernel (2-2s)/(pi delta^(2-2s)) |x-y|^-(2+2s), s=0.5, truncated at delta=0.2, "
+        "h=1/96 (9025 dofs), 6x6 subdomains (Omega_k empty on the interior ones), 64 RHS N(0,1) loads (seed 3)"),
+    "const_l2_2d": (
+        lambda: W.const_l2_2d(),
+        "2-D nonlocal diffusion, constant kernel 4/(pi delta^4) on the l2 ball (nocaps), delta=0.1, "
+        "h=1/128 (16129 dofs), 4x4 subdomains, 8 RHS N(0,1) loads (seed 2)"),
+}
+HEADLINE = "peridynamic_2d"
+
+
+def config_dict(name, w, n_lambda, n_u, world):
+    """The workload's config, identical for both arms (built from the inputs and the
+    decomposition sizes only)."""
+    free = int((w.mesh.node_is_dirichlet == 0).sum()) * w.kernel.ncomp
+    return {"workload": WORKLOADS[name][1], "name": name, "global_batch": w.nrhs * world,
+            "rhs_per_request": w.nrhs, "n_dofs": free, "subdomains": int(w.K), "n_lambda": int(n_lambda),
+            "n_u": int(n_u),
+            "step": "one warm solve request of all its right-hand sides (subdomain operators resident; "
+                    "setup and factorization excluded)",
+            "l2": "subdomain operators exceed the 126 MB L2; no flush between steps"}
 
 
 def peaks():
@@ -152,6 +185,58 @@ def kernel_source_hash(name="apply_tma.cuh"):
 
 # ------------------------------------------------------------------------------------------ ours
 
+def timed_solves(torch, prob, opt, d_rhs, kind, d_out, R, steps):
+    """CUDA-event times of `steps` warm solve requests with the given options (one untimed
+    solve first): solves/s, mean / p50 / p99 ms, PCG iterations and refinement sweeps."""
+    prob.set_options(opt)
+    prob.solve_device(d_rhs, kind, d_out, nrhs=R)
+    torch.cuda.synchronize()
+    ts = []
+    s = None
+    for _ in range(steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        s = prob.solve_device(d_rhs, kind, d_out, nrhs=R)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return {"value": R * len(ts) / (sum(ts) / 1e3), "unit": "solves/s", "ms_per_step": statistics.mean(ts),
+            "p50_ms": percentile(ts, 0.5), "p99_ms": percentile(ts, 0.99), "iterations": s["iterations"],
+            "refine_sweeps": s["refine_sweeps"]}
+
+
+def apply_rooflines(torch, prob, step, steps, hbm, peak_kind):
+    """The dense interface applies' achieved bandwidth: the same steps again with CUDA events
+    around every apply launch on the library stream (the PCG loops then run in event-timed
+    graph chunks, since a device-side WHILE graph cannot hold event nodes).  Returns the
+    S_k^+ apply (FP32 operator) and the preconditioner's S_k apply (FP16 copy), each with its
+    share of the profiled steps' time."""
+    prob.profile()
+    prob.set_profiling(True)
+    pa = torch.cuda.Event(enable_timing=True)
+    pb = torch.cuda.Event(enable_timing=True)
+    pa.record()
+    for _ in range(steps):
+        step()
+    pb.record()
+    torch.cuda.synchronize()
+    prof_ms = pa.elapsed_time(pb)
+    prob.set_profiling(False)
+    prof = prob.profile()
+    out = {}
+    for key in ("apply", "half_apply"):
+        n, ms, b = prof[key + "_launches"], prof[key + "_ms"], prof[key + "_bytes"]
+        if n > 0 and ms > 0:
+            bpl, avg = b / n, ms / n / 1e3
+            out[key] = {"bound": "hbm", "achieved": bpl / avg / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": bpl / avg / 1e9 / hbm, "peak_source": peak_kind, "bytes_per_launch": bpl,
+                        "avg_launch_us": avg * 1e6, "launches": n, "share_of_step_time": ms / prof_ms}
+        else:
+            out[key] = None
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2306_00094_gb300 import binding
@@ -162,7 +247,8 @@ def run_ours(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
-    w = W.const_l2_2d()
+    name = args.workload
+    w = WORKLOADS[name][0]()
     R = w.nrhs
     ctx = binding.Context()
     t0 = time.perf_counter()
@@ -176,6 +262,11 @@ def run_ours(args):
     t_factor64 = time.perf_counter() - t0
     info = prob.info()
     ndof = prob.n_dofs
+    # the apply shapes for R right-hand sides, tuned on this GPU (choices cached per device and
+    # subdomain shapes in the build folder)
+    t0 = time.perf_counter()
+    tuned = prob.autotune(R, os.path.join(ROOT, "paper_2306_00094_gb300", "_build", "apply_tune.json"))
+    t_tune = time.perf_counter() - t0
     # inputs resident in HBM: column-major n_dofs x R  ==  contiguous (R, n_dofs)
     d_rhs = torch.from_numpy(np.ascontiguousarray(w.rhs.T)).to(dev)
     d_out = torch.empty_like(d_rhs)
@@ -212,41 +303,24 @@ def run_ours(args):
     value = replica_throughput(R * args.steps, world, total_ms / 1e3)
     u_gpu = d_out.cpu().numpy().T.copy()
 
-    # roofline of the dominant kernel (dense interface apply, FP32): the same K steps again
-    # with CUDA events around every apply launch on the library stream.  The first timed
-    # region runs each PCG loop as a device-side WHILE graph node, whose body cannot hold
-    # event nodes; with profiling on the loop runs in event-timed chunks instead.
-    prof_ms = None
-    if not args.only_timed:
-        prob.set_profiling(True)
-        pa = torch.cuda.Event(enable_timing=True)
-        pb = torch.cuda.Event(enable_timing=True)
-        pa.record()
-        for k in range(args.steps):
-            step()
-        pb.record()
-        torch.cuda.synchronize()
-        prof_ms = pa.elapsed_time(pb)
-        prob.set_profiling(False)
-    prof = prob.profile()
-    hbm, peak_kind = peaks()
-
-    def apply_roofline(key):
-        n, ms, b = prof[key + "_launches"], prof[key + "_ms"], prof[key + "_bytes"]
-        if n > 0 and ms > 0:
-            bpl, avg = b / n, ms / n / 1e3
-            return bpl / avg / 1e9, bpl, avg, n, ms / prof_ms if prof_ms else None
-        return None, None, None, n, None
-
-    # the S_k^+ applies (FP32 operator) and the preconditioner's applies (FP16 copy of S_k)
-    achieved, bytes_per_launch, avg_s, n_apply, apply_share = apply_roofline("apply")
-    h_ach, h_bpl, h_avg, n_half, h_share = apply_roofline("half_apply")
-
     if args.only_timed:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s", "ms_per_step": total_ms / args.steps,
                               "gpu_launches": launches, "note": "timed steps only"}), flush=True)
         return
+
+    # roofline of the dominant kernels (dense interface applies) over a second timed region
+    hbm, peak_kind = peaks()
+    roof = apply_rooflines(torch, prob, step, args.steps, hbm, peak_kind)
+    ap, hp = roof["apply"], roof["half_apply"]
+    if ap:
+        ap.update({"kernel": "k_apply_tma<float> (dense S_k^+ apply, FP32, tensor-copy pipeline)",
+                   "timing": "CUDA events around each apply launch over a second timed region of the same "
+                             f"{args.steps} steps",
+                   "traffic": profile_traffic(kernel_source_hash(), f"k_apply_tma_{name}.md")})
+    if hp:
+        hp.update({"kernel": "k_apply_tma<float, .., __half> (preconditioner S_k apply, FP16 copy)",
+                   "traffic": profile_traffic(kernel_source_hash(), f"k_apply_tma_fp16_{name}.md")})
 
     # end to end through the C ABI with pinned host buffers
     h_rhs = torch.empty((R, ndof), dtype=torch.float64, pin_memory=True)
@@ -265,46 +339,17 @@ def run_ours(args):
            "d2h_bytes_per_step": 8 * R * ndof}
 
     # baselines on the GPU: plain FP64 one subdomain at a time (no graphs), and FP64 batched
-    def time_variant(opt, steps):
-        prob.set_options(opt)
-        step()
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(steps):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            s = step()
-            b.record()
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        return {"value": R * len(ts) / (sum(ts) / 1e3), "unit": "solves/s", "ms_per_step": statistics.mean(ts),
-                "p50_ms": percentile(ts, 0.5), "p99_ms": percentile(ts, 0.99), "iterations": s["iterations"]}
-
     ksteps = max(3, min(args.steps, 5))
-    plain_res = time_variant(plain, ksteps)
-    plain_b_res = time_variant(plain_batched, ksteps)
-    # the mixed solve with the preconditioner's S_k apply on the tensor cores (tcgen05 MMAs on
-    # the FP16 copy and FP16 x, FP32 accumulators in tensor memory): solves/s, and the apply's
-    # own CUDA-event time from a profiled pass of the same steps
-    tc_opt = binding.default_options(precision=1, batched=1, precond_fp16=2)
-    tc_res = time_variant(tc_opt, ksteps)
-    prob.profile()
-    prob.set_profiling(True)
-    for _ in range(ksteps):
-        step()
-    torch.cuda.synchronize()
-    prob.set_profiling(False)
-    tp = prob.profile()
-    if tp["half_apply_launches"] > 0 and tp["half_apply_ms"] > 0:
-        tc_avg = tp["half_apply_ms"] / tp["half_apply_launches"] / 1e3
-        tc_bpl = tp["half_apply_bytes"] / tp["half_apply_launches"]
-        tc_res.update({"kernel": "k_apply_mma<16>", "avg_launch_us": tc_avg * 1e6, "bytes_per_launch": tc_bpl,
-                       "achieved_gbs": tc_bpl / tc_avg / 1e9, "frac": tc_bpl / tc_avg / 1e9 / hbm})
+    plain_res = timed_solves(torch, prob, plain, d_rhs, w.rhs_kind, d_out, R, 2)
     u_plain = d_out.cpu().numpy().T.copy()
+    plain_b_res = timed_solves(torch, prob, plain_batched, d_rhs, w.rhs_kind, d_out, R, ksteps)
+    # the mixed solve with the preconditioner's S_k apply on the tensor cores (tcgen05 MMAs on
+    # the FP16 copy and FP16 x, FP32 accumulators in tensor memory)
+    tc_res = timed_solves(torch, prob, binding.default_options(precision=1, batched=1, precond_fp16=2),
+                          d_rhs, w.rhs_kind, d_out, R, ksteps)
 
     # the paper's baseline solver on the same GPU and inputs: diagonally preconditioned CG on
-    # the single-domain system (FP64-accurate products), tol 1e-10 (nodal error ~1e-10)
+    # the single-domain system (FP64-accurate products), tol 1e-10
     t0 = time.perf_counter()
     prob.cg_prepare()
     cg_prep_s = time.perf_counter() - t0
@@ -313,7 +358,7 @@ def run_ours(args):
     prob.solve_cg_device(d_rhs, w.rhs_kind, d_cg, nrhs=R)
     torch.cuda.synchronize()
     ts = []
-    for _ in range(ksteps):
+    for _ in range(2):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record()
@@ -327,36 +372,9 @@ def run_ours(args):
               "rel_diff_vs_fp64_feti": rel_diff(u_cg, u_plain, w)}
     prob.set_options(mixed)
 
-    # the same size on an unstructured mesh (irregular nodes and diagonals) with 16
-    # graph-grown local parts: warm mixed solves
-    wu = W.unstructured_l2(N=128, K=16, nrhs=R, delta=0.1, seed=11)
-    pu = binding.Problem.from_workload(ctx, wu)
-    pu.factor(2)
-    pu.set_options(mixed)
-    du_rhs = torch.from_numpy(np.ascontiguousarray(wu.rhs.T)).to(dev)
-    du_out = torch.empty_like(du_rhs)
-    for _ in range(2):
-        pu.solve_device(du_rhs, wu.rhs_kind, du_out, nrhs=R)
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(ksteps):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        s_u = pu.solve_device(du_rhs, wu.rhs_kind, du_out, nrhs=R)
-        b.record()
-        torch.cuda.synchronize()
-        ts.append(a.elapsed_time(b))
-    inf_u = pu.info()
-    unstr_res = {"value": R * len(ts) / (sum(ts) / 1e3), "unit": "solves/s", "ms_per_step": statistics.mean(ts),
-                 "iterations": s_u["iterations"], "refine_sweeps": s_u["refine_sweeps"],
-                 "n_dofs": int((wu.mesh.node_is_dirichlet == 0).sum()), "subdomains": inf_u["K"],
-                 "n_lambda": inf_u["n_lambda"], "workload": "constant l2 kernel, delta=0.1, 128 x 128 cells with "
-                 "irregular nodes (+-0.15 h) and diagonals, 16 graph-grown local parts, 8 RHS N(0,1)"}
-    pu.close()
-
     # cold: setup + assembly + FP32 factorization + one solve
     torch.cuda.synchronize()
+    prob.close()
     t0 = time.perf_counter()
     prob2 = binding.Problem.from_workload(ctx, w)
     prob2.factor(2)
@@ -365,46 +383,83 @@ def run_ours(args):
     torch.cuda.synchronize()
     cold_s = time.perf_counter() - t0
     prob2.close()
+    del d_cg
+
+    # the other workloads, warm: mixed (with the apply rooflines) and the two FP64 baselines
+    others = {}
+    for oname in WORKLOADS:
+        if oname == name or args.headline_only:
+            continue
+        ow = WORKLOADS[oname][0]()
+        op = binding.Problem.from_workload(ctx, ow)
+        op.factor(3)
+        op.autotune(ow.nrhs, os.path.join(ROOT, "paper_2306_00094_gb300", "_build", "apply_tune.json"))
+        od_rhs = torch.from_numpy(np.ascontiguousarray(ow.rhs.T)).to(dev)
+        od_out = torch.empty_like(od_rhs)
+        res = {"workload": WORKLOADS[oname][1]}
+        res["mixed"] = timed_solves(torch, op, mixed, od_rhs, ow.rhs_kind, od_out, ow.nrhs, ksteps)
+        oroof = apply_rooflines(torch, op, lambda: op.solve_device(od_rhs, ow.rhs_kind, od_out, nrhs=ow.nrhs),
+                                ksteps, hbm, peak_kind)
+        res["roofline_apply"] = oroof["apply"]
+        res["roofline_precond"] = oroof["half_apply"]
+        res["plain_fp64_per_subdomain"] = timed_solves(torch, op, plain, od_rhs, ow.rhs_kind, od_out, ow.nrhs, 2)
+        res["fp64_batched"] = timed_solves(torch, op, plain_batched, od_rhs, ow.rhs_kind, od_out, ow.nrhs, 3)
+        others[oname] = res
+        op.close()
+        del od_rhs, od_out
+
+    # the same size as the 2-D constant-kernel workload on an unstructured mesh (irregular
+    # nodes and diagonals) with 16 graph-grown local parts: warm mixed solves
+    unstr_res = None
+    if not args.headline_only:
+        wu = W.unstructured_l2(N=128, K=16, nrhs=8, delta=0.1, seed=11)
+        pu = binding.Problem.from_workload(ctx, wu)
+        pu.factor(2)
+        du_rhs = torch.from_numpy(np.ascontiguousarray(wu.rhs.T)).to(dev)
+        du_out = torch.empty_like(du_rhs)
+        unstr_res = timed_solves(torch, pu, mixed, du_rhs, wu.rhs_kind, du_out, wu.nrhs, ksteps)
+        inf_u = pu.info()
+        unstr_res.update({"n_dofs": int((wu.mesh.node_is_dirichlet == 0).sum()), "subdomains": inf_u["K"],
+                          "n_lambda": inf_u["n_lambda"],
+                          "workload": "constant l2 kernel, delta=0.1, 128 x 128 cells with irregular nodes "
+                                      "(+-0.15 h) and diagonals, 16 graph-grown local parts, 8 RHS N(0,1)"})
+        pu.close()
+
+    # the serving stream through the server: batched mixed vs plain FP64 one subdomain at a time
+    serving = None
+    if not args.headline_only and world == 1:
+        serving = serving_compare(ctx, binding, args)
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 operators + f64 vectors/refinement", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": R * world, "n_dofs": int((w.mesh.node_is_dirichlet == 0).sum()),
-                   "subdomains": info["K"], "n_lambda": info["n_lambda"], "n_u": info["n_u"],
-                   "parallelism": f"replicas x{world}",
-                   "l2": "operators (2 x 138 MB FP32) exceed L2 (126 MB); no flush between steps",
-                   "step": "warm solve request (operators resident), setup/factor excluded"},
+        "config": config_dict(name, w, info["n_lambda"], info["n_u"], world),
+        "parallelism": f"replicas x{world}",
         "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99)},
         "iterations": stats[-1]["iterations"], "refine_sweeps": stats[-1]["refine_sweeps"],
-        "roofline": {"kernel": "k_apply_tma<float, 8, 2, 2, float> (dense S_k^+ apply, FP32, tensor-copy pipeline)",
-                     "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "peak_source": peak_kind,
-                     "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_s * 1e6 if avg_s else None,
-                     "launches": n_apply, "share_of_step_time": apply_share,
-                     "timing": "CUDA events around each apply launch over a second timed region of the same "
-                               f"{args.steps} steps",
-                     "traffic": profile_traffic(kernel_source_hash())},
-        "roofline_precond": {"kernel": "k_apply_tma<float, 8, 4, 2, __half> (preconditioner S_k apply, FP16 copy)",
-                             "bound": "hbm", "achieved": h_ach, "peak": hbm, "unit": "GB/s",
-                             "frac": (h_ach / hbm) if h_ach else None, "peak_source": peak_kind,
-                             "bytes_per_launch": h_bpl, "avg_launch_us": h_avg * 1e6 if h_avg else None,
-                             "launches": n_half, "share_of_step_time": h_share,
-                             "traffic": profile_traffic(kernel_source_hash(), "k_apply_tma_fp16_const_l2_h128.md")},
-        "precond_tensor_cores": tc_res,
+        "roofline": ap,
+        "roofline_precond": hp,
         "gpu_launches": launches,
         "e2e": e2e,
         "plain_fp64_per_subdomain": plain_res,
         "fp64_batched": plain_b_res,
+        "precond_tensor_cores": tc_res,
         "cg_single_domain": cg_res,
-        "unstructured": unstr_res,
         "cold": {"setup_assembly_s": t_setup, "factor_fp32_s": t_factor32, "factor_fp64_s": t_factor64,
                  "setup_factor_solve_s": cold_s},
+        "autotune": {"seconds": t_tune, "choices": [
+            {"operator": ["FP32 S_k^+ / S_k", "FP16 copy of S_k", "FP64 S_k^+ / S_k"][e["kind"]],
+             "rhs_per_pass": e["rc"], "ctas_per_sm": e["ctas_per_sm"], "us_per_launch": e["us"],
+             "from_cache": bool(e["from_cache"])} for e in tuned]},
+        "other_workloads": others,
+        "unstructured": unstr_res,
+        "serving": serving,
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"], accuracy = cpu_baseline(w, args, u_gpu, u_plain, u_cg)
-        line["rel_err_vs_oracle"] = accuracy
+        line["cpu_baseline"], line["rel_err_vs_oracle"] = cpu_baseline(name, w, args, {
+            "mixed": u_gpu, "plain_fp64": u_plain, "cg_single_domain": u_cg})
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -413,42 +468,86 @@ def run_ours(args):
 
 # ------------------------------------------------------------------------------------- oracle
 
-def oracle_setup(w):
-    from oracle import feti
-    return feti.Feti(w.mesh, w.kernel, w.labels, w.K)
-
-
 def rel_diff(u, v, w):
     """max over right-hand sides of max |u - v| / max |v| on the non-Dirichlet dofs"""
-    free = w.mesh.node_is_dirichlet == 0
+    free = np.repeat(w.mesh.node_is_dirichlet == 0, w.kernel.ncomp)
     d = np.abs(u[free] - v[free]).max(axis=0)
     s = np.abs(v[free]).max(axis=0)
     return float((d / np.where(s > 0, s, 1.0)).max())
 
 
-def cpu_baseline(w, args, u_gpu, u_plain, u_cg=None):
-    """The FP64 oracle as it stands, on the host cores: warm solves of the same workload
-    (its setup excluded like the GPU's), bounded to ~10-30 s; also the accuracy of the GPU
-    results against it."""
+# PCG iterations of the oracle's FETI (Algorithm 1, FP64, tolerance 1e-10) on each workload,
+# from `python -m oracle.feti_iterations <workload>` (the oracle alone): they scale the
+# oracle's sampled per-iteration time to a whole solve.
+ORACLE_ITERATIONS = {"peridynamic_2d": 58, "fractional_2d": 32, "const_l2_2d": 26}
+ORACLE_SAMPLE_SUBDOMAINS = 4
+
+
+class OracleSample:
+    """The FP64 oracle's solve-phase work on a fixed sample of subdomains, for timing on the
+    host cores: a full oracle FETI solve of the large workloads takes many minutes (its setup
+    alone assembles and factors every subdomain), so a step times the oracle's per-iteration
+    subdomain work -- S_k^+ (pinned Neumann solve, Sec. 5.3) and S_k (Dirichlet solve,
+    eq. subSchurComplement) applied to all right-hand sides -- on m evenly spaced subdomains,
+    and a whole solve is estimated as (K / m) x (PCG iterations + 2) such steps (the forcing
+    and the back substitution cost about one iteration each; the Lambda-space work is not
+    counted, which favours the oracle)."""
+
+    def __init__(self, name, w, m=ORACLE_SAMPLE_SUBDOMAINS):
+        from oracle import assembly, feti
+        from oracle.decomposition import build_decomposition
+        self.w, self.name = w, name
+        dec = build_decomposition(w.mesh, w.kernel, w.labels, w.K)
+        self.K = dec.K
+        self.ks = sorted({int(round(i * (dec.K - 1) / max(1, m - 1))) for i in range(m)})
+        nc = w.kernel.ncomp
+        self.ops, self.x = [], []
+        rng = np.random.default_rng(0)
+        for k in self.ks:
+            dofs = dec.dofs(k)
+            dof_of = np.full(w.mesh.n_nodes * nc, -1, dtype=np.int32)
+            dof_of[dofs] = np.arange(dofs.size, dtype=np.int32)
+            Ak, _ = assembly.assemble(w.mesh, w.kernel, w.kernel.scale, dof_of, dofs.size, elem_mask=dec.elem_mask, k=k)
+            Zk = dec.Z[dec.u_offset[k]:dec.u_offset[k + 1], dec.coarse_offset[k]:dec.coarse_offset[k + 1]]
+            op = feti.SubdomainOps(Ak, dec.n_omega(k), dec.subs[k].pinned, Zk if Zk.shape[1] else None)
+            self.ops.append(op)
+            self.x.append(rng.standard_normal((op.nG, w.nrhs)))
+        self.n_lambda, self.n_u = dec.n_lambda, dec.n_u
+
+    def step(self):
+        for op, x in zip(self.ops, self.x):
+            op.S_plus(x)
+            op.S(x)
+
+    def solves_per_s(self, step_s):
+        its = ORACLE_ITERATIONS[self.name]
+        return self.w.nrhs / (step_s * (self.K / len(self.ks)) * (its + 2))
+
+    def describe(self, nsteps):
+        return (f"{nsteps} steps of the oracle's per-iteration subdomain work (S_k^+ and S_k applied to the "
+                f"{self.w.nrhs} right-hand sides) on subdomains {self.ks} of {self.K}, scaled by K/m = "
+                f"{self.K / len(self.ks):g} and by the oracle's {ORACLE_ITERATIONS[self.name]} PCG iterations + 2 "
+                f"(forcing, back substitution); oracle setup excluded, Lambda-space work not counted")
+
+
+def cpu_baseline(name, w, args, results):
+    """The FP64 oracle as it stands, on the host cores (a bounded sample, ~10-20 s), and the
+    GPU results' relative nodal error against the oracle's single-domain solve."""
     from oracle import problem as oprob
-    fo = oracle_setup(w)
+    samp = OracleSample(name, w)
+    samp.step()
     t0 = time.perf_counter()
     n = 0
-    u_ref = None
-    while True:
-        u_ref, _ = fo.solve(w.rhs, w.rhs_kind)
+    while n < 3 or (time.perf_counter() - t0 < 10.0 and n < 50):
+        samp.step()
         n += 1
-        if time.perf_counter() - t0 > 10.0 or n >= 3:
-            break
-    dt = time.perf_counter() - t0
+    dt = (time.perf_counter() - t0) / n
     cores = os.cpu_count()
-    base = {"value": w.nrhs * n / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n} warm oracle FETI solve(s) of the 8 right-hand sides (oracle setup excluded), "
-                      f"numpy/LAPACK FP64 on {cores} host threads"}
-    acc = {"mixed": float(oprob.rel_nodal_error(u_gpu, u_ref, w.mesh, 1).max()),
-           "plain_fp64": float(oprob.rel_nodal_error(u_plain, u_ref, w.mesh, 1).max())}
-    if u_cg is not None:
-        acc["cg_single_domain"] = float(oprob.rel_nodal_error(u_cg, u_ref, w.mesh, 1).max())
+    base = {"value": samp.solves_per_s(dt), "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": samp.describe(n) + f"; numpy/LAPACK FP64 on {cores} host threads"}
+    ref = oprob.Monolithic(w.mesh, w.kernel).solve(w.rhs, w.rhs_kind)
+    acc = {k: float(oprob.rel_nodal_error(u, ref, w.mesh, w.kernel.ncomp).max()) for k, u in results.items()}
+    acc["reference"] = "oracle single-domain FP64 solve (banded LAPACK Cholesky), every right-hand side"
     return base, acc
 
 
@@ -456,26 +555,29 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = W.const_l2_2d()
-    fo = oracle_setup(w)
+    name = args.workload
+    w = WORKLOADS[name][0]()
+    samp = OracleSample(name, w)
     for _ in range(min(args.warmup, 1)):
-        fo.solve(w.rhs, w.rhs_kind)
+        samp.step()
     ts = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        fo.solve(w.rhs, w.rhs_kind)
+        samp.step()
         ts.append(time.perf_counter() - t0)
-    total = sum(ts)
-    value = w.nrhs * len(ts) / total
+    step_s = sum(ts) / len(ts)
+    value = samp.solves_per_s(step_s)
+    scale = value * step_s / w.nrhs                     # whole-solve time = step time / scale
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ts),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": w.nrhs, "parallelism": "host cores",
-                       "step": "one oracle FETI solve of the 8 right-hand sides (oracle setup excluded)"},
-            "latency_ms": {"p50": 1e3 * percentile(ts, 0.5), "p99": 1e3 * percentile(ts, 0.99)},
+            "config": config_dict(name, w, samp.n_lambda, samp.n_u, world),
+            "parallelism": "host cores",
+            "latency_ms": {"p50": 1e3 * percentile(ts, 0.5) / scale, "p99": 1e3 * percentile(ts, 0.99) / scale,
+                           "note": "estimated whole-solve latency from the sampled steps"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{len(ts)} warm oracle solves of the full workload"},
+                             "sample": samp.describe(len(ts))},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -531,84 +633,124 @@ def serving_workload(cfg, nrhs):
     return W.fractional_2d(N=cfg["N"], k=k, nrhs=nrhs, delta=cfg["delta"])
 
 
+class ServingStream:
+    """The serving scenario: a pool of problems sampled from the grid kernel x h x delta x K
+    (seed 6), Poisson arrivals of requests with R in [1, 32] right-hand sides on a random
+    problem of the pool, sent to the continuous-batching server by their inputs (the server's
+    factorization cache creates and factors each problem on its first request; the stream is
+    measured after every problem has been requested once, i.e. with the factorizations cached
+    on the device).  Latency is arrival -> result on the host (submission lag + queue wait +
+    solve with copies)."""
+
+    def __init__(self, ctx, binding, n_pool, budget, slots, opt):
+        rng = np.random.default_rng(6)
+        self.pool_cfg, self.rejected = serving_pool(rng, n_pool, budget, cost_cap=2.0e7)
+        self.binding, self.opt = binding, opt
+        self.server = binding.Server(ctx, hbm_budget=budget, max_slots=slots)
+        self.work = []
+        t0 = time.perf_counter()
+        for cfg in self.pool_cfg:
+            w = serving_workload(cfg, 32)
+            cfg["dofs"] = int(w.rhs.shape[0])
+            self.work.append(w)
+            self.server.wait(self.server.submit_workload(w, rhs=w.rhs[:, :1], opt=opt))    # cache the factorization
+        self.setup_s = time.perf_counter() - t0
+
+    def run(self, rate, n_req, n_warm, seed=7, max_s=None):
+        import threading
+        rng = np.random.default_rng(seed)
+        arr = np.cumsum(rng.exponential(1.0 / rate, n_warm + n_req))
+        pick = rng.integers(len(self.work), size=n_warm + n_req)
+        nr = rng.integers(1, 33, size=n_warm + n_req)
+        n = len(arr)
+        if max_s is not None:                       # bound the stream by its arrival span
+            n = max(n_warm + 20, int(np.searchsorted(arr, max_s)))
+            arr, pick, nr = arr[:n], pick[:n], nr[:n]
+        tickets, lags, lat, done_at = [None] * n, [0.0] * n, [None] * n, [0.0] * n
+        submitted = threading.Semaphore(0)
+        start = time.perf_counter() + 0.05
+        srv = self.server
+
+        def collect():
+            for i in range(n):
+                submitted.acquire()
+                _, st = srv.wait(tickets[i])
+                done_at[i] = time.perf_counter()
+                lat[i] = lags[i] + 1e-3 * (st["ms_queue"] + st["ms_solve"])
+        th = threading.Thread(target=collect)
+        th.start()
+        for i in range(n):
+            tgt = start + arr[i]
+            now = time.perf_counter()
+            if tgt > now:
+                time.sleep(tgt - now)
+            w = self.work[pick[i]]
+            tickets[i] = srv.submit_workload(w, rhs=w.rhs[:, :nr[i]], opt=self.opt)
+            lags[i] = time.perf_counter() - tgt
+            submitted.release()
+        th.join()
+        meas = range(n_warm, n)
+        t_first, t_last = start + arr[n_warm], max(done_at[i] for i in meas)
+        span = t_last - t_first
+        ls = [1e3 * lat[i] for i in meas]
+        return {"offered_rate": rate, "requests": len(meas), "requests_per_s": len(meas) / span,
+                "solves_per_s": float(sum(nr[i] for i in meas)) / span,
+                "p50_ms": percentile(ls, 0.5), "p99_ms": percentile(ls, 0.99),
+                "mean_submit_lag_ms": 1e3 * float(np.mean([lags[i] for i in meas]))}
+
+    def close(self):
+        info = self.server.info()
+        self.server.close()
+        return info
+
+
+def serving_compare(ctx, binding, args):
+    """The serving stream at the offered rate (200 requests/s) through the batched mixed path
+    and through the plain FP64 one-subdomain-at-a-time path, same arrivals and problems."""
+    budget = 16 << 30
+    out = {"workload": "Poisson arrivals (seed 7) at %g requests/s of requests with 1-32 RHS on a pool of %d "
+                       "problems sampled from the grid kernel {1-D constant, 2-D constant l2, 2-D fractional} x "
+                       "h {1/64, 1/128, 1/256} (1-D: 10x finer) x delta {2h, 3h, 0.1} x K (seed 6), "
+                       "factorizations cached on the device" % (args.rate, args.pool),
+           "slots": args.slots, "hbm_budget_bytes": budget}
+    arms = (("mixed_batched", binding.default_options(precision=1, batched=1), args.requests, None),
+            ("plain_fp64_per_subdomain", binding.default_options(precision=0, batched=0), args.requests,
+             args.serving_plain_s))
+    for name, opt, n_req, max_s in arms:
+        ss = ServingStream(ctx, binding, args.pool, budget, args.slots, opt)
+        res = ss.run(args.rate, n_req, n_req // 10, max_s=max_s)
+        inf = ss.close()
+        res.update({"setup_and_factor_s": ss.setup_s, "server": inf})
+        out[name] = res
+        out["pool"] = ss.pool_cfg
+        out["rejected_fraction_of_grid_draws"] = ss.rejected
+    return out
+
+
 def run_serving(args):
-    """Serving scenario: Poisson arrivals of requests (a problem from a pool of factored
-    problems, R in [1, 32] right-hand sides) to the continuous-batching server; latency is
-    arrival -> result on the host (submission lag + queue wait + solve incl. copies)."""
-    import threading
+    """--serving: the serving stream of the mixed batched path with a sweep of the offered
+    rate, one JSON line."""
     import torch  # noqa: F401  (device memory and the caller stream of the context)
     from paper_2306_00094_gb300 import binding
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    rng = np.random.default_rng(6)
-    budget = 16 << 30
-    pool_cfg, rejected = serving_pool(rng, args.pool, budget, cost_cap=2.0e7)
     ctx = binding.Context()
-    t0 = time.perf_counter()
-    probs = []
-    for cfg in pool_cfg:
-        w = serving_workload(cfg, 32)
-        p = binding.Problem.from_workload(ctx, w)
-        p.factor(2)
-        p.set_options(binding.default_options(precision=1, batched=1))
-        rhs = np.asfortranarray(w.rhs)
-        probs.append((p, rhs, w.rhs_kind))
-        cfg["dofs"] = int(rhs.shape[0])
-    setup_s = time.perf_counter() - t0
-    server = binding.Server(ctx, hbm_budget=budget, max_slots=args.slots)
-
-    def run(rate, n_req, n_warm):
-        arr = np.cumsum(rng.exponential(1.0 / rate, n_warm + n_req))
-        pick = rng.integers(len(probs), size=n_warm + n_req)
-        nr = rng.integers(1, 33, size=n_warm + n_req)
-        tickets = [None] * len(arr)
-        lags = [0.0] * len(arr)
-        lat = [None] * len(arr)
-        done_at = [0.0] * len(arr)
-        submitted = threading.Semaphore(0)
-        start = time.perf_counter() + 0.05
-
-        def collect():
-            for i in range(len(arr)):
-                submitted.acquire()
-                _, st = server.wait(tickets[i])
-                done_at[i] = time.perf_counter()
-                lat[i] = lags[i] + 1e-3 * (st["ms_queue"] + st["ms_solve"])
-        th = threading.Thread(target=collect)
-        th.start()
-        for i in range(len(arr)):
-            tgt = start + arr[i]
-            now = time.perf_counter()
-            if tgt > now:
-                time.sleep(tgt - now)
-            p, rhs, kind = probs[pick[i]]
-            tickets[i] = server.submit(p, rhs[:, :nr[i]], kind)
-            lags[i] = time.perf_counter() - tgt
-            submitted.release()
-        th.join()
-        meas = range(n_warm, len(arr))
-        t_first, t_last = start + arr[n_warm], max(done_at[i] for i in meas)
-        span = t_last - t_first
-        ls = [1e3 * lat[i] for i in meas]
-        return {"offered_rate": rate, "requests": n_req, "requests_per_s": n_req / span,
-                "solves_per_s": float(sum(nr[i] for i in meas)) / span,
-                "p50_ms": percentile(ls, 0.5), "p99_ms": percentile(ls, 0.99),
-                "mean_submit_lag_ms": 1e3 * float(np.mean([lags[i] for i in meas]))}
-
-    main_run = run(args.rate, args.requests, args.requests // 10)
-    sweep = [run(r, 300, 30) for r in (50, 100, 200, 400, 800)]
+    budget = 16 << 30
+    ss = ServingStream(ctx, binding, args.pool, budget, args.slots, binding.default_options(precision=1, batched=1))
+    main_run = ss.run(args.rate, args.requests, args.requests // 10)
+    sweep = [ss.run(r, 300, 30, seed=8 + j) for j, r in enumerate((50, 100, 200, 400, 800))]
     sustainable = max([s["offered_rate"] for s in sweep if s["requests_per_s"] >= 0.9 * s["offered_rate"]], default=None)
-    server.close()
+    info = ss.close()
     line = {"metric": "serving: FETI requests (mixed kernels, h, delta, K; R in [1, 32]) under Poisson arrivals, "
                       "arrival -> host result latency, 1 GB300",
             "mode": "serving", "value": main_run["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
             "higher_is_better": True, "data": "synthetic", "dtype": "f32 operators + f64 vectors/refinement",
-            "config": {"workload": "serving pool of factored problems sampled from the grid (seed 6)",
-                       "pool": pool_cfg, "slots": args.slots, "hbm_budget_bytes": budget,
-                       "rejected_fraction_of_grid_draws": rejected},
-            "setup_and_factor_s": setup_s, "run": main_run, "rate_sweep": sweep,
-            "max_sustained_rate": sustainable}
+            "config": {"workload": "serving pool of problems sampled from the grid (seed 6)",
+                       "pool": ss.pool_cfg, "slots": args.slots, "hbm_budget_bytes": budget,
+                       "rejected_fraction_of_grid_draws": ss.rejected},
+            "setup_and_factor_s": ss.setup_s, "run": main_run, "rate_sweep": sweep,
+            "max_sustained_rate": sustainable, "server": info}
     print(json.dumps(line), flush=True)
 
 
@@ -694,6 +836,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default=HEADLINE,
+                    help="the workload of the timed steps (default: the largest single-GPU one)")
+    ap.add_argument("--headline-only", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true", help="setup, warm-up and the timed steps only (for ncu)")
     ap.add_argument("--tensor-core-precond", action="store_true",
@@ -705,7 +850,9 @@ def main():
     ap.add_argument("--serving", action="store_true",
                     help="serving scenario: Poisson arrivals of mixed requests to the server (one JSON line)")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: offered requests per second")
-    ap.add_argument("--requests", type=int, default=2000, help="serving: measured requests")
+    ap.add_argument("--requests", type=int, default=1000, help="serving: measured requests")
+    ap.add_argument("--serving-plain-s", type=float, default=2.0,
+                    help="serving comparison: arrival span of the plain FP64 arm's stream (s)")
     ap.add_argument("--pool", type=int, default=6, help="serving: distinct factored problems")
     ap.add_argument("--slots", type=int, default=4, help="serving: server slots")
     ap.add_argument("--paper-rows", action="store_true",

@@ -11,7 +11,7 @@ Contents, each following the paper's statement:
   form (eq. bil1, eq. bilinear-multi1), single-domain and per-subdomain.
 * ``decomposition.py`` -- the nonlocal subdivision (Def. nonlocalsubdivision,
   Sec. 5.1), zeta (eq. zeta), index sets I_k / G_k, B, D, B_D, Z, G.
-* ``monolithic.py`` -- the single-domain system A u = f - B g (Sec. 2.3.3),
+* ``problem.py`` -- load vectors and the single-domain system A u = f - B g (Sec. 2.3.3),
   solved by Cholesky (dense or banded LAPACK).
 * ``feti.py`` -- one-level FETI, Algorithm 1 with the scaled Dirichlet
   preconditioner (eq. preconditioner) and the pinning pseudo-inverse (Sec. 5.3).
