@@ -51,7 +51,8 @@ def _load():
             lib.oracle_point_integral.argtypes = [C.POINTER(_Mesh), C.POINTER(_Kernel), C.c_int64, C.c_int64,
                                                   C.c_double, C.c_double, C.c_void_p, C.c_void_p]
             lib.oracle_assemble.restype = C.c_int
-            lib.oracle_assemble.argtypes = [C.POINTER(_Mesh), C.POINTER(_Kernel), C.c_void_p, C.c_int, C.c_void_p,
+            lib.oracle_assemble.argtypes = [C.POINTER(_Mesh), C.POINTER(_Kernel), C.c_void_p, C.c_int, C.c_int,
+                                            C.c_void_p,
                                             C.c_int64, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_int]
             lib.oracle_assemble_rows.restype = C.c_int
@@ -129,14 +130,19 @@ def assemble(mesh, kernel, scale, dof_of, n_dofs, elem_mask=None, k=-1, band=Non
         A = np.zeros((band + 1, n_dofs), dtype=np.float64)
         mode, kd = 1, band
     mask = None
+    mask_words = 1
     if elem_mask is not None:
         mask = np.ascontiguousarray(elem_mask, dtype=np.uint64)
+        if mask.ndim == 1:
+            mask = mask.reshape(-1, 1)
+        mask_words = mask.shape[1]
     gbuf = None
     Bg = None
     if g is not None:
         gbuf = np.ascontiguousarray(g, dtype=np.float64)
         Bg = np.zeros(n_dofs, dtype=np.float64)
-    st = lib.oracle_assemble(C.byref(ctx.m), C.byref(ctx.k), None if mask is None else mask.ctypes.data, int(k),
+    st = lib.oracle_assemble(C.byref(ctx.m), C.byref(ctx.k), None if mask is None else mask.ctypes.data,
+                             int(mask_words), int(k),
                              dof_of.ctypes.data, int(n_dofs), mode, int(kd), None if A is None else A.ctypes.data,
                              None if gbuf is None else gbuf.ctypes.data, None if Bg is None else Bg.ctypes.data,
                              _threads(nthreads))

@@ -53,7 +53,8 @@ class Decomposition:
     ncomp: int
     subs: list
     node_zeta: np.ndarray        # (n_nodes,) number of Omega-hat_k holding the node
-    elem_mask: np.ndarray        # (n_elems,) uint64 bit k <=> element in Omega-hat_k u Gamma^D_k
+    elem_mask: np.ndarray        # (n_elems, ceil(K / 64)) uint64: bit k % 64 of word k // 64 <=> element in
+                                 # Omega-hat_k u Gamma^D_k
     u_offset: np.ndarray         # (K+1,) offsets of Gamma_k blocks in U (in dofs)
     B_plus: np.ndarray           # (M_C,) U index with +1
     B_minus: np.ndarray          # (M_C,) U index with -1
@@ -69,6 +70,10 @@ class Decomposition:
     @property
     def n_u(self) -> int:
         return int(self.u_offset[-1])
+
+    def in_sub(self, k):
+        """(n_elems,) bool: the element belongs to Omega-hat_k u Gamma^D_k."""
+        return ((self.elem_mask[:, k // 64] >> np.uint64(k % 64)) & np.uint64(1)).astype(bool)
 
     def dofs(self, k):
         """Global dof ids (node*nc + comp) of subdomain k, Omega block first."""
@@ -153,9 +158,7 @@ def build_decomposition(mesh, kernel, labels, K) -> Decomposition:
     collar = ~interior
     r_ext = (0.5 * delta) * (1.0 + 1e-9)
     r_dir = delta * (1.0 + 1e-9)
-    if K > 64:
-        raise ValueError("at most 64 subdomains")
-    elem_mask = np.zeros(mesh.n_elems, dtype=np.uint64)
+    elem_mask = np.zeros((mesh.n_elems, (K + 63) // 64), dtype=np.uint64)
     hat_sets, dir_sets = [], []
     for k in range(K):
         src = np.flatnonzero(labels == k)
@@ -166,8 +169,8 @@ def build_decomposition(mesh, kernel, labels, K) -> Decomposition:
         dirk = _within(mesh, lo, hi, src, collar, r_dir)
         hat_sets.append(np.flatnonzero(hat))
         dir_sets.append(np.flatnonzero(dirk))
-        elem_mask[hat] |= np.uint64(1) << np.uint64(k)
-        elem_mask[dirk] |= np.uint64(1) << np.uint64(k)
+        elem_mask[hat, k // 64] |= np.uint64(1) << np.uint64(k % 64)
+        elem_mask[dirk, k // 64] |= np.uint64(1) << np.uint64(k % 64)
     # nodes of each Omega-hat_k (non-Dirichlet)
     node_sets = []
     node_zeta = np.zeros(mesh.n_nodes, dtype=np.int64)

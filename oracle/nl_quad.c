@@ -650,12 +650,24 @@ static int popcount64(uint64_t x) {
     return c;
 }
 
+/* element e in subdomain k: bit k % 64 of word k / 64 of its mask (W words per element) */
+static int mask_has(const uint64_t *elem_mask, int W, int64_t e, int k) {
+    return (int)((elem_mask[e * W + k / 64] >> (k % 64)) & 1u);
+}
+
+/* zeta(E, E'): the number of subdomains holding both elements */
+static int mask_common(const uint64_t *elem_mask, int W, int64_t e, int64_t ep) {
+    int c = 0;
+    for (int w = 0; w < W; ++w) c += popcount64(elem_mask[e * W + w] & elem_mask[ep * W + w]);
+    return c;
+}
+
 /* ------------------------------------------------------------------- assembly */
 
 /*
  * Assemble sum over ordered element pairs into A.
- *   elem_mask : per element, bit k set when the element belongs to subdomain k
- *               (Omega-hat_k union Gamma^D_k); may be NULL when k < 0.
+ *   elem_mask : per element W words, bit k % 64 of word k / 64 set when the element belongs
+ *               to subdomain k (Omega-hat_k union Gamma^D_k); may be NULL when k < 0.
  *   k         : subdomain index (pairs with both bits set, weight 1/zeta(E,E'))
  *               or -1 (all pairs, weight 1).
  *   dof_of    : (n_nodes*nc) local dof index of (node, comp), or -1.
@@ -666,7 +678,7 @@ static int popcount64(uint64_t x) {
  * Pairs of two Dirichlet elements are skipped: all their nodes are Dirichlet.
  * Returns 0 on success, -1 on a band overflow.
  */
-int oracle_assemble(const om_mesh *M, const om_kernel *K, const uint64_t *elem_mask, int k,
+int oracle_assemble(const om_mesh *M, const om_kernel *K, const uint64_t *elem_mask, int W, int k,
                     const int32_t *dof_of, int64_t n_dofs, int mode, int64_t kd, double *A,
                     const double *g, double *Bg, int nthreads) {
     int nc = (K->type == K_PERIDYNAMIC) ? 2 : 1;
@@ -693,7 +705,7 @@ int oracle_assemble(const om_mesh *M, const om_kernel *K, const uint64_t *elem_m
             int64_t *list = (int64_t *)malloc(sizeof(int64_t) * cap);
             int64_t n = 0;
             int use = 1;
-            if (k >= 0 && !((elem_mask[e] >> k) & 1)) use = 0;
+            if (k >= 0 && !mask_has(elem_mask, W, e, k)) use = 0;
             if (use) n = grid_query(&G, &G.bb[e], K->delta, list, cap);
             if (n > cap) n = cap;
             nnb[slot] = 0;
@@ -705,7 +717,7 @@ int oracle_assemble(const om_mesh *M, const om_kernel *K, const uint64_t *elem_m
             for (int64_t t = 0; t < n; ++t) {
                 int64_t ep = list[t];
                 if (M->elem_dir[e] && M->elem_dir[ep]) continue;
-                if (k >= 0 && !((elem_mask[ep] >> k) & 1)) continue;
+                if (k >= 0 && !mask_has(elem_mask, W, ep, k)) continue;
                 list[kept] = ep;
                 locnl[slot][kept] = oracle_pair_matrix(M, K, e, ep, loc[slot] + kept * maxld * maxld,
                                                        locn[slot] + kept * MAXL);
@@ -718,7 +730,7 @@ int oracle_assemble(const om_mesh *M, const om_kernel *K, const uint64_t *elem_m
             for (int64_t t = 0; t < nnb[slot]; ++t) {
                 int64_t ep = nbr[slot][t];
                 double wgt = 1.0;
-                if (k >= 0) wgt = 1.0 / (double)popcount64(elem_mask[e] & elem_mask[ep]);
+                if (k >= 0) wgt = 1.0 / (double)mask_common(elem_mask, W, e, ep);
                 int nl = locnl[slot][t];
                 int ld = nl * nc;
                 const double *L = loc[slot] + t * maxld * maxld;

@@ -33,6 +33,7 @@ CASES = {
     "l2_neumann": lambda: W.neumann_l2(N=20, k=3, nrhs=2),                # Neumann region on two sides
     "pd_neumann": lambda: W.neumann_pd(N=24, k=3, nrhs=2),
     "l2_rounded_collar": lambda: W.l2_collar_const(N=20, k=3, nrhs=2, delta=0.15),
+    "l2_9x9": lambda: W.const_l2_2d(N=36, k=9, nrhs=1, delta=2.0 / 36),   # K = 81: more than 64 subdomains
 }
 
 
@@ -59,10 +60,9 @@ def test_subdivision_covers_interactions(built, name):
     near = _pairs_within(w.mesh, w.kernel.delta)
     both_dir = (w.mesh.elem_is_dirichlet[:, None] == 1) & (w.mesh.elem_is_dirichlet[None, :] == 1)
     need = near & ~both_dir
-    m = d.elem_mask
     zeta = np.zeros(need.shape, dtype=np.int64)
     for k in range(d.K):
-        b = ((m >> np.uint64(k)) & np.uint64(1)).astype(bool)
+        b = d.in_sub(k)
         zeta += (b[:, None] & b[None, :])
     assert (zeta[need] >= 1).all()
     # every non-Dirichlet node is a dof of some subdomain
