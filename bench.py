@@ -756,13 +756,16 @@ def run_serving(args):
 
 PAPER_ROWS = [
     # (table, kernel, N, delta, k): the rows of the paper's Tables fixedHorizon and fixedRatio
-    # that fit this implementation (K <= 64 subdomains, dense subdomain matrices; the
-    # peridynamic fixed-ratio row would need about 200 GB of dense matrices and is left out)
+    # that fit one GPU with dense subdomain matrices (the fixed-ratio rows at 12 x 12 hold about
+    # 170 GB of subdomain matrices, the larger rows more than the device holds)
     ("fixedHorizon", "constant", 250, 0.008, 6),
     ("fixedHorizon", "fractional", 250, 0.008, 6),
     ("fixedHorizon", "peridynamic", 250, 0.008, 6),
     ("fixedRatio", "constant", 500, 0.008, 6),
     ("fixedRatio", "fractional", 500, 0.008, 6),
+    ("fixedHorizon", "constant", 500, 0.008, 12),
+    ("fixedHorizon", "fractional", 500, 0.008, 12),
+    ("fixedHorizon", "peridynamic", 500, 0.008, 12),
 ]
 
 

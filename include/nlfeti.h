@@ -88,7 +88,7 @@ typedef struct {
 } nlfeti_kernel;
 
 /* Local decomposition (Sec. 5.1): K parts, one label in [0, K) per non-Dirichlet
- * element (labels of collar elements are ignored).  K <= 64. */
+ * element (labels of collar elements are ignored).  1 <= K <= 4096. */
 typedef struct {
     int32_t K;
     const int32_t *elem_subdomain;
@@ -114,12 +114,13 @@ typedef struct {
  *          cores (x in FP16, scaled per column by a power of two from its norm; FP32
  *          accumulation) for at most 64 right-hand sides, else as 1; 0 = the FP32 S_k.
  *          nlfeti_apply ops 0-4 always use the FP32 S_k.
- * factor_tc (FP32 operators): 1 = the rank-64 updates of the factorization sweeps run on the
- *          tensor cores (tcgen05 kind::tf32, each FP32 panel entry split into three TF32 terms);
- *          0 = on the FP32 pipes (the default).  The tensor cores accumulate with truncation, so
- *          their FP32 operators carry a few times the rounding error of the FP32-pipe ones, which
- *          can cost the mixed path's refinement an extra sweep; both meet the same tolerances.
- *          Read by nlfeti_factor. */
+ * factor_tc (FP32 operators): the rank-64 updates of the factorization sweeps on the tensor
+ *          cores (tcgen05 kind::tf32, each FP32 panel entry split into three TF32 terms) --
+ *          1 = in both sweeps (the Omega sweep of A^k and the sweep of the pinned S_k), 2 = in the
+ *          Omega sweep only (the default), 0 = on the FP32 pipes only.  The tensor cores
+ *          accumulate with truncation: in the sweep of the pinned S_k (the pseudo-inverse S_k^+)
+ *          that error costs the mixed path's refinement an extra sweep on some problems, in the
+ *          Omega sweep it does not; all settings meet the same tolerances.  Read by nlfeti_factor. */
 typedef struct {
     int precision;
     double tol;
@@ -241,10 +242,16 @@ nlfeti_status nlfeti_problem_set_matrix(nlfeti_problem *p, int k, const double *
  * and applies with nrhs right-hand sides use it.  cache_path (nullable): a JSON file of earlier
  * choices keyed by the device, the subdomain operator shapes, the kind and nrhs; a choice found
  * there is used without timing (from_cache = 1), new ones are added (the file is rewritten).
- * out: up to 3 entries (one per kind), *n_out their number.  Every shape gives bitwise the same
- * results (each column is summed in the same order whatever the pass width and schedule).
+ * For kind 1 the candidates also include the tensor-core apply of the FP16 copy (tcgen05 kind::f16
+ * with x in FP16 scaled per column, as precond_fp16 = 2 selects; nrhs <= 64), reported as
+ * rc = -1; it builds the tiled FP16 copy of S_k when chosen.
+ * out: up to 3 entries (one per kind), *n_out their number.  Every shape of the bulk-copy apply
+ * gives bitwise the same results (each column is summed in the same order whatever the pass
+ * width and schedule); the tensor-core preconditioner rounds differently (it only steers the
+ * PCG: the iteration count may change, not the accuracy reached).
  * nlfeti_set_apply_choice pins a shape (rc 0 clears it, back to the default: the widest block
- * up to nrhs, two CTAs per SM); NLFETI_E_INVALID for shapes outside the lists above. */
+ * up to nrhs, two CTAs per SM; rc -1 selects the tensor-core apply for kind 1);
+ * NLFETI_E_INVALID for shapes outside the lists above. */
 typedef struct {
     int32_t kind, nrhs, rc, ctas_per_sm;
     double us;              /* mean time per apply launch of the chosen shape */

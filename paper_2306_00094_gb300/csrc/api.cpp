@@ -402,7 +402,7 @@ void nlfeti_default_options(nlfeti_options *o) {
     o->hbm_budget = 0;
     o->graph_loop = 1;
     o->precond_fp16 = 1;
-    o->factor_tc = 0;
+    o->factor_tc = 2;
 }
 
 nlfeti_status nlfeti_create(nlfeti_ctx **out, const nlfeti_options *opt, void *cuda_stream,
@@ -612,7 +612,7 @@ nlfeti_status nlfeti_problem_set_options(nlfeti_problem *p, const nlfeti_options
     if (!p || !opt) return NLFETI_E_INVALID;
     if (opt->precision != 0 && opt->precision != 1) return NLFETI_E_INVALID;
     if (opt->precond_fp16 < 0 || opt->precond_fp16 > 2) return NLFETI_E_INVALID;
-    if (opt->factor_tc != 0 && opt->factor_tc != 1) return NLFETI_E_INVALID;
+    if (opt->factor_tc < 0 || opt->factor_tc > 2) return NLFETI_E_INVALID;
     return guarded(p->ctx, [&] {
         p->opt = *opt;
         if (p->opt.precond_fp16 == 2 && p->op32.ready) build_tiled_half(p);
@@ -778,12 +778,18 @@ nlfeti_status nlfeti_set_apply_choice(nlfeti_problem *p, int kind, int nrhs, int
     return guarded(p->ctx, [&] {
         if (rc == 0) {
             p->tune.erase({kind, nrhs});
+        } else if (rc == -1) {
+            if (kind != 1 || nrhs > MMA_MAX_RHS || !p->op32.ready)
+                fail(NLFETI_E_INVALID, "the tensor-core apply serves the FP16 copy of S_k (kind 1), at most 64 "
+                                       "right-hand sides, with FP32 operators factored");
+            build_tiled_half(p);
+            p->tune[{kind, nrhs}] = ApplyChoice{0, 2, 1};
         } else {
             const bool pow2 = rc == 1 || rc == 2 || rc == 4 || rc == 8 || rc == 16;
             if (!pow2 || (kind == 2 && rc > 8) || (rc > nrhs && rc > 1) || (ctas_per_sm != 1 && ctas_per_sm != 2))
                 fail(NLFETI_E_INVALID, "column block must be 1, 2, 4, 8 or 16 (8 for FP64) and at most nrhs; "
                                        "CTAs per SM 1 or 2");
-            p->tune[{kind, nrhs}] = ApplyChoice{rc, ctas_per_sm};
+            p->tune[{kind, nrhs}] = ApplyChoice{rc, ctas_per_sm, 0};
         }
         ++p->tune_gen;
     });

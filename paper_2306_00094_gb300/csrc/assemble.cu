@@ -37,7 +37,8 @@ struct AsmArgs {
     const double *xy;
     const int32_t *elems;
     const int8_t *node_dir;
-    const uint64_t *mask;
+    const uint64_t *mask;     // mask_words words per element: bit k % 64 of word k / 64 = subdomain k
+    int mask_words;
     const int32_t *pairs;     // 2 * npairs
     int64_t npairs;
     const int32_t *nodemap;   // K x n_nodes
@@ -479,10 +480,14 @@ __global__ void __launch_bounds__(64) k_assemble(AsmArgs a) {
         }
     }
     // scatter into every subdomain holding the pair
-    uint64_t both = a.mask[E0] & a.mask[E1];
-    const double wz = 1.0 / (double)__popcll(both);
+    int zeta = 0;
+    for (int w = 0; w < a.mask_words; ++w)
+        zeta += __popcll(a.mask[(int64_t)E0 * a.mask_words + w] & a.mask[(int64_t)E1 * a.mask_words + w]);
+    const double wz = 1.0 / (double)zeta;
+    for (int w = 0; w < a.mask_words; ++w) {
+    uint64_t both = a.mask[(int64_t)E0 * a.mask_words + w] & a.mask[(int64_t)E1 * a.mask_words + w];
     while (both) {
-        const int k = __ffsll((long long)both) - 1;
+        const int k = 64 * w + __ffsll((long long)both) - 1;
         both &= both - 1;
         const SubdomainDesc d = a.sd[k];
         const int32_t *map = a.nodemap + (int64_t)k * a.n_nodes;
@@ -502,6 +507,7 @@ __global__ void __launch_bounds__(64) k_assemble(AsmArgs a) {
                 }
             }
         }
+    }
     }
 }
 
@@ -560,7 +566,7 @@ void assemble_all(nlfeti_problem *p) {
     std::vector<int32_t> pairs;
     pairs.reserve(1 << 20);
     for (int64_t e = 0; e < m.n_elems; ++e) {
-        if (!p->dec.elem_mask[e]) continue;
+        if (!p->dec.any_sub(e)) continue;
         int64_t clo[2] = {0, 0}, chi[2] = {0, 0};
         for (int a = 0; a < m.dim; ++a) {
             clo[a] = std::max<int64_t>(0, (int64_t)std::floor((lo[2 * e + a] - r - H - glo[a]) / H) - 1);
@@ -572,7 +578,7 @@ void assemble_all(nlfeti_problem *p) {
                 for (int64_t t = start[cidx]; t < start[cidx + 1]; ++t) {
                     int64_t f = items[t];
                     if (f < e) continue;
-                    if (!(p->dec.elem_mask[e] & p->dec.elem_mask[f])) continue;
+                    if (!p->dec.share_sub(e, f)) continue;
                     if (m.elem_dir[e] && m.elem_dir[f]) continue;
                     double gap = 0.0;
                     for (int a = 0; a < m.dim; ++a)
@@ -593,6 +599,7 @@ void assemble_all(nlfeti_problem *p) {
     a.elems = p->d_elems.as<int32_t>();
     a.node_dir = p->d_node_dir.as<int8_t>();
     a.mask = p->d_elem_mask.as<uint64_t>();
+    a.mask_words = p->dec.mask_words;
     a.pairs = d_pairs.as<int32_t>();
     a.npairs = npairs;
     a.nodemap = p->d_nodemap.as<int32_t>();

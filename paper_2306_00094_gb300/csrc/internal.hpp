@@ -72,9 +72,24 @@ template <typename T> void upload(nlfeti_ctx *c, DevMem &m, const std::vector<T>
 }
 
 // ------------------------------------------------------------------ host decomposition
+constexpr int kMaxSubdomains = 4096;
+
 struct Decomp {
     int K = 0, nc = 1;
-    std::vector<uint64_t> elem_mask;      // bit k: element in Omega-hat_k u Gamma^D_k
+    int mask_words = 1;                   // words of an element's subdomain mask: ceil(K / 64)
+    std::vector<uint64_t> elem_mask;      // per element mask_words words, bit k % 64 of word k / 64:
+                                          // element in Omega-hat_k u Gamma^D_k
+    bool in_sub(int64_t e, int k) const { return (elem_mask[e * mask_words + k / 64] >> (k % 64)) & 1u; }
+    bool any_sub(int64_t e) const {
+        for (int w = 0; w < mask_words; ++w)
+            if (elem_mask[e * mask_words + w]) return true;
+        return false;
+    }
+    bool share_sub(int64_t e, int64_t f) const {
+        for (int w = 0; w < mask_words; ++w)
+            if (elem_mask[e * mask_words + w] & elem_mask[f * mask_words + w]) return true;
+        return false;
+    }
     std::vector<int32_t> node_zeta;       // number of Omega-hat_k holding the node
     std::vector<std::vector<int32_t>> nodes;   // per k: Omega nodes then Gamma nodes (ascending each)
     std::vector<int32_t> n_omega_nodes, n_gamma_nodes;
@@ -134,6 +149,7 @@ __host__ __device__ inline int mma_ktiles(int nG, int ldG) {
 }
 
 constexpr int kApplyRows = 32;          // rows of an interface-apply work item
+constexpr int MMA_MAX_RHS = 64;         // right-hand sides of the tensor-core preconditioner apply
 
 template <typename T> struct OpPool {   // operators of one precision
     nlf::DevMem M, S, Sp;                // swept matrices, Schur complements, pseudo-inverses
@@ -156,10 +172,12 @@ template <typename T> struct OpPool {   // operators of one precision
 namespace nlf { struct SolveWS; }
 
 // a configuration of the bulk-copy interface apply: right-hand sides per streamed pass (1, 2,
-// 4, 8 or 16) and CTAs per SM of its persistent grid (1 or 2)
+// 4, 8 or 16) and CTAs per SM of its persistent grid (1 or 2); for the FP16 copy of S_k the
+// tensor-core apply instead (mma)
 struct ApplyChoice {
     int rc = 0;
     int per_sm = 2;
+    int mma = 0;
 };
 
 struct nlfeti_problem {

@@ -1341,14 +1341,15 @@ struct Runner {
     // half: S_k from the FP16 copy (FP32 pool, use_sp = 0)
     long long wait_tries() const { return p->dbg_wait_tries > 0 ? p->dbg_wait_tries : APPLY_WAIT_TRIES; }
 
+
     template <typename T> int apply_tma(const OpPool<T> &pool, int use_sp, double *y, bool half = false) {
         // the autotuner's choice for this operator kind and R (column block, CTAs per SM), else
         // the default block and two CTAs per SM
         const ApplyChoice ch = apply_choice(p, half ? 1 : (sizeof(T) == 8 ? 2 : 0), R);
-        const int rc = ch.rc;
+        const int rc = ch.rc > 0 ? ch.rc : apply_rc(R, (int)sizeof(T));
         const int ri = rc >= 16 ? 4 : (rc >= 8 ? 3 : (rc >= 4 ? 2 : (rc >= 2 ? 1 : 0)));
         const CUtensorMap *xm = ws.xmaps_rc[sizeof(T) == 8 ? 1 : 0][ri].template as<CUtensorMap>();
-        const bool one = ch.per_sm == 1 && p->sched1_ctas > 0;
+        const bool one = ch.rc > 0 && ch.per_sm == 1 && p->sched1_ctas > 0;
         const int ctas = one ? p->sched1_ctas : p->sched_ctas;
         const int32_t *sptr = (one ? p->d_sched1_ptr : p->d_sched_ptr).as<int32_t>();
         const int32_t *sitems = (one ? p->d_sched1_items : p->d_sched_items).as<int32_t>();
@@ -1502,8 +1503,9 @@ struct Runner {
     // the preconditioner's S_k apply runs on the tensor cores (FP16 copy, FP16 x): mixed path
     // with precond_fp16 = 2, at most MMA_MAX_R right-hand sides
     template <typename T> bool use_mma(const OpPool<T> &pool, bool precond) const {
-        return std::is_same<T, float>::value && precond && p->opt.precond_fp16 == 2 && p->msched_ctas > 0 &&
-               R <= MMA_MAX_R && pool.St.p && ws.xhmaps.p;
+        const bool want = p->opt.precond_fp16 == 2 || (p->opt.precond_fp16 == 1 && apply_choice(p, 1, R).mma);
+        return std::is_same<T, float>::value && precond && want && p->msched_ctas > 0 && R <= MMA_MAX_R &&
+               pool.St.p && ws.xhmaps.p;
     }
 
     template <typename T> void applyMinv(const OpPool<T> &pool, const double *v, double *out, bool precond = false) {
@@ -1892,9 +1894,15 @@ EncodeTiledFn encode_tiled() {
 
 void SolveWS::drop_graphs() {
     if (graphs.empty()) return;
-    // a graph may still run on the workspace's stream
-    if (async_stream) cudaStreamSynchronize(async_stream);
-    else if (prob) cudaStreamSynchronize(prob->ctx->stream);
+    // a graph may still run on the workspace's stream (a server's workspaces are idle when they
+    // are dropped: their slot synchronized its stream, which another slot's thread may be
+    // capturing into now, so it is not touched here)
+    if (alloc_stream) {
+    } else if (async_stream) {
+        cudaStreamSynchronize(async_stream);
+    } else if (prob) {
+        cudaStreamSynchronize(prob->ctx->stream);
+    }
     for (auto &g : graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     graphs.clear();
@@ -1916,7 +1924,8 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
                   nv = std::max<int64_t>(1, p->sum_nk), nd = std::max<int64_t>(1, p->n_dofs_total);
     const int64_t nco = std::max(1, p->n_co);
     auto alloc = [&](DevMem &m, size_t bytes) {
-        if (async_stream) m.alloc_async(async_stream, bytes);
+        if (alloc_stream) m.alloc_async(alloc_stream, bytes);
+        else if (async_stream) m.alloc_async(async_stream, bytes);
         else m.alloc(c, bytes);
     };
     auto A = [&](DevMem &m, int64_t n) { alloc(m, sizeof(double) * n * R); };
@@ -1925,6 +1934,7 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     A(xU, std::max<int64_t>(1, p->n_up));   // apply layout (padding zeroed by the gathers)
     alloc(uhl, sizeof(float) * 2 * std::max<int64_t>(1, p->n_vp) * ((R + 1) / 2 * 2));
     alloc(xscale, sizeof(double) * R);
+    if (alloc_stream) NLF_CUDA(cudaStreamSynchronize(alloc_stream));
     {
         const std::vector<double> ones(R, 1.0);
         NLF_CUDA(cudaMemcpyAsync(xscale.p, ones.data(), sizeof(double) * R, cudaMemcpyHostToDevice,
@@ -2029,6 +2039,7 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     alloc(scal, sizeof(double) * R * 7 + sizeof(int) * (2 * R + 8));
     alloc(slot_flags, sizeof(int) * kSlotFlags);
     alloc(frozen, sizeof(int) * R);
+    if (alloc_stream) NLF_CUDA(cudaStreamSynchronize(alloc_stream));
     NLF_CUDA(cudaMemsetAsync(scal.p, 0, scal.bytes, async_stream ? async_stream : c->stream));
     host_flag.assign(4, 0);
     this->R = nR;
@@ -2277,7 +2288,7 @@ void autotune_applies(nlfeti_problem *p, int R, const char *cache_path, std::vec
                     if (rc > R && rc > 1) break;
                     if (kind == 2 && rc > 8) break;
                     for (int per_sm = 1; per_sm <= 2; ++per_sm) {
-                        p->tune[{kind, R}] = ApplyChoice{rc, per_sm};
+                        p->tune[{kind, R}] = ApplyChoice{rc, per_sm, 0};
                         auto launch = [&] {
                             if (kind == 0) run.symv<float>(p->op32, 1, ws.xU.as<float>(), ws.yU.as<double>());
                             else if (kind == 1) run.symv<float>(p->op32, 0, ws.xU.as<float>(), ws.yU.as<double>(), true);
@@ -2299,6 +2310,27 @@ void autotune_applies(nlfeti_problem *p, int R, const char *cache_path, std::vec
                         }
                     }
                 }
+                // the preconditioner's copy of S_k also on the tensor cores (FP16 x scaled per column)
+                if (kind == 1 && R <= MMA_MAX_R && p->msched_ctas > 0) {
+                    build_tiled_half(p);
+                    if (p->op32.St.p && ws.xhmaps.p) {
+                        auto launch = [&] { run.symv_mma<float>(p->op32, ws.yU.as<double>()); };
+                        launch();
+                        NLF_CUDA(cudaEventRecord(ea, st));
+                        for (int r = 0; r < 3; ++r) launch();
+                        NLF_CUDA(cudaEventRecord(eb, st));
+                        NLF_CUDA(cudaEventSynchronize(eb));
+                        float ms = 0.f;
+                        NLF_CUDA(cudaEventElapsedTime(&ms, ea, eb));
+                        const double us = 1e3 * ms / 3.0;
+                        if (us < best) {
+                            best = us;
+                            te.rc = -1;
+                            te.per_sm = 1;
+                            te.us = us;
+                        }
+                    }
+                }
                 run.check_waits_now();
                 CacheLine c;
                 c.key = key;
@@ -2310,7 +2342,12 @@ void autotune_applies(nlfeti_problem *p, int R, const char *cache_path, std::vec
                 cache.push_back(c);
                 changed = true;
             }
-            p->tune[{kind, R}] = ApplyChoice{te.rc, te.per_sm};
+            if (te.rc == -1) {
+                build_tiled_half(p);
+                p->tune[{kind, R}] = ApplyChoice{apply_rc(R, 4), 2, 1};
+            } else {
+                p->tune[{kind, R}] = ApplyChoice{te.rc, te.per_sm, 0};
+            }
             out.push_back(te);
         }
     } catch (...) {
@@ -2382,8 +2419,14 @@ void cg_solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int
     const int64_t n = p->n_dofs_total, nv = p->sum_nk;
     auto need = [&](DevMem &m, size_t bytes) {
         if (m.bytes >= bytes) return;
-        if (ws.async_stream) m.alloc_async(ws.async_stream, bytes);
-        else m.alloc(p->ctx, bytes);
+        if (ws.alloc_stream) {
+            m.alloc_async(ws.alloc_stream, bytes);
+            NLF_CUDA(cudaStreamSynchronize(ws.alloc_stream));
+        } else if (ws.async_stream) {
+            m.alloc_async(ws.async_stream, bytes);
+        } else {
+            m.alloc(p->ctx, bytes);
+        }
     };
     const size_t vb = sizeof(double) * (size_t)std::max<int64_t>(1, n) * R;
     need(ws.cg_u, vb); need(ws.cg_r, vb); need(ws.cg_z, vb); need(ws.cg_p, vb); need(ws.cg_q, vb); need(ws.cg_b, vb);
@@ -2530,6 +2573,7 @@ template <typename T> void encode_apply_maps(nlfeti_problem *p, OpPool<T> &pool)
     pool.maps.alloc(p->ctx, sizeof(CUtensorMap) * maps.size());
     NLF_CUDA(cudaMemcpyAsync(pool.maps.p, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
                              p->ctx->stream));
+
     // swept-matrix blocks of the forcing (rows n_O.., columns ..n_O) and of the back
     // substitution (rows ..n_O, all columns)
     std::vector<CUtensorMap> fm(std::max(1, p->K)), om(std::max(1, p->K));

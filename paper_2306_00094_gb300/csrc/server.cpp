@@ -133,6 +133,7 @@ struct nlfeti_server {
     std::list<CachedProblem> probs;
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;      // one per slot, alive until the server is destroyed
+    cudaStream_t alloc_stream = nullptr;    // allocations and frees of the workspaces (never captured)
 
     void charge(size_t b) {
         bytes += b;
@@ -306,6 +307,7 @@ struct nlfeti_server {
             e.bytes = ws_bytes;
             e.in_use = true;
             e.ws.reset(new SolveWS());
+            e.ws->alloc_stream = alloc_stream;
             wss.push_back(std::move(e));
             wsent = &wss.back();
             charge(ws_bytes);
@@ -399,11 +401,12 @@ struct nlfeti_server {
                 ws->async_stream = st;      // the slot's stream (the workspace may have served another)
                 const int64_t nd = p->n_dofs_total;
                 const size_t bytes_b = sizeof(double) * (size_t)nd * Rb;
-                if (ws->in_rhs.bytes < bytes_b) ws->in_rhs.alloc_async(st, bytes_b);
-                if (ws->out_u.bytes < bytes_b) ws->out_u.alloc_async(st, bytes_b);
+                if (ws->in_rhs.bytes < bytes_b) ws->in_rhs.alloc_async(alloc_stream, bytes_b);
+                if (ws->out_u.bytes < bytes_b) ws->out_u.alloc_async(alloc_stream, bytes_b);
                 bool any_g = false;
                 for (auto &r : batch) any_g |= r->has_g;
-                if (any_g && ws->in_g.bytes < bytes_b) ws->in_g.alloc_async(st, bytes_b);
+                if (any_g && ws->in_g.bytes < bytes_b) ws->in_g.alloc_async(alloc_stream, bytes_b);
+                NLF_CUDA(cudaStreamSynchronize(alloc_stream));
                 // the columns of the batch, then zero columns up to the bucket
                 size_t col = 0;
                 for (auto &r : batch) {
@@ -528,11 +531,17 @@ nlfeti_status nlfeti_server_create(nlfeti_ctx *ctx, size_t hbm_budget, int max_s
     s->ctx = ctx;
     s->budget = hbm_budget;
     s->slots = max_slots;
+    if (cudaStreamCreateWithFlags(&s->alloc_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return NLFETI_E_CUDA;
+    }
     for (int i = 0; i < max_slots; ++i) {
         cudaStream_t st = nullptr;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();
             for (auto x : s->streams) cudaStreamDestroy(x);
+            cudaStreamDestroy(s->alloc_stream);
             delete s;
             return NLFETI_E_CUDA;
         }
@@ -548,6 +557,7 @@ nlfeti_status nlfeti_server_create(nlfeti_ctx *ctx, size_t hbm_budget, int max_s
         s->cv_work.notify_all();
         for (auto &t : s->workers) t.join();
         for (auto x : s->streams) cudaStreamDestroy(x);
+        cudaStreamDestroy(s->alloc_stream);
         delete s;
         return NLFETI_E_INVALID;
     }
@@ -693,12 +703,14 @@ void nlfeti_server_destroy(nlfeti_server *s) {
     }
     s->cv_work.notify_all();
     for (auto &t : s->workers) t.join();
-    s->wss.clear();                         // stream-ordered frees on the slots' streams
     for (auto x : s->streams) cudaStreamSynchronize(x);
+    s->wss.clear();                         // stream-ordered frees on the allocation stream
+    cudaStreamSynchronize(s->alloc_stream);
     for (auto &c : s->probs)
         if (c.p) nlfeti_problem_destroy(c.p);
     s->probs.clear();
     for (auto x : s->streams) cudaStreamDestroy(x);
+    cudaStreamDestroy(s->alloc_stream);
     nlfeti_ctx *c = s->ctx;
     delete s;
     ctx_detach(c);

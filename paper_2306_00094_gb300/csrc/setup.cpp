@@ -115,8 +115,10 @@ template <typename F> void for_near(const Buckets &G, const std::vector<Box> &bb
 
 void build_decomposition(const MeshHost &m, const nlfeti_kernel &kern, const std::vector<int32_t> &labels, int K,
                          Decomp &d) {
-    if (K < 1 || K > 64) fail(NLFETI_E_INVALID, "K must be in [1, 64]");
+    if (K < 1 || K > kMaxSubdomains) fail(NLFETI_E_INVALID, "K must be in [1, 4096]");
     d.K = K;
+    const int W = (K + 63) / 64;
+    d.mask_words = W;
     d.nc = kern.type == NLFETI_K_PERIDYNAMIC ? 2 : 1;
     const int nc = d.nc;
     const int nv = m.dim + 1;
@@ -126,7 +128,7 @@ void build_decomposition(const MeshHost &m, const nlfeti_kernel &kern, const std
     make_buckets(m, bb, G);
     const double r_ext = (0.5 * kern.delta) * (1.0 + 1e-9);
     const double r_dir = kern.delta * (1.0 + 1e-9);
-    d.elem_mask.assign(m.n_elems, 0);
+    d.elem_mask.assign((size_t)m.n_elems * W, 0);
     std::vector<std::vector<int64_t>> parts(K);
     for (int64_t e = 0; e < m.n_elems; ++e) {
         if (m.elem_dir[e]) continue;
@@ -137,16 +139,17 @@ void build_decomposition(const MeshHost &m, const nlfeti_kernel &kern, const std
     std::vector<char> has_dir(K, 0);
     for (int k = 0; k < K; ++k) {
         if (parts[k].empty()) fail(NLFETI_E_INVALID, "empty local subdomain");
-        const uint64_t bit = uint64_t(1) << k;
+        const uint64_t bit = uint64_t(1) << (k % 64);
+        const int wk = k / 64;
         for (int64_t f : parts[k]) {
-            d.elem_mask[f] |= bit;
+            d.elem_mask[f * W + wk] |= bit;
             for_near(G, bb, bb[f], r_dir, [&](int64_t e) {
-                if (d.elem_mask[e] & bit) return;
+                if (d.elem_mask[e * W + wk] & bit) return;
                 if (m.elem_dir[e]) {
-                    d.elem_mask[e] |= bit;
+                    d.elem_mask[e * W + wk] |= bit;
                     has_dir[k] = 1;
                 } else if (box_gap(bb[e], bb[f], m.dim) <= r_ext) {
-                    d.elem_mask[e] |= bit;
+                    d.elem_mask[e * W + wk] |= bit;
                 }
             });
         }
@@ -155,30 +158,36 @@ void build_decomposition(const MeshHost &m, const nlfeti_kernel &kern, const std
     d.node_zeta.assign(m.n_nodes, 0);
     std::vector<std::vector<int32_t>> hat_nodes(K), dnodes(K);
     {
-        std::vector<uint64_t> node_mask(m.n_nodes, 0), node_dmask(m.n_nodes, 0);
+        std::vector<uint64_t> node_mask((size_t)m.n_nodes * W, 0), node_dmask((size_t)m.n_nodes * W, 0);
         for (int64_t e = 0; e < m.n_elems; ++e) {
-            uint64_t msk = d.elem_mask[e];
-            if (!msk) continue;
+            if (!d.any_sub(e)) continue;
             for (int i = 0; i < nv; ++i) {
                 int32_t n = m.elems[e * nv + i];
-                if (m.node_dir[n]) node_dmask[n] |= msk;
-                else if (!m.elem_dir[e]) node_mask[n] |= msk;
+                for (int w = 0; w < W; ++w) {
+                    const uint64_t msk = d.elem_mask[e * W + w];
+                    if (m.node_dir[n]) node_dmask[(int64_t)n * W + w] |= msk;
+                    else if (!m.elem_dir[e]) node_mask[(int64_t)n * W + w] |= msk;
+                }
             }
         }
         for (int64_t n = 0; n < m.n_nodes; ++n) {
-            uint64_t msk = node_mask[n];
-            d.node_zeta[n] = __builtin_popcountll(msk);
-            while (msk) {
-                int k = __builtin_ctzll(msk);
-                hat_nodes[k].push_back((int32_t)n);
-                msk &= msk - 1;
+            int z = 0;
+            for (int w = 0; w < W; ++w) {
+                uint64_t msk = node_mask[n * W + w];
+                z += __builtin_popcountll(msk);
+                while (msk) {
+                    int k = 64 * w + __builtin_ctzll(msk);
+                    hat_nodes[k].push_back((int32_t)n);
+                    msk &= msk - 1;
+                }
+                uint64_t dm = node_dmask[n * W + w];
+                while (dm) {
+                    int k = 64 * w + __builtin_ctzll(dm);
+                    dnodes[k].push_back((int32_t)n);
+                    dm &= dm - 1;
+                }
             }
-            uint64_t dm = node_dmask[n];
-            while (dm) {
-                int k = __builtin_ctzll(dm);
-                dnodes[k].push_back((int32_t)n);
-                dm &= dm - 1;
-            }
+            d.node_zeta[n] = z;
         }
     }
     d.nodes.assign(K, {});
@@ -219,11 +228,13 @@ void build_decomposition(const MeshHost &m, const nlfeti_kernel &kern, const std
     }
     // B: chain rows per interface node
     d.B_plus.clear(); d.B_minus.clear(); d.B_node.clear();
+    // per interface node, its subdomains in ascending order
+    std::vector<std::vector<int>> owners(m.n_nodes);
+    for (int k = 0; k < K; ++k)
+        for (const auto &kv : gpos[k]) owners[kv.first].push_back(k);
     for (int64_t n = 0; n < m.n_nodes; ++n) {
         if (d.node_zeta[n] < 2) continue;
-        std::vector<int> ks;
-        for (int k = 0; k < K; ++k)
-            if (gpos[k].count((int32_t)n)) ks.push_back(k);
+        const std::vector<int> &ks = owners[n];
         for (size_t j = 0; j + 1 < ks.size(); ++j) {
             int ka = ks[j], kb = ks[j + 1];
             for (int c = 0; c < nc; ++c) {

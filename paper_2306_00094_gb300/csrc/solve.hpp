@@ -49,7 +49,11 @@ struct SolveWS {
     DevMem cg_u, cg_r, cg_z, cg_p, cg_q, cg_b, cg_part;  // single-domain CG (global dofs x R)
     DevMem cg_ph, cg_pl;                                // p as FP32 hi / lo pairs (SpMV operand)
     std::vector<int> host_flag;
-    cudaStream_t async_stream = nullptr;   // set: stream-ordered allocations (server slots)
+    cudaStream_t async_stream = nullptr;   // set: the stream the workspace works on (a server slot's)
+    cudaStream_t alloc_stream = nullptr;   // set: stream-ordered allocations and frees of its buffers
+                                           // on this stream (a server's, never captured), so that a
+                                           // workspace freed by another slot never enqueues into a
+                                           // stream that is capturing a graph
     std::vector<PcgGraph> graphs;
     void ensure(nlfeti_problem *p, int R);
     void drop_graphs();

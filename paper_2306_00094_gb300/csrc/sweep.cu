@@ -14,8 +14,9 @@
 //
 // Pivot blocks are NB = 64 wide; a step is three launches over all subdomains: invert
 // the pivot block (one CTA per subdomain, in shared memory), form the pivot panels,
-// update all tiles (FP32 operators: 128x128 tiles on the tensor cores, split-TF32, in
-// sweep_tc.cuh; FP64 operators: 64x64 CTA tiles, 4x4 register blocking).  A non-positive pivot
+// update all tiles (64x64 CTA tiles, 4x4 register blocking; for the FP32 operators per the
+// factor_tc option 128x128 tiles on the tensor cores, split-TF32, in sweep_tc.cuh: by default
+// in the Omega sweep of A^k, the sweep of the pinned S_k staying on the FP32 pipes).  A non-positive pivot
 // sets the device status word (NLFETI_E_NOT_SPD) instead of trapping.
 #include <algorithm>
 #include <type_traits>
@@ -402,7 +403,7 @@ template <typename T> __global__ void k_project(T *Sppool, const SubdomainDesc *
 
 template <typename T> void run_sweeps(nlfeti_problem *p, T *pool, const std::vector<int64_t> &moff,
                                       const std::vector<int32_t> &mdim, const std::vector<int32_t> &mld,
-                                      const std::vector<int32_t> &pend, DevMem &scratch) {
+                                      const std::vector<int32_t> &pend, DevMem &scratch, bool allow_tc) {
     nlfeti_ctx *c = p->ctx;
     const int K = p->K;
     std::vector<int64_t> soff(K);
@@ -439,7 +440,7 @@ template <typename T> void run_sweeps(nlfeti_problem *p, T *pool, const std::vec
     const size_t smu = sizeof(T) * 2 * NB * TILE;
     NLF_CUDA(cudaFuncSetAttribute(k_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smu));
     // FP32 operators with factor_tc: the rank-64 updates on the tensor cores (split-TF32)
-    const bool tc = std::is_same<T, float>::value && p->opt.factor_tc == 1;
+    const bool tc = std::is_same<T, float>::value && allow_tc;
     const int ntc = (maxn + TC_TILE - 1) / TC_TILE;
     if (tc) NLF_CUDA(cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     for (int j0 = 0; j0 < maxp; j0 += NB) {
@@ -507,7 +508,7 @@ template <typename T> void factor_ops(nlfeti_problem *p, OpPool<T> &pool) {
         gld[k] = p->sd[k].ldG;
         gend[k] = p->sd[k].nG;
     }
-    run_sweeps<T>(p, pool.M.template as<T>(), moff, mdim, mld, pend, pool.scratch);
+    run_sweeps<T>(p, pool.M.template as<T>(), moff, mdim, mld, pend, pool.scratch, p->opt.factor_tc != 0);
     // S_k and the pinned copy
     int maxg = 0;
     for (auto &d : p->sd) maxg = std::max(maxg, d.nG);
@@ -517,7 +518,7 @@ template <typename T> void factor_ops(nlfeti_problem *p, OpPool<T> &pool) {
                                                pool.Sp.template as<T>(), p->d_sd.as<SubdomainDesc>());
         NLF_CUDA(cudaGetLastError());
         // phase 2: sweep all pivots of the pinned S~_k
-        run_sweeps<T>(p, pool.Sp.template as<T>(), soff, gdim, gld, gend, pool.scratch);
+        run_sweeps<T>(p, pool.Sp.template as<T>(), soff, gdim, gld, gend, pool.scratch, p->opt.factor_tc == 1);
         k_finish_inverse<T><<<g, 256, 0, c->stream>>>(pool.Sp.template as<T>(), p->d_sd.as<SubdomainDesc>());
         if (p->n_floating > 0) {
             DevMem V, C;

@@ -15,12 +15,15 @@
 //            hi lo, lo hi, mid mid; the rest lie below 2^-33 of the product) into accumulator 1,
 //            both FP32 in tensor memory (128 lanes = rows, 2 x 128 columns), so that the small
 //            terms are not added to the large ones inside the tensor core; committed to an
-//            mbarrier.  The two splits of FP32 data into TF32 pairs lose about 2 bits against
-//            the FP32 products of the SIMT kernel, which costs the mixed solve an extra
-//            refinement sweep; the third term restores FP32 accuracy;
+//            mbarrier.  The tensor core truncates while it accumulates, so the update carries a
+//            few times the rounding error of the FP32-pipe kernel: measured, harmless in the Omega
+//            sweep of A^k, but in the sweep of the pinned S_k it cost the mixed solve of the
+//            2-D constant-kernel workload an extra refinement sweep (26 -> 32 PCG iterations), so
+//            by default only the Omega sweep runs here;
 //   epilogue (8 warps): warp w reads lanes 32 (w mod 4).. of its column half, adds the two
-//            accumulators (acc0 + acc1) and applies the update (or the J-block values) to the
-//            tile, as the SIMT kernel does.
+//            accumulators (acc0 + acc1) and stages the tile in shared memory; then the tile of M
+//            is read, updated (or given the J-block values, as the SIMT kernel does) and written
+//            with 16-byte accesses along the rows.
 // The MMA wait is bounded: if it runs out the CTA sets the sweep's timeout word, waits once more
 // (bounded) for its MMAs, frees its tensor memory and returns without writing.
 #pragma once
@@ -31,6 +34,7 @@ constexpr int TC_ATOM = TC_TILE * 128;              // one 128-byte K atom of 12
 constexpr int TC_OP = 2 * TC_ATOM;                  // a 128 x 64 FP32 operand: 32 KB
 constexpr int TC_SMEM = 6 * TC_OP + 1024;           // A hi, mid, lo and B hi, mid, lo (+ 1 KB alignment)
 constexpr int TC_TMEM_COLS = 2 * TC_TILE;           // two FP32 accumulators
+constexpr int TC_CT = TC_TILE + 4;                  // row stride of the staged tile (floats)
 constexpr long long TC_WAIT_TRIES = 1ll << 24;
 
 __device__ __forceinline__ uint32_t tc_s32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -119,6 +123,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_update_tc(SweepArgs<float> a,
     unsigned char *sm = tc_raw + ((1024u - (tc_s32(tc_raw) & 1023u)) & 1023u);
     __shared__ uint64_t done_bar;
     __shared__ uint32_t tmem_base;
+    __shared__ int tc_fail;
     const int r0 = ti * TC_TILE, c0 = tl * TC_TILE;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     // ---- staging: three-term TF32 splits of the panels (A at 0, 1, 2 TC_OP; B at 3, 4, 5 TC_OP)
@@ -153,6 +158,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_update_tc(SweepArgs<float> a,
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 0) {
+        tc_fail = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_s32(&done_bar)), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -182,33 +188,70 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_update_tc(SweepArgs<float> a,
                          tc_s32(&done_bar))
                      : "memory");
     }
-    bool ok = tc_wait(&done_bar, 0, TC_WAIT_TRIES);
+    const bool ok = tc_wait(&done_bar, 0, TC_WAIT_TRIES);
     if (__any_sync(0xffffffffu, !ok)) {
-        ok = false;
-        if (lane == 0) atomicExch(tflag, 1);
+        if (lane == 0) {
+            atomicExch(tflag, 1);
+            tc_fail = 1;
+        }
         tc_wait(&done_bar, 0, TC_WAIT_TRIES);           // let the MMAs finish before freeing
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // ---- epilogue: warp w, lane quarter w mod 4 (one row per lane), column half w / 4
-    const int q4 = warp & 3, hf = warp >> 2;
-    const int i = r0 + 32 * q4 + lane;
-    const bool iJ = i >= j0 && i < j1;
+    // ---- epilogue, 1: warp w reads lane quarter w mod 4 (one row per lane) of its column half
+    // w / 4 from tensor memory, adds the two accumulators and stages the tile in shared memory
+    // (the operand buffers, no longer read once the MMAs are done), row stride TC_CT floats
+    float *ct = reinterpret_cast<float *>(sm);
+    {
+        const int q4 = warp & 3, hf = warp >> 2;
+        const int rl = 32 * q4 + lane;
 #pragma unroll 1
-    for (int cc = 0; cc < TC_TILE / 2; cc += 16) {
-        const int lc = hf * (TC_TILE / 2) + cc;
-        float v[16], v1[16];
-        tc_load16(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)lc, v);
-        tc_load16(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(TC_TILE + lc), v1);
+        for (int cc = 0; cc < TC_TILE / 2; cc += 16) {
+            const int lc = hf * (TC_TILE / 2) + cc;
+            float v[16], v1[16];
+            tc_load16(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)lc, v);
+            tc_load16(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(TC_TILE + lc), v1);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) v[e] += v1[e];
-        if (ok && i < n) {
+            for (int e = 0; e < 16; ++e) ct[rl * TC_CT + lc + e] = v[e] + v1[e];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // ---- epilogue, 2: the tile of M read, updated and written with the columns fastest (a warp
+    // covers one row of 128 columns); J rows and columns take their values from pan and D^-1
+    if (!tc_fail) {
+        const int c4 = (threadIdx.x % 32) * 4, rw = threadIdx.x / 32;
+        constexpr int RPT = TC_TILE / (TC_THREADS / 32);          // rows per thread: 16
+        const bool interior = r0 + TC_TILE <= n && c0 + TC_TILE <= n && (j1 <= r0 || j0 >= r0 + TC_TILE) &&
+                              (j1 <= c0 || j0 >= c0 + TC_TILE);
+        if (interior) {
+            // all 16 rows of the thread in flight at once (64 KB per CTA), then the updates
+            float4 m[RPT];
+#pragma unroll
+            for (int q = 0; q < RPT; ++q)
+                m[q] = *reinterpret_cast<const float4 *>(M + (int64_t)(r0 + rw + q * (TC_THREADS / 32)) * ld + c0 + c4);
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                const int rr = rw + q * (TC_THREADS / 32);
+                const float4 u = *reinterpret_cast<const float4 *>(ct + rr * TC_CT + c4);
+                m[q].x -= u.x; m[q].y -= u.y; m[q].z -= u.z; m[q].w -= u.w;
+                *reinterpret_cast<float4 *>(M + (int64_t)(r0 + rr) * ld + c0 + c4) = m[q];
+            }
+        }
+#pragma unroll 1
+        for (int rr = rw; rr < TC_TILE && !interior; rr += TC_THREADS / 32) {
+            const int i = r0 + rr;
+            const float4 u = *reinterpret_cast<const float4 *>(ct + rr * TC_CT + c4);
+            if (i >= n) continue;
+            const bool iJ = i >= j0 && i < j1;
+            const float uv[4] = {u.x, u.y, u.z, u.w};
             float *row = M + (int64_t)i * ld;
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int l = c0 + lc + e;
+            for (int e = 0; e < 4; ++e) {
+                const int l = c0 + c4 + e;
                 if (l >= n) break;
                 const bool lJ = l >= j0 && l < j1;
-                if (!iJ && !lJ) row[l] = row[l] - v[e];
+                if (!iJ && !lJ) row[l] = row[l] - uv[e];
                 else if (!iJ && lJ) row[l] = pan[(int64_t)i * NB + (l - j0)];
                 else if (iJ && !lJ) row[l] = pan[(int64_t)l * NB + (i - j0)];
                 else row[l] = -D[(i - j0) * NB + (l - j0)];

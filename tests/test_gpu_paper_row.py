@@ -1,12 +1,13 @@
-"""The paper's Table fixedHorizon, constant kernel, 6 x 6 row on the GPU (h = 0.004,
-delta = 0.008, 62001 dofs, 36 subdomains), with the manufactured problem of Sec. 6.2:
+"""The paper's Table fixedHorizon, constant kernel, 6 x 6 and 12 x 12 rows on the GPU (h = 0.004
+and 0.002, delta = 0.008: 62001 dofs on 36 subdomains and 249001 dofs on 144 subdomains), with
+the manufactured problem of Sec. 6.2:
 
 * the diagonally preconditioned CG on the single-domain system takes the paper's printed
   iteration count (343 at tolerance 1e-10; `tests/golden/paper_table_fixed_horizon.txt`):
   the count depends only on the matrix, the right-hand side and the tolerance, so this
   pins the assembled system (kernel constant, quadrature, mesh, loads) at the paper's size;
-* FETI in FP64 reaches the nodal values of u (delta / h = 2: exact at the nodes) and needs
-  no more iterations than the paper's 40 (the paper does not state its stopping norm).
+* FETI in FP64 reaches the nodal values of u (delta / h = 2 and 4: exact at the nodes) and
+  needs no more iterations than the paper's 40 (the paper does not state its stopping norm).
 """
 import os
 
@@ -20,9 +21,11 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_table_fixed_horizon.txt")
 
 
-def test_constant_6x6_row_cg_iterations_and_feti():
+@pytest.mark.parametrize("label", ["6x6", "12x12"])
+def test_constant_row_cg_iterations_and_feti(label):
     from paper_2306_00094_gb300 import binding
-    row = next(l.split() for l in open(GOLDEN) if l.startswith("constant 6x6"))
+    row = next(l.split() for l in open(GOLDEN) if l.startswith("constant " + label))
+    k = int(label.split("x")[0])
     cg_its, feti_its = int(row[3]), int(row[5])
     N, delta = int(round(1.0 / float(row[2]))), 0.008
     mesh = W.make_mesh(2, N, W.collar_cells(delta, N))
@@ -31,7 +34,7 @@ def test_constant_6x6_row_cg_iterations_and_feti():
     x, y = mesh.xy[:, 0], mesh.xy[:, 1]
     u = (x * x * y + y * y).reshape(-1, 1)
     f = (-2.0 * (1.0 + y)).reshape(-1, 1)
-    w = W.Workload("paper_6x6", mesh, kern, W.rect_labels(mesh, 6, 6), 36, np.asfortranarray(f), 0,
+    w = W.Workload("paper_" + label, mesh, kern, W.rect_labels(mesh, k, k), k * k, np.asfortranarray(f), 0,
                    g=np.asfortranarray(u))
     ctx = binding.Context()
     p = binding.Problem.from_workload(ctx, w)

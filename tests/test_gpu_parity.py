@@ -12,7 +12,8 @@
   meshes (irregular nodes and diagonals) with graph-grown local parts, the whole-element
   approximate balls (barycenter, 123vertices, 23vertices), the approxcaps ball (cap
   triangles on the nocaps polygon; structured and unstructured), Neumann volume constraints
-  (a free, loaded collar region on two sides) and the l2 (rounded-corner) collar.
+  (a free, loaded collar region on two sides), the l2 (rounded-corner) collar, and 81
+  subdomains (subdomain masks of more than one 64-bit word).
 """
 import numpy as np
 import pytest
@@ -43,6 +44,7 @@ CASES = {
     "l2_neumann": lambda: W.neumann_l2(N=24, k=3, nrhs=2),
     "pd_neumann": lambda: W.neumann_pd(N=30, k=3, nrhs=2),
     "l2_rounded_collar": lambda: W.l2_collar_const(N=24, k=3, nrhs=2, delta=0.15),
+    "l2_9x9": lambda: W.const_l2_2d(N=36, k=9, nrhs=2, delta=2.0 / 36),   # K = 81: more than 64 subdomains
 }
 
 
