@@ -127,6 +127,17 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 // 1-D bulk copy global -> shared memory completing on an mbarrier (16-byte aligned, bytes a
+// multiple of 16), with an L2 cache policy for the source
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, unsigned bytes, uint64_t *bar,
+                                              uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+// 1-D bulk copy global -> shared memory completing on an mbarrier (16-byte aligned, bytes a
 // multiple of 16)
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -184,6 +195,7 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
         if (lane == 0) {
             int q = 0;
             bool ok = true;
+            const uint64_t stream_policy = l2_evict_first_policy();
             for (int it = it0; it < it1 && ok; ++it) {
                 const int k = sched_items[2 * it], i0 = sched_items[2 * it + 1];
                 const int ncp = min(sd[k].ldG, (sd[k].nG + 7) / 8 * 8);
@@ -198,7 +210,8 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
                     }
                     unsigned char *stg = ring + s * STAGE;
                     mbar_arrive_expect_tx(&full[s], STAGE);
-                    bulk_g2s(stg, tiles + (int64_t)(l0 / MMA_KB) * (MMA_A_BYTES / 2), MMA_A_BYTES, &full[s]);
+                    bulk_g2s_hint(stg, tiles + (int64_t)(l0 / MMA_KB) * (MMA_A_BYTES / 2), MMA_A_BYTES, &full[s],
+                                  stream_policy);
                     tile_g2s(stg + MMA_A_BYTES, xmap, l0, 0, &full[s]);
                 }
             }

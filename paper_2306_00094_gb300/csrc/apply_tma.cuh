@@ -94,6 +94,25 @@ __device__ __forceinline__ void tile_g2s(void *dst, const CUtensorMap *map, int 
         : "memory");
 }
 
+// L2 policy of the streamed operator tiles: evicted first, so that a stream of operators larger
+// than L2 does not push out the vectors the next kernels read (the Lambda and U vectors of the
+// PCG, a few tens of MB, stay in L2 between the interface applies)
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// tile_g2s with an L2 cache policy for the source
+__device__ __forceinline__ void tile_g2s_hint(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar,
+                                              uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
 // tensor map of a row-major block (n rows of ld entries, 16-byte aligned rows) for tiles of
 // box_rows rows x box_bytes bytes: an operator (box_rows 32) or the R columns of x of one
 // subdomain in the apply layout (box_rows RC); encode: the driver's cuTensorMapEncodeTiled
@@ -177,6 +196,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
         if (withhold) return;
         int q = 0;
         bool ok = true;
+        const uint64_t stream_policy = l2_evict_first_policy();
         for (int it = it0; it < it1 && ok; ++it) {
             // descriptor fields in registers: the asm statements below clobber memory
             const int k = sched_items[2 * it], i0 = sched_items[2 * it + 1];
@@ -197,7 +217,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
                 if (lane == 0) {
                     unsigned char *stg = ring + s * STAGE;
                     mbar_arrive_expect_tx(&full[s], STAGE);
-                    tile_g2s(stg, map, l0, i0, &full[s]);
+                    tile_g2s_hint(stg, map, l0, i0, &full[s], stream_policy);
                     tile_g2s(stg + 32 * MROW, xmap, l0, c0, &full[s]);
                 }
                 __syncwarp();

@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(RES_THREADS)
         // ------------------------------------------------------------------ producer
         int q = 0;
         bool ok = true;
+        const uint64_t stream_policy = l2_evict_first_policy();
         for (int it = it0; it < it1 && ok; ++it) {
             const int k = sched_items[2 * it], i0 = sched_items[2 * it + 1];
             const int ld = sd[k].ldM, n = sd[k].nk;
@@ -74,8 +75,8 @@ __global__ void __launch_bounds__(RES_THREADS)
                     if (lane == 0) {
                         unsigned char *stg = ring + s * STAGE;
                         mbar_arrive_expect_tx(&full[s], STAGE);
-                        tile_g2s(stg, ahi, l0, i0, &full[s]);
-                        tile_g2s(stg + 32 * RES_CB, alo, l0, i0, &full[s]);
+                        tile_g2s_hint(stg, ahi, l0, i0, &full[s], stream_policy);
+                        tile_g2s_hint(stg + 32 * RES_CB, alo, l0, i0, &full[s], stream_policy);
                         tile_g2s(stg + 64 * RES_CB, uhm, 2 * l0, c0 / 2, &full[s]);
                         tile_g2s(stg + (64 + 2 * res_pairs(RC)) * RES_CB, ulm, 2 * l0, c0 / 2, &full[s]);
                     }
