@@ -51,16 +51,16 @@ METRIC = "FETI solves/sec at rel. error 1e-8 + p50/p99 latency: batched mixed vs
 # beside it.
 WORKLOADS = {
     "peridynamic_2d": (
-        lambda: W.peridynamic_2d(),
+        lambda **kw: W.peridynamic_2d(**kw),
         "2-D bond-based peridynamics, micromodulus 3/delta^3 xi xi^T/|xi|^3 on the l2 ball (nocaps), "
         "delta=3h, h=1/256 (130050 dofs, 2 per node), 8x8 subdomains with seeded jittered cuts "
         "(+-20%, seed 4), 16 RHS N(0,1) loads per dof (seed 5)"),
     "fractional_2d": (
-        lambda: W.fractional_2d(),
+        lambda **kw: W.fractional_2d(**kw),
         "2-D fractional kernel (2-2s)/(pi delta^(2-2s)) |x-y|^-(2+2s), s=0.5, truncated at delta=0.2, "
         "h=1/96 (9025 dofs), 6x6 subdomains (Omega_k empty on the interior ones), 64 RHS N(0,1) loads (seed 3)"),
     "const_l2_2d": (
-        lambda: W.const_l2_2d(),
+        lambda **kw: W.const_l2_2d(**kw),
         "2-D nonlocal diffusion, constant kernel 4/(pi delta^4) on the l2 ball (nocaps), delta=0.1, "
         "h=1/128 (16129 dofs), 4x4 subdomains, 8 RHS N(0,1) loads (seed 2)"),
 }
@@ -248,7 +248,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
     name = args.workload
-    w = WORKLOADS[name][0]()
+    w = WORKLOADS[name][0](**({"N": args.cells} if args.cells else {}))
     R = w.nrhs
     ctx = binding.Context()
     t0 = time.perf_counter()
@@ -282,18 +282,32 @@ def run_ours(args):
     for _ in range(args.warmup):
         st = step()
     torch.cuda.synchronize()
+    if args.profile_range == "factor":
+        # one FP32 factorization inside a CUDA profiler range (ncu --profile-from-start off)
+        torch.cuda.profiler.start()
+        prob.factor(2)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        if rank == 0:
+            print(json.dumps({"note": "one FP32 factorization in the profiler range", "workload": name,
+                              "cells": args.cells}), flush=True)
+        return
     prob.profile()                       # reset counters
     sampler = ClockSampler(local)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    if args.profile_range == "solve":
+        torch.cuda.profiler.start()
     ev[0].record()
     stats = []
     for k in range(args.steps):
         stats.append(step())
         ev[k + 1].record()
     torch.cuda.synchronize()
+    if args.profile_range == "solve":
+        torch.cuda.profiler.stop()
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
@@ -303,10 +317,11 @@ def run_ours(args):
     value = replica_throughput(R * args.steps, world, total_ms / 1e3)
     u_gpu = d_out.cpu().numpy().T.copy()
 
-    if args.only_timed:
+    if args.only_timed or args.cells:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s", "ms_per_step": total_ms / args.steps,
-                              "gpu_launches": launches, "note": "timed steps only"}), flush=True)
+                              "gpu_launches": launches, "workload": name, "cells": args.cells,
+                              "note": "timed steps only (a profiling run, not a bench line)"}), flush=True)
         return
 
     # roofline of the dominant kernels (dense interface applies) over a second timed region
@@ -319,8 +334,14 @@ def run_ours(args):
                              f"{args.steps} steps",
                    "traffic": profile_traffic(kernel_source_hash(), f"k_apply_tma_{name}.md")})
     if hp:
-        hp.update({"kernel": "k_apply_tma<float, .., __half> (preconditioner S_k apply, FP16 copy)",
-                   "traffic": profile_traffic(kernel_source_hash(), f"k_apply_tma_fp16_{name}.md")})
+        tc_pre = any(e["kind"] == 1 and e["rc"] == -1 for e in tuned) or args.tensor_core_precond
+        if tc_pre:
+            hp.update({"kernel": "k_apply_mma (preconditioner S_k apply on the tensor cores: tcgen05 kind::f16, "
+                                 "FP16 copy, FP32 accumulators in tensor memory)",
+                       "traffic": profile_traffic(kernel_source_hash("apply_mma.cuh"), f"k_apply_mma_{name}.md")})
+        else:
+            hp.update({"kernel": "k_apply_tma<float, .., __half> (preconditioner S_k apply, FP16 copy)",
+                       "traffic": profile_traffic(kernel_source_hash(), f"k_apply_tma_fp16_{name}.md")})
 
     # end to end through the C ABI with pinned host buffers
     h_rhs = torch.empty((R, ndof), dtype=torch.float64, pin_memory=True)
@@ -450,7 +471,8 @@ def run_ours(args):
                  "setup_factor_solve_s": cold_s},
         "autotune": {"seconds": t_tune, "choices": [
             {"operator": ["FP32 S_k^+ / S_k", "FP16 copy of S_k", "FP64 S_k^+ / S_k"][e["kind"]],
-             "rhs_per_pass": e["rc"], "ctas_per_sm": e["ctas_per_sm"], "us_per_launch": e["us"],
+             "rhs_per_pass": e["rc"], "ctas_per_sm": e["ctas_per_sm"], "rows_per_warp": e["rows_per_warp"],
+             "us_per_launch": e["us"],
              "from_cache": bool(e["from_cache"])} for e in tuned]},
         "other_workloads": others,
         "unstructured": unstr_res,
@@ -844,6 +866,12 @@ def main():
     ap.add_argument("--headline-only", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-timed", action="store_true", help="setup, warm-up and the timed steps only (for ncu)")
+    ap.add_argument("--cells", type=int, default=0,
+                    help="profiling: the workload at h = 1/CELLS (same kernel, subdomains and right-hand "
+                         "sides) for ncu captures that must stay small; implies --only-timed")
+    ap.add_argument("--profile-range", choices=["solve", "factor"], default=None,
+                    help="profiling: wrap the timed steps (solve) or one extra FP32 factorization (factor) "
+                         "in a CUDA profiler range, for ncu --profile-from-start off")
     ap.add_argument("--tensor-core-precond", action="store_true",
                     help="the timed mixed solve applies the preconditioner's S_k on the tensor cores "
                          "(precond_fp16 = 2; default: the FP16 copy on the FP32 pipes)")

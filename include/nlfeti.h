@@ -235,7 +235,9 @@ nlfeti_status nlfeti_problem_set_matrix(nlfeti_problem *p, int k, const double *
  * S_k^+ and S_k in every PCG iteration; the paper has no counterpart, its subdomain solves run
  * on CPUs).  Its shape for nrhs right-hand sides: rc, the right-hand sides per streamed pass
  * over the operator (1, 2, 4, 8 or 16, at most nrhs; 8 for FP64: fewer passes read the operator
- * fewer times but hold more accumulators), and ctas_per_sm (1 or 2) of its persistent grid.
+ * fewer times but hold more accumulators), ctas_per_sm (1 or 2) of its persistent grid, and
+ * rows_per_warp (4, or 8 for the FP32 and FP16 operators with rc >= 4: half the consumer warps,
+ * each shared-memory load of x serving twice the rows).
  * nlfeti_autotune times every candidate with CUDA events on the problem's factored operators
  * for each operator kind it has -- 0 FP32 S_k^+ and S_k, 1 the FP16 copy of S_k the mixed
  * path's preconditioner applies, 2 FP64 -- and keeps the fastest in the problem: later solves
@@ -250,16 +252,19 @@ nlfeti_status nlfeti_problem_set_matrix(nlfeti_problem *p, int k, const double *
  * width and schedule); the tensor-core preconditioner rounds differently (it only steers the
  * PCG: the iteration count may change, not the accuracy reached).
  * nlfeti_set_apply_choice pins a shape (rc 0 clears it, back to the default: the widest block
- * up to nrhs, two CTAs per SM; rc -1 selects the tensor-core apply for kind 1);
+ * up to nrhs, two CTAs per SM, 4 rows per warp; rc -1 selects the tensor-core apply for kind 1;
+ * rows_per_warp 0 means 4);
  * NLFETI_E_INVALID for shapes outside the lists above. */
 typedef struct {
     int32_t kind, nrhs, rc, ctas_per_sm;
     double us;              /* mean time per apply launch of the chosen shape */
     int32_t from_cache;
+    int32_t rows_per_warp;  /* 4 or 8 */
 } nlfeti_tune_entry;
 nlfeti_status nlfeti_autotune(nlfeti_problem *p, int nrhs, const char *cache_path, nlfeti_tune_entry *out,
                               int *n_out);
-nlfeti_status nlfeti_set_apply_choice(nlfeti_problem *p, int kind, int nrhs, int rc, int ctas_per_sm);
+nlfeti_status nlfeti_set_apply_choice(nlfeti_problem *p, int kind, int nrhs, int rc, int ctas_per_sm,
+                                      int rows_per_warp);
 
 /* Fault injection for tests of the bounded device waits (not for production use; the paper has
  * no counterpart).  The batched interface apply (a persistent bulk-copy pipeline) bounds every

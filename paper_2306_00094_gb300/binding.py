@@ -73,7 +73,7 @@ class ServerInfo(C.Structure):
 
 class TuneEntry(C.Structure):
     _fields_ = [("kind", C.c_int32), ("nrhs", C.c_int32), ("rc", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("us", C.c_double), ("from_cache", C.c_int32)]
+                ("us", C.c_double), ("from_cache", C.c_int32), ("rows_per_warp", C.c_int32)]
 
 
 class Mesh(C.Structure):
@@ -129,7 +129,7 @@ def load(build_if_missing: bool = True):
         "nlfeti_problem_set_matrix": (i32, [vp, i32, vp]),
         "nlfeti_debug_apply_waits": (i32, [vp, C.c_longlong, i32]),
         "nlfeti_autotune": (i32, [vp, i32, C.c_char_p, C.POINTER(TuneEntry), C.POINTER(C.c_int)]),
-        "nlfeti_set_apply_choice": (i32, [vp, i32, i32, i32, i32]),
+        "nlfeti_set_apply_choice": (i32, [vp, i32, i32, i32, i32, i32]),
         "nlfeti_apply": (i32, [vp, i32, i32, i32, vp, vp]),
         "nlfeti_set_profiling": (i32, [vp, i32]),
         "nlfeti_get_profile": (i32, [vp, C.POINTER(Profile)]),
@@ -351,8 +351,9 @@ class Problem:
                                                     arr, C.byref(n)))
         return [{k: getattr(arr[i], k) for k, _ in TuneEntry._fields_} for i in range(n.value)]
 
-    def set_apply_choice(self, kind, nrhs, rc, ctas_per_sm=2, raise_on_error=True):
-        code = self.ctx.lib.nlfeti_set_apply_choice(self.h, int(kind), int(nrhs), int(rc), int(ctas_per_sm))
+    def set_apply_choice(self, kind, nrhs, rc, ctas_per_sm=2, rows_per_warp=4, raise_on_error=True):
+        code = self.ctx.lib.nlfeti_set_apply_choice(self.h, int(kind), int(nrhs), int(rc), int(ctas_per_sm),
+                                                    int(rows_per_warp))
         if raise_on_error:
             self.ctx.check(code)
         return code

@@ -769,12 +769,15 @@ nlfeti_status nlfeti_autotune(nlfeti_problem *p, int nrhs, const char *cache_pat
                 out[i].ctas_per_sm = res[i].per_sm;
                 out[i].us = res[i].us;
                 out[i].from_cache = res[i].from_cache ? 1 : 0;
+                out[i].rows_per_warp = res[i].rpw;
             }
     });
 }
 
-nlfeti_status nlfeti_set_apply_choice(nlfeti_problem *p, int kind, int nrhs, int rc, int ctas_per_sm) {
+nlfeti_status nlfeti_set_apply_choice(nlfeti_problem *p, int kind, int nrhs, int rc, int ctas_per_sm,
+                                      int rows_per_warp) {
     if (!p || kind < 0 || kind > 2 || nrhs < 1) return NLFETI_E_INVALID;
+    if (rows_per_warp == 0) rows_per_warp = 4;
     return guarded(p->ctx, [&] {
         if (rc == 0) {
             p->tune.erase({kind, nrhs});
@@ -789,7 +792,10 @@ nlfeti_status nlfeti_set_apply_choice(nlfeti_problem *p, int kind, int nrhs, int
             if (!pow2 || (kind == 2 && rc > 8) || (rc > nrhs && rc > 1) || (ctas_per_sm != 1 && ctas_per_sm != 2))
                 fail(NLFETI_E_INVALID, "column block must be 1, 2, 4, 8 or 16 (8 for FP64) and at most nrhs; "
                                        "CTAs per SM 1 or 2");
-            p->tune[{kind, nrhs}] = ApplyChoice{rc, ctas_per_sm, 0};
+            if (rows_per_warp != 4 && (rows_per_warp != 8 || kind == 2 || rc < 4))
+                fail(NLFETI_E_INVALID, "rows per warp must be 4, or 8 for the FP32 and FP16 operators with a "
+                                       "column block of at least 4");
+            p->tune[{kind, nrhs}] = ApplyChoice{rc, ctas_per_sm, 0, rows_per_warp};
         }
         ++p->tune_gen;
     });

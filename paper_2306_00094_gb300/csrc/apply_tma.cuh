@@ -2,16 +2,19 @@
 // streamed by the bulk-copy engine.
 //
 // Persistent CTAs (a host-built schedule gives each CTA a list of 32-row work items, balanced
-// by their cost).  Warp 8 is the producer: for every item of the CTA and every chunk of
+// by their cost).  The last warp is the producer: for every item of the CTA and every chunk of
 // APPLY_CB bytes of columns it loads the 32 x APPLY_CB tile of the item's rows and the same
 // columns of RC right-hand sides of x with two 2-D tensor copies (tensor maps per subdomain
 // operator and per subdomain block of x in the apply layout; rows past n_gamma or past R
 // arrive as zeros) into a ring of NS shared-memory stages, each signalled by an mbarrier
-// with the byte count of its copies.  Warps 0..7 consume: warp w owns rows 4w..4w+3 of the item, each lane 4
-// (FP32) or 2 (FP64) consecutive columns per 128-/64-column step, in the same per-lane order
-// of operations as the register-streaming row kernel, so both give bitwise the same y.  A consumed stage is released to the producer
-// through a second mbarrier.  The producer runs ahead across item boundaries, so the copy
-// engine keeps up to NS * 32 KB per CTA in flight while the consumers compute.
+// with the byte count of its copies.  The other warps consume: with RPW rows per warp (4:
+// eight consumer warps; 8: four, each x vector read from shared memory then serves 8 rows),
+// warp w owns rows RPW w .. RPW w + RPW - 1 of the item, each lane 4 (FP32) or 2 (FP64)
+// consecutive columns per 128-/64-column step, in the same per-lane order of operations as the
+// register-streaming row kernel, so every variant gives bitwise the same y.  A consumed stage
+// is released to the producer through a second mbarrier.  The producer runs ahead across item
+// boundaries, so the copy engine keeps up to NS stages per CTA in flight while the consumers
+// compute.
 // With more than RC right-hand sides the rows of an item are streamed once per block of RC.
 // The operator may be stored in a narrower type MT than the arithmetic type T (FP16 copy of
 // S_k for the preconditioner of the mixed path): a stage then holds the same columns with
@@ -45,7 +48,14 @@ __host__ __device__ constexpr int apply_stage_bytes(int rc, int mrow = APPLY_CB)
 __host__ __device__ constexpr int apply_smem_bytes(int rc, int ns, int mrow = APPLY_CB) {
     return ns * apply_stage_bytes(rc, mrow) + 1024;
 }
-constexpr int APPLY_THREADS = 9 * 32;               // 8 consumer warps + 1 producer warp
+// rows of an item per consumer warp: 4 (eight consumer warps) or 8 (four consumer warps, twice
+// the accumulators per lane; each x vector loaded from shared memory serves 8 rows instead of 4)
+__host__ __device__ constexpr int apply_threads(int rpw) { return (32 / rpw + 1) * 32; }
+constexpr int APPLY_THREADS = apply_threads(4);     // 8 consumer warps + 1 producer warp
+// stages of a one-CTA-per-SM variant: as many as fit in 200 KB, at most 8
+__host__ __device__ constexpr int apply_ns_one(int rc, int mrow) {
+    return (200 * 1024) / (32 * mrow + rc * APPLY_CB) < 8 ? (200 * 1024) / (32 * mrow + rc * APPLY_CB) : 8;
+}
 constexpr long long APPLY_WAIT_TRIES = 1ll << 24;   // bounded mbarrier waits (seconds)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -162,14 +172,17 @@ __device__ __forceinline__ void apply_shape(const SubdomainDesc &d, int &n, int 
 //   FORCING   y[(offU + i) R + c] = xa[(offV + n_O + i) R + c] - acc   (reduced forcing, f_G - T_k f_O);
 //   BACKSUB   y[(offV + i) R + c] = -acc                              (u_O from the swept -A_OO^-1 rows),
 // the same outputs, in the same order of operations per lane, as k_rows.
-template <typename T, int RC, int NS = APPLY_NS, int MINB = APPLY_MINB, typename MT = T, int MODE = ROWS_APPLY>
-__global__ void __launch_bounds__(APPLY_THREADS, MINB)
+template <typename T, int RC, int NS = APPLY_NS, int MINB = APPLY_MINB, typename MT = T, int MODE = ROWS_APPLY,
+          int RPW = 4>
+__global__ void __launch_bounds__(apply_threads(RPW), MINB)
     k_apply_tma(const CUtensorMap *maps, const CUtensorMap *xmaps, int use_sp, const SubdomainDesc *sd,
                 const int32_t *sched_ptr, const int32_t *sched_items, double *y, int R, const int *gate, int *err,
                 double oscale = 1.0, const double *xa = nullptr, long long wait_tries = APPLY_WAIT_TRIES,
                 int withhold = 0) {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
+    constexpr int NCW = 32 / RPW;                   // consumer warps (the producer is warp NCW)
+    static_assert(RPW == 4 || RPW == 8, "4 or 8 rows per consumer warp");
     constexpr int CW = APPLY_CB / (int)sizeof(T);   // columns per stage row
     constexpr int MROW = CW * (int)sizeof(MT);      // operator bytes per stage row
     constexpr int STAGE = apply_stage_bytes(RC, MROW);
@@ -182,14 +195,14 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 8);
+            mbar_init(&empty[s], NCW);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     const int it0 = sched_ptr[blockIdx.x], it1 = sched_ptr[blockIdx.x + 1];
-    if (warp == 8) {
+    if (warp == NCW) {
         // ------------------------------------------------------------------ producer
         // withhold (fault injection for tests of the bounded waits): issue nothing, so that the
         // consumers' first stage wait runs out with no copy in flight
@@ -237,12 +250,12 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
         int n, ncp;
         apply_shape<MODE>(sd[k], n, ncp);
         const int64_t yoff = sd[k].offU, voff = sd[k].offV, nO = sd[k].nO;
-        const int ib = i0 + warp * 4;
+        const int ib = i0 + warp * RPW;
         for (int c0 = 0; c0 < R; c0 += RC) {
             const int rc = min(RC, R - c0);
-            T acc[4][RC];
+            T acc[RPW][RC];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < RPW; ++r)
 #pragma unroll
                 for (int c = 0; c < RC; ++c) acc[r][c] = T(0);
             for (int l0 = 0; l0 < ncp; l0 += CW, ++q) {
@@ -258,21 +271,30 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
                 // without bounds tests: the extra products are exact zeros and the rows and
                 // columns past the operator are never stored
                 if (ib < n) {
-#pragma unroll
+#pragma unroll(RPW == 8 ? 1 : 8)
                     for (int j = 0; j < CW / (32 * W); ++j) {
                         const int l = lane * W + j * 32 * W;
-                        V mv[4];
+                        if constexpr (RPW == 8) {
+                            // eight rows: the lane's 4 columns in two halves (bitwise the same sums)
+                            static_assert(std::is_same<T, float>::value, "eight rows per warp: FP32 arithmetic");
+                            rows_step_pairs<RC, RPW, MT>(st + (warp * RPW) * CW + l, CW, xs + l, CW, acc);
+                        } else {
+                            V mv[RPW];
 #pragma unroll
-                        for (int r = 0; r < 4; ++r) mv[r] = load_widen<T, MT>(st + (warp * 4 + r) * CW + l);
-                        rows_step<T, RC>(mv, [&](int c) { return *reinterpret_cast<const V *>(xs + c * CW + l); }, acc);
+                            for (int r = 0; r < RPW; ++r) mv[r] = load_widen<T, MT>(st + (warp * RPW + r) * CW + l);
+                            rows_step<T, RC>(mv, [&](int c) { return *reinterpret_cast<const V *>(xs + c * CW + l); },
+                                             acc);
+                        }
                     }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
             }
-            // lane sums by reduce-scatter in groups of at most 8 columns (4 rows x 8 = 32 values,
-            // one per lane): every sum takes the same shuffle tree whatever RC is
+            // lane sums by reduce-scatter in groups of 4 rows and at most 8 columns (4 x 8 = 32
+            // values, one per lane): every sum takes the same shuffle tree whatever RC and RPW are
             constexpr int CG = RC < 8 ? RC : 8;
+#pragma unroll
+            for (int rh = 0; rh < RPW; rh += 4)
 #pragma unroll
             for (int g0 = 0; g0 < RC; g0 += CG) {
                 constexpr int NV = 4 * CG;
@@ -280,10 +302,10 @@ __global__ void __launch_bounds__(APPLY_THREADS, MINB)
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int c = 0; c < CG; ++c) v[r * CG + c] = acc[r][g0 + c];
+                    for (int c = 0; c < CG; ++c) v[r * CG + c] = acc[rh + r][g0 + c];
                 const T tot = warp_reduce_scatter<T, NV>(v, lane);
                 constexpr int G = 32 / NV;
-                const int idx = lane / G, r = idx / CG, c = g0 + idx % CG, i = ib + r;
+                const int idx = lane / G, r = idx / CG, c = g0 + idx % CG, i = ib + rh + r;
                 if (lane % G == 0 && c < rc && i < n) {
                     if (MODE == ROWS_APPLY) y[(yoff + i) * R + c0 + c] = (double)tot * oscale;
                     else if (MODE == ROWS_FORCING)

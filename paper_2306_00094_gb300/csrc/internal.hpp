@@ -73,6 +73,7 @@ template <typename T> void upload(nlfeti_ctx *c, DevMem &m, const std::vector<T>
 
 // ------------------------------------------------------------------ host decomposition
 constexpr int kMaxSubdomains = 4096;
+constexpr int kMaxCoarse = 3 * kMaxSubdomains;     // coarse columns: at most three rigid modes per subdomain
 
 struct Decomp {
     int K = 0, nc = 1;
@@ -178,6 +179,7 @@ struct ApplyChoice {
     int rc = 0;
     int per_sm = 2;
     int mma = 0;
+    int rpw = 4;      // rows per consumer warp of the bulk-copy apply (4 or 8)
 };
 
 struct nlfeti_problem {

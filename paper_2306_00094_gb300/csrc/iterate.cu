@@ -30,6 +30,8 @@
 namespace nlf {
 namespace {
 
+template <typename X> struct TypeTag { using type = X; };
+
 constexpr int RED_BLOCKS = 304;     // two CTAs per SM for reductions
 constexpr int RED_THREADS = 256;
 
@@ -1354,17 +1356,52 @@ struct Runner {
         const int32_t *sptr = (one ? p->d_sched1_ptr : p->d_sched_ptr).as<int32_t>();
         const int32_t *sitems = (one ? p->d_sched1_items : p->d_sched_items).as<int32_t>();
         if (!xm) fail(NLFETI_E_INVALID, "no tensor maps for the chosen column block");
+        // one variant of the kernel: NS stages, MINB CTAs per SM in its register budget, RPW rows
+        // per consumer warp, operator stored as MT
+        auto launch = [&](auto ns_tag, auto minb_tag, auto rpw_tag, auto rc_tag, auto mt_tag) {
+            constexpr int NS = decltype(ns_tag)::value, MINB = decltype(minb_tag)::value;
+            constexpr int RPW = decltype(rpw_tag)::value, RCT = decltype(rc_tag)::value;
+            using MT = typename decltype(mt_tag)::type;
+            constexpr int MROW = APPLY_CB / (int)sizeof(T) * (int)sizeof(MT);
+            const CUtensorMap *maps = std::is_same<MT, T>::value ? pool.maps.template as<CUtensorMap>()
+                                                                 : pool.hmaps.template as<CUtensorMap>();
+            k_apply_tma<T, RCT, NS, MINB, MT, ROWS_APPLY, RPW>
+                <<<ctas, apply_threads(RPW), apply_smem_bytes(RCT, NS, MROW), st>>>(
+                    maps, xm, std::is_same<MT, T>::value ? use_sp : 0, sd, sptr, sitems, y, R, gate, S.err,
+                    std::is_same<MT, T>::value ? 1.0 : 1.0 / pool.hscale, nullptr, wait_tries(), p->dbg_withhold);
+        };
+        using I1 = std::integral_constant<int, 1>;
+        using I2 = std::integral_constant<int, 2>;
+        using I4 = std::integral_constant<int, 4>;
+        using I8 = std::integral_constant<int, 8>;
         auto go = [&](auto rc_tag) {
             constexpr int RCT = decltype(rc_tag)::value;
             if constexpr (std::is_same<T, float>::value) {
-                if (half) {
-                    constexpr int NSH = RCT >= 16 ? APPLY_NS_H16 : APPLY_NS_H;
-                    k_apply_tma<float, RCT, NSH, APPLY_MINB, __half>
-                        <<<ctas, APPLY_THREADS, apply_smem_bytes(RCT, NSH, APPLY_CB / 2), st>>>(
-                            pool.hmaps.template as<CUtensorMap>(), xm, 0, sd, sptr, sitems, y, R, gate, S.err,
-                            1.0 / pool.hscale, nullptr, wait_tries(), p->dbg_withhold);
+                // one CTA per SM with eight or more columns: its own instantiation (the register
+                // budget of one CTA, a deeper ring)
+                if constexpr (RCT >= 8) {
+                  if (one) {
+                    if (half) {
+                        using NS1 = std::integral_constant<int, apply_ns_one(RCT, APPLY_CB / 2)>;
+                        if (ch.rpw == 8) launch(NS1{}, I1{}, I8{}, rc_tag, TypeTag<__half>{});
+                        else launch(NS1{}, I1{}, I4{}, rc_tag, TypeTag<__half>{});
+                    } else {
+                        using NS1 = std::integral_constant<int, apply_ns_one(RCT, APPLY_CB)>;
+                        if (ch.rpw == 8) launch(NS1{}, I1{}, I8{}, rc_tag, TypeTag<float>{});
+                        else launch(NS1{}, I1{}, I4{}, rc_tag, TypeTag<float>{});
+                    }
                     return;
+                  }
                 }
+                if (half) {
+                    using NSH = std::integral_constant<int, RCT >= 16 ? APPLY_NS_H16 : APPLY_NS_H>;
+                    if constexpr (RCT >= 4)
+                        if (ch.rpw == 8) return launch(NSH{}, I2{}, I8{}, rc_tag, TypeTag<__half>{});
+                    return launch(NSH{}, I2{}, I4{}, rc_tag, TypeTag<__half>{});
+                }
+                using NSF = std::integral_constant<int, APPLY_NS>;
+                if constexpr (RCT >= 4)
+                    if (ch.rpw == 8) return launch(NSF{}, I2{}, I8{}, rc_tag, TypeTag<float>{});
             }
             k_apply_tma<T, RCT><<<ctas, APPLY_THREADS, apply_smem_bytes(RCT, APPLY_NS), st>>>(
                 pool.maps.template as<CUtensorMap>(), xm, use_sp, sd, sptr, sitems, y, R, gate, S.err, 1.0, nullptr,
@@ -2211,7 +2248,7 @@ std::string tune_key(const nlfeti_problem *p, int kind, int R) {
 
 struct CacheLine {
     std::string key;
-    int kind = 0, R = 0, rc = 0, per_sm = 0;
+    int kind = 0, R = 0, rc = 0, per_sm = 0, rpw = 4;
     double us = 0;
 };
 
@@ -2227,6 +2264,9 @@ std::vector<CacheLine> read_tune_cache(const char *path) {
         if (sscanf(line, " {\"key\": \"%63[0-9a-f]\", \"kind\": %d, \"R\": %d, \"rc\": %d, \"ctas_per_sm\": %d, \"us\": %lf",
                    key, &c.kind, &c.R, &c.rc, &c.per_sm, &c.us) == 6) {
             c.key = key;
+            const char *w = strstr(line, "\"rows_per_warp\": ");
+            if (w && sscanf(w, "\"rows_per_warp\": %d", &c.rpw) != 1) c.rpw = 4;
+            if (c.rpw != 4 && c.rpw != 8) c.rpw = 4;
             out.push_back(c);
         }
     }
@@ -2240,8 +2280,11 @@ void write_tune_cache(const char *path, const std::vector<CacheLine> &v) {
     if (!f) return;
     fprintf(f, "{\"entries\": [\n");
     for (size_t i = 0; i < v.size(); ++i)
-        fprintf(f, "  {\"key\": \"%s\", \"kind\": %d, \"R\": %d, \"rc\": %d, \"ctas_per_sm\": %d, \"us\": %.3f}%s\n",
-                v[i].key.c_str(), v[i].kind, v[i].R, v[i].rc, v[i].per_sm, v[i].us, i + 1 < v.size() ? "," : "");
+        fprintf(f,
+                "  {\"key\": \"%s\", \"kind\": %d, \"R\": %d, \"rc\": %d, \"ctas_per_sm\": %d, \"us\": %.3f, "
+                "\"rows_per_warp\": %d}%s\n",
+                v[i].key.c_str(), v[i].kind, v[i].R, v[i].rc, v[i].per_sm, v[i].us, v[i].rpw,
+                i + 1 < v.size() ? "," : "");
     fprintf(f, "]}\n");
     fclose(f);
     std::rename(tmp.c_str(), path);
@@ -2278,6 +2321,7 @@ void autotune_applies(nlfeti_problem *p, int R, const char *cache_path, std::vec
                 if (c.key == key && c.kind == kind && c.R == R) {
                     te.rc = c.rc;
                     te.per_sm = c.per_sm;
+                    te.rpw = c.rpw;
                     te.us = c.us;
                     te.from_cache = true;
                 }
@@ -2287,8 +2331,11 @@ void autotune_applies(nlfeti_problem *p, int R, const char *cache_path, std::vec
                 for (int rc = 1; rc <= 16; rc *= 2) {
                     if (rc > R && rc > 1) break;
                     if (kind == 2 && rc > 8) break;
-                    for (int per_sm = 1; per_sm <= 2; ++per_sm) {
-                        p->tune[{kind, R}] = ApplyChoice{rc, per_sm, 0};
+                    for (int per_sm = 1; per_sm <= 2; ++per_sm)
+                    for (int rpw = 4; rpw <= 8; rpw += 4) {
+                        // eight rows per warp: the FP32 and FP16 operators, four or more columns
+                        if (rpw == 8 && (kind == 2 || rc < 4)) continue;
+                        p->tune[{kind, R}] = ApplyChoice{rc, per_sm, 0, rpw};
                         auto launch = [&] {
                             if (kind == 0) run.symv<float>(p->op32, 1, ws.xU.as<float>(), ws.yU.as<double>());
                             else if (kind == 1) run.symv<float>(p->op32, 0, ws.xU.as<float>(), ws.yU.as<double>(), true);
@@ -2306,6 +2353,7 @@ void autotune_applies(nlfeti_problem *p, int R, const char *cache_path, std::vec
                             best = us;
                             te.rc = rc;
                             te.per_sm = per_sm;
+                            te.rpw = rpw;
                             te.us = us;
                         }
                     }
@@ -2327,6 +2375,7 @@ void autotune_applies(nlfeti_problem *p, int R, const char *cache_path, std::vec
                             best = us;
                             te.rc = -1;
                             te.per_sm = 1;
+                            te.rpw = 4;
                             te.us = us;
                         }
                     }
@@ -2338,6 +2387,7 @@ void autotune_applies(nlfeti_problem *p, int R, const char *cache_path, std::vec
                 c.R = R;
                 c.rc = te.rc;
                 c.per_sm = te.per_sm;
+                c.rpw = te.rpw;
                 c.us = te.us;
                 cache.push_back(c);
                 changed = true;
@@ -2346,7 +2396,7 @@ void autotune_applies(nlfeti_problem *p, int R, const char *cache_path, std::vec
                 build_tiled_half(p);
                 p->tune[{kind, R}] = ApplyChoice{apply_rc(R, 4), 2, 1};
             } else {
-                p->tune[{kind, R}] = ApplyChoice{te.rc, te.per_sm, 0};
+                p->tune[{kind, R}] = ApplyChoice{te.rc, te.per_sm, 0, te.rpw};
             }
             out.push_back(te);
         }
@@ -2519,7 +2569,42 @@ int apply_tma_ctas() {
         NLF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, APPLY_THREADS, smem));
         per_sm = std::min(per_sm, b);
     }
+    // eight rows per consumer warp (four consumer warps)
+    auto fit8 = [&](auto kern, int smem) {
+        NLF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int b = 0;
+        NLF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, apply_threads(8), smem));
+        per_sm = std::min(per_sm, b);
+    };
+    fit8(k_apply_tma<float, 4, APPLY_NS, APPLY_MINB, float, ROWS_APPLY, 8>, apply_smem_bytes(4, APPLY_NS));
+    fit8(k_apply_tma<float, 8, APPLY_NS, APPLY_MINB, float, ROWS_APPLY, 8>, apply_smem_bytes(8, APPLY_NS));
+    fit8(k_apply_tma<float, 16, APPLY_NS, APPLY_MINB, float, ROWS_APPLY, 8>, apply_smem_bytes(16, APPLY_NS));
+    fit8(k_apply_tma<float, 4, APPLY_NS_H, APPLY_MINB, __half, ROWS_APPLY, 8>,
+         apply_smem_bytes(4, APPLY_NS_H, APPLY_CB / 2));
+    fit8(k_apply_tma<float, 8, APPLY_NS_H, APPLY_MINB, __half, ROWS_APPLY, 8>,
+         apply_smem_bytes(8, APPLY_NS_H, APPLY_CB / 2));
+    fit8(k_apply_tma<float, 16, APPLY_NS_H16, APPLY_MINB, __half, ROWS_APPLY, 8>,
+         apply_smem_bytes(16, APPLY_NS_H16, APPLY_CB / 2));
     if (per_sm < 1) fail(NLFETI_E_CUDA, "the interface apply does not fit on an SM");
+    // the one-CTA-per-SM variants (schedules of one CTA per SM): their attributes only
+    int one = 1 << 20;
+    auto fit1 = [&](auto kern, int rpw, int smem) {
+        NLF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int b = 0;
+        NLF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, apply_threads(rpw), smem));
+        one = std::min(one, b);
+    };
+    constexpr int F8 = apply_ns_one(8, APPLY_CB), F16 = apply_ns_one(16, APPLY_CB);
+    constexpr int H8 = apply_ns_one(8, APPLY_CB / 2), H16 = apply_ns_one(16, APPLY_CB / 2);
+    fit1(k_apply_tma<float, 8, F8, 1, float, ROWS_APPLY, 4>, 4, apply_smem_bytes(8, F8));
+    fit1(k_apply_tma<float, 16, F16, 1, float, ROWS_APPLY, 4>, 4, apply_smem_bytes(16, F16));
+    fit1(k_apply_tma<float, 8, F8, 1, float, ROWS_APPLY, 8>, 8, apply_smem_bytes(8, F8));
+    fit1(k_apply_tma<float, 16, F16, 1, float, ROWS_APPLY, 8>, 8, apply_smem_bytes(16, F16));
+    fit1(k_apply_tma<float, 8, H8, 1, __half, ROWS_APPLY, 4>, 4, apply_smem_bytes(8, H8, APPLY_CB / 2));
+    fit1(k_apply_tma<float, 16, H16, 1, __half, ROWS_APPLY, 4>, 4, apply_smem_bytes(16, H16, APPLY_CB / 2));
+    fit1(k_apply_tma<float, 8, H8, 1, __half, ROWS_APPLY, 8>, 8, apply_smem_bytes(8, H8, APPLY_CB / 2));
+    fit1(k_apply_tma<float, 16, H16, 1, __half, ROWS_APPLY, 8>, 8, apply_smem_bytes(16, H16, APPLY_CB / 2));
+    if (one < 1) fail(NLFETI_E_CUDA, "the one-CTA-per-SM interface apply does not fit on an SM");
     return sms * per_sm;
 }
 

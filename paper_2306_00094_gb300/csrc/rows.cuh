@@ -70,11 +70,11 @@ __device__ __forceinline__ void apply_store(T *x, const SubdomainDesc *sd, const
         for (int q = nG; q < ldG; ++q) x[col + q] = T(0);
 }
 
-// 4-row x RC-column update from one step of the stream: acc[r][c] += M[r][l..l+W) . x[c][l..l+W)
+// NR-row x RC-column update from one step of the stream: acc[r][c] += M[r][l..l+W) . x[c][l..l+W)
 // (one FMA per product in the order w = 0 .. W-1; packed FP32-pair FMAs over two columns were
 // measured slower here: 128 vs 107 us per launch on the peridynamic workload)
-template <typename T, int RC, typename XF>
-__device__ __forceinline__ void rows_step(const typename Vec<T>::type (&mv)[4], XF &&xload, T (&acc)[4][RC]) {
+template <typename T, int RC, typename XF, int NR = 4>
+__device__ __forceinline__ void rows_step(const typename Vec<T>::type (&mv)[NR], XF &&xload, T (&acc)[NR][RC]) {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
 #pragma unroll
@@ -82,10 +82,44 @@ __device__ __forceinline__ void rows_step(const typename Vec<T>::type (&mv)[4], 
         V xv = xload(c);
         const T *xp = reinterpret_cast<const T *>(&xv);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < NR; ++r) {
             const T *mp = reinterpret_cast<const T *>(&mv[r]);
 #pragma unroll
             for (int w = 0; w < W; ++w) acc[r][c] += mp[w] * xp[w];
+        }
+    }
+}
+
+// The same update for NR rows with each lane's 4 FP32 columns taken as two halves of 2: first
+// columns l, l+1 of every row and right-hand side, then l+2, l+3.  Every acc[r][c] still receives
+// its four products in the order w = 0 .. 3, so the result is bitwise that of rows_step; the
+// operands live in half the registers (for NR = 8 rows of 16 accumulators each).  MT: stored
+// operator type (float, or an FP16 copy widened exactly).
+template <typename MT>
+__device__ __forceinline__ float2 load_pair_widen(const MT *p) {
+    if constexpr (std::is_same<MT, float>::value) {
+        return *reinterpret_cast<const float2 *>(p);
+    } else {
+        static_assert(std::is_same<MT, __half>::value, "FP32 or FP16 operators");
+        return __half22float2(*reinterpret_cast<const __half2 *>(p));
+    }
+}
+template <int RC, int NR, typename MT>
+__device__ __forceinline__ void rows_step_pairs(const MT *mrow0, int mstride, const float *x0, int xstride,
+                                                float (&acc)[NR][RC]) {
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+        float2 mv[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) mv[r] = load_pair_widen<MT>(mrow0 + r * mstride + 2 * hh);
+#pragma unroll
+        for (int c = 0; c < RC; ++c) {
+            const float2 xv = *reinterpret_cast<const float2 *>(x0 + c * xstride + 2 * hh);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                acc[r][c] += mv[r].x * xv.x;
+                acc[r][c] += mv[r].y * xv.y;
+            }
         }
     }
 }

@@ -82,7 +82,7 @@ void apply_operator(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int op, int
 // the problem.  With a cache path, choices found there (same device, subdomain shapes, kind and
 // R) are used without timing, and new ones are written back (JSON).
 struct TuneEntry {
-    int kind = 0, R = 0, rc = 0, per_sm = 0;
+    int kind = 0, R = 0, rc = 0, per_sm = 0, rpw = 4;
     double us = 0;
     bool from_cache = false;
 };

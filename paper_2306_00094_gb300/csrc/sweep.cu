@@ -634,6 +634,33 @@ __global__ void k_small_inverse(double *A, int n, int *flag) {
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] = -S[t];
 }
 
+// The same sweep for a coarse matrix too large for shared memory (n_co > 128: the peridynamic
+// kernel's three rigid modes on many floating subdomains), one pivot per launch: every entry
+// (i, l) of the n x n matrix in global memory takes pivot p from rowp_in (row p before this
+// pivot, = column p by symmetry) exactly as sweep_block_shared does, and the thread of row
+// p + 1 also writes that row's new values to rowp_out for the next launch.  Grid over n^2.
+__global__ void k_sweep_pivot_global(double *S, int n, int p, const double *rowp_in, double *rowp_out, int *flag) {
+    const double d = rowp_in[p];
+    const double inv = 1.0 / d;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / n), l = (int)(t % n);
+        double v;
+        if (i == p && l == p) v = -inv;
+        else if (i == p) v = rowp_in[l] * inv;
+        else if (l == p) v = rowp_in[i] * inv;
+        else v = S[t] - rowp_in[i] * rowp_in[l] * inv;
+        S[t] = v;
+        if (i == p + 1) rowp_out[l] = v;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !(d > 0.0)) atomicMax(flag, 1);
+}
+
+__global__ void k_negate(double *A, int64_t n) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        A[t] = -A[t];
+}
+
 // B_D = (B D^-1 B^T)^-1 B D^-1 per node block (chain rows, D = zeta on every copy):
 // B B^T = tridiag(-1, 2, -1) on the z-1 links of a node with z copies
 __global__ void k_bd_blocks(const int32_t *blk_ptr, int64_t nblk, const int32_t *blk_rows, const int64_t *bd_ptr,
@@ -744,15 +771,30 @@ void setup_coarse(nlfeti_problem *p) {
                                              p->gw, p->d_Gcol.as<int32_t>(), p->d_Gval.as<double>());
     p->d_GtGinv.alloc(c, sizeof(double) * std::max(1, nco * nco));
     if (nco > 0) {
-        if (nco > 128) fail(NLFETI_E_INVALID, "more than 128 coarse columns");
-        NLF_CUDA(cudaMemsetAsync(p->d_GtGinv.p, 0, sizeof(double) * nco * nco, c->stream));
+        if (nco > kMaxCoarse) fail(NLFETI_E_INVALID, "more than 12288 coarse columns");
+        NLF_CUDA(cudaMemsetAsync(p->d_GtGinv.p, 0, sizeof(double) * (size_t)nco * nco, c->stream));
         if (p->n_lambda > 0)
             k_gtg<<<256, 256, 0, c->stream>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), p->n_lambda,
                                               p->d_u2sub.as<int32_t>(), p->d_sd.as<SubdomainDesc>(),
                                               p->d_Z.as<double>(), nco, p->d_GtGinv.as<double>());
-        size_t sm = sizeof(double) * (nco * nco + nco);
-        NLF_CUDA(cudaFuncSetAttribute(k_small_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_small_inverse<<<1, 256, sm, c->stream>>>(p->d_GtGinv.as<double>(), nco, p->d_flag.as<int>());
+        if (nco <= 128) {
+            size_t sm = sizeof(double) * (nco * nco + nco);
+            NLF_CUDA(cudaFuncSetAttribute(k_small_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_small_inverse<<<1, 256, sm, c->stream>>>(p->d_GtGinv.as<double>(), nco, p->d_flag.as<int>());
+        } else {
+            DevMem rows;
+            rows.alloc(c, sizeof(double) * 2 * (size_t)nco);
+            double *r0 = rows.as<double>(), *r1 = r0 + nco;
+            double *G = p->d_GtGinv.as<double>();
+            NLF_CUDA(cudaMemcpyAsync(r0, G, sizeof(double) * nco, cudaMemcpyDeviceToDevice, c->stream));
+            const int blocks = (int)std::min<int64_t>(4096, ((int64_t)nco * nco + 255) / 256);
+            for (int q = 0; q < nco; ++q) {
+                k_sweep_pivot_global<<<blocks, 256, 0, c->stream>>>(G, nco, q, (q & 1) ? r1 : r0, (q & 1) ? r0 : r1,
+                                                                    p->d_flag.as<int>());
+            }
+            k_negate<<<blocks, 256, 0, c->stream>>>(G, (int64_t)nco * nco);
+            NLF_CUDA(cudaStreamSynchronize(c->stream));
+        }
         NLF_CUDA(cudaGetLastError());
     }
     NLF_CUDA(cudaStreamSynchronize(c->stream));

@@ -9,7 +9,8 @@ clean solve of the same problem that matches the oracle:
 * NLFETI_E_NOMEM: the allocator callback returns NULL for the solve's workspace;
 * NLFETI_E_TIMEOUT: the batched interface apply's producer withholds its copies and the
   consumers' stage waits are bounded to a few thousand polls, so the first wait runs out with
-  no copy in flight; the CTAs return and the error word reaches the host.
+  no copy in flight; the CTAs return and the error word reaches the host;
+* NLFETI_E_INVALID: malformed meshes, kernels and decompositions, refused on the host.
 """
 import numpy as np
 import pytest
@@ -134,6 +135,52 @@ def test_apply_wait_runs_out_then_solves(ref, precision):
     p.debug_apply_waits(wait_tries=4096, withhold_copies=0)
     p.solve(w.rhs, w.rhs_kind, raise_on_error=False)
     p.debug_apply_waits(0, 0)
+    u, _ = p.solve(w.rhs, w.rhs_kind)
+    _check(w, u, ref_u)
+    p.close()
+    ctx.close()
+
+
+def test_malformed_inputs_rejected(ref):
+    """A malformed mesh, kernel or decomposition is refused on the host with NLFETI_E_INVALID and
+    a message, before any device work; a valid problem on the same context then solves."""
+    from paper_2306_00094_gb300 import binding
+    w, ref_u = ref
+    m, k = w.mesh, w.kernel
+    ctx = binding.Context()
+
+    def make(**kw):
+        a = dict(dim=m.dim, xy=m.xy, elems=m.elems, node_is_dirichlet=m.node_is_dirichlet,
+                 elem_is_dirichlet=m.elem_is_dirichlet, kernel_type=k.type, delta=k.delta, s=k.s,
+                 scale=k.scale, labels=w.labels, K=w.K)
+        a.update(kw)
+        return binding.Problem(ctx, **a)
+
+    bad_el = m.elems.copy()
+    bad_el.flat[7] = m.xy.shape[0]                       # a node index past the last node
+    bad_xy = m.xy.copy()
+    bad_xy[3, 1] = np.inf
+    bad_lab = w.labels.copy()
+    bad_lab[np.flatnonzero(m.elem_is_dirichlet == 0)[0]] = w.K   # a label past the last subdomain
+    gap_lab = np.where(w.labels == 2, 1, w.labels)       # subdomain 2 left empty
+    cases = {"element node index out of range": dict(elems=bad_el),
+             "non-finite node coordinate": dict(xy=bad_xy),
+             "the Dirichlet volume constraint is empty": dict(
+                 node_is_dirichlet=np.zeros_like(m.node_is_dirichlet),
+                 elem_is_dirichlet=np.zeros_like(m.elem_is_dirichlet)),
+             "delta must be positive": dict(delta=-k.delta),
+             "unknown kernel type": dict(kernel_type=9),
+             "element label out of range": dict(labels=bad_lab),
+             "empty local subdomain": dict(labels=gap_lab),
+             "K must be in": dict(K=0)}
+    for msg, kw in cases.items():
+        with pytest.raises(binding.NlfetiError) as e:
+            make(**kw)
+        assert e.value.status == binding.E_INVALID, msg
+        assert msg in ctx.lib.nlfeti_last_error(ctx.h).decode(), msg
+    p = make()
+    p.factor(2)
+    p.set_options(binding.default_options(precision=1))
     u, _ = p.solve(w.rhs, w.rhs_kind)
     _check(w, u, ref_u)
     p.close()

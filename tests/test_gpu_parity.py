@@ -45,6 +45,7 @@ CASES = {
     "pd_neumann": lambda: W.neumann_pd(N=30, k=3, nrhs=2),
     "l2_rounded_collar": lambda: W.l2_collar_const(N=24, k=3, nrhs=2, delta=0.15),
     "l2_9x9": lambda: W.const_l2_2d(N=36, k=9, nrhs=2, delta=2.0 / 36),   # K = 81: more than 64 subdomains
+    "pd_9x9": lambda: W.peridynamic_2d(N=36, k=9, nrhs=2),   # 147 rigid modes: coarse matrix past 128
 }
 
 
