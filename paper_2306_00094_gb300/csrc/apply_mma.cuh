@@ -30,7 +30,8 @@
 //   warps 0..3  epilogue: wait tmem_full, read the MMA_ACC 128 x NP accumulators (warp w
 //               reads lanes 32w..32w+31, its row of the item) and add them in order, release
 //               them through tmem_empty, and store y[(offU + row) * R + c] for rows < n_gamma,
-//               columns < R.
+//               columns < R (times oscale / xscale[c], formed once per column: FP64 division is
+//               slow on this GPU, and one per entry kept the FP64 pipe a third busy).
 //
 // Every wait is bounded: a wait that runs out sets *err and the abort flag, the other roles
 // stop at their next wait, outstanding copies and MMAs are waited for (bounded), and the
@@ -161,8 +162,10 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
     __shared__ uint64_t full[MMA_NS], empty[MMA_NS], tmem_full, tmem_empty, drain;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
+    __shared__ double colfac[NP];       // oscale / xscale[c]: one FP64 division per column, not per entry
     if (gate && *gate == 0) return;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x < NP) colfac[threadIdx.x] = threadIdx.x < R ? oscale / xscale[threadIdx.x] : 0.0;
     if (threadIdx.x == 0) {
         for (int s = 0; s < MMA_NS; ++s) {
             mbar_init(&full[s], 1);
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
                 if (row < n)
 #pragma unroll
                     for (int c = 0; c < 16; ++c)
-                        if (c0 + c < R) y[(yoff + row) * R + c0 + c] = (double)v[c] * (oscale / xscale[c0 + c]);
+                        if (c0 + c < R) y[(yoff + row) * R + c0 + c] = (double)v[c] * colfac[c0 + c];
             }
             tc_fence_before();
             mbar_arrive(&tmem_empty);

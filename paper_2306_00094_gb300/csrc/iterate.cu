@@ -308,7 +308,9 @@ __device__ __forceinline__ bool arrive_last(unsigned *counter) {
 // order of the additions, so every column is summed in the same order whatever the batch it
 // is part of; the lanes of a unit read 4 rows x cw consecutive columns per step, and each lane
 // has two rows in flight.  f(i, c) is called once per entry (i < n, c < R) and returns its
-// addend.
+// addend.  The block partials are stored column by column (partial[c * blocks + b]), so that the
+// last block reads each column's partials as whole lines (measured: the finish of 608 blocks x 16
+// columns took 10 us with the partials row by row, 6 us column by column).
 constexpr int RT = 8;
 constexpr int RSMEM = 2048;             // doubles of tile sums per round (16 KB)
 constexpr int RCOLS = RED_THREADS;      // columns per pass (one accumulating thread each)
@@ -356,7 +358,7 @@ __device__ __forceinline__ void tile_reduce(int64_t n, int R, double *partial, F
                 for (int tl = 0; tl < ntl; ++tl) acc += ts[tl * ncol + threadIdx.x];
             __syncthreads();
         }
-        if (threadIdx.x < ncol) partial[(int64_t)blockIdx.x * R + cc0 + threadIdx.x] = acc;
+        if (threadIdx.x < ncol) partial[(int64_t)(cc0 + threadIdx.x) * gridDim.x + blockIdx.x] = acc;
     }
 }
 
@@ -364,6 +366,7 @@ __device__ __forceinline__ void tile_reduce(int64_t n, int R, double *partial, F
 // and the PCG scalar update:
 //   NPD:   ||P d|| and the initial state;      CHECK: ||w|| and the active mask;
 //   BETA:  (y,w) and beta = (y,w)/(y,w)_old;    ETA:   (p,q) and eta = (y,w)/(p,q).
+constexpr int FIN_GROUP = 8;            // partials per lane loaded together by the last block
 template <int MODE>
 __device__ void finish_scalars(const double *partial, int nb, int R, PcgScalars s, double tol, int max_it) {
     __shared__ int n_act;
@@ -371,8 +374,18 @@ __device__ void finish_scalars(const double *partial, int nb, int R, PcgScalars 
     if (threadIdx.x == 0) n_act = 0;
     __syncthreads();
     for (int c = warp; c < R; c += RED_THREADS / 32) {
+        // the column's nb partials are contiguous: each group of loads reads whole lines, with
+        // FIN_GROUP loads of a lane in flight together, added in block order
+        const double *pc = partial + (int64_t)c * nb;
         double v = 0;
-        for (int bl = lane; bl < nb; bl += 32) v += __ldcg(partial + (int64_t)bl * R + c);
+        for (int b0 = lane; b0 < nb; b0 += 32 * FIN_GROUP) {
+            double pv[FIN_GROUP];
+#pragma unroll
+            for (int m = 0; m < FIN_GROUP; ++m) pv[m] = b0 + 32 * m < nb ? __ldcg(pc + b0 + 32 * m) : 0.0;
+#pragma unroll
+            for (int m = 0; m < FIN_GROUP; ++m)
+                if (b0 + 32 * m < nb) v += pv[m];
+        }
         v = warp_sum(v);
         if (lane == 0) {
             if (MODE == FIN_NPD) {
