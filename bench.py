@@ -376,14 +376,23 @@ def run_ours(args):
     cg_prep_s = time.perf_counter() - t0
     d_cg = torch.empty_like(d_rhs)
     prob.set_options(binding.default_options(tol=1e-10, max_it=20000))
-    prob.solve_cg_device(d_rhs, w.rhs_kind, d_cg, nrhs=R)
+
+    def cg_all():
+        # the CG entry point takes at most 32 right-hand sides per call
+        st = None
+        for c0 in range(0, R, 32):
+            c1 = min(R, c0 + 32)
+            st = prob.solve_cg_device(d_rhs[c0:c1], w.rhs_kind, d_cg[c0:c1], nrhs=c1 - c0)
+        return st
+
+    cg_all()
     torch.cuda.synchronize()
     ts = []
     for _ in range(2):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record()
-        s_cg = prob.solve_cg_device(d_rhs, w.rhs_kind, d_cg, nrhs=R)
+        s_cg = cg_all()
         b.record()
         torch.cuda.synchronize()
         ts.append(a.elapsed_time(b))

@@ -179,7 +179,7 @@ void build_maps(nlfeti_problem *p) {
     p->n_u = d.u_off[K];
     p->n_co = d.co_off[K];
     p->sd.assign(K, SubdomainDesc{});
-    int64_t offA = 0, offAD = 0, offM = 0, offG = 0, offV = 0, offUp = 0, offVp = 0, offT = 0;
+    int64_t offA = 0, offAD = 0, offM = 0, offG = 0, offV = 0, offUp = 0, offVp = 0, offT = 0, offXp = 0;
     p->n_floating = 0;
     p->max_ldG = 8;
     for (int k = 0; k < K; ++k) {
@@ -198,6 +198,7 @@ void build_maps(nlfeti_problem *p) {
         s.offT = offT; offT += s.nG > 0 ? (int64_t)((s.nG + 127) / 128) * mma_ktiles(s.nG, s.ldG) : 0;
         s.offU = d.u_off[k];
         s.offUp = offUp; offUp += s.ldG;
+        s.offXp = offXp; offXp += ldgx(s.ldG);
         s.offVp = offVp; offVp += s.ldM;
         s.offV = offV; offV += s.nk;
         s.co_off = d.co_off[k];
@@ -211,6 +212,7 @@ void build_maps(nlfeti_problem *p) {
     p->poolA = offA; p->poolAD = offAD; p->poolM = offM; p->poolG = offG; p->poolT = offT;
     p->sum_nk = offV;
     p->n_up = offUp;
+    p->n_xp = offXp;
     p->n_vp = offVp;
     // node maps
     std::vector<int32_t> nodemap((size_t)K * m.n_nodes, -1);

@@ -30,8 +30,10 @@
 //   warps 0..3  epilogue: wait tmem_full, read the MMA_ACC 128 x NP accumulators (warp w
 //               reads lanes 32w..32w+31, its row of the item) and add them in order, release
 //               them through tmem_empty, and store y[(offU + row) * R + c] for rows < n_gamma,
-//               columns < R (times oscale / xscale[c], formed once per column: FP64 division is
-//               slow on this GPU, and one per entry kept the FP64 pipe a third busy).
+//               columns < R, times oscale / xscale[c] (a power of two formed once per column;
+//               the FP64 pipe of this GPU runs at a small fraction of the FP32 rate, and a division
+//               per entry kept it a third busy: 63.6 -> 37.8 us per apply on the peridynamic
+//               workload once hoisted), applied to the exponent with integer operations.
 //
 // Every wait is bounded: a wait that runs out sets *err and the abort flag, the other roles
 // stop at their next wait, outstanding copies and MMAs are waited for (bounded), and the
@@ -147,6 +149,18 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                  : "memory");
 }
 
+// v * 2^e as a double (fac = 2^e), exactly: the double's bits composed with integer
+// operations for a normal v whose scaled exponent stays in range; otherwise (zero, subnormal,
+// inf, nan, out of range) by the FP64 product.  The same bits as (double)v * fac either way.
+__device__ __forceinline__ double f2d_pow2(float v, int e, double fac) {
+    const uint32_t b = __float_as_uint(v);
+    const int ex = (int)((b >> 23) & 0xffu);
+    const int de = ex - 127 + 1023 + e;
+    if (ex == 0 || ex == 0xff || de <= 0 || de >= 2047) return (double)v * fac;
+    const uint64_t d = ((uint64_t)(b >> 31) << 63) | ((uint64_t)de << 52) | ((uint64_t)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
 template <int NP>
 __global__ void __launch_bounds__(MMA_THREADS, 1)
     k_apply_mma(const __half *St, const CUtensorMap *xmaps, const SubdomainDesc *sd, const int32_t *sched_ptr,
@@ -162,10 +176,15 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
     __shared__ uint64_t full[MMA_NS], empty[MMA_NS], tmem_full, tmem_empty, drain;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
-    __shared__ double colfac[NP];       // oscale / xscale[c]: one FP64 division per column, not per entry
+    __shared__ double colfac[NP];       // oscale / xscale[c] (a power of two): formed once per column
+    __shared__ int colexp[NP];          // its exponent
     if (gate && *gate == 0) return;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (threadIdx.x < NP) colfac[threadIdx.x] = threadIdx.x < R ? oscale / xscale[threadIdx.x] : 0.0;
+    if (threadIdx.x < NP) {
+        const double f = threadIdx.x < R ? oscale / xscale[threadIdx.x] : 0.0;
+        colfac[threadIdx.x] = f;
+        colexp[threadIdx.x] = f != 0.0 ? ilogb(f) : 0;
+    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < MMA_NS; ++s) {
             mbar_init(&full[s], 1);
@@ -285,7 +304,7 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
                 if (row < n)
 #pragma unroll
                     for (int c = 0; c < 16; ++c)
-                        if (c0 + c < R) y[(yoff + row) * R + c0 + c] = (double)v[c] * colfac[c0 + c];
+                        if (c0 + c < R) y[(yoff + row) * R + c0 + c] = f2d_pow2(v[c], colexp[c0 + c], colfac[c0 + c]);
             }
             tc_fence_before();
             mbar_arrive(&tmem_empty);

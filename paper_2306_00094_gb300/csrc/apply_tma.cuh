@@ -15,6 +15,13 @@
 // is released to the producer through a second mbarrier.  The producer runs ahead across item
 // boundaries, so the copy engine keeps up to NS stages per CTA in flight while the consumers
 // compute.
+// The FP32 interface apply reads x in the paired layout (apply_paired_index: two right-hand
+// sides interleaved, and each 128-column group in the order the lanes read it), one pair row
+// per two right-hand sides of the stage, so that a lane's columns of two right-hand sides are
+// two conflict-free 16-byte shared loads and their products are packed FMAs (fma.rn.f32x2), each
+// element rounded as the scalar FMA: bitwise the sums of the scalar step, with half the FMA
+// instructions (the consumers were issue-bound: the producer waited on free stages, the
+// consumers about a tenth of their time on data).
 // With more than RC right-hand sides the rows of an item are streamed once per block of RC.
 // The operator may be stored in a narrower type MT than the arithmetic type T (FP16 copy of
 // S_k for the preconditioner of the mixed path): a stage then holds the same columns with
@@ -42,11 +49,14 @@ constexpr int APPLY_NS_H16 = 3;                     // ... at RC = 16 (32 KB eac
 __host__ __device__ constexpr int apply_rc(int R, int elem_size) {
     return (R >= 16 && elem_size == 4) ? 16 : (R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1)));
 }
-// a stage: 32 operator rows of mrow bytes, then RC columns of x (APPLY_CB bytes each)
-__host__ __device__ constexpr int apply_stage_bytes(int rc, int mrow = APPLY_CB) { return 32 * mrow + rc * APPLY_CB; }
+// a stage: 32 operator rows of mrow bytes, then the RC columns of x: RC rows of APPLY_CB bytes,
+// or (paired: the FP32 interface apply) (RC + 1) / 2 pair rows of 2 APPLY_CB bytes
+__host__ __device__ constexpr int apply_stage_bytes(int rc, int mrow = APPLY_CB, bool paired = false) {
+    return 32 * mrow + (paired ? (rc + 1) / 2 * 2 : rc) * APPLY_CB;
+}
 // the ring is aligned to 1 KB inside the dynamic shared memory (tensor copies want 128 B)
-__host__ __device__ constexpr int apply_smem_bytes(int rc, int ns, int mrow = APPLY_CB) {
-    return ns * apply_stage_bytes(rc, mrow) + 1024;
+__host__ __device__ constexpr int apply_smem_bytes(int rc, int ns, int mrow = APPLY_CB, bool paired = false) {
+    return ns * apply_stage_bytes(rc, mrow, paired) + 1024;
 }
 // rows of an item per consumer warp: 4 (eight consumer warps) or 8 (four consumer warps, twice
 // the accumulators per lane; each x vector loaded from shared memory serves 8 rows instead of 4)
@@ -185,7 +195,11 @@ __global__ void __launch_bounds__(apply_threads(RPW), MINB)
     static_assert(RPW == 4 || RPW == 8, "4 or 8 rows per consumer warp");
     constexpr int CW = APPLY_CB / (int)sizeof(T);   // columns per stage row
     constexpr int MROW = CW * (int)sizeof(MT);      // operator bytes per stage row
-    constexpr int STAGE = apply_stage_bytes(RC, MROW);
+    // FP32 interface apply: x in the paired layout (apply_paired_index), two right-hand sides per
+    // pair row, so that the products of two right-hand sides are one packed FMA
+    constexpr bool PAIRED = std::is_same<T, float>::value && MODE == ROWS_APPLY;
+    constexpr bool PAIRS = PAIRED && RC >= 2;
+    constexpr int STAGE = apply_stage_bytes(RC, MROW, PAIRED);
     extern __shared__ __align__(128) unsigned char ring_raw[];
     unsigned char *ring = ring_raw + ((1024u - (smem_u32(ring_raw) & 1023u)) & 1023u);
     __shared__ uint64_t full[NS], empty[NS];
@@ -231,7 +245,7 @@ __global__ void __launch_bounds__(apply_threads(RPW), MINB)
                     unsigned char *stg = ring + s * STAGE;
                     mbar_arrive_expect_tx(&full[s], STAGE);
                     tile_g2s_hint(stg, map, l0, i0, &full[s], stream_policy);
-                    tile_g2s(stg + 32 * MROW, xmap, l0, c0, &full[s]);
+                    tile_g2s(stg + 32 * MROW, xmap, l0, PAIRED ? c0 / 2 : c0, &full[s]);
                 }
                 __syncwarp();
             }
@@ -253,11 +267,15 @@ __global__ void __launch_bounds__(apply_threads(RPW), MINB)
         const int ib = i0 + warp * RPW;
         for (int c0 = 0; c0 < R; c0 += RC) {
             const int rc = min(RC, R - c0);
-            T acc[RPW][RC];
+            T acc[RPW][PAIRS ? 1 : RC];
+            float2 acc2[RPW][PAIRS ? RC / 2 : 1];
 #pragma unroll
-            for (int r = 0; r < RPW; ++r)
+            for (int r = 0; r < RPW; ++r) {
 #pragma unroll
-                for (int c = 0; c < RC; ++c) acc[r][c] = T(0);
+                for (int c = 0; c < (PAIRS ? 1 : RC); ++c) acc[r][c] = T(0);
+#pragma unroll
+                for (int c = 0; c < (PAIRS ? RC / 2 : 1); ++c) acc2[r][c] = make_float2(0.f, 0.f);
+            }
             for (int l0 = 0; l0 < ncp; l0 += CW, ++q) {
                 const int s = q % NS;
                 if (__any_sync(0xffffffffu, !mbar_wait(&full[s], (q / NS) & 1, wait_tries, &abort_flag) || abort_flag)) {
@@ -271,19 +289,27 @@ __global__ void __launch_bounds__(apply_threads(RPW), MINB)
                 // without bounds tests: the extra products are exact zeros and the rows and
                 // columns past the operator are never stored
                 if (ib < n) {
-#pragma unroll(RPW == 8 ? 1 : 8)
+#pragma unroll
                     for (int j = 0; j < CW / (32 * W); ++j) {
                         const int l = lane * W + j * 32 * W;
-                        if constexpr (RPW == 8) {
-                            // eight rows: the lane's 4 columns in two halves (bitwise the same sums)
-                            static_assert(std::is_same<T, float>::value, "eight rows per warp: FP32 arithmetic");
-                            rows_step_pairs<RC, RPW, MT>(st + (warp * RPW) * CW + l, CW, xs + l, CW, acc);
+                        if constexpr (PAIRS) {
+                            // the lane's float4s of each pair row: j * 256 + 4 lane and 128 further
+                            rows_step_paired<RC, RPW, MT>(st + (warp * RPW) * CW + l, CW,
+                                                          reinterpret_cast<const float *>(xs) + j * 256 + lane * 4,
+                                                          acc2);
                         } else {
                             V mv[RPW];
 #pragma unroll
                             for (int r = 0; r < RPW; ++r) mv[r] = load_widen<T, MT>(st + (warp * RPW + r) * CW + l);
-                            rows_step<T, RC>(mv, [&](int c) { return *reinterpret_cast<const V *>(xs + c * CW + l); },
-                                             acc);
+                            if constexpr (PAIRED) {
+                                // one right-hand side: its slot of the pair row
+                                const float *q = reinterpret_cast<const float *>(xs) + j * 256 + lane * 4 + (c0 & 1);
+                                const V xv = make_float4(q[0], q[2], q[128], q[130]);
+                                rows_step<T, RC>(mv, [&](int) { return xv; }, acc);
+                            } else {
+                                rows_step<T, RC>(mv, [&](int c) { return *reinterpret_cast<const V *>(xs + c * CW + l); },
+                                                 acc);
+                            }
                         }
                     }
                 }
@@ -302,7 +328,14 @@ __global__ void __launch_bounds__(apply_threads(RPW), MINB)
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int c = 0; c < CG; ++c) v[r * CG + c] = acc[rh + r][g0 + c];
+                    for (int c = 0; c < CG; ++c) {
+                        if constexpr (PAIRS) {
+                            const float2 a2 = acc2[rh + r][(g0 + c) / 2];
+                            v[r * CG + c] = ((g0 + c) & 1) ? a2.y : a2.x;
+                        } else {
+                            v[r * CG + c] = acc[rh + r][g0 + c];
+                        }
+                    }
                 const T tot = warp_reduce_scatter<T, NV>(v, lane);
                 constexpr int G = 32 / NV;
                 const int idx = lane / G, r = idx / CG, c = g0 + idx % CG, i = ib + rh + r;

@@ -140,7 +140,24 @@ struct SubdomainDesc {      // per subdomain, device resident (POD)
                             // ldM): R columns of ldM entries at offVp*R (refinement residual input)
     int64_t offT;           // first tile of S_k in the tiled FP16 copy (tensor-core apply): tiles of
                             // 128 rows x 64 columns, ceil(nG/128) row tiles x mma_ktiles(nG, ldG)
+    int64_t offXp;          // start of Gamma_k in the paired FP32 apply input (sum of ldG rounded up
+                            // to 128): for R right-hand sides at offXp * R2 (R2 = R rounded up to
+                            // even), see apply_paired_index
 };
+
+// the paired FP32 apply input: the right-hand sides of a subdomain taken two at a time (pair
+// row cp = columns 2 cp, 2 cp + 1; R2 / 2 pair rows of 2 ldgx(ldG) floats), and within a pair row
+// the 128-column group g of operator columns in the order a lane of the apply reads them: lane k
+// (columns 4k .. 4k+3 of the group) finds columns 4k, 4k+1 of both right-hand sides as one float4
+// at 256 g + 4 k and columns 4k+2, 4k+3 as one float4 128 floats further
+__host__ __device__ inline int64_t ldgx(int ldG) { return (int64_t)(ldG + 127) / 128 * 128; }
+__host__ __device__ inline int64_t paired_col(int j) {
+    return 256 * (int64_t)(j >> 7) + 128 * ((j >> 1) & 1) + 4 * ((j & 127) >> 2) + 2 * (j & 1);
+}
+__host__ __device__ inline int64_t apply_paired_index(int64_t offXp, int ldG, int j, int c, int R) {
+    const int R2 = (R + 1) / 2 * 2;
+    return offXp * R2 + (int64_t)(c >> 1) * 2 * ldgx(ldG) + paired_col(j) + (c & 1);
+}
 
 // column tiles of 64 of an operator in the tiled FP16 copy: the streamed columns, min(ldG,
 // nG rounded up to 8), in 64-column tiles
@@ -191,7 +208,7 @@ struct nlfeti_problem {
     nlfeti_kernel kern;
     nlf::Decomp dec;
     int K = 0, nc = 1;
-    int64_t n_lambda = 0, n_u = 0, sum_nk = 0, n_dofs_total = 0, n_up = 0, n_vp = 0;
+    int64_t n_lambda = 0, n_u = 0, sum_nk = 0, n_dofs_total = 0, n_up = 0, n_vp = 0, n_xp = 0;
     int n_co = 0, n_floating = 0, max_ldG = 0;
     std::vector<SubdomainDesc> sd;      // host copy
     nlf::DevMem d_sd;

@@ -1109,6 +1109,13 @@ void residual_ds(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, const d
     else go(std::integral_constant<int, 1>{});
 }
 
+// the interface apply's input buffer of an arithmetic type: FP32 in the paired layout (xP),
+// FP64 in the column layout (xU)
+template <typename T> T *apply_input(SolveWS &ws) {
+    if constexpr (std::is_same<T, float>::value) return ws.xP.as<float>();
+    else return ws.xU.as<T>();
+}
+
 struct Runner {
     nlfeti_problem *p;
     SolveWS &ws;
@@ -1379,7 +1386,7 @@ struct Runner {
             const CUtensorMap *maps = std::is_same<MT, T>::value ? pool.maps.template as<CUtensorMap>()
                                                                  : pool.hmaps.template as<CUtensorMap>();
             k_apply_tma<T, RCT, NS, MINB, MT, ROWS_APPLY, RPW>
-                <<<ctas, apply_threads(RPW), apply_smem_bytes(RCT, NS, MROW), st>>>(
+                <<<ctas, apply_threads(RPW), apply_smem_bytes(RCT, NS, MROW, std::is_same<T, float>::value), st>>>(
                     maps, xm, std::is_same<MT, T>::value ? use_sp : 0, sd, sptr, sitems, y, R, gate, S.err,
                     std::is_same<MT, T>::value ? 1.0 : 1.0 / pool.hscale, nullptr, wait_tries(), p->dbg_withhold);
         };
@@ -1416,9 +1423,9 @@ struct Runner {
                 if constexpr (RCT >= 4)
                     if (ch.rpw == 8) return launch(NSF{}, I2{}, I8{}, rc_tag, TypeTag<float>{});
             }
-            k_apply_tma<T, RCT><<<ctas, APPLY_THREADS, apply_smem_bytes(RCT, APPLY_NS), st>>>(
-                pool.maps.template as<CUtensorMap>(), xm, use_sp, sd, sptr, sitems, y, R, gate, S.err, 1.0, nullptr,
-                wait_tries(), p->dbg_withhold);
+            k_apply_tma<T, RCT><<<ctas, APPLY_THREADS, apply_smem_bytes(RCT, APPLY_NS, APPLY_CB, std::is_same<T, float>::value),
+                                  st>>>(pool.maps.template as<CUtensorMap>(), xm, use_sp, sd, sptr, sitems, y, R, gate,
+                                        S.err, 1.0, nullptr, wait_tries(), p->dbg_withhold);
         };
         switch (rc) {
             case 16:
@@ -1542,7 +1549,7 @@ struct Runner {
 
     template <typename T> void applyF(const OpPool<T> &pool, const double *v, double *out, const double *cvec = nullptr) {
         const int64_t nl = p->n_lambda, nu = p->n_u;
-        T *x = ws.xU.as<T>();
+        T *x = apply_input<T>(ws);
         if (nu > 0) gather_x<T>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), nullptr, v, x);
         symv<T>(pool, 1, x, ws.yU.as<double>());
         k_gather_b<<<grid_for(nl * R), 256, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), ws.yU.as<double>(),
@@ -1560,7 +1567,7 @@ struct Runner {
 
     template <typename T> void applyMinv(const OpPool<T> &pool, const double *v, double *out, bool precond = false) {
         const int64_t nl = p->n_lambda, nu = p->n_u;
-        T *x = ws.xU.as<T>();
+        T *x = apply_input<T>(ws);
         if (use_mma(pool, precond)) {
             if (nu > 0) {
                 k_gather_apply_f16<<<grid_for(nu * R), 256, 0, st>>>(
@@ -1585,7 +1592,7 @@ struct Runner {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         double *r = ws.r.as<double>(), *w = ws.w.as<double>(), *z = ws.z.as<double>(), *y = ws.y.as<double>(),
                *pv = ws.pv.as<double>(), *q = ws.q.as<double>(), *lam = ws.dlam.as<double>(), *yU = ws.yU.as<double>();
-        T *x = ws.xU.as<T>();
+        T *x = apply_input<T>(ws);
         const double *alpha = p->n_co > 0 ? ws.alpha.as<double>() : nullptr;
         // p, lambda, r updated; w = P r, ||w||, stop test
         if (p->n_co > 0) coarse_alpha(r, PG_LAM_R, q);
@@ -1793,7 +1800,7 @@ struct Runner {
                                        p->item_off);
         }
         double *lam = ws.dlam.as<double>();
-        T *x = ws.xU.as<T>();
+        T *x = apply_input<T>(ws);
         if (nl > 0) {
             k_to_apply<T><<<grid_for(nu * R), 256, 0, st>>>(ws.fU.as<double>(), x, sd, p->d_u2sub.as<int32_t>(), nu, R);
             note_launch();
@@ -1982,6 +1989,8 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     A(lam, nl); A(r, nl); A(w, nl); A(z, nl); A(y, nl); A(pv, nl); A(q, nl); A(d, nl); A(cvec, nl); A(dlam, nl);
     A(fU, nu); A(yU, nu); A(uU, nu);
     A(xU, std::max<int64_t>(1, p->n_up));   // apply layout (padding zeroed by the gathers)
+    const int R2x = (R + 1) / 2 * 2;
+    alloc(xP, sizeof(float) * std::max<int64_t>(1, p->n_xp) * R2x);   // paired FP32 layout, zeroed below
     alloc(uhl, sizeof(float) * 2 * std::max<int64_t>(1, p->n_vp) * ((R + 1) / 2 * 2));
     alloc(xscale, sizeof(double) * R);
     if (alloc_stream) NLF_CUDA(cudaStreamSynchronize(alloc_stream));
@@ -1992,6 +2001,9 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
         NLF_CUDA(cudaStreamSynchronize(async_stream ? async_stream : c->stream));
     }
     NLF_CUDA(cudaMemsetAsync(xU.p, 0, xU.bytes, async_stream ? async_stream : c->stream));
+    // the paired FP32 input: its padding (columns past n_gamma of each 128-column group, the
+    // partner of an odd last right-hand side) is never written again and stays zero
+    NLF_CUDA(cudaMemsetAsync(xP.p, 0, xP.bytes, async_stream ? async_stream : c->stream));
     // tensor maps of xU per subdomain (R rows of ld_gamma entries at offUp * R), read as FP32
     // and as FP64, tiles of rc rows as the apply kernel of this R uses
     {
@@ -2008,9 +2020,18 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
                 for (int k = 0; k < p->K; ++k) {
                     const SubdomainDesc &d = p->sd[k];
                     if (d.nG == 0) continue;
-                    const unsigned char *b = xU.as<unsigned char>() + d.offUp * R * es;
-                    if (encode_apply_map(encode_tiled(), &maps[k], b, d.ldG, R, es, rce) != CUDA_SUCCESS)
-                        fail(NLFETI_E_CUDA, "cuTensorMapEncodeTiled failed for the apply input");
+                    CUresult er;
+                    if (e == 0) {
+                        // FP32: the paired layout, R2 / 2 pair rows of ldgx(ld_gamma) 8-byte pairs,
+                        // tiles of 256 pairs (one stage of columns) x max(1, rce / 2) pair rows
+                        const float *b = xP.as<float>() + d.offXp * R2x;
+                        er = encode_apply_map(encode_tiled(), &maps[k], b, (int)ldgx(d.ldG), R2x / 2, 8,
+                                              std::max(1, rce / 2), 2 * APPLY_CB);
+                    } else {
+                        const unsigned char *b = xU.as<unsigned char>() + d.offUp * R * es;
+                        er = encode_apply_map(encode_tiled(), &maps[k], b, d.ldG, R, es, rce);
+                    }
+                    if (er != CUDA_SUCCESS) fail(NLFETI_E_CUDA, "cuTensorMapEncodeTiled failed for the apply input");
                 }
                 alloc(xmaps_rc[e][ri], sizeof(CUtensorMap) * maps.size());
                 NLF_CUDA(cudaMemcpyAsync(xmaps_rc[e][ri].p, maps.data(), sizeof(CUtensorMap) * maps.size(),
@@ -2313,6 +2334,7 @@ void autotune_applies(nlfeti_problem *p, int R, const char *cache_path, std::vec
     cudaStream_t st = p->ctx->stream;
     ws.ensure(p, R);
     NLF_CUDA(cudaMemsetAsync(ws.xU.p, 0, ws.xU.bytes, st));
+    NLF_CUDA(cudaMemsetAsync(ws.xP.p, 0, ws.xP.bytes, st));
     std::vector<CacheLine> cache = read_tune_cache(cache_path);
     const int saved_batched = p->opt.batched, saved_fp16 = p->opt.precond_fp16;
     p->opt.batched = 1;
@@ -2350,8 +2372,8 @@ void autotune_applies(nlfeti_problem *p, int R, const char *cache_path, std::vec
                         if (rpw == 8 && (kind == 2 || rc < 4)) continue;
                         p->tune[{kind, R}] = ApplyChoice{rc, per_sm, 0, rpw};
                         auto launch = [&] {
-                            if (kind == 0) run.symv<float>(p->op32, 1, ws.xU.as<float>(), ws.yU.as<double>());
-                            else if (kind == 1) run.symv<float>(p->op32, 0, ws.xU.as<float>(), ws.yU.as<double>(), true);
+                            if (kind == 0) run.symv<float>(p->op32, 1, ws.xP.as<float>(), ws.yU.as<double>());
+                            else if (kind == 1) run.symv<float>(p->op32, 0, ws.xP.as<float>(), ws.yU.as<double>(), true);
                             else run.symv<double>(p->op64, 1, ws.xU.as<double>(), ws.yU.as<double>());
                         };
                         launch();
@@ -2443,7 +2465,7 @@ void apply_operator(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int op, int
             case 2: run.project(in, out); break;
             case 3:
             case 4: {
-                T *x = ws.xU.as<T>();
+                T *x = apply_input<T>(ws);
                 k_to_apply<T><<<grid_for(nu * R), 256, 0, st>>>(in, x, run.sd, p->d_u2sub.as<int32_t>(), nu, R);
                 run.symv<T>(pool, op == 3 ? 1 : 0, x, out);
                 break;
@@ -2456,7 +2478,7 @@ void apply_operator(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int op, int
                                                                      run.sd, p->d_u2sub.as<int32_t>(), nu, R);
                     run.symv_mma(pool, out);
                 } else {
-                    T *x = ws.xU.as<T>();
+                    T *x = apply_input<T>(ws);
                     k_to_apply<T><<<grid_for(nu * R), 256, 0, st>>>(in, x, run.sd, p->d_u2sub.as<int32_t>(), nu, R);
                     run.symv<T>(pool, 0, x, out, true);
                 }
@@ -2535,15 +2557,15 @@ int apply_tma_ctas() {
     NLF_CUDA(cudaGetDevice(&dev));
     NLF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int per_sm = 1 << 20;
-    auto fit = [&](auto kern, int rc) {
-        const int smem = apply_smem_bytes(rc, APPLY_NS);
+    auto fit = [&](auto kern, int rc, bool paired = false) {
+        const int smem = apply_smem_bytes(rc, APPLY_NS, APPLY_CB, paired);
         NLF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         int b = 0;
         NLF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, APPLY_THREADS, smem));
         per_sm = std::min(per_sm, b);
     };
-    fit(k_apply_tma<float, 1>, 1); fit(k_apply_tma<float, 2>, 2); fit(k_apply_tma<float, 4>, 4);
-    fit(k_apply_tma<float, 8>, 8); fit(k_apply_tma<float, 16>, 16);
+    fit(k_apply_tma<float, 1>, 1, true); fit(k_apply_tma<float, 2>, 2, true); fit(k_apply_tma<float, 4>, 4, true);
+    fit(k_apply_tma<float, 8>, 8, true); fit(k_apply_tma<float, 16>, 16, true);
     fit(k_apply_tma<double, 1>, 1); fit(k_apply_tma<double, 2>, 2);
     fit(k_apply_tma<double, 4>, 4); fit(k_apply_tma<double, 8>, 8);
     // the forcing and back-substitution modes (same pipeline and shared memory)
@@ -2566,7 +2588,7 @@ int apply_tma_ctas() {
     fit(k_apply_tma<double, 4, APPLY_NS, APPLY_MINB, double, ROWS_BACKSUB>, 4);
     fit(k_apply_tma<double, 8, APPLY_NS, APPLY_MINB, double, ROWS_BACKSUB>, 8);
     auto fit_h = [&](auto kern, int rc) {
-        const int smem = apply_smem_bytes(rc, APPLY_NS_H, APPLY_CB / 2);
+        const int smem = apply_smem_bytes(rc, APPLY_NS_H, APPLY_CB / 2, true);
         NLF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         int b = 0;
         NLF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, APPLY_THREADS, smem));

@@ -77,7 +77,12 @@ __global__ void k_stage_colmajor(const double *in, T *x, const SubdomainDesc *sd
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(t / nu);
         const int64_t u = t % nu;
-        apply_store<T>(x, sd, u2sub, u, c, R, (T)in[t]);
+        const SubdomainDesc &d = sd[u2sub[u]];
+        const int64_t col = d.offUp * R + (int64_t)c * d.ldG;
+        const int j = (int)(u - d.offU);
+        x[col + j] = (T)in[t];
+        if (j == d.nG - 1)
+            for (int q = d.nG; q < d.ldG; ++q) x[col + q] = T(0);
     }
 }
 

@@ -8,8 +8,9 @@
 //
 // Modes (same streaming structure, different rows / columns / vectors):
 //   ROWS_APPLY:   y_U = M x_U with M = S_k^+ or S_k (rows and columns Gamma_k).  x is read
-//                 directly (L1-cached) from the apply layout: for subdomain k, R columns of
-//                 ldG entries starting at offUp*R (zero padded), written by the gathers.
+//                 directly (L1-cached) from the apply input written by the gathers: FP64, for
+//                 subdomain k R columns of ldG entries at offUp*R (zero padded); FP32, the paired
+//                 layout (apply_paired_index).
 //   ROWS_FORCING: f_U = f_G - (A_GO A_OO^-1) f_O, rows Gamma / columns Omega of the swept
 //                 matrix (eq. subForcing);
 //   ROWS_BACKSUB: u_O = -(M_OO f_O + M_OG u_G) = A_OO^-1 (f_O - A_OG u_G), rows Omega / all
@@ -59,15 +60,34 @@ enum { ROWS_APPLY = 0, ROWS_FORCING = 1, ROWS_BACKSUB = 2 };
 // store v at (U dof u, column c) of the apply layout; the thread of the last Gamma dof of a
 // subdomain also zeroes the column's padding [n_gamma, ld_gamma), so that the padding never
 // holds stale bits (the buffer is shared by both precisions and every column count)
+// FP32 (the paired layout, apply_paired_index): only the dof's own entry is written; the
+// padding of that buffer (columns past n_gamma, the missing partner of an odd R) is zeroed when
+// it is allocated and never written, so it stays zero
 template <typename T>
 __device__ __forceinline__ void apply_store(T *x, const SubdomainDesc *sd, const int32_t *u2sub, int64_t u, int c, int R,
                                             T v) {
     const SubdomainDesc &d = sd[u2sub[u]];
-    const int64_t offU = d.offU, col = d.offUp * R + (int64_t)c * d.ldG;
-    const int j = (int)(u - offU), nG = d.nG, ldG = d.ldG;
-    x[col + j] = v;
-    if (j == nG - 1)
-        for (int q = nG; q < ldG; ++q) x[col + q] = T(0);
+    const int j = (int)(u - d.offU);
+    if constexpr (std::is_same<T, float>::value) {
+        x[apply_paired_index(d.offXp, d.ldG, j, c, R)] = v;
+    } else {
+        const int64_t col = d.offUp * R + (int64_t)c * d.ldG;
+        const int nG = d.nG, ldG = d.ldG;
+        x[col + j] = v;
+        if (j == nG - 1)
+            for (int q = nG; q < ldG; ++q) x[col + q] = T(0);
+    }
+}
+
+// entries j .. j + W - 1 (j a multiple of W) of right-hand side c of subdomain d in the apply input
+template <typename T>
+__device__ __forceinline__ typename Vec<T>::type load_apply_x(const T *x, const SubdomainDesc &d, int j, int c, int R) {
+    if constexpr (std::is_same<T, float>::value) {
+        const float *p = x + apply_paired_index(d.offXp, d.ldG, j, c, R);
+        return make_float4(__ldg(p), __ldg(p + 2), __ldg(p + 128), __ldg(p + 130));
+    } else {
+        return __ldg(reinterpret_cast<const typename Vec<T>::type *>(x + d.offUp * R + (int64_t)c * d.ldG + j));
+    }
 }
 
 // NR-row x RC-column update from one step of the stream: acc[r][c] += M[r][l..l+W) . x[c][l..l+W)
@@ -90,36 +110,34 @@ __device__ __forceinline__ void rows_step(const typename Vec<T>::type (&mv)[NR],
     }
 }
 
-// The same update for NR rows with each lane's 4 FP32 columns taken as two halves of 2: first
-// columns l, l+1 of every row and right-hand side, then l+2, l+3.  Every acc[r][c] still receives
-// its four products in the order w = 0 .. 3, so the result is bitwise that of rows_step; the
-// operands live in half the registers (for NR = 8 rows of 16 accumulators each).  MT: stored
-// operator type (float, or an FP16 copy widened exactly).
-template <typename MT>
-__device__ __forceinline__ float2 load_pair_widen(const MT *p) {
-    if constexpr (std::is_same<MT, float>::value) {
-        return *reinterpret_cast<const float2 *>(p);
-    } else {
-        static_assert(std::is_same<MT, __half>::value, "FP32 or FP16 operators");
-        return __half22float2(*reinterpret_cast<const __half2 *>(p));
-    }
-}
+// The update of rows_step for NR rows and RC (even) right-hand sides with x in the paired layout:
+// per pair row cp of the stage (512 floats: 256 columns of two right-hand sides), the lane's
+// columns l .. l+3 of both right-hand sides are the float4s at xq + 512 cp and xq + 512 cp + 128
+// ((x[2cp][l], x[2cp+1][l], x[2cp][l+1], x[2cp+1][l+1]) and the same for l+2, l+3), and
+// acc[r][cp] holds the sums of right-hand sides 2cp and 2cp+1 as one pair.  Each element gets
+// fma(m, x, acc) in the order w = 0 .. 3, as in rows_step, with one packed FMA per two
+// right-hand sides: bitwise the result of rows_step.  MT: stored operator type (FP32, or an
+// FP16 copy widened exactly).
 template <int RC, int NR, typename MT>
-__device__ __forceinline__ void rows_step_pairs(const MT *mrow0, int mstride, const float *x0, int xstride,
-                                                float (&acc)[NR][RC]) {
+__device__ __forceinline__ void rows_step_paired(const MT *mrow0, int mstride, const float *xq,
+                                                 float2 (&acc)[NR][RC / 2]) {
+    float4 mv[NR];
 #pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-        float2 mv[NR];
+    for (int r = 0; r < NR; ++r) mv[r] = load_widen<float, MT>(mrow0 + r * mstride);
 #pragma unroll
-        for (int r = 0; r < NR; ++r) mv[r] = load_pair_widen<MT>(mrow0 + r * mstride + 2 * hh);
+    for (int cp = 0; cp < RC / 2; ++cp) {
+        const float4 xa = *reinterpret_cast<const float4 *>(xq + 512 * cp);
+        const float4 xb = *reinterpret_cast<const float4 *>(xq + 512 * cp + 128);
+        const float2 x0 = make_float2(xa.x, xa.y), x1 = make_float2(xa.z, xa.w);
+        const float2 x2 = make_float2(xb.x, xb.y), x3 = make_float2(xb.z, xb.w);
 #pragma unroll
-        for (int c = 0; c < RC; ++c) {
-            const float2 xv = *reinterpret_cast<const float2 *>(x0 + c * xstride + 2 * hh);
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                acc[r][c] += mv[r].x * xv.x;
-                acc[r][c] += mv[r].y * xv.y;
-            }
+        for (int r = 0; r < NR; ++r) {
+            float2 a = acc[r][cp];
+            a = __ffma2_rn(make_float2(mv[r].x, mv[r].x), x0, a);
+            a = __ffma2_rn(make_float2(mv[r].y, mv[r].y), x1, a);
+            a = __ffma2_rn(make_float2(mv[r].z, mv[r].z), x2, a);
+            a = __ffma2_rn(make_float2(mv[r].w, mv[r].w), x3, a);
+            acc[r][cp] = a;
         }
     }
 }
@@ -182,7 +200,6 @@ __global__ void __launch_bounds__(256, 2) k_rows(const MT *base, int use_sp, con
 #pragma unroll
             for (int c = 0; c < RC; ++c) acc[r][c] = T(0);
         if constexpr (MODE == ROWS_APPLY) {
-            const T *xk = x + d.offUp * R + (int64_t)c0 * ld;
             if (ib < n) {
                 int l = lane * W;
                 for (; l + 32 * W < ncp; l += 64 * W) {
@@ -194,16 +211,15 @@ __global__ void __launch_bounds__(256, 2) k_rows(const MT *base, int use_sp, con
 #pragma unroll
                     for (int u = 0; u < 2; ++u)
                         rows_step<T, RC>(mv[u], [&](int c) {
-                            return c < rc ? __ldg(reinterpret_cast<const V *>(xk + (int64_t)c * ld + l + u * 32 * W)) : V{};
+                            return c < rc ? load_apply_x<T>(x, d, l + u * 32 * W, c0 + c, R) : V{};
                         }, acc);
                 }
                 for (; l < ncp; l += 32 * W) {
                     V mv[4];
 #pragma unroll
                     for (int r = 0; r < 4; ++r) mv[r] = ldcs_widen<T, MT>(Mr[r] + l);
-                    rows_step<T, RC>(mv, [&](int c) {
-                        return c < rc ? __ldg(reinterpret_cast<const V *>(xk + (int64_t)c * ld + l)) : V{};
-                    }, acc);
+                    rows_step<T, RC>(mv, [&](int c) { return c < rc ? load_apply_x<T>(x, d, l, c0 + c, R) : V{}; },
+                                     acc);
                 }
             }
         } else {

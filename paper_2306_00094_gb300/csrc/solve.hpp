@@ -27,7 +27,8 @@ struct SolveWS {
     uint64_t prob_uid = 0;
     int R = 0;
     DevMem lam, r, w, z, y, pv, q, d, cvec, dlam;      // Lambda space (FP64)
-    DevMem fU, yU, uU, xU;                              // U space
+    DevMem fU, yU, uU, xU;                              // U space (xU: apply input, FP64 and FP16 layouts)
+    DevMem xP;                                          // FP32 apply input, paired layout (apply_paired_index)
     DevMem xmaps[2];                                    // tensor maps of xU per subdomain (FP32, FP64),
                                                         // tiles of the default column block apply_rc(R)
     DevMem xmaps_rc[2][5];                              // the same for column blocks 1, 2, 4, 8, 16 (the
