@@ -176,6 +176,26 @@ __device__ __forceinline__ void apply_shape(const SubdomainDesc &d, int &n, int 
     else { n = d.nO; ncp = min(d.ldM, (d.nk + 7) / 8 * 8); }
 }
 
+// an item's fields, loaded one item ahead (the chain schedule -> subdomain descriptor is two
+// dependent global loads; issued while the previous item streams, it no longer stalls the warps
+// at item boundaries)
+struct ApplyItem {
+    int k, i0, n, ncp;
+    int64_t yoff, voff, nO;
+};
+template <int MODE>
+__device__ __forceinline__ ApplyItem load_apply_item(const int32_t *sched_items, const SubdomainDesc *sd, int it) {
+    ApplyItem a;
+    a.k = sched_items[2 * it];
+    a.i0 = sched_items[2 * it + 1];
+    const SubdomainDesc &d = sd[a.k];
+    apply_shape<MODE>(d, a.n, a.ncp);
+    a.yoff = d.offU;
+    a.voff = d.offV;
+    a.nO = d.nO;
+    return a;
+}
+
 // MODE (ROWS_APPLY, ROWS_FORCING, ROWS_BACKSUB) selects the operator block (above), the tensor
 // maps (APPLY: 2 per subdomain, use_sp picks; else 1 per subdomain) and the output:
 //   APPLY     y[(offU + i) R + c] = acc * oscale;
@@ -224,11 +244,14 @@ __global__ void __launch_bounds__(apply_threads(RPW), MINB)
         int q = 0;
         bool ok = true;
         const uint64_t stream_policy = l2_evict_first_policy();
+        ApplyItem nxt{};
+        if (it0 < it1) nxt = load_apply_item<MODE>(sched_items, sd, it0);
         for (int it = it0; it < it1 && ok; ++it) {
-            // descriptor fields in registers: the asm statements below clobber memory
-            const int k = sched_items[2 * it], i0 = sched_items[2 * it + 1];
-            int n, ncp;
-            apply_shape<MODE>(sd[k], n, ncp);
+            // descriptor fields in registers (the asm statements below clobber memory); the next
+            // item's are loaded now and used one item later
+            const ApplyItem cur = nxt;
+            if (it + 1 < it1) nxt = load_apply_item<MODE>(sched_items, sd, it + 1);
+            const int k = cur.k, i0 = cur.i0, ncp = cur.ncp;
             const CUtensorMap *map = MODE == ROWS_APPLY ? maps + 2 * k + use_sp : maps + k, *xmap = xmaps + k;
             for (int c0 = 0; c0 < R && ok; c0 += RC)        // the rows again for every column block
             for (int l0 = 0; l0 < ncp; l0 += CW, ++q) {
@@ -259,11 +282,13 @@ __global__ void __launch_bounds__(apply_threads(RPW), MINB)
     }
     // ---------------------------------------------------------------------- consumers
     int q = 0;
+    ApplyItem nxt{};
+    if (it0 < it1) nxt = load_apply_item<MODE>(sched_items, sd, it0);
     for (int it = it0; it < it1; ++it) {
-        const int k = sched_items[2 * it], i0 = sched_items[2 * it + 1];
-        int n, ncp;
-        apply_shape<MODE>(sd[k], n, ncp);
-        const int64_t yoff = sd[k].offU, voff = sd[k].offV, nO = sd[k].nO;
+        const ApplyItem cur = nxt;
+        if (it + 1 < it1) nxt = load_apply_item<MODE>(sched_items, sd, it + 1);
+        const int i0 = cur.i0, n = cur.n, ncp = cur.ncp;
+        const int64_t yoff = cur.yoff, voff = cur.voff, nO = cur.nO;
         const int ib = i0 + warp * RPW;
         for (int c0 = 0; c0 < R; c0 += RC) {
             const int rc = min(RC, R - c0);
