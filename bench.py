@@ -161,7 +161,7 @@ def percentile(xs, q):
     return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
 
 
-def profile_traffic(kernel_src_hash, name="k_apply_tma_const_l2_h128.md"):
+def profile_traffic(kernel_src_hash, name="k_apply_tma_peridynamic_2d.md"):
     """DRAM bytes per launch of an apply kernel from the committed ncu summary, if it matches
     the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", name)
