@@ -25,11 +25,12 @@
 //               of mma_ns stages (full[s]: copy bytes landed; empty[s]: MMAs done reading);
 //   warp 5      owns the tensor-memory allocation; one lane issues the MMAs of an item, the
 //               k-th MMA of every stage into accumulator k of MMA_ACC (each cleared by its
-//               first MMA: independent chains), commits every stage to empty[s] and the item
-//               to tmem_full;
-//   warps 0..3  epilogue: wait tmem_full, read the MMA_ACC 128 x NP accumulators (warp w
+//               first MMA: independent chains) of the item's set (items alternate between two
+//               sets, so that an item's MMAs run while the epilogue drains the one before),
+//               commits every stage to empty[s] and the item to tmem_full[set];
+//   warps 0..3  epilogue: wait tmem_full[set], read the MMA_ACC 128 x NP accumulators (warp w
 //               reads lanes 32w..32w+31, its row of the item) and add them in order, release
-//               them through tmem_empty, and store y[(offU + row) * R + c] for rows < n_gamma,
+//               them through tmem_empty[set], and store y[(offU + row) * R + c] for rows < n_gamma,
 //               columns < R, times oscale / xscale[c] (a power of two formed once per column;
 //               the FP64 pipe of this GPU runs at a small fraction of the FP32 rate, and a division
 //               per entry kept it a third busy: 63.6 -> 37.8 us per apply on the peridynamic
@@ -56,8 +57,13 @@ __host__ __device__ constexpr int mma_smem_bytes(int np) { return mma_ns(np) * m
 // that no chain of dependent accumulations into one tile can set the pace of the small
 // 128 x 16 x 16 MMAs (on that workload one accumulator measured the same: the copies set it)
 constexpr int MMA_ACC = 4;
+// two accumulator sets (items alternate between them, so that the MMAs of an item overlap the
+// epilogue of the one before)
 __host__ __device__ constexpr int mma_tmem_cols(int np) {
-    return MMA_ACC * np <= 32 ? 32 : (MMA_ACC * np <= 64 ? 64 : (MMA_ACC * np <= 128 ? 128 : 256));
+    return 2 * MMA_ACC * np <= 32 ? 32
+                                  : (2 * MMA_ACC * np <= 64 ? 64
+                                                            : (2 * MMA_ACC * np <= 128 ? 128
+                                                                                       : (2 * MMA_ACC * np <= 256 ? 256 : 512)));
 }
 
 // N of the MMA for R right-hand sides (R <= MMA_MAX_R): 16, 32 or 64
@@ -173,7 +179,7 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
     constexpr uint32_t IDESC = mma_idesc_f16(MMA_M, NP);
     extern __shared__ __align__(128) unsigned char mma_raw[];
     unsigned char *ring = mma_raw + ((1024u - (smem_u32(mma_raw) & 1023u)) & 1023u);
-    __shared__ uint64_t full[MMA_NS], empty[MMA_NS], tmem_full, tmem_empty, drain;
+    __shared__ uint64_t full[MMA_NS], empty[MMA_NS], tmem_full[2], tmem_empty[2], drain;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     __shared__ double colfac[NP];       // oscale / xscale[c] (a power of two): formed once per column
@@ -190,8 +196,10 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&tmem_full, 1);
-        mbar_init(&tmem_empty, 4 * 32);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tmem_full[b], 1);
+            mbar_init(&tmem_empty[b], 4 * 32);
+        }
         mbar_init(&drain, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -250,8 +258,10 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
             for (int it = it0; it < it1 && ok; ++it, ++j) {
                 const int k = sched_items[2 * it];
                 const int ncp = min(sd[k].ldG, (sd[k].nG + 7) / 8 * 8);
-                if (j > 0) {
-                    if (abort_flag || !mbar_wait(&tmem_empty, (j - 1) & 1)) { ok = false; break; }
+                const uint32_t acc0 = tmem + (uint32_t)((j & 1) * MMA_ACC * NP);
+                if (j > 1) {
+                    // accumulator set j & 1 was last used by item j - 2
+                    if (abort_flag || !mbar_wait(&tmem_empty[j & 1], ((j - 2) >> 1) & 1)) { ok = false; break; }
                     tc_fence_after();
                 }
                 for (int l0 = 0; l0 < ncp; l0 += MMA_KB, ++q) {
@@ -262,12 +272,12 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
                     static_assert(MMA_KB / 16 == MMA_ACC, "one accumulator per K step of a stage");
 #pragma unroll
                     for (int kk = 0; kk < MMA_KB / 16; ++kk)    // K = 16 per MMA: 32 bytes along the row
-                        tc_mma_f16(tmem + (uint32_t)(kk * NP), mma_smem_desc(a + 32 * kk), mma_smem_desc(b + 32 * kk),
+                        tc_mma_f16(acc0 + (uint32_t)(kk * NP), mma_smem_desc(a + 32 * kk), mma_smem_desc(b + 32 * kk),
                                    IDESC, l0 > 0 ? 1 : 0);
                     issued = true;
                     tc_commit(&empty[s]);
                 }
-                if (ok) tc_commit(&tmem_full);
+                if (ok) tc_commit(&tmem_full[j & 1]);
             }
             if (!ok) {
                 fail();
@@ -282,7 +292,7 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
         int j = 0;
         for (int it = it0; it < it1; ++it, ++j) {
             const int k = sched_items[2 * it], i0 = sched_items[2 * it + 1];
-            bool ok = !abort_flag && mbar_wait(&tmem_full, j & 1);
+            bool ok = !abort_flag && mbar_wait(&tmem_full[j & 1], (j >> 1) & 1);
             if (__any_sync(0xffffffffu, !ok)) {
                 if (lane == 0) fail();
                 break;
@@ -293,7 +303,7 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
 #pragma unroll
             for (int c0 = 0; c0 < NP; c0 += 16) {
                 float v[16], t[16];
-                const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+                const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((j & 1) * MMA_ACC * NP + c0);
                 tc_ld16(ta, v);
 #pragma unroll
                 for (int a = 1; a < MMA_ACC; ++a) {
@@ -307,7 +317,7 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
                         if (c0 + c < R) y[(yoff + row) * R + c0 + c] = f2d_pow2(v[c], colexp[c0 + c], colfac[c0 + c]);
             }
             tc_fence_before();
-            mbar_arrive(&tmem_empty);
+            mbar_arrive(&tmem_empty[j & 1]);
         }
     }
     tc_fence_before();
