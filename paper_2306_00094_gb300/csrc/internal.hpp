@@ -225,18 +225,19 @@ struct nlfeti_problem {
     nlf::DevMem d_Bt_ptr, d_Bt_row;      // per U dof: rows, signed (r+1 for +1, -(r+1) for -1)
     nlf::DevMem d_BD_ptr, d_BD_col, d_BD_val;    // B_D rows (U index, value)
     nlf::DevMem d_BDt_ptr, d_BDt_row, d_BDt_val; // B_D^T rows per U dof
+    nlf::DevMem d_BD_val32, d_BDt_val32;         // FP32 copies of the values (FP32 PCG iterations)
     nlf::DevMem d_Z;                     // (n_u x 3) FP64 kernel basis of floating subdomains
     nlf::DevMem d_Q;                     // (n_u x 3) FP64 orthonormal kernel basis
     nlf::DevMem d_GtGinv;                // n_co x n_co FP64
     // rows of G = B Z: per Lambda row gw slots (coarse column, value), the first gw/2 for the
     // +1 side (Z rows of B_plus), the rest for the -1 side; empty slots have column -1
     int gw = 0;
-    nlf::DevMem d_Gcol, d_Gval;
+    nlf::DevMem d_Gcol, d_Gval, d_Gval32;        // d_Gval32: FP32 copy
     nlf::DevMem d_float_ids;             // floating subdomains (int32)
     // G^T gathers per floating subdomain f: entry ranges (4 int64: Lambda-mode e0, e1 into the
     // B^T entries, U-mode u0, u1), (co_off, n_co), and per B^T entry its Lambda row and the
     // weights sign * Z[u] (3 doubles)
-    nlf::DevMem d_gt_range, d_gt_co, d_gt_rows, d_gt_w;
+    nlf::DevMem d_gt_range, d_gt_co, d_gt_rows, d_gt_w, d_gt_w32;   // d_gt_w32: FP32 copy
     nlf::DevMem d_u2sub;                 // per U dof: subdomain (int32)
     nlf::DevMem d_u2v;                   // per U dof: position in the subdomain vectors (int64)
     nlf::DevMem d_vdofs;                 // per subdomain-vector entry: global dof (int32)

@@ -35,7 +35,7 @@ template <typename X> struct TypeTag { using type = X; };
 constexpr int RED_BLOCKS = 304;     // two CTAs per SM for reductions
 constexpr int RED_THREADS = 256;
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename V> __device__ __forceinline__ V warp_sum(V v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
@@ -109,14 +109,15 @@ __global__ void k_constraint_residual(const int64_t *Bp, const int64_t *Bm, cons
     }
 }
 
-// out = B_D y
-__global__ void k_gather_bd(const int64_t *ptr, const int64_t *col, const double *val, const double *y, double *out,
-                            int64_t nl, int R) {
+// out = B_D y (y an FP64 U vector, the sum in the type L of the Lambda vectors)
+template <typename L>
+__global__ void k_gather_bd(const int64_t *ptr, const int64_t *col, const L *val, const double *y, L *out, int64_t nl,
+                            int R) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl * R; t += (int64_t)gridDim.x * blockDim.x) {
         int64_t r = t / R;
         int c = (int)(t % R);
-        double s = 0;
-        for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) s += val[q] * y[col[q] * R + c];
+        L s = 0;
+        for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) s += val[q] * (L)y[col[q] * R + c];
         out[t] = s;
     }
 }
@@ -218,11 +219,13 @@ __device__ __forceinline__ double z_alpha(const SubdomainDesc *sd, const int32_t
     return s;
 }
 
-// (G alpha)_r for column c from the slots of row r of G = B Z
-__device__ __forceinline__ double g_alpha(const int32_t *gcol, const double *gval, int gw, const double *alpha,
-                                          int64_t r, int c, int R) {
+// (G alpha)_r for column c from the slots of row r of G = B Z, in the arithmetic type L of
+// the Lambda vectors (FP64, or FP32 in the FP32 pass with FP32 copies of G and alpha)
+template <typename L>
+__device__ __forceinline__ L g_alpha(const int32_t *gcol, const L *gval, int gw, const L *alpha, int64_t r, int c,
+                                     int R) {
     const int h = gw / 2;
-    double sp = 0, sm = 0;
+    L sp = 0, sm = 0;
     for (int e = 0; e < h; ++e) {
         const int cp = gcol[r * gw + e], cm = gcol[r * gw + h + e];
         if (cp >= 0) sp += gval[r * gw + e] * alpha[(int64_t)cp * R + c];
@@ -255,6 +258,7 @@ __global__ void k_apply_zalpha(const SubdomainDesc *sd, const int32_t *u2sub, co
 struct PcgScalars {
     double *nPd, *yw_old, *yw, *eta, *beta, *relres, *corr;
     double *xscale;        // per column: 2^-floor(log2 ||w||) (FP16 input of the tensor-core apply)
+    float *eta_f, *beta_f, *xscale_f;   // FP32 copies of eta, beta, xscale (the FP32 pass's steps)
     int *active, *iters, *n_active;
     int *loops;            // PCG iterations run by the current graph loop
     int *err;              // set by a device wait that ran out (checked after the solve)
@@ -262,6 +266,22 @@ struct PcgScalars {
 };
 
 enum { FIN_NPD = 0, FIN_CHECK = 1, FIN_BETA = 2, FIN_ETA = 3 };
+
+// the step scalars in the arithmetic type L of the Lambda vectors
+template <typename L> __device__ __forceinline__ const L *eta_of(const PcgScalars &s) {
+    if constexpr (std::is_same<L, float>::value) return s.eta_f;
+    else return s.eta;
+}
+template <typename L> __device__ __forceinline__ const L *beta_of(const PcgScalars &s) {
+    if constexpr (std::is_same<L, float>::value) return s.beta_f;
+    else return s.beta;
+}
+template <typename L> __device__ __forceinline__ const L *xscale_of(const PcgScalars &s) {
+    if constexpr (std::is_same<L, float>::value) return s.xscale_f;
+    else return s.xscale;
+}
+__device__ __forceinline__ double fma_l(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_l(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 // Reductions over Lambda: grid (row blocks, right-hand sides), one thread per row of one
 // column.  The row blocks depend on the vector length only, so every column is summed in the
@@ -308,7 +328,8 @@ __device__ __forceinline__ bool arrive_last(unsigned *counter) {
 // order of the additions, so every column is summed in the same order whatever the batch it
 // is part of; the lanes of a unit read 4 rows x cw consecutive columns per step, and each lane
 // has two rows in flight.  f(i, c) is called once per entry (i < n, c < R) and returns its
-// addend.  The block partials are stored column by column (partial[c * blocks + b]), so that the
+// addend; a unit's sum is formed in the addends' type (FP32 in the FP32 pass), the tile sums
+// onward in FP64.  The block partials are stored column by column (partial[c * blocks + b]), so that the
 // last block reads each column's partials as whole lines (measured: the finish of 608 blocks x 16
 // columns took 10 us with the partials row by row, 6 us column by column).
 constexpr int RT = 8;
@@ -323,6 +344,7 @@ inline int tile_blocks(int64_t n) {
 
 template <typename F>
 __device__ __forceinline__ void tile_reduce(int64_t n, int R, double *partial, F &&f) {
+    using A = decltype(f(int64_t(0), 0));   // the addends' type: the four-lane unit sums in it
     __shared__ double ts[RSMEM];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t ntiles = (n + RT - 1) / RT;
@@ -343,7 +365,7 @@ __device__ __forceinline__ void tile_reduce(int64_t n, int R, double *partial, F
                 const int u = ub + ju;
                 const int tl = u / nchunk, cl = (u % nchunk) * cw + cj;
                 const bool ok = u < units && cl < ncol;
-                double v = 0;
+                A v = 0;
                 if (ok) {
                     const int64_t i0 = (tb + tl) * RT + h;
                     if (i0 < n) v += f(i0, cc0 + cl);
@@ -351,7 +373,7 @@ __device__ __forceinline__ void tile_reduce(int64_t n, int R, double *partial, F
                 }
                 v += __shfl_down_sync(0xffffffffu, v, 2 * cw);
                 v += __shfl_down_sync(0xffffffffu, v, cw);
-                if (ok && h == 0) ts[tl * ncol + cl] = v;
+                if (ok && h == 0) ts[tl * ncol + cl] = (double)v;
             }
             __syncthreads();
             if (threadIdx.x < ncol)
@@ -396,9 +418,15 @@ __device__ void finish_scalars(const double *partial, int nb, int R, PcgScalars 
                 s.relres[c] = 1.0;
                 s.eta[c] = 0.0;
                 s.beta[c] = 0.0;
+                s.eta_f[c] = 0.0f;
+                s.beta_f[c] = 0.0f;
+                s.xscale_f[c] = 1.0f;
             } else if (MODE == FIN_CHECK) {
                 const double nw = sqrt(v), ref = s.nPd[c];
-                s.xscale[c] = (nw > 0.0 && nw < INFINITY) ? ldexp(1.0, -ilogb(nw)) : 1.0;
+                // a power of two that FP32 holds too (the FP32 pass scales with the same factor)
+                const double xs = (nw > 0.0 && nw < INFINITY) ? ldexp(1.0, max(-126, min(126, -ilogb(nw)))) : 1.0;
+                s.xscale[c] = xs;
+                s.xscale_f[c] = (float)xs;
                 int act = s.active[c];
                 if (act) s.relres[c] = ref > 0 ? nw / ref : 0.0;
                 if (act && (nw <= tol * ref || s.iters[c] >= max_it)) act = 0;
@@ -406,10 +434,14 @@ __device__ void finish_scalars(const double *partial, int nb, int R, PcgScalars 
                 if (act) atomicAdd(&n_act, 1);
             } else if (MODE == FIN_BETA) {
                 s.yw[c] = v;
-                s.beta[c] = (s.iters[c] == 0 || s.yw_old[c] == 0.0) ? 0.0 : v / s.yw_old[c];
+                const double b = (s.iters[c] == 0 || s.yw_old[c] == 0.0) ? 0.0 : v / s.yw_old[c];
+                s.beta[c] = b;
+                s.beta_f[c] = (float)b;
             } else {
                 const bool act = s.active[c] != 0;
-                s.eta[c] = (act && v != 0.0) ? s.yw[c] / v : 0.0;
+                const double e = (act && v != 0.0) ? s.yw[c] / v : 0.0;
+                s.eta[c] = e;
+                s.eta_f[c] = (float)e;
                 if (act) { s.yw_old[c] = s.yw[c]; s.iters[c] += 1; }
             }
         }
@@ -436,25 +468,26 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot_final(const double *__restr
 // (the same bits everywhere):
 //   p_new = y + beta p on active columns (p unchanged on converged ones),
 //   r_new = r - eta q (eta = 0 on converged columns and before the first iteration).
-__device__ __forceinline__ double p_next(double p, double y, double beta, bool active) {
-    return active ? __fma_rn(beta, p, y) : p;
+// L: the arithmetic type of the Lambda vectors (FP64; FP32 in the FP32 pass).
+template <typename L> __device__ __forceinline__ L p_next(L p, L y, L beta, bool active) {
+    return active ? fma_l(beta, p, y) : p;
 }
-__device__ __forceinline__ double r_next(double r, double q, double eta) { return __fma_rn(-eta, q, r); }
+template <typename L> __device__ __forceinline__ L r_next(L r, L q, L eta) { return fma_l(-eta, q, r); }
 
 // out = P v = v - G alpha (alpha from k_proj_g; NULL when there is no coarse space), with the
 // dot product of MODE: CHECK (out, out), BETA (out, other).  Grid tile_blocks(nl).
-template <int MODE>
+template <int MODE, typename L>
 __global__ void __launch_bounds__(RED_THREADS) k_project_dot(const int32_t *__restrict__ gcol,
-                                                              const double *__restrict__ gval, int gw,
-                                                              const double *__restrict__ alpha,
-                                                              const double *__restrict__ v,
-                                                              const double *__restrict__ other,
-                                                              double *__restrict__ out, int64_t nl, int R,
+                                                              const L *__restrict__ gval, int gw,
+                                                              const L *__restrict__ alpha,
+                                                              const L *__restrict__ v,
+                                                              const L *__restrict__ other,
+                                                              L *__restrict__ out, int64_t nl, int R,
                                                               double *partial, PcgScalars s, double tol, int max_it) {
     tile_reduce(nl, R, partial, [&](int64_t i, int c) {
         const int64_t t = i * R + c;
-        double x = v[t];
-        if (alpha) x += -1.0 * g_alpha(gcol, gval, gw, alpha, i, c, R);
+        L x = v[t];
+        if (alpha) x += -g_alpha(gcol, gval, gw, alpha, i, c, R);
         out[t] = x;
         return x * (MODE == FIN_CHECK ? x : other[t]);
     });
@@ -463,17 +496,19 @@ __global__ void __launch_bounds__(RED_THREADS) k_project_dot(const int32_t *__re
 
 // q = B y_U with (p_new, q) and the ETA update (p_new formed per row, stored by the next
 // iteration's k_check_update).  Grid tile_blocks(nl).
+template <typename L>
 __global__ void __launch_bounds__(RED_THREADS) k_gather_b_eta(const int64_t *__restrict__ Bp,
                                                                const int64_t *__restrict__ Bm,
                                                                const double *__restrict__ yU,
-                                                               const double *__restrict__ pv,
-                                                               const double *__restrict__ y, double *__restrict__ q,
+                                                               const L *__restrict__ pv,
+                                                               const L *__restrict__ y, L *__restrict__ q,
                                                                int64_t nl, int R, double *partial, PcgScalars s) {
+    const L *beta = beta_of<L>(s);
     tile_reduce(nl, R, partial, [&](int64_t i, int c) {
         const int64_t t = i * R + c;
-        const double x = yU[Bp[i] * R + c] - yU[Bm[i] * R + c];
+        const L x = (L)(yU[Bp[i] * R + c] - yU[Bm[i] * R + c]);
         q[t] = x;
-        return p_next(pv[t], y[t], s.beta[c], s.active[c] != 0) * x;
+        return p_next(pv[t], y[t], beta[c], s.active[c] != 0) * x;
     });
     if (arrive_last(s.counter)) finish_scalars<FIN_ETA>(partial, gridDim.x, R, s, 0.0, 0);
 }
@@ -486,26 +521,27 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_b_eta(const int64_t *__r
 // right-hand side is active and fewer than limit iterations have run, so the loop ends
 // whatever the scalars hold); a separate instantiation, as profilers skip kernels that set
 // graph conditions.
-template <int COND>
+template <int COND, typename L>
 __global__ void __launch_bounds__(RED_THREADS) k_check_update(const int32_t *__restrict__ gcol,
-                                                               const double *__restrict__ gval, int gw,
-                                                               const double *__restrict__ alpha,
-                                                               const double *__restrict__ y, double *__restrict__ pv,
-                                                               double *__restrict__ lam, double *__restrict__ r,
-                                                               const double *__restrict__ q, double *__restrict__ w,
+                                                               const L *__restrict__ gval, int gw,
+                                                               const L *__restrict__ alpha,
+                                                               const L *__restrict__ y, L *__restrict__ pv,
+                                                               L *__restrict__ lam, L *__restrict__ r,
+                                                               const L *__restrict__ q, L *__restrict__ w,
                                                                int64_t nl, int R, double *partial, PcgScalars s,
                                                                double tol, int max_it, cudaGraphConditionalHandle cond,
                                                                int limit) {
+    const L *eta = eta_of<L>(s), *beta = beta_of<L>(s);
     tile_reduce(nl, R, partial, [&](int64_t i, int c) {
         const int64_t t = i * R + c;
-        const double e = s.eta[c];
-        const double pn = p_next(pv[t], y[t], s.beta[c], s.active[c] != 0);
+        const L e = eta[c];
+        const L pn = p_next(pv[t], y[t], beta[c], s.active[c] != 0);
         pv[t] = pn;
-        lam[t] = __fma_rn(e, pn, lam[t]);
-        const double rn = r_next(r[t], q[t], e);
+        lam[t] = fma_l(e, pn, lam[t]);
+        const L rn = r_next(r[t], q[t], e);
         r[t] = rn;
-        double x = rn;
-        if (alpha) x += -1.0 * g_alpha(gcol, gval, gw, alpha, i, c, R);
+        L x = rn;
+        if (alpha) x += -g_alpha(gcol, gval, gw, alpha, i, c, R);
         w[t] = x;
         return x * x;
     });
@@ -519,22 +555,41 @@ __global__ void __launch_bounds__(RED_THREADS) k_check_update(const int32_t *__r
     }
 }
 
+// Entry of the FP32 pass's iterations: r and lambda rounded to FP32, p, y and q zero; and its
+// exit: lambda and r back in FP64.  n = n_lambda R entries.
+__global__ void k_lam_enter(const double *r, const double *lam, float *rf, float *lf, float *pf, float *yf, float *qf,
+                            int64_t n) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        rf[t] = (float)r[t];
+        lf[t] = (float)lam[t];
+        pf[t] = 0.0f;
+        yf[t] = 0.0f;
+        qf[t] = 0.0f;
+    }
+}
+__global__ void k_lam_exit(const float *lf, const float *rf, double *lam, double *r, int64_t n) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        lam[t] = (double)lf[t];
+        r[t] = (double)rf[t];
+    }
+}
+
 // x (apply layout) = B^T p_new (B^T rows signed r+1 / -(r+1)), p_new formed per row: the input
 // of the S^+ apply of a PCG iteration
-template <typename T>
-__global__ void k_gather_apply_p(const int64_t *ptr, const int64_t *row, const double *pv, const double *y,
-                                 const double *beta, const int *active, T *x, const SubdomainDesc *sd,
-                                 const int32_t *u2sub, int64_t nu, int R, const int *gate) {
+template <typename T, typename L>
+__global__ void k_gather_apply_p(const int64_t *ptr, const int64_t *row, const L *pv, const L *y, const L *beta,
+                                 const int *active, T *x, const SubdomainDesc *sd, const int32_t *u2sub, int64_t nu,
+                                 int R, const int *gate) {
     if (gate && *gate == 0) return;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(t / nu);
         const int64_t u = t % nu;
         const bool act = active[c] != 0;
-        const double be = beta[c];
-        double s = 0;
+        const L be = beta[c];
+        L s = 0;
         for (int64_t q = ptr[u]; q < ptr[u + 1]; ++q) {
             const int64_t r = row[q], i = r > 0 ? r - 1 : -r - 1;
-            const double pn = p_next(pv[i * R + c], y[i * R + c], be, act);
+            const L pn = p_next(pv[i * R + c], y[i * R + c], be, act);
             s += r > 0 ? pn : -pn;
         }
         apply_store<T>(x, sd, u2sub, u, c, R, (T)s);
@@ -545,15 +600,18 @@ __global__ void k_gather_apply_p(const int64_t *ptr, const int64_t *row, const d
 // with all R columns; the sums are formed with the columns fastest (the R entries of a Lambda
 // row are consecutive: coalesced reads), staged as [c][u], and stored with the U dofs fastest
 // (coalesced stores into the per-subdomain columns).  Each sum runs over its CSR entries in the
-// same order as in the column-major kernels, so the stored values are the same bits.
-// Dynamic shared memory GX_U * R doubles (R <= GX_MAXR).
+// same order as in the column-major kernels, so the stored values are the same bits.  The sums
+// are staged in their own type (that of the Lambda vectors).  Dynamic shared memory GX_U * R
+// doubles (R <= GX_MAXR).
 constexpr int GX_U = 32;
 constexpr int GX_MAXR = 64;
 
 template <typename T, typename G>
 __device__ __forceinline__ void gather_x_block(T *x, const SubdomainDesc *sd, const int32_t *u2sub, int64_t nu, int R,
                                                G &&g) {
-    extern __shared__ double gx_sm[];
+    using S = decltype(g(int64_t(0), 0));
+    extern __shared__ double gx_raw[];
+    S *gx_sm = reinterpret_cast<S *>(gx_raw);
     const int64_t u0 = (int64_t)blockIdx.x * GX_U;
     const int nuu = (int)min((int64_t)GX_U, nu - u0);
     for (int t = threadIdx.x; t < nuu * R; t += blockDim.x) {
@@ -568,21 +626,21 @@ __device__ __forceinline__ void gather_x_block(T *x, const SubdomainDesc *sd, co
 }
 
 // x = B^T p_new (as k_gather_apply_p)
-template <typename T>
+template <typename T, typename L>
 __global__ void __launch_bounds__(256) k_gather_apply_p_t(const int64_t *__restrict__ ptr,
                                                           const int64_t *__restrict__ row,
-                                                          const double *__restrict__ pv, const double *__restrict__ y,
-                                                          const double *beta, const int *active, T *x,
+                                                          const L *__restrict__ pv, const L *__restrict__ y,
+                                                          const L *beta, const int *active, T *x,
                                                           const SubdomainDesc *sd, const int32_t *u2sub, int64_t nu,
                                                           int R, const int *gate) {
     if (gate && *gate == 0) return;
     gather_x_block<T>(x, sd, u2sub, nu, R, [&](int64_t u, int c) {
         const bool act = active[c] != 0;
-        const double be = beta[c];
-        double s = 0;
+        const L be = beta[c];
+        L s = 0;
         for (int64_t q = ptr[u]; q < ptr[u + 1]; ++q) {
             const int64_t r = row[q], i = r > 0 ? r - 1 : -r - 1;
-            const double pn = p_next(pv[i * R + c], y[i * R + c], be, act);
+            const L pn = p_next(pv[i * R + c], y[i * R + c], be, act);
             s += r > 0 ? pn : -pn;
         }
         return s;
@@ -590,15 +648,15 @@ __global__ void __launch_bounds__(256) k_gather_apply_p_t(const int64_t *__restr
 }
 
 // x = B^T v, or B_D^T v when val is given (as k_gather_apply)
-template <typename T>
+template <typename T, typename L>
 __global__ void __launch_bounds__(256) k_gather_apply_t(const int64_t *__restrict__ ptr,
                                                         const int64_t *__restrict__ row,
-                                                        const double *__restrict__ val,
-                                                        const double *__restrict__ v, T *x, const SubdomainDesc *sd,
+                                                        const L *__restrict__ val,
+                                                        const L *__restrict__ v, T *x, const SubdomainDesc *sd,
                                                         const int32_t *u2sub, int64_t nu, int R, const int *gate) {
     if (gate && *gate == 0) return;
     gather_x_block<T>(x, sd, u2sub, nu, R, [&](int64_t u, int c) {
-        double s = 0;
+        L s = 0;
         if (val) {
             for (int64_t q = ptr[u]; q < ptr[u + 1]; ++q) s += val[q] * v[row[q] * R + c];
         } else {
@@ -613,26 +671,30 @@ __global__ void __launch_bounds__(256) k_gather_apply_t(const int64_t *__restric
 
 // store v * xscale (a power of two), rounded once to FP16, at (U dof u, column c) of the
 // apply layout; the thread of the last Gamma dof of a subdomain zeroes the column's padding
+__device__ __forceinline__ __half to_half(double v) { return __double2half(v); }
+__device__ __forceinline__ __half to_half(float v) { return __float2half_rn(v); }
+template <typename V>
 __device__ __forceinline__ void store_f16(__half *x, const SubdomainDesc *sd, const int32_t *u2sub, int64_t u, int c,
-                                          int R, double v) {
+                                          int R, V v) {
     const SubdomainDesc &d = sd[u2sub[u]];
     const int64_t col = d.offUp * R + (int64_t)c * d.ldG;
     const int j = (int)(u - d.offU);
-    x[col + j] = __double2half(v);
+    x[col + j] = to_half(v);
     if (j == d.nG - 1)
         for (int q = d.nG; q < d.ldG; ++q) x[col + q] = __float2half(0.0f);
 }
 
 // x (apply layout, FP16) = xscale B_D^T v for the tensor-core preconditioner apply (the sums
-// of k_gather_apply in FP64, scaled exactly, rounded once)
-__global__ void k_gather_apply_f16(const int64_t *ptr, const int64_t *row, const double *val, const double *v,
-                                   const double *xscale, __half *x, const SubdomainDesc *sd, const int32_t *u2sub,
-                                   int64_t nu, int R, const int *gate) {
+// of k_gather_apply in the type of the Lambda vectors, scaled exactly, rounded once)
+template <typename L>
+__global__ void k_gather_apply_f16(const int64_t *ptr, const int64_t *row, const L *val, const L *v, const L *xscale,
+                                   __half *x, const SubdomainDesc *sd, const int32_t *u2sub, int64_t nu, int R,
+                                   const int *gate) {
     if (gate && *gate == 0) return;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(t / nu);
         const int64_t u = t % nu;
-        double s = 0;
+        L s = 0;
         for (int64_t q = ptr[u]; q < ptr[u + 1]; ++q) s += val[q] * v[row[q] * R + c];
         store_f16(x, sd, u2sub, u, c, R, s * xscale[c]);
     }
@@ -696,25 +758,26 @@ __global__ void k_stage_rows_x(const double *xa, const double *xb, const Subdoma
 constexpr int PSPLIT = 8;
 constexpr int kCoarseFusedMax = 16;     // n_co up to which the last block of k_proj_g solves
 enum { PG_U = 0, PG_LAM = 1, PG_LAM_R = 2 };
-template <int VMODE>
+// L: the type of v, q, the weights, the per-block sums and alpha (FP32 in the FP32 pass, with
+// FP32 copies of the weights); the slices' sums and (G^T G)^-1 are FP64.
+template <int VMODE, typename L>
 __global__ void __launch_bounds__(256) k_proj_g(const int64_t *range, const int32_t *fco, const int64_t *rows,
-                                                const double *w, const double *v, const double *q,
-                                                const double *eta, double *gpart, double *gsum, const double *GtGinv,
-                                                int nco, double *alpha, int R, unsigned *counter, int psplit,
-                                                int fused) {
+                                                const L *w, const L *v, const L *q, const L *eta, double *gpart,
+                                                double *gsum, const double *GtGinv, int nco, L *alpha, int R,
+                                                unsigned *counter, int psplit, int fused) {
     constexpr int lam_mode = VMODE != PG_U;
     extern __shared__ double gs_dyn[];
-    __shared__ double red[8][3];
+    __shared__ L red[8][3];
     const int f = blockIdx.x, c = blockIdx.z;
     const int64_t e0 = range[4 * f + (lam_mode ? 0 : 2)], e1 = range[4 * f + (lam_mode ? 1 : 3)];
     const int co_off = fco[2 * f], nq = fco[2 * f + 1];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t chunk = (e1 - e0 + psplit - 1) / psplit;
     const int64_t l0 = e0 + blockIdx.y * chunk, l1 = min(e1, l0 + chunk);
-    double acc[3] = {0, 0, 0};
-    const double eta_c = VMODE == PG_LAM_R ? eta[c] : 0.0;
+    L acc[3] = {0, 0, 0};
+    const L eta_c = VMODE == PG_LAM_R ? eta[c] : L(0);
     for (int64_t e = l0 + threadIdx.x; e < l1; e += blockDim.x) {
-        double x;
+        L x;
         if (VMODE == PG_U) x = v[e * R + c];
         else if (VMODE == PG_LAM) x = v[rows[e] * R + c];
         else x = r_next(v[rows[e] * R + c], q[rows[e] * R + c], eta_c);
@@ -727,9 +790,9 @@ __global__ void __launch_bounds__(256) k_proj_g(const int64_t *range, const int3
         for (int q = 0; q < 3; ++q) red[warp][q] = acc[q];
     __syncthreads();
     if (threadIdx.x < nq) {
-        double x = 0;
+        L x = 0;
         for (int ww = 0; ww < 8; ++ww) x += red[ww][threadIdx.x];
-        gpart[((int64_t)(co_off + threadIdx.x) * psplit + blockIdx.y) * R + c] = x;
+        gpart[((int64_t)(co_off + threadIdx.x) * psplit + blockIdx.y) * R + c] = (double)x;
     }
     if (!fused) return;
     if (!arrive_last(counter)) return;
@@ -745,7 +808,7 @@ __global__ void __launch_bounds__(256) k_proj_g(const int64_t *range, const int3
         const int i = t / R, cc = t % R;
         double a = 0;
         for (int j = 0; j < nco; ++j) a += GtGinv[(int64_t)i * nco + j] * gs[(int64_t)j * R + cc];
-        alpha[t] = a;
+        alpha[t] = (L)a;
     }
     if (threadIdx.x == 0) *counter = 0u;
 }
@@ -753,8 +816,9 @@ __global__ void __launch_bounds__(256) k_proj_g(const int64_t *range, const int3
 // alpha[i][c] = sum_j (G^T G)^-1[i][j] (G^T v)[j][c], G^T v summed from the psplit slices of
 // k_proj_g: one warp per (i, c), lanes over j (fixed order: per lane ascending, then the warp
 // tree).  Grid (ceil(n_co / 8), R), 256 threads.
+template <typename L>
 __global__ void __launch_bounds__(256) k_coarse_solve(const double *gpart, int psplit, const double *GtGinv, int nco,
-                                                      double *alpha, int R) {
+                                                      L *alpha, int R) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int i = blockIdx.x * 8 + warp, c = blockIdx.y;
     if (i >= nco) return;
@@ -765,7 +829,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(const double *gpart, int p
         a += GtGinv[(int64_t)i * nco + j] * g;
     }
     a = warp_sum(a);
-    if (lane == 0) alpha[(int64_t)i * R + c] = a;
+    if (lane == 0) alpha[(int64_t)i * R + c] = (L)a;
 }
 
 // refinement update u += du with corr = max |du| / max |u| per column: grid (row blocks,
@@ -1157,6 +1221,8 @@ struct Runner {
         S.active = ib; S.iters = ib + R; S.n_active = ib + 2 * R; S.loops = ib + 2 * R + 1;
         S.counter = reinterpret_cast<unsigned *>(ib + 2 * R + 2);
         S.err = ib + 2 * R + 3;
+        float *fb = reinterpret_cast<float *>(ib + 2 * R + 8);
+        S.eta_f = fb; S.beta_f = fb + R; S.xscale_f = fb + 2 * R;
         sd = p->d_sd.as<SubdomainDesc>();
         set_attributes();
     }
@@ -1243,28 +1309,63 @@ struct Runner {
         if (clear) drop(v);
     }
 
-    // alpha = (G^T G)^-1 Z^T B^T v  (or (G^T G)^-1 Z^T v for v in U)
-    // alpha = (G^T G)^-1 G^T v: v on U (PG_U), on Lambda (PG_LAM) or r_new = v - eta q (PG_LAM_R)
-    void coarse_alpha(const double *v, int vmode, const double *q = nullptr) {
+    // The arithmetic type L of the Lambda vectors: FP64, or FP32 in the PCG iterations of the
+    // FP32 pass, which read FP32 copies of the weights of G, G^T and B_D.
+    template <typename L> static const L *wt(const DevMem &d64, const DevMem &d32) {
+        if constexpr (std::is_same<L, float>::value) return d32.as<float>();
+        else return d64.as<double>();
+    }
+    template <typename L> const L *eta_ptr() const {
+        if constexpr (std::is_same<L, float>::value) return S.eta_f;
+        else return S.eta;
+    }
+    template <typename L> const L *beta_ptr() const {
+        if constexpr (std::is_same<L, float>::value) return S.beta_f;
+        else return S.beta;
+    }
+    template <typename L> const L *xscale_ptr() const {
+        if constexpr (std::is_same<L, float>::value) return S.xscale_f;
+        else return ws.xscale.as<double>();
+    }
+    // the PCG vectors of the iterations (r, w, z, y, p, q, lambda) in L
+    template <typename L> struct LamVecs { L *r, *w, *z, *y, *pv, *q, *lam; };
+    template <typename L> LamVecs<L> lam_vecs() {
+        if constexpr (std::is_same<L, float>::value) {
+            const int64_t n = std::max<int64_t>(1, p->n_lambda) * R;
+            float *b = ws.lamf.as<float>();
+            return {b, b + n, b + 2 * n, b + 3 * n, b + 4 * n, b + 5 * n, b + 6 * n};
+        } else {
+            return {ws.r.as<double>(), ws.w.as<double>(), ws.z.as<double>(), ws.y.as<double>(), ws.pv.as<double>(),
+                    ws.q.as<double>(), ws.dlam.as<double>()};
+        }
+    }
+
+    // alpha = (G^T G)^-1 G^T v: v on U (PG_U, FP64), on Lambda (PG_LAM) or r_new = v - eta q
+    // (PG_LAM_R); alpha in L
+    template <typename L> void coarse_alpha(const L *v, int vmode, const L *q = nullptr) {
         const bool fused = p->n_co <= kCoarseFusedMax;
         const int psplit = fused ? PSPLIT : 1;
         const size_t gs_bytes = sizeof(double) * (size_t)p->n_co * R;
         const bool in_smem = fused && gs_bytes <= 32768;
-        auto go = [&](auto kern) {
+        L *alpha = ws.alpha.as<L>();
+        auto go = [&](auto kern, const L *w) {
             kern<<<dim3(p->n_floating, psplit, R), 256, in_smem ? gs_bytes : 0, st>>>(
-                p->d_gt_range.as<int64_t>(), p->d_gt_co.as<int32_t>(), p->d_gt_rows.as<int64_t>(),
-                vmode == PG_U ? p->d_Z.as<double>() : p->d_gt_w.as<double>(), v, q, S.eta, ws.gco.as<double>(),
-                in_smem ? nullptr : ws.gsum.as<double>(), p->d_GtGinv.as<double>(), p->n_co, ws.alpha.as<double>(), R,
-                S.counter, psplit, fused ? 1 : 0);
+                p->d_gt_range.as<int64_t>(), p->d_gt_co.as<int32_t>(), p->d_gt_rows.as<int64_t>(), w, v, q,
+                eta_ptr<L>(), ws.gco.as<double>(), in_smem ? nullptr : ws.gsum.as<double>(), p->d_GtGinv.as<double>(),
+                p->n_co, alpha, R, S.counter, psplit, fused ? 1 : 0);
         };
-        if (vmode == PG_U) go(k_proj_g<PG_U>);
-        else if (vmode == PG_LAM) go(k_proj_g<PG_LAM>);
-        else go(k_proj_g<PG_LAM_R>);
+        if (vmode == PG_U) {
+            if constexpr (std::is_same<L, double>::value) go(k_proj_g<PG_U, double>, p->d_Z.as<double>());
+            else fail(NLFETI_E_INVALID, "the U-space coarse gather runs in FP64");
+        } else if (vmode == PG_LAM) {
+            go(k_proj_g<PG_LAM, L>, wt<L>(p->d_gt_w, p->d_gt_w32));
+        } else {
+            go(k_proj_g<PG_LAM_R, L>, wt<L>(p->d_gt_w, p->d_gt_w32));
+        }
         note_launch();
         if (!fused) {
-            k_coarse_solve<<<dim3((p->n_co + 7) / 8, R), 256, 0, st>>>(ws.gco.as<double>(), psplit,
-                                                                      p->d_GtGinv.as<double>(), p->n_co,
-                                                                      ws.alpha.as<double>(), R);
+            k_coarse_solve<L><<<dim3((p->n_co + 7) / 8, R), 256, 0, st>>>(ws.gco.as<double>(), psplit,
+                                                                         p->d_GtGinv.as<double>(), p->n_co, alpha, R);
             note_launch();
         }
     }
@@ -1283,12 +1384,12 @@ struct Runner {
     }
 
     // out = P v with the PCG dot product of MODE fused in (CHECK: (out, out); BETA: (out, other))
-    template <int MODE> void project_dot(const double *v, const double *other, double *out, double tol = 0,
-                                         int max_it = 0) {
+    template <int MODE, typename L> void project_dot(const L *v, const L *other, L *out, double tol = 0,
+                                                     int max_it = 0) {
         const int64_t nl = p->n_lambda;
-        if (p->n_co > 0) coarse_alpha(v, PG_LAM);
-        k_project_dot<MODE><<<tile_blocks(nl), RED_THREADS, 0, st>>>(
-            p->d_Gcol.as<int32_t>(), p->d_Gval.as<double>(), p->gw, p->n_co > 0 ? ws.alpha.as<double>() : nullptr, v,
+        if (p->n_co > 0) coarse_alpha<L>(v, PG_LAM);
+        k_project_dot<MODE, L><<<tile_blocks(nl), RED_THREADS, 0, st>>>(
+            p->d_Gcol.as<int32_t>(), wt<L>(p->d_Gval, p->d_Gval32), p->gw, p->n_co > 0 ? ws.alpha.as<L>() : nullptr, v,
             other, out, nl, R, ws.partial.as<double>(), S, tol, max_it);
         note_launch();
     }
@@ -1536,21 +1637,22 @@ struct Runner {
     }
 
     // x (apply layout) = B^T v, or B_D^T v with weights
-    template <typename T> void gather_x(const int64_t *ptr, const int64_t *row, const double *val, const double *v, T *x) {
+    template <typename T, typename L>
+    void gather_x(const int64_t *ptr, const int64_t *row, const L *val, const L *v, T *x) {
         const int64_t nu = p->n_u;
         if (R <= GX_MAXR)
-            k_gather_apply_t<T><<<(unsigned)((nu + GX_U - 1) / GX_U), 256, sizeof(double) * GX_U * R, st>>>(
+            k_gather_apply_t<T, L><<<(unsigned)((nu + GX_U - 1) / GX_U), 256, sizeof(double) * GX_U * R, st>>>(
                 ptr, row, val, v, x, sd, p->d_u2sub.as<int32_t>(), nu, R, gate);
         else
-            k_gather_apply<T><<<grid_for(nu * R), 256, 0, st>>>(ptr, row, val, v, x, sd, p->d_u2sub.as<int32_t>(), nu,
-                                                                R, gate);
+            k_gather_apply<T, L><<<grid_for(nu * R), 256, 0, st>>>(ptr, row, val, v, x, sd, p->d_u2sub.as<int32_t>(),
+                                                                   nu, R, gate);
         note_launch();
     }
 
     template <typename T> void applyF(const OpPool<T> &pool, const double *v, double *out, const double *cvec = nullptr) {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         T *x = apply_input<T>(ws);
-        if (nu > 0) gather_x<T>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), nullptr, v, x);
+        if (nu > 0) gather_x<T, double>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), nullptr, v, x);
         symv<T>(pool, 1, x, ws.yU.as<double>());
         k_gather_b<<<grid_for(nl * R), 256, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), ws.yU.as<double>(),
                                                      cvec, out, nl, R);
@@ -1565,61 +1667,72 @@ struct Runner {
                pool.St.p && ws.xhmaps.p;
     }
 
-    template <typename T> void applyMinv(const OpPool<T> &pool, const double *v, double *out, bool precond = false) {
+    // out = M^-1 v (the scaled Dirichlet preconditioner), v and out in L
+    template <typename T, typename L = double>
+    void applyMinv(const OpPool<T> &pool, const L *v, L *out, bool precond = false) {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         T *x = apply_input<T>(ws);
         if (use_mma(pool, precond)) {
             if (nu > 0) {
-                k_gather_apply_f16<<<grid_for(nu * R), 256, 0, st>>>(
-                    p->d_BDt_ptr.as<int64_t>(), p->d_BDt_row.as<int64_t>(), p->d_BDt_val.as<double>(), v,
-                    ws.xscale.as<double>(), ws.xU.as<__half>(), sd, p->d_u2sub.as<int32_t>(), nu, R, gate);
+                k_gather_apply_f16<L><<<grid_for(nu * R), 256, 0, st>>>(
+                    p->d_BDt_ptr.as<int64_t>(), p->d_BDt_row.as<int64_t>(), wt<L>(p->d_BDt_val, p->d_BDt_val32), v,
+                    xscale_ptr<L>(), ws.xU.as<__half>(), sd, p->d_u2sub.as<int32_t>(), nu, R, gate);
                 note_launch();
                 symv_mma(pool, ws.yU.as<double>());
             }
         } else {
-            if (nu > 0) gather_x<T>(p->d_BDt_ptr.as<int64_t>(), p->d_BDt_row.as<int64_t>(), p->d_BDt_val.as<double>(), v, x);
+            if (nu > 0)
+                gather_x<T, L>(p->d_BDt_ptr.as<int64_t>(), p->d_BDt_row.as<int64_t>(),
+                               wt<L>(p->d_BDt_val, p->d_BDt_val32), v, x);
             symv<T>(pool, 0, x, ws.yU.as<double>(), precond);
         }
-        k_gather_bd<<<grid_for(nl * R), 256, 0, st>>>(p->d_BD_ptr.as<int64_t>(), p->d_BD_col.as<int64_t>(),
-                                                      p->d_BD_val.as<double>(), ws.yU.as<double>(), out, nl, R);
-                                                      note_launch();
+        k_gather_bd<L><<<grid_for(nl * R), 256, 0, st>>>(p->d_BD_ptr.as<int64_t>(), p->d_BD_col.as<int64_t>(),
+                                                         wt<L>(p->d_BD_val, p->d_BD_val32), ws.yU.as<double>(), out, nl,
+                                                         R);
+        note_launch();
     }
 
     // One PCG iteration, ten kernels.  The updates of p, lambda and r are stored by the next
     // iteration's k_check_update (kernels before it form p_new and r_new per row), and
-    // k_check_update sets the loop condition inside a graph loop.
+    // k_check_update sets the loop condition inside a graph loop.  The Lambda vectors and their
+    // arithmetic are in the operators' type T: FP64 in the FP64 pass; FP32 in the FP32 pass,
+    // whose iterations only have to reduce the residual by inner_tol (the refinement's FP64
+    // residual corrects what FP32 leaves).  The dot products' tile sums and the PCG scalars are
+    // FP64 in both.
     template <typename T> void iteration(const OpPool<T> &pool, double tol, int max_it) {
+        using L = T;
         const int64_t nl = p->n_lambda, nu = p->n_u;
-        double *r = ws.r.as<double>(), *w = ws.w.as<double>(), *z = ws.z.as<double>(), *y = ws.y.as<double>(),
-               *pv = ws.pv.as<double>(), *q = ws.q.as<double>(), *lam = ws.dlam.as<double>(), *yU = ws.yU.as<double>();
+        const LamVecs<L> v = lam_vecs<L>();
+        const double *yU = ws.yU.as<double>();
         T *x = apply_input<T>(ws);
-        const double *alpha = p->n_co > 0 ? ws.alpha.as<double>() : nullptr;
+        const L *alpha = p->n_co > 0 ? ws.alpha.as<L>() : nullptr;
         // p, lambda, r updated; w = P r, ||w||, stop test
-        if (p->n_co > 0) coarse_alpha(r, PG_LAM_R, q);
+        if (p->n_co > 0) coarse_alpha<L>(v.r, PG_LAM_R, v.q);
         auto check = [&](auto kern) {
-            kern<<<tile_blocks(nl), RED_THREADS, 0, st>>>(p->d_Gcol.as<int32_t>(), p->d_Gval.as<double>(), p->gw, alpha, y,
-                                                          pv, lam, r, q, w, nl, R, ws.partial.as<double>(), S, tol,
-                                                          max_it, cond, max_it + 1);
+            kern<<<tile_blocks(nl), RED_THREADS, 0, st>>>(p->d_Gcol.as<int32_t>(), wt<L>(p->d_Gval, p->d_Gval32), p->gw,
+                                                          alpha, v.y, v.pv, v.lam, v.r, v.q, v.w, nl, R,
+                                                          ws.partial.as<double>(), S, tol, max_it, cond, max_it + 1);
         };
-        if (use_cond) check(k_check_update<1>);
-        else check(k_check_update<0>);
+        if (use_cond) check(k_check_update<1, L>);
+        else check(k_check_update<0, L>);
         note_launch();
         gate = S.n_active;
-        applyMinv<T>(pool, w, z, true);                          // z = M^-1 w
-        project_dot<FIN_BETA>(z, w, y);                          // y = P z, (y, w), beta
+        applyMinv<T, L>(pool, v.w, v.z, true);                   // z = M^-1 w
+        project_dot<FIN_BETA, L>(v.z, v.w, v.y);                 // y = P z, (y, w), beta
         // q = F p_new, (p_new, q), eta
         if (R <= GX_MAXR)
-            k_gather_apply_p_t<T><<<(unsigned)((nu + GX_U - 1) / GX_U), 256, sizeof(double) * GX_U * R, st>>>(
-                p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), pv, y, S.beta, S.active, x, sd,
+            k_gather_apply_p_t<T, L><<<(unsigned)((nu + GX_U - 1) / GX_U), 256, sizeof(double) * GX_U * R, st>>>(
+                p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), v.pv, v.y, beta_ptr<L>(), S.active, x, sd,
                 p->d_u2sub.as<int32_t>(), nu, R, gate);
         else
-            k_gather_apply_p<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(),
-                                                                  pv, y, S.beta, S.active, x, sd,
-                                                                  p->d_u2sub.as<int32_t>(), nu, R, gate);
+            k_gather_apply_p<T, L><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(),
+                                                                     p->d_Bt_row.as<int64_t>(), v.pv, v.y,
+                                                                     beta_ptr<L>(), S.active, x, sd,
+                                                                     p->d_u2sub.as<int32_t>(), nu, R, gate);
         note_launch();
-        symv<T>(pool, 1, x, yU);
-        k_gather_b_eta<<<tile_blocks(nl), RED_THREADS, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), yU, pv, y,
-                                                               q, nl, R, ws.partial.as<double>(), S);
+        symv<T>(pool, 1, x, ws.yU.as<double>());
+        k_gather_b_eta<L><<<tile_blocks(nl), RED_THREADS, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), yU,
+                                                                  v.pv, v.y, v.q, nl, R, ws.partial.as<double>(), S);
         note_launch();
         gate = nullptr;
     }
@@ -1822,10 +1935,17 @@ struct Runner {
             project(ws.d.as<double>(), ws.w.as<double>());
             dot_final<FIN_NPD>(ws.w.as<double>(), ws.w.as<double>(), nl);
             // p, y and q start at zero and FIN_NPD set eta = beta = 0: the updates the first
-            // iteration stores are empty
-            NLF_CUDA(cudaMemsetAsync(ws.pv.p, 0, sizeof(double) * nl * R, st));
-            NLF_CUDA(cudaMemsetAsync(ws.y.p, 0, sizeof(double) * nl * R, st));
-            NLF_CUDA(cudaMemsetAsync(ws.q.p, 0, sizeof(double) * nl * R, st));
+            // iteration stores are empty.  The FP32 pass iterates on FP32 copies of r and lambda.
+            if constexpr (std::is_same<T, float>::value) {
+                const LamVecs<float> v = lam_vecs<float>();
+                k_lam_enter<<<grid_for(nl * R), 256, 0, st>>>(ws.r.as<double>(), lam, v.r, v.lam, v.pv, v.y, v.q,
+                                                              nl * R);
+                note_launch();
+            } else {
+                NLF_CUDA(cudaMemsetAsync(ws.pv.p, 0, sizeof(double) * nl * R, st));
+                NLF_CUDA(cudaMemsetAsync(ws.y.p, 0, sizeof(double) * nl * R, st));
+                NLF_CUDA(cudaMemsetAsync(ws.q.p, 0, sizeof(double) * nl * R, st));
+            }
             const int chunk = 4;
             int done = 0, n_active = R;
             cudaGraphExec_t exec = nullptr;
@@ -1867,6 +1987,11 @@ struct Runner {
             }
             if (exec) NLF_CUDA(cudaGraphExecDestroy(exec));
             drop(graph_slots);
+            if constexpr (std::is_same<T, float>::value) {
+                const LamVecs<float> v = lam_vecs<float>();
+                k_lam_exit<<<grid_for(nl * R), 256, 0, st>>>(v.lam, v.r, lam, ws.r.as<double>(), nl * R);
+                note_launch();
+            }
             // alpha from the PCG residual r = d - F lambda, kept current by the recurrence
             // (eq. forAlpha); u_G = S^+ (fU - B^T lambda) - Z alpha  (eq. forU)
             k_gather_sub_apply<T><<<grid_for(nu * R), 256, 0, st>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(),
@@ -2107,7 +2232,8 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     A(gco, nco * PSPLIT); A(gsum, nco); A(alpha, nco);
     alloc(partial, sizeof(double) * std::max(RED_BLOCKS, TILE_MAX_BLOCKS) * R);
     alloc(partial2, sizeof(double) * std::max(RED_BLOCKS, TILE_MAX_BLOCKS) * R);
-    alloc(scal, sizeof(double) * R * 7 + sizeof(int) * (2 * R + 8));
+    alloc(scal, sizeof(double) * R * 7 + sizeof(int) * (2 * R + 8) + sizeof(float) * 3 * R);
+    alloc(lamf, sizeof(float) * 7 * nl * R);
     alloc(slot_flags, sizeof(int) * kSlotFlags);
     alloc(frozen, sizeof(int) * R);
     if (alloc_stream) NLF_CUDA(cudaStreamSynchronize(alloc_stream));

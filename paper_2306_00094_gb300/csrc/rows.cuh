@@ -270,14 +270,15 @@ __global__ void __launch_bounds__(256, 2) k_rows(const MT *base, int use_sp, con
 
 // x (apply layout) = B^T v, or B_D^T v when val is given (CSR per U dof; B^T rows signed r+1 /
 // -(r+1)); consecutive threads take consecutive U dofs of one column (coalesced stores)
-template <typename T>
-__global__ void k_gather_apply(const int64_t *ptr, const int64_t *row, const double *val, const double *v, T *x,
+// (the sums in the type L of the Lambda vectors)
+template <typename T, typename L>
+__global__ void k_gather_apply(const int64_t *ptr, const int64_t *row, const L *val, const L *v, T *x,
                                const SubdomainDesc *sd, const int32_t *u2sub, int64_t nu, int R, const int *gate) {
     if (gate && *gate == 0) return;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(t / nu);
         const int64_t u = t % nu;
-        double s = 0;
+        L s = 0;
         if (val) {
             for (int64_t q = ptr[u]; q < ptr[u + 1]; ++q) s += val[q] * v[row[q] * R + c];
         } else {

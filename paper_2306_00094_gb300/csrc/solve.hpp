@@ -27,6 +27,7 @@ struct SolveWS {
     uint64_t prob_uid = 0;
     int R = 0;
     DevMem lam, r, w, z, y, pv, q, d, cvec, dlam;      // Lambda space (FP64)
+    DevMem lamf;                                        // r, w, z, y, p, q, lambda of the FP32 pass (FP32)
     DevMem fU, yU, uU, xU;                              // U space (xU: apply input, FP64 and FP16 layouts)
     DevMem xP;                                          // FP32 apply input, paired layout (apply_paired_index)
     DevMem xmaps[2];                                    // tensor maps of xU per subdomain (FP32, FP64),

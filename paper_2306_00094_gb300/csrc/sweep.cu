@@ -703,6 +703,18 @@ __global__ void k_gather_vals(const int64_t *src_idx, const double *src, double 
         dst[i] = src[src_idx[i]];
 }
 
+__global__ void k_round_f32(const double *src, float *dst, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+// dst = src (n doubles) rounded to FP32: the weights the FP32 PCG iterations read
+void f32_copy(nlfeti_ctx *c, DevMem &dst, const DevMem &src, int64_t n) {
+    dst.alloc(c, sizeof(float) * std::max<int64_t>(1, n));
+    if (n > 0) k_round_f32<<<256, 256, 0, c->stream>>>(src.as<double>(), dst.as<float>(), n);
+    NLF_CUDA(cudaGetLastError());
+}
+
 }  // namespace
 
 void setup_coarse(nlfeti_problem *p) {
@@ -761,6 +773,7 @@ void setup_coarse(nlfeti_problem *p) {
             k_gt_entries<<<256, 256, 0, c->stream>>>(p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(),
                                                      p->d_Z.as<double>(), p->n_u, p->d_gt_rows.as<int64_t>(),
                                                      p->d_gt_w.as<double>());
+        f32_copy(c, p->d_gt_w32, p->d_gt_w, p->n_u > 0 ? 3 * ne : 0);
     }
     p->gw = 2 * max_nco;
     p->d_Gcol.alloc(c, sizeof(int32_t) * std::max<int64_t>(1, p->n_lambda * p->gw));
@@ -769,6 +782,7 @@ void setup_coarse(nlfeti_problem *p) {
         k_g_rows<<<256, 256, 0, c->stream>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), p->n_lambda,
                                              p->d_u2sub.as<int32_t>(), p->d_sd.as<SubdomainDesc>(), p->d_Z.as<double>(),
                                              p->gw, p->d_Gcol.as<int32_t>(), p->d_Gval.as<double>());
+    f32_copy(c, p->d_Gval32, p->d_Gval, (p->gw > 0 && p->n_lambda > 0) ? p->n_lambda * p->gw : 0);
     p->d_GtGinv.alloc(c, sizeof(double) * std::max(1, nco * nco));
     if (nco > 0) {
         if (nco > kMaxCoarse) fail(NLFETI_E_INVALID, "more than 12288 coarse columns");
@@ -854,6 +868,7 @@ void setup_jump_weights(nlfeti_problem *p) {
             p->d_BD_val.as<double>(), p->d_flag.as<int>() + 1);
         NLF_CUDA(cudaGetLastError());
     }
+    f32_copy(c, p->d_BD_val32, p->d_BD_val, nblk > 0 ? bd_ptr[nl] : 0);
     // transpose CSR (per U dof: rows and value positions)
     std::vector<int64_t> t_ptr(p->n_u + 1, 0), t_row, t_src;
     for (int64_t i = 0; i < (int64_t)bd_col.size(); ++i) t_ptr[bd_col[i] + 1]++;
@@ -880,6 +895,7 @@ void setup_jump_weights(nlfeti_problem *p) {
                                                   p->d_BDt_val.as<double>(), (int64_t)t_src.size());
         NLF_CUDA(cudaGetLastError());
     }
+    f32_copy(c, p->d_BDt_val32, p->d_BDt_val, (int64_t)t_src.size());
     NLF_CUDA(cudaStreamSynchronize(c->stream));
 }
 
