@@ -120,7 +120,12 @@ typedef struct {
  *          Omega sweep only (the default), 0 = on the FP32 pipes only.  The tensor cores
  *          accumulate with truncation: in the sweep of the pinned S_k (the pseudo-inverse S_k^+)
  *          that error costs the mixed path's refinement an extra sweep on some problems, in the
- *          Omega sweep it does not; all settings meet the same tolerances.  Read by nlfeti_factor. */
+ *          Omega sweep it does not; all settings meet the same tolerances.  Read by nlfeti_factor.
+ * residual_format (mixed path): how the FP32 factorization keeps A^k for the FP64-accurate
+ *          refinement residual (double-single arithmetic either way) -- 0 = chosen from the
+ *          sparsity of A^k (the default): a CSR when at most an eighth of the dense entries are
+ *          nonzero (kernels of compact support with a horizon of a few mesh sizes), else dense
+ *          pairs streamed in tiles; 1 = dense; 2 = CSR.  Read by nlfeti_factor. */
 typedef struct {
     int precision;
     double tol;
@@ -133,6 +138,7 @@ typedef struct {
     int graph_loop;
     int precond_fp16;
     int factor_tc;
+    int residual_format;
 } nlfeti_options;
 
 typedef struct {
@@ -145,11 +151,14 @@ typedef struct {
                                   request (ms_solve then runs to its result on the host side) */
 } nlfeti_stats;
 
-/* Sizes of a created problem. */
+/* Sizes of a created problem.  residual_nnz: nonzeros of A^k (all subdomains) when the FP32
+ * factorization keeps it as a CSR for the refinement residual (options.residual_format), else
+ * 0 (dense, or the FP32 operators not factored). */
 typedef struct {
     int32_t K, ncomp, n_floating, n_coarse;
     int64_t n_lambda, n_u, sum_nk, sum_nk2, sum_ngamma2;
     int32_t max_nk, max_ngamma;
+    int64_t residual_nnz;
 } nlfeti_info;
 
 /* Default options: FP64 plain, tol 1e-10, max_it 1000, at most 10 refinement sweeps,

@@ -40,7 +40,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_it", C.c_int), ("max_refine", C.c_int),
                 ("inner_tol", C.c_double), ("refine_tol", C.c_double), ("batched", C.c_int),
                 ("hbm_budget", C.c_size_t), ("graph_loop", C.c_int),
-                ("precond_fp16", C.c_int), ("factor_tc", C.c_int)]
+                ("precond_fp16", C.c_int), ("factor_tc", C.c_int), ("residual_format", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -55,7 +55,8 @@ class Stats(C.Structure):
 class Info(C.Structure):
     _fields_ = [("K", C.c_int32), ("ncomp", C.c_int32), ("n_floating", C.c_int32), ("n_coarse", C.c_int32),
                 ("n_lambda", C.c_int64), ("n_u", C.c_int64), ("sum_nk", C.c_int64), ("sum_nk2", C.c_int64),
-                ("sum_ngamma2", C.c_int64), ("max_nk", C.c_int32), ("max_ngamma", C.c_int32)]
+                ("sum_ngamma2", C.c_int64), ("max_nk", C.c_int32), ("max_ngamma", C.c_int32),
+                ("residual_nnz", C.c_int64)]
 
 
 class Profile(C.Structure):

@@ -405,6 +405,7 @@ void nlfeti_default_options(nlfeti_options *o) {
     o->graph_loop = 1;
     o->precond_fp16 = 1;
     o->factor_tc = 2;
+    o->residual_format = 0;
 }
 
 nlfeti_status nlfeti_create(nlfeti_ctx **out, const nlfeti_options *opt, void *cuda_stream,
@@ -607,6 +608,7 @@ nlfeti_status nlfeti_problem_info(const nlfeti_problem *p, nlfeti_info *info) {
     info->sum_ngamma2 = g2;
     info->max_nk = mk;
     info->max_ngamma = mg;
+    info->residual_nnz = (p->op32.ready && p->op32.a_sparse) ? p->op32.a_nnz : 0;
     return NLFETI_OK;
 }
 
@@ -615,6 +617,7 @@ nlfeti_status nlfeti_problem_set_options(nlfeti_problem *p, const nlfeti_options
     if (opt->precision != 0 && opt->precision != 1) return NLFETI_E_INVALID;
     if (opt->precond_fp16 < 0 || opt->precond_fp16 > 2) return NLFETI_E_INVALID;
     if (opt->factor_tc < 0 || opt->factor_tc > 2) return NLFETI_E_INVALID;
+    if (opt->residual_format < 0 || opt->residual_format > 2) return NLFETI_E_INVALID;
     return guarded(p->ctx, [&] {
         p->opt = *opt;
         if (p->opt.precond_fp16 == 2 && p->op32.ready) build_tiled_half(p);

@@ -178,6 +178,11 @@ template <typename T> struct OpPool {   // operators of one precision
     nlf::DevMem Ahi, Alo;                // FP32 pool only: A^k = Ahi + Alo (FP32 pairs, swept-matrix layout),
                                          // for the double-single refinement residual
     nlf::DevMem amaps;                   // FP32 pool only: tensor maps of Ahi and Alo (2 per subdomain)
+    bool a_sparse = false;               // FP32 pool only: A^k kept as a CSR of FP32 pairs instead of
+    int64_t a_nnz = 0;                   // Ahi / Alo (a_nnz entries, at most a third of sum n_k^2)
+    nlf::DevMem Aptr, Aent;              // row pointers (int64, sum n_k + 1) and entries (int4: column
+                                         // position, hi bits, lo bits, 0) of that CSR
+    nlf::DevMem row_u;                   // per subdomain-vector row: U index (Gamma dof) or -1
     nlf::DevMem Sh;                      // FP32 pool only: S_k * hscale in FP16 (preconditioner of the PCG)
     nlf::DevMem hmaps;                   // FP32 pool only: tensor maps of Sh (slot 2k per subdomain)
     double hscale = 1.0;                 // power of two: largest |S_k| entry * hscale in [2^13, 2^14)
@@ -229,6 +234,7 @@ struct nlfeti_problem {
     nlf::DevMem d_Z;                     // (n_u x 3) FP64 kernel basis of floating subdomains
     nlf::DevMem d_Q;                     // (n_u x 3) FP64 orthonormal kernel basis
     nlf::DevMem d_GtGinv;                // n_co x n_co FP64
+    nlf::DevMem d_GtGinv32;              // its FP32 copy, transposed (FP32 PCG iterations)
     // rows of G = B Z: per Lambda row gw slots (coarse column, value), the first gw/2 for the
     // +1 side (Z rows of B_plus), the rest for the -1 side; empty slots have column -1
     int gw = 0;

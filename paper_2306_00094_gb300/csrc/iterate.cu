@@ -126,6 +126,7 @@ __global__ void k_gather_bd(const int64_t *ptr, const int64_t *col, const L *val
 #include "apply_tma.cuh"
 #include "apply_mma.cuh"
 #include "residual_tma.cuh"
+#include "residual_csr.cuh"
 
 __global__ void k_scatter_u(const int64_t *u2v, const double *uU, double *v, int64_t nu, int R) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nu * R; t += (int64_t)gridDim.x * blockDim.x) {
@@ -263,6 +264,7 @@ struct PcgScalars {
     int *loops;            // PCG iterations run by the current graph loop
     int *err;              // set by a device wait that ran out (checked after the solve)
     unsigned *counter;     // arrival counter of the fused reductions (reset by the last block)
+    unsigned *colcnt;      // per column: arrival counters of the per-column coarse solve
 };
 
 enum { FIN_NPD = 0, FIN_CHECK = 1, FIN_BETA = 2, FIN_ETA = 3 };
@@ -334,9 +336,13 @@ __device__ __forceinline__ bool arrive_last(unsigned *counter) {
 // columns took 10 us with the partials row by row, 6 us column by column).
 constexpr int RT = 8;
 constexpr int RSMEM = 2048;             // doubles of tile sums per round (16 KB)
-constexpr int RCOLS = RED_THREADS;      // columns per pass (one accumulating thread each)
+constexpr int TILE_THREADS = 1024;      // threads of a tile-reduction block (one block per SM)
+constexpr int RCOLS = TILE_THREADS;     // columns per pass (one accumulating thread each)
 
-constexpr int TILE_MAX_BLOCKS = 608;    // four CTAs per SM
+// one 1024-thread CTA per SM: the warps of four 256-thread CTAs, a quarter of the partials for
+// the last block to add (measured: the finish with 608 blocks took about 6 us of each fused
+// reduction, its loads in several dependent rounds)
+constexpr int TILE_MAX_BLOCKS = 152;
 inline int tile_blocks(int64_t n) {
     const int64_t nt = (n + RT - 1) / RT;
     return (int)std::max<int64_t>(1, std::min<int64_t>(TILE_MAX_BLOCKS, (nt + 1) / 2));
@@ -361,7 +367,7 @@ __device__ __forceinline__ void tile_reduce(int64_t n, int R, double *partial, F
         for (int64_t tb = t0; tb < t1; tb += rtiles) {
             const int ntl = (int)min((int64_t)rtiles, t1 - tb);
             const int units = ntl * nchunk;
-            for (int ub = warp * upw; ub < units; ub += (RED_THREADS / 32) * upw) {
+            for (int ub = warp * upw; ub < units; ub += (TILE_THREADS / 32) * upw) {
                 const int u = ub + ju;
                 const int tl = u / nchunk, cl = (u % nchunk) * cw + cj;
                 const bool ok = u < units && cl < ncol;
@@ -395,7 +401,7 @@ __device__ void finish_scalars(const double *partial, int nb, int R, PcgScalars 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) n_act = 0;
     __syncthreads();
-    for (int c = warp; c < R; c += RED_THREADS / 32) {
+    for (int c = warp; c < R; c += TILE_THREADS / 32) {
         // the column's nb partials are contiguous: each group of loads reads whole lines, with
         // FIN_GROUP loads of a lane in flight together, added in block order
         const double *pc = partial + (int64_t)c * nb;
@@ -456,7 +462,7 @@ __device__ void finish_scalars(const double *partial, int nb, int R, PcgScalars 
 
 // (a, b) per column with the scalar update of MODE (grid tile_blocks(n))
 template <int MODE>
-__global__ void __launch_bounds__(RED_THREADS) k_dot_final(const double *__restrict__ a, const double *__restrict__ b,
+__global__ void __launch_bounds__(TILE_THREADS) k_dot_final(const double *__restrict__ a, const double *__restrict__ b,
                                                             int64_t n, int R, double *partial, PcgScalars s, double tol,
                                                             int max_it) {
     tile_reduce(n, R, partial, [&](int64_t i, int c) { return a[i * R + c] * b[i * R + c]; });
@@ -477,7 +483,7 @@ template <typename L> __device__ __forceinline__ L r_next(L r, L q, L eta) { ret
 // out = P v = v - G alpha (alpha from k_proj_g; NULL when there is no coarse space), with the
 // dot product of MODE: CHECK (out, out), BETA (out, other).  Grid tile_blocks(nl).
 template <int MODE, typename L>
-__global__ void __launch_bounds__(RED_THREADS) k_project_dot(const int32_t *__restrict__ gcol,
+__global__ void __launch_bounds__(TILE_THREADS) k_project_dot(const int32_t *__restrict__ gcol,
                                                               const L *__restrict__ gval, int gw,
                                                               const L *__restrict__ alpha,
                                                               const L *__restrict__ v,
@@ -497,7 +503,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_project_dot(const int32_t *__re
 // q = B y_U with (p_new, q) and the ETA update (p_new formed per row, stored by the next
 // iteration's k_check_update).  Grid tile_blocks(nl).
 template <typename L>
-__global__ void __launch_bounds__(RED_THREADS) k_gather_b_eta(const int64_t *__restrict__ Bp,
+__global__ void __launch_bounds__(TILE_THREADS) k_gather_b_eta(const int64_t *__restrict__ Bp,
                                                                const int64_t *__restrict__ Bm,
                                                                const double *__restrict__ yU,
                                                                const L *__restrict__ pv,
@@ -522,7 +528,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_gather_b_eta(const int64_t *__r
 // whatever the scalars hold); a separate instantiation, as profilers skip kernels that set
 // graph conditions.
 template <int COND, typename L>
-__global__ void __launch_bounds__(RED_THREADS) k_check_update(const int32_t *__restrict__ gcol,
+__global__ void __launch_bounds__(TILE_THREADS) k_check_update(const int32_t *__restrict__ gcol,
                                                                const L *__restrict__ gval, int gw,
                                                                const L *__restrict__ alpha,
                                                                const L *__restrict__ y, L *__restrict__ pv,
@@ -752,19 +758,37 @@ __global__ void k_stage_rows_x(const double *xa, const double *xb, const Subdoma
 // arrive adds the slices in order (into shared memory when they fit, else gsum) and applies
 // (G^T G)^-1.  Large ones: k_coarse_solve does that over many CTAs (FP64 runs at a small
 // fraction of the FP32 rate here, so one CTA would take ~100 us for n_co = 108 and 16
-// right-hand sides).  psplit and the choice depend on the problem only, so every column is
-// summed in the same order whatever batch it is part of.
+// right-hand sides).  In the FP32 pass the large ones are fused per column instead (fused = 2,
+// one slice): the last of a column's blocks to arrive applies the FP32 copy of (G^T G)^-1,
+// stored transposed (GtGinv32[j n_co + i] = (G^T G)^-1[i][j]), to that column, thread i
+// summing over j in ascending order (n_co^2 FP32 FMAs per column: a few thousand cycles of
+// one SM).  psplit and the choice depend on the problem only, so every column is summed in the
+// same order whatever batch it is part of.
 // v_mode: PG_U v on U; PG_LAM v on Lambda; PG_LAM_R r_new = r - eta q on Lambda (v = r)
 constexpr int PSPLIT = 8;
 constexpr int kCoarseFusedMax = 16;     // n_co up to which the last block of k_proj_g solves
+constexpr int kCoarseColMax = 2048;     // n_co up to which the FP32 pass fuses per column
 enum { PG_U = 0, PG_LAM = 1, PG_LAM_R = 2 };
+
+// true in the last of column c's blocks (gridDim.x gridDim.y of them) to arrive
+__device__ __forceinline__ bool arrive_last_col(unsigned *counters, int c) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&counters[c], 1u) == gridDim.x * gridDim.y - 1;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
 // L: the type of v, q, the weights, the per-block sums and alpha (FP32 in the FP32 pass, with
-// FP32 copies of the weights); the slices' sums and (G^T G)^-1 are FP64.
+// FP32 copies of the weights); the slices' sums and (G^T G)^-1 are FP64 (but for fused = 2).
 template <int VMODE, typename L>
 __global__ void __launch_bounds__(256) k_proj_g(const int64_t *range, const int32_t *fco, const int64_t *rows,
                                                 const L *w, const L *v, const L *q, const L *eta, double *gpart,
                                                 double *gsum, const double *GtGinv, int nco, L *alpha, int R,
-                                                unsigned *counter, int psplit, int fused) {
+                                                unsigned *counter, int psplit, int fused,
+                                                const float *GtGinv32 = nullptr, unsigned *colcnt = nullptr) {
     constexpr int lam_mode = VMODE != PG_U;
     extern __shared__ double gs_dyn[];
     __shared__ L red[8][3];
@@ -795,6 +819,34 @@ __global__ void __launch_bounds__(256) k_proj_g(const int64_t *range, const int3
         gpart[((int64_t)(co_off + threadIdx.x) * psplit + blockIdx.y) * R + c] = (double)x;
     }
     if (!fused) return;
+    if constexpr (std::is_same<L, float>::value) {
+        if (fused == 2) {
+            if (!arrive_last_col(colcnt, c)) return;
+            float *gc = reinterpret_cast<float *>(gs_dyn);       // n_co entries of G^T v, column c
+            for (int j = threadIdx.x; j < nco; j += blockDim.x) {
+                double g = 0;
+                for (int s = 0; s < psplit; ++s) g += __ldcg(gpart + ((int64_t)j * psplit + s) * R + c);
+                gc[j] = (float)g;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < nco; i += blockDim.x) {
+                // j ascending; the loads of 16 consecutive j in flight together
+                float a = 0.0f;
+                int j = 0;
+                for (; j + 16 <= nco; j += 16) {
+                    float gv[16];
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) gv[m] = __ldg(GtGinv32 + (int64_t)(j + m) * nco + i);
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) a = __fmaf_rn(gv[m], gc[j + m], a);
+                }
+                for (; j < nco; ++j) a = __fmaf_rn(__ldg(GtGinv32 + (int64_t)j * nco + i), gc[j], a);
+                alpha[(int64_t)i * R + c] = a;
+            }
+            if (threadIdx.x == 0) colcnt[c] = 0u;
+            return;
+        }
+    }
     if (!arrive_last(counter)) return;
     double *gs = gsum ? gsum : gs_dyn;
     for (int t = threadIdx.x; t < nco * R; t += blockDim.x) {
@@ -1153,10 +1205,31 @@ __global__ void k_cg_output(const double *u, const int8_t *node_dir, int nc, con
 inline int *ws_err(SolveWS &ws, int R) { return reinterpret_cast<int *>(ws.scal.as<double>() + 7 * R) + 2 * R + 3; }
 
 // ws.res = ftil - A^k u - [0; B^T lambda] on every subdomain (double-single, FP32 pool pairs):
-// u is first split into FP32 hi / lo pairs in the padded layout, then the pipeline kernel runs
-void residual_ds(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, const double *lam) {
-    if (p->rsched_ctas == 0) return;
+// u is first split into FP32 hi / lo pairs, then the sparse kernel (A^k kept as a CSR) or the
+// dense pipeline kernel runs.  Returns the number of kernels launched.
+int residual_ds(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, const double *lam) {
     const OpPool<float> &pool = p->op32;
+    if (pool.a_sparse) {
+        const int64_t nrows = p->sum_nk;
+        if (nrows == 0) return 0;
+        const int P = (R + 1) / 2;
+        float2 *uh = reinterpret_cast<float2 *>(ws.uhl.as<float>()), *ul = uh + nrows * P;
+        k_split_u_rows<<<grid_for(nrows * P), 256, 0, st>>>(ws.u.as<double>(), uh, ul, nrows, R);
+        auto go = [&](auto lpr_tag) {
+            constexpr int LPR = decltype(lpr_tag)::value;
+            k_residual_csr<LPR><<<grid_for(nrows * LPR), 256, 0, st>>>(
+                pool.Aptr.as<int64_t>(), pool.Aent.as<int4>(), pool.row_u.as<int32_t>(), uh, ul, ws.ftil.as<double>(),
+                p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), lam, ws.res.as<double>(), nrows, R);
+        };
+        if (P > 16) go(std::integral_constant<int, 32>{});
+        else if (P > 8) go(std::integral_constant<int, 16>{});
+        else if (P > 4) go(std::integral_constant<int, 8>{});
+        else if (P > 2) go(std::integral_constant<int, 4>{});
+        else if (P > 1) go(std::integral_constant<int, 2>{});
+        else go(std::integral_constant<int, 1>{});
+        return 2;
+    }
+    if (p->rsched_ctas == 0) return 0;
     const int R2 = (R + 1) / 2 * 2;
     float *uh = ws.uhl.as<float>(), *ul = uh + std::max<int64_t>(1, p->n_vp) * R2;
     k_split_u<<<dim3(p->K, R2), 256, 0, st>>>(ws.u.as<double>(), p->d_sd.as<SubdomainDesc>(), uh, ul, R);
@@ -1171,6 +1244,7 @@ void residual_ds(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, const d
     else if (R >= 4) go(std::integral_constant<int, 4>{});
     else if (R >= 2) go(std::integral_constant<int, 2>{});
     else go(std::integral_constant<int, 1>{});
+    return 2;
 }
 
 // the interface apply's input buffer of an arithmetic type: FP32 in the paired layout (xP),
@@ -1223,12 +1297,13 @@ struct Runner {
         S.err = ib + 2 * R + 3;
         float *fb = reinterpret_cast<float *>(ib + 2 * R + 8);
         S.eta_f = fb; S.beta_f = fb + R; S.xscale_f = fb + 2 * R;
+        S.colcnt = reinterpret_cast<unsigned *>(fb + 3 * R);
         sd = p->d_sd.as<SubdomainDesc>();
         set_attributes();
     }
 
     template <int MODE> void dot_final(const double *a, const double *b, int64_t n, double tol = 0, int max_it = 0) {
-        k_dot_final<MODE><<<tile_blocks(n), RED_THREADS, 0, st>>>(a, b, n, R, ws.partial.as<double>(), S, tol, max_it);
+        k_dot_final<MODE><<<tile_blocks(n), TILE_THREADS, 0, st>>>(a, b, n, R, ws.partial.as<double>(), S, tol, max_it);
         note_launch();
     }
 
@@ -1344,15 +1419,18 @@ struct Runner {
     // (PG_LAM_R); alpha in L
     template <typename L> void coarse_alpha(const L *v, int vmode, const L *q = nullptr) {
         const bool fused = p->n_co <= kCoarseFusedMax;
+        const bool colfused = std::is_same<L, float>::value && !fused && p->n_co <= kCoarseColMax;
         const int psplit = fused ? PSPLIT : 1;
         const size_t gs_bytes = sizeof(double) * (size_t)p->n_co * R;
         const bool in_smem = fused && gs_bytes <= 32768;
+        const size_t smem = in_smem ? gs_bytes : (colfused ? sizeof(float) * (size_t)p->n_co : 0);
         L *alpha = ws.alpha.as<L>();
         auto go = [&](auto kern, const L *w) {
-            kern<<<dim3(p->n_floating, psplit, R), 256, in_smem ? gs_bytes : 0, st>>>(
+            kern<<<dim3(p->n_floating, psplit, R), 256, smem, st>>>(
                 p->d_gt_range.as<int64_t>(), p->d_gt_co.as<int32_t>(), p->d_gt_rows.as<int64_t>(), w, v, q,
                 eta_ptr<L>(), ws.gco.as<double>(), in_smem ? nullptr : ws.gsum.as<double>(), p->d_GtGinv.as<double>(),
-                p->n_co, alpha, R, S.counter, psplit, fused ? 1 : 0);
+                p->n_co, alpha, R, S.counter, psplit, fused ? 1 : (colfused ? 2 : 0), p->d_GtGinv32.as<float>(),
+                S.colcnt);
         };
         if (vmode == PG_U) {
             if constexpr (std::is_same<L, double>::value) go(k_proj_g<PG_U, double>, p->d_Z.as<double>());
@@ -1363,7 +1441,7 @@ struct Runner {
             go(k_proj_g<PG_LAM_R, L>, wt<L>(p->d_gt_w, p->d_gt_w32));
         }
         note_launch();
-        if (!fused) {
+        if (!fused && !colfused) {
             k_coarse_solve<L><<<dim3((p->n_co + 7) / 8, R), 256, 0, st>>>(ws.gco.as<double>(), psplit,
                                                                          p->d_GtGinv.as<double>(), p->n_co, alpha, R);
             note_launch();
@@ -1388,7 +1466,7 @@ struct Runner {
                                                      int max_it = 0) {
         const int64_t nl = p->n_lambda;
         if (p->n_co > 0) coarse_alpha<L>(v, PG_LAM);
-        k_project_dot<MODE, L><<<tile_blocks(nl), RED_THREADS, 0, st>>>(
+        k_project_dot<MODE, L><<<tile_blocks(nl), TILE_THREADS, 0, st>>>(
             p->d_Gcol.as<int32_t>(), wt<L>(p->d_Gval, p->d_Gval32), p->gw, p->n_co > 0 ? ws.alpha.as<L>() : nullptr, v,
             other, out, nl, R, ws.partial.as<double>(), S, tol, max_it);
         note_launch();
@@ -1709,7 +1787,7 @@ struct Runner {
         // p, lambda, r updated; w = P r, ||w||, stop test
         if (p->n_co > 0) coarse_alpha<L>(v.r, PG_LAM_R, v.q);
         auto check = [&](auto kern) {
-            kern<<<tile_blocks(nl), RED_THREADS, 0, st>>>(p->d_Gcol.as<int32_t>(), wt<L>(p->d_Gval, p->d_Gval32), p->gw,
+            kern<<<tile_blocks(nl), TILE_THREADS, 0, st>>>(p->d_Gcol.as<int32_t>(), wt<L>(p->d_Gval, p->d_Gval32), p->gw,
                                                           alpha, v.y, v.pv, v.lam, v.r, v.q, v.w, nl, R,
                                                           ws.partial.as<double>(), S, tol, max_it, cond, max_it + 1);
         };
@@ -1731,7 +1809,7 @@ struct Runner {
                                                                      p->d_u2sub.as<int32_t>(), nu, R, gate);
         note_launch();
         symv<T>(pool, 1, x, ws.yU.as<double>());
-        k_gather_b_eta<L><<<tile_blocks(nl), RED_THREADS, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), yU,
+        k_gather_b_eta<L><<<tile_blocks(nl), TILE_THREADS, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), yU,
                                                                   v.pv, v.y, v.q, nl, R, ws.partial.as<double>(), S);
         note_launch();
         gate = nullptr;
@@ -2232,7 +2310,7 @@ void SolveWS::ensure(nlfeti_problem *p, int nR) {
     A(gco, nco * PSPLIT); A(gsum, nco); A(alpha, nco);
     alloc(partial, sizeof(double) * std::max(RED_BLOCKS, TILE_MAX_BLOCKS) * R);
     alloc(partial2, sizeof(double) * std::max(RED_BLOCKS, TILE_MAX_BLOCKS) * R);
-    alloc(scal, sizeof(double) * R * 7 + sizeof(int) * (2 * R + 8) + sizeof(float) * 3 * R);
+    alloc(scal, sizeof(double) * R * 7 + sizeof(int) * (2 * R + 8) + sizeof(float) * 3 * R + sizeof(unsigned) * R);
     alloc(lamf, sizeof(float) * 7 * nl * R);
     alloc(slot_flags, sizeof(int) * kSlotFlags);
     alloc(frozen, sizeof(int) * R);
@@ -2301,12 +2379,12 @@ void solve_device(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, int rh
             if (sw == 0) {
                 NLF_CUDA(cudaMemcpyAsync(ws.res.p, ws.ftil.p, sizeof(double) * nv * R, cudaMemcpyDeviceToDevice, st));
             } else {
-                residual_ds(p, ws, st, R, nl > 0 ? ws.lam.as<double>() : nullptr);
+                run.eager_launches += residual_ds(p, ws, st, R, nl > 0 ? ws.lam.as<double>() : nullptr);
                 if (nl > 0)
                     k_constraint_residual<<<grid_for(nl * R), 256, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(),
                                                                             p->d_u2v.as<int64_t>(), ws.u.as<double>(),
                                                                             ws.cvec.as<double>(), nl, R);
-                run.eager_launches += 1 + (nl > 0);
+                run.eager_launches += (nl > 0);
                 if (any_frozen) {
                     NLF_CUDA(cudaMemcpyAsync(ws.frozen.p, frozen.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
                     k_zero_frozen<<<grid_for(nv * R), 256, 0, st>>>(ws.res.as<double>(), nv, R, ws.frozen.as<int>());
@@ -2844,7 +2922,7 @@ template <typename T> void encode_apply_maps(nlfeti_problem *p, OpPool<T> &pool)
         // A^k as FP32 pairs (n_k rows of ld_M) for the refinement residual
         std::vector<CUtensorMap> am(2 * std::max(1, p->K));
         std::memset(am.data(), 0, sizeof(CUtensorMap) * am.size());
-        for (int k = 0; k < p->K; ++k) {
+        for (int k = 0; k < p->K && !pool.a_sparse; ++k) {
             const SubdomainDesc &d = p->sd[k];
             if (d.nk == 0) continue;
             if (encode_apply_map(encode_tiled(), &am[2 * k], pool.Ahi.template as<float>() + d.offM, d.ldM, d.nk, 4, 32,

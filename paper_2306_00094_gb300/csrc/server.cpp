@@ -633,8 +633,8 @@ nlfeti_status nlfeti_submit_mesh(nlfeti_server *s, const nlfeti_mesh *mesh, cons
     h = fnv(h, kf, sizeof(kf));
     h = fnv(h, ki, sizeof(ki));
     const double of[3] = {o.tol, o.inner_tol, o.refine_tol};
-    const int64_t oi[8] = {o.precision, o.max_it, o.max_refine, o.batched, o.graph_loop, o.precond_fp16,
-                           (int64_t)o.hbm_budget, o.factor_tc};
+    const int64_t oi[9] = {o.precision, o.max_it, o.max_refine, o.batched, o.graph_loop, o.precond_fp16,
+                           (int64_t)o.hbm_budget, o.factor_tc, o.residual_format};
     h = fnv(h, of, sizeof(of));
     h = fnv(h, oi, sizeof(oi));
     if (h == 0) h = 1;

@@ -195,6 +195,41 @@ template <typename T> __global__ void k_load_matrix(const double *A, T *Mpool, c
 
 // A^k (FP64) -> hi + lo FP32 pairs in the swept-matrix layout (ld_M, zero padding):
 // hi = fl32(a), lo = fl32(a - hi), so hi + lo equals a to about 2^-48 relative
+// nonzeros per row of A^k (warp per row), at the row's subdomain-vector position
+__global__ void k_row_nnz(const double *A, const SubdomainDesc *sd, int64_t *cnt) {
+    const SubdomainDesc d = sd[blockIdx.y];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int i = blockIdx.x * 8 + warp; i < d.nk; i += gridDim.x * 8) {
+        const double *Ai = A + d.offA + (int64_t)i * d.nk;
+        unsigned n = 0;
+        for (int l = lane; l < d.nk; l += 32) n += Ai[l] != 0.0 ? 1u : 0u;
+        n = __reduce_add_sync(0xffffffffu, n);
+        if (lane == 0) cnt[d.offV + i] = n;
+    }
+}
+
+// the CSR entries of A^k, in ascending column order per row (warp per row, ballot compaction):
+// column position offV + l, hi = A rounded to FP32, lo = the rest rounded to FP32
+__global__ void k_fill_csr(const double *A, const SubdomainDesc *sd, const int64_t *ptr, int4 *ent) {
+    const SubdomainDesc d = sd[blockIdx.y];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int i = blockIdx.x * 8 + warp; i < d.nk; i += gridDim.x * 8) {
+        const double *Ai = A + d.offA + (int64_t)i * d.nk;
+        int64_t base = ptr[d.offV + i];
+        for (int l0 = 0; l0 < d.nk; l0 += 32) {
+            const int l = l0 + lane;
+            const double a = l < d.nk ? Ai[l] : 0.0;
+            const unsigned m = __ballot_sync(0xffffffffu, a != 0.0);
+            if (a != 0.0) {
+                const float h = (float)a;
+                ent[base + __popc(m & ((1u << lane) - 1u))] =
+                    make_int4((int)(d.offV + l), __float_as_int(h), __float_as_int((float)(a - (double)h)), 0);
+            }
+            base += __popc(m);
+        }
+    }
+}
+
 __global__ void k_split_ds(const double *A, float *hi, float *lo, const SubdomainDesc *sd) {
     const SubdomainDesc d = sd[blockIdx.y];
     const int64_t ld = d.ldM;
@@ -475,6 +510,61 @@ void build_tiled_half(nlfeti_problem *p) {
     NLF_CUDA(cudaStreamSynchronize(c->stream));
 }
 
+// The operator of the refinement residual: A^k as a CSR of FP32 pairs when at most an eighth
+// of the dense entries are nonzero (kernels of compact support with a horizon of a few mesh
+// sizes), else dense FP32 pairs in the swept-matrix layout (Ahi, Alo); opt.residual_format 1 / 2
+// forces one of the two.  The crossover: per nonzero the CSR kernel gathers the 8 R bytes of u
+// it multiplies through L1 / L2, where the dense kernel stages u once per 32 rows, and measured
+// about 7.5 times the dense kernel's time per entry.  Depends on A^k and the option only.
+void build_residual_operator(nlfeti_problem *p, OpPool<float> &pool) {
+    nlfeti_ctx *c = p->ctx;
+    const int K = p->K;
+    const int64_t nrows = p->sum_nk;
+    pool.a_sparse = false;
+    pool.a_nnz = 0;
+    pool.Aptr.release();
+    pool.Aent.release();
+    pool.row_u.release();
+    double dense = 0;
+    for (const auto &d : p->sd) dense += (double)d.nk * d.nk;
+    if (nrows > 0 && K > 0) {
+        DevMem cnt;
+        cnt.alloc(c, sizeof(int64_t) * nrows);
+        k_row_nnz<<<dim3(64, K), 256, 0, c->stream>>>(p->d_A.as<double>(), p->d_sd.as<SubdomainDesc>(),
+                                                      cnt.as<int64_t>());
+        NLF_CUDA(cudaGetLastError());
+        std::vector<int64_t> h(nrows), ptr(nrows + 1, 0);
+        NLF_CUDA(cudaMemcpyAsync(h.data(), cnt.p, sizeof(int64_t) * nrows, cudaMemcpyDeviceToHost, c->stream));
+        NLF_CUDA(cudaStreamSynchronize(c->stream));
+        for (int64_t g = 0; g < nrows; ++g) ptr[g + 1] = ptr[g] + h[g];
+        const int64_t nnz = ptr[nrows];
+        const int fmt = p->opt.residual_format;
+        if (fmt == 2 || (fmt == 0 && 8.0 * (double)nnz <= dense)) {
+            upload(c, pool.Aptr, ptr);
+            pool.Aent.alloc(c, sizeof(int4) * std::max<int64_t>(1, nnz));
+            k_fill_csr<<<dim3(64, K), 256, 0, c->stream>>>(p->d_A.as<double>(), p->d_sd.as<SubdomainDesc>(),
+                                                           pool.Aptr.as<int64_t>(), pool.Aent.as<int4>());
+            NLF_CUDA(cudaGetLastError());
+            std::vector<int32_t> ru(nrows, -1);
+            for (const auto &d : p->sd)
+                for (int i = d.nO; i < d.nk; ++i) ru[d.offV + i] = (int32_t)(d.offU + (i - d.nO));
+            upload(c, pool.row_u, ru);
+            NLF_CUDA(cudaStreamSynchronize(c->stream));
+            pool.Ahi.release();
+            pool.Alo.release();
+            pool.a_sparse = true;
+            pool.a_nnz = nnz;
+            return;
+        }
+    }
+    const int64_t poolM = p->poolM;
+    pool.Ahi.alloc(c, sizeof(float) * std::max<int64_t>(poolM, 1));
+    pool.Alo.alloc(c, sizeof(float) * std::max<int64_t>(poolM, 1));
+    k_split_ds<<<dim3(256, std::max(1, K)), 256, 0, c->stream>>>(p->d_A.as<double>(), pool.Ahi.as<float>(),
+                                                                 pool.Alo.as<float>(), p->d_sd.as<SubdomainDesc>());
+    NLF_CUDA(cudaGetLastError());
+}
+
 template <typename T> void factor_ops(nlfeti_problem *p, OpPool<T> &pool) {
     nlfeti_ctx *c = p->ctx;
     const int K = p->K;
@@ -489,12 +579,7 @@ template <typename T> void factor_ops(nlfeti_problem *p, OpPool<T> &pool) {
     NLF_CUDA(cudaMemsetAsync(pool.Sp.p, 0, pool.Sp.bytes, c->stream));
     k_load_matrix<T><<<dim3(256, K), 256, 0, c->stream>>>(p->d_A.as<double>(), pool.M.template as<T>(),
                                                           p->d_sd.as<SubdomainDesc>());
-    if constexpr (std::is_same<T, float>::value) {
-        pool.Ahi.alloc(c, sizeof(float) * std::max<int64_t>(poolM, 1));
-        pool.Alo.alloc(c, sizeof(float) * std::max<int64_t>(poolM, 1));
-        k_split_ds<<<dim3(256, K), 256, 0, c->stream>>>(p->d_A.as<double>(), pool.Ahi.template as<float>(),
-                                                        pool.Alo.template as<float>(), p->d_sd.as<SubdomainDesc>());
-    }
+    if constexpr (std::is_same<T, float>::value) build_residual_operator(p, pool);
     NLF_CUDA(cudaGetLastError());
     std::vector<int64_t> moff(K), soff(K);
     std::vector<int32_t> mdim(K), mld(K), pend(K), gdim(K), gld(K), gend(K);
@@ -703,6 +788,15 @@ __global__ void k_gather_vals(const int64_t *src_idx, const double *src, double 
         dst[i] = src[src_idx[i]];
 }
 
+// dst[j n + i] = src[i n + j] rounded to FP32 (n x n)
+__global__ void k_round_f32_t(const double *src, float *dst, int n) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / n, i = t % n;
+        dst[t] = (float)src[i * n + j];
+    }
+}
+
 __global__ void k_round_f32(const double *src, float *dst, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         dst[i] = (float)src[i];
@@ -811,6 +905,9 @@ void setup_coarse(nlfeti_problem *p) {
         }
         NLF_CUDA(cudaGetLastError());
     }
+    p->d_GtGinv32.alloc(c, sizeof(float) * std::max(1, nco * nco));
+    if (nco > 0) k_round_f32_t<<<256, 256, 0, c->stream>>>(p->d_GtGinv.as<double>(), p->d_GtGinv32.as<float>(), nco);
+    NLF_CUDA(cudaGetLastError());
     NLF_CUDA(cudaStreamSynchronize(c->stream));
 }
 
