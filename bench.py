@@ -466,7 +466,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 operators + f64 vectors/refinement", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32 operators and PCG iterations + f64 refinement", "data": "synthetic",
         "config": config_dict(name, w, info["n_lambda"], info["n_u"], world),
         "parallelism": f"replicas x{world}",
         "latency_ms": {"p50": percentile(lat, 0.5), "p99": percentile(lat, 0.99)},
@@ -779,7 +779,7 @@ def run_serving(args):
     line = {"metric": "serving: FETI requests (mixed kernels, h, delta, K; R in [1, 32]) under Poisson arrivals, "
                       "arrival -> host result latency, 1 GB300",
             "mode": "serving", "value": main_run["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
-            "higher_is_better": True, "data": "synthetic", "dtype": "f32 operators + f64 vectors/refinement",
+            "higher_is_better": True, "data": "synthetic", "dtype": "f32 operators and PCG iterations + f64 refinement",
             "config": {"workload": "serving pool of problems sampled from the grid (seed 6)",
                        "pool": ss.pool_cfg, "slots": args.slots, "hbm_budget_bytes": budget,
                        "rejected_fraction_of_grid_draws": ss.rejected},

@@ -800,13 +800,36 @@ __global__ void __launch_bounds__(256) k_proj_g(const int64_t *range, const int3
     const int64_t l0 = e0 + blockIdx.y * chunk, l1 = min(e1, l0 + chunk);
     L acc[3] = {0, 0, 0};
     const L eta_c = VMODE == PG_LAM_R ? eta[c] : L(0);
-    for (int64_t e = l0 + threadIdx.x; e < l1; e += blockDim.x) {
-        L x;
-        if (VMODE == PG_U) x = v[e * R + c];
-        else if (VMODE == PG_LAM) x = v[rows[e] * R + c];
-        else x = r_next(v[rows[e] * R + c], q[rows[e] * R + c], eta_c);
+    // a thread's entries e0, e0 + 256, ... taken PGU at a time: the loads of PGU entries (row
+    // index, then the gathered value) in flight together, the products added in ascending e
+    constexpr int PGU = 8;
+    for (int64_t e0 = l0 + threadIdx.x; e0 < l1; e0 += PGU * (int64_t)blockDim.x) {
+        int64_t rr[PGU];
+        L xv[PGU];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) acc[q] += w[e * 3 + q] * x;
+        for (int m = 0; m < PGU; ++m) {
+            const int64_t e = e0 + (int64_t)m * blockDim.x;
+            rr[m] = (VMODE != PG_U && e < l1) ? rows[e] : 0;
+        }
+#pragma unroll
+        for (int m = 0; m < PGU; ++m) {
+            const int64_t e = e0 + (int64_t)m * blockDim.x;
+            L x = 0;
+            if (e < l1) {
+                if (VMODE == PG_U) x = v[e * R + c];
+                else if (VMODE == PG_LAM) x = v[rr[m] * R + c];
+                else x = r_next(v[rr[m] * R + c], q[rr[m] * R + c], eta_c);
+            }
+            xv[m] = x;
+        }
+#pragma unroll
+        for (int m = 0; m < PGU; ++m) {
+            const int64_t e = e0 + (int64_t)m * blockDim.x;
+            if (e < l1) {
+#pragma unroll
+                for (int qq = 0; qq < 3; ++qq) acc[qq] += w[e * 3 + qq] * xv[m];
+            }
+        }
     }
 #pragma unroll
     for (int q = 0; q < 3; ++q) acc[q] = warp_sum(acc[q]);
