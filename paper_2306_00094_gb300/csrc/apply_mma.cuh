@@ -34,7 +34,8 @@
 //               columns < R, times oscale / xscale[c] (a power of two formed once per column;
 //               the FP64 pipe of this GPU runs at a small fraction of the FP32 rate, and a division
 //               per entry kept it a third busy: 63.6 -> 37.8 us per apply on the peridynamic
-//               workload once hoisted), applied to the exponent with integer operations.
+//               workload once hoisted), applied to the exponent with integer operations; as
+//               FP64 into y, or (yf given: the FP32 PCG iterations) as FP32 into yf.
 //
 // Every wait is bounded: a wait that runs out sets *err and the abort flag, the other roles
 // stop at their next wait, outstanding copies and MMAs are waited for (bounded), and the
@@ -167,11 +168,22 @@ __device__ __forceinline__ double f2d_pow2(float v, int e, double fac) {
     return __longlong_as_double((long long)d);
 }
 
+// v * 2^e as a float, exactly while the result is a normal float (the exponent field set with
+// integer operations); otherwise ldexpf
+__device__ __forceinline__ float f2f_pow2(float v, int e) {
+    const uint32_t b = __float_as_uint(v);
+    const int ex = (int)((b >> 23) & 0xffu);
+    const int de = ex + e;
+    if (ex == 0 || ex == 0xff || de <= 0 || de >= 255) return ldexpf(v, e);
+    return __uint_as_float((b & 0x807fffffu) | ((uint32_t)de << 23));
+}
+
+// yf: the result stored in FP32 there instead of y (the FP32 PCG iterations)
 template <int NP>
 __global__ void __launch_bounds__(MMA_THREADS, 1)
     k_apply_mma(const __half *St, const CUtensorMap *xmaps, const SubdomainDesc *sd, const int32_t *sched_ptr,
                 const int32_t *sched_items, double *y, int R, const int *gate, int *err, double oscale,
-                const double *xscale) {
+                const double *xscale, float *yf = nullptr) {
     static_assert(NP % 16 == 0 && NP >= 16 && NP <= MMA_MAX_R, "N of the MMA");
     constexpr int MMA_NS = mma_ns(NP);
     constexpr int STAGE = mma_stage_bytes(NP);
@@ -311,10 +323,15 @@ __global__ void __launch_bounds__(MMA_THREADS, 1)
 #pragma unroll
                     for (int c = 0; c < 16; ++c) v[c] += t[c];
                 }
-                if (row < n)
+                if (row < n && yf) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        if (c0 + c < R) yf[(yoff + row) * R + c0 + c] = f2f_pow2(v[c], colexp[c0 + c]);
+                } else if (row < n) {
 #pragma unroll
                     for (int c = 0; c < 16; ++c)
                         if (c0 + c < R) y[(yoff + row) * R + c0 + c] = f2d_pow2(v[c], colexp[c0 + c], colfac[c0 + c]);
+                }
             }
             tc_fence_before();
             mbar_arrive(&tmem_empty[j & 1]);

@@ -198,7 +198,7 @@ __device__ __forceinline__ ApplyItem load_apply_item(const int32_t *sched_items,
 
 // MODE (ROWS_APPLY, ROWS_FORCING, ROWS_BACKSUB) selects the operator block (above), the tensor
 // maps (APPLY: 2 per subdomain, use_sp picks; else 1 per subdomain) and the output:
-//   APPLY     y[(offU + i) R + c] = acc * oscale;
+//   APPLY     y[(offU + i) R + c] = acc * oscale   (FP32 into yf instead when given, T = float);
 //   FORCING   y[(offU + i) R + c] = xa[(offV + n_O + i) R + c] - acc   (reduced forcing, f_G - T_k f_O);
 //   BACKSUB   y[(offV + i) R + c] = -acc                              (u_O from the swept -A_OO^-1 rows),
 // the same outputs, in the same order of operations per lane, as k_rows.
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(apply_threads(RPW), MINB)
     k_apply_tma(const CUtensorMap *maps, const CUtensorMap *xmaps, int use_sp, const SubdomainDesc *sd,
                 const int32_t *sched_ptr, const int32_t *sched_items, double *y, int R, const int *gate, int *err,
                 double oscale = 1.0, const double *xa = nullptr, long long wait_tries = APPLY_WAIT_TRIES,
-                int withhold = 0) {
+                int withhold = 0, float *yf = nullptr) {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
     constexpr int NCW = 32 / RPW;                   // consumer warps (the producer is warp NCW)
@@ -365,7 +365,9 @@ __global__ void __launch_bounds__(apply_threads(RPW), MINB)
                 constexpr int G = 32 / NV;
                 const int idx = lane / G, r = idx / CG, c = g0 + idx % CG, i = ib + rh + r;
                 if (lane % G == 0 && c < rc && i < n) {
-                    if (MODE == ROWS_APPLY) y[(yoff + i) * R + c0 + c] = (double)tot * oscale;
+                    if (MODE == ROWS_APPLY && std::is_same<T, float>::value && yf)
+                        yf[(yoff + i) * R + c0 + c] = (float)tot * (float)oscale;
+                    else if (MODE == ROWS_APPLY) y[(yoff + i) * R + c0 + c] = (double)tot * oscale;
                     else if (MODE == ROWS_FORCING)
                         y[(yoff + i) * R + c0 + c] = xa[(voff + nO + i) * R + c0 + c] - (double)tot;
                     else y[(voff + i) * R + c0 + c] = -(double)tot;

@@ -109,15 +109,15 @@ __global__ void k_constraint_residual(const int64_t *Bp, const int64_t *Bm, cons
     }
 }
 
-// out = B_D y (y an FP64 U vector, the sum in the type L of the Lambda vectors)
+// out = B_D y (y, the sum and out in the type L of the Lambda vectors)
 template <typename L>
-__global__ void k_gather_bd(const int64_t *ptr, const int64_t *col, const L *val, const double *y, L *out, int64_t nl,
+__global__ void k_gather_bd(const int64_t *ptr, const int64_t *col, const L *val, const L *y, L *out, int64_t nl,
                             int R) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl * R; t += (int64_t)gridDim.x * blockDim.x) {
         int64_t r = t / R;
         int c = (int)(t % R);
         L s = 0;
-        for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) s += val[q] * (L)y[col[q] * R + c];
+        for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q) s += val[q] * y[col[q] * R + c];
         out[t] = s;
     }
 }
@@ -505,14 +505,14 @@ __global__ void __launch_bounds__(TILE_THREADS) k_project_dot(const int32_t *__r
 template <typename L>
 __global__ void __launch_bounds__(TILE_THREADS) k_gather_b_eta(const int64_t *__restrict__ Bp,
                                                                const int64_t *__restrict__ Bm,
-                                                               const double *__restrict__ yU,
+                                                               const L *__restrict__ yU,
                                                                const L *__restrict__ pv,
                                                                const L *__restrict__ y, L *__restrict__ q,
                                                                int64_t nl, int R, double *partial, PcgScalars s) {
     const L *beta = beta_of<L>(s);
     tile_reduce(nl, R, partial, [&](int64_t i, int c) {
         const int64_t t = i * R + c;
-        const L x = (L)(yU[Bp[i] * R + c] - yU[Bm[i] * R + c]);
+        const L x = yU[Bp[i] * R + c] - yU[Bm[i] * R + c];
         q[t] = x;
         return p_next(pv[t], y[t], beta[c], s.active[c] != 0) * x;
     });
@@ -1304,6 +1304,9 @@ struct Runner {
     int64_t loop_body_launches = 0;     // kernels per iteration of the last device-side loop
     // the WHILE node of the graph loop being captured (set by k_check_update)
     cudaGraphConditionalHandle cond = 0;
+    // set (FP32 PCG iterations): the interface applies store their results here in FP32 instead
+    // of the FP64 output they are given
+    float *yout_f = nullptr;
     bool use_cond = false;
     int64_t apply_launches = 0, half_launches = 0;
     double apply_ms = 0, apply_bytes = 0, half_ms = 0, half_bytes = 0;
@@ -1499,7 +1502,8 @@ struct Runner {
                                                                          int nitems, const T *x, const double *xa,
                                                                          const double *xb, double *y, double oscale) {
         k_rows<T, RC, MODE, MT><<<nitems, 256, 0, st>>>(base, use_sp, sd, it, x, xa, xb, y, R,
-                                                        MODE == ROWS_APPLY ? gate : nullptr, oscale);
+                                                        MODE == ROWS_APPLY ? gate : nullptr, oscale,
+                                                        MODE == ROWS_APPLY ? yout_f : nullptr);
         note_launch();
     }
 
@@ -1590,7 +1594,8 @@ struct Runner {
             k_apply_tma<T, RCT, NS, MINB, MT, ROWS_APPLY, RPW>
                 <<<ctas, apply_threads(RPW), apply_smem_bytes(RCT, NS, MROW, std::is_same<T, float>::value), st>>>(
                     maps, xm, std::is_same<MT, T>::value ? use_sp : 0, sd, sptr, sitems, y, R, gate, S.err,
-                    std::is_same<MT, T>::value ? 1.0 : 1.0 / pool.hscale, nullptr, wait_tries(), p->dbg_withhold);
+                    std::is_same<MT, T>::value ? 1.0 : 1.0 / pool.hscale, nullptr, wait_tries(), p->dbg_withhold,
+                    yout_f);
         };
         using I1 = std::integral_constant<int, 1>;
         using I2 = std::integral_constant<int, 2>;
@@ -1627,7 +1632,7 @@ struct Runner {
             }
             k_apply_tma<T, RCT><<<ctas, APPLY_THREADS, apply_smem_bytes(RCT, APPLY_NS, APPLY_CB, std::is_same<T, float>::value),
                                   st>>>(pool.maps.template as<CUtensorMap>(), xm, use_sp, sd, sptr, sitems, y, R, gate,
-                                        S.err, 1.0, nullptr, wait_tries(), p->dbg_withhold);
+                                        S.err, 1.0, nullptr, wait_tries(), p->dbg_withhold, yout_f);
         };
         switch (rc) {
             case 16:
@@ -1672,8 +1677,8 @@ struct Runner {
             NLF_CUDA(cudaEventRecordWithFlags(slot.b, st, rec_flags));
             double bytes = 0;
             const double me = half ? 2.0 : (double)sizeof(T);
-            for (const auto &d : p->sd)
-                bytes += (double)d.nG * d.ldG * me + (double)d.nG * R * (sizeof(T) + sizeof(double));
+            const double ob = yout_f ? sizeof(float) : sizeof(double);      // the output's type
+            for (const auto &d : p->sd) bytes += (double)d.nG * d.ldG * me + (double)d.nG * R * (sizeof(T) + ob);
             slot.launches = launches;
             slot.bytes = bytes;
             slot.half = half;
@@ -1702,15 +1707,15 @@ struct Runner {
             switch (mma_np(R)) {
                 case 16:
                     k_apply_mma<16><<<ctas, MMA_THREADS, mma_smem_bytes(16), st>>>(am, xm, sd, sp, si, y, R, gate, S.err,
-                                                                                    osc, xs);
+                                                                                    osc, xs, yout_f);
                     break;
                 case 32:
                     k_apply_mma<32><<<ctas, MMA_THREADS, mma_smem_bytes(32), st>>>(am, xm, sd, sp, si, y, R, gate, S.err,
-                                                                                    osc, xs);
+                                                                                    osc, xs, yout_f);
                     break;
                 default:
                     k_apply_mma<64><<<ctas, MMA_THREADS, mma_smem_bytes(64), st>>>(am, xm, sd, sp, si, y, R, gate, S.err,
-                                                                                    osc, xs);
+                                                                                    osc, xs, yout_f);
                     break;
             }
             note_launch();
@@ -1729,7 +1734,8 @@ struct Runner {
         if (timed) {
             NLF_CUDA(cudaEventRecordWithFlags(slot.b, st, rec_flags));
             double bytes = 0;
-            for (const auto &d : p->sd) bytes += (double)d.nG * d.ldG * 2.0 + (double)d.nG * R * (2.0 + sizeof(double));
+            const double ob = yout_f ? sizeof(float) : sizeof(double);
+            for (const auto &d : p->sd) bytes += (double)d.nG * d.ldG * 2.0 + (double)d.nG * R * (2.0 + ob);
             slot.launches = launches;
             slot.bytes = bytes;
             slot.half = true;
@@ -1773,6 +1779,8 @@ struct Runner {
     void applyMinv(const OpPool<T> &pool, const L *v, L *out, bool precond = false) {
         const int64_t nl = p->n_lambda, nu = p->n_u;
         T *x = apply_input<T>(ws);
+        float *const saved_out = yout_f;
+        yout_f = std::is_same<L, float>::value ? ws.yU.as<float>() : nullptr;   // y_U in L
         if (use_mma(pool, precond)) {
             if (nu > 0) {
                 k_gather_apply_f16<L><<<grid_for(nu * R), 256, 0, st>>>(
@@ -1787,9 +1795,9 @@ struct Runner {
                                wt<L>(p->d_BDt_val, p->d_BDt_val32), v, x);
             symv<T>(pool, 0, x, ws.yU.as<double>(), precond);
         }
+        yout_f = saved_out;
         k_gather_bd<L><<<grid_for(nl * R), 256, 0, st>>>(p->d_BD_ptr.as<int64_t>(), p->d_BD_col.as<int64_t>(),
-                                                         wt<L>(p->d_BD_val, p->d_BD_val32), ws.yU.as<double>(), out, nl,
-                                                         R);
+                                                         wt<L>(p->d_BD_val, p->d_BD_val32), ws.yU.as<L>(), out, nl, R);
         note_launch();
     }
 
@@ -1804,7 +1812,7 @@ struct Runner {
         using L = T;
         const int64_t nl = p->n_lambda, nu = p->n_u;
         const LamVecs<L> v = lam_vecs<L>();
-        const double *yU = ws.yU.as<double>();
+        L *yU = ws.yU.as<L>();          // the applies' output, in L
         T *x = apply_input<T>(ws);
         const L *alpha = p->n_co > 0 ? ws.alpha.as<L>() : nullptr;
         // p, lambda, r updated; w = P r, ||w||, stop test
@@ -1831,7 +1839,9 @@ struct Runner {
                                                                      beta_ptr<L>(), S.active, x, sd,
                                                                      p->d_u2sub.as<int32_t>(), nu, R, gate);
         note_launch();
+        yout_f = std::is_same<L, float>::value ? ws.yU.as<float>() : nullptr;
         symv<T>(pool, 1, x, ws.yU.as<double>());
+        yout_f = nullptr;
         k_gather_b_eta<L><<<tile_blocks(nl), TILE_THREADS, 0, st>>>(p->d_Bp.as<int64_t>(), p->d_Bm.as<int64_t>(), yU,
                                                                   v.pv, v.y, v.q, nl, R, ws.partial.as<double>(), S);
         note_launch();

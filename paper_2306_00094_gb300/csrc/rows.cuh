@@ -169,11 +169,12 @@ __device__ __forceinline__ T warp_reduce_scatter(T (&v)[V], int lane) {
 }
 
 // MT: type of the stored operator (APPLY with the FP16 copy of S_k: __half, the result scaled by
-// oscale); T otherwise
+// oscale); T otherwise.  yf (APPLY, FP32 only): the result stored in FP32 there instead of y
+// (the FP32 PCG iterations; the sums are FP32 either way)
 template <typename T, int RC, int MODE, typename MT = T>
 __global__ void __launch_bounds__(256, 2) k_rows(const MT *base, int use_sp, const SubdomainDesc *sd, const int32_t *items,
                                                  const T *x, const double *xa, const double *xb, double *y, int R,
-                                                 const int *gate, double oscale = 1.0) {
+                                                 const int *gate, double oscale = 1.0, float *yf = nullptr) {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::W;
     constexpr int XS = ROWS_CW + 4;
@@ -260,7 +261,9 @@ __global__ void __launch_bounds__(256, 2) k_rows(const MT *base, int use_sp, con
         const int idx = lane / G, r = idx / RC, c = idx % RC;
         const int i = ib + r;
         if (lane % G == 0 && c < rc && i < n) {
-            if (MODE == ROWS_APPLY) y[(d.offU + i) * R + c0 + c] = (double)tot * oscale;
+            if (MODE == ROWS_APPLY && std::is_same<T, float>::value && yf)
+                yf[(d.offU + i) * R + c0 + c] = (float)tot * (float)oscale;
+            else if (MODE == ROWS_APPLY) y[(d.offU + i) * R + c0 + c] = (double)tot * oscale;
             else if (MODE == ROWS_FORCING)
                 y[(d.offU + i) * R + c0 + c] = xa[(d.offV + d.nO + i) * R + c0 + c] - (double)tot;
             else y[(d.offV + i) * R + c0 + c] = -(double)tot;
