@@ -1236,11 +1236,16 @@ int residual_ds(nlfeti_problem *p, SolveWS &ws, cudaStream_t st, int R, const do
         const int64_t nrows = p->sum_nk;
         if (nrows == 0) return 0;
         const int P = (R + 1) / 2;
+        int sms = 0;
+        NLF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->ctx->device));
         float2 *uh = reinterpret_cast<float2 *>(ws.uhl.as<float>()), *ul = uh + nrows * P;
         k_split_u_rows<<<grid_for(nrows * P), 256, 0, st>>>(ws.u.as<double>(), uh, ul, nrows, R);
         auto go = [&](auto lpr_tag) {
             constexpr int LPR = decltype(lpr_tag)::value;
-            k_residual_csr<LPR><<<grid_for(nrows * LPR), 256, 0, st>>>(
+            // one CTA per SM, each over a contiguous range of rows
+            const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(sms, (nrows * LPR + RES_CSR_THREADS - 1) /
+                                                                                 RES_CSR_THREADS));
+            k_residual_csr<LPR><<<ctas, RES_CSR_THREADS, 0, st>>>(
                 pool.Aptr.as<int64_t>(), pool.Aent.as<int4>(), pool.row_u.as<int32_t>(), uh, ul, ws.ftil.as<double>(),
                 p->d_Bt_ptr.as<int64_t>(), p->d_Bt_row.as<int64_t>(), lam, ws.res.as<double>(), nrows, R);
         };

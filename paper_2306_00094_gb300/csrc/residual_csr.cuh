@@ -16,8 +16,10 @@
 // two sums added in FP64.  Here one lane owns one (row, column pair) and runs over the row's
 // entries in order: two right-hand sides per instruction (the float2 operations, each element
 // rounded as the scalar operation), no cross-lane reduction.  A warp takes 32 / LPR
-// consecutive rows with LPR lanes each (LPR = column pairs per pass, a power of two up to 32),
-// so that the rows of a block share most of their columns in L1.  u is read as hi / lo FP32
+// consecutive rows with LPR lanes each (LPR = column pairs per pass, a power of two up to 32).
+// One 1024-thread CTA per SM walks a contiguous range of rows, 32 * 32 / LPR rows at a time, so
+// that the u entries of neighbouring rows (the columns their horizons share) stay in L1 from
+// one step to the next.  u is read as hi / lo FP32
 // pairs with the right-hand sides of a row consecutive (k_split_u_rows); every (row, column)
 // is computed by the same operations whatever the number of right-hand sides.
 #pragma once
@@ -45,8 +47,10 @@ __device__ __forceinline__ void csr_entry(const int4 &e, int &col, float &hi, fl
 }
 
 // row_u[g]: the U index of row g (a Gamma dof) or -1 (an Omega dof)
+constexpr int RES_CSR_THREADS = 1024;
+
 template <int LPR>
-__global__ void __launch_bounds__(256) k_residual_csr(const int64_t *__restrict__ rowptr, const int4 *__restrict__ ent,
+__global__ void __launch_bounds__(RES_CSR_THREADS) k_residual_csr(const int64_t *__restrict__ rowptr, const int4 *__restrict__ ent,
                                                       const int32_t *__restrict__ row_u, const float2 *__restrict__ uh,
                                                       const float2 *__restrict__ ul, const double *__restrict__ f,
                                                       const int64_t *__restrict__ bt_ptr,
@@ -55,11 +59,12 @@ __global__ void __launch_bounds__(256) k_residual_csr(const int64_t *__restrict_
     constexpr int RPW = 32 / LPR;
     const int lane = threadIdx.x & 31, sub = lane / LPR, lp = lane % LPR;
     const int P = (R + 1) / 2;
-    const int64_t warp_g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-    const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
-    for (int64_t g0 = warp_g * RPW; g0 < nrows; g0 += nwarps * RPW) {
+    const int64_t chunk = (nrows + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(nrows, r0 + chunk);
+    const int warp = threadIdx.x / 32, nw = blockDim.x / 32;
+    for (int64_t g0 = r0 + (int64_t)warp * RPW; g0 < r1; g0 += (int64_t)nw * RPW) {
         const int64_t g = g0 + sub;
-        if (g >= nrows) continue;
+        if (g >= r1) continue;
         const int64_t t0 = rowptr[g], t1 = rowptr[g + 1];
         for (int p0 = 0; p0 < P; p0 += LPR) {
             const int q = p0 + lp;
