@@ -83,8 +83,11 @@ size_t predict_ws_bytes(const nlfeti_problem *p, int R) {
                  nv = (size_t)std::max<int64_t>(p->sum_nk, 1), nd = (size_t)std::max<int64_t>(p->n_dofs_total, 1),
                  nup = (size_t)std::max<int64_t>(p->n_up, 1), nvp = (size_t)std::max<int64_t>(p->n_vp, 1);
     // Lambda (10), U (3) and subdomain (4) vectors, the apply and residual inputs, the forcing
-    // right-hand sides, the load vector, and the input / output / Dirichlet staging (3 n_dofs)
-    return sizeof(double) * (size_t)R * (10 * nl + 3 * nu + nup + 4 * nv + 2 * nvp + 4 * nd) + (size_t(2) << 20);
+    // right-hand sides, the load vector, and the input / output / Dirichlet staging (3 n_dofs);
+    // in FP32: the 7 Lambda vectors of the FP32 PCG iterations and the paired apply input
+    const size_t nxp = (size_t)std::max<int64_t>(p->n_xp, 1), R2 = (size_t)(R + 1) / 2 * 2;
+    return sizeof(double) * (size_t)R * (10 * nl + 3 * nu + nup + 4 * nv + 2 * nvp + 4 * nd) +
+           sizeof(float) * (7 * nl * (size_t)R + nxp * R2) + (size_t(2) << 20);
 }
 
 // Right-hand-side counts are rounded up to a few bucket sizes (the extra columns are zero and
