@@ -506,6 +506,10 @@ size_t problem_bytes(const Decomp &d, int64_t n_nodes, int mask) {
     if (mask & 2) b += 4.0 * scr;
     b += 4.0 * (double)K * (double)n_nodes;                               // node -> subdomain-local maps
     b += 64.0 * sum_nk;                                                   // index maps, vectors, tensor maps
+    // (G^T G)^-1 in FP64 and its FP32 copy, at most every subdomain floating (1 kernel vector
+    // per scalar subdomain, 3 rigid modes per 2-D peridynamic one)
+    const double nco = (double)K * (nc == 1 ? 1 : 3);
+    b += 8.0 * nco * nco + ((mask & 2) ? 4.0 * nco * nco : 0.0);
     return (size_t)(b * 1.05) + (size_t(16) << 20);
 }
 
